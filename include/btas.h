@@ -1,0 +1,197 @@
+/*
+ * btas.h -- C ABI of the GB300 (sm_103a) Basic Tropical Algebra Subroutines.
+ *
+ * Tropical semirings (Sec. I): max-plus, x (+) y = max(x, y), x (.) y = x + y
+ * (Eq. 1-2), and min-plus, x (+) y = min(x, y), x (.) y = x + y (Eq. 3-4).
+ * The library offers the "standard vector and matrix operations" of the
+ * abstract and Sec. III in the BLAS style the paper takes as its model
+ * (Related Work), plus all-pairs shortest paths by repeated squaring of the
+ * weighted adjacency matrix (Sec. III).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are dense and row-major (the paper indexes a[x][y] and
+ *    a*M+b, Algorithms 2 and 3); leading dimensions are in elements.
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *    argument's description says "host".  The library never frees a caller's
+ *    pointer.  Temporary device workspace is taken from the stream-ordered
+ *    allocator (cudaMallocAsync on `stream`) and released on the same stream.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All work is enqueued asynchronously on it; a call returns once
+ *    the work is enqueued, except where an out-parameter needs a device
+ *    result (documented per call), in which case the call synchronises
+ *    `stream`.
+ *  - Argument errors are detected on the host before anything is enqueued
+ *    and return BTAS_ERR_ARG (nothing is written).  A failed CUDA call returns
+ *    BTAS_ERR_CUDA.  btas_last_error_string() describes the most recent
+ *    failure of the calling thread.
+ *
+ * Integer encoding of "no edge" / the semiring zero
+ *  The paper marks a missing edge with 0 (Algorithm 2) or -1 (Algorithm 3);
+ *  this library uses a dedicated value instead:
+ *    BTAS_INF_I32  = 0x3FFFFFFF   min-plus (+)-identity, absorbing for (.)
+ *    BTAS_NINF_I32 = -0x3FFFFFFF  max-plus (+)-identity, absorbing for (.)
+ *  Finite int32 operands must lie in [-BTAS_I32_FINITE_MAX, BTAS_I32_FINITE_MAX]
+ *  (2^28).  Then every sum of two operands fits in int32, and a result equal
+ *  to or beyond BTAS_INF_I32 - 2^28 (resp. below -(BTAS_INF_I32 - 2^28)) can
+ *  only come from an INF term and is stored as BTAS_INF_I32
+ *  (BTAS_NINF_I32).  Finite results are exact.
+ *  The 16-bit storage type (BTAS_U16) holds min-plus values in [0, 0x7FFF];
+ *  BTAS_INF_U16 = 0x7FFF is INF and every result saturates at it.
+ *  FP32 uses IEEE +inf (min-plus) / -inf (max-plus); each term a + b is one
+ *  round-to-nearest-even add, so results are independent of summation order
+ *  and bit-exact.  NaN, -inf in min-plus and +inf in max-plus operands are
+ *  outside the domain.
+ */
+#ifndef BTAS_H
+#define BTAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BTAS_INF_I32 0x3FFFFFFF
+#define BTAS_NINF_I32 (-0x3FFFFFFF)
+#define BTAS_I32_FINITE_MAX (1 << 28)
+#define BTAS_INF_U16 0x7FFF
+
+/* Semiring selector; may be OR-ed with the BTAS_GEMM_* flags below. */
+typedef enum {
+    BTAS_MINPLUS = 0, /* Eq. 3-4 */
+    BTAS_MAXPLUS = 1  /* Eq. 1-2 */
+} btas_semiring;
+
+/* Flags OR-ed into the semiring argument of btas_gemm. */
+#define BTAS_GEMM_ACCUMULATE 0x100 /* C <- C (+) A (.) B, the paper's Z <- Z (+) X (.) Y */
+#define BTAS_GEMM_TRANS_B 0x200    /* B is given transposed: an n x k row-major matrix */
+#define BTAS_GEMM_NO_CARRIER 0x400 /* int32: never use the exact FP32-carrier path */
+
+typedef enum {
+    BTAS_I32 = 0, /* int32, encoding above */
+    BTAS_F32 = 1, /* IEEE binary32 */
+    BTAS_U16 = 2  /* uint16 min-plus values in [0, 0x7FFF], packed two per 32-bit lane */
+} btas_dtype;
+
+typedef enum {
+    BTAS_OK = 0,
+    BTAS_ERR_ARG = 1,         /* invalid argument; nothing enqueued */
+    BTAS_ERR_BOUND = 2,       /* a requested exact reduced-precision path is not provably exact */
+    BTAS_ERR_NOMEM = 3,       /* device workspace allocation failed */
+    BTAS_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    BTAS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (batched scheduler) */
+    BTAS_ERR_BUDGET = 6,      /* request exceeds the configured device-memory budget */
+    BTAS_ERR_UNSUPPORTED = 7  /* semiring/dtype combination not offered */
+} btas_status;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int btas_version(void);
+
+/* Human-readable description of the calling thread's most recent error. */
+const char *btas_last_error_string(void);
+
+/* ------------------------------------------------------------------------
+ * Level 3: tropical matrix product (the product listing of Sec. IV, titled
+ * "Matrix-Matrix Multiplication for Floyd-Warshall": replace + by min (or
+ * max) and x by +).
+ *
+ *   C[i][j] = (+)_{0<=l<k} A[i][l] (.) B[l][j]           (default)
+ *   C[i][j] = C[i][j] (+) (+)_l A[i][l] (.) B[l][j]      (BTAS_GEMM_ACCUMULATE)
+ *
+ * semiring : BTAS_MINPLUS or BTAS_MAXPLUS, optionally OR BTAS_GEMM_* flags.
+ * dtype    : BTAS_I32, BTAS_F32, or BTAS_U16 (min-plus only).
+ * m, n, k  : sizes, each >= 0.  k == 0 writes the (+)-identity (or leaves C
+ *            unchanged with ACCUMULATE).  m == 0 or n == 0 is a no-op.
+ * A        : m x k, leading dimension lda >= max(1, k).
+ * B        : k x n with ldb >= max(1, n); with BTAS_GEMM_TRANS_B it is the
+ *            n x k matrix B^T with ldb >= max(1, k).
+ * C        : m x n, ldc >= max(1, n).  C must not overlap A or B.
+ * Errors   : BTAS_ERR_ARG for negative sizes, short leading dimensions,
+ *            NULL pointers with non-empty extents, unknown semiring/dtype;
+ *            BTAS_ERR_UNSUPPORTED for max-plus with BTAS_U16.
+ * Results are bit-exact with the definition for every tiling.
+ * ------------------------------------------------------------------------ */
+btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k,
+                      const void *A, int64_t lda, const void *B, int64_t ldb,
+                      void *C, int64_t ldc, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Level 1: tropical vector operations ("standard vector operations",
+ * abstract and Sec. III).  Strides may be negative only where stated; here
+ * they must be >= 1.
+ *
+ * btas_dot : *result = (+)_{i<n} x[i*incx] (.) y[i*incy].  `result` is a
+ *            DEVICE pointer to one element of `dtype`.  n == 0 writes the
+ *            (+)-identity.
+ * btas_axpy: y[i*incy] <- y[i*incy] (+) (alpha (.) x[i*incx]).  `alpha` is a
+ *            HOST pointer to one element of `dtype`.
+ * btas_add : z[i] = x[i] (+) y[i]   (contiguous vectors of length n)
+ * btas_mul : z[i] = x[i] (.) y[i]   (int32 result saturates to INF as above)
+ * dtype    : BTAS_I32 or BTAS_F32.
+ * ------------------------------------------------------------------------ */
+btas_status btas_dot(int semiring, int dtype, int64_t n, const void *x, int64_t incx,
+                     const void *y, int64_t incy, void *result, void *stream);
+btas_status btas_axpy(int semiring, int dtype, int64_t n, const void *alpha,
+                      const void *x, int64_t incx, void *y, int64_t incy, void *stream);
+btas_status btas_add(int semiring, int dtype, int64_t n, const void *x, const void *y,
+                     void *z, void *stream);
+btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const void *y,
+                     void *z, void *stream);
+
+/* ------------------------------------------------------------------------
+ * All-pairs shortest paths by repeated squaring (Sec. III): D_0 = W,
+ * D_{s+1} = D_s (x) D_s in min-plus, for S = ceil(log2(n-1)) squarings
+ * (S = 0 for n <= 2).  After s squarings D_s holds the shortest walks of at
+ * most 2^s edges; a shortest path has at most n-1 edges, so D_S is the APSP
+ * distance matrix -- the same matrix Floyd-Warshall (Algorithm 2) computes.
+ *
+ * n : number of vertices, >= 0.
+ * W : n x n int32 weighted adjacency matrix (row-major, leading dimension n):
+ *     W[i][i] == 0, W[i][j] in [0, BTAS_I32_FINITE_MAX] for an edge,
+ *     BTAS_INF_I32 for no edge.  Weights are non-negative (Sec. IV states
+ *     the algorithm for non-negative edge weights).
+ * D : n x n int32 output; D == W (in place) is allowed, any other overlap is
+ *     not.
+ * Domain checks run on the device and are not reported by btas_apsp; use
+ * btas_apsp_ex to get them.
+ * ------------------------------------------------------------------------ */
+btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
+
+/* Flags for btas_apsp_ex. */
+#define BTAS_APSP_EARLY_EXIT 0x1   /* stop squaring once D_{s+1} == D_s (result unchanged) */
+#define BTAS_APSP_FORCE_I32 0x2    /* always run the plain int32 kernels */
+#define BTAS_APSP_FORCE_U16 0x4    /* require the packed 16-bit path; BTAS_ERR_BOUND if not exact */
+#define BTAS_APSP_FORCE_CARRIER 0x8 /* require the FP32-carrier path; BTAS_ERR_BOUND if not exact */
+
+/* btas_apsp_ex: as btas_apsp, with
+ *  flags           : BTAS_APSP_* bits.  Without FORCE bits the fastest exact
+ *                    path is chosen from the bound B = (n-1) * max finite w:
+ *                    packed 16-bit if B < 0x7FFF, FP32 carrier if
+ *                    B < 2^23, else int32.  The bound is computed on the
+ *                    device, so path selection synchronises `stream`.
+ *  squarings_done  : HOST pointer or NULL; receives the number of squarings
+ *                    that changed D (<= S).  Non-NULL synchronises `stream`.
+ *  bound           : HOST pointer or NULL; receives B (or -1 if W has a
+ *                    negative or out-of-domain entry, in which case the call
+ *                    returns BTAS_ERR_ARG after synchronising).
+ *  path            : HOST pointer or NULL; receives 0 = int32, 1 = FP32
+ *                    carrier, 2 = packed 16-bit.
+ */
+btas_status btas_apsp_ex(int64_t n, const int32_t *W, int32_t *D, int flags,
+                         int *squarings_done, int64_t *bound, int *path, void *stream);
+
+/* btas_apsp_u16: APSP on 16-bit storage (BTAS_U16 encoding, INF = 0x7FFF).
+ * W and D are n x n uint16 device matrices, D == W allowed.  The caller
+ * asserts max_w, the largest finite weight; the call returns BTAS_ERR_BOUND
+ * unless (n-1) * max_w < 0x7FFF, which makes every intermediate distance
+ * exact.  flags: BTAS_APSP_EARLY_EXIT or 0. */
+btas_status btas_apsp_u16(int64_t n, const uint16_t *W, uint16_t *D, int max_w, int flags,
+                          void *stream);
+
+/* Number of squarings btas_apsp performs for n vertices: ceil(log2(n-1)). */
+int btas_apsp_squarings(int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTAS_H */
