@@ -1,0 +1,386 @@
+"""Benchmark of the tropical-algebra hot path on GB300.
+
+One step = one pass of the hot path over the n = 8192 workload:
+  * tropical matrix product M = N = K = 8192: int32 (uniform [0, 10^6]) in
+    min-plus and max-plus, FP32 (uniform [0, 1)) in min-plus and max-plus;
+  * APSP by repeated squaring of one random directed graph, n = 8192, edge
+    probability 0.01, int32 weights uniform [1, 1000], 13 squarings with
+    early exit (the library picks the exact path from the weight bound).
+Metric: tropical Gop/s = (add-min/max terms computed) / time, where a
+product is M*N*K terms and APSP counts n^3 per squaring actually computed.
+
+Other keys: the roofline of the dominant kernel (the int32 min-plus product,
+ALU-bound; peak = SMs x 128 lanes x SM clock), the CPU oracle timed on a
+bounded sample (`cpu_baseline`), the end-to-end number through the public
+API with host buffers (`e2e`), SM clocks sampled during the timed region,
+and the number of library kernels launched in it.
+
+`--impl reference` times the CPU oracle (the plain triple loop of
+oracle/btas_oracle.c) on a bounded row sample of the same products.
+
+Under torchrun (N > 1) every rank runs the same step on its own GPU
+(replicas: the workload is independent per GPU); value = total terms of all
+ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tropical Gop/s & % ALU peak (n=8192); batched APSP graphs/s; serve p50/p99 ms"
+N = 8192
+LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="btas", choices=["btas", "reference"])
+    p.add_argument("--n", type=int, default=N)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(units_per_rank, seconds_per_rank):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return sum(units_per_rank) / max(seconds_per_rank)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        load = [s for s in sm if s >= 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ---------------------------------------------------------------- inputs
+def make_inputs(n):
+    import numpy as np
+    import gen
+    s = gen.BASE_SEED
+    Ai = gen.uniform_int(s, 21, (n, n), 0, 10 ** 6)
+    Bi = gen.uniform_int(s, 22, (n, n), 0, 10 ** 6)
+    Af = gen.uniform_f32(s, 23, (n, n))
+    Bf = gen.uniform_f32(s, 24, (n, n))
+    W = gen.random_graph(s, 2, n, 0.01, 1, 1000)
+    return {"Ai": Ai, "Bi": Bi, "Af": Af, "Bf": Bf, "W": W,
+            "BiT": np.ascontiguousarray(Bi.T), "BfT": np.ascontiguousarray(Bf.T)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(inp, budget_s=15.0, threads=None):
+    """Oracle triple loop on a bounded row sample of the four products;
+    returns (Gop/s, threads, sample description)."""
+    import oracle
+    n = inp["Ai"].shape[0]
+    threads = threads or os.cpu_count() or 1
+    oracle.set_threads(threads)
+    try:
+        rows = max(1, threads)
+        t0 = time.perf_counter()
+        oracle.tgemm(0, inp["Ai"][:rows], inp["Bi"])
+        dt = time.perf_counter() - t0
+        per_row = dt / rows
+        R = int(max(rows, min(n, budget_s / 4 / per_row)))
+        R = max(threads, (R // threads) * threads)
+        total = 0.0
+        t0 = time.perf_counter()
+        for sr, A, B in ((0, "Ai", "Bi"), (1, "Ai", "Bi"), (0, "Af", "Bf"), (1, "Af", "Bf")):
+            oracle.tgemm(sr, inp[A][:R], inp[B])
+            total += float(R) * n * n
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    return total / dt / 1e9, threads, f"{R} rows x {n} x {n} of each of the 4 products ({total:.3g} terms, {dt:.1f} s)"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import gen
+    n = args.n
+    inp = {"Ai": gen.uniform_int(gen.BASE_SEED, 21, (n, n), 0, 10 ** 6),
+           "Bi": gen.uniform_int(gen.BASE_SEED, 22, (n, n), 0, 10 ** 6),
+           "Af": gen.uniform_f32(gen.BASE_SEED, 23, (n, n)), "Bf": gen.uniform_f32(gen.BASE_SEED, 24, (n, n))}
+    total_steps = args.steps + args.warmup
+    budget = max(2.0, min(20.0, 150.0 / max(total_steps, 1)))
+    rates = []
+    sample = ""
+    threads = os.cpu_count() or 1
+    for i in range(total_steps):
+        rate, threads, sample = cpu_oracle_rate(inp, budget_s=budget, threads=threads)
+        if i >= args.warmup:
+            rates.append(rate)
+    value = statistics.median(rates)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "Gop/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"tropical product {n}^3 int32/f32 min/max-plus (oracle row sample)",
+                       "n": n},
+            "cpu_baseline": {"value": round(value, 3), "unit": "Gop/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm
+def run_btas(args):
+    import numpy as np
+    import torch
+    import paper_1701_04733_gb300 as btas
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.n
+    inp = make_inputs(n)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in inp.items()}
+    Ci = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    Cf = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    D = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    n3 = float(n) ** 3
+
+    # APSP: squarings actually computed (early exit) for this fixed graph
+    _, info = btas.apsp(dev["W"], out=D, info=True)
+    S = btas.btas_apsp_squarings(n)
+    computed = min(S, info["squarings"] + 1)
+    units_per_step = 4 * n3 + computed * n3
+    ev = {}
+
+    def step(record=False):
+        def rec(name):
+            if record:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                ev.setdefault(name, []).append(e)
+        rec("i32min0")
+        btas.gemm(dev["Ai"], dev["BiT"], btas.MINPLUS, out=Ci, trans_b=True)
+        rec("i32min1")
+        btas.gemm(dev["Ai"], dev["BiT"], btas.MAXPLUS, out=Ci, trans_b=True)
+        rec("f32min0")
+        btas.gemm(dev["Af"], dev["BfT"], btas.MINPLUS, out=Cf, trans_b=True)
+        rec("f32min1")
+        btas.gemm(dev["Af"], dev["BfT"], btas.MAXPLUS, out=Cf, trans_b=True)
+        rec("apsp0")
+        btas.apsp(dev["W"], out=D)
+        rec("apsp1")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = btas.btas_kernel_launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = btas.btas_kernel_launches() - launches0
+    seconds = t0.elapsed_time(t1) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([seconds], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        seconds = float(tt.item())
+        dist.barrier()
+    value = aggregate([units_per_step * args.steps] * world, [seconds]) / 1e9
+
+    def dur(a, b):
+        return statistics.mean(x.elapsed_time(y) for x, y in zip(ev[a], ev[b])) / 1e3
+
+    t_i32min = dur("i32min0", "i32min1")
+    t_i32max = dur("i32min1", "f32min0")
+    t_f32min = dur("f32min0", "f32min1")
+    t_f32max = dur("f32min1", "apsp0")
+    t_apsp = dur("apsp0", "apsp1")
+    clocks = clk.summary()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or peaks().get("sm_max_mhz") or 2070.0
+    peak_tops = sms * LANES_PER_SM * max_mhz * 1e6 / 1e12
+    achieved = n3 / t_i32min / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get("tgemm_nt_i32_min_8192")
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Gop/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(seconds / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+        "config": {"workload": f"tropical product {n}^3 (int32 [0,1e6] and f32 [0,1), min-plus and max-plus) + "
+                               f"int32 APSP n={n} p=0.01 w[1,1000] ({S} squarings, early exit)",
+                   "n": n, "apsp_path": info["path"], "apsp_squarings_computed": computed,
+                   "apsp_bound": info["bound"], "b_operand": "supplied transposed (BTAS_GEMM_TRANS_B)",
+                   "l2": "inputs (256 MiB per matrix) larger than L2 (129 MB)", "parallelism": f"replicas x{world}"},
+        "parts_ms": {"i32_minplus": round(t_i32min * 1e3, 3), "i32_maxplus": round(t_i32max * 1e3, 3),
+                     "f32_minplus": round(t_f32min * 1e3, 3), "f32_maxplus": round(t_f32max * 1e3, 3),
+                     "apsp": round(t_apsp * 1e3, 3)},
+        "parts_gops": {"i32_minplus": round(n3 / t_i32min / 1e9, 1), "i32_maxplus": round(n3 / t_i32max / 1e9, 1),
+                       "f32_minplus": round(n3 / t_f32min / 1e9, 1), "f32_maxplus": round(n3 / t_f32max / 1e9, 1),
+                       "apsp": round(computed * n3 / t_apsp / 1e9, 1)},
+        "roofline": {"bound": "alu", "kernel": "tgemm_nt int32 min-plus 8192^3", "achieved": round(achieved, 3),
+                     "peak": round(peak_tops, 3), "unit": "Top/s", "frac": round(achieved / peak_tops, 4),
+                     "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {max_mhz:.0f} MHz (max SM clock)",
+                     "frac_at_median_clock": (round(achieved / (sms * LANES_PER_SM * clocks['sm_mhz'] * 1e-6), 4)
+                                              if clocks.get("sm_mhz") else None),
+                     "traffic": traffic},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, inp, btas, torch, units_per_step)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, threads, sample = cpu_oracle_rate(inp)
+        line["cpu_baseline"] = {"value": round(rate, 3), "unit": "Gop/s", "cores": threads, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def e2e(args, inp, btas, torch, units_per_step):
+    """Same step through the public API with pinned host buffers: every step
+    copies its inputs host -> device and its results device -> host."""
+    n = inp["Ai"].shape[0]
+    h = {k: torch.from_numpy(v).pin_memory() for k, v in inp.items() if k in ("Ai", "BiT", "Af", "BfT", "W")}
+    outs = {"i": torch.empty((n, n), dtype=torch.int32).pin_memory(),
+            "f": torch.empty((n, n), dtype=torch.float32).pin_memory(),
+            "d": torch.empty((n, n), dtype=torch.int32).pin_memory()}
+    bi = bo = 0
+
+    def step():
+        nonlocal bi, bo
+        bi = bo = 0
+        for sr in (btas.MINPLUS, btas.MAXPLUS):
+            btas.gemm(h["Ai"], h["BiT"], sr, out=outs["i"], trans_b=True)
+            bi += 2 * h["Ai"].numel() * 4
+            bo += outs["i"].numel() * 4
+        for sr in (btas.MINPLUS, btas.MAXPLUS):
+            btas.gemm(h["Af"], h["BfT"], sr, out=outs["f"], trans_b=True)
+            bi += 2 * h["Af"].numel() * 4
+            bo += outs["f"].numel() * 4
+        Wd = h["W"].cuda(non_blocking=True)
+        outs["d"].copy_(btas.apsp(Wd), non_blocking=True)
+        bi += h["W"].numel() * 4
+        bo += outs["d"].numel() * 4
+        torch.cuda.synchronize()
+
+    step()
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = time.perf_counter() - t0
+    return {"value": round(units_per_step * steps / dt / 1e9, 2), "unit": "Gop/s", "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bo, "steps": steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_btas(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -90,6 +90,10 @@ int btas_version(void);
 /* Human-readable description of the calling thread's most recent error. */
 const char *btas_last_error_string(void);
 
+/* Number of CUDA kernels this library has enqueued in this process so far
+ * (all threads, all devices).  Diagnostic counter; never reset. */
+int64_t btas_kernel_launches(void);
+
 /* ------------------------------------------------------------------------
  * Level 3: tropical matrix product (the product listing of Sec. IV, titled
  * "Matrix-Matrix Multiplication for Floyd-Warshall": replace + by min (or

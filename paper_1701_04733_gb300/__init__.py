@@ -1,0 +1,286 @@
+"""Python binding of the GB300 tropical-algebra library (C ABI in include/btas.h).
+
+The `btas_*` functions are one-to-one ctypes bindings of the C entry points
+(argument marshalling only; every step runs in the CUDA kernels of
+libbtas.so).  The lower-case helpers (`gemm`, `apsp`, `dot`, ...) take torch
+tensors, pass their device pointers and the current CUDA stream, and raise
+`BtasError` on a non-zero status.  PyTorch only provides device memory and
+streams.
+
+Semirings (Sec. I): MINPLUS, x (+) y = min(x, y), x (.) y = x + y (Eq. 3-4);
+MAXPLUS, x (+) y = max(x, y), x (.) y = x + y (Eq. 1-2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libbtas.so")
+
+MINPLUS = 0
+MAXPLUS = 1
+GEMM_ACCUMULATE = 0x100
+GEMM_TRANS_B = 0x200
+GEMM_NO_CARRIER = 0x400
+I32 = 0
+F32 = 1
+U16 = 2
+APSP_EARLY_EXIT = 0x1
+APSP_FORCE_I32 = 0x2
+APSP_FORCE_U16 = 0x4
+APSP_FORCE_CARRIER = 0x8
+INF_I32 = 0x3FFFFFFF
+NINF_I32 = -0x3FFFFFFF
+I32_FINITE_MAX = 1 << 28
+INF_U16 = 0x7FFF
+
+STATUS = {0: "BTAS_OK", 1: "BTAS_ERR_ARG", 2: "BTAS_ERR_BOUND", 3: "BTAS_ERR_NOMEM", 4: "BTAS_ERR_CUDA",
+          5: "BTAS_ERR_TIMEOUT", 6: "BTAS_ERR_BUDGET", 7: "BTAS_ERR_UNSUPPORTED"}
+
+
+class BtasError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+_i64, _i32, _vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+# name -> (restype, argtypes); mirrors include/btas.h
+SIGNATURES = {
+    "btas_version": (_i32, []),
+    "btas_last_error_string": (ctypes.c_char_p, []),
+    "btas_kernel_launches": (_i64, []),
+    "btas_gemm": (_i32, [_i32, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
+    "btas_dot": (_i32, [_i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp, _vp]),
+    "btas_axpy": (_i32, [_i32, _i32, _i64, _vp, _vp, _i64, _vp, _i64, _vp]),
+    "btas_add": (_i32, [_i32, _i32, _i64, _vp, _vp, _vp, _vp]),
+    "btas_mul": (_i32, [_i32, _i32, _i64, _vp, _vp, _vp, _vp]),
+    "btas_apsp": (_i32, [_i64, _vp, _vp, _vp]),
+    "btas_apsp_ex": (_i32, [_i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "btas_apsp_u16": (_i32, [_i64, _vp, _vp, _i32, _i32, _vp]),
+    "btas_apsp_squarings": (_i32, [_i64]),
+}
+
+
+def lib():
+    """The loaded libbtas.so.  Raises if it has not been built: there is no
+    fallback implementation."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                                   "g.build()'` (nvcc, sm_103a); the library has no CPU fallback")
+            handle = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(handle, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = handle
+        return _lib
+
+
+def build(verbose: bool = False) -> str:
+    from . import _build
+    return _build.build(verbose=verbose)
+
+
+def last_error() -> str:
+    return lib().btas_last_error_string().decode()
+
+
+def check(status: int) -> None:
+    if status != 0:
+        raise BtasError(status, last_error())
+
+
+# ---------------------------------------------------------------- raw ABI
+def btas_version() -> int:
+    return lib().btas_version()
+
+
+def btas_kernel_launches() -> int:
+    return lib().btas_kernel_launches()
+
+
+def btas_gemm(semiring, dtype, m, n, k, A, lda, B, ldb, C, ldc, stream) -> int:
+    return lib().btas_gemm(semiring, dtype, m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def btas_dot(semiring, dtype, n, x, incx, y, incy, result, stream) -> int:
+    return lib().btas_dot(semiring, dtype, n, x, incx, y, incy, result, stream)
+
+
+def btas_axpy(semiring, dtype, n, alpha_host_ptr, x, incx, y, incy, stream) -> int:
+    return lib().btas_axpy(semiring, dtype, n, alpha_host_ptr, x, incx, y, incy, stream)
+
+
+def btas_add(semiring, dtype, n, x, y, z, stream) -> int:
+    return lib().btas_add(semiring, dtype, n, x, y, z, stream)
+
+
+def btas_mul(semiring, dtype, n, x, y, z, stream) -> int:
+    return lib().btas_mul(semiring, dtype, n, x, y, z, stream)
+
+
+def btas_apsp(n, W, D, stream) -> int:
+    return lib().btas_apsp(n, W, D, stream)
+
+
+def btas_apsp_ex(n, W, D, flags, squarings_done_ptr, bound_ptr, path_ptr, stream) -> int:
+    return lib().btas_apsp_ex(n, W, D, flags, squarings_done_ptr, bound_ptr, path_ptr, stream)
+
+
+def btas_apsp_u16(n, W, D, max_w, flags, stream) -> int:
+    return lib().btas_apsp_u16(n, W, D, max_w, flags, stream)
+
+
+def btas_apsp_squarings(n) -> int:
+    return lib().btas_apsp_squarings(n)
+
+
+# ------------------------------------------------------- torch helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _sr(semiring) -> int:
+    if semiring in (MINPLUS, "min", "minplus", "min-plus"):
+        return MINPLUS
+    if semiring in (MAXPLUS, "max", "maxplus", "max-plus"):
+        return MAXPLUS
+    raise ValueError(f"unknown semiring {semiring!r}")
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.int32:
+        return I32
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        return U16
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _rowmajor(t, name):
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a 2-D row-major tensor (unit column stride)")
+    return max(t.stride(0), 1) if t.shape[0] > 1 else max(t.shape[1], 1)
+
+
+def gemm(A, B, semiring="min", out=None, accumulate=False, trans_b=False, stream=None, no_carrier=False):
+    """Tropical product C = A (x) B (or C (+)= A (x) B with accumulate).
+
+    A, B are CUDA tensors (int32, float32, or int16 holding values in
+    [0, 0x7FFF] for the packed min-plus path).  With trans_b, B is given as
+    B^T (n x k).  CPU tensors are copied to the current device and the result
+    is copied back (host -> device -> kernel -> host, the flow of Fig. 1)."""
+    torch = _torch()
+    host = A.device.type == "cpu"
+    if host:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        Ad, Bd = A.to(dev, non_blocking=True), B.to(dev, non_blocking=True)
+        od = out.to(dev, non_blocking=True) if (out is not None and accumulate) else None
+        C = gemm(Ad, Bd, semiring, od, accumulate, trans_b, stream, no_carrier)
+        if out is None:
+            return C.cpu()
+        out.copy_(C)
+        return out
+    m, k = A.shape
+    n = B.shape[0] if trans_b else B.shape[1]
+    if (B.shape[1] if trans_b else B.shape[0]) != k:
+        raise ValueError("inner dimensions differ")
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate needs `out`")
+        out = torch.empty((m, n), dtype=A.dtype, device=A.device)
+    flags = _sr(semiring) | (GEMM_ACCUMULATE if accumulate else 0) | (GEMM_TRANS_B if trans_b else 0)
+    flags |= GEMM_NO_CARRIER if no_carrier else 0
+    check(btas_gemm(flags, _dtype_code(A), m, n, k, A.data_ptr(), _rowmajor(A, "A"), B.data_ptr(),
+                    _rowmajor(B, "B"), out.data_ptr(), _rowmajor(out, "out"), _stream(stream)))
+    return out
+
+
+def apsp(W, out=None, flags=APSP_EARLY_EXIT, stream=None, info=False):
+    """All-pairs shortest paths of the int32 adjacency matrix W by repeated
+    min-plus squaring (Sec. III).  out may be W (in place).  With info=True
+    returns (D, {"squarings": ..., "bound": ..., "path": ...})."""
+    torch = _torch()
+    n = W.shape[0]
+    if W.shape != (n, n) or not W.is_contiguous() or W.dtype != torch.int32:
+        raise ValueError("W must be a contiguous n x n int32 tensor")
+    if out is None:
+        out = torch.empty_like(W)
+    sq, bd, pt = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int(0)
+    if info:
+        check(btas_apsp_ex(n, W.data_ptr(), out.data_ptr(), flags, ctypes.addressof(sq), ctypes.addressof(bd),
+                           ctypes.addressof(pt), _stream(stream)))
+        return out, {"squarings": sq.value, "bound": bd.value, "path": ("int32", "fp32-carrier", "u16x2")[pt.value]}
+    if flags == APSP_EARLY_EXIT:
+        check(btas_apsp(n, W.data_ptr(), out.data_ptr(), _stream(stream)))
+    else:
+        check(btas_apsp_ex(n, W.data_ptr(), out.data_ptr(), flags, None, None, None, _stream(stream)))
+    return out
+
+
+def apsp_u16(W, max_w, out=None, early_exit=True, stream=None):
+    """APSP on 16-bit storage (INF = 0x7FFF) through the packed path; requires
+    (n-1) * max_w < 0x7FFF."""
+    torch = _torch()
+    n = W.shape[0]
+    if out is None:
+        out = torch.empty_like(W)
+    check(btas_apsp_u16(n, W.data_ptr(), out.data_ptr(), int(max_w), APSP_EARLY_EXIT if early_exit else 0,
+                        _stream(stream)))
+    return out
+
+
+def dot(x, y, semiring="min", incx=1, incy=1, n=None, out=None, stream=None):
+    torch = _torch()
+    if n is None:
+        n = (x.numel() + incx - 1) // incx
+    if out is None:
+        out = torch.empty((), dtype=x.dtype, device=x.device)
+    check(btas_dot(_sr(semiring), _dtype_code(x), n, x.data_ptr(), incx, y.data_ptr(), incy, out.data_ptr(),
+                   _stream(stream)))
+    return out
+
+
+def axpy(alpha, x, y, semiring="min", incx=1, incy=1, n=None, stream=None):
+    """y <- y (+) (alpha (.) x), in place on y."""
+    if n is None:
+        n = (x.numel() + incx - 1) // incx
+    code = _dtype_code(x)
+    a = ctypes.c_int32(int(alpha)) if code == I32 else ctypes.c_float(float(alpha))
+    check(btas_axpy(_sr(semiring), code, n, ctypes.addressof(a), x.data_ptr(), incx, y.data_ptr(), incy,
+                    _stream(stream)))
+    return y
+
+
+def add(x, y, semiring="min", out=None, stream=None):
+    torch = _torch()
+    out = torch.empty_like(x) if out is None else out
+    check(btas_add(_sr(semiring), _dtype_code(x), x.numel(), x.data_ptr(), y.data_ptr(), out.data_ptr(),
+                   _stream(stream)))
+    return out
+
+
+def mul(x, y, semiring="min", out=None, stream=None):
+    torch = _torch()
+    out = torch.empty_like(x) if out is None else out
+    check(btas_mul(_sr(semiring), _dtype_code(x), x.numel(), x.data_ptr(), y.data_ptr(), out.data_ptr(),
+                   _stream(stream)))
+    return out

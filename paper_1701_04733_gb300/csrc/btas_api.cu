@@ -1,0 +1,477 @@
+// C-ABI entry points declared in include/btas.h: argument validation, kernel
+// selection, stream-ordered workspace, and the APSP squaring driver.
+#include <atomic>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace btas {
+extern const GemmKernel kGemmI32Dpx[];
+extern const int kGemmI32DpxCount;
+extern const GemmKernel kGemmI32Mix[];
+extern const int kGemmI32MixCount;
+extern const GemmKernel kGemmF32[];
+extern const int kGemmF32Count;
+}  // namespace btas
+
+using namespace btas;
+
+namespace btas {
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace btas
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+btas_status fail(btas_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+btas_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(BTAS_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define BTAS_CUDA(call, what)                              \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Stream-ordered scratch that is released on the same stream when it goes
+// out of scope.
+struct Workspace {
+    void *p = nullptr;
+    cudaStream_t st;
+    explicit Workspace(cudaStream_t s) : st(s) {}
+    cudaError_t alloc(size_t bytes) { return bytes ? cudaMallocAsync(&p, bytes, st) : cudaSuccess; }
+    ~Workspace() {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+bool aligned16(const void *p, long long ld) {
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld & 3) == 0;
+}
+
+int env_int(const char *name, int dflt) {
+    const char *v = getenv(name);
+    return v && *v ? atoi(v) : dflt;
+}
+
+// Kernel choice.  Variant and tile defaults come from measurement on GB300;
+// BTAS_I32_VARIANT (0 = DPX, 1 = mixed), BTAS_I32_NS, BTAS_F32_VARIANT
+// (2 = f32x2, 3 = scalar) and BTAS_CFG override them.
+const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n) {
+    int var, ns = 0;
+    if (dtype == BTAS_F32) {
+        var = env_int("BTAS_F32_VARIANT", kF32X2);
+    } else {
+        var = env_int("BTAS_I32_VARIANT", kI32Mix);
+        ns = var == kI32Mix ? env_int("BTAS_I32_NS", 5) : 0;
+    }
+    const long long big_tiles = ((m + 127) / 128) * ((n + 127) / 128);
+    int cfg = env_int("BTAS_CFG", big_tiles >= 2 * 152 ? 0 : 2);
+    const GemmKernel *k = find_gemm_kernel(var, sr, ns, cfg);
+    if (!k) k = find_gemm_kernel(var, sr, ns, 0);
+    if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Dpx, sr, 0, cfg);
+    if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Dpx, sr, 0, 0);
+    if (!k && dtype == BTAS_F32) k = find_gemm_kernel(kF32X2, sr, 0, 0);
+    return k;
+}
+
+// Run the NT kernel on A (m x k) and Bt (n x k).
+btas_status run_nt(int dtype, int sr, const GemmArgs &a, cudaStream_t st) {
+    const GemmKernel *k = select_kernel(dtype, sr, a.m, a.n);
+    if (!k) return fail(BTAS_ERR_UNSUPPORTED, "no kernel for dtype %d semiring %d", dtype, sr);
+    GemmArgs args = a;
+    args.group_m = 8;
+    args.one = 1;
+    BTAS_CUDA(k->launch(args, st), "tropical gemm launch");
+    return BTAS_OK;
+}
+
+uint32_t ident_bits(int dtype, int sr) {
+    if (dtype == BTAS_I32) return static_cast<uint32_t>(sr == kMin ? kInfI32 : kNinfI32);
+    return sr == kMin ? 0x7f800000u : 0xff800000u;
+}
+
+}  // namespace
+
+namespace btas {
+const GemmKernel *find_gemm_kernel(int var, int sr, int ns, int cfg) {
+    const GemmKernel *tabs[3] = {kGemmI32Dpx, kGemmI32Mix, kGemmF32};
+    const int counts[3] = {kGemmI32DpxCount, kGemmI32MixCount, kGemmF32Count};
+    for (int t = 0; t < 3; ++t)
+        for (int i = 0; i < counts[t]; ++i) {
+            const GemmKernel &k = tabs[t][i];
+            if (k.var == var && k.sr == sr && k.cfg == cfg && (var != kI32Mix || k.ns == ns)) return &k;
+        }
+    return nullptr;
+}
+}  // namespace btas
+
+extern "C" {
+
+int btas_version(void) { return 100; }
+
+int64_t btas_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *btas_last_error_string(void) { return g_err.c_str(); }
+
+int btas_apsp_squarings(int64_t n) {
+    int s = 0;
+    int64_t reach = 1;
+    while (reach < n - 1) {
+        reach *= 2;
+        ++s;
+    }
+    return s;
+}
+
+btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, const void *A, int64_t lda,
+                      const void *B, int64_t ldb, void *C, int64_t ldc, void *stream) {
+    const int sr = semiring & 0xff;
+    const bool accumulate = (semiring & BTAS_GEMM_ACCUMULATE) != 0;
+    const bool trans_b = (semiring & BTAS_GEMM_TRANS_B) != 0;
+    if (semiring & ~(0xff | BTAS_GEMM_ACCUMULATE | BTAS_GEMM_TRANS_B | BTAS_GEMM_NO_CARRIER))
+        return fail(BTAS_ERR_ARG, "btas_gemm: unknown flag bits 0x%x", semiring);
+    if (sr != BTAS_MINPLUS && sr != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_gemm: unknown semiring %d", sr);
+    if (dtype != BTAS_I32 && dtype != BTAS_F32 && dtype != BTAS_U16)
+        return fail(BTAS_ERR_ARG, "btas_gemm: unknown dtype %d", dtype);
+    if (m < 0 || n < 0 || k < 0) return fail(BTAS_ERR_ARG, "btas_gemm: negative size");
+    if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return fail(BTAS_ERR_ARG, "btas_gemm: size beyond 2^31-1");
+    if (lda < (k > 1 ? k : 1)) return fail(BTAS_ERR_ARG, "btas_gemm: lda %lld < k", (long long)lda);
+    if (ldb < (trans_b ? (k > 1 ? k : 1) : (n > 1 ? n : 1)))
+        return fail(BTAS_ERR_ARG, "btas_gemm: ldb %lld too small", (long long)ldb);
+    if (ldc < (n > 1 ? n : 1)) return fail(BTAS_ERR_ARG, "btas_gemm: ldc %lld < n", (long long)ldc);
+    if (m == 0 || n == 0) return BTAS_OK;
+    if (!C || (k > 0 && (!A || !B))) return fail(BTAS_ERR_ARG, "btas_gemm: NULL pointer");
+    if (dtype == BTAS_U16 && sr != BTAS_MINPLUS)
+        return fail(BTAS_ERR_UNSUPPORTED, "btas_gemm: BTAS_U16 is min-plus only");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    if (dtype == BTAS_U16) {
+        if (trans_b) return fail(BTAS_ERR_UNSUPPORTED, "btas_gemm: BTAS_U16 takes B untransposed");
+        if (k == 0) {
+            if (accumulate) return BTAS_OK;
+            return fail(BTAS_ERR_UNSUPPORTED, "btas_gemm: BTAS_U16 with k == 0");
+        }
+        U16Args a{};
+        a.m = (int)m; a.n = (int)n; a.k = (int)k;
+        a.A = static_cast<const uint16_t *>(A); a.lda = lda;
+        a.B = static_cast<const uint16_t *>(B); a.ldb = ldb;
+        a.C = static_cast<uint16_t *>(C); a.ldc = ldc;
+        a.one = 1;
+        if (accumulate) return fail(BTAS_ERR_UNSUPPORTED, "btas_gemm: BTAS_U16 accumulate");
+        Workspace ws(st);
+        BTAS_CUDA(ws.alloc((size_t)m * ((k + 3) & ~3LL) * 4), "workspace alloc");
+        BTAS_CUDA(launch_tgemm_u16_ws(a, static_cast<uint32_t *>(ws.p), env_int("BTAS_U16_NS", 5), st),
+                  "u16 gemm launch");
+        return BTAS_OK;
+    }
+
+    if (k == 0) {
+        if (accumulate) return BTAS_OK;
+        BTAS_CUDA(launch_fill4(C, ldc, (int)m, (int)n, ident_bits(dtype, sr), st), "fill");
+        return BTAS_OK;
+    }
+
+    Workspace ws(st);
+    const void *Bt = B;
+    long long ldbt = ldb;
+    if (!trans_b) {
+        const long long ldt = (k + 3) & ~3LL;
+        BTAS_CUDA(ws.alloc((size_t)n * ldt * 4), "workspace alloc");
+        BTAS_CUDA(launch_transpose4(B, ldb, (int)k, (int)n, ws.p, ldt, 0, nullptr, st), "transpose B");
+        Bt = ws.p;
+        ldbt = ldt;
+    }
+    GemmArgs a{};
+    a.m = (int)m; a.n = (int)n; a.k = (int)k;
+    a.A = A; a.lda = lda;
+    a.Bt = Bt; a.ldb = ldbt;
+    a.C = C; a.ldc = ldc;
+    a.accumulate = accumulate ? 1 : 0;
+    a.vec_a = aligned16(A, lda);
+    a.vec_b = aligned16(Bt, ldbt);
+    return run_nt(dtype, sr, a, st);
+}
+
+// ----------------------------------------------------------------- vectors
+
+btas_status btas_dot(int semiring, int dtype, int64_t n, const void *x, int64_t incx, const void *y,
+                     int64_t incy, void *result, void *stream) {
+    if (semiring != BTAS_MINPLUS && semiring != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_dot: semiring");
+    if (dtype != BTAS_I32 && dtype != BTAS_F32) return fail(BTAS_ERR_ARG, "btas_dot: dtype");
+    if (n < 0 || incx < 1 || incy < 1) return fail(BTAS_ERR_ARG, "btas_dot: size or stride");
+    if (!result || (n > 0 && (!x || !y))) return fail(BTAS_ERR_ARG, "btas_dot: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) {
+        BTAS_CUDA(launch_fill4(result, 1, 1, 1, ident_bits(dtype, semiring), st), "fill");
+        return BTAS_OK;
+    }
+    long long nb = (n + 2047) / 2048;
+    if (nb > 2 * 152) nb = 2 * 152;
+    Workspace ws(st);
+    BTAS_CUDA(ws.alloc((size_t)nb * 4), "workspace alloc");
+    BTAS_CUDA(launch_dot(semiring, dtype, n, x, incx, y, incy, result, ws.p, (int)nb, st), "dot");
+    return BTAS_OK;
+}
+
+btas_status btas_axpy(int semiring, int dtype, int64_t n, const void *alpha, const void *x, int64_t incx, void *y,
+                      int64_t incy, void *stream) {
+    if (semiring != BTAS_MINPLUS && semiring != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_axpy: semiring");
+    if (dtype != BTAS_I32 && dtype != BTAS_F32) return fail(BTAS_ERR_ARG, "btas_axpy: dtype");
+    if (n < 0 || incx < 1 || incy < 1) return fail(BTAS_ERR_ARG, "btas_axpy: size or stride");
+    if (n == 0) return BTAS_OK;
+    if (!alpha || !x || !y) return fail(BTAS_ERR_ARG, "btas_axpy: NULL pointer");
+    uint32_t bits;
+    memcpy(&bits, alpha, 4);
+    BTAS_CUDA(launch_axpy(semiring, dtype, n, bits, x, incx, y, incy, static_cast<cudaStream_t>(stream)), "axpy");
+    return BTAS_OK;
+}
+
+static btas_status ewise(int op, int semiring, int dtype, int64_t n, const void *x, const void *y, void *z,
+                         void *stream) {
+    if (semiring != BTAS_MINPLUS && semiring != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "semiring");
+    if (dtype != BTAS_I32 && dtype != BTAS_F32) return fail(BTAS_ERR_ARG, "dtype");
+    if (n < 0) return fail(BTAS_ERR_ARG, "negative size");
+    if (n == 0) return BTAS_OK;
+    if (!x || !y || !z) return fail(BTAS_ERR_ARG, "NULL pointer");
+    BTAS_CUDA(launch_ewise(op, semiring, dtype, n, x, y, z, static_cast<cudaStream_t>(stream)), "elementwise");
+    return BTAS_OK;
+}
+
+btas_status btas_add(int semiring, int dtype, int64_t n, const void *x, const void *y, void *z, void *stream) {
+    return ewise(0, semiring, dtype, n, x, y, z, stream);
+}
+
+btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const void *y, void *z, void *stream) {
+    return ewise(1, semiring, dtype, n, x, y, z, stream);
+}
+
+// -------------------------------------------------------------------- APSP
+
+// Squaring loop on 4-byte data (int32 or the fp32 carrier).  cur0 holds D_0
+// (may be W itself).  bufs[0], bufs[1] are n x n ping-pong outputs; the
+// last squaring writes bufs[last].  T is an n x n transpose buffer.  flags[s]
+// is set when squaring s changed D.
+static btas_status squaring_loop(int dtype, long long n, int S, const void *cur0, void *const bufs[2], void *T,
+                                 int *flags, bool early_exit, cudaStream_t st) {
+    const void *cur = cur0;
+    const long long ldt = (n + 3) & ~3LL;
+    for (int s = 0; s < S; ++s) {
+        void *out = bufs[(S - 1 - s) & 1];
+        const int *skip = (early_exit && s > 0) ? &flags[s - 1] : nullptr;
+        BTAS_CUDA(launch_transpose4(cur, n, (int)n, (int)n, T, ldt, 0, skip, st), "transpose");
+        GemmArgs a{};
+        a.m = a.n = a.k = (int)n;
+        a.A = cur; a.lda = n;
+        a.Bt = T; a.ldb = ldt;
+        a.C = out; a.ldc = n;
+        a.prev = cur; a.ldp = n;
+        a.changed = &flags[s];
+        a.skip = skip;
+        a.vec_a = aligned16(cur, n);
+        a.vec_b = aligned16(T, ldt);
+        btas_status r = run_nt(dtype, kMin, a, st);
+        if (r != BTAS_OK) return r;
+        cur = out;
+    }
+    return BTAS_OK;
+}
+
+static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags, int *squarings_done,
+                             int64_t *bound_out, int *path_out, cudaStream_t st) {
+    if (n < 0) return fail(BTAS_ERR_ARG, "btas_apsp: negative n");
+    if (n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp: n too large");
+    if (n == 0) {
+        if (squarings_done) *squarings_done = 0;
+        if (bound_out) *bound_out = 0;
+        if (path_out) *path_out = 0;
+        return BTAS_OK;
+    }
+    if (!W || !D) return fail(BTAS_ERR_ARG, "btas_apsp: NULL pointer");
+    const int known = BTAS_APSP_EARLY_EXIT | BTAS_APSP_FORCE_I32 | BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER;
+    if (flags & ~known) return fail(BTAS_ERR_ARG, "btas_apsp: unknown flags 0x%x", flags);
+    const int forced = (flags & BTAS_APSP_FORCE_I32 ? 1 : 0) + (flags & BTAS_APSP_FORCE_U16 ? 1 : 0) +
+                       (flags & BTAS_APSP_FORCE_CARRIER ? 1 : 0);
+    if (forced > 1) return fail(BTAS_ERR_ARG, "btas_apsp: more than one FORCE flag");
+    const int S = btas_apsp_squarings(n);
+    const bool early = (flags & BTAS_APSP_EARLY_EXIT) != 0;
+    const size_t nn = (size_t)n * (size_t)n;
+
+    Workspace ws(st);
+    const size_t flag_bytes = align256((size_t)(S + 4) * 4);
+    // layout: [flags | X | Y | T]; T holds a transpose (or the duplicated
+    // 16-bit operand) with a leading dimension rounded up to 4 elements
+    const long long ldt = (n + 3) & ~3LL;
+    const size_t t_bytes = align256((size_t)n * (size_t)ldt * 4);
+    BTAS_CUDA(ws.alloc(flag_bytes + 2 * align256(nn * 4) + t_bytes), "workspace alloc");
+    char *base = static_cast<char *>(ws.p);
+    int *dflags = reinterpret_cast<int *>(base);
+    char *X = base + flag_bytes;
+    char *Y = X + align256(nn * 4);
+    char *T = Y + align256(nn * 4);
+    BTAS_CUDA(cudaMemsetAsync(dflags, 0, flag_bytes, st), "memset");
+
+    // domain scan and bound: (n-1) * max finite weight
+    long long bound = -1;
+    const bool need_scan = !(flags & BTAS_APSP_FORCE_I32) || bound_out != nullptr;
+    if (need_scan) {
+        int host[2] = {0, 0};
+        int *scan = dflags + S + 1;
+        BTAS_CUDA(launch_apsp_scan(W, n, scan, st), "domain scan");
+        BTAS_CUDA(cudaMemcpyAsync(host, scan, 8, cudaMemcpyDeviceToHost, st), "scan readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "scan sync");
+        if (host[1] != 0) {
+            if (bound_out) *bound_out = -1;
+            return fail(BTAS_ERR_ARG,
+                        "btas_apsp: %d entries outside the domain (negative weight, weight > 2^28, or non-zero "
+                        "diagonal)",
+                        host[1]);
+        }
+        bound = (long long)(n - 1) * host[0];
+        if (bound_out) *bound_out = bound;
+    }
+    int path = 0;
+    if (flags & BTAS_APSP_FORCE_U16) {
+        if (bound >= BTAS_INF_U16) return fail(BTAS_ERR_BOUND, "btas_apsp: bound %lld >= 0x7FFF", bound);
+        path = 2;
+    } else if (flags & BTAS_APSP_FORCE_CARRIER) {
+        if (bound >= (1LL << 23)) return fail(BTAS_ERR_BOUND, "btas_apsp: bound %lld >= 2^23", bound);
+        path = 1;
+    } else if (!(flags & BTAS_APSP_FORCE_I32)) {
+        if (bound < BTAS_INF_U16 && env_int("BTAS_APSP_NO_U16", 0) == 0) path = 2;
+        else if (bound < (1LL << 23) && env_int("BTAS_APSP_NO_CARRIER", 0) == 0) path = 1;
+    }
+    if (path_out) *path_out = path;
+
+    if (S == 0) {
+        if (D != W) BTAS_CUDA(cudaMemcpyAsync(D, W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
+        if (squarings_done) *squarings_done = 0;
+        return BTAS_OK;
+    }
+
+    btas_status r = BTAS_OK;
+    if (path == 0) {
+        const void *cur0 = W;
+        if ((const void *)W == (const void *)D && ((S - 1) & 1) == 0) {
+            // the first squaring would write D == W while reading it
+            BTAS_CUDA(cudaMemcpyAsync(Y, W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
+            cur0 = Y;
+        }
+        void *bufs[2] = {D, X};
+        r = squaring_loop(BTAS_I32, n, S, cur0, bufs, T, dflags, early, st);
+    } else if (path == 1) {
+        // the first squaring writes bufs[(S-1)&1]; the input goes to the other one
+        void *bufs[2] = {X, Y};
+        void *in = bufs[S & 1];
+        BTAS_CUDA(launch_convert4(W, n, (int)n, (int)n, in, n, 1, st), "to carrier");
+        r = squaring_loop(BTAS_F32, n, S, in, bufs, T, dflags, early, st);
+        if (r == BTAS_OK)
+            BTAS_CUDA(launch_convert4(bufs[0], n, (int)n, (int)n, D, n, 2, st), "from carrier");
+    } else {
+        uint16_t *U0 = reinterpret_cast<uint16_t *>(X);
+        uint16_t *U1 = reinterpret_cast<uint16_t *>(Y);
+        uint32_t *Ad = reinterpret_cast<uint32_t *>(T);
+        BTAS_CUDA(launch_narrow_u16(W, (long long)nn, U0, st), "narrow");
+        uint16_t *cur = U0;
+        for (int s = 0; s < S; ++s) {
+            uint16_t *out = cur == U0 ? U1 : U0;
+            U16Args a{};
+            a.m = a.n = a.k = (int)n;
+            a.A = cur; a.lda = n;
+            a.B = cur; a.ldb = n;
+            a.C = out; a.ldc = n;
+            a.prev = cur; a.ldp = n;
+            a.changed = &dflags[s];
+            a.skip = (early && s > 0) ? &dflags[s - 1] : nullptr;
+            a.one = 1;
+            BTAS_CUDA(launch_tgemm_u16_ws(a, Ad, env_int("BTAS_U16_NS", 5), st), "u16 squaring");
+            cur = out;
+        }
+        BTAS_CUDA(launch_widen_u16_i32(cur, (long long)nn, D, st), "widen");
+    }
+    if (r != BTAS_OK) return r;
+    if (squarings_done) {
+        int host[64];
+        BTAS_CUDA(cudaMemcpyAsync(host, dflags, (size_t)S * 4, cudaMemcpyDeviceToHost, st), "flags readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "flags sync");
+        int done = 0;
+        for (int s = 0; s < S; ++s) done += host[s] != 0;
+        *squarings_done = done;
+    }
+    return BTAS_OK;
+}
+
+btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream) {
+    return apsp_impl(n, W, D, BTAS_APSP_EARLY_EXIT, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+btas_status btas_apsp_ex(int64_t n, const int32_t *W, int32_t *D, int flags, int *squarings_done, int64_t *bound,
+                         int *path, void *stream) {
+    return apsp_impl(n, W, D, flags, squarings_done, bound, path, static_cast<cudaStream_t>(stream));
+}
+
+btas_status btas_apsp_u16(int64_t n, const uint16_t *W, uint16_t *D, int max_w, int flags, void *stream) {
+    if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp_u16: n out of range");
+    if (max_w < 0 || max_w >= BTAS_INF_U16) return fail(BTAS_ERR_ARG, "btas_apsp_u16: max_w out of range");
+    if (flags & ~BTAS_APSP_EARLY_EXIT) return fail(BTAS_ERR_ARG, "btas_apsp_u16: unknown flags");
+    if (n == 0) return BTAS_OK;
+    if (!W || !D) return fail(BTAS_ERR_ARG, "btas_apsp_u16: NULL pointer");
+    if ((long long)(n - 1) * max_w >= BTAS_INF_U16)
+        return fail(BTAS_ERR_BOUND, "btas_apsp_u16: (n-1)*max_w = %lld >= 0x7FFF", (long long)(n - 1) * max_w);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int S = btas_apsp_squarings(n);
+    const size_t nn = (size_t)n * (size_t)n;
+    if (S == 0) {
+        if (D != W) BTAS_CUDA(cudaMemcpyAsync(D, W, nn * 2, cudaMemcpyDeviceToDevice, st), "copy");
+        return BTAS_OK;
+    }
+    Workspace ws(st);
+    const size_t flag_bytes = align256((size_t)(S + 1) * 4);
+    const size_t ad_bytes = align256((size_t)n * (size_t)((n + 3) & ~3LL) * 4);
+    BTAS_CUDA(ws.alloc(flag_bytes + 2 * align256(nn * 2) + ad_bytes), "workspace alloc");
+    int *dflags = static_cast<int *>(ws.p);
+    uint16_t *U1 = reinterpret_cast<uint16_t *>(static_cast<char *>(ws.p) + flag_bytes);
+    uint16_t *U2 = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(U1) + align256(nn * 2));
+    uint32_t *Ad = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(U2) + align256(nn * 2));
+    BTAS_CUDA(cudaMemsetAsync(dflags, 0, flag_bytes, st), "memset");
+    const bool early = (flags & BTAS_APSP_EARLY_EXIT) != 0;
+    const uint16_t *cur = W;
+    for (int s = 0; s < S; ++s) {
+        uint16_t *out = cur == U1 ? U2 : U1;
+        U16Args a{};
+        a.m = a.n = a.k = (int)n;
+        a.A = cur; a.lda = n;
+        a.B = cur; a.ldb = n;
+        a.C = out; a.ldc = n;
+        a.prev = cur; a.ldp = n;
+        a.changed = &dflags[s];
+        a.skip = (early && s > 0) ? &dflags[s - 1] : nullptr;
+        a.one = 1;
+        BTAS_CUDA(launch_tgemm_u16_ws(a, Ad, env_int("BTAS_U16_NS", 5), st), "u16 squaring");
+        cur = out;
+    }
+    if (cur != D) BTAS_CUDA(cudaMemcpyAsync(D, cur, nn * 2, cudaMemcpyDeviceToDevice, st), "copy");
+    return BTAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Internal interface between the C-ABI layer (btas_api.cu) and the kernel
+// translation units.  Host-side declarations only.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tgemm_args.h"
+
+namespace btas {
+
+// Process-wide count of kernels this library has enqueued (btas_kernel_launches).
+void note_launch(int n = 1);
+
+// ---- tropical GEMM kernel registry (tgemm_*.cu)
+struct GemmKernel {
+    int var;      // Variant
+    int sr;       // Semiring
+    int ns;       // kI32Mix: columns on the IMAD path
+    int cfg;      // tile configuration id
+    int bm, bn, threads, smem;
+    cudaError_t (*launch)(const GemmArgs &, cudaStream_t);
+};
+const GemmKernel *find_gemm_kernel(int var, int sr, int ns, int cfg);
+
+// ---- auxiliary kernels (aux.cu)
+// dst (cols x rows, ldd) = transpose of src (rows x cols, lds); 4-byte elements.
+// mode: 0 = copy, 1 = int32 -> fp32 carrier (INF -> +inf, -INF -> -inf),
+// 2 = fp32 carrier -> int32 (inverse).
+cudaError_t launch_transpose4(const void *src, long long lds, int rows, int cols, void *dst,
+                              long long ldd, int mode, const int *skip, cudaStream_t st);
+// Element-wise conversion of a rows x cols matrix (mode as above, 0 = copy).
+cudaError_t launch_convert4(const void *src, long long lds, int rows, int cols, void *dst,
+                            long long ldd, int mode, cudaStream_t st);
+// Fill a rows x cols matrix of 4-byte elements with `bits`.
+cudaError_t launch_fill4(void *dst, long long ldd, int rows, int cols, uint32_t bits, cudaStream_t st);
+// APSP domain scan of an n x n int32 matrix: out[0] = max finite weight,
+// out[1] = number of entries out of the domain (negative, > 2^28 and not INF,
+// or a non-zero diagonal).  out must be zeroed first.
+cudaError_t launch_apsp_scan(const int *W, long long n, int *out, cudaStream_t st);
+
+// ---- vector kernels (tvec.cu)
+cudaError_t launch_dot(int sr, int dtype, long long n, const void *x, long long incx, const void *y,
+                       long long incy, void *result, void *partials, int nblocks, cudaStream_t st);
+cudaError_t launch_axpy(int sr, int dtype, long long n, uint32_t alpha_bits, const void *x,
+                        long long incx, void *y, long long incy, cudaStream_t st);
+cudaError_t launch_ewise(int op, int sr, int dtype, long long n, const void *x, const void *y,
+                         void *z, cudaStream_t st);
+
+// ---- packed 16-bit GEMM (tgemm_u16.cu)
+struct U16Args {
+    int m, n, k;
+    const uint16_t *A; long long lda;
+    const uint16_t *B; long long ldb;   // k x n row-major (not transposed)
+    uint16_t *C; long long ldc;
+    const uint16_t *prev; long long ldp;
+    int *changed;
+    const int *skip;
+    int one;
+};
+// Duplicates A into `adup` (m x round4(k) 32-bit words, caller workspace) and
+// runs the packed product; ns = number of the 8 column pairs per thread that
+// take the IMAD + 3-input-min path (the rest use DPX).
+cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaStream_t st);
+cudaError_t launch_narrow_u16(const int *src, long long total, uint16_t *dst, cudaStream_t st);
+cudaError_t launch_widen_u16_i32(const uint16_t *src, long long total, int *dst, cudaStream_t st);
+
+}  // namespace btas

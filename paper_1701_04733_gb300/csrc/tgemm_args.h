@@ -1,0 +1,26 @@
+// Arguments of the tropical GEMM kernels (host and device visible).
+#pragma once
+
+namespace btas {
+
+enum Variant : int { kI32Dpx = 0, kI32Mix = 1, kF32X2 = 2, kF32Scalar = 3 };
+
+struct GemmArgs {
+    int m, n, k;
+    const void *A;
+    long long lda;
+    const void *Bt;  // B transposed: n x k
+    long long ldb;
+    void *C;
+    long long ldc;
+    int accumulate;     // C <- C (+) A (x) B
+    const void *prev;   // optional: output (i,j) is compared with prev[i*ldp+j]
+    long long ldp;
+    int *changed;       // set to 1 if any output differs from prev
+    const int *skip;    // optional: *skip == 0 => C = prev (converged squaring)
+    int one;            // the constant 1, opaque to the compiler
+    int vec_a, vec_b;   // operand rows are 16-byte aligned (cp.async usable)
+    int group_m;        // CTA rasterisation: tile rows per group
+};
+
+}  // namespace btas

@@ -1,0 +1,10 @@
+// Instantiations: int32, one fused DPX add-min/max per term.
+#include "tgemm_launch.cuh"
+
+namespace btas {
+const GemmKernel kGemmI32Dpx[] = {
+    entry<Cfg0, kI32Dpx, kMin, 0, 0>(), entry<Cfg0, kI32Dpx, kMax, 0, 0>(),
+    entry<Cfg2, kI32Dpx, kMin, 0, 2>(), entry<Cfg2, kI32Dpx, kMax, 0, 2>(),
+};
+const int kGemmI32DpxCount = sizeof(kGemmI32Dpx) / sizeof(kGemmI32Dpx[0]);
+}  // namespace btas

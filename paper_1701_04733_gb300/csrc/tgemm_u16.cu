@@ -1,0 +1,301 @@
+// Exact packed 16-bit min-plus product: two outputs per 32-bit lane.
+//
+// Values live in [0, 0x7FFF] with INF16 = 0x7FFF.  Output pair
+// (C[i][j], C[i][j+1]) sits in one 32-bit register; the A value A[i][l] is
+// duplicated into both halfwords (a pre-pass writes A as 32-bit words
+// A[i][l] * 0x10001), and (B[l][j], B[l][j+1]) is already adjacent in
+// row-major B.  Because every operand is <= 0x7FFF, a halfword sum is at most
+// 0xFFFE: a plain 32-bit add of two packed words never carries between the
+// halves, and the unsigned per-halfword min never sees a wrapped value.  The
+// accumulator starts at INF16 in both halves, so every result is
+// min(INF16, exact minimum) -- the saturating semantics of the 16-bit
+// encoding.  For APSP with (n-1) * max w < 0x7FFF every distance is below
+// INF16, so the result equals the int32 computation (Sec. III squaring).
+//
+// Tile: BM = 128 rows x 128 column pairs (256 columns) x BK = 32, 256
+// threads, 8 rows x 8 pairs per thread.  A (duplicated) is staged k-contiguous
+// with padded rows like the int32 kernel; B is staged as 32 rows of 128 packed
+// words.  A thread owns pairs tx*4 + {0..3} + 32*h (h = 0..3 over the two
+// warp columns), so each B fragment load is a conflict-free 128-bit load.
+// Inner loop: on NS of the 8 pairs, two 32-bit IMAD adds (FMA pipe) + one
+// 3-input per-halfword min; DPX __viaddmin_u16x2 on the others.
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace btas {
+
+namespace u16 {
+constexpr int BM = 128, BNP = 128, BK = 32, ST = 3, NT = 256;
+constexpr int LDA = BK + 4;          // words per A smem row
+constexpr int LDB = BNP;             // words per B smem row (reads are row-contiguous)
+constexpr int A_ELEMS = BM * LDA;
+constexpr int B_ELEMS = BK * LDB;
+constexpr int STAGE = A_ELEMS + B_ELEMS;
+constexpr int SMEM = ST * STAGE * 4;
+}  // namespace u16
+
+struct U16KArgs {
+    int m, n, k;
+    const uint32_t *Ad;  // m x k duplicated words
+    long long ldad;
+    const uint16_t *B;
+    long long ldb;
+    uint16_t *C;
+    long long ldc;
+    const uint16_t *prev;
+    long long ldp;
+    int *changed;
+    const int *skip;
+    int one;
+    int vec_a, vec_b;
+};
+
+__global__ void dup_u16_kernel(const uint16_t *__restrict__ A, long long lda, int m, int k, uint32_t *__restrict__ Ad,
+                               long long ldad, const int *skip) {
+    if (skip != nullptr && *skip == 0) return;
+    const long long total = (long long)m * k;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long r = idx / k, c = idx % k;
+        Ad[r * ldad + c] = 0x10001u * A[r * lda + c];
+    }
+}
+
+__global__ void narrow_u16_kernel(const int *__restrict__ src, long long total, uint16_t *__restrict__ dst) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int v = src[idx];
+        dst[idx] = (uint16_t)(v >= BTAS_INF_U16 ? BTAS_INF_U16 : v);
+    }
+}
+
+__global__ void widen_u16_i32_kernel(const uint16_t *__restrict__ src, long long total, int *__restrict__ dst) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int v = src[idx];
+        dst[idx] = v >= BTAS_INF_U16 ? kInfI32 : v;
+    }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs args) {
+    using namespace u16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *smem = reinterpret_cast<uint32_t *>(smem_raw);
+    const int M = args.m, N = args.n, K = args.k;
+    const int NP = (N + 1) / 2;  // column pairs
+    const int tid = threadIdx.x;
+    const int tiles_m = (M + BM - 1) / BM, tiles_n = (NP + BNP - 1) / BNP;
+    constexpr int GM = 8;
+    const int pid = blockIdx.x;
+    const int per_group = GM * tiles_n;
+    const int g = pid / per_group;
+    const int first_m = g * GM;
+    const int gsz = min(tiles_m - first_m, GM);
+    const int tm = first_m + (pid % per_group) % gsz;
+    const int tn = (pid % per_group) / gsz;
+    const int bm = tm * BM, bnp = tn * BNP;  // bnp in pairs; column = 2*pair
+
+    if (args.skip != nullptr && *args.skip == 0) {
+        for (int idx = tid; idx < BM * BNP * 2; idx += NT) {
+            const int r = bm + idx / (BNP * 2), c = 2 * bnp + idx % (BNP * 2);
+            if (r < M && c < N) args.C[(long long)r * args.ldc + c] = args.prev[(long long)r * args.ldp + c];
+        }
+        return;
+    }
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int ty = lane >> 3, tx = lane & 7;
+    const int row_base = wm * 32 + ty;       // + 4*i
+    const int pair_base = wn * 64 + tx * 4;  // + 32*h + q, h in {0,1}, q in 0..3
+
+    uint32_t acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = kInfU16x2;
+
+    const int KT = (K + BK - 1) / BK;
+    auto load_stage = [&](int s, int kt) {
+        uint32_t *sa = smem + s * STAGE;
+        uint32_t *sb = sa + A_ELEMS;
+        const int k0 = kt * BK;
+        // A: BM rows x BK words, 8 chunks per row
+#pragma unroll
+        for (int t = 0; t < (BM * BK / 4) / NT; ++t) {
+            const int c = tid + t * NT;
+            const int r = c >> 3, kc = (c & 7) * 4;
+            const int gr = bm + r, gk = k0 + kc;
+            uint32_t *dst = sa + r * LDA + kc;
+            if (args.vec_a && gr < M && gk + 4 <= K) {
+                cp_async16(dst, args.Ad + (long long)gr * args.ldad + gk);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    dst[e] = (gr < M && gk + e < K) ? args.Ad[(long long)gr * args.ldad + gk + e] : kInfU16x2;
+            }
+        }
+        // B: BK rows x BNP words (2*BNP u16), 32 chunks of 8 u16 per row
+#pragma unroll
+        for (int t = 0; t < (BK * BNP / 4) / NT; ++t) {
+            const int c = tid + t * NT;
+            const int r = c >> 5, wc = (c & 31) * 4;  // word column within tile
+            const int gk = k0 + r, gcol = 2 * (bnp + wc);
+            uint32_t *dst = sb + r * LDB + wc;
+            if (args.vec_b && gk < K && gcol + 8 <= N) {
+                cp_async16(dst, args.B + (long long)gk * args.ldb + gcol);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c0 = gcol + 2 * e;
+                    uint32_t lo = BTAS_INF_U16, hi = BTAS_INF_U16;
+                    if (gk < K) {
+                        if (c0 < N) lo = args.B[(long long)gk * args.ldb + c0];
+                        if (c0 + 1 < N) hi = args.B[(long long)gk * args.ldb + c0 + 1];
+                    }
+                    dst[e] = lo | (hi << 16);
+                }
+            }
+        }
+    };
+
+#pragma unroll
+    for (int s = 0; s < ST - 1; ++s) {
+        if (s < KT) load_stage(s, s);
+        cp_async_commit();
+    }
+    const int one = args.one;
+    for (int kt = 0; kt < KT; ++kt) {
+        cp_async_wait<ST - 2>();
+        __syncthreads();
+        {
+            const int nk = kt + ST - 1;
+            if (nk < KT) load_stage(nk % ST, nk);
+            cp_async_commit();
+        }
+        const uint32_t *sa = smem + (kt % ST) * STAGE;
+        const uint32_t *sb = sa + A_ELEMS;
+#pragma unroll 2
+        for (int kk = 0; kk < BK; kk += 4) {
+            uint4 a[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = *reinterpret_cast<const uint4 *>(sa + (row_base + 4 * i) * LDA + kk);
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                uint4 b0[2], b1[2];  // k = kk+2p and kk+2p+1, pairs h*32 + 0..3
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    b0[h] = *reinterpret_cast<const uint4 *>(sb + (kk + 2 * p) * LDB + pair_base + 32 * h);
+                    b1[h] = *reinterpret_cast<const uint4 *>(sb + (kk + 2 * p + 1) * LDB + pair_base + 32 * h);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const uint32_t a0 = p == 0 ? a[i].x : a[i].z, a1 = p == 0 ? a[i].y : a[i].w;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int h = j >> 2, q = j & 3;
+                        const uint32_t bb0 = q == 0 ? b0[h].x : q == 1 ? b0[h].y : q == 2 ? b0[h].z : b0[h].w;
+                        const uint32_t bb1 = q == 0 ? b1[h].x : q == 1 ? b1[h].y : q == 2 ? b1[h].z : b1[h].w;
+                        if (j < NS) {
+                            const uint32_t s0 = (uint32_t)imad_add((int)a0, one, (int)bb0);
+                            const uint32_t s1 = (uint32_t)imad_add((int)a1, one, (int)bb1);
+                            acc[i][j] = u16x2_min3(acc[i][j], s0, s1);
+                        } else {
+                            acc[i][j] = u16x2_addmin(a1, bb1, u16x2_addmin(a0, bb0, acc[i][j]));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+
+    bool ch = false;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = bm + row_base + 4 * i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int h = j >> 2, q = j & 3;
+            const int c = 2 * (bnp + pair_base + 32 * h + q);
+            const uint32_t v = acc[i][j];
+            const uint16_t lo = (uint16_t)(v & 0xFFFF), hi = (uint16_t)(v >> 16);
+            if (c < N) {
+                if (args.prev && lo != args.prev[(long long)r * args.ldp + c]) ch = true;
+                args.C[(long long)r * args.ldc + c] = lo;
+            }
+            if (c + 1 < N) {
+                if (args.prev && hi != args.prev[(long long)r * args.ldp + c + 1]) ch = true;
+                args.C[(long long)r * args.ldc + c + 1] = hi;
+            }
+        }
+    }
+    if (args.changed != nullptr) {
+        if (__any_sync(0xffffffffu, ch) && lane == 0) atomicOr(args.changed, 1);
+    }
+}
+
+static int grid_for(long long total) {
+    long long b = (total + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return b < 1 ? 1 : (int)b;
+}
+
+cudaError_t launch_narrow_u16(const int *src, long long total, uint16_t *dst, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    narrow_u16_kernel<<<grid_for(total), 256, 0, st>>>(src, total, dst);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_widen_u16_i32(const uint16_t *src, long long total, int *dst, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    widen_u16_i32_kernel<<<grid_for(total), 256, 0, st>>>(src, total, dst);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int NS>
+static cudaError_t launch_ns(const U16KArgs &ka, cudaStream_t st) {
+    auto kern = tgemm_u16_kernel<NS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, u16::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)((ka.m + u16::BM - 1) / u16::BM) * (((ka.n + 1) / 2 + u16::BNP - 1) / u16::BNP);
+    kern<<<(unsigned)tiles, u16::NT, u16::SMEM, st>>>(ka);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Runs the duplication pre-pass into `adup` (m x round4(k) words, caller
+// workspace) and the packed product.  ns selects the IMAD/DPX split.
+cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaStream_t st) {
+    const long long ldad = (a.k + 3) & ~3LL;
+    dup_u16_kernel<<<grid_for((long long)a.m * a.k), 256, 0, st>>>(a.A, a.lda, a.m, a.k, adup, ldad, a.skip);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    U16KArgs ka{};
+    ka.m = a.m; ka.n = a.n; ka.k = a.k;
+    ka.Ad = adup; ka.ldad = ldad;
+    ka.B = a.B; ka.ldb = a.ldb;
+    ka.C = a.C; ka.ldc = a.ldc;
+    ka.prev = a.prev; ka.ldp = a.ldp;
+    ka.changed = a.changed;
+    ka.skip = a.skip;
+    ka.one = 1;
+    ka.vec_a = (reinterpret_cast<uintptr_t>(adup) & 15) == 0;
+    ka.vec_b = (reinterpret_cast<uintptr_t>(a.B) & 15) == 0 && (a.ldb & 7) == 0;
+    switch (ns) {
+        case 0: return launch_ns<0>(ka, st);
+        case 4: return launch_ns<4>(ka, st);
+        case 6: return launch_ns<6>(ka, st);
+        case 8: return launch_ns<8>(ka, st);
+        default: return launch_ns<5>(ka, st);
+    }
+}
+
+}  // namespace btas

@@ -1,0 +1,157 @@
+"""GPU parity of APSP by repeated squaring (Sec. III) against the oracle:
+Floyd-Warshall (Algorithm 2), the oracle's own squaring, Dijkstra and graph
+invariants.  Distances are integers: bit-exact."""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+from gpu_util import INF, dev, host
+
+pytestmark = pytest.mark.gpu
+
+PATHS = {"int32": 0x2, "carrier": 0x8, "u16": 0x4}
+
+
+@pytest.fixture(scope="module")
+def btas():
+    import torch
+    import paper_1701_04733_gb300 as b
+    assert torch.cuda.is_available()
+    b.lib()
+    return b
+
+
+def test_config_n256_all_paths(btas, oracle_mod):
+    """One random directed graph: n = 256, p = 0.1, w in [1, 100], INF
+    off-edges, zero diagonal, 8 squarings; full matrix vs Floyd-Warshall and
+    the oracle's squaring."""
+    W = gen.random_graph(gen.BASE_SEED, 1, 256, 0.1, 1, 100)
+    ref = oracle_mod.floyd_warshall(W)
+    np.testing.assert_array_equal(oracle_mod.apsp_squaring(W), ref)
+    for name, force in PATHS.items():
+        for early in (0, 1):
+            D, info = btas.apsp(dev(W), flags=force | early, info=True)
+            np.testing.assert_array_equal(host(D), ref, err_msg=f"{name} early={early}")
+            assert info["path"] == {"int32": "int32", "carrier": "fp32-carrier", "u16": "u16x2"}[name]
+            assert info["bound"] == 255 * int(W[W < INF].max())
+    D = host(btas.apsp(dev(W)))
+    np.testing.assert_array_equal(D, ref)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 16, 32, 64, 128, 129, 200])
+def test_sizes_and_paths(btas, oracle_mod, n):
+    """Table II sizes (4..128) plus degenerate and ragged sizes."""
+    W = gen.random_graph(gen.BASE_SEED, 200 + n, n, 0.1 if n > 8 else 0.5, 1, 100)
+    ref = oracle_mod.floyd_warshall(W)
+    for force in PATHS.values():
+        np.testing.assert_array_equal(host(btas.apsp(dev(W), flags=force | 1)), ref)
+
+
+def test_in_place_and_squarings_count(btas, oracle_mod):
+    for n in (6, 9, 100, 257):  # odd and even squaring counts
+        W = gen.random_graph(3, n, n, 0.05, 0, 50)
+        ref = oracle_mod.floyd_warshall(W)
+        for force in PATHS.values():
+            t = dev(W)
+            D, info = btas.apsp(t, out=t, flags=force | 1, info=True)
+            np.testing.assert_array_equal(host(t), ref)
+            assert 0 <= info["squarings"] <= btas.btas_apsp_squarings(n)
+
+
+def test_chain_uses_every_squaring(btas):
+    """A directed path needs all ceil(log2(n-1)) squarings: early exit must
+    not stop it, and the count of changing squarings equals S."""
+    n = 300
+    W = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(W, 0)
+    W[np.arange(n - 1), np.arange(1, n)] = 1
+    D, info = btas.apsp(dev(W), flags=0x1 | 0x2, info=True)
+    D = host(D)
+    assert D[0, n - 1] == n - 1 and D[n - 1, 0] == INF
+    assert info["squarings"] == btas.btas_apsp_squarings(n)
+
+
+def test_early_exit_converges(btas, oracle_mod):
+    """A dense graph has shortest paths of few edges: early exit stops after a
+    couple of squarings and gives the same matrix."""
+    W = gen.random_graph(4, 4, 500, 0.5, 1, 10)
+    ref = oracle_mod.floyd_warshall(W)
+    D, info = btas.apsp(dev(W), flags=0x1 | 0x2, info=True)
+    np.testing.assert_array_equal(host(D), ref)
+    assert info["squarings"] < btas.btas_apsp_squarings(500)
+
+
+def test_domain_errors(btas):
+    import paper_1701_04733_gb300 as b
+    W = gen.random_graph(5, 5, 40, 0.2, 1, 9)
+    bad = W.copy()
+    bad[0, 1] = -3
+    with pytest.raises(b.BtasError):
+        btas.apsp(dev(bad))
+    bad = W.copy()
+    bad[2, 2] = 4
+    with pytest.raises(b.BtasError):
+        btas.apsp(dev(bad))
+    big = W.copy()
+    big[0, 1] = 10 ** 6  # bound 39e6 > 2^23 and > 0x7FFF
+    with pytest.raises(b.BtasError):
+        btas.apsp(dev(big), flags=0x4 | 1)
+    with pytest.raises(b.BtasError):
+        btas.apsp(dev(big), flags=0x8 | 1)
+
+
+def test_u16_entry_point(btas, oracle_mod):
+    import torch
+    n = 300
+    W32 = gen.random_graph(6, 6, n, 0.05, 1, 7)
+    W16 = np.where(W32 == INF, 0x7FFF, W32).astype(np.uint16)
+    ref = oracle_mod.apsp_squaring(W16)
+    D = btas.apsp_u16(dev(W16.view(np.int16)), 7)
+    np.testing.assert_array_equal(host(D).view(np.uint16), ref)
+    t = dev(W16.view(np.int16))
+    btas.apsp_u16(t, 7, out=t, early_exit=False)
+    np.testing.assert_array_equal(host(t).view(np.uint16), ref)
+
+
+def test_config_n4096_packed_vs_int32(btas, oracle_mod):
+    """n = 4096, p = 0.05, w in [1, 7]: (n-1)*7 = 28665 < 0x7FFF.  The packed
+    16-bit path and the int32 path agree bit-exactly, and 64 seeded rows
+    match Dijkstra."""
+    n = 4096
+    W = gen.random_graph(gen.BASE_SEED, 3, n, 0.05, 1, 7)
+    Wd = dev(W)
+    D16, i16 = btas.apsp(Wd, flags=0x4 | 1, info=True)
+    D32, i32 = btas.apsp(Wd, flags=0x2 | 1, info=True)
+    assert i16["bound"] == (n - 1) * 7
+    D16, D32 = host(D16), host(D32)
+    np.testing.assert_array_equal(D16, D32)
+    srcs = gen.sample_indices(gen.BASE_SEED, 33, 64, n)
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    try:
+        rows = oracle_mod.dijkstra_rows(W, srcs)
+    finally:
+        oracle_mod.set_threads(1)
+    np.testing.assert_array_equal(D16[srcs], rows)
+
+
+def test_config_n8192_sampled(btas, oracle_mod):
+    """n = 8192, p = 0.01, w in [1, 1000], 13 squarings: 64 seeded Dijkstra
+    rows, plus the fixpoint D (x) D = D on 64 seeded rows (oracle product
+    rows) and the zero diagonal."""
+    n = 8192
+    W = gen.random_graph(gen.BASE_SEED, 2, n, 0.01, 1, 1000)
+    D, info = btas.apsp(dev(W), info=True)
+    D = host(D)
+    assert (np.diag(D) == 0).all()
+    srcs = gen.sample_indices(gen.BASE_SEED, 34, 64, n)
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    try:
+        np.testing.assert_array_equal(D[srcs], oracle_mod.dijkstra_rows(W, srcs))
+        np.testing.assert_array_equal(oracle_mod.tgemm(0, D[srcs], D), D[srcs])
+    finally:
+        oracle_mod.set_threads(1)
+    # the int32 kernels agree with the automatically chosen path
+    D32 = host(btas.apsp(dev(W), flags=0x2 | 1))
+    np.testing.assert_array_equal(D32, D)
