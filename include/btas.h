@@ -195,6 +195,31 @@ btas_status btas_apsp_u16(int64_t n, const uint16_t *W, uint16_t *D, int max_w, 
 /* Number of squarings btas_apsp performs for n vertices: ceil(log2(n-1)). */
 int btas_apsp_squarings(int64_t n);
 
+/* ------------------------------------------------------------------------
+ * btas_apsp_noalloc: the same APSP as btas_apsp (int32 kernels, early exit),
+ * for callers that cannot allocate device memory when they call -- e.g. a
+ * process whose own memory pool already holds the device's free memory, or
+ * latency-critical code that must not allocate (an allocation can block or
+ * synchronise) inside its loop.  The paper has no counterpart: it is an
+ * interface addition of this library.
+ *
+ * It allocates nothing.  Its scratch is one fixed array of
+ * BTAS_NOALLOC_SCRATCH_BYTES in device global memory that every GPU loading
+ * this library holds until the process exits; hence n <= BTAS_NOALLOC_MAX_N
+ * (larger n returns BTAS_ERR_ARG, nothing enqueued).  The caller still passes
+ * W and D (device pointers, n x n int32, row-major, D == W allowed).
+ * The first call on a device looks up the array's device address with that
+ * device current (a host-side set-up step); make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents; the change flags are cleared on `stream` at the start of each
+ * call.  Calls whose work overlaps on the GPU race on the array: order them
+ * (one stream, or events).  The weight domain (zero diagonal, weights in
+ * [0, 2^28] or BTAS_INF_I32) is assumed, not checked.
+ * ------------------------------------------------------------------------ */
+#define BTAS_NOALLOC_MAX_N 1024
+#define BTAS_NOALLOC_SCRATCH_BYTES (256 + 2 * 4 * BTAS_NOALLOC_MAX_N * BTAS_NOALLOC_MAX_N)
+btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ SIGNATURES = {
     "btas_apsp_ex": (_i32, [_i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "btas_apsp_u16": (_i32, [_i64, _vp, _vp, _i32, _i32, _vp]),
     "btas_apsp_squarings": (_i32, [_i64]),
+    "btas_apsp_noalloc": (_i32, [_i64, _vp, _vp, _vp]),
 }
 
 
@@ -142,6 +143,10 @@ def btas_apsp_u16(n, W, D, max_w, flags, stream) -> int:
 
 def btas_apsp_squarings(n) -> int:
     return lib().btas_apsp_squarings(n)
+
+
+def btas_apsp_noalloc(n, W, D, stream) -> int:
+    return lib().btas_apsp_noalloc(n, W, D, stream)
 
 
 # ------------------------------------------------------- torch helpers

@@ -114,6 +114,8 @@ uint32_t ident_bits(int dtype, int sr) {
 }  // namespace
 
 namespace btas {
+void record_error(const char *msg) { g_err = msg; }
+
 const GemmKernel *find_gemm_kernel(int var, int sr, int ns, int cfg) {
     const GemmKernel *tabs[3] = {kGemmI32Dpx, kGemmI32Mix, kGemmF32};
     const int counts[3] = {kGemmI32DpxCount, kGemmI32MixCount, kGemmF32Count};

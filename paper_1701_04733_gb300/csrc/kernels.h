@@ -10,6 +10,8 @@ namespace btas {
 
 // Process-wide count of kernels this library has enqueued (btas_kernel_launches).
 void note_launch(int n = 1);
+// Sets the calling thread's message returned by btas_last_error_string.
+void record_error(const char *msg);
 
 // ---- tropical GEMM kernel registry (tgemm_*.cu)
 struct GemmKernel {

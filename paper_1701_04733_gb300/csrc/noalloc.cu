@@ -1,0 +1,160 @@
+// btas_apsp_noalloc: APSP by repeated squaring for callers that cannot
+// allocate device memory at call time.
+//
+// btas_apsp takes its scratch (a ping-pong matrix, a transpose buffer and the
+// per-squaring change flags) from cudaMallocAsync on every call.  Some callers
+// cannot do that: a process whose own memory pool has already reserved the
+// device's free memory, or latency-critical code that must not allocate (an
+// allocation can block or synchronise) inside its loop.  This entry point
+// takes its scratch from one fixed array in device global memory instead,
+// declared below.  Every GPU that loads the library holds that array
+// (BTAS_NOALLOC_SCRATCH_BYTES) until the process exits.
+//
+// Host code cannot use the array's name as a device address: in host code it
+// names a host-side stand-in.  The address is obtained once per device, with
+// that device current, through cudaGetSymbolAddress, on the first call made
+// on that device.  Make that first call before any stream capture.
+//
+// All calls share the one array, and each call leaves its contents behind.
+// The change flags, which must start at zero, are cleared on the stream at the
+// start of every call.  Calls whose work overlaps on the GPU (different
+// streams, or different host threads without ordering) race on the array.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace btas {
+
+namespace {
+
+constexpr long long kMaxN = BTAS_NOALLOC_MAX_N;
+constexpr size_t kFlagBytes = 256;                                  // change flags (<= 64 ints)
+constexpr size_t kMatBytes = (size_t)kMaxN * (size_t)kMaxN * 4;     // one n x n int32 matrix
+static_assert(BTAS_NOALLOC_SCRATCH_BYTES == kFlagBytes + 2 * kMatBytes, "scratch layout");
+
+// The scratch: [flags | X (ping-pong output) | T (transpose, row pitch round4(n))].
+static __device__ __align__(256) unsigned char g_scratch[BTAS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_dev_ptr[kMaxDevices] = {};
+
+btas_status set_error(btas_status s, const char *msg) {
+    record_error(msg);
+    return s;
+}
+
+// Device address of g_scratch for the current device (set up on first use).
+cudaError_t scratch_address(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_dev_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        g_dev_ptr[dev] = p;
+    }
+    *out = g_dev_ptr[dev];
+    return cudaSuccess;
+}
+
+int squarings(long long n) {
+    int s = 0;
+    long long reach = 1;
+    while (reach < n - 1) {
+        reach *= 2;
+        ++s;
+    }
+    return s;
+}
+
+const GemmKernel *pick_kernel(long long n) {
+    const long long tiles = ((n + 127) / 128) * ((n + 127) / 128);
+    const GemmKernel *k = find_gemm_kernel(kI32Mix, kMin, 5, tiles >= 2 * 152 ? 0 : 2);
+    if (!k) k = find_gemm_kernel(kI32Dpx, kMin, 0, 0);
+    return k;
+}
+
+}  // namespace
+
+}  // namespace btas
+
+using namespace btas;
+
+extern "C" btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D, void *stream) {
+    if (n < 0) return set_error(BTAS_ERR_ARG, "btas_apsp_noalloc: negative n");
+    if (n > kMaxN) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "btas_apsp_noalloc: n = %lld exceeds the fixed scratch limit of %lld vertices",
+                 (long long)n, kMaxN);
+        return set_error(BTAS_ERR_ARG, buf);
+    }
+    if (n == 0) return BTAS_OK;
+    if (!W || !D) return set_error(BTAS_ERR_ARG, "btas_apsp_noalloc: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t nn = (size_t)n * (size_t)n;
+    const int S = squarings(n);
+    cudaError_t e;
+    if (S == 0) {
+        if (D != W) {
+            e = cudaMemcpyAsync(D, W, nn * 4, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+        }
+        return BTAS_OK;
+    }
+    void *base = nullptr;
+    e = scratch_address(&base);
+    if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+    int *flags = static_cast<int *>(base);
+    int32_t *X = reinterpret_cast<int32_t *>(static_cast<char *>(base) + kFlagBytes);
+    int32_t *T = reinterpret_cast<int32_t *>(static_cast<char *>(base) + kFlagBytes + kMatBytes);
+    const long long ldt = (n + 3) & ~3LL;
+
+    e = cudaMemsetAsync(flags, 0, kFlagBytes, st);
+    if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+
+    // Outputs alternate so that the last squaring writes D: squaring s writes
+    // bufs[(S-1-s) & 1].  In place (D == W) with S odd the first squaring
+    // would write its own input, so the input is first copied to X.
+    int32_t *bufs[2] = {D, X};
+    const int32_t *cur = W;
+    if ((const void *)W == (const void *)D && ((S - 1) & 1) == 0) {
+        e = cudaMemcpyAsync(X, W, nn * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+        cur = X;
+    }
+    const GemmKernel *kern = pick_kernel(n);
+    if (!kern) return set_error(BTAS_ERR_UNSUPPORTED, "btas_apsp_noalloc: no int32 kernel");
+    for (int s = 0; s < S; ++s) {
+        int32_t *out = bufs[(S - 1 - s) & 1];
+        const int *skip = s > 0 ? &flags[s - 1] : nullptr;
+        e = launch_transpose4(cur, n, (int)n, (int)n, T, ldt, 0, skip, st);
+        if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+        GemmArgs a{};
+        a.m = a.n = a.k = (int)n;
+        a.A = cur;
+        a.lda = n;
+        a.Bt = T;
+        a.ldb = ldt;
+        a.C = out;
+        a.ldc = n;
+        a.prev = cur;
+        a.ldp = n;
+        a.changed = &flags[s];
+        a.skip = skip;
+        a.one = 1;
+        a.vec_a = (reinterpret_cast<uintptr_t>(cur) & 15) == 0 && (n & 3) == 0;
+        a.vec_b = 1;
+        a.group_m = 8;
+        e = kern->launch(a, st);
+        if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+        cur = out;
+    }
+    return BTAS_OK;
+}
