@@ -156,8 +156,10 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  *     the algorithm for non-negative edge weights).
  * D : n x n int32 output; D == W (in place) is allowed, any other overlap is
  *     not.
- * Domain checks run on the device and are not reported by btas_apsp; use
- * btas_apsp_ex to get them.
+ * btas_apsp checks the domain on the device (one synchronisation of
+ * `stream`; BTAS_ERR_ARG if violated), enables the early exit, and picks the
+ * exact representation per squaring as btas_apsp_ex does without FORCE
+ * flags.
  * ------------------------------------------------------------------------ */
 btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
@@ -168,18 +170,30 @@ btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
 #define BTAS_APSP_FORCE_CARRIER 0x8 /* require the FP32-carrier path; BTAS_ERR_BOUND if not exact */
 
 /* btas_apsp_ex: as btas_apsp, with
- *  flags           : BTAS_APSP_* bits.  Without FORCE bits the fastest exact
- *                    path is chosen from the bound B = (n-1) * max finite w:
- *                    packed 16-bit if B < 0x7FFF, FP32 carrier if
- *                    B < 2^23, else int32.  The bound is computed on the
- *                    device, so path selection synchronises `stream`.
+ *  flags           : BTAS_APSP_* bits.
+ *                    Without FORCE bits the representation is chosen per
+ *                    squaring from m = the largest finite entry of D_s (every
+ *                    finite entry of D_{s+1} and every pairwise sum is <= 2m):
+ *                    packed 16-bit if 2m < 0x7FFF, exact FP32 carrier if
+ *                    2m < 2^24, else int32.  Each squaring's epilogue reports
+ *                    the next m, so this mode synchronises `stream` once per
+ *                    squaring.  FORCE_U16 / FORCE_CARRIER pin one
+ *                    representation and require the static bound
+ *                    B = (n-1) * max w to be below 0x7FFF / 2^23
+ *                    (BTAS_ERR_BOUND otherwise).  FORCE_I32 with
+ *                    bound == NULL runs int32 squarings without any host
+ *                    synchronisation (the early exit is then decided on the
+ *                    device: a converged squaring copies its input through).
  *  squarings_done  : HOST pointer or NULL; receives the number of squarings
- *                    that changed D (<= S).  Non-NULL synchronises `stream`.
+ *                    that changed D (<= S).
  *  bound           : HOST pointer or NULL; receives B (or -1 if W has a
  *                    negative or out-of-domain entry, in which case the call
  *                    returns BTAS_ERR_ARG after synchronising).
- *  path            : HOST pointer or NULL; receives 0 = int32, 1 = FP32
- *                    carrier, 2 = packed 16-bit.
+ *  path            : HOST pointer or NULL; receives the set of
+ *                    representations used, as bits: 1 = int32, 2 = FP32
+ *                    carrier, 4 = packed 16-bit.
+ * The domain scan (zero diagonal, weights in [0, 2^28] or INF) runs on the
+ * device and synchronises `stream` once, except in the FORCE_I32 mode above.
  */
 btas_status btas_apsp_ex(int64_t n, const int32_t *W, int32_t *D, int flags,
                          int *squarings_done, int64_t *bound, int *path, void *stream);
@@ -219,6 +233,51 @@ int btas_apsp_squarings(int64_t n);
 #define BTAS_NOALLOC_MAX_N 1024
 #define BTAS_NOALLOC_SCRATCH_BYTES (256 + 2 * 4 * BTAS_NOALLOC_MAX_N * BTAS_NOALLOC_MAX_N)
 btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched execution: many independent tropical products and APSP solves of
+ * uneven sizes in ONE persistent kernel launch (captured once in a CUDA
+ * graph and replayed).  Same arithmetic and bit-identical results as the
+ * single calls; the batch only changes scheduling: 128 x 128 tile tasks are
+ * ordered by level (transposes, then squaring 1, 2, ...) and, within a level,
+ * largest instance first; persistent CTAs claim tasks from a global counter
+ * and wait (bounded) for the previous level of their own instance.
+ *
+ * btas_batch_create  : *out receives a new empty batch.  flags:
+ *                      BTAS_BATCH_NO_GRAPH launches the kernel directly
+ *                      instead of replaying a captured graph.
+ * btas_batch_add_apsp: APSP by repeated squaring of W into D (device, n x n
+ *                      int32, leading dimension n), as btas_apsp with int32
+ *                      kernels and the early exit.  D must not overlap W.
+ *                      The domain (zero diagonal, weights in [0, 2^28] or
+ *                      INF) is assumed, not checked.
+ * btas_batch_add_gemm: C = A (x) B as btas_gemm (int32 or fp32, min-plus or
+ *                      max-plus, optional BTAS_GEMM_TRANS_B; m, n, k >= 1).
+ * btas_batch_launch  : enqueues the whole batch on `stream`.  The first
+ *                      launch after an add builds the plan: it allocates the
+ *                      device workspace (cudaMalloc; not stream-ordered) and
+ *                      captures the graph, so it must not itself be inside a
+ *                      stream capture.  Later launches replay the graph.
+ *                      The caller's buffers must stay valid until the work
+ *                      completes.
+ * btas_batch_wait    : synchronises `stream` and returns the device status
+ *                      word: BTAS_ERR_TIMEOUT if a bounded wait expired
+ *                      (every CTA then stops; results are incomplete).
+ * btas_batch_destroy : frees the plan and the batch (call after the work has
+ *                      completed).
+ * btas_batch_workspace_bytes / btas_batch_tasks: plan size diagnostics.
+ * ------------------------------------------------------------------------ */
+typedef struct btas_batch_t btas_batch_t;
+#define BTAS_BATCH_NO_GRAPH 0x1
+btas_status btas_batch_create(btas_batch_t **out, int flags);
+btas_status btas_batch_add_apsp(btas_batch_t *b, int64_t n, const int32_t *W, int32_t *D);
+btas_status btas_batch_add_gemm(btas_batch_t *b, int semiring, int dtype, int64_t m, int64_t n, int64_t k,
+                                const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc);
+btas_status btas_batch_launch(btas_batch_t *b, void *stream);
+btas_status btas_batch_wait(btas_batch_t *b, void *stream);
+btas_status btas_batch_destroy(btas_batch_t *b);
+int64_t btas_batch_workspace_bytes(btas_batch_t *b);
+int btas_batch_tasks(btas_batch_t *b);
 
 #ifdef __cplusplus
 }

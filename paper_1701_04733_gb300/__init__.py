@@ -65,6 +65,14 @@ SIGNATURES = {
     "btas_apsp_u16": (_i32, [_i64, _vp, _vp, _i32, _i32, _vp]),
     "btas_apsp_squarings": (_i32, [_i64]),
     "btas_apsp_noalloc": (_i32, [_i64, _vp, _vp, _vp]),
+    "btas_batch_create": (_i32, [_vp, _i32]),
+    "btas_batch_add_apsp": (_i32, [_vp, _i64, _vp, _vp]),
+    "btas_batch_add_gemm": (_i32, [_vp, _i32, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64]),
+    "btas_batch_launch": (_i32, [_vp, _vp]),
+    "btas_batch_wait": (_i32, [_vp, _vp]),
+    "btas_batch_destroy": (_i32, [_vp]),
+    "btas_batch_workspace_bytes": (_i64, [_vp]),
+    "btas_batch_tasks": (_i32, [_vp]),
 }
 
 
@@ -147,6 +155,38 @@ def btas_apsp_squarings(n) -> int:
 
 def btas_apsp_noalloc(n, W, D, stream) -> int:
     return lib().btas_apsp_noalloc(n, W, D, stream)
+
+
+def btas_batch_create(out_ptr, flags) -> int:
+    return lib().btas_batch_create(out_ptr, flags)
+
+
+def btas_batch_add_apsp(b, n, W, D) -> int:
+    return lib().btas_batch_add_apsp(b, n, W, D)
+
+
+def btas_batch_add_gemm(b, semiring, dtype, m, n, k, A, lda, B, ldb, C, ldc) -> int:
+    return lib().btas_batch_add_gemm(b, semiring, dtype, m, n, k, A, lda, B, ldb, C, ldc)
+
+
+def btas_batch_launch(b, stream) -> int:
+    return lib().btas_batch_launch(b, stream)
+
+
+def btas_batch_wait(b, stream) -> int:
+    return lib().btas_batch_wait(b, stream)
+
+
+def btas_batch_destroy(b) -> int:
+    return lib().btas_batch_destroy(b)
+
+
+def btas_batch_workspace_bytes(b) -> int:
+    return lib().btas_batch_workspace_bytes(b)
+
+
+def btas_batch_tasks(b) -> int:
+    return lib().btas_batch_tasks(b)
 
 
 # ------------------------------------------------------- torch helpers
@@ -233,7 +273,8 @@ def apsp(W, out=None, flags=APSP_EARLY_EXIT, stream=None, info=False):
     if info:
         check(btas_apsp_ex(n, W.data_ptr(), out.data_ptr(), flags, ctypes.addressof(sq), ctypes.addressof(bd),
                            ctypes.addressof(pt), _stream(stream)))
-        return out, {"squarings": sq.value, "bound": bd.value, "path": ("int32", "fp32-carrier", "u16x2")[pt.value]}
+        names = [nm for bit, nm in ((1, "int32"), (2, "fp32-carrier"), (4, "u16x2")) if pt.value & bit]
+        return out, {"squarings": sq.value, "bound": bd.value, "path": "+".join(names)}
     if flags == APSP_EARLY_EXIT:
         check(btas_apsp(n, W.data_ptr(), out.data_ptr(), _stream(stream)))
     else:
@@ -289,3 +330,61 @@ def mul(x, y, semiring="min", out=None, stream=None):
     check(btas_mul(_sr(semiring), _dtype_code(x), x.numel(), x.data_ptr(), y.data_ptr(), out.data_ptr(),
                    _stream(stream)))
     return out
+
+
+BATCH_NO_GRAPH = 0x1
+
+
+class Batch:
+    """Many APSP solves and tropical products in one persistent launch
+    (btas_batch_*).  Keep the tensors alive until `wait()` returns."""
+
+    def __init__(self, graph: bool = True):
+        h = ctypes.c_void_p()
+        check(btas_batch_create(ctypes.addressof(h), 0 if graph else BATCH_NO_GRAPH))
+        self.handle = h.value
+        self._keep = []
+
+    def add_apsp(self, W, D):
+        torch = _torch()
+        n = W.shape[0]
+        if W.dtype != torch.int32 or W.shape != (n, n) or not W.is_contiguous() or not D.is_contiguous():
+            raise ValueError("W, D must be contiguous n x n int32 tensors")
+        check(btas_batch_add_apsp(self.handle, n, W.data_ptr(), D.data_ptr()))
+        self._keep += [W, D]
+        return D
+
+    def add_gemm(self, A, B, C, semiring="min", trans_b=False):
+        m, k = A.shape
+        n = B.shape[0] if trans_b else B.shape[1]
+        flags = _sr(semiring) | (GEMM_TRANS_B if trans_b else 0)
+        check(btas_batch_add_gemm(self.handle, flags, _dtype_code(A), m, n, k, A.data_ptr(), _rowmajor(A, "A"),
+                                  B.data_ptr(), _rowmajor(B, "B"), C.data_ptr(), _rowmajor(C, "C")))
+        self._keep += [A, B, C]
+        return C
+
+    def launch(self, stream=None):
+        check(btas_batch_launch(self.handle, _stream(stream)))
+
+    def wait(self, stream=None):
+        check(btas_batch_wait(self.handle, _stream(stream)))
+
+    @property
+    def tasks(self) -> int:
+        return btas_batch_tasks(self.handle)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return btas_batch_workspace_bytes(self.handle)
+
+    def close(self):
+        if self.handle:
+            btas_batch_destroy(self.handle)
+            self.handle = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,521 @@
+// Batched tropical products and APSP solves in one persistent launch.
+//
+// Many independent problems of uneven size (APSP by repeated squaring,
+// Sec. III, and single tropical products) are cut into 128 x 128 tile tasks.
+// Tasks are ordered by level -- level 0: transposes into the k-contiguous
+// B-operand layout; level s >= 1: the tiles of squaring s (a product has one
+// level) -- and, within a level, by instance, largest first.  Persistent CTAs
+// claim tasks from one global counter.  A task of level s waits until every
+// task of level s-1 of its own instance is done (a per-(instance, level)
+// completion counter).  Tasks are claimed in level order, so every task a CTA
+// waits on was claimed earlier by a CTA that is running: the schedule cannot
+// deadlock, and no co-residency assumption is needed.  Every wait is bounded
+// (clock64 budget); on expiry the CTA records BTAS_ERR_TIMEOUT in a device
+// status word and stops, and the other CTAs see the word and stop too.
+//
+// An APSP squaring tile also stores its output transposed (through shared
+// memory), so the next squaring finds its B operand ready; a squaring whose
+// predecessor changed nothing copies its input through (early exit with an
+// unchanged result).  The launch (counter reset + kernel) is captured once in
+// a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tgemm.cuh"
+
+namespace btas {
+
+using BCfg = TileCfg<128, 128, 32, 3, 2, 2, 1>;  // 2 CTAs/SM, <= 128 registers
+constexpr int kBT = 128;                          // task tile edge
+
+enum TaskType : int { kTaskTranspose = 0, kTaskApsp = 1, kTaskGemm = 2, kTaskCopy = 3 };
+enum InstKind : int { kInstApsp = 0, kInstGemm = 1 };
+
+struct BInst {
+    int kind, sr, dtype;
+    int m, n, k;
+    int levels;           // APSP: S (>= 1); GEMM: 1
+    int tiles_m, tiles_n; // output tiles
+    int t0_rows, t0_cols; // level-0 transpose source shape (0 x 0: none)
+    int done_base;        // done[done_base + level]
+    int flag_base;        // changed[flag_base + level]
+    int trans_b;
+    const void *A;        // GEMM A / APSP W
+    long long lda;
+    const void *B;        // GEMM B (k x n, or n x k if trans_b)
+    long long ldb;
+    void *C;              // GEMM C / APSP D
+    long long ldc;
+    void *X0, *X1;        // APSP intermediate D_s (n x n, pitch ldx)
+    long long ldx;
+    void *Q0, *Q1;        // APSP transposes / GEMM B^T (Q0)
+    long long ldq;
+};
+
+struct BatchParams {
+    const int4 *tasks;  // (type, inst, level, tile)
+    int total;
+    int *next;
+    int *done;
+    int *changed;
+    int *status;
+    const BInst *insts;
+    long long timeout_cycles;
+    int withhold_inst;  // fault injection for tests: this instance's level-1+ tasks never become ready
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int tasks_at(const BInst &I, int level) {
+    if (level == 0) return I.t0_rows > 0 ? ((I.t0_rows + kBT - 1) / kBT) * ((I.t0_cols + kBT - 1) / kBT) : 0;
+    return I.tiles_m * I.tiles_n;
+}
+
+// 128 x 128 transpose of a 4-byte matrix through shared memory.
+__device__ __forceinline__ void transpose_tile(const uint32_t *src, long long lds, int rows, int cols, uint32_t *dst,
+                                               long long ldd, int tile, uint32_t *sm, int tid) {
+    const int tiles_c = (cols + kBT - 1) / kBT;
+    const int r0 = (tile / tiles_c) * kBT, c0 = (tile % tiles_c) * kBT;
+    for (int idx = tid; idx < kBT * kBT; idx += BCfg::kThreads) {
+        const int r = idx / kBT, c = idx % kBT;
+        if (r0 + r < rows && c0 + c < cols) sm[c * (kBT + 1) + r] = __ldcg(src + (long long)(r0 + r) * lds + c0 + c);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < kBT * kBT; idx += BCfg::kThreads) {
+        const int c = idx / kBT, r = idx % kBT;
+        if (r0 + r < rows && c0 + c < cols) dst[(long long)(c0 + c) * ldd + r0 + r] = sm[c * (kBT + 1) + r];
+    }
+    __syncthreads();
+}
+
+template <int VAR, int SR>
+__device__ __forceinline__ bool gemm_tile(const GemmArgs &a, int bm, int bn, unsigned char *smem, int tid,
+                                          void *Ct = nullptr, long long ldct = 0) {
+    return nt_tile<BCfg, VAR, SR, 4>(a, bm, bn, smem, tid, Ct, ldct);
+}
+
+__global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const BatchParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_task[4];
+    __shared__ int s_flag;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            const int t = atomicAdd(p.next, 1);
+            int4 w = make_int4(-1, 0, 0, 0);
+            if (t < p.total && ld_acquire(p.status) == 0) w = p.tasks[t];
+            s_task[0] = w.x; s_task[1] = w.y; s_task[2] = w.z; s_task[3] = w.w;
+            s_flag = 1;
+            if (w.x >= 0 && w.z > 0) {
+                // wait until every task of the previous level of this instance is done
+                const BInst &I = p.insts[w.y];
+                const int need = tasks_at(I, w.z - 1) + (w.y == p.withhold_inst ? 1 : 0);
+                const int *cnt = p.done + I.done_base + w.z - 1;
+                const long long t0 = clock64();
+                while (ld_acquire(cnt) < need) {
+                    if (ld_acquire(p.status) != 0) { s_task[0] = -1; break; }
+                    if (clock64() - t0 > p.timeout_cycles) {
+                        atomicCAS(p.status, 0, BTAS_ERR_TIMEOUT);
+                        s_task[0] = -1;
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                if (s_task[0] >= 0 && I.kind == kInstApsp && w.z >= 2)
+                    s_flag = ld_acquire(p.changed + I.flag_base + w.z - 1);
+            }
+        }
+        __syncthreads();
+        const int type = s_task[0], inst = s_task[1], level = s_task[2], tile = s_task[3];
+        const int prev_changed = s_flag;
+        __syncthreads();
+        if (type < 0) break;
+        const BInst I = p.insts[inst];
+        bool ch = false;
+        if (type == kTaskTranspose) {
+            const uint32_t *src = static_cast<const uint32_t *>(I.kind == kInstApsp ? I.A : I.B);
+            const long long lds = I.kind == kInstApsp ? I.lda : I.ldb;
+            transpose_tile(src, lds, I.t0_rows, I.t0_cols, static_cast<uint32_t *>(I.Q0), I.ldq, tile,
+                           reinterpret_cast<uint32_t *>(smem_raw), tid);
+        } else if (type == kTaskCopy) {
+            // n <= 2: D = W
+            const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
+            GemmArgs a{};
+            a.m = I.n; a.n = I.n;
+            a.prev = I.A; a.ldp = I.lda;
+            a.C = I.C; a.ldc = I.ldc;
+            copy_tile<BCfg, int>(a, bm, bn, tid);
+        } else if (type == kTaskApsp) {
+            const int S = I.levels, s = level;  // squaring s (1-based) of S
+            // D_1..D_{S-1} alternate between X0 and X1 (aligned pitch ldx);
+            // the last squaring writes D
+            const void *cur = s == 1 ? I.A : ((s - 1) & 1 ? I.X0 : I.X1);
+            const long long ldcur = s == 1 ? I.lda : I.ldx;
+            void *out = s == S ? I.C : (s & 1 ? I.X0 : I.X1);
+            const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
+            GemmArgs a{};
+            a.m = a.n = a.k = I.n;
+            a.A = cur; a.lda = ldcur;
+            a.Bt = (s & 1) ? I.Q0 : I.Q1; a.ldb = I.ldq;
+            a.C = out; a.ldc = s == S ? I.ldc : I.ldx;
+            a.prev = cur; a.ldp = ldcur;
+            a.one = 1;
+            a.vec_a = ((reinterpret_cast<uintptr_t>(cur) & 15) == 0) && ((ldcur & 3) == 0);
+            a.vec_b = 1;
+            if (s >= 2 && prev_changed == 0) {
+                copy_tile<BCfg, int>(a, bm, bn, tid);
+            } else {
+                void *Ct = s < S ? ((s & 1) ? I.Q1 : I.Q0) : nullptr;
+                ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, Ct, I.ldq);
+            }
+        } else {  // kTaskGemm
+            const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
+            GemmArgs a{};
+            a.m = I.m; a.n = I.n; a.k = I.k;
+            a.A = I.A; a.lda = I.lda;
+            a.Bt = I.trans_b ? I.B : I.Q0; a.ldb = I.trans_b ? I.ldb : I.ldq;
+            a.C = I.C; a.ldc = I.ldc;
+            a.one = 1;
+            a.vec_a = ((reinterpret_cast<uintptr_t>(I.A) & 15) == 0) && ((I.lda & 3) == 0);
+            a.vec_b = ((reinterpret_cast<uintptr_t>(a.Bt) & 15) == 0) && ((a.ldb & 3) == 0);
+            if (I.dtype == BTAS_I32) {
+                if (I.sr == kMin) gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid);
+                else gemm_tile<kI32Mix, kMax>(a, bm, bn, smem_raw, tid);
+            } else {
+                if (I.sr == kMin) gemm_tile<kF32X2, kMin>(a, bm, bn, smem_raw, tid);
+                else gemm_tile<kF32X2, kMax>(a, bm, bn, smem_raw, tid);
+            }
+        }
+        if (type == kTaskApsp && __any_sync(0xffffffffu, ch) && (tid & 31) == 0)
+            atomicOr(p.changed + I.flag_base + level, 1);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(p.done + I.done_base + level, 1);
+    }
+}
+
+}  // namespace btas
+
+using namespace btas;
+
+// ------------------------------------------------------------------ host side
+
+struct btas_batch_t {
+    struct Req {
+        BInst inst;
+        long long work;  // terms, for ordering
+    };
+    std::vector<Req> reqs;
+    int flags = 0;
+    bool dirty = true;
+    // plan
+    void *dev_mem = nullptr;  // tasks | insts | counters | workspace
+    size_t dev_bytes = 0;
+    int total = 0;
+    int *d_counters = nullptr;  // next | status | done[] | changed[]
+    size_t counter_bytes = 0;
+    BatchParams params{};
+    int grid = 0;
+    int smem = 0;
+    int device = -1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    long long workspace_bytes = 0;
+};
+
+namespace {
+
+size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int squarings_of(long long n) {
+    int s = 0;
+    long long reach = 1;
+    while (reach < n - 1) {
+        reach *= 2;
+        ++s;
+    }
+    return s;
+}
+
+void release_plan(btas_batch_t *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->dev_mem) cudaFree(b->dev_mem);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->dev_mem = nullptr;
+}
+
+btas_status bfail(btas_status s, const char *msg) {
+    record_error(msg);
+    return s;
+}
+
+btas_status build_plan(btas_batch_t *b) {
+    release_plan(b);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return bfail(BTAS_ERR_CUDA, "btas_batch: cudaGetDevice failed");
+    b->device = dev;
+    const size_t ninst = b->reqs.size();
+    // order instances by work, largest first
+    std::vector<int> order(ninst);
+    for (size_t i = 0; i < ninst; ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->reqs[x].work > b->reqs[y].work; });
+    // workspace per instance and counter bases
+    std::vector<BInst> insts(ninst);
+    size_t ws = 0;
+    int counters = 0, max_level = 0;
+    std::vector<size_t> ws_off(ninst);
+    for (size_t i = 0; i < ninst; ++i) {
+        BInst I = b->reqs[i].inst;
+        ws_off[i] = ws;
+        if (I.kind == kInstApsp) {
+            if (I.levels > 0) {
+                I.ldq = (I.n + 3) & ~3LL;
+                I.ldx = I.ldq;
+                ws += 4 * al256((size_t)I.n * I.ldq * 4);
+            }
+        } else if (!I.trans_b) {
+            I.ldq = (I.k + 3) & ~3LL;
+            ws += al256((size_t)I.n * I.ldq * 4);
+        }
+        I.done_base = counters;
+        I.flag_base = counters;
+        counters += (I.levels > 0 ? I.levels : 1) + 1;
+        max_level = std::max(max_level, I.levels > 0 ? I.levels : 1);
+        insts[i] = I;
+    }
+    // tasks
+    std::vector<int4> tasks;
+    for (int level = 0; level <= max_level; ++level) {
+        for (int oi : order) {
+            const BInst &I = insts[oi];
+            if (level == 0) {
+                if (I.t0_rows > 0) {
+                    const int nt = ((I.t0_rows + kBT - 1) / kBT) * ((I.t0_cols + kBT - 1) / kBT);
+                    for (int t = 0; t < nt; ++t) tasks.push_back(make_int4(kTaskTranspose, oi, 0, t));
+                }
+                continue;
+            }
+            const int nt = I.tiles_m * I.tiles_n;
+            if (I.kind == kInstApsp && I.levels == 0) {
+                if (level == 1)
+                    for (int t = 0; t < nt; ++t) tasks.push_back(make_int4(kTaskCopy, oi, 1, t));
+            } else if (I.kind == kInstApsp && level <= I.levels) {
+                for (int t = 0; t < nt; ++t) tasks.push_back(make_int4(kTaskApsp, oi, level, t));
+            } else if (I.kind == kInstGemm && level == 1) {
+                for (int t = 0; t < nt; ++t) tasks.push_back(make_int4(kTaskGemm, oi, 1, t));
+            }
+        }
+    }
+    b->total = (int)tasks.size();
+    const size_t task_bytes = al256(tasks.size() * sizeof(int4));
+    const size_t inst_bytes = al256(ninst * sizeof(BInst));
+    b->counter_bytes = al256((size_t)(2 + 2 * counters) * 4);
+    b->workspace_bytes = (long long)ws;
+    b->dev_bytes = task_bytes + inst_bytes + b->counter_bytes + ws;
+    if (cudaMalloc(&b->dev_mem, b->dev_bytes ? b->dev_bytes : 256) != cudaSuccess)
+        return bfail(BTAS_ERR_NOMEM, "btas_batch: workspace allocation failed");
+    char *base = static_cast<char *>(b->dev_mem);
+    int4 *d_tasks = reinterpret_cast<int4 *>(base);
+    BInst *d_insts = reinterpret_cast<BInst *>(base + task_bytes);
+    b->d_counters = reinterpret_cast<int *>(base + task_bytes + inst_bytes);
+    char *d_ws = base + task_bytes + inst_bytes + b->counter_bytes;
+    for (size_t i = 0; i < ninst; ++i) {
+        BInst &I = insts[i];
+        char *w = d_ws + ws_off[i];
+        if (I.kind == kInstApsp && I.levels > 0) {
+            const size_t blk = al256((size_t)I.n * I.ldq * 4);
+            I.X0 = w;
+            I.X1 = w + blk;
+            I.Q0 = w + 2 * blk;
+            I.Q1 = w + 3 * blk;
+        } else if (I.kind == kInstGemm && !I.trans_b) {
+            I.Q0 = w;
+        }
+    }
+    if (cudaMemcpy(d_tasks, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_insts, insts.data(), ninst * sizeof(BInst), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(BTAS_ERR_CUDA, "btas_batch: plan upload failed");
+    BatchParams &p = b->params;
+    p.tasks = d_tasks;
+    p.total = b->total;
+    p.next = b->d_counters;
+    p.status = b->d_counters + 1;
+    p.done = b->d_counters + 2;
+    p.changed = b->d_counters + 2 + counters;
+    p.insts = d_insts;
+    int clk_khz = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    const double secs = 2.0;
+    p.timeout_cycles = (long long)(secs * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);
+    const char *tmo = getenv("BTAS_BATCH_TIMEOUT_CYCLES");
+    if (tmo && *tmo) p.timeout_cycles = atoll(tmo);
+    // Fault injection (tests only): BTAS_BATCH_WITHHOLD=i makes the host
+    // withhold one completion of instance i (in add order), so its bounded
+    // waits run out and the launch ends with BTAS_ERR_TIMEOUT.
+    const char *wh = getenv("BTAS_BATCH_WITHHOLD");
+    p.withhold_inst = (wh && *wh) ? atoi(wh) : -1;
+    // grid: resident CTAs
+    b->smem = std::max(BCfg::kSmemBytes, kBT * (kBT + 1) * 4);
+    if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem) != cudaSuccess)
+        return bfail(BTAS_ERR_CUDA, "btas_batch: smem attribute");
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, BCfg::kThreads, b->smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = std::max(1, std::min(per_sm * sms, std::max(1, b->total)));
+    // capture: counter reset + persistent kernel
+    if (!(b->flags & BTAS_BATCH_NO_GRAPH)) {
+        if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+            return bfail(BTAS_ERR_CUDA, "btas_batch: stream create");
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return bfail(BTAS_ERR_CUDA, "btas_batch: begin capture");
+        cudaMemsetAsync(b->d_counters, 0, b->counter_bytes, b->cap);
+        batch_kernel<<<b->grid, BCfg::kThreads, b->smem, b->cap>>>(p);
+        const cudaError_t e1 = cudaStreamEndCapture(b->cap, &b->graph);
+        if (e1 != cudaSuccess) return bfail(BTAS_ERR_CUDA, "btas_batch: end capture");
+        if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+            return bfail(BTAS_ERR_CUDA, "btas_batch: graph instantiate");
+    }
+    b->dirty = false;
+    return BTAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+btas_status btas_batch_create(btas_batch_t **out, int flags) {
+    if (!out) return bfail(BTAS_ERR_ARG, "btas_batch_create: NULL out");
+    if (flags & ~BTAS_BATCH_NO_GRAPH) return bfail(BTAS_ERR_ARG, "btas_batch_create: unknown flags");
+    btas_batch_t *b = new btas_batch_t();
+    b->flags = flags;
+    *out = b;
+    return BTAS_OK;
+}
+
+btas_status btas_batch_destroy(btas_batch_t *b) {
+    if (!b) return BTAS_OK;
+    release_plan(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return BTAS_OK;
+}
+
+btas_status btas_batch_add_apsp(btas_batch_t *b, int64_t n, const int32_t *W, int32_t *D) {
+    if (!b) return bfail(BTAS_ERR_ARG, "btas_batch_add_apsp: NULL batch");
+    if (n < 1 || n > 46340) return bfail(BTAS_ERR_ARG, "btas_batch_add_apsp: n out of range");
+    if (!W || !D) return bfail(BTAS_ERR_ARG, "btas_batch_add_apsp: NULL pointer");
+    const char *wb = reinterpret_cast<const char *>(W), *db = reinterpret_cast<const char *>(D);
+    const size_t bytes = (size_t)n * n * 4;
+    if (wb < db + bytes && db < wb + bytes) return bfail(BTAS_ERR_ARG, "btas_batch_add_apsp: W and D overlap");
+    BInst I{};
+    I.kind = kInstApsp;
+    I.sr = kMin;
+    I.dtype = BTAS_I32;
+    I.m = I.n = I.k = (int)n;
+    I.levels = squarings_of(n);
+    I.tiles_m = I.tiles_n = (int)((n + kBT - 1) / kBT);
+    if (I.levels > 0) {
+        I.t0_rows = I.t0_cols = (int)n;
+    }
+    I.A = W;
+    I.lda = n;
+    I.C = D;
+    I.ldc = n;
+    b->reqs.push_back({I, (long long)n * n * n * std::max(1, I.levels)});
+    b->dirty = true;
+    return BTAS_OK;
+}
+
+btas_status btas_batch_add_gemm(btas_batch_t *b, int semiring, int dtype, int64_t m, int64_t n, int64_t k,
+                                const void *A, int64_t lda, const void *B, int64_t ldb, void *C, int64_t ldc) {
+    if (!b) return bfail(BTAS_ERR_ARG, "btas_batch_add_gemm: NULL batch");
+    const int sr = semiring & 0xff;
+    const bool trans_b = (semiring & BTAS_GEMM_TRANS_B) != 0;
+    if (semiring & ~(0xff | BTAS_GEMM_TRANS_B)) return bfail(BTAS_ERR_ARG, "btas_batch_add_gemm: flags");
+    if (sr != kMin && sr != kMax) return bfail(BTAS_ERR_ARG, "btas_batch_add_gemm: semiring");
+    if (dtype != BTAS_I32 && dtype != BTAS_F32) return bfail(BTAS_ERR_UNSUPPORTED, "btas_batch_add_gemm: dtype");
+    if (m < 1 || n < 1 || k < 1 || m > INT32_MAX || n > INT32_MAX || k > INT32_MAX)
+        return bfail(BTAS_ERR_ARG, "btas_batch_add_gemm: sizes must be >= 1");
+    if (lda < k || ldc < n || ldb < (trans_b ? k : n)) return bfail(BTAS_ERR_ARG, "btas_batch_add_gemm: ld");
+    if (!A || !B || !C) return bfail(BTAS_ERR_ARG, "btas_batch_add_gemm: NULL pointer");
+    BInst I{};
+    I.kind = kInstGemm;
+    I.sr = sr;
+    I.dtype = dtype;
+    I.m = (int)m;
+    I.n = (int)n;
+    I.k = (int)k;
+    I.levels = 1;
+    I.tiles_m = (int)((m + kBT - 1) / kBT);
+    I.tiles_n = (int)((n + kBT - 1) / kBT);
+    I.trans_b = trans_b ? 1 : 0;
+    if (!trans_b) {
+        I.t0_rows = (int)k;
+        I.t0_cols = (int)n;
+    }
+    I.A = A;
+    I.lda = lda;
+    I.B = B;
+    I.ldb = ldb;
+    I.C = C;
+    I.ldc = ldc;
+    b->reqs.push_back({I, (long long)m * n * k});
+    b->dirty = true;
+    return BTAS_OK;
+}
+
+btas_status btas_batch_launch(btas_batch_t *b, void *stream) {
+    if (!b) return bfail(BTAS_ERR_ARG, "btas_batch_launch: NULL batch");
+    if (b->reqs.empty()) return BTAS_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (b->dirty || dev != b->device) {
+        const btas_status s = build_plan(b);
+        if (s != BTAS_OK) return s;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (b->exec) {
+        e = cudaGraphLaunch(b->exec, st);
+        note_launch();
+    } else {
+        e = cudaMemsetAsync(b->d_counters, 0, b->counter_bytes, st);
+        if (e == cudaSuccess) {
+            batch_kernel<<<b->grid, BCfg::kThreads, b->smem, st>>>(b->params);
+            note_launch();
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) return bfail(BTAS_ERR_CUDA, cudaGetErrorString(e));
+    return BTAS_OK;
+}
+
+btas_status btas_batch_wait(btas_batch_t *b, void *stream) {
+    if (!b) return bfail(BTAS_ERR_ARG, "btas_batch_wait: NULL batch");
+    if (!b->d_counters) return BTAS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, b->params.status, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bfail(BTAS_ERR_CUDA, cudaGetErrorString(e));
+    if (status != 0) return bfail(static_cast<btas_status>(status), "btas_batch: a bounded device wait expired");
+    return BTAS_OK;
+}
+
+int64_t btas_batch_workspace_bytes(btas_batch_t *b) { return b ? b->workspace_bytes : 0; }
+
+int btas_batch_tasks(btas_batch_t *b) { return b ? b->total : 0; }
+
+}  // extern "C"

@@ -320,7 +320,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     const size_t nn = (size_t)n * (size_t)n;
 
     Workspace ws(st);
-    const size_t flag_bytes = align256((size_t)(S + 4) * 4);
+    const size_t flag_bytes = align256((size_t)(2 * S + 8) * 4);
     // layout: [flags | X | Y | T]; T holds a transpose (or the duplicated
     // 16-bit operand) with a leading dimension rounded up to 4 elements
     const long long ldt = (n + 3) & ~3LL;
@@ -352,27 +352,16 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         bound = (long long)(n - 1) * host[0];
         if (bound_out) *bound_out = bound;
     }
-    int path = 0;
-    if (flags & BTAS_APSP_FORCE_U16) {
-        if (bound >= BTAS_INF_U16) return fail(BTAS_ERR_BOUND, "btas_apsp: bound %lld >= 0x7FFF", bound);
-        path = 2;
-    } else if (flags & BTAS_APSP_FORCE_CARRIER) {
-        if (bound >= (1LL << 23)) return fail(BTAS_ERR_BOUND, "btas_apsp: bound %lld >= 2^23", bound);
-        path = 1;
-    } else if (!(flags & BTAS_APSP_FORCE_I32)) {
-        if (bound < BTAS_INF_U16 && env_int("BTAS_APSP_NO_U16", 0) == 0) path = 2;
-        else if (bound < (1LL << 23) && env_int("BTAS_APSP_NO_CARRIER", 0) == 0) path = 1;
-    }
-    if (path_out) *path_out = path;
-
     if (S == 0) {
         if (D != W) BTAS_CUDA(cudaMemcpyAsync(D, W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
         if (squarings_done) *squarings_done = 0;
+        if (path_out) *path_out = 0;
         return BTAS_OK;
     }
 
-    btas_status r = BTAS_OK;
-    if (path == 0) {
+    if ((flags & BTAS_APSP_FORCE_I32) && !need_scan) {
+        // int32 only, no host synchronisation: the early exit is decided on
+        // the device (a converged squaring copies its input through)
         const void *cur0 = W;
         if ((const void *)W == (const void *)D && ((S - 1) & 1) == 0) {
             // the first squaring would write D == W while reading it
@@ -380,46 +369,114 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
             cur0 = Y;
         }
         void *bufs[2] = {D, X};
-        r = squaring_loop(BTAS_I32, n, S, cur0, bufs, T, dflags, early, st);
-    } else if (path == 1) {
-        // the first squaring writes bufs[(S-1)&1]; the input goes to the other one
-        void *bufs[2] = {X, Y};
-        void *in = bufs[S & 1];
-        BTAS_CUDA(launch_convert4(W, n, (int)n, (int)n, in, n, 1, st), "to carrier");
-        r = squaring_loop(BTAS_F32, n, S, in, bufs, T, dflags, early, st);
-        if (r == BTAS_OK)
-            BTAS_CUDA(launch_convert4(bufs[0], n, (int)n, (int)n, D, n, 2, st), "from carrier");
-    } else {
-        uint16_t *U0 = reinterpret_cast<uint16_t *>(X);
-        uint16_t *U1 = reinterpret_cast<uint16_t *>(Y);
-        uint32_t *Ad = reinterpret_cast<uint32_t *>(T);
-        BTAS_CUDA(launch_narrow_u16(W, (long long)nn, U0, st), "narrow");
-        uint16_t *cur = U0;
-        for (int s = 0; s < S; ++s) {
-            uint16_t *out = cur == U0 ? U1 : U0;
+        btas_status r = squaring_loop(BTAS_I32, n, S, cur0, bufs, T, dflags, early, st);
+        if (r != BTAS_OK) return r;
+        if (path_out) *path_out = 1;
+        if (squarings_done) {
+            int host[64];
+            BTAS_CUDA(cudaMemcpyAsync(host, dflags, (size_t)S * 4, cudaMemcpyDeviceToHost, st), "flags readback");
+            BTAS_CUDA(cudaStreamSynchronize(st), "flags sync");
+            int done = 0;
+            for (int q = 0; q < S; ++q) done += host[q] != 0;
+            *squarings_done = done;
+        }
+        return BTAS_OK;
+    }
+
+    // Representation per squaring: 0 = int32, 1 = exact fp32 carrier, 2 =
+    // packed u16x2.  With m the largest finite entry of D_s, every finite
+    // entry of D_{s+1} = D_s (x) D_s is at most 2m, and so is every pairwise
+    // sum.  Hence 2m < 0x7FFF makes the 16-bit squaring exact, and 2m < 2^24
+    // makes the fp32 one exact (all values and sums are exact integers).  The
+    // squaring's epilogue reports the next m.  FORCE flags pin one
+    // representation and require the static bound (n-1) * max w instead.
+    int force_rep = -1;
+    if (flags & BTAS_APSP_FORCE_U16) {
+        if (bound >= BTAS_INF_U16) return fail(BTAS_ERR_BOUND, "btas_apsp: bound %lld >= 0x7FFF", bound);
+        force_rep = 2;
+    } else if (flags & BTAS_APSP_FORCE_CARRIER) {
+        if (bound >= (1LL << 23)) return fail(BTAS_ERR_BOUND, "btas_apsp: bound %lld >= 2^23", bound);
+        force_rep = 1;
+    } else if (flags & BTAS_APSP_FORCE_I32) {
+        force_rep = 0;
+    }
+    const bool no_u16 = env_int("BTAS_APSP_NO_U16", 0) != 0;
+    const bool no_carrier = env_int("BTAS_APSP_NO_CARRIER", 0) != 0;
+    int *chg = dflags;
+    int *mxs = dflags + S + 4;
+    const int ns16 = env_int("BTAS_U16_NS", 5);
+    auto other = [&](const void *p) -> void * { return p == (const void *)X ? (void *)Y : (void *)X; };
+    // convert an n x n matrix between representations (T is free scratch here)
+    auto convert = [&](int from, int to, const void *src, void *dst) -> cudaError_t {
+        if (from == to) return cudaSuccess;
+        const void *s32 = src;
+        cudaError_t e = cudaSuccess;
+        if (from == 1) e = launch_convert4(src, n, (int)n, (int)n, (to == 0 ? dst : T), n, 2, st);
+        if (from == 2) e = launch_widen_u16_i32(static_cast<const uint16_t *>(src), (long long)nn,
+                                                static_cast<int *>(to == 0 ? dst : (void *)T), st);
+        if (e != cudaSuccess || to == 0) return e;
+        if (from != 0) s32 = T;
+        if (to == 1) return launch_convert4(s32, n, (int)n, (int)n, dst, n, 1, st);
+        return launch_narrow_u16(static_cast<const int *>(s32), (long long)nn, static_cast<uint16_t *>(dst), st);
+    };
+
+    int rep = 0, used = 0, done = 0;
+    long long m = bound >= 0 ? (n > 1 ? bound / (n - 1) : 0) : 0;
+    const void *cur = W;
+    for (int s = 0; s < S; ++s) {
+        int want = force_rep;
+        if (want < 0) want = (2 * m < BTAS_INF_U16 && !no_u16) ? 2 : (2 * m < (1LL << 24) && !no_carrier) ? 1 : 0;
+        if (want != rep) {
+            void *dst = other(cur);
+            BTAS_CUDA(convert(rep, want, cur, dst), "representation change");
+            cur = dst;
+            rep = want;
+        }
+        void *out = other(cur);
+        if (rep == 2) {
             U16Args a{};
             a.m = a.n = a.k = (int)n;
+            a.A = static_cast<const uint16_t *>(cur); a.lda = n;
+            a.B = static_cast<const uint16_t *>(cur); a.ldb = n;
+            a.C = static_cast<uint16_t *>(out); a.ldc = n;
+            a.prev = static_cast<const uint16_t *>(cur); a.ldp = n;
+            a.changed = &chg[s];
+            a.one = 1;
+            a.maxfin = &mxs[s];
+            BTAS_CUDA(launch_tgemm_u16_ws(a, reinterpret_cast<uint32_t *>(T), ns16, st), "u16 squaring");
+        } else {
+            const long long ldt = (n + 3) & ~3LL;
+            BTAS_CUDA(launch_transpose4(cur, n, (int)n, (int)n, T, ldt, 0, nullptr, st), "transpose");
+            GemmArgs a{};
+            a.m = a.n = a.k = (int)n;
             a.A = cur; a.lda = n;
-            a.B = cur; a.ldb = n;
+            a.Bt = T; a.ldb = ldt;
             a.C = out; a.ldc = n;
             a.prev = cur; a.ldp = n;
-            a.changed = &dflags[s];
-            a.skip = (early && s > 0) ? &dflags[s - 1] : nullptr;
-            a.one = 1;
-            BTAS_CUDA(launch_tgemm_u16_ws(a, Ad, env_int("BTAS_U16_NS", 5), st), "u16 squaring");
-            cur = out;
+            a.changed = &chg[s];
+            a.maxfin = &mxs[s];
+            a.vec_a = aligned16(cur, n);
+            a.vec_b = aligned16(T, ldt);
+            btas_status r = run_nt(rep == 1 ? BTAS_F32 : BTAS_I32, kMin, a, st);
+            if (r != BTAS_OK) return r;
         }
-        BTAS_CUDA(launch_widen_u16_i32(cur, (long long)nn, D, st), "widen");
+        used |= 1 << rep;
+        int host[2] = {0, 0};
+        BTAS_CUDA(cudaMemcpyAsync(&host[0], &chg[s], 4, cudaMemcpyDeviceToHost, st), "flag readback");
+        BTAS_CUDA(cudaMemcpyAsync(&host[1], &mxs[s], 4, cudaMemcpyDeviceToHost, st), "max readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "squaring sync");
+        cur = out;
+        m = host[1] < 0 ? 0 : host[1];
+        if (host[0]) ++done;
+        if (early && !host[0]) break;
     }
-    if (r != BTAS_OK) return r;
-    if (squarings_done) {
-        int host[64];
-        BTAS_CUDA(cudaMemcpyAsync(host, dflags, (size_t)S * 4, cudaMemcpyDeviceToHost, st), "flags readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "flags sync");
-        int done = 0;
-        for (int s = 0; s < S; ++s) done += host[s] != 0;
-        *squarings_done = done;
+    if (rep == 0) {
+        if (cur != (const void *)D) BTAS_CUDA(cudaMemcpyAsync(D, cur, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
+    } else {
+        BTAS_CUDA(convert(rep, 0, cur, D), "final conversion");
     }
+    if (squarings_done) *squarings_done = done;
+    if (path_out) *path_out = used;
     return BTAS_OK;
 }
 

@@ -58,6 +58,7 @@ struct U16Args {
     int *changed;
     const int *skip;
     int one;
+    int *maxfin;  // optional: atomicMax of the largest output below INF16
 };
 // Duplicates A into `adup` (m x round4(k) 32-bit words, caller workspace) and
 // runs the packed product; ns = number of the 8 column pairs per thread that

@@ -27,6 +27,7 @@
 //              (FMA pipe) + one 3-input min; DPX on the others, balancing the
 //              ALU and FMA pipes
 //   kF32X2     add.f32x2 (two RN adds, FMA pipe) + one 3-input min.f32
+//   kF32Add2   two scalar RN adds + one 3-input min.f32 per k pair
 //   kF32Scalar FADD + FMNMX per term (reference variant)
 // All variants compute the same exact result: each term is one exact
 // integer add or one round-to-nearest fp32 add, and min/max is independent
@@ -39,15 +40,20 @@
 
 namespace btas {
 
-template <int BM_, int BN_, int BK_, int STAGES_>
+// MINB: CTAs per SM the register budget is sized for (1: <= 255 registers,
+// 2: <= 128).  FK: k depth of one register fragment (4 = 128-bit smem loads,
+// 2 = 64-bit loads and half the fragment registers).
+// UNR: unroll factor of the k-slice loop inside one smem stage.
+template <int BM_, int BN_, int BK_, int STAGES_, int MINB_ = 1, int FK_ = 4, int UNR_ = 2>
 struct TileCfg {
-    static constexpr int BM = BM_, BN = BN_, BK = BK_, STAGES = STAGES_;
+    static constexpr int BM = BM_, BN = BN_, BK = BK_, STAGES = STAGES_, MINB = MINB_, FK = FK_, UNR = UNR_;
     static constexpr int WARPS_M = BM / 32, WARPS_N = BN / 64;
     static constexpr int kThreads = WARPS_M * WARPS_N * 32;
     static constexpr int kLd = BK + 4;
     static constexpr int kStageElems = (BM + BN) * kLd;
     static constexpr int kSmemBytes = STAGES * kStageElems * 4;
     static_assert(BM % 32 == 0 && BN % 64 == 0 && BK % 8 == 0, "tile shape");
+    static_assert(FK == 2 || FK == 4, "fragment depth");
 };
 
 template <typename T, int ROWS, int BK, int LD, int NT>
@@ -68,44 +74,71 @@ __device__ __forceinline__ void stage_rows(T *sm, const T *g, long long ldg, int
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 T v = fill;
-                if (gr < rows_total && gk + e < K) v = g[(long long)gr * ldg + gk + e];
+                if (gr < rows_total && gk + e < K) v = __ldcg(g + (long long)gr * ldg + gk + e);
                 dst[e] = v;
             }
         }
     }
 }
 
-// One 4-deep k slice of the 8x8 register tile.
-template <int VAR, int SR, int NS>
+// Register fragments: for each of the 8 rows (A) or 8 columns (B) of a
+// thread, FK consecutive k values.  Integer and scalar-fp32 variants view
+// them as 32-bit words; the f32x2 variant as FK/2 64-bit pairs.
+template <int FK>
+struct Frag32 { uint32_t v[FK]; };
+template <>
+struct __align__(16) Frag32<4> { uint32_t v[4]; };
+template <>
+struct __align__(8) Frag32<2> { uint32_t v[2]; };
+
+template <int FK>
+__device__ __forceinline__ Frag32<FK> lds_frag(const void *p) {
+    Frag32<FK> f;
+    if constexpr (FK == 4) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(p);
+        f.v[0] = t.x; f.v[1] = t.y; f.v[2] = t.z; f.v[3] = t.w;
+    } else {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        f.v[0] = t.x; f.v[1] = t.y;
+    }
+    return f;
+}
+
+__device__ __forceinline__ uint64_t pack64(uint32_t lo, uint32_t hi) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+    return d;
+}
+
+// One FK-deep k slice of the 8x8 register tile.
+template <int VAR, int SR, int NS, int FK>
 struct Step;
 
-template <int SR, int NS>
-struct Step<kI32Dpx, SR, NS> {
-    static __device__ __forceinline__ void run(int (&acc)[8][8], const int4 (&a)[8], const int4 (&b)[8], int) {
+template <int SR, int NS, int FK>
+struct Step<kI32Dpx, SR, NS, FK> {
+    static __device__ __forceinline__ void run(int (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
+                                               int) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < FK; ++q)
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int av = q == 0 ? a[i].x : q == 1 ? a[i].y : q == 2 ? a[i].z : a[i].w;
-                    const int bv = q == 0 ? b[j].x : q == 1 ? b[j].y : q == 2 ? b[j].z : b[j].w;
-                    acc[i][j] = iaddsel<SR>(av, bv, acc[i][j]);
-                }
+                for (int j = 0; j < 8; ++j) acc[i][j] = iaddsel<SR>((int)a[i].v[q], (int)b[j].v[q], acc[i][j]);
     }
 };
 
-template <int SR, int NS>
-struct Step<kI32Mix, SR, NS> {
-    static __device__ __forceinline__ void run(int (&acc)[8][8], const int4 (&a)[8], const int4 (&b)[8], int one) {
+template <int SR, int NS, int FK>
+struct Step<kI32Mix, SR, NS, FK> {
+    static __device__ __forceinline__ void run(int (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
+                                               int one) {
 #pragma unroll
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < FK / 2; ++p)
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int a0 = p == 0 ? a[i].x : a[i].z, a1 = p == 0 ? a[i].y : a[i].w;
-                    const int b0 = p == 0 ? b[j].x : b[j].z, b1 = p == 0 ? b[j].y : b[j].w;
+                    const int a0 = (int)a[i].v[2 * p], a1 = (int)a[i].v[2 * p + 1];
+                    const int b0 = (int)b[j].v[2 * p], b1 = (int)b[j].v[2 * p + 1];
                     if (j < NS) {
                         const int s0 = imad_add(a0, one, b0);
                         const int s1 = imad_add(a1, one, b1);
@@ -117,17 +150,18 @@ struct Step<kI32Mix, SR, NS> {
     }
 };
 
-template <int SR, int NS>
-struct Step<kF32X2, SR, NS> {
-    static __device__ __forceinline__ void run(float (&acc)[8][8], const ulonglong2 (&a)[8],
-                                               const ulonglong2 (&b)[8], int) {
+template <int SR, int NS, int FK>
+struct Step<kF32X2, SR, NS, FK> {
+    static __device__ __forceinline__ void run(float (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
+                                               int) {
 #pragma unroll
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < FK / 2; ++p)
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const uint64_t s = fadd2(p == 0 ? a[i].x : a[i].y, p == 0 ? b[j].x : b[j].y);
+                    const uint64_t s = fadd2(pack64(a[i].v[2 * p], a[i].v[2 * p + 1]),
+                                             pack64(b[j].v[2 * p], b[j].v[2 * p + 1]));
                     float lo, hi;
                     unpack2(s, lo, hi);
                     acc[i][j] = fsel3<SR>(acc[i][j], lo, hi);
@@ -135,32 +169,52 @@ struct Step<kF32X2, SR, NS> {
     }
 };
 
-template <int SR, int NS>
-struct Step<kF32Scalar, SR, NS> {
-    static __device__ __forceinline__ void run(float (&acc)[8][8], const float4 (&a)[8], const float4 (&b)[8], int) {
+// Two scalar RN adds + one 3-input min/max per k pair.
+template <int SR, int NS, int FK>
+struct Step<kF32Add2, SR, NS, FK> {
+    static __device__ __forceinline__ void run(float (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
+                                               int) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int p = 0; p < FK / 2; ++p)
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float av = q == 0 ? a[i].x : q == 1 ? a[i].y : q == 2 ? a[i].z : a[i].w;
-                    const float bv = q == 0 ? b[j].x : q == 1 ? b[j].y : q == 2 ? b[j].z : b[j].w;
-                    acc[i][j] = fsel2<SR>(acc[i][j], __fadd_rn(av, bv));
+                    const float s0 = __fadd_rn(__uint_as_float(a[i].v[2 * p]), __uint_as_float(b[j].v[2 * p]));
+                    const float s1 = __fadd_rn(__uint_as_float(a[i].v[2 * p + 1]), __uint_as_float(b[j].v[2 * p + 1]));
+                    acc[i][j] = fsel3<SR>(acc[i][j], s0, s1);
                 }
     }
 };
 
+template <int SR, int NS, int FK>
+struct Step<kF32Scalar, SR, NS, FK> {
+    static __device__ __forceinline__ void run(float (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
+                                               int) {
+#pragma unroll
+        for (int q = 0; q < FK; ++q)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[i][j] = fsel2<SR>(acc[i][j], __fadd_rn(__uint_as_float(a[i].v[q]), __uint_as_float(b[j].v[q])));
+    }
+};
+
 template <int VAR>
-struct VarTypes;
+struct VarTypes { using T = float; };
 template <>
-struct VarTypes<kI32Dpx> { using T = int; using Frag = int4; };
+struct VarTypes<kI32Dpx> { using T = int; };
 template <>
-struct VarTypes<kI32Mix> { using T = int; using Frag = int4; };
-template <>
-struct VarTypes<kF32X2> { using T = float; using Frag = ulonglong2; };
-template <>
-struct VarTypes<kF32Scalar> { using T = float; using Frag = float4; };
+struct VarTypes<kI32Mix> { using T = int; };
+
+// Largest finite value of a min-plus output as an int (-1 for INF).  FP32
+// outputs here are carriers of exact integers (APSP), so the cast is exact.
+template <typename T>
+__device__ __forceinline__ int finite_int(T v) {
+    if constexpr (std::is_same<T, int>::value) return v < kInfI32 ? v : -1;
+    else return v < __int_as_float(0x7f800000) ? static_cast<int>(v) : -1;
+}
 
 template <typename T, int SR>
 __device__ __forceinline__ T finish(T v) {
@@ -168,43 +222,37 @@ __device__ __forceinline__ T finish(T v) {
     else return v;
 }
 
+// Converged squaring (D_{s+1} = D_s): copy one BM x BN tile of P into C.
+template <class Cfg, typename T>
+__device__ __forceinline__ void copy_tile(const GemmArgs &args, int bm, int bn, int tid) {
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, NT = Cfg::kThreads;
+    const T *P = static_cast<const T *>(args.prev);
+    T *C = static_cast<T *>(args.C);
+    for (int idx = tid; idx < BM * BN; idx += NT) {
+        const int r = bm + idx / BN, c = bn + idx % BN;
+        if (r < args.m && c < args.n) C[(long long)r * args.ldc + c] = __ldcg(P + (long long)r * args.ldp + c);
+    }
+}
+
+// One BM x BN output tile at (bm, bn).  Returns this thread's "some output
+// differs from prev" bit.  With Ct != nullptr the tile is also stored
+// transposed (Ct[c][r], leading dimension ldct) through shared memory, so a
+// following squaring finds its k-contiguous B operand ready.  Loads of data
+// that other CTAs of the same launch may have written go through L2
+// (cp.async.cg, __ldcg), never through the non-coherent L1.
 template <class Cfg, int VAR, int SR, int NS>
-__global__ void __launch_bounds__(Cfg::kThreads, 1) tgemm_nt_kernel(const GemmArgs args) {
+__device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, unsigned char *smem_raw, int tid,
+                                        void *Ct = nullptr, long long ldct = 0) {
     using T = typename VarTypes<VAR>::T;
-    using Frag = typename VarTypes<VAR>::Frag;
+    constexpr int FK = Cfg::FK;
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, LD = Cfg::kLd, ST = Cfg::STAGES;
     constexpr int NT = Cfg::kThreads;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
-
     const int M = args.m, N = args.n, K = args.k;
-    const int tid = threadIdx.x;
-    // grouped rasterisation: consecutive CTAs share A row panels and walk
-    // group_m tile rows before moving to the next column of tiles
-    const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-    const int gm = args.group_m;
-    const int pid = blockIdx.x;
-    const int per_group = gm * tiles_n;
-    const int g = pid / per_group;
-    const int first_m = g * gm;
-    const int gsz = min(tiles_m - first_m, gm);
-    const int tm = first_m + (pid % per_group) % gsz;
-    const int tn = (pid % per_group) / gsz;
-    const int bm = tm * BM, bn = tn * BN;
-
     const T *A = static_cast<const T *>(args.A);
     const T *Bt = static_cast<const T *>(args.Bt);
     T *C = static_cast<T *>(args.C);
     const T *P = static_cast<const T *>(args.prev);
-
-    if (args.skip != nullptr && *args.skip == 0) {
-        // converged squaring: D_{s+1} = D_s, copy the tile through
-        for (int idx = tid; idx < BM * BN; idx += NT) {
-            const int r = bm + idx / BN, c = bn + idx % BN;
-            if (r < M && c < N) C[(long long)r * args.ldc + c] = P[(long long)r * args.ldp + c];
-        }
-        return;
-    }
 
     const int warp = tid >> 5, lane = tid & 31;
     const int wm = warp / Cfg::WARPS_N, wn = warp % Cfg::WARPS_N;
@@ -221,7 +269,7 @@ __global__ void __launch_bounds__(Cfg::kThreads, 1) tgemm_nt_kernel(const GemmAr
             T v = ident;
             if (args.accumulate) {
                 const int r = bm + row_base + 4 * i, c = bn + col_base + 8 * j;
-                if (r < M && c < N) v = C[(long long)r * args.ldc + c];
+                if (r < M && c < N) v = __ldcg(C + (long long)r * args.ldc + c);
             }
             acc[i][j] = v;
         }
@@ -251,34 +299,84 @@ __global__ void __launch_bounds__(Cfg::kThreads, 1) tgemm_nt_kernel(const GemmAr
         }
         const T *sa = smem + (kt % ST) * Cfg::kStageElems;
         const T *sb = sa + BM * LD;
-#pragma unroll 2
-        for (int kk = 0; kk < BK; kk += 4) {
-            Frag a[8], b[8];
+#pragma unroll Cfg::UNR
+        for (int kk = 0; kk < BK; kk += FK) {
+            Frag32<FK> a[8], b[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                a[i] = *reinterpret_cast<const Frag *>(sa + (row_base + 4 * i) * LD + kk);
+            for (int i = 0; i < 8; ++i) a[i] = lds_frag<FK>(sa + (row_base + 4 * i) * LD + kk);
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                b[j] = *reinterpret_cast<const Frag *>(sb + (col_base + 8 * j) * LD + kk);
-            Step<VAR, SR, NS>::run(acc, a, b, args.one);
+            for (int j = 0; j < 8; ++j) b[j] = lds_frag<FK>(sb + (col_base + 8 * j) * LD + kk);
+            Step<VAR, SR, NS, FK>::run(acc, a, b, args.one);
         }
     }
     cp_async_wait<0>();
 
     bool ch = false;
+    int mx = -1;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int r = bm + row_base + 4 * i, c = bn + col_base + 8 * j;
+            acc[i][j] = finish<T, SR>(acc[i][j]);
             if (r < M && c < N) {
-                const T v = finish<T, SR>(acc[i][j]);
-                if (P != nullptr && v != P[(long long)r * args.ldp + c]) ch = true;
+                const T v = acc[i][j];
+                if (P != nullptr && v != __ldcg(P + (long long)r * args.ldp + c)) ch = true;
+                if (SR == kMin && args.maxfin != nullptr) mx = max(mx, finite_int(v));
                 C[(long long)r * args.ldc + c] = v;
             }
         }
+    if (SR == kMin && args.maxfin != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0 && mx >= 0) atomicMax(args.maxfin, mx);
+    }
+    if (Ct != nullptr) {
+        // stage the tile transposed: tile[c][r], row pitch BM + 1 words
+        static_assert(BN * (BM + 1) <= Cfg::STAGES * Cfg::kStageElems, "transpose staging fits");
+        __syncthreads();  // every warp is done reading the last k stage
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) smem[(col_base + 8 * j) * (BM + 1) + row_base + 4 * i] = acc[i][j];
+        __syncthreads();
+        T *CT = static_cast<T *>(Ct);
+        for (int idx = tid; idx < BM * BN; idx += NT) {
+            const int c = idx / BM, r = idx % BM;
+            if (bn + c < N && bm + r < M) CT[(long long)(bn + c) * ldct + bm + r] = smem[c * (BM + 1) + r];
+        }
+        __syncthreads();  // smem is reused by the caller's next tile
+    }
+    return ch;
+}
+
+// Grouped rasterisation: consecutive CTAs share A row panels and walk
+// group_m tile rows before moving to the next column of tiles.
+__device__ __forceinline__ void raster(int pid, int tiles_m, int tiles_n, int gm, int &tm, int &tn) {
+    const int per_group = gm * tiles_n;
+    const int g = pid / per_group;
+    const int first_m = g * gm;
+    const int gsz = min(tiles_m - first_m, gm);
+    tm = first_m + (pid % per_group) % gsz;
+    tn = (pid % per_group) / gsz;
+}
+
+template <class Cfg, int VAR, int SR, int NS>
+__global__ void __launch_bounds__(Cfg::kThreads, Cfg::MINB) tgemm_nt_kernel(const GemmArgs args) {
+    using T = typename VarTypes<VAR>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const int tiles_m = (args.m + Cfg::BM - 1) / Cfg::BM, tiles_n = (args.n + Cfg::BN - 1) / Cfg::BN;
+    int tm, tn;
+    raster(blockIdx.x, tiles_m, tiles_n, args.group_m, tm, tn);
+    const int bm = tm * Cfg::BM, bn = tn * Cfg::BN;
+    if (args.skip != nullptr && __ldcg(args.skip) == 0) {
+        copy_tile<Cfg, T>(args, bm, bn, tid);
+        return;
+    }
+    const bool ch = nt_tile<Cfg, VAR, SR, NS>(args, bm, bn, smem_raw, tid);
     if (args.changed != nullptr) {
-        if (__any_sync(0xffffffffu, ch) && lane == 0) atomicOr(args.changed, 1);
+        if (__any_sync(0xffffffffu, ch) && (tid & 31) == 0) atomicOr(args.changed, 1);
     }
 }
 

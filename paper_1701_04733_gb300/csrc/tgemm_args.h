@@ -3,7 +3,7 @@
 
 namespace btas {
 
-enum Variant : int { kI32Dpx = 0, kI32Mix = 1, kF32X2 = 2, kF32Scalar = 3 };
+enum Variant : int { kI32Dpx = 0, kI32Mix = 1, kF32X2 = 2, kF32Scalar = 3, kF32Add2 = 4 };
 
 struct GemmArgs {
     int m, n, k;
@@ -21,6 +21,7 @@ struct GemmArgs {
     int one;            // the constant 1, opaque to the compiler
     int vec_a, vec_b;   // operand rows are 16-byte aligned (cp.async usable)
     int group_m;        // CTA rasterisation: tile rows per group
+    int *maxfin;        // optional: atomicMax of the largest finite output (as int)
 };
 
 }  // namespace btas

@@ -19,6 +19,8 @@ using Cfg0 = TileCfg<128, 128, 32, 3>;  // 256 threads, 108 KiB smem
 using Cfg1 = TileCfg<128, 128, 32, 4>;  // 256 threads, 144 KiB smem
 using Cfg2 = TileCfg<64, 64, 32, 4>;    //  64 threads,  72 KiB smem (small problems)
 using Cfg3 = TileCfg<128, 64, 32, 4>;   // 128 threads, 108 KiB smem
+using Cfg4 = TileCfg<128, 128, 32, 3, 2, 2, 1>;  // 2 CTAs/SM, 64-bit fragments
+using Cfg5 = TileCfg<128, 128, 32, 3, 2, 4, 1>;  // 2 CTAs/SM, 128-bit fragments
 
 template <class Cfg, int VAR, int SR, int NS>
 cudaError_t launch_nt(const GemmArgs &a, cudaStream_t st) {

@@ -50,6 +50,7 @@ struct U16KArgs {
     const int *skip;
     int one;
     int vec_a, vec_b;
+    int *maxfin;
 };
 
 __global__ void dup_u16_kernel(const uint16_t *__restrict__ A, long long lda, int m, int k, uint32_t *__restrict__ Ad,
@@ -214,6 +215,7 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
     cp_async_wait<0>();
 
     bool ch = false;
+    int mx = -1;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int r = bm + row_base + 4 * i;
@@ -226,13 +228,20 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
             const uint16_t lo = (uint16_t)(v & 0xFFFF), hi = (uint16_t)(v >> 16);
             if (c < N) {
                 if (args.prev && lo != args.prev[(long long)r * args.ldp + c]) ch = true;
+                if (lo < BTAS_INF_U16) mx = max(mx, (int)lo);
                 args.C[(long long)r * args.ldc + c] = lo;
             }
             if (c + 1 < N) {
                 if (args.prev && hi != args.prev[(long long)r * args.ldp + c + 1]) ch = true;
+                if (hi < BTAS_INF_U16) mx = max(mx, (int)hi);
                 args.C[(long long)r * args.ldc + c + 1] = hi;
             }
         }
+    }
+    if (args.maxfin != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx >= 0) atomicMax(args.maxfin, mx);
     }
     if (args.changed != nullptr) {
         if (__any_sync(0xffffffffu, ch) && lane == 0) atomicOr(args.changed, 1);
@@ -287,6 +296,7 @@ cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaSt
     ka.changed = a.changed;
     ka.skip = a.skip;
     ka.one = 1;
+    ka.maxfin = a.maxfin;
     ka.vec_a = (reinterpret_cast<uintptr_t>(adup) & 15) == 0;
     ka.vec_b = (reinterpret_cast<uintptr_t>(a.B) & 15) == 0 && (a.ldb & 7) == 0;
     switch (ns) {

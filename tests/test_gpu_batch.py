@@ -1,0 +1,124 @@
+"""Batched persistent launch (many APSP solves and tropical products of
+uneven sizes in one kernel): every instance's result is bit-identical to the
+single call and to the oracle; graph replay and the plain launch agree; a
+withheld dependency ends in BTAS_ERR_TIMEOUT (bounded device wait) and leaves
+the context usable."""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+from gpu_util import bits, dev, f32_matrix, host, int_matrix
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def btas():
+    import torch
+    import paper_1701_04733_gb300 as b
+    assert torch.cuda.is_available()
+    b.lib()
+    return b
+
+
+def _mixed(btas, seed=0):
+    import torch
+    sizes = [1, 2, 3, 5, 31, 64, 100, 129, 200, 257, 300, 411]
+    apsp = []
+    for i, n in enumerate(sizes):
+        W = gen.random_graph(seed + 500 + i, i, n, 0.1 if n > 8 else 0.5, 1, 100)
+        apsp.append((W, dev(W), torch.empty((n, n), dtype=torch.int32, device="cuda")))
+    gemm = []
+    shapes = [(1, 1, 1), (7, 5, 3), (130, 129, 77), (256, 300, 200), (33, 400, 129)]
+    for i, (m, n, k) in enumerate(shapes):
+        for dt, sr, tb in (("f32", 1, False), ("i32", 0, True), ("f32", 0, True), ("i32", 1, False)):
+            mk = int_matrix if dt == "i32" else f32_matrix
+            A = mk(seed + 900 + i, (m, k), sr)
+            B = mk(seed + 950 + i, (k, n), sr)
+            Bd = dev(np.ascontiguousarray(B.T)) if tb else dev(B)
+            C = torch.empty((m, n), dtype=torch.int32 if dt == "i32" else torch.float32, device="cuda")
+            gemm.append((A, B, dev(A), Bd, C, sr, tb))
+    return apsp, gemm
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_mixed_batch_matches_single_calls_and_oracle(btas, oracle_mod, graph):
+    import torch
+    apsp, gemm = _mixed(btas)
+    b = btas.Batch(graph=graph)
+    for W, Wd, D in apsp:
+        b.add_apsp(Wd, D)
+    for A, B, Ad, Bd, C, sr, tb in gemm:
+        b.add_gemm(Ad, Bd, C, sr, trans_b=tb)
+    for rep in range(2):  # second launch replays the plan (graph)
+        for _, _, D in apsp:
+            D.fill_(-5)
+        for g in gemm:
+            g[4].fill_(-5)
+        b.launch()
+        b.wait()
+        for W, Wd, D in apsp:
+            ref = oracle_mod.floyd_warshall(W)
+            np.testing.assert_array_equal(host(D), ref, err_msg=f"apsp n={W.shape[0]} rep={rep}")
+            np.testing.assert_array_equal(host(D), host(btas.apsp(Wd)))
+        for A, B, Ad, Bd, C, sr, tb in gemm:
+            ref = oracle_mod.tgemm(sr, A, B)
+            np.testing.assert_array_equal(bits(host(C)), bits(ref), err_msg=f"gemm {A.shape}x{B.shape} sr={sr}")
+    assert b.tasks > 0
+    b.close()
+
+
+def test_batch_of_config_sizes(btas, oracle_mod):
+    """64 graphs with n uniform in [32, 1024], p = 0.1, w in [1, 100] (a slice
+    of the 512-graph batched workload); 8 sampled instances vs Dijkstra rows,
+    all of them vs the single-call path."""
+    import torch
+    sizes = gen.graph_sizes(gen.BASE_SEED, 40, 64, 32, 1024)
+    b = btas.Batch()
+    items = []
+    for i, n in enumerate(sizes):
+        W = gen.random_graph(gen.BASE_SEED, 1000 + i, int(n), 0.1, 1, 100)
+        Wd = dev(W)
+        D = torch.empty_like(Wd)
+        b.add_apsp(Wd, D)
+        items.append((W, Wd, D))
+    b.launch()
+    b.wait()
+    for i, (W, Wd, D) in enumerate(items):
+        np.testing.assert_array_equal(host(D), host(btas.apsp(Wd, flags=0x2 | 1)))
+        if i % 8 == 0:
+            srcs = gen.sample_indices(gen.BASE_SEED, 41 + i, 16, W.shape[0])
+            np.testing.assert_array_equal(host(D)[srcs], oracle_mod.dijkstra_rows(W, srcs))
+    b.close()
+
+
+def test_withheld_dependency_times_out(btas):
+    """The host withholds one completion of instance 0: its tasks' bounded
+    waits run out, the launch reports BTAS_ERR_TIMEOUT, and a later batch on
+    the same context still computes correct results."""
+    import torch
+    import paper_1701_04733_gb300 as b_mod
+    W = gen.random_graph(3, 3, 300, 0.1, 1, 100)
+    Wd = dev(W)
+    D = torch.empty_like(Wd)
+    os.environ["BTAS_BATCH_WITHHOLD"] = "0"
+    os.environ["BTAS_BATCH_TIMEOUT_CYCLES"] = "2000000"
+    try:
+        bb = btas.Batch()
+        bb.add_apsp(Wd, D)
+        bb.launch()
+        with pytest.raises(b_mod.BtasError) as ei:
+            bb.wait()
+        assert ei.value.status == 5
+        bb.close()
+    finally:
+        os.environ.pop("BTAS_BATCH_WITHHOLD", None)
+        os.environ.pop("BTAS_BATCH_TIMEOUT_CYCLES", None)
+    ok = btas.Batch()
+    ok.add_apsp(Wd, D)
+    ok.launch()
+    ok.wait()
+    np.testing.assert_array_equal(host(D), host(btas.apsp(Wd)))
+    ok.close()
