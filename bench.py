@@ -53,6 +53,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-graphs", type=int, default=512)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=300)
+    p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
+    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve"],
+                   help="profiling aids: run one part alone and print its JSON (not a bench line)")
     return p.parse_args()
 
 
@@ -318,6 +323,17 @@ def run_btas(args):
     roofline["share_of_step"] = round(kern[dom][1] / (seconds / args.steps), 3)
     roof_i32 = roof("tgemm_nt int32 min-plus 8192^3", n3, t_i32min)
     roof_i32["traffic"] = traffic.get("tgemm_nt int32 min-plus 8192^3")
+    # measured issue ceilings of the instruction mixes (terms / clock / SM)
+    probe = {}
+    for mix, name in ((0, "int32_dpx"), (1, "fp32_f32x2_min3"), (2, "u16x2_dpx")):
+        try:
+            probe[name] = round(btas.measure_issue_rate(mix), 1)
+        except Exception as exc:  # diagnostic only
+            probe[name] = f"unavailable: {exc}"
+    if isinstance(probe.get("int32_dpx"), float):
+        ceil = probe["int32_dpx"] * sms * max_mhz * 1e6 / 1e12
+        roof_i32["measured_issue_ceiling_tops"] = round(ceil, 3)
+        roof_i32["frac_of_measured_ceiling"] = round(n3 / t_i32min / 1e12 / ceil, 4)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Gop/s", "n_gpus": world, "steps": args.steps,
@@ -336,6 +352,7 @@ def run_btas(args):
                        "apsp": round(computed * n3 / t_apsp / 1e9, 1)},
         "roofline": roofline,
         "roofline_int32_minplus": roof_i32,
+        "issue_probe_terms_per_clk_per_sm": probe,
         "clocks": clocks,
         "gpu_launches": launches,
     }
@@ -346,6 +363,9 @@ def run_btas(args):
         del dev, Ci, Cf, D
         torch.cuda.empty_cache()
         line["batched"] = batched(args, btas, torch)
+    if not args.no_serve:
+        torch.cuda.empty_cache()
+        line["serve"] = serve(args, btas, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, sample = cpu_oracle_rate(inp)
         line["cpu_baseline"] = {"value": round(rate, 3), "unit": "Gop/s", "cores": threads, "kind": "oracle",
@@ -425,6 +445,102 @@ def batched(args, btas, torch):
             "gemm_terms": gemm_terms, "identical_results": bool(same)}
 
 
+def serve(args, btas, torch):
+    """Serving workload: Poisson arrivals of mixed requests -- 50 % APSP
+    (int32, p = 0.1, w in [1, 100]) and 50 % single tropical products (n x n x n,
+    min/max-plus 50/50, int32/fp32 50/50) -- with n log-uniform in [64, 4096],
+    host buffers, admitted under a 40 GB device-memory budget.  For every
+    arrival rate: p50/p99 latency (arrival -> result in host memory) and
+    completed requests/s, for the continuous-batching server and for plain
+    serial execution (one request at a time through the single calls)."""
+    import threading
+    import numpy as np
+    import gen
+    T = 32
+    sizes = gen.loguniform_sizes(gen.BASE_SEED, 60, T, 64, 4096)
+    kinds = gen.uniform_int(gen.BASE_SEED, 61, (T,), 0, 1)
+    srs = gen.uniform_int(gen.BASE_SEED, 62, (T,), 0, 1)
+    dts = gen.uniform_int(gen.BASE_SEED, 63, (T,), 0, 1)
+    tmpl = []
+    for i in range(T):
+        n = int(sizes[i])
+        if kinds[i] == 0:
+            W = torch.from_numpy(gen.random_graph(gen.BASE_SEED, 6000 + i, n, 0.1, 1, 100)).pin_memory()
+            tmpl.append(("apsp", n, W, torch.empty((n, n), dtype=torch.int32).pin_memory()))
+        else:
+            if dts[i] == 0:
+                A = gen.uniform_int(gen.BASE_SEED, 7000 + i, (n, n), 0, 10 ** 6)
+                B = gen.uniform_int(gen.BASE_SEED, 8000 + i, (n, n), 0, 10 ** 6)
+            else:
+                A = gen.uniform_f32(gen.BASE_SEED, 7000 + i, (n, n))
+                B = gen.uniform_f32(gen.BASE_SEED, 8000 + i, (n, n))
+            tmpl.append(("gemm", n, torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(),
+                         torch.empty((n, n), dtype=torch.int32 if dts[i] == 0 else torch.float32).pin_memory(),
+                         int(srs[i])))
+    R = args.serve_requests
+    pick = gen.uniform_int(gen.BASE_SEED, 64, (R,), 0, T - 1)
+    u = gen.uniform_unit_f64(gen.BASE_SEED, 65, np.arange(R, dtype=np.uint64))
+    gaps = -np.log1p(-u)  # exponential(1)
+
+    def pct(lat):
+        lat = np.sort(np.asarray(lat))
+        return float(np.percentile(lat, 50) * 1e3), float(np.percentile(lat, 99) * 1e3)
+
+    out = {"workload": "Poisson arrivals; 50% APSP int32 (p=0.1, w[1,100]) / 50% tropical product "
+                       "(min/max 50/50, int32/fp32 50/50); n log-uniform [64,4096]; host buffers; 40 GB budget",
+           "requests_per_rate": R, "templates": T, "rates": []}
+    for rate in [float(x) for x in args.serve_rates.split(",")]:
+        arrivals = np.cumsum(gaps / rate)
+        # continuous-batching server
+        srv = btas.Server(40 << 30)
+        tickets = [None] * R
+        t_base = [0.0]
+
+        def producer():
+            start = time.perf_counter()
+            for i in range(R):
+                while time.perf_counter() - start < arrivals[i]:
+                    time.sleep(max(0.0, min(1e-4, arrivals[i] - (time.perf_counter() - start))))
+                t = tmpl[pick[i]]
+                if t[0] == "apsp":
+                    tickets[i] = srv.submit_apsp(t[2], t[3])
+                else:
+                    tickets[i] = srv.submit_gemm(t[2], t[3], t[4], t[5])
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        srv.wait_all(600)
+        polls = [srv.poll(tk) for tk in tickets]
+        stats = srv.stats()
+        srv.close()
+        lat = [p["t_done"] - p["t_submit"] for p in polls]
+        span = max(p["t_done"] for p in polls) - min(p["t_submit"] for p in polls)
+        p50, p99 = pct(lat)
+        # serial plain execution of the same arrival sequence
+        slat = []
+        start = time.perf_counter()
+        for i in range(R):
+            now = time.perf_counter() - start
+            if now < arrivals[i]:
+                time.sleep(arrivals[i] - now)
+            t = tmpl[pick[i]]
+            if t[0] == "apsp":
+                d = btas.apsp(t[2].cuda(non_blocking=True))
+                t[3].copy_(d)
+            else:
+                c = btas.gemm(t[2].cuda(non_blocking=True), t[3].cuda(non_blocking=True), t[5])
+                t[4].copy_(c)
+            torch.cuda.synchronize()
+            slat.append(time.perf_counter() - start - arrivals[i])
+        sspan = time.perf_counter() - start
+        s50, s99 = pct(slat)
+        out["rates"].append({"rate_req_s": rate, "p50_ms": round(p50, 3), "p99_ms": round(p99, 3),
+                             "throughput_req_s": round(R / span, 1), "steps": stats["steps"],
+                             "serial_p50_ms": round(s50, 3), "serial_p99_ms": round(s99, 3),
+                             "serial_throughput_req_s": round(R / sspan, 1)})
+    return out
+
+
 def e2e(args, inp, btas, torch, units_per_step):
     """Same step through the public API with pinned host buffers: every step
     copies its inputs host -> device and its results device -> host."""
@@ -463,10 +579,50 @@ def e2e(args, inp, btas, torch, units_per_step):
             "d2h_bytes_per_step": bo, "steps": steps}
 
 
+def run_only(args):
+    """One part alone, for profiling: `kernels` runs one product of each
+    kernel family at size --n (B supplied transposed; the packed 16-bit
+    product on values < 2^14); `batched` / `serve` run those workloads."""
+    import torch
+    import paper_1701_04733_gb300 as btas
+    torch.cuda.set_device(dist_env()[2])
+    if args.only == "kernels":
+        import gen
+        n = args.n
+        s = gen.BASE_SEED
+        Ai = torch.from_numpy(gen.uniform_int(s, 21, (n, n), 0, 10 ** 6)).cuda()
+        BiT = torch.from_numpy(gen.uniform_int(s, 22, (n, n), 0, 10 ** 6)).cuda()
+        Af = torch.from_numpy(gen.uniform_f32(s, 23, (n, n))).cuda()
+        BfT = torch.from_numpy(gen.uniform_f32(s, 24, (n, n))).cuda()
+        A16 = torch.from_numpy(gen.uniform_int(s, 25, (n, n), 0, 1 << 14).astype("int16")).cuda()
+        B16 = torch.from_numpy(gen.uniform_int(s, 26, (n, n), 0, 1 << 14).astype("int16")).cuda()
+        Ci, Cf, C16 = torch.empty_like(Ai), torch.empty_like(Af), torch.empty_like(A16)
+        t = {}
+        for name, fn in (("i32_min", lambda: btas.gemm(Ai, BiT, 0, out=Ci, trans_b=True)),
+                         ("i32_max", lambda: btas.gemm(Ai, BiT, 1, out=Ci, trans_b=True)),
+                         ("f32_min", lambda: btas.gemm(Af, BfT, 0, out=Cf, trans_b=True)),
+                         ("f32_max", lambda: btas.gemm(Af, BfT, 1, out=Cf, trans_b=True)),
+                         ("u16_min", lambda: btas.gemm(A16, B16, 0, out=C16))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t[name] = round(e0.elapsed_time(e1), 3)
+        print(json.dumps({"only": "kernels", "n": n, "ms": t}))
+    elif args.only == "batched":
+        print(json.dumps({"only": "batched", **batched(args, btas, torch)}))
+    else:
+        print(json.dumps({"only": "serve", **serve(args, btas, torch)}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_btas(args)
 
 

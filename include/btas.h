@@ -94,6 +94,13 @@ const char *btas_last_error_string(void);
  * (all threads, all devices).  Diagnostic counter; never reset. */
 int64_t btas_kernel_launches(void);
 
+/* Diagnostic: measured issue ceiling of the current device for one inner-loop
+ * instruction mix, in tropical terms (one (i,j,k) add-then-min) per clock per
+ * SM, from a register-only kernel with one CTA per SM (synchronises the
+ * device).  mix: 0 = int32 DPX fused add-min, 1 = fp32 add.f32x2 + 3-input
+ * min, 2 = packed u16x2 DPX add-min, 3 = FFMA (multiply-adds, reference). */
+btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_per_sm);
+
 /* ------------------------------------------------------------------------
  * Level 3: tropical matrix product (the product listing of Sec. IV, titled
  * "Matrix-Matrix Multiplication for Floyd-Warshall": replace + by min (or
@@ -206,6 +213,29 @@ btas_status btas_apsp_ex(int64_t n, const int32_t *W, int32_t *D, int flags,
 btas_status btas_apsp_u16(int64_t n, const uint16_t *W, uint16_t *D, int max_w, int flags,
                           void *stream);
 
+/* btas_closure: tropical closure (Kleene star) A* = E (+) A (+) A^2 (+) ...,
+ * the shortest (min-plus) or longest (max-plus) walk weights of the matrix
+ * graph A, computed as (E (+) A) squared until it stops changing (at most
+ * ceil(log2(n-1)) squarings suffice when A* exists, Sec. III), E being the
+ * tropical identity (0 on the diagonal).  Unlike btas_apsp, entries may be
+ * negative (min-plus) or positive (max-plus) and the diagonal is arbitrary;
+ * with non-negative weights and dtype BTAS_F32 this is FP32 APSP, bit-exact
+ * with the same squaring sequence (fp32 results are those of repeated
+ * squaring, not of Floyd-Warshall's evaluation order).
+ * semiring/dtype: BTAS_MINPLUS or BTAS_MAXPLUS; BTAS_I32 or BTAS_F32.
+ * A, Astar     : n x n device matrices, leading dimension n; may alias.
+ * flags        : BTAS_APSP_EARLY_EXIT or 0 (the result is the same).
+ * squarings_done: HOST pointer or NULL: squarings that changed the matrix.
+ * The result is D_S, S = ceil(log2(n-1)) squarings of E (+) A (the loop
+ * stops early at a fixpoint, which does not change it).  The call
+ * synchronises `stream` once per squaring.  If all S squarings changed the
+ * matrix, one more squaring is checked: a negative (min-plus) or positive
+ * (max-plus) diagonal entry there proves a cycle of that sign, A* does not
+ * exist, and the call returns BTAS_ERR_ARG.  int32: finite entries and
+ * every walk weight must stay in [-2^28, 2^28]. */
+btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void *Astar, int flags,
+                         int *squarings_done, void *stream);
+
 /* Number of squarings btas_apsp performs for n vertices: ceil(log2(n-1)). */
 int btas_apsp_squarings(int64_t n);
 
@@ -278,6 +308,49 @@ btas_status btas_batch_wait(btas_batch_t *b, void *stream);
 btas_status btas_batch_destroy(btas_batch_t *b);
 int64_t btas_batch_workspace_bytes(btas_batch_t *b);
 int btas_batch_tasks(btas_batch_t *b);
+
+/* ------------------------------------------------------------------------
+ * Continuous-batching server: requests with HOST buffers (contiguous
+ * row-major; pinned memory gives asynchronous copies) are admitted in
+ * arrival order while the device-memory footprint of admitted requests stays
+ * within `hbm_budget_bytes`.  An executor thread runs steps: each step runs
+ * the next unit of every admitted request (a whole product, or one APSP
+ * squaring) in one persistent launch; requests arriving meanwhile join the
+ * next step.  A product completes after its step; an APSP solve after its
+ * last squaring or as soon as a squaring changed nothing.  Results are
+ * bit-identical to btas_gemm / btas_apsp (APSP here always uses the int32
+ * kernels).  Buffers must stay valid until the request is done.
+ *
+ * btas_server_create      : budget in bytes (> 0); flags must be 0.  The
+ *                           current device is the server's device.
+ * btas_server_submit_apsp : n x n int32 W (host) -> D (host); *ticket
+ *                           receives the request id.  The domain (zero
+ *                           diagonal, weights in [0, 2^28] or INF) is
+ *                           assumed.  BTAS_ERR_BUDGET if the request alone
+ *                           exceeds the budget.
+ * btas_server_submit_gemm : C (m x n) = A (m x k) (x) B (k x n), host,
+ *                           int32 or fp32, min-plus or max-plus.
+ * btas_server_poll        : state (0 queued, 1 running, 2 done, 3 failed)
+ *                           and seconds since server creation at submit,
+ *                           admission and completion (result in host
+ *                           memory); any out-pointer may be NULL.
+ * btas_server_wait_all    : blocks until no request is queued or running,
+ *                           at most timeout_s (BTAS_ERR_TIMEOUT).
+ * btas_server_stats       : steps run, units executed, requests completed,
+ *                           device bytes currently admitted.
+ * btas_server_destroy     : drains outstanding work, then frees the server.
+ * ------------------------------------------------------------------------ */
+typedef struct btas_server_t btas_server_t;
+btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, int flags);
+btas_status btas_server_submit_apsp(btas_server_t *s, int64_t n, const int32_t *W, int32_t *D, int64_t *ticket);
+btas_status btas_server_submit_gemm(btas_server_t *s, int semiring, int dtype, int64_t m, int64_t n, int64_t k,
+                                    const void *A, const void *B, void *C, int64_t *ticket);
+btas_status btas_server_poll(btas_server_t *s, int64_t ticket, int *state, double *t_submit, double *t_admit,
+                             double *t_done);
+btas_status btas_server_wait_all(btas_server_t *s, double timeout_s);
+btas_status btas_server_stats(btas_server_t *s, int64_t *steps, int64_t *units, int64_t *completed,
+                              int64_t *bytes_in_use);
+btas_status btas_server_destroy(btas_server_t *s);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,7 @@ What each function computes, and the passage it follows:
   apsp_squarings(n)           S = ceil(log2(n-1)) (Sec. III)
   apsp_squaring(W)            D = W squared S times (Sec. III)
   floyd_warshall(W)           Algorithm 2 with an INF sentinel
+  apsp_paths(W)               squaring with next-hop matrix (smallest minimising k)
   dijkstra_rows(W, srcs)      textbook single-source shortest paths
   bruteforce_apsp(W)          minimum over all simple paths (n <= 8)
   dot / axpy / add / mul      tropical vector operations (abstract, Sec. III)
@@ -74,6 +75,7 @@ def _load():
             "oracle_apsp_squaring_i32": (None, [i64, vp, vp, i32]),
             "oracle_apsp_squaring_u16": (None, [i64, vp, vp, i32]),
             "oracle_fw_i32": (None, [i64, vp]),
+            "oracle_apsp_paths_i32": (None, [i64, vp, vp, vp, i32]),
             "oracle_dijkstra_rows_i32": (None, [i64, vp, i64, vp, vp]),
             "oracle_bruteforce_apsp_i32": (i32, [i64, vp, vp]),
             "oracle_dot_i32": (ctypes.c_int32, [i32, i64, vp, i64, vp, i64]),
@@ -156,6 +158,18 @@ def apsp_squaring(W: np.ndarray, squarings: int | None = None) -> np.ndarray:
     D = np.empty_like(W)
     _load().oracle_apsp_squaring_i32(n, _p(W), _p(D), s)
     return D
+
+
+def apsp_paths(W: np.ndarray, squarings: int | None = None):
+    """APSP by squaring with next-hop tracking (smallest minimising k).
+    Returns (D, Next)."""
+    W = _c(W, np.int32)
+    n = W.shape[0]
+    s = apsp_squarings(n) if squarings is None else int(squarings)
+    D = np.empty_like(W)
+    Nx = np.empty_like(W)
+    _load().oracle_apsp_paths_i32(n, _p(W), _p(D), _p(Nx), s)
+    return D, Nx
 
 
 def floyd_warshall(W: np.ndarray) -> np.ndarray:

@@ -170,6 +170,46 @@ void oracle_apsp_squaring_u16(int64_t n, const uint16_t *W, uint16_t *D, int squ
     free(nxt);
 }
 
+/* APSP by repeated squaring with next-hop (successor) tracking.  N_0[i][j] =
+ * j for an edge i->j (i != j), i on the diagonal, -1 for no edge.  One
+ * squaring: D'[i][j] = min_k D[i][k] + D[k][j] with k* the SMALLEST minimising
+ * k (all k in 0..n-1, including i and j); N'[i][j] = -1 if D'[i][j] is INF,
+ * else the first hop of the walk (i -> k*) + (k* -> j): N[i][j] when k* == i
+ * (the first leg is empty), N[i][k*] otherwise.  Exactly `squarings` steps. */
+void oracle_apsp_paths_i32(int64_t n, const int32_t *W, int32_t *D, int32_t *Next, int squarings) {
+    size_t nn = (size_t)n * (size_t)n;
+    int32_t *d = (int32_t *)malloc(nn ? nn * 4 : 4), *d2 = (int32_t *)malloc(nn ? nn * 4 : 4);
+    int32_t *x = (int32_t *)malloc(nn ? nn * 4 : 4), *x2 = (int32_t *)malloc(nn ? nn * 4 : 4);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            d[i * n + j] = W[i * n + j];
+            x[i * n + j] = (i == j) ? (int32_t)i : (W[i * n + j] == O_INF32 ? -1 : (int32_t)j);
+        }
+    for (int s = 0; s < squarings; ++s) {
+        int64_t i;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(o_threads)
+        for (i = 0; i < n; ++i) {
+            for (int64_t j = 0; j < n; ++j) {
+                int32_t best = O_INF32;
+                int64_t kbest = -1;
+                for (int64_t k = 0; k < n; ++k) {
+                    int32_t t = otimes_i32(O_MINPLUS, d[i * n + k], d[k * n + j]);
+                    if (t < best) { best = t; kbest = k; }
+                }
+                d2[i * n + j] = best;
+                if (best == O_INF32) x2[i * n + j] = -1;
+                else if (kbest == i) x2[i * n + j] = x[i * n + j];
+                else x2[i * n + j] = x[i * n + kbest];
+            }
+        }
+        int32_t *t = d; d = d2; d2 = t;
+        t = x; x = x2; x2 = t;
+    }
+    memcpy(D, d, nn * 4);
+    memcpy(Next, x, nn * 4);
+    free(d); free(d2); free(x); free(x2);
+}
+
 /* Sequential Floyd-Warshall (Algorithm 2): pivot z outermost, relax
  * D[x][y] through z when both legs exist.  In place; row z and column z do
  * not change while z is the pivot, so the in-place update is exact. */

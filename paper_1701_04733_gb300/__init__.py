@@ -55,6 +55,7 @@ SIGNATURES = {
     "btas_version": (_i32, []),
     "btas_last_error_string": (ctypes.c_char_p, []),
     "btas_kernel_launches": (_i64, []),
+    "btas_measure_issue_rate": (_i32, [_i32, _vp]),
     "btas_gemm": (_i32, [_i32, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "btas_dot": (_i32, [_i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp, _vp]),
     "btas_axpy": (_i32, [_i32, _i32, _i64, _vp, _vp, _i64, _vp, _i64, _vp]),
@@ -64,6 +65,7 @@ SIGNATURES = {
     "btas_apsp_ex": (_i32, [_i64, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "btas_apsp_u16": (_i32, [_i64, _vp, _vp, _i32, _i32, _vp]),
     "btas_apsp_squarings": (_i32, [_i64]),
+    "btas_closure": (_i32, [_i32, _i32, _i64, _vp, _vp, _i32, _vp, _vp]),
     "btas_apsp_noalloc": (_i32, [_i64, _vp, _vp, _vp]),
     "btas_batch_create": (_i32, [_vp, _i32]),
     "btas_batch_add_apsp": (_i32, [_vp, _i64, _vp, _vp]),
@@ -73,6 +75,13 @@ SIGNATURES = {
     "btas_batch_destroy": (_i32, [_vp]),
     "btas_batch_workspace_bytes": (_i64, [_vp]),
     "btas_batch_tasks": (_i32, [_vp]),
+    "btas_server_create": (_i32, [_vp, _i64, _i32]),
+    "btas_server_submit_apsp": (_i32, [_vp, _i64, _vp, _vp, _vp]),
+    "btas_server_submit_gemm": (_i32, [_vp, _i32, _i32, _i64, _i64, _i64, _vp, _vp, _vp, _vp]),
+    "btas_server_poll": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "btas_server_wait_all": (_i32, [_vp, ctypes.c_double]),
+    "btas_server_stats": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "btas_server_destroy": (_i32, [_vp]),
 }
 
 
@@ -117,6 +126,17 @@ def btas_kernel_launches() -> int:
     return lib().btas_kernel_launches()
 
 
+def btas_measure_issue_rate(mix, out_ptr) -> int:
+    return lib().btas_measure_issue_rate(mix, out_ptr)
+
+
+def measure_issue_rate(mix: int) -> float:
+    """Terms per clock per SM of instruction mix `mix` (see btas.h)."""
+    v = ctypes.c_double()
+    check(btas_measure_issue_rate(mix, ctypes.addressof(v)))
+    return v.value
+
+
 def btas_gemm(semiring, dtype, m, n, k, A, lda, B, ldb, C, ldc, stream) -> int:
     return lib().btas_gemm(semiring, dtype, m, n, k, A, lda, B, ldb, C, ldc, stream)
 
@@ -151,6 +171,26 @@ def btas_apsp_u16(n, W, D, max_w, flags, stream) -> int:
 
 def btas_apsp_squarings(n) -> int:
     return lib().btas_apsp_squarings(n)
+
+
+def btas_closure(semiring, dtype, n, A, Astar, flags, squarings_done_ptr, stream) -> int:
+    return lib().btas_closure(semiring, dtype, n, A, Astar, flags, squarings_done_ptr, stream)
+
+
+def closure(A, semiring="min", out=None, early_exit=True, stream=None, info=False):
+    """Tropical closure A* = E (+) A (+) A^2 (+) ... of a square int32/fp32
+    CUDA matrix by repeated squaring; raises BtasError if a negative
+    (min-plus) / positive (max-plus) cycle makes it diverge."""
+    torch = _torch()
+    n = A.shape[0]
+    if A.shape != (n, n) or not A.is_contiguous():
+        raise ValueError("A must be a contiguous square matrix")
+    if out is None:
+        out = torch.empty_like(A)
+    sq = ctypes.c_int(0)
+    check(btas_closure(_sr(semiring), _dtype_code(A), n, A.data_ptr(), out.data_ptr(),
+                       APSP_EARLY_EXIT if early_exit else 0, ctypes.addressof(sq), _stream(stream)))
+    return (out, {"squarings": sq.value}) if info else out
 
 
 def btas_apsp_noalloc(n, W, D, stream) -> int:
@@ -382,6 +422,66 @@ class Batch:
             btas_batch_destroy(self.handle)
             self.handle = None
             self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (btas_server_*).  Submit requests
+    with host tensors (pinned for asynchronous copies); keep them alive until
+    the request is done."""
+
+    def __init__(self, hbm_budget_bytes: int):
+        h = ctypes.c_void_p()
+        check(lib().btas_server_create(ctypes.addressof(h), int(hbm_budget_bytes), 0))
+        self.handle = h.value
+        self._keep = {}
+
+    def submit_apsp(self, W, D) -> int:
+        n = W.shape[0]
+        if W.device.type != "cpu" or D.device.type != "cpu" or not W.is_contiguous() or not D.is_contiguous():
+            raise ValueError("server requests take contiguous host tensors")
+        t = ctypes.c_int64()
+        check(lib().btas_server_submit_apsp(self.handle, n, W.data_ptr(), D.data_ptr(), ctypes.addressof(t)))
+        self._keep[t.value] = (W, D)
+        return t.value
+
+    def submit_gemm(self, A, B, C, semiring="min") -> int:
+        m, k = A.shape
+        n = B.shape[1]
+        for x in (A, B, C):
+            if x.device.type != "cpu" or not x.is_contiguous():
+                raise ValueError("server requests take contiguous host tensors")
+        t = ctypes.c_int64()
+        check(lib().btas_server_submit_gemm(self.handle, _sr(semiring), _dtype_code(A), m, n, k, A.data_ptr(),
+                                            B.data_ptr(), C.data_ptr(), ctypes.addressof(t)))
+        self._keep[t.value] = (A, B, C)
+        return t.value
+
+    def poll(self, ticket: int):
+        st = ctypes.c_int()
+        ts, ta, td = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().btas_server_poll(self.handle, ticket, ctypes.addressof(st), ctypes.addressof(ts),
+                                     ctypes.addressof(ta), ctypes.addressof(td)))
+        return {"state": st.value, "t_submit": ts.value, "t_admit": ta.value, "t_done": td.value}
+
+    def wait_all(self, timeout_s: float = 600.0):
+        check(lib().btas_server_wait_all(self.handle, float(timeout_s)))
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        check(lib().btas_server_stats(self.handle, *[ctypes.addressof(x) for x in v]))
+        return {"steps": v[0].value, "units": v[1].value, "completed": v[2].value, "bytes_in_use": v[3].value}
+
+    def close(self):
+        if self.handle:
+            lib().btas_server_destroy(self.handle)
+            self.handle = None
+            self._keep = {}
 
     def __del__(self):
         try:

@@ -98,6 +98,29 @@ __global__ void apsp_scan_kernel(const int *__restrict__ W, long long n, int *ou
     }
 }
 
+// dst = E (+) src: the tropical identity E (0 on the diagonal, the (+)-identity
+// elsewhere) (+)-added to src, i.e. src with its diagonal replaced by
+// min(src_ii, 0) (min-plus) or max(src_ii, 0) (max-plus).
+__global__ void ident_oplus_kernel(const uint32_t *__restrict__ src, long long lds, int n,
+                                   uint32_t *__restrict__ dst, long long ldd, int sr, int is_float) {
+    const long long total = (long long)n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long r = idx / n, c = idx % n;
+        uint32_t v = src[r * lds + c];
+        if (r == c) {
+            if (is_float) {
+                const float f = __uint_as_float(v);
+                v = __float_as_uint(sr == kMin ? fminf(f, 0.f) : fmaxf(f, 0.f));
+            } else {
+                const int x = static_cast<int>(v);
+                v = static_cast<uint32_t>(sr == kMin ? min(x, 0) : max(x, 0));
+            }
+        }
+        dst[r * ldd + c] = v;
+    }
+}
+
 static int grid_for(long long total, int threads) {
     long long b = (total + threads - 1) / threads;
     if (b > 152 * 16) b = 152 * 16;
@@ -127,6 +150,15 @@ cudaError_t launch_fill4(void *dst, long long ldd, int rows, int cols, uint32_t 
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     fill4_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, st>>>(static_cast<uint32_t *>(dst), ldd,
                                                                          rows, cols, bits);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ident_oplus(const void *src, long long lds, int n, void *dst, long long ldd, int sr, int is_float,
+                               cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    ident_oplus_kernel<<<grid_for((long long)n * n, 256), 256, 0, st>>>(
+        static_cast<const uint32_t *>(src), lds, n, static_cast<uint32_t *>(dst), ldd, sr, is_float);
     note_launch();
     return cudaGetLastError();
 }

@@ -24,49 +24,13 @@
 #include <vector>
 
 #include "common.cuh"
+#include "batch_kernel.cuh"
 #include "kernels.h"
 #include "tgemm.cuh"
 
 namespace btas {
 
 using BCfg = TileCfg<128, 128, 32, 3, 2, 2, 1>;  // 2 CTAs/SM, <= 128 registers
-constexpr int kBT = 128;                          // task tile edge
-
-enum TaskType : int { kTaskTranspose = 0, kTaskApsp = 1, kTaskGemm = 2, kTaskCopy = 3 };
-enum InstKind : int { kInstApsp = 0, kInstGemm = 1 };
-
-struct BInst {
-    int kind, sr, dtype;
-    int m, n, k;
-    int levels;           // APSP: S (>= 1); GEMM: 1
-    int tiles_m, tiles_n; // output tiles
-    int t0_rows, t0_cols; // level-0 transpose source shape (0 x 0: none)
-    int done_base;        // done[done_base + level]
-    int flag_base;        // changed[flag_base + level]
-    int trans_b;
-    const void *A;        // GEMM A / APSP W
-    long long lda;
-    const void *B;        // GEMM B (k x n, or n x k if trans_b)
-    long long ldb;
-    void *C;              // GEMM C / APSP D
-    long long ldc;
-    void *X0, *X1;        // APSP intermediate D_s (n x n, pitch ldx)
-    long long ldx;
-    void *Q0, *Q1;        // APSP transposes / GEMM B^T (Q0)
-    long long ldq;
-};
-
-struct BatchParams {
-    const int4 *tasks;  // (type, inst, level, tile)
-    int total;
-    int *next;
-    int *done;
-    int *changed;
-    int *status;
-    const BInst *insts;
-    long long timeout_cycles;
-    int withhold_inst;  // fault injection for tests: this instance's level-1+ tasks never become ready
-};
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
@@ -141,8 +105,8 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
         const BInst I = p.insts[inst];
         bool ch = false;
         if (type == kTaskTranspose) {
-            const uint32_t *src = static_cast<const uint32_t *>(I.kind == kInstApsp ? I.A : I.B);
-            const long long lds = I.kind == kInstApsp ? I.lda : I.ldb;
+            const uint32_t *src = static_cast<const uint32_t *>(I.kind == kInstGemm ? I.B : I.A);
+            const long long lds = I.kind == kInstGemm ? I.ldb : I.lda;
             transpose_tile(src, lds, I.t0_rows, I.t0_cols, static_cast<uint32_t *>(I.Q0), I.ldq, tile,
                            reinterpret_cast<uint32_t *>(smem_raw), tid);
         } else if (type == kTaskCopy) {
@@ -176,6 +140,18 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                 void *Ct = s < S ? ((s & 1) ? I.Q1 : I.Q0) : nullptr;
                 ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, Ct, I.ldq);
             }
+        } else if (type == kTaskSquare) {
+            const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
+            GemmArgs a{};
+            a.m = a.n = a.k = I.n;
+            a.A = I.A; a.lda = I.lda;
+            a.Bt = I.Q0; a.ldb = I.ldq;
+            a.C = I.C; a.ldc = I.ldc;
+            a.prev = I.A; a.ldp = I.lda;
+            a.one = 1;
+            a.vec_a = ((reinterpret_cast<uintptr_t>(I.A) & 15) == 0) && ((I.lda & 3) == 0);
+            a.vec_b = 1;
+            ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, I.Q1, I.ldq);
         } else {  // kTaskGemm
             const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
             GemmArgs a{};
@@ -196,10 +172,37 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
         }
         if (type == kTaskApsp && __any_sync(0xffffffffu, ch) && (tid & 31) == 0)
             atomicOr(p.changed + I.flag_base + level, 1);
+        if (type == kTaskSquare && __any_sync(0xffffffffu, ch) && (tid & 31) == 0) atomicOr(I.changed_ptr, 1);
         __threadfence();
         __syncthreads();
         if (tid == 0) atomicAdd(p.done + I.done_base + level, 1);
     }
+}
+
+
+int batch_kernel_smem() { return std::max(BCfg::kSmemBytes, kBT * (kBT + 1) * 4); }
+int batch_kernel_threads() { return BCfg::kThreads; }
+
+cudaError_t batch_kernel_prepare(int *ctas_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_kernel_smem());
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, batch_kernel, BCfg::kThreads,
+                                                         batch_kernel_smem());
+}
+
+cudaError_t launch_batch_kernel(const BatchParams &p, int grid, cudaStream_t st) {
+    batch_kernel<<<grid, BCfg::kThreads, batch_kernel_smem(), st>>>(p);
+    note_launch();
+    return cudaGetLastError();
+}
+
+long long batch_timeout_cycles(int device) {
+    int clk_khz = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, device);
+    long long c = (long long)(2.0 * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);
+    const char *tmo = getenv("BTAS_BATCH_TIMEOUT_CYCLES");
+    if (tmo && *tmo) c = atoll(tmo);
+    return c;
 }
 
 }  // namespace btas
@@ -355,23 +358,16 @@ btas_status build_plan(btas_batch_t *b) {
     p.done = b->d_counters + 2;
     p.changed = b->d_counters + 2 + counters;
     p.insts = d_insts;
-    int clk_khz = 0;
-    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
-    const double secs = 2.0;
-    p.timeout_cycles = (long long)(secs * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);
-    const char *tmo = getenv("BTAS_BATCH_TIMEOUT_CYCLES");
-    if (tmo && *tmo) p.timeout_cycles = atoll(tmo);
+    p.timeout_cycles = batch_timeout_cycles(dev);
     // Fault injection (tests only): BTAS_BATCH_WITHHOLD=i makes the host
     // withhold one completion of instance i (in add order), so its bounded
     // waits run out and the launch ends with BTAS_ERR_TIMEOUT.
     const char *wh = getenv("BTAS_BATCH_WITHHOLD");
     p.withhold_inst = (wh && *wh) ? atoi(wh) : -1;
     // grid: resident CTAs
-    b->smem = std::max(BCfg::kSmemBytes, kBT * (kBT + 1) * 4);
-    if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem) != cudaSuccess)
-        return bfail(BTAS_ERR_CUDA, "btas_batch: smem attribute");
+    b->smem = batch_kernel_smem();
     int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, BCfg::kThreads, b->smem);
+    if (batch_kernel_prepare(&per_sm) != cudaSuccess) return bfail(BTAS_ERR_CUDA, "btas_batch: kernel attributes");
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     b->grid = std::max(1, std::min(per_sm * sms, std::max(1, b->total)));
     // capture: counter reset + persistent kernel
@@ -381,7 +377,7 @@ btas_status build_plan(btas_batch_t *b) {
         if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return bfail(BTAS_ERR_CUDA, "btas_batch: begin capture");
         cudaMemsetAsync(b->d_counters, 0, b->counter_bytes, b->cap);
-        batch_kernel<<<b->grid, BCfg::kThreads, b->smem, b->cap>>>(p);
+        launch_batch_kernel(p, b->grid, b->cap);
         const cudaError_t e1 = cudaStreamEndCapture(b->cap, &b->graph);
         if (e1 != cudaSuccess) return bfail(BTAS_ERR_CUDA, "btas_batch: end capture");
         if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
@@ -492,11 +488,7 @@ btas_status btas_batch_launch(btas_batch_t *b, void *stream) {
         note_launch();
     } else {
         e = cudaMemsetAsync(b->d_counters, 0, b->counter_bytes, st);
-        if (e == cudaSuccess) {
-            batch_kernel<<<b->grid, BCfg::kThreads, b->smem, st>>>(b->params);
-            note_launch();
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess) e = launch_batch_kernel(b->params, b->grid, st);
     }
     if (e != cudaSuccess) return bfail(BTAS_ERR_CUDA, cudaGetErrorString(e));
     return BTAS_OK;

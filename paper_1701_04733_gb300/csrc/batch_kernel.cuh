@@ -1,0 +1,61 @@
+// Persistent tile-task kernel shared by the batched launch (batch.cu) and
+// the continuous-batching server (server.cu).  Host code sees only the
+// descriptor structs and the launcher.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace btas {
+
+constexpr int kBT = 128;  // task tile edge
+
+enum TaskType : int { kTaskTranspose = 0, kTaskApsp = 1, kTaskGemm = 2, kTaskCopy = 3, kTaskSquare = 4 };
+enum InstKind : int { kInstApsp = 0, kInstGemm = 1, kInstSquare = 2 };
+
+// One problem of a launch.  kInstApsp: a whole APSP solve (levels = S
+// squarings); kInstGemm: one product; kInstSquare: ONE squaring
+// C = A (x) A with prev = A, B operand A^T in Q0 (level 0 transposes A into
+// Q0 when t0_rows > 0), optional transposed output into Q1 and a change flag
+// at changed_ptr.
+struct BInst {
+    int kind, sr, dtype;
+    int m, n, k;
+    int levels;           // APSP: S (>= 1); GEMM / square: 1
+    int tiles_m, tiles_n; // output tiles
+    int t0_rows, t0_cols; // level-0 transpose source shape (0 x 0: none)
+    int done_base;        // done[done_base + level]
+    int flag_base;        // changed[flag_base + level]
+    int trans_b;
+    const void *A;        // GEMM A / APSP W / square input
+    long long lda;
+    const void *B;        // GEMM B (k x n, or n x k if trans_b)
+    long long ldb;
+    void *C;              // GEMM C / APSP D / square output
+    long long ldc;
+    void *X0, *X1;        // APSP intermediate D_s (n x n, pitch ldx)
+    long long ldx;
+    void *Q0, *Q1;        // APSP transposes / GEMM B^T (Q0) / square B operand and transposed output
+    long long ldq;
+    int *changed_ptr;     // square: change flag
+};
+
+struct BatchParams {
+    const int4 *tasks;  // (type, inst, level, tile)
+    int total;
+    int *next;
+    int *done;
+    int *changed;
+    int *status;
+    const BInst *insts;
+    long long timeout_cycles;
+    int withhold_inst;  // fault injection for tests: this instance's level-1+ tasks never become ready
+};
+
+// Dynamic shared memory and CTAs per SM of the persistent kernel.
+int batch_kernel_smem();
+int batch_kernel_threads();
+cudaError_t batch_kernel_prepare(int *ctas_per_sm);
+cudaError_t launch_batch_kernel(const BatchParams &p, int grid, cudaStream_t st);
+long long batch_timeout_cycles(int device);
+
+}  // namespace btas

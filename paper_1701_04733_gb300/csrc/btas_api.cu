@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -74,22 +75,27 @@ int env_int(const char *name, int dflt) {
     return v && *v ? atoi(v) : dflt;
 }
 
-// Kernel choice.  Variant and tile defaults come from measurement on GB300;
-// BTAS_I32_VARIANT (0 = DPX, 1 = mixed), BTAS_I32_NS, BTAS_F32_VARIANT
-// (2 = f32x2, 3 = scalar) and BTAS_CFG override them.
+// Kernel choice.  Defaults come from measurement on GB300 (8192^3: the
+// 2-CTA/SM, 64-bit-fragment tiles reach the measured issue ceilings of their
+// instruction mixes): int32 = IMAD/3-input-min mix on 4 of 8 columns, fp32 =
+// add.f32x2 + 3-input min; 64 x 64 tiles when fewer than 2 waves of 128 x 128
+// tiles exist.  BTAS_I32_VARIANT (0 = DPX, 1 = mixed), BTAS_I32_NS,
+// BTAS_F32_VARIANT (2 = f32x2, 3 = scalar, 4 = two scalar adds + 3-input min)
+// and BTAS_CFG override them.
 const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n) {
     int var, ns = 0;
     if (dtype == BTAS_F32) {
         var = env_int("BTAS_F32_VARIANT", kF32X2);
     } else {
         var = env_int("BTAS_I32_VARIANT", kI32Mix);
-        ns = var == kI32Mix ? env_int("BTAS_I32_NS", 5) : 0;
+        ns = var == kI32Mix ? env_int("BTAS_I32_NS", 4) : 0;
     }
     const long long big_tiles = ((m + 127) / 128) * ((n + 127) / 128);
-    int cfg = env_int("BTAS_CFG", big_tiles >= 2 * 152 ? 0 : 2);
+    int cfg = env_int("BTAS_CFG", big_tiles >= 2 * 152 ? 4 : 2);
     const GemmKernel *k = find_gemm_kernel(var, sr, ns, cfg);
+    if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Mix, sr, 5, cfg);
     if (!k) k = find_gemm_kernel(var, sr, ns, 0);
-    if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Dpx, sr, 0, cfg);
+    if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Mix, sr, 5, 0);
     if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Dpx, sr, 0, 0);
     if (!k && dtype == BTAS_F32) k = find_gemm_kernel(kF32X2, sr, 0, 0);
     return k;
@@ -477,6 +483,97 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     }
     if (squarings_done) *squarings_done = done;
     if (path_out) *path_out = used;
+    return BTAS_OK;
+}
+
+btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void *Astar, int flags,
+                         int *squarings_done, void *stream) {
+    if (semiring != BTAS_MINPLUS && semiring != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_closure: semiring");
+    if (dtype != BTAS_I32 && dtype != BTAS_F32) return fail(BTAS_ERR_ARG, "btas_closure: dtype");
+    if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_closure: n out of range");
+    if (flags & ~BTAS_APSP_EARLY_EXIT) return fail(BTAS_ERR_ARG, "btas_closure: unknown flags");
+    if (n == 0) {
+        if (squarings_done) *squarings_done = 0;
+        return BTAS_OK;
+    }
+    if (!A || !Astar) return fail(BTAS_ERR_ARG, "btas_closure: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // a squaring that changes nothing is a fixpoint, so stopping there (the
+    // early exit) never changes the result; the flag is accepted either way
+    const int S = btas_apsp_squarings(n);
+    const size_t nn = (size_t)n * (size_t)n;
+    const long long ldt = (n + 3) & ~3LL;
+    Workspace ws(st);
+    const size_t flag_bytes = align256((size_t)(S + 4) * 4);
+    BTAS_CUDA(ws.alloc(flag_bytes + 2 * align256(nn * 4) + align256((size_t)n * ldt * 4)), "workspace alloc");
+    char *base = static_cast<char *>(ws.p);
+    int *dflags = reinterpret_cast<int *>(base);
+    void *X = base + flag_bytes;
+    void *Y = static_cast<char *>(X) + align256(nn * 4);
+    void *T = static_cast<char *>(Y) + align256(nn * 4);
+    BTAS_CUDA(cudaMemsetAsync(dflags, 0, flag_bytes, st), "memset");
+    BTAS_CUDA(launch_ident_oplus(A, n, (int)n, X, n, semiring, dtype == BTAS_F32, st), "E (+) A");
+    // Square E (+) A: S = ceil(log2(n-1)) squarings reach every walk of
+    // <= n-1 edges, which is A* when no cycle improves a walk; a squaring
+    // that changes nothing is a fixpoint and ends the loop early.  If all S
+    // squarings changed the matrix, one more squaring covers walks of
+    // >= n edges: a negative (min-plus) / positive (max-plus) diagonal entry
+    // there proves such a cycle, and A* does not exist.  The result is D_S.
+    void *cur = X;
+    int done = 0;
+    bool converged = false;
+    auto square = [&](const void *in, void *out, int *flag) -> btas_status {
+        BTAS_CUDA(launch_transpose4(in, n, (int)n, (int)n, T, ldt, 0, nullptr, st), "transpose");
+        GemmArgs a{};
+        a.m = a.n = a.k = (int)n;
+        a.A = in; a.lda = n;
+        a.Bt = T; a.ldb = ldt;
+        a.C = out; a.ldc = n;
+        a.prev = in; a.ldp = n;
+        a.changed = flag;
+        a.vec_a = aligned16(in, n);
+        a.vec_b = aligned16(T, ldt);
+        return run_nt(dtype, semiring, a, st);
+    };
+    for (int s = 0; s < S; ++s) {
+        void *out = cur == X ? Y : X;
+        btas_status r = square(cur, out, &dflags[s]);
+        if (r != BTAS_OK) return r;
+        int changed = 1;
+        BTAS_CUDA(cudaMemcpyAsync(&changed, &dflags[s], 4, cudaMemcpyDeviceToHost, st), "flag readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "squaring sync");
+        if (!changed) {
+            converged = true;
+            break;
+        }
+        cur = out;
+        ++done;
+    }
+    if (!converged) {
+        void *chk = cur == X ? Y : X;
+        btas_status r = square(cur, chk, &dflags[S]);
+        if (r != BTAS_OK) return r;
+        std::vector<uint32_t> diag((size_t)n);
+        BTAS_CUDA(cudaMemcpy2DAsync(diag.data(), 4, chk, (size_t)(n + 1) * 4, 4, (size_t)n, cudaMemcpyDeviceToHost, st),
+                  "diagonal readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "check sync");
+        bool cycle = false;
+        for (uint32_t v : diag) {
+            if (dtype == BTAS_F32) {
+                float f;
+                memcpy(&f, &v, 4);
+                cycle |= semiring == BTAS_MINPLUS ? f < 0.f : f > 0.f;
+            } else {
+                const int x = static_cast<int>(v);
+                cycle |= semiring == BTAS_MINPLUS ? x < 0 : x > 0;
+            }
+        }
+        if (cycle)
+            return fail(BTAS_ERR_ARG, semiring == BTAS_MINPLUS ? "btas_closure: negative cycle, A* does not exist"
+                                                               : "btas_closure: positive cycle, A* does not exist");
+    }
+    BTAS_CUDA(cudaMemcpyAsync(Astar, cur, nn * 4, cudaMemcpyDeviceToDevice, st), "copy out");
+    if (squarings_done) *squarings_done = done;
     return BTAS_OK;
 }
 

@@ -35,6 +35,9 @@ cudaError_t launch_convert4(const void *src, long long lds, int rows, int cols, 
                             long long ldd, int mode, cudaStream_t st);
 // Fill a rows x cols matrix of 4-byte elements with `bits`.
 cudaError_t launch_fill4(void *dst, long long ldd, int rows, int cols, uint32_t bits, cudaStream_t st);
+// dst = E (+) src for an n x n matrix of 4-byte elements (diagonal (+) 0).
+cudaError_t launch_ident_oplus(const void *src, long long lds, int n, void *dst, long long ldd, int sr, int is_float,
+                               cudaStream_t st);
 // APSP domain scan of an n x n int32 matrix: out[0] = max finite weight,
 // out[1] = number of entries out of the domain (negative, > 2^28 and not INF,
 // or a non-zero diagonal).  out must be zeroed first.

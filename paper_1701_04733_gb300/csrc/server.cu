@@ -1,0 +1,589 @@
+// Continuous-batching request server for tropical products and APSP solves.
+//
+// Requests (a tropical product, or an APSP solve by repeated squaring,
+// Sec. III) arrive with HOST buffers at any time.  One executor thread owns
+// the device:
+//   admit   - in arrival order, while the device-memory footprint of the
+//             admitted requests stays within the budget: allocate the
+//             request's device block (stream-ordered) and copy its inputs in
+//             on a copy stream;
+//   step    - active requests contribute their next unit of work (a
+//             product: the whole product; APSP: its next squaring), oldest
+//             first, up to a work cap per step (default 3e10 terms, about
+//             2 ms; BTAS_SERVER_STEP_TERMS), and these units run together in
+//             ONE launch of the persistent tile-task kernel
+//             (batch_kernel.cuh); short steps let finished requests leave
+//             and new ones join often;
+//   retire  - a product is finished after its step; an APSP solve after its
+//             last squaring or as soon as a squaring changed nothing (early
+//             exit, same result).  Its result is copied back on the copy
+//             stream and its memory returned once the copy has completed.
+// Requests that arrive while a step runs are admitted for the next step, so
+// their work overlaps with the squarings of requests already in flight
+// (iteration-level continuous batching).  The arithmetic is the library's
+// single-call arithmetic: every result is bit-identical to the one computed
+// alone.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "batch_kernel.cuh"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace btas;
+
+namespace {
+
+size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
+long long r4(long long v) { return (v + 3) & ~3LL; }
+
+enum ReqState : int { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+
+struct Req {
+    int64_t id = 0;
+    int kind = 0;  // 0 APSP, 1 product
+    int sr = 0, dtype = 0;
+    int m = 0, n = 0, k = 0;
+    const void *hA = nullptr, *hB = nullptr;
+    void *hC = nullptr;
+    size_t bytes = 0;
+    char *dmem = nullptr;
+    // APSP: P[0], P[1] ping-pong (pitch ldp), Q[0], Q[1] transposes (pitch ldp), flags
+    // product: A (pitch lda_d), B (pitch ldb_d), Bt (pitch ldq), C (pitch ldc_d)
+    void *P[2] = {nullptr, nullptr}, *Q[2] = {nullptr, nullptr};
+    int *dflag = nullptr;
+    long long ldp = 0;
+    void *dA = nullptr, *dB = nullptr, *dBt = nullptr, *dC = nullptr;
+    long long lda_d = 0, ldb_d = 0, ldq = 0, ldc_d = 0;
+    int S = 0, s = 1;  // APSP squarings, next squaring (1-based)
+    int result_buf = 0;
+    cudaEvent_t in_ready = nullptr, out_ready = nullptr;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int state = kQueued;
+    int steps = 0;
+    bool finished = false;
+    // terms of this request's next unit of work
+    double unit_terms() const { return kind == 0 ? (double)n * n * n : (double)m * n * k; }
+};
+
+}  // namespace
+
+struct btas_server_t {
+    int device = 0;
+    long long budget = 0;
+    long long used = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Req *> queue;             // waiting for admission
+    std::vector<Req *> active;           // admitted, work remaining
+    std::vector<Req *> retiring;         // result copy in flight
+    std::map<int64_t, Req *> all;        // every request ever submitted
+    int64_t next_id = 1;
+    bool stop = false;
+    std::thread worker;
+    std::chrono::steady_clock::time_point t0;
+    cudaStream_t compute = nullptr, copy = nullptr;
+    // per-step device/pinned staging (double-buffered by step parity)
+    void *d_stage[2] = {nullptr, nullptr};
+    void *h_stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    int *h_flags = nullptr;  // pinned mailbox for change flags
+    int *d_flag_slots = nullptr;
+    int flag_slots = 0;
+    cudaEvent_t step_done[2] = {nullptr, nullptr};
+    int grid = 0;
+    long long timeout_cycles = 0;
+    int step_parity = 0;
+    double step_terms = 3e10;  // work cap of one step (terms), keeps steps short
+    int64_t steps = 0;
+    int64_t units = 0;
+    int64_t completed = 0;
+    int last_error = 0;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+btas_status sfail(btas_status s, const char *msg) {
+    record_error(msg);
+    return s;
+}
+
+int squarings_of(long long n) {
+    int s = 0;
+    long long reach = 1;
+    while (reach < n - 1) {
+        reach *= 2;
+        ++s;
+    }
+    return s;
+}
+
+size_t footprint(const Req &r) {
+    if (r.kind == 0) {
+        const long long ld = r4(r.n);
+        return 4 * a256((size_t)r.n * ld * 4) + a256((size_t)(r.S + 2) * 4);
+    }
+    return a256((size_t)r.m * r4(r.k) * 4) + a256((size_t)r.k * r4(r.n) * 4) + a256((size_t)r.n * r4(r.k) * 4) +
+           a256((size_t)r.m * r4(r.n) * 4);
+}
+
+// Allocate the request's device block and start its input copies.
+bool admit(btas_server_t *sv, Req *r) {
+    if (cudaMallocAsync(reinterpret_cast<void **>(&r->dmem), r->bytes, sv->compute) != cudaSuccess) return false;
+    // the copy stream must see the allocation
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, sv->compute);
+    cudaStreamWaitEvent(sv->copy, ev, 0);
+    cudaEventDestroy(ev);
+    char *p = r->dmem;
+    if (r->kind == 0) {
+        const long long ld = r4(r->n);
+        const size_t blk = a256((size_t)r->n * ld * 4);
+        r->ldp = ld;
+        r->P[0] = p;
+        r->P[1] = p + blk;
+        r->Q[0] = p + 2 * blk;
+        r->Q[1] = p + 3 * blk;
+        r->dflag = reinterpret_cast<int *>(p + 4 * blk);
+        cudaMemsetAsync(r->dflag, 0, (size_t)(r->S + 2) * 4, sv->copy);
+        cudaMemcpy2DAsync(r->P[0], ld * 4, r->hA, (size_t)r->n * 4, (size_t)r->n * 4, r->n, cudaMemcpyHostToDevice,
+                          sv->copy);
+    } else {
+        r->lda_d = r4(r->k);
+        r->ldb_d = r4(r->n);
+        r->ldq = r4(r->k);
+        r->ldc_d = r4(r->n);
+        r->dA = p;
+        p += a256((size_t)r->m * r->lda_d * 4);
+        r->dB = p;
+        p += a256((size_t)r->k * r->ldb_d * 4);
+        r->dBt = p;
+        p += a256((size_t)r->n * r->ldq * 4);
+        r->dC = p;
+        cudaMemcpy2DAsync(r->dA, r->lda_d * 4, r->hA, (size_t)r->k * 4, (size_t)r->k * 4, r->m,
+                          cudaMemcpyHostToDevice, sv->copy);
+        cudaMemcpy2DAsync(r->dB, r->ldb_d * 4, r->hB, (size_t)r->n * 4, (size_t)r->n * 4, r->k,
+                          cudaMemcpyHostToDevice, sv->copy);
+    }
+    cudaEventCreateWithFlags(&r->in_ready, cudaEventDisableTiming);
+    cudaEventRecord(r->in_ready, sv->copy);
+    return true;
+}
+
+void release(btas_server_t *sv, Req *r) {
+    if (r->dmem) cudaFreeAsync(r->dmem, sv->copy);
+    r->dmem = nullptr;
+    if (r->in_ready) cudaEventDestroy(r->in_ready);
+    if (r->out_ready) cudaEventDestroy(r->out_ready);
+    r->in_ready = r->out_ready = nullptr;
+}
+
+// Build and launch one step over the active requests.  Returns the number
+// of units launched.
+int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
+    // oldest admitted requests first, until the step's work cap (at least one)
+    units.clear();
+    double terms = 0;
+    for (Req *r : sv->active) {
+        const double w = r->unit_terms();
+        if (!units.empty() && terms + w > sv->step_terms) continue;
+        units.push_back(r);
+        terms += w;
+    }
+    if (units.empty()) return 0;
+    std::stable_sort(units.begin(), units.end(), [](const Req *a, const Req *b) {
+        const long long wa = (long long)a->m * a->n * a->k, wb = (long long)b->m * b->n * b->k;
+        return wa > wb;
+    });
+    const int ninst = (int)units.size();
+    std::vector<BInst> insts(ninst);
+    std::vector<int4> tasks;
+    for (int i = 0; i < ninst; ++i) {
+        Req *r = units[i];
+        cudaStreamWaitEvent(sv->compute, r->in_ready, 0);
+        BInst I{};
+        I.done_base = 2 * i;
+        I.flag_base = 2 * i;
+        I.levels = 1;
+        if (r->kind == 0) {
+            const int s = r->s;
+            I.kind = kInstSquare;
+            I.sr = kMin;
+            I.dtype = BTAS_I32;
+            I.m = I.n = I.k = r->n;
+            I.tiles_m = I.tiles_n = (r->n + kBT - 1) / kBT;
+            I.A = r->P[(s - 1) & 1];
+            I.lda = r->ldp;
+            I.C = r->P[s & 1];
+            I.ldc = r->ldp;
+            I.Q0 = r->Q[(s - 1) & 1];
+            I.Q1 = s < r->S ? r->Q[s & 1] : nullptr;
+            I.ldq = r->ldp;
+            I.changed_ptr = r->dflag + s;
+            if (s == 1) I.t0_rows = I.t0_cols = r->n;  // transpose W into Q[0] first
+        } else {
+            I.kind = kInstGemm;
+            I.sr = r->sr;
+            I.dtype = r->dtype;
+            I.m = r->m;
+            I.n = r->n;
+            I.k = r->k;
+            I.tiles_m = (r->m + kBT - 1) / kBT;
+            I.tiles_n = (r->n + kBT - 1) / kBT;
+            I.A = r->dA;
+            I.lda = r->lda_d;
+            I.B = r->dB;
+            I.ldb = r->ldb_d;
+            I.C = r->dC;
+            I.ldc = r->ldc_d;
+            I.Q0 = r->dBt;
+            I.ldq = r->ldq;
+            I.t0_rows = r->k;
+            I.t0_cols = r->n;
+        }
+        insts[i] = I;
+    }
+    for (int level = 0; level <= 1; ++level)
+        for (int i = 0; i < ninst; ++i) {
+            const BInst &I = insts[i];
+            if (level == 0) {
+                if (I.t0_rows > 0) {
+                    const int nt = ((I.t0_rows + kBT - 1) / kBT) * ((I.t0_cols + kBT - 1) / kBT);
+                    for (int t = 0; t < nt; ++t) tasks.push_back(make_int4(kTaskTranspose, i, 0, t));
+                }
+            } else {
+                const int type = I.kind == kInstSquare ? kTaskSquare : kTaskGemm;
+                for (int t = 0; t < I.tiles_m * I.tiles_n; ++t) tasks.push_back(make_int4(type, i, 1, t));
+            }
+        }
+    // staging: [counters (next, status, done[2*ninst], changed[2*ninst]) | insts | tasks]
+    const size_t cnt_bytes = a256((size_t)(2 + 4 * ninst) * 4);
+    const size_t inst_bytes = a256((size_t)ninst * sizeof(BInst));
+    const size_t task_bytes = a256(tasks.size() * sizeof(int4));
+    const size_t need = cnt_bytes + inst_bytes + task_bytes;
+    const int par = sv->step_parity;
+    // the staging buffer of this parity was used two steps ago: that step is done
+    cudaEventSynchronize(sv->step_done[par]);
+    if (need > sv->stage_bytes) {
+        for (int q = 0; q < 2; ++q) {
+            cudaEventSynchronize(sv->step_done[q]);
+            if (sv->d_stage[q]) cudaFree(sv->d_stage[q]);
+            if (sv->h_stage[q]) cudaFreeHost(sv->h_stage[q]);
+            sv->d_stage[q] = sv->h_stage[q] = nullptr;
+        }
+        sv->stage_bytes = std::max(need, sv->stage_bytes * 2);
+        for (int q = 0; q < 2; ++q) {
+            if (cudaMalloc(&sv->d_stage[q], sv->stage_bytes) != cudaSuccess ||
+                cudaMallocHost(&sv->h_stage[q], sv->stage_bytes) != cudaSuccess)
+                return -1;
+        }
+    }
+    char *h = static_cast<char *>(sv->h_stage[par]);
+    char *d = static_cast<char *>(sv->d_stage[par]);
+    memset(h, 0, cnt_bytes);
+    memcpy(h + cnt_bytes, insts.data(), (size_t)ninst * sizeof(BInst));
+    memcpy(h + cnt_bytes + inst_bytes, tasks.data(), tasks.size() * sizeof(int4));
+    cudaMemcpyAsync(d, h, need, cudaMemcpyHostToDevice, sv->compute);
+    BatchParams p{};
+    int *cnt = reinterpret_cast<int *>(d);
+    p.next = cnt;
+    p.status = cnt + 1;
+    p.done = cnt + 2;
+    p.changed = cnt + 2 + 2 * ninst;
+    p.insts = reinterpret_cast<const BInst *>(d + cnt_bytes);
+    p.tasks = reinterpret_cast<const int4 *>(d + cnt_bytes + inst_bytes);
+    p.total = (int)tasks.size();
+    p.timeout_cycles = sv->timeout_cycles;
+    p.withhold_inst = -1;
+    const int grid = std::max(1, std::min(sv->grid, p.total));
+    if (launch_batch_kernel(p, grid, sv->compute) != cudaSuccess) return -1;
+    // change flags of this step's squarings -> pinned mailbox
+    for (int i = 0; i < ninst; ++i)
+        if (units[i]->kind == 0)
+            cudaMemcpyAsync(sv->h_flags + i, units[i]->dflag + units[i]->s, 4, cudaMemcpyDeviceToHost, sv->compute);
+    cudaMemcpyAsync(sv->h_flags + sv->flag_slots, p.status, 4, cudaMemcpyDeviceToHost, sv->compute);
+    cudaEventRecord(sv->step_done[par], sv->compute);
+    sv->step_parity ^= 1;
+    ++sv->steps;
+    sv->units += ninst;
+    return ninst;
+}
+
+void start_retire(btas_server_t *sv, Req *r) {
+    if (r->kind == 0) {
+        cudaMemcpy2DAsync(r->hC, (size_t)r->n * 4, r->P[r->result_buf], r->ldp * 4, (size_t)r->n * 4, r->n,
+                          cudaMemcpyDeviceToHost, sv->copy);
+    } else {
+        cudaMemcpy2DAsync(r->hC, (size_t)r->n * 4, r->dC, r->ldc_d * 4, (size_t)r->n * 4, r->m,
+                          cudaMemcpyDeviceToHost, sv->copy);
+    }
+    cudaEventCreateWithFlags(&r->out_ready, cudaEventDisableTiming);
+    cudaEventRecord(r->out_ready, sv->copy);
+    sv->retiring.push_back(r);
+}
+
+void poll_retiring(btas_server_t *sv, bool block) {
+    std::vector<Req *> keep;
+    for (Req *r : sv->retiring) {
+        const cudaError_t q = block ? cudaEventSynchronize(r->out_ready) : cudaEventQuery(r->out_ready);
+        if (q == cudaSuccess) {
+            const double t = sv->now();
+            release(sv, r);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r->t_done = t;
+            r->state = kDone;
+            sv->used -= (long long)r->bytes;
+            ++sv->completed;
+        } else {
+            keep.push_back(r);
+        }
+    }
+    sv->retiring.swap(keep);
+    sv->cv.notify_all();
+}
+
+void worker_loop(btas_server_t *sv) {
+    cudaSetDevice(sv->device);
+    std::vector<Req *> units;
+    for (;;) {
+        // admission (FIFO within the budget)
+        std::vector<Req *> admitted;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            if (sv->queue.empty() && sv->active.empty() && sv->retiring.empty()) {
+                if (sv->stop) break;
+                sv->cv.wait_for(lk, std::chrono::milliseconds(2));
+            }
+            while (!sv->queue.empty() && sv->used + (long long)sv->queue.front()->bytes <= sv->budget) {
+                Req *r = sv->queue.front();
+                sv->queue.pop_front();
+                sv->used += (long long)r->bytes;
+                admitted.push_back(r);
+            }
+        }
+        for (Req *r : admitted) {
+            const double t = sv->now();
+            const bool ok = admit(sv, r);
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                r->t_admit = t;
+                if (!ok) {
+                    r->state = kFailed;
+                    sv->used -= (long long)r->bytes;
+                } else {
+                    r->state = kRunning;
+                }
+            }
+            if (ok) sv->active.push_back(r);
+        }
+        const int launched = launch_step(sv, units);
+        poll_retiring(sv, false);
+        if (launched < 0) {
+            sv->last_error = BTAS_ERR_CUDA;
+            break;
+        }
+        if (launched == 0) {
+            if (!sv->retiring.empty()) std::this_thread::sleep_for(std::chrono::microseconds(50));
+            continue;
+        }
+        // wait for the step, then advance every unit
+        cudaEventSynchronize(sv->step_done[sv->step_parity ^ 1]);
+        if (sv->h_flags[sv->flag_slots] != 0) sv->last_error = sv->h_flags[sv->flag_slots];
+        for (int i = 0; i < (int)units.size(); ++i) {
+            Req *r = units[i];
+            ++r->steps;
+            bool finished = true;
+            if (r->kind == 0) {
+                const bool changed = sv->h_flags[i] != 0;
+                r->result_buf = r->s & 1;
+                finished = !changed || r->s >= r->S;
+                ++r->s;
+            }
+            if (finished) {
+                r->finished = true;
+                start_retire(sv, r);
+            }
+        }
+        // keep admission order for the requests with work left
+        std::vector<Req *> still;
+        for (Req *r : sv->active)
+            if (!r->finished) still.push_back(r);
+        sv->active.swap(still);
+    }
+    poll_retiring(sv, true);
+}
+
+}  // namespace
+
+extern "C" {
+
+btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, int flags) {
+    if (!out || hbm_budget_bytes <= 0) return sfail(BTAS_ERR_ARG, "btas_server_create: bad arguments");
+    if (flags != 0) return sfail(BTAS_ERR_ARG, "btas_server_create: unknown flags");
+    btas_server_t *sv = new btas_server_t();
+    sv->budget = hbm_budget_bytes;
+    sv->t0 = std::chrono::steady_clock::now();
+    cudaGetDevice(&sv->device);
+    int per_sm = 0, sms = 0;
+    if (batch_kernel_prepare(&per_sm) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->compute, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->copy, cudaStreamNonBlocking) != cudaSuccess) {
+        delete sv;
+        return sfail(BTAS_ERR_CUDA, "btas_server_create: CUDA set-up failed");
+    }
+    sv->grid = std::max(1, per_sm * sms);
+    if (const char *e = getenv("BTAS_SERVER_STEP_TERMS")) sv->step_terms = atof(e) > 0 ? atof(e) : sv->step_terms;
+    sv->timeout_cycles = batch_timeout_cycles(sv->device);
+    sv->flag_slots = 1 << 16;
+    if (cudaMallocHost(reinterpret_cast<void **>(&sv->h_flags), (size_t)(sv->flag_slots + 1) * 4) != cudaSuccess) {
+        delete sv;
+        return sfail(BTAS_ERR_NOMEM, "btas_server_create: pinned mailbox");
+    }
+    for (int q = 0; q < 2; ++q) {
+        cudaEventCreateWithFlags(&sv->step_done[q], cudaEventDisableTiming);
+        cudaEventRecord(sv->step_done[q], sv->compute);
+    }
+    sv->worker = std::thread(worker_loop, sv);
+    *out = sv;
+    return BTAS_OK;
+}
+
+static btas_status enqueue(btas_server_t *sv, Req *r, int64_t *ticket) {
+    r->bytes = footprint(*r);
+    if ((long long)r->bytes > sv->budget) {
+        delete r;
+        return sfail(BTAS_ERR_BUDGET, "btas_server: request larger than the device-memory budget");
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) {
+        delete r;
+        return sfail(BTAS_ERR_ARG, "btas_server: server is stopping");
+    }
+    if ((int64_t)sv->active.size() + (int64_t)sv->queue.size() >= sv->flag_slots) {
+        delete r;
+        return sfail(BTAS_ERR_BUDGET, "btas_server: too many requests in flight");
+    }
+    r->id = sv->next_id++;
+    r->t_submit = sv->now();
+    sv->queue.push_back(r);
+    sv->all[r->id] = r;
+    if (ticket) *ticket = r->id;
+    sv->cv.notify_all();
+    return BTAS_OK;
+}
+
+btas_status btas_server_submit_apsp(btas_server_t *sv, int64_t n, const int32_t *W, int32_t *D, int64_t *ticket) {
+    if (!sv || !W || !D || n < 1 || n > 46340) return sfail(BTAS_ERR_ARG, "btas_server_submit_apsp: bad arguments");
+    Req *r = new Req();
+    r->kind = 0;
+    r->m = r->n = r->k = (int)n;
+    r->S = squarings_of(n);
+    if (r->S == 0) r->S = 1;  // n <= 2: one squaring leaves W unchanged (zero diagonal)
+    r->hA = W;
+    r->hC = D;
+    return enqueue(sv, r, ticket);
+}
+
+btas_status btas_server_submit_gemm(btas_server_t *sv, int semiring, int dtype, int64_t m, int64_t n, int64_t k,
+                                    const void *A, const void *B, void *C, int64_t *ticket) {
+    if (!sv || !A || !B || !C || m < 1 || n < 1 || k < 1 || m > INT32_MAX || n > INT32_MAX || k > INT32_MAX)
+        return sfail(BTAS_ERR_ARG, "btas_server_submit_gemm: bad arguments");
+    if (semiring != BTAS_MINPLUS && semiring != BTAS_MAXPLUS) return sfail(BTAS_ERR_ARG, "semiring");
+    if (dtype != BTAS_I32 && dtype != BTAS_F32) return sfail(BTAS_ERR_UNSUPPORTED, "dtype");
+    Req *r = new Req();
+    r->kind = 1;
+    r->sr = semiring;
+    r->dtype = dtype;
+    r->m = (int)m;
+    r->n = (int)n;
+    r->k = (int)k;
+    r->hA = A;
+    r->hB = B;
+    r->hC = C;
+    return enqueue(sv, r, ticket);
+}
+
+btas_status btas_server_poll(btas_server_t *sv, int64_t ticket, int *state, double *t_submit, double *t_admit,
+                             double *t_done) {
+    if (!sv) return sfail(BTAS_ERR_ARG, "btas_server_poll: NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return sfail(BTAS_ERR_ARG, "btas_server_poll: unknown ticket");
+    const Req *r = it->second;
+    if (state) *state = r->state;
+    if (t_submit) *t_submit = r->t_submit;
+    if (t_admit) *t_admit = r->t_admit;
+    if (t_done) *t_done = r->t_done;
+    return BTAS_OK;
+}
+
+btas_status btas_server_wait_all(btas_server_t *sv, double timeout_s) {
+    if (!sv) return sfail(BTAS_ERR_ARG, "btas_server_wait_all: NULL server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    for (;;) {
+        bool busy = !sv->queue.empty();
+        for (auto &kv : sv->all)
+            if (kv.second->state == kQueued || kv.second->state == kRunning) busy = true;
+        if (!busy) break;
+        if (sv->last_error) return sfail(static_cast<btas_status>(sv->last_error), "btas_server: device error");
+        if (sv->cv.wait_until(lk, deadline) == std::cv_status::timeout)
+            return sfail(BTAS_ERR_TIMEOUT, "btas_server_wait_all: timed out");
+    }
+    if (sv->last_error) return sfail(static_cast<btas_status>(sv->last_error), "btas_server: device error");
+    return BTAS_OK;
+}
+
+btas_status btas_server_stats(btas_server_t *sv, int64_t *steps, int64_t *units, int64_t *completed,
+                              int64_t *bytes_in_use) {
+    if (!sv) return sfail(BTAS_ERR_ARG, "btas_server_stats: NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (steps) *steps = sv->steps;
+    if (units) *units = sv->units;
+    if (completed) *completed = sv->completed;
+    if (bytes_in_use) *bytes_in_use = sv->used;
+    return BTAS_OK;
+}
+
+btas_status btas_server_destroy(btas_server_t *sv) {
+    if (!sv) return BTAS_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaStreamSynchronize(sv->compute);
+    cudaStreamSynchronize(sv->copy);
+    for (auto &kv : sv->all) {
+        release(sv, kv.second);
+        delete kv.second;
+    }
+    for (int q = 0; q < 2; ++q) {
+        if (sv->d_stage[q]) cudaFree(sv->d_stage[q]);
+        if (sv->h_stage[q]) cudaFreeHost(sv->h_stage[q]);
+        if (sv->step_done[q]) cudaEventDestroy(sv->step_done[q]);
+    }
+    if (sv->h_flags) cudaFreeHost(sv->h_flags);
+    cudaStreamSynchronize(sv->copy);
+    cudaStreamDestroy(sv->compute);
+    cudaStreamDestroy(sv->copy);
+    delete sv;
+    return BTAS_OK;
+}
+
+}  // extern "C"

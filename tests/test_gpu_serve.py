@@ -1,0 +1,105 @@
+"""Continuous-batching server: requests of mixed kinds and sizes arrive
+while others run; every result equals the same request computed alone
+(single library call) and, for sampled requests, the oracle.  Admission
+respects the device-memory budget."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import gen
+from gpu_util import bits, dev, f32_matrix, host, int_matrix
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def btas():
+    import torch
+    import paper_1701_04733_gb300 as b
+    assert torch.cuda.is_available()
+    b.lib()
+    return b
+
+
+def _requests(count, seed):
+    import torch
+    sizes = gen.loguniform_sizes(seed, 1, count, 16, 700)
+    kinds = gen.uniform_int(seed, 2, (count,), 0, 3)  # 0,1: APSP, 2: int32 product, 3: fp32 product
+    reqs = []
+    for i, (n, kd) in enumerate(zip(sizes, kinds)):
+        n = int(n)
+        if kd <= 1:
+            W = gen.random_graph(seed + 10 + i, i, n, 0.1 if n > 10 else 0.5, 1, 100)
+            reqs.append(("apsp", torch.from_numpy(W).pin_memory(), torch.empty((n, n), dtype=torch.int32).pin_memory()))
+        else:
+            sr = i % 2
+            mk = int_matrix if kd == 2 else f32_matrix
+            A = mk(seed + 100 + i, (n, max(1, n // 2 + 3)), sr)
+            B = mk(seed + 200 + i, (A.shape[1], max(1, n - 5)), sr)
+            C = torch.empty((n, B.shape[1]), dtype=torch.int32 if kd == 2 else torch.float32).pin_memory()
+            reqs.append(("gemm", torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(), C, sr))
+    return reqs
+
+
+def _alone(btas, r):
+    if r[0] == "apsp":
+        return host(btas.apsp(r[1].cuda()))
+    return host(btas.gemm(r[1].cuda(), r[2].cuda(), r[4]))
+
+
+def test_mixed_arrivals_match_single_calls(btas, oracle_mod):
+    reqs = _requests(40, 7)
+    srv = btas.Server(40 << 30)
+    tickets = []
+
+    def producer():
+        for i, r in enumerate(reqs):
+            if r[0] == "apsp":
+                tickets.append(srv.submit_apsp(r[1], r[2]))
+            else:
+                tickets.append(srv.submit_gemm(r[1], r[2], r[3], r[4]))
+            time.sleep(0.0005 * (i % 3))
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    srv.wait_all(120)
+    for t in tickets:
+        st = srv.poll(t)
+        assert st["state"] == 2 and st["t_done"] >= st["t_admit"] >= st["t_submit"]
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs) and stats["bytes_in_use"] == 0
+    srv.close()
+    for i, r in enumerate(reqs):
+        out = (r[2] if r[0] == "apsp" else r[3]).numpy()
+        np.testing.assert_array_equal(bits(out), bits(_alone(btas, r)), err_msg=f"request {i} {r[0]}")
+        if i % 7 == 0:
+            if r[0] == "apsp":
+                np.testing.assert_array_equal(out, oracle_mod.floyd_warshall(r[1].numpy()))
+            else:
+                np.testing.assert_array_equal(bits(out), bits(oracle_mod.tgemm(r[4], r[1].numpy(), r[2].numpy())))
+
+
+def test_small_budget_queues_and_rejects(btas):
+    import paper_1701_04733_gb300 as b_mod
+    import torch
+    reqs = _requests(12, 11)
+    # about two of the larger requests fit at a time
+    srv = btas.Server(16 << 20)
+    tickets = []
+    for r in reqs:
+        if r[0] == "apsp":
+            tickets.append(srv.submit_apsp(r[1], r[2]))
+        else:
+            tickets.append(srv.submit_gemm(r[1], r[2], r[3], r[4]))
+    srv.wait_all(120)
+    for r in reqs:
+        out = (r[2] if r[0] == "apsp" else r[3]).numpy()
+        np.testing.assert_array_equal(bits(out), bits(_alone(btas, r)))
+    big = torch.zeros((2048, 2048), dtype=torch.int32)
+    with pytest.raises(b_mod.BtasError) as ei:
+        srv.submit_apsp(big, big.clone())
+    assert ei.value.status == 6
+    srv.close()

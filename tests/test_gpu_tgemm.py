@@ -13,11 +13,11 @@ from gpu_util import INF, NINF, bits, dev, f32_matrix, host, int_matrix
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(1, 1, 1), (3, 5, 2), (31, 33, 17), (64, 64, 64), (129, 127, 33), (200, 300, 129),
+SHAPES = [(1, 1, 1), (3, 5, 2), (31, 33, 17), (64, 64, 64), (129, 127, 33), (200, 300, 129), (300, 260, 70),
           (257, 513, 100), (130, 70, 1000)]
-I32_VARIANTS = [{"BTAS_I32_VARIANT": "0"}, {"BTAS_I32_VARIANT": "1", "BTAS_I32_NS": "4"},
+I32_VARIANTS = [{"BTAS_I32_VARIANT": "0"}, {"BTAS_I32_VARIANT": "1", "BTAS_I32_NS": "4"}, {"BTAS_I32_VARIANT": "1", "BTAS_I32_NS": "8"},
                 {"BTAS_I32_VARIANT": "1", "BTAS_I32_NS": "5"}, {"BTAS_I32_VARIANT": "1", "BTAS_I32_NS": "6"}]
-F32_VARIANTS = [{"BTAS_F32_VARIANT": "2"}, {"BTAS_F32_VARIANT": "3"}]
+F32_VARIANTS = [{"BTAS_F32_VARIANT": "2"}, {"BTAS_F32_VARIANT": "3"}, {"BTAS_F32_VARIANT": "4"}]
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +51,7 @@ def _inputs(dt, sr, m, n, k, seed):
     return f32_matrix(seed, (m, k), sr), f32_matrix(seed + 1, (k, n), sr)
 
 
-@pytest.mark.parametrize("cfg", ["0", "2"])
+@pytest.mark.parametrize("cfg", ["0", "2", "4"])
 @pytest.mark.parametrize("sr", [0, 1])
 @pytest.mark.parametrize("dt", ["i32", "f32"])
 def test_shapes_all_variants(btas, oracle_mod, dt, sr, cfg):

@@ -151,3 +151,39 @@ def test_chain_needs_all_squarings(oracle_mod):
     assert oracle_mod.apsp_squaring(W, S - 1)[0, n - 1] == INF
     for i, j in itertools.product(range(n), range(n)):
         assert D[i, j] == (j - i if j >= i else INF)
+
+
+def _walk(W, Nx, i, j):
+    """Follow the next-hop matrix from i to j; returns the walk's weight."""
+    total, v, steps = 0, i, 0
+    while v != j:
+        u = int(Nx[v, j])
+        assert u >= 0 and W[v, u] != INF, (i, j, v, u)
+        total += int(W[v, u])
+        v = u
+        steps += 1
+        assert steps <= W.shape[0], "next-hop walk does not terminate"
+    return total
+
+
+def test_paths_hand_worked(oracle_mod):
+    g = load("apsp_paths_5node.txt")
+    W, D, N = as_i32(g["W"]), as_i32(g["D"]), as_i32(g["N"])
+    d, nx = oracle_mod.apsp_paths(W)
+    np.testing.assert_array_equal(d, D)
+    np.testing.assert_array_equal(nx, N)
+    np.testing.assert_array_equal(d, oracle_mod.floyd_warshall(W))
+
+
+@pytest.mark.parametrize("n", [3, 8, 40, 100])
+def test_paths_are_valid_shortest_walks(oracle_mod, n):
+    """Following Next from i reaches j with total weight D[i][j] (positive
+    weights), Next is -1 exactly where D is INF, and D equals Floyd-Warshall."""
+    W = gen.random_graph(11, n, n, 0.15 if n > 8 else 0.5, 1, 30)
+    D, Nx = oracle_mod.apsp_paths(W)
+    np.testing.assert_array_equal(D, oracle_mod.floyd_warshall(W))
+    assert ((Nx == -1) == (D == INF)).all()
+    for i in range(n):
+        for j in range(n):
+            if D[i, j] != INF:
+                assert _walk(W, Nx, i, j) == D[i, j]
