@@ -14,6 +14,8 @@ What each function computes, and the passage it follows:
   floyd_warshall(W)           Algorithm 2 with an INF sentinel
   apsp_paths(W)               squaring with next-hop matrix (smallest minimising k)
   dijkstra_rows(W, srcs)      textbook single-source shortest paths
+  gemv(sr, A, x, trans)       tropical matrix-vector product (level 2)
+  sssp(W, src)                Bellman-Ford as repeated min-plus vector-matrix products
   bruteforce_apsp(W)          minimum over all simple paths (n <= 8)
   dot / axpy / add / mul      tropical vector operations (abstract, Sec. III)
 
@@ -78,6 +80,9 @@ def _load():
             "oracle_apsp_paths_i32": (None, [i64, vp, vp, vp, i32]),
             "oracle_dijkstra_rows_i32": (None, [i64, vp, i64, vp, vp]),
             "oracle_bruteforce_apsp_i32": (i32, [i64, vp, vp]),
+            "oracle_gemv_i32": (None, [i32, i32, i32, i64, i64, vp, i64, vp, vp]),
+            "oracle_gemv_f32": (None, [i32, i32, i32, i64, i64, vp, i64, vp, vp]),
+            "oracle_sssp_i32": (i32, [i64, vp, i64, vp]),
             "oracle_dot_i32": (ctypes.c_int32, [i32, i64, vp, i64, vp, i64]),
             "oracle_dot_f32": (ctypes.c_float, [i32, i64, vp, i64, vp, i64]),
             "oracle_axpy_i32": (None, [i32, i64, ctypes.c_int32, vp, i64, vp, i64]),
@@ -194,6 +199,28 @@ def bruteforce_apsp(W: np.ndarray) -> np.ndarray:
     if rc != 0:
         raise ValueError("brute force is limited to n <= 8")
     return D
+
+
+def gemv(sr: int, A: np.ndarray, x: np.ndarray, trans: bool = False, y: np.ndarray | None = None):
+    """trans=False: y_i = (+)_j A[i,j] (.) x_j; trans=True: y_j = (+)_i x_i (.) A[i,j]."""
+    dt = np.int32 if np.asarray(A).dtype.kind in "iu" else np.float32
+    A = _c(A, dt)
+    x = _c(x, dt)
+    m, n = A.shape
+    acc = y is not None
+    out = _c(y, dt).copy() if acc else np.empty(n if trans else m, dtype=dt)
+    f = _load().oracle_gemv_i32 if dt == np.int32 else _load().oracle_gemv_f32
+    f(sr, int(trans), int(acc), m, n, _p(A), max(n, 1), _p(x), _p(out))
+    return out
+
+
+def sssp(W: np.ndarray, src: int):
+    """Bellman-Ford by repeated min-plus vector-matrix products: (dist, changed steps)."""
+    W = _c(W, np.int32)
+    n = W.shape[0]
+    d = np.empty(n, dtype=np.int32)
+    steps = _load().oracle_sssp_i32(n, _p(W), int(src), _p(d))
+    return d, int(steps)
 
 
 def dot(sr: int, x: np.ndarray, y: np.ndarray, incx: int = 1, incy: int = 1, n: int | None = None):

@@ -282,6 +282,60 @@ int oracle_bruteforce_apsp_i32(int64_t n, const int32_t *W, int32_t *D) {
     return 0;
 }
 
+/* ---------- level 2: tropical matrix-vector products ----------
+ * trans == 0: y[i] = (+)_j A[i][j] (.) x[j]   (i < m, j < n)
+ * trans == 1: y[j] = (+)_i x[i] (.) A[i][j]   (j < n, i < m)
+ * accumulate: the old y entry enters the (+). */
+void oracle_gemv_i32(int sr, int trans, int accumulate, int64_t m, int64_t n, const int32_t *A, int64_t lda,
+                     const int32_t *x, int32_t *y) {
+    int32_t ident = (sr == O_MINPLUS) ? O_INF32 : O_NINF32;
+    int64_t outer = trans ? n : m, inner = trans ? m : n;
+    for (int64_t o = 0; o < outer; ++o) {
+        int32_t acc = accumulate ? y[o] : ident;
+        for (int64_t q = 0; q < inner; ++q) {
+            int32_t a = trans ? A[q * lda + o] : A[o * lda + q];
+            acc = oplus_i32(sr, acc, otimes_i32(sr, trans ? x[q] : x[q], a));
+        }
+        y[o] = acc;
+    }
+}
+
+void oracle_gemv_f32(int sr, int trans, int accumulate, int64_t m, int64_t n, const float *A, int64_t lda,
+                     const float *x, float *y) {
+    float ident = (sr == O_MINPLUS) ? INFINITY : -INFINITY;
+    int64_t outer = trans ? n : m, inner = trans ? m : n;
+    for (int64_t o = 0; o < outer; ++o) {
+        float acc = accumulate ? y[o] : ident;
+        for (int64_t q = 0; q < inner; ++q) {
+            float a = trans ? A[q * lda + o] : A[o * lda + q];
+            acc = oplus_f32(sr, acc, otimes_f32(x[q], a));
+        }
+        y[o] = acc;
+    }
+}
+
+/* Single-source shortest paths by repeated vector-matrix products
+ * (Bellman-Ford in min-plus form): d_0 = e_src (0 at src, INF elsewhere),
+ * d_{t+1} = d_t (x) W (row vector times matrix; W[j][j] = 0 keeps d_t[j]),
+ * until d stops changing, at most n-1 products.  Returns the number of
+ * products that changed d. */
+int oracle_sssp_i32(int64_t n, const int32_t *W, int64_t src, int32_t *dist) {
+    int32_t *nxt = (int32_t *)malloc((size_t)(n ? n : 1) * 4);
+    for (int64_t v = 0; v < n; ++v) dist[v] = O_INF32;
+    dist[src] = 0;
+    int changed_steps = 0;
+    for (int64_t t = 0; t + 1 < n; ++t) {
+        oracle_gemv_i32(O_MINPLUS, 1, 0, n, n, W, n, dist, nxt);
+        int changed = 0;
+        for (int64_t v = 0; v < n; ++v) changed |= nxt[v] != dist[v];
+        memcpy(dist, nxt, (size_t)n * 4);
+        if (!changed) break;
+        ++changed_steps;
+    }
+    free(nxt);
+    return changed_steps;
+}
+
 /* ---------- tropical vector operations ("standard vector operations", Abstract / Sec. III) ---------- */
 
 /* dot: (+)_i x_i (.) y_i */

@@ -71,3 +71,35 @@ def test_add_is_commutative_idempotent(oracle_mod):
     for sr in (0, 1):
         np.testing.assert_array_equal(oracle_mod.add(sr, x, y), oracle_mod.add(sr, y, x))
         np.testing.assert_array_equal(oracle_mod.add(sr, x, x), x)
+
+
+def test_gemv_hand_worked(oracle_mod):
+    A = np.array([[1, 5, INF], [0, 2, 3]], np.int32)
+    x = np.array([4, 1, 0], np.int32)
+    # y0 = min(1+4, 5+1, INF+0) = 5 ; y1 = min(0+4, 2+1, 3+0) = 3
+    np.testing.assert_array_equal(oracle_mod.gemv(0, A, x), [5, 3])
+    # trans: y_j = min_i x_i + A[i][j] with x = (2, 1)
+    xt = np.array([2, 1], np.int32)
+    # y0 = min(2+1, 1+0) = 1 ; y1 = min(2+5, 1+2) = 3 ; y2 = min(2+INF, 1+3) = 4
+    np.testing.assert_array_equal(oracle_mod.gemv(0, A, xt, trans=True), [1, 3, 4])
+    # max-plus: y0 = max(1+4, 5+1) = 6 (the INF entry is a large finite here, so use a finite matrix)
+    Af = np.array([[1, 5], [0, 2]], np.int32)
+    np.testing.assert_array_equal(oracle_mod.gemv(1, Af, np.array([4, 1], np.int32)), [6, 4])
+
+
+def test_gemv_is_one_column_product(oracle_mod):
+    A = gen.uniform_f32(7, 1, (33, 21))
+    x = gen.uniform_f32(8, 1, (21,))
+    for sr in (0, 1):
+        np.testing.assert_array_equal(oracle_mod.gemv(sr, A, x), oracle_mod.tgemm(sr, A, x[:, None])[:, 0])
+        xt = gen.uniform_f32(9, 1, (33,))
+        np.testing.assert_array_equal(oracle_mod.gemv(sr, A, xt, trans=True), oracle_mod.tgemm(sr, xt[None, :], A)[0])
+
+
+def test_sssp_equals_dijkstra(oracle_mod):
+    for n in (1, 2, 7, 50, 200):
+        W = gen.random_graph(12, n, n, 0.05 if n > 10 else 0.4, 1, 50)
+        for src in {0, n // 2, n - 1}:
+            d, steps = oracle_mod.sssp(W, src)
+            np.testing.assert_array_equal(d, oracle_mod.dijkstra_rows(W, [src])[0])
+            assert 0 <= steps <= max(0, n - 1)
