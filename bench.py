@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-requests", type=int, default=300)
     p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
-    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve"],
+    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next"],
                    help="profiling aids: run one part alone and print its JSON (not a bench line)")
     return p.parse_args()
 
@@ -579,6 +579,59 @@ def e2e(args, inp, btas, torch, units_per_step):
             "d2h_bytes_per_step": bo, "steps": steps}
 
 
+def next_rows(args, btas, torch):
+    """The follow-on routines at the n = 8192 graph: tropical gemv (HBM
+    roofline), Bellman-Ford SSSP by repeated vector-matrix products, blocked
+    Floyd-Warshall vs squaring, APSP with next-hop matrix, FP32 closure."""
+    import gen
+    n = args.n
+    s = gen.BASE_SEED
+    W = torch.from_numpy(gen.random_graph(s, 2, n, 0.01, 1, 1000)).cuda()
+    A = torch.from_numpy(gen.uniform_int(s, 21, (n, n), 0, 10 ** 6)).cuda()
+    x = torch.from_numpy(gen.uniform_int(s, 27, (n,), 0, 10 ** 6)).cuda()
+    hbm = peaks().get("hbm_gbs") or 6800.0
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        return best
+    out = {"n": n, "hbm_peak_gbs_measured": hbm}
+    y = torch.empty(n, dtype=torch.int32, device="cuda")
+    for trans in (False, True):
+        t = timed(lambda: btas.gemv(A, x, 0, trans=trans, out=y), reps=10)
+        gbs = (n * n * 4 + 2 * n * 4) / t / 1e9
+        out[f"gemv_{'trans' if trans else 'rows'}"] = {"ms": round(t * 1e3, 4), "GB_s": round(gbs, 1),
+                                                        "frac_of_hbm": round(gbs / hbm, 3)}
+    d, info = btas.sssp(W, 0, info=True)
+    t = timed(lambda: btas.sssp(W, 0))
+    out["sssp"] = {"ms": round(t * 1e3, 3), "products": info["iterations"] + 1,
+                   "GB_s_per_product": round((info["iterations"] + 1) * n * n * 4 / t / 1e9, 1)}
+    t_fw = timed(lambda: btas.apsp_fw(W), reps=2)
+    t_sq = timed(lambda: btas.apsp(W), reps=2)
+    t_i32 = timed(lambda: btas.apsp(W, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32), reps=2)
+    out["apsp_blocked_fw"] = {"ms": round(t_fw * 1e3, 3), "terms_tops": round(float(n) ** 3 / t_fw / 1e12, 2)}
+    out["apsp_squaring_auto_ms"] = round(t_sq * 1e3, 3)
+    out["apsp_squaring_int32_ms"] = round(t_i32 * 1e3, 3)
+    np_ = min(n, 4096)
+    Wp = W[:np_, :np_].contiguous()
+    t_p = timed(lambda: btas.apsp_paths(Wp), reps=1)
+    out["apsp_paths"] = {"n": np_, "ms": round(t_p * 1e3, 3)}
+    Wf = torch.where(W[:np_, :np_] == btas.INF_I32, torch.tensor(float("inf"), device="cuda"),
+                     W[:np_, :np_].float()).contiguous()
+    t_c = timed(lambda: btas.closure(Wf, "min"), reps=1)
+    out["closure_fp32_minplus"] = {"n": np_, "ms": round(t_c * 1e3, 3)}
+    return out
+
+
 def run_only(args):
     """One part alone, for profiling: `kernels` runs one product of each
     kernel family at size --n (B supplied transposed; the packed 16-bit
@@ -612,6 +665,8 @@ def run_only(args):
         print(json.dumps({"only": "kernels", "n": n, "ms": t}))
     elif args.only == "batched":
         print(json.dumps({"only": "batched", **batched(args, btas, torch)}))
+    elif args.only == "next":
+        print(json.dumps({"only": "next", **next_rows(args, btas, torch)}))
     else:
         print(json.dumps({"only": "serve", **serve(args, btas, torch)}))
     return 0

@@ -127,6 +127,28 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k,
                       void *C, int64_t ldc, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Level 2: tropical matrix-vector product (the "standard vector and matrix
+ * operations" of the abstract / Sec. III between levels 1 and 3).
+ *   trans == 0: y[i] = (+)_j A[i][j] (.) x[j]    x: n, y: m
+ *   trans == 1: y[j] = (+)_i x[i] (.) A[i][j]    x: m, y: n  (y = x^T A)
+ * semiring may carry BTAS_GEMM_ACCUMULATE (y (+)= ...).  A: m x n device,
+ * row-major, lda >= max(1, n); x, y contiguous device vectors.  dtype
+ * BTAS_I32 or BTAS_F32.  An empty reduction writes the (+)-identity.
+ * HBM-bound: A is streamed once.  Results are exact (order-independent).
+ * ------------------------------------------------------------------------ */
+btas_status btas_gemv(int semiring, int dtype, int trans, int64_t m, int64_t n, const void *A, int64_t lda,
+                      const void *x, void *y, void *stream);
+
+/* btas_sssp: single-source shortest paths from `src` by repeated min-plus
+ * vector-matrix products d_{t+1} = d_t (x) W (Bellman-Ford; W[j][j] = 0
+ * keeps d_t[j]) until d stops changing, at most n-1 products.  W: n x n int32
+ * device matrix (domain as btas_apsp, checked); dist: n int32 device vector
+ * (INF = unreachable) = row `src` of btas_apsp's result.  iterations: HOST
+ * pointer or NULL, receives the number of products that changed d.
+ * Synchronises `stream` once per product. */
+btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, int *iterations, void *stream);
+
+/* ------------------------------------------------------------------------
  * Level 1: tropical vector operations ("standard vector operations",
  * abstract and Sec. III).  Strides may be negative only where stated; here
  * they must be >= 1.
@@ -235,6 +257,32 @@ btas_status btas_apsp_u16(int64_t n, const uint16_t *W, uint16_t *D, int max_w, 
  * every walk weight must stay in [-2^28, 2^28]. */
 btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void *Astar, int flags,
                          int *squarings_done, void *stream);
+
+/* btas_apsp_paths: APSP by repeated squaring (Sec. III) with path
+ * reconstruction.  D receives the distances (as btas_apsp) and Next the
+ * next-hop matrix: Next[i][j] = the vertex after i on a shortest path from i
+ * to j, Next[i][i] = i, -1 if j is unreachable.  Ties are broken by one fixed
+ * rule, so Next is reproducible: each squaring
+ * D'[i][j] = min_k D[i][k] + D[k][j] takes the SMALLEST minimising k = k*,
+ * and Next'[i][j] = Next[i][j] if k* == i, else Next[i][k*].  With positive
+ * weights, following Next from i reaches j with total weight D[i][j].
+ * W, D, Next: n x n int32 device matrices, leading dimension n (W must not
+ * overlap D or Next).  Domain as btas_apsp (checked: BTAS_ERR_ARG).
+ * flags: BTAS_APSP_EARLY_EXIT stops once a squaring changes neither D nor
+ * Next (same result).  squarings_done: HOST pointer or NULL.  The call
+ * synchronises `stream` once per squaring.  int32 kernels only. */
+btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Next, int flags, int *squarings_done,
+                            void *stream);
+
+/* btas_apsp_fw: the same APSP distance matrix by blocked Floyd-Warshall --
+ * Algorithm 2's pivot loop reorganised in 128 x 128 tiles: per pivot block,
+ * the diagonal tile and its row and column panels relax in order, and every
+ * other tile is updated by a tropical product with accumulate over the
+ * block's pivots (the semiring GEMM kernel).  n^3 terms instead of
+ * ceil(log2(n-1)) * n^3; int32 results identical to btas_apsp.  W, D as
+ * btas_apsp (D == W allowed, any other overlap not); domain checked
+ * (synchronises `stream` once). */
+btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
 /* Number of squarings btas_apsp performs for n vertices: ceil(log2(n-1)). */
 int btas_apsp_squarings(int64_t n);

@@ -66,6 +66,10 @@ SIGNATURES = {
     "btas_apsp_u16": (_i32, [_i64, _vp, _vp, _i32, _i32, _vp]),
     "btas_apsp_squarings": (_i32, [_i64]),
     "btas_closure": (_i32, [_i32, _i32, _i64, _vp, _vp, _i32, _vp, _vp]),
+    "btas_apsp_paths": (_i32, [_i64, _vp, _vp, _vp, _i32, _vp, _vp]),
+    "btas_gemv": (_i32, [_i32, _i32, _i32, _i64, _i64, _vp, _i64, _vp, _vp, _vp]),
+    "btas_apsp_fw": (_i32, [_i64, _vp, _vp, _vp]),
+    "btas_sssp": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp]),
     "btas_apsp_noalloc": (_i32, [_i64, _vp, _vp, _vp]),
     "btas_batch_create": (_i32, [_vp, _i32]),
     "btas_batch_add_apsp": (_i32, [_vp, _i64, _vp, _vp]),
@@ -191,6 +195,67 @@ def closure(A, semiring="min", out=None, early_exit=True, stream=None, info=Fals
     check(btas_closure(_sr(semiring), _dtype_code(A), n, A.data_ptr(), out.data_ptr(),
                        APSP_EARLY_EXIT if early_exit else 0, ctypes.addressof(sq), _stream(stream)))
     return (out, {"squarings": sq.value}) if info else out
+
+
+def btas_apsp_paths(n, W, D, Next, flags, squarings_done_ptr, stream) -> int:
+    return lib().btas_apsp_paths(n, W, D, Next, flags, squarings_done_ptr, stream)
+
+
+def apsp_paths(W, early_exit=True, stream=None):
+    """APSP distances and next-hop matrix (int32 CUDA tensors)."""
+    torch = _torch()
+    n = W.shape[0]
+    D = torch.empty_like(W)
+    Nx = torch.empty_like(W)
+    check(btas_apsp_paths(n, W.data_ptr(), D.data_ptr(), Nx.data_ptr(), APSP_EARLY_EXIT if early_exit else 0, None,
+                          _stream(stream)))
+    return D, Nx
+
+
+def btas_apsp_fw(n, W, D, stream) -> int:
+    return lib().btas_apsp_fw(n, W, D, stream)
+
+
+def apsp_fw(W, out=None, stream=None):
+    """APSP by blocked Floyd-Warshall (int32 CUDA matrix; out may be W)."""
+    torch = _torch()
+    n = W.shape[0]
+    out = torch.empty_like(W) if out is None else out
+    check(btas_apsp_fw(n, W.data_ptr(), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def btas_gemv(semiring, dtype, trans, m, n, A, lda, x, y, stream) -> int:
+    return lib().btas_gemv(semiring, dtype, trans, m, n, A, lda, x, y, stream)
+
+
+def btas_sssp(n, W, src, dist, iterations_ptr, stream) -> int:
+    return lib().btas_sssp(n, W, src, dist, iterations_ptr, stream)
+
+
+def gemv(A, x, semiring="min", trans=False, out=None, accumulate=False, stream=None):
+    """trans=False: y_i = (+)_j A[i,j] (.) x_j; trans=True: y_j = (+)_i x_i (.) A[i,j]."""
+    torch = _torch()
+    m, n = A.shape
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate needs `out`")
+        out = torch.empty(n if trans else m, dtype=A.dtype, device=A.device)
+    flags = _sr(semiring) | (GEMM_ACCUMULATE if accumulate else 0)
+    check(btas_gemv(flags, _dtype_code(A), 1 if trans else 0, m, n, A.data_ptr(), _rowmajor(A, "A"), x.data_ptr(),
+                    out.data_ptr(), _stream(stream)))
+    return out
+
+
+def sssp(W, src, stream=None, info=False):
+    """Single-source shortest paths (Bellman-Ford by repeated min-plus
+    vector-matrix products) from vertex `src` of the int32 matrix W."""
+    torch = _torch()
+    n = W.shape[0]
+    d = torch.empty(n, dtype=torch.int32, device=W.device)
+    it = ctypes.c_int(0)
+    check(btas_sssp(n, W.data_ptr(), int(src), d.data_ptr(), ctypes.addressof(it), _stream(stream)))
+    return (d, {"iterations": it.value}) if info else d
 
 
 def btas_apsp_noalloc(n, W, D, stream) -> int:

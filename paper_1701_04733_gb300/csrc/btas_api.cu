@@ -1,5 +1,6 @@
 // C-ABI entry points declared in include/btas.h: argument validation, kernel
 // selection, stream-ordered workspace, and the APSP squaring driver.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdint>
@@ -219,6 +220,75 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
     a.vec_a = aligned16(A, lda);
     a.vec_b = aligned16(Bt, ldbt);
     return run_nt(dtype, sr, a, st);
+}
+
+// ----------------------------------------------------------------- level 2
+
+btas_status btas_gemv(int semiring, int dtype, int trans, int64_t m, int64_t n, const void *A, int64_t lda,
+                      const void *x, void *y, void *stream) {
+    const int sr = semiring & 0xff;
+    const bool accumulate = (semiring & BTAS_GEMM_ACCUMULATE) != 0;
+    if (semiring & ~(0xff | BTAS_GEMM_ACCUMULATE)) return fail(BTAS_ERR_ARG, "btas_gemv: unknown flags");
+    if (sr != BTAS_MINPLUS && sr != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_gemv: semiring");
+    if (dtype != BTAS_I32 && dtype != BTAS_F32) return fail(BTAS_ERR_ARG, "btas_gemv: dtype");
+    if (trans != 0 && trans != 1) return fail(BTAS_ERR_ARG, "btas_gemv: trans must be 0 or 1");
+    if (m < 0 || n < 0 || m > INT32_MAX || n > INT32_MAX) return fail(BTAS_ERR_ARG, "btas_gemv: sizes");
+    if (lda < (n > 1 ? n : 1)) return fail(BTAS_ERR_ARG, "btas_gemv: lda < n");
+    const int64_t ylen = trans ? n : m, xlen = trans ? m : n;
+    if (ylen == 0) return BTAS_OK;
+    if (!y || (xlen > 0 && (!A || !x))) return fail(BTAS_ERR_ARG, "btas_gemv: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (xlen == 0) {
+        if (accumulate) return BTAS_OK;
+        BTAS_CUDA(launch_fill4(y, ylen, 1, (int)ylen, ident_bits(dtype, sr), st), "fill");
+        return BTAS_OK;
+    }
+    BTAS_CUDA(launch_gemv(sr, dtype, trans, (int)m, (int)n, A, lda, x, y, accumulate ? 1 : 0, nullptr, st), "gemv");
+    return BTAS_OK;
+}
+
+btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, int *iterations, void *stream) {
+    if (n < 0 || n > INT32_MAX) return fail(BTAS_ERR_ARG, "btas_sssp: n out of range");
+    if (n == 0) {
+        if (iterations) *iterations = 0;
+        return BTAS_OK;
+    }
+    if (src < 0 || src >= n) return fail(BTAS_ERR_ARG, "btas_sssp: source out of range");
+    if (!W || !dist) return fail(BTAS_ERR_ARG, "btas_sssp: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Workspace ws(st);
+    const size_t vb = align256((size_t)n * 4);
+    BTAS_CUDA(ws.alloc(256 + 2 * vb), "workspace alloc");
+    int *flag = static_cast<int *>(ws.p);
+    int *d[2] = {reinterpret_cast<int *>(static_cast<char *>(ws.p) + 256),
+                 reinterpret_cast<int *>(static_cast<char *>(ws.p) + 256 + vb)};
+    {
+        int host[2] = {0, 0};
+        BTAS_CUDA(cudaMemsetAsync(flag, 0, 256, st), "memset");
+        BTAS_CUDA(launch_apsp_scan(W, n, flag + 8, st), "domain scan");
+        BTAS_CUDA(cudaMemcpyAsync(host, flag + 8, 8, cudaMemcpyDeviceToHost, st), "scan readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "scan sync");
+        if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_sssp: %d entries outside the domain", host[1]);
+    }
+    // d_0 = e_src; d_{t+1} = d_t (x) W until unchanged (at most n-1 products)
+    BTAS_CUDA(launch_fill4(d[0], n, 1, (int)n, static_cast<uint32_t>(kInfI32), st), "init");
+    const int zero = 0;
+    BTAS_CUDA(cudaMemcpyAsync(d[0] + src, &zero, 4, cudaMemcpyHostToDevice, st), "init source");
+    int cur = 0, steps = 0;
+    for (int64_t t = 0; t + 1 < n; ++t) {
+        BTAS_CUDA(cudaMemcpyAsync(d[cur ^ 1], d[cur], (size_t)n * 4, cudaMemcpyDeviceToDevice, st), "copy");
+        BTAS_CUDA(cudaMemsetAsync(flag, 0, 4, st), "flag reset");
+        BTAS_CUDA(launch_gemv(kMin, BTAS_I32, 1, (int)n, (int)n, W, n, d[cur], d[cur ^ 1], 1, flag, st), "relax");
+        int changed = 0;
+        BTAS_CUDA(cudaMemcpyAsync(&changed, flag, 4, cudaMemcpyDeviceToHost, st), "flag readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "step sync");
+        cur ^= 1;
+        if (!changed) break;
+        ++steps;
+    }
+    BTAS_CUDA(cudaMemcpyAsync(dist, d[cur], (size_t)n * 4, cudaMemcpyDeviceToDevice, st), "copy out");
+    if (iterations) *iterations = steps;
+    return BTAS_OK;
 }
 
 // ----------------------------------------------------------------- vectors
@@ -574,6 +644,108 @@ btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void
     }
     BTAS_CUDA(cudaMemcpyAsync(Astar, cur, nn * 4, cudaMemcpyDeviceToDevice, st), "copy out");
     if (squarings_done) *squarings_done = done;
+    return BTAS_OK;
+}
+
+btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Next, int flags, int *squarings_done,
+                            void *stream) {
+    if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp_paths: n out of range");
+    if (flags & ~BTAS_APSP_EARLY_EXIT) return fail(BTAS_ERR_ARG, "btas_apsp_paths: unknown flags");
+    if (n == 0) {
+        if (squarings_done) *squarings_done = 0;
+        return BTAS_OK;
+    }
+    if (!W || !D || !Next) return fail(BTAS_ERR_ARG, "btas_apsp_paths: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int S = btas_apsp_squarings(n);
+    const size_t nn = (size_t)n * (size_t)n;
+    const long long ldt = (n + 3) & ~3LL;
+    Workspace ws(st);
+    const size_t flag_bytes = align256((size_t)(S + 4) * 4);
+    BTAS_CUDA(ws.alloc(flag_bytes + 4 * align256(nn * 4) + align256((size_t)n * ldt * 4)), "workspace alloc");
+    char *base = static_cast<char *>(ws.p);
+    int *dflags = reinterpret_cast<int *>(base);
+    int *Db[2], *Nb[2];
+    Db[0] = reinterpret_cast<int *>(base + flag_bytes);
+    Db[1] = reinterpret_cast<int *>(reinterpret_cast<char *>(Db[0]) + align256(nn * 4));
+    Nb[0] = reinterpret_cast<int *>(reinterpret_cast<char *>(Db[1]) + align256(nn * 4));
+    Nb[1] = reinterpret_cast<int *>(reinterpret_cast<char *>(Nb[0]) + align256(nn * 4));
+    int *T = reinterpret_cast<int *>(reinterpret_cast<char *>(Nb[1]) + align256(nn * 4));
+    BTAS_CUDA(cudaMemsetAsync(dflags, 0, flag_bytes, st), "memset");
+    // domain: zero diagonal, weights in [0, 2^28] or INF
+    {
+        int host[2] = {0, 0};
+        BTAS_CUDA(launch_apsp_scan(W, n, dflags + S + 1, st), "domain scan");
+        BTAS_CUDA(cudaMemcpyAsync(host, dflags + S + 1, 8, cudaMemcpyDeviceToHost, st), "scan readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "scan sync");
+        if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_apsp_paths: %d entries outside the domain", host[1]);
+    }
+    BTAS_CUDA(cudaMemcpyAsync(Db[0], W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
+    BTAS_CUDA(launch_next_init(W, n, Nb[0], st), "next-hop init");
+    int cur = 0, done = 0;
+    for (int s = 0; s < S; ++s) {
+        BTAS_CUDA(launch_transpose4(Db[cur], n, (int)n, (int)n, T, ldt, 0, nullptr, st), "transpose");
+        BTAS_CUDA(launch_paths_square((int)n, Db[cur], n, T, ldt, Nb[cur], Db[cur ^ 1], Nb[cur ^ 1], &dflags[s], st),
+                  "paths squaring");
+        cur ^= 1;
+        int changed = 1;
+        BTAS_CUDA(cudaMemcpyAsync(&changed, &dflags[s], 4, cudaMemcpyDeviceToHost, st), "flag readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "squaring sync");
+        if (changed) ++done;
+        if (!changed && (flags & BTAS_APSP_EARLY_EXIT)) break;
+    }
+    BTAS_CUDA(cudaMemcpyAsync(D, Db[cur], nn * 4, cudaMemcpyDeviceToDevice, st), "copy D");
+    BTAS_CUDA(cudaMemcpyAsync(Next, Nb[cur], nn * 4, cudaMemcpyDeviceToDevice, st), "copy Next");
+    if (squarings_done) *squarings_done = done;
+    return BTAS_OK;
+}
+
+btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) {
+    if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp_fw: n out of range");
+    if (n == 0) return BTAS_OK;
+    if (!W || !D) return fail(BTAS_ERR_ARG, "btas_apsp_fw: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int B = fw_block();
+    const size_t nn = (size_t)n * (size_t)n;
+    Workspace ws(st);
+    BTAS_CUDA(ws.alloc(256 + align256((size_t)n * B * 4)), "workspace alloc");
+    int *scan = static_cast<int *>(ws.p);
+    int *RPT = reinterpret_cast<int *>(static_cast<char *>(ws.p) + 256);
+    {
+        int host[2] = {0, 0};
+        BTAS_CUDA(cudaMemsetAsync(scan, 0, 8, st), "memset");
+        BTAS_CUDA(launch_apsp_scan(W, n, scan, st), "domain scan");
+        BTAS_CUDA(cudaMemcpyAsync(host, scan, 8, cudaMemcpyDeviceToHost, st), "scan readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "scan sync");
+        if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_apsp_fw: %d entries outside the domain", host[1]);
+    }
+    if (D != W) BTAS_CUDA(cudaMemcpyAsync(D, W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
+    const int nb = (int)((n + B - 1) / B);
+    for (int kb = 0; kb < nb; ++kb) {
+        const long long o = (long long)kb * B, bw = std::min<long long>(B, n - o);
+        BTAS_CUDA(launch_fw_phase12(D, n, kb, st), "phases 1-2");
+        if (nb == 1) break;
+        // row panel D[o:o+bw, :] transposed into RPT (n x B): the k-contiguous B operand
+        BTAS_CUDA(launch_transpose4(D + o * n, n, (int)bw, (int)n, RPT, B, 0, nullptr, st), "panel transpose");
+        const long long rr[2][2] = {{0, o}, {o + bw, n}};
+        for (int ri = 0; ri < 2; ++ri)
+            for (int ci = 0; ci < 2; ++ci) {
+                const long long r0 = rr[ri][0], r1 = rr[ri][1], c0 = rr[ci][0], c1 = rr[ci][1];
+                if (r1 <= r0 || c1 <= c0) continue;
+                GemmArgs a{};
+                a.m = (int)(r1 - r0);
+                a.n = (int)(c1 - c0);
+                a.k = (int)bw;
+                a.A = D + r0 * n + o; a.lda = n;
+                a.Bt = RPT + c0 * B; a.ldb = B;
+                a.C = D + r0 * n + c0; a.ldc = n;
+                a.accumulate = 1;
+                a.vec_a = aligned16(a.A, n);
+                a.vec_b = aligned16(a.Bt, B);
+                btas_status r = run_nt(BTAS_I32, kMin, a, st);
+                if (r != BTAS_OK) return r;
+            }
+    }
     return BTAS_OK;
 }
 

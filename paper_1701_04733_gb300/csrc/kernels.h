@@ -43,6 +43,21 @@ cudaError_t launch_ident_oplus(const void *src, long long lds, int n, void *dst,
 // or a non-zero diagonal).  out must be zeroed first.
 cudaError_t launch_apsp_scan(const int *W, long long n, int *out, cudaStream_t st);
 
+// ---- APSP with next-hop matrix (paths.cu)
+cudaError_t launch_next_init(const int *W, long long n, int *N, cudaStream_t st);
+cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *Dt, long long ldt, const int *N,
+                                int *D2, int *N2, int *changed, cudaStream_t st);
+
+// ---- level 2 (gemv.cu): trans 0: y_i = (+)_j A[i][j] (.) x_j; trans 1:
+// y_j = (+)_i x_i (.) A[i][j]; accumulate keeps y as a (+) start value;
+// changed (trans 1, optional) is set when some y entry changes.
+cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *A, long long lda, const void *x,
+                        void *y, int accumulate, int *changed, cudaStream_t st);
+
+// ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
+cudaError_t launch_fw_phase12(int *D, long long n, int kb, cudaStream_t st);
+int fw_block();
+
 // ---- vector kernels (tvec.cu)
 cudaError_t launch_dot(int sr, int dtype, long long n, const void *x, long long incx, const void *y,
                        long long incy, void *result, void *partials, int nblocks, cudaStream_t st);

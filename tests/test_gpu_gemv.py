@@ -1,0 +1,58 @@
+"""Level 2 (tropical gemv) and Bellman-Ford SSSP by repeated vector-matrix
+products, against the oracle (bit-exact) and Dijkstra."""
+import numpy as np
+import pytest
+
+import gen
+from gpu_util import bits, dev, f32_matrix, host, int_matrix
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def btas():
+    import torch
+    import paper_1701_04733_gb300 as b
+    assert torch.cuda.is_available()
+    b.lib()
+    return b
+
+
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("sr", [0, 1])
+@pytest.mark.parametrize("dt", ["i32", "f32"])
+def test_gemv_shapes(btas, oracle_mod, dt, sr, trans):
+    mk = int_matrix if dt == "i32" else f32_matrix
+    for (m, n) in [(1, 1), (3, 5), (33, 130), (257, 63), (1000, 1001), (64, 4096)]:
+        A = mk(300 + m, (m, n), sr)
+        x = mk(400 + n, ((m if trans else n),), sr)
+        ref = oracle_mod.gemv(sr, A, x, trans=trans)
+        y = host(btas.gemv(dev(A), dev(x), sr, trans=trans))
+        np.testing.assert_array_equal(bits(y), bits(ref), err_msg=f"{dt} sr={sr} trans={trans} {m}x{n}")
+        y0 = mk(500 + m, ((n if trans else m),), sr)
+        yd = dev(y0)
+        btas.gemv(dev(A), dev(x), sr, trans=trans, out=yd, accumulate=True)
+        np.testing.assert_array_equal(bits(host(yd)), bits(oracle_mod.gemv(sr, A, x, trans=trans, y=y0)))
+
+
+def test_gemv_strided_and_unaligned(btas, oracle_mod):
+    import torch
+    A = int_matrix(7, (70, 91), 0)
+    Abig = dev(np.pad(A, ((0, 0), (0, 3))))
+    x = int_matrix(8, (91,), 0)
+    ref = oracle_mod.gemv(0, A, x)
+    np.testing.assert_array_equal(host(btas.gemv(Abig[:, :91], dev(x), 0)), ref)
+
+
+@pytest.mark.parametrize("n", [1, 2, 50, 777, 4096])
+def test_sssp_matches_dijkstra_and_oracle(btas, oracle_mod, n):
+    W = gen.random_graph(gen.BASE_SEED, 90 + n % 7, n, 0.01 if n > 1000 else 0.1, 1, 1000)
+    Wd = dev(W)
+    for src in sorted({0, n // 3, n - 1}):
+        d, info = btas.sssp(Wd, src, info=True)
+        d = host(d)
+        np.testing.assert_array_equal(d, oracle_mod.dijkstra_rows(W, [src])[0])
+        if n <= 777:
+            ref, steps = oracle_mod.sssp(W, src)
+            np.testing.assert_array_equal(d, ref)
+            assert info["iterations"] == steps
