@@ -55,7 +55,28 @@ __global__ void gemv_rows_kernel(int m, int n, const T *__restrict__ A, long lon
     const T *row = A + (long long)warp * lda;
     T acc = Ident<T, SR>::v();
     if (vec) {
-        for (int j = lane * 4; j < n; j += 128) {
+        int j = lane * 4;
+        // four independent 128-bit loads in flight per lane
+        for (; j + 384 + 4 <= n; j += 512) {
+            uint4 a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = __ldg(reinterpret_cast<const uint4 *>(row + j + 128 * u));
+                b[u] = __ldg(reinterpret_cast<const uint4 *>(x + j + 128 * u));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t av[4] = {a[u].x, a[u].y, a[u].z, a[u].w}, bv[4] = {b[u].x, b[u].y, b[u].z, b[u].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    T ae, be;
+                    memcpy(&ae, &av[q], 4);
+                    memcpy(&be, &bv[q], 4);
+                    acc = op_plus<T, SR>(acc, op_times<SR>(ae, be));
+                }
+            }
+        }
+        for (; j < n; j += 128) {
             if (j + 4 <= n) {
                 const uint4 a = __ldg(reinterpret_cast<const uint4 *>(row + j));
                 const uint4 b = __ldg(reinterpret_cast<const uint4 *>(x + j));
@@ -93,6 +114,7 @@ __global__ void gemv_cols_kernel(int m, int n, const T *__restrict__ A, long lon
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] = Ident<T, SR>::v();
     const bool full = vec && j0 + 4 <= n;
+#pragma unroll 8
     for (int i = i0; i < i1; ++i) {
         const T xi = __ldg(x + i);
         const T *row = A + (long long)i * lda;
