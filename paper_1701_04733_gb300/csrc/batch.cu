@@ -27,6 +27,7 @@
 #include "batch_kernel.cuh"
 #include "kernels.h"
 #include "tgemm.cuh"
+#include "u16_tile.cuh"
 
 namespace btas {
 
@@ -43,14 +44,34 @@ __device__ __forceinline__ int tasks_at(const BInst &I, int level) {
     return I.tiles_m * I.tiles_n;
 }
 
-// 128 x 128 transpose of a 4-byte matrix through shared memory.
+// 128 x 128 transpose of a 4-byte matrix through shared memory.  With Cd /
+// Cu it also stores the tile's packed 16-bit forms (row-major, not
+// transposed) and reports the largest finite int32 entry to *maxfin.
 __device__ __forceinline__ void transpose_tile(const uint32_t *src, long long lds, int rows, int cols, uint32_t *dst,
-                                               long long ldd, int tile, uint32_t *sm, int tid) {
+                                               long long ldd, int tile, uint32_t *sm, int tid,
+                                               uint32_t *Cd = nullptr, uint16_t *Cu = nullptr, long long ldcd = 0,
+                                               long long ldcu = 0, int *maxfin = nullptr) {
     const int tiles_c = (cols + kBT - 1) / kBT;
     const int r0 = (tile / tiles_c) * kBT, c0 = (tile % tiles_c) * kBT;
+    int mx = -1;
     for (int idx = tid; idx < kBT * kBT; idx += BCfg::kThreads) {
         const int r = idx / kBT, c = idx % kBT;
-        if (r0 + r < rows && c0 + c < cols) sm[c * (kBT + 1) + r] = __ldcg(src + (long long)(r0 + r) * lds + c0 + c);
+        if (r0 + r < rows && c0 + c < cols) {
+            const uint32_t v = __ldcg(src + (long long)(r0 + r) * lds + c0 + c);
+            sm[c * (kBT + 1) + r] = v;
+            if (Cd != nullptr) {
+                const int iv = static_cast<int>(v);
+                const uint32_t u = iv >= BTAS_INF_U16 ? BTAS_INF_U16 : (uint32_t)iv;
+                Cd[(long long)(r0 + r) * ldcd + c0 + c] = u * 0x10001u;
+                Cu[(long long)(r0 + r) * ldcu + c0 + c] = (uint16_t)u;
+                if (iv < kInfI32) mx = max(mx, iv);
+            }
+        }
+    }
+    if (maxfin != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0 && mx >= 0) atomicMax(maxfin, mx);
     }
     __syncthreads();
     for (int idx = tid; idx < kBT * kBT; idx += BCfg::kThreads) {
@@ -62,14 +83,16 @@ __device__ __forceinline__ void transpose_tile(const uint32_t *src, long long ld
 
 template <int VAR, int SR>
 __device__ __forceinline__ bool gemm_tile(const GemmArgs &a, int bm, int bn, unsigned char *smem, int tid,
-                                          void *Ct = nullptr, long long ldct = 0) {
-    return nt_tile<BCfg, VAR, SR, 4>(a, bm, bn, smem, tid, Ct, ldct);
+                                          void *Ct = nullptr, long long ldct = 0, uint32_t *Cd = nullptr,
+                                          long long ldcd = 0, uint16_t *Cu = nullptr, long long ldcu = 0) {
+    return nt_tile<BCfg, VAR, SR, 4>(a, bm, bn, smem, tid, Ct, ldct, Cd, ldcd, Cu, ldcu);
 }
 
 __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const BatchParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_task[4];
     __shared__ int s_flag;
+    __shared__ int s_m;
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) {
@@ -78,6 +101,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             if (t < p.total && ld_acquire(p.status) == 0) w = p.tasks[t];
             s_task[0] = w.x; s_task[1] = w.y; s_task[2] = w.z; s_task[3] = w.w;
             s_flag = 1;
+            s_m = 0x7FFFFFFF;
             if (w.x >= 0 && w.z > 0) {
                 // wait until every task of the previous level of this instance is done
                 const BInst &I = p.insts[w.y];
@@ -95,11 +119,13 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                 }
                 if (s_task[0] >= 0 && I.kind == kInstApsp && w.z >= 2)
                     s_flag = ld_acquire(p.changed + I.flag_base + w.z - 1);
+                if (s_task[0] >= 0 && I.kind == kInstApsp) s_m = ld_acquire(p.maxfin + I.flag_base + w.z - 1);
             }
         }
         __syncthreads();
         const int type = s_task[0], inst = s_task[1], level = s_task[2], tile = s_task[3];
         const int prev_changed = s_flag;
+        const int prev_max = s_m;
         __syncthreads();
         if (type < 0) break;
         const BInst I = p.insts[inst];
@@ -107,8 +133,10 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
         if (type == kTaskTranspose) {
             const uint32_t *src = static_cast<const uint32_t *>(I.kind == kInstGemm ? I.B : I.A);
             const long long lds = I.kind == kInstGemm ? I.ldb : I.lda;
+            const bool forms = I.kind == kInstApsp && I.use_u16;
             transpose_tile(src, lds, I.t0_rows, I.t0_cols, static_cast<uint32_t *>(I.Q0), I.ldq, tile,
-                           reinterpret_cast<uint32_t *>(smem_raw), tid);
+                           reinterpret_cast<uint32_t *>(smem_raw), tid, forms ? I.Ad0 : nullptr,
+                           forms ? I.U0 : nullptr, I.ldq, I.ldu, forms ? p.maxfin + I.flag_base : nullptr);
         } else if (type == kTaskCopy) {
             // n <= 2: D = W
             const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
@@ -134,11 +162,29 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.one = 1;
             a.vec_a = ((reinterpret_cast<uintptr_t>(cur) & 15) == 0) && ((ldcur & 3) == 0);
             a.vec_b = 1;
+            // forms of D_{s-1} are in set (s-1) & 1, D_s goes to set s & 1
+            const bool more = s < S && I.use_u16;
+            int *Ct = s < S ? static_cast<int *>((s & 1) ? I.Q1 : I.Q0) : nullptr;
+            uint32_t *Cd = more ? ((s & 1) ? I.Ad1 : I.Ad0) : nullptr;
+            uint16_t *Cu = more ? ((s & 1) ? I.U1 : I.U0) : nullptr;
+            if (more) a.maxfin = p.maxfin + I.flag_base + s;
             if (s >= 2 && prev_changed == 0) {
                 copy_tile<BCfg, int>(a, bm, bn, tid);
+            } else if (I.use_u16 && 2LL * prev_max < BTAS_INF_U16) {
+                // every finite entry of D_{s-1} is < 0x7FFF / 2: the packed squaring is exact
+                U16Tile u{};
+                u.n = I.n;
+                u.Ad = ((s - 1) & 1) ? I.Ad1 : I.Ad0; u.ldad = I.ldq;
+                u.U = ((s - 1) & 1) ? I.U1 : I.U0; u.ldu = I.ldu;
+                u.prev = static_cast<const int *>(cur); u.ldp = ldcur;
+                u.C = static_cast<int *>(out); u.ldc = a.ldc;
+                u.Ct = Ct; u.ldct = I.ldq;
+                u.Cd = Cd; u.ldcd = I.ldq;
+                u.Cu = Cu; u.ldcu = I.ldu;
+                u.maxfin = a.maxfin;
+                ch = u16_tile(u, bm, bn, smem_raw, tid);
             } else {
-                void *Ct = s < S ? ((s & 1) ? I.Q1 : I.Q0) : nullptr;
-                ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, Ct, I.ldq);
+                ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, Ct, I.ldq, Cd, I.ldq, Cu, I.ldu);
             }
         } else if (type == kTaskSquare) {
             const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
@@ -151,7 +197,22 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.one = 1;
             a.vec_a = ((reinterpret_cast<uintptr_t>(I.A) & 15) == 0) && ((I.lda & 3) == 0);
             a.vec_b = 1;
-            ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, I.Q1, I.ldq);
+            a.maxfin = I.maxfin_ptr;
+            if (I.use_u16) {
+                U16Tile u{};
+                u.n = I.n;
+                u.Ad = I.Ad0; u.ldad = I.ldq;
+                u.U = I.U0; u.ldu = I.ldu;
+                u.prev = static_cast<const int *>(I.A); u.ldp = I.lda;
+                u.C = static_cast<int *>(I.C); u.ldc = I.ldc;
+                u.Ct = static_cast<int *>(I.Q1); u.ldct = I.ldq;
+                u.Cd = I.Ad1; u.ldcd = I.ldq;
+                u.Cu = I.U1; u.ldcu = I.ldu;
+                u.maxfin = I.maxfin_ptr;
+                ch = u16_tile(u, bm, bn, smem_raw, tid);
+            } else {
+                ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, I.Q1, I.ldq, I.Ad1, I.ldq, I.U1, I.ldu);
+            }
         } else {  // kTaskGemm
             const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
             GemmArgs a{};
@@ -279,6 +340,9 @@ btas_status build_plan(btas_batch_t *b) {
     size_t ws = 0;
     int counters = 0, max_level = 0;
     std::vector<size_t> ws_off(ninst);
+    // BTAS_BATCH_NO_U16 keeps every batched squaring in int32
+    const char *no16 = getenv("BTAS_BATCH_NO_U16");
+    const int allow16 = (no16 && *no16 && atoi(no16) != 0) ? 0 : 1;
     for (size_t i = 0; i < ninst; ++i) {
         BInst I = b->reqs[i].inst;
         ws_off[i] = ws;
@@ -286,7 +350,10 @@ btas_status build_plan(btas_batch_t *b) {
             if (I.levels > 0) {
                 I.ldq = (I.n + 3) & ~3LL;
                 I.ldx = I.ldq;
-                ws += 4 * al256((size_t)I.n * I.ldq * 4);
+                I.ldu = (I.n + 7) & ~7LL;
+                I.use_u16 = allow16;
+                // X0, X1, Q0, Q1 (int32), Ad0, Ad1 (duplicated words), U0, U1 (uint16)
+                ws += 6 * al256((size_t)I.n * I.ldq * 4) + 2 * al256((size_t)I.n * I.ldu * 2);
             }
         } else if (!I.trans_b) {
             I.ldq = (I.k + 3) & ~3LL;
@@ -324,7 +391,7 @@ btas_status build_plan(btas_batch_t *b) {
     b->total = (int)tasks.size();
     const size_t task_bytes = al256(tasks.size() * sizeof(int4));
     const size_t inst_bytes = al256(ninst * sizeof(BInst));
-    b->counter_bytes = al256((size_t)(2 + 2 * counters) * 4);
+    b->counter_bytes = al256((size_t)(2 + 3 * counters) * 4);
     b->workspace_bytes = (long long)ws;
     b->dev_bytes = task_bytes + inst_bytes + b->counter_bytes + ws;
     if (cudaMalloc(&b->dev_mem, b->dev_bytes ? b->dev_bytes : 256) != cudaSuccess)
@@ -343,6 +410,10 @@ btas_status build_plan(btas_batch_t *b) {
             I.X1 = w + blk;
             I.Q0 = w + 2 * blk;
             I.Q1 = w + 3 * blk;
+            I.Ad0 = reinterpret_cast<uint32_t *>(w + 4 * blk);
+            I.Ad1 = reinterpret_cast<uint32_t *>(w + 5 * blk);
+            I.U0 = reinterpret_cast<uint16_t *>(w + 6 * blk);
+            I.U1 = reinterpret_cast<uint16_t *>(w + 6 * blk + al256((size_t)I.n * I.ldu * 2));
         } else if (I.kind == kInstGemm && !I.trans_b) {
             I.Q0 = w;
         }
@@ -357,6 +428,7 @@ btas_status build_plan(btas_batch_t *b) {
     p.status = b->d_counters + 1;
     p.done = b->d_counters + 2;
     p.changed = b->d_counters + 2 + counters;
+    p.maxfin = b->d_counters + 2 + 2 * counters;
     p.insts = d_insts;
     p.timeout_cycles = batch_timeout_cycles(dev);
     // Fault injection (tests only): BTAS_BATCH_WITHHOLD=i makes the host

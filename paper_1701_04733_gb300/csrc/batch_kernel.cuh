@@ -37,6 +37,14 @@ struct BInst {
     void *Q0, *Q1;        // APSP transposes / GEMM B^T (Q0) / square B operand and transposed output
     long long ldq;
     int *changed_ptr;     // square: change flag
+    // packed 16-bit operand forms of D (set 0 / set 1): duplicated words
+    // (pitch ldq) and uint16 values (pitch ldu); APSP: D_s lives in set s & 1;
+    // square: input in set 0, output in set 1
+    uint32_t *Ad0, *Ad1;
+    uint16_t *U0, *U1;
+    long long ldu;
+    int use_u16;          // APSP: packed squarings allowed; square: run this one packed
+    int *maxfin_ptr;      // square: atomicMax of the largest finite output
 };
 
 struct BatchParams {
@@ -45,6 +53,7 @@ struct BatchParams {
     int *next;
     int *done;
     int *changed;
+    int *maxfin;        // per (instance, level): largest finite entry of D_level
     int *status;
     const BInst *insts;
     long long timeout_cycles;

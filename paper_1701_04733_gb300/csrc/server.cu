@@ -64,6 +64,12 @@ struct Req {
     void *dA = nullptr, *dB = nullptr, *dBt = nullptr, *dC = nullptr;
     long long lda_d = 0, ldb_d = 0, ldq = 0, ldc_d = 0;
     int S = 0, s = 1;  // APSP squarings, next squaring (1-based)
+    // APSP: packed 16-bit operand forms of D (two sets) and the largest
+    // finite entry of the latest D (-1: not known yet)
+    uint32_t *Ad[2] = {nullptr, nullptr};
+    uint16_t *U[2] = {nullptr, nullptr};
+    long long ldu = 0;
+    int last_max = -1;
     int result_buf = 0;
     cudaEvent_t in_ready = nullptr, out_ready = nullptr;
     double t_submit = 0, t_admit = 0, t_done = 0;
@@ -103,6 +109,7 @@ struct btas_server_t {
     long long timeout_cycles = 0;
     int step_parity = 0;
     double step_terms = 3e10;  // work cap of one step (terms), keeps steps short
+    int allow_u16 = 1;         // BTAS_SERVER_NO_U16=1 keeps every squaring in int32
     int64_t steps = 0;
     int64_t units = 0;
     int64_t completed = 0;
@@ -132,8 +139,8 @@ int squarings_of(long long n) {
 
 size_t footprint(const Req &r) {
     if (r.kind == 0) {
-        const long long ld = r4(r.n);
-        return 4 * a256((size_t)r.n * ld * 4) + a256((size_t)(r.S + 2) * 4);
+        const long long ld = r4(r.n), ldu = (r.n + 7) & ~7LL;
+        return 6 * a256((size_t)r.n * ld * 4) + 2 * a256((size_t)r.n * ldu * 2) + a256((size_t)(2 * r.S + 4) * 4);
     }
     return a256((size_t)r.m * r4(r.k) * 4) + a256((size_t)r.k * r4(r.n) * 4) + a256((size_t)r.n * r4(r.k) * 4) +
            a256((size_t)r.m * r4(r.n) * 4);
@@ -157,8 +164,15 @@ bool admit(btas_server_t *sv, Req *r) {
         r->P[1] = p + blk;
         r->Q[0] = p + 2 * blk;
         r->Q[1] = p + 3 * blk;
-        r->dflag = reinterpret_cast<int *>(p + 4 * blk);
-        cudaMemsetAsync(r->dflag, 0, (size_t)(r->S + 2) * 4, sv->copy);
+        r->Ad[0] = reinterpret_cast<uint32_t *>(p + 4 * blk);
+        r->Ad[1] = reinterpret_cast<uint32_t *>(p + 5 * blk);
+        r->ldu = (r->n + 7) & ~7LL;
+        const size_t ublk = a256((size_t)r->n * r->ldu * 2);
+        r->U[0] = reinterpret_cast<uint16_t *>(p + 6 * blk);
+        r->U[1] = reinterpret_cast<uint16_t *>(p + 6 * blk + ublk);
+        // change flags [0, S+2) and largest finite entries [S+2, 2S+4)
+        r->dflag = reinterpret_cast<int *>(p + 6 * blk + 2 * ublk);
+        cudaMemsetAsync(r->dflag, 0, (size_t)(2 * r->S + 4) * 4, sv->copy);
         cudaMemcpy2DAsync(r->P[0], ld * 4, r->hA, (size_t)r->n * 4, (size_t)r->n * 4, r->n, cudaMemcpyHostToDevice,
                           sv->copy);
     } else {
@@ -234,6 +248,15 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
             I.ldq = r->ldp;
             I.changed_ptr = r->dflag + s;
             if (s == 1) I.t0_rows = I.t0_cols = r->n;  // transpose W into Q[0] first
+            // packed squaring when every finite entry of D_{s-1} is < 0x7FFF / 2
+            // (exact); the forms of D_s are written for the next squaring
+            I.use_u16 = (s >= 2 && r->last_max >= 0 && 2LL * r->last_max < BTAS_INF_U16 && sv->allow_u16) ? 1 : 0;
+            I.Ad0 = r->Ad[(s - 1) & 1];
+            I.U0 = r->U[(s - 1) & 1];
+            I.Ad1 = s < r->S ? r->Ad[s & 1] : nullptr;
+            I.U1 = s < r->S ? r->U[s & 1] : nullptr;
+            I.ldu = r->ldu;
+            I.maxfin_ptr = s < r->S ? r->dflag + r->S + 2 + s : nullptr;
         } else {
             I.kind = kInstGemm;
             I.sr = r->sr;
@@ -310,10 +333,14 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
     p.withhold_inst = -1;
     const int grid = std::max(1, std::min(sv->grid, p.total));
     if (launch_batch_kernel(p, grid, sv->compute) != cudaSuccess) return -1;
-    // change flags of this step's squarings -> pinned mailbox
-    for (int i = 0; i < ninst; ++i)
-        if (units[i]->kind == 0)
-            cudaMemcpyAsync(sv->h_flags + i, units[i]->dflag + units[i]->s, 4, cudaMemcpyDeviceToHost, sv->compute);
+    // change flags and largest finite entries of this step's squarings ->
+    // pinned mailbox
+    for (int i = 0; i < ninst; ++i) {
+        if (units[i]->kind != 0) continue;
+        cudaMemcpyAsync(sv->h_flags + i, units[i]->dflag + units[i]->s, 4, cudaMemcpyDeviceToHost, sv->compute);
+        cudaMemcpyAsync(sv->h_flags + sv->flag_slots + 1 + i, units[i]->dflag + units[i]->S + 2 + units[i]->s, 4,
+                        cudaMemcpyDeviceToHost, sv->compute);
+    }
     cudaMemcpyAsync(sv->h_flags + sv->flag_slots, p.status, 4, cudaMemcpyDeviceToHost, sv->compute);
     cudaEventRecord(sv->step_done[par], sv->compute);
     sv->step_parity ^= 1;
@@ -408,6 +435,7 @@ void worker_loop(btas_server_t *sv) {
             bool finished = true;
             if (r->kind == 0) {
                 const bool changed = sv->h_flags[i] != 0;
+                r->last_max = r->s < r->S ? sv->h_flags[sv->flag_slots + 1 + i] : -1;
                 r->result_buf = r->s & 1;
                 finished = !changed || r->s >= r->S;
                 ++r->s;
@@ -447,9 +475,10 @@ btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, in
     }
     sv->grid = std::max(1, per_sm * sms);
     if (const char *e = getenv("BTAS_SERVER_STEP_TERMS")) sv->step_terms = atof(e) > 0 ? atof(e) : sv->step_terms;
+    if (const char *e = getenv("BTAS_SERVER_NO_U16")) sv->allow_u16 = (*e && atoi(e) != 0) ? 0 : 1;
     sv->timeout_cycles = batch_timeout_cycles(sv->device);
     sv->flag_slots = 1 << 16;
-    if (cudaMallocHost(reinterpret_cast<void **>(&sv->h_flags), (size_t)(sv->flag_slots + 1) * 4) != cudaSuccess) {
+    if (cudaMallocHost(reinterpret_cast<void **>(&sv->h_flags), (size_t)(2 * sv->flag_slots + 1) * 4) != cudaSuccess) {
         delete sv;
         return sfail(BTAS_ERR_NOMEM, "btas_server_create: pinned mailbox");
     }

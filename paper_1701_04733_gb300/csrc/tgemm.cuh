@@ -237,12 +237,16 @@ __device__ __forceinline__ void copy_tile(const GemmArgs &args, int bm, int bn, 
 // One BM x BN output tile at (bm, bn).  Returns this thread's "some output
 // differs from prev" bit.  With Ct != nullptr the tile is also stored
 // transposed (Ct[c][r], leading dimension ldct) through shared memory, so a
-// following squaring finds its k-contiguous B operand ready.  Loads of data
+// following squaring finds its k-contiguous B operand ready.  With Cd / Cu
+// (int32 only) it also stores the packed 16-bit operand forms: Cd = the value
+// clamped to INF16 and duplicated into both halfwords, Cu = the clamped
+// value (values are non-negative APSP distances here).  Loads of data
 // that other CTAs of the same launch may have written go through L2
 // (cp.async.cg, __ldcg), never through the non-coherent L1.
 template <class Cfg, int VAR, int SR, int NS>
 __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, unsigned char *smem_raw, int tid,
-                                        void *Ct = nullptr, long long ldct = 0) {
+                                        void *Ct = nullptr, long long ldct = 0, uint32_t *Cd = nullptr,
+                                        long long ldcd = 0, uint16_t *Cu = nullptr, long long ldcu = 0) {
     using T = typename VarTypes<VAR>::T;
     constexpr int FK = Cfg::FK;
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, LD = Cfg::kLd, ST = Cfg::STAGES;
@@ -324,6 +328,15 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
                 if (P != nullptr && v != __ldcg(P + (long long)r * args.ldp + c)) ch = true;
                 if (SR == kMin && args.maxfin != nullptr) mx = max(mx, finite_int(v));
                 C[(long long)r * args.ldc + c] = v;
+                if constexpr (std::is_same<T, int>::value) {
+                    if (Cd != nullptr) {
+                        // 16-bit forms for a following packed squaring (used only
+                        // when every finite entry is < 0x7FFF / 2, so exact)
+                        const uint32_t u = v >= BTAS_INF_U16 ? BTAS_INF_U16 : (uint32_t)v;
+                        Cd[(long long)r * ldcd + c] = u * 0x10001u;
+                        Cu[(long long)r * ldcu + c] = (uint16_t)u;
+                    }
+                }
             }
         }
     if (SR == kMin && args.maxfin != nullptr) {

@@ -1,0 +1,179 @@
+// One 128 x 128 output tile of an exact packed 16-bit min-plus squaring, for
+// the persistent tile-task kernel.  Same arithmetic as tgemm_u16.cu (two
+// outputs per 32-bit lane, A duplicated into both halfwords, B pairs adjacent
+// in row-major storage, per-halfword DPX add-min; exact when every operand is
+// <= 0x7FFF), sized for 256 threads at 2 CTAs/SM: 8 rows x 4 column pairs
+// per thread.  Inputs come from the 16-bit forms of D_{s-1} (Ad: duplicated
+// words, U: uint16 values); the epilogue writes D_s as int32 (INF16 widened to
+// INF), transposed int32, and again in both 16-bit forms, so the next
+// squaring can run in either precision.
+#pragma once
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace btas {
+
+struct U16Tile {
+    int n;
+    const uint32_t *Ad;  // n x n duplicated words, pitch ldad (multiple of 4)
+    long long ldad;
+    const uint16_t *U;   // n x n values, pitch ldu (multiple of 8)
+    long long ldu;
+    const int *prev;     // int32 D_{s-1} (change detection)
+    long long ldp;
+    int *C;              // int32 D_s
+    long long ldc;
+    int *Ct;             // optional: int32 D_s transposed
+    long long ldct;
+    uint32_t *Cd;        // optional: duplicated words of D_s
+    long long ldcd;
+    uint16_t *Cu;        // optional: uint16 D_s
+    long long ldcu;
+    int *maxfin;         // optional: atomicMax of the largest finite output
+};
+
+namespace u16t {
+constexpr int BM = 128, BNP = 64, BK = 32, ST = 3, NT = 256;
+constexpr int LDA = BK + 4;  // words per A row
+constexpr int LDB = BNP;     // words per B row
+constexpr int STAGE = BM * LDA + BK * LDB;
+constexpr int SMEM = ST * STAGE * 4;  // 79872 bytes
+}  // namespace u16t
+
+// Returns this thread's "some output differs from prev" bit.  smem must hold
+// max(u16t::SMEM, 128 * 129 * 4) bytes.
+__device__ __forceinline__ bool u16_tile(const U16Tile &a, int bm, int bn, unsigned char *smem_raw, int tid) {
+    using namespace u16t;
+    uint32_t *smem = reinterpret_cast<uint32_t *>(smem_raw);
+    const int n = a.n;
+    const int bnp = bn / 2;  // first column pair of the tile
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int ty = lane >> 3, tx = lane & 7;
+    const int row_base = wm * 32 + ty;       // + 4*i
+    const int pair_base = wn * 32 + tx * 4;  // + q
+    uint32_t acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = kInfU16x2;
+    const bool va = ((reinterpret_cast<uintptr_t>(a.Ad) & 15) == 0) && ((a.ldad & 3) == 0);
+    const bool vb = ((reinterpret_cast<uintptr_t>(a.U) & 15) == 0) && ((a.ldu & 7) == 0);
+    const int KT = (n + BK - 1) / BK;
+    auto load = [&](int s, int kt) {
+        uint32_t *sa = smem + s * STAGE;
+        uint32_t *sb = sa + BM * LDA;
+        const int k0 = kt * BK;
+#pragma unroll
+        for (int t = 0; t < (BM * BK / 4) / NT; ++t) {
+            const int c = tid + t * NT;
+            const int r = c >> 3, kc = (c & 7) * 4;
+            const int gr = bm + r, gk = k0 + kc;
+            uint32_t *dst = sa + r * LDA + kc;
+            if (va && gr < n && gk + 4 <= n) {
+                cp_async16(dst, a.Ad + (long long)gr * a.ldad + gk);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    dst[e] = (gr < n && gk + e < n) ? __ldcg(a.Ad + (long long)gr * a.ldad + gk + e) : kInfU16x2;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < (BK * BNP / 4) / NT; ++t) {
+            const int c = tid + t * NT;
+            const int r = c >> 4, wc = (c & 15) * 4;  // 16 chunks of 4 words per B row
+            const int gk = k0 + r, gcol = 2 * (bnp + wc);
+            uint32_t *dst = sb + r * LDB + wc;
+            if (vb && gk < n && gcol + 8 <= n) {
+                cp_async16(dst, a.U + (long long)gk * a.ldu + gcol);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c0 = gcol + 2 * e;
+                    uint32_t lo = BTAS_INF_U16, hi = BTAS_INF_U16;
+                    if (gk < n) {
+                        if (c0 < n) lo = __ldcg(a.U + (long long)gk * a.ldu + c0);
+                        if (c0 + 1 < n) hi = __ldcg(a.U + (long long)gk * a.ldu + c0 + 1);
+                    }
+                    dst[e] = lo | (hi << 16);
+                }
+            }
+        }
+    };
+#pragma unroll
+    for (int s = 0; s < ST - 1; ++s) {
+        if (s < KT) load(s, s);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < KT; ++kt) {
+        cp_async_wait<ST - 2>();
+        __syncthreads();
+        if (kt + ST - 1 < KT) load((kt + ST - 1) % ST, kt + ST - 1);
+        cp_async_commit();
+        const uint32_t *sa = smem + (kt % ST) * STAGE;
+        const uint32_t *sb = sa + BM * LDA;
+#pragma unroll 2
+        for (int kk = 0; kk < BK; kk += 4) {
+            uint4 av[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) av[i] = *reinterpret_cast<const uint4 *>(sa + (row_base + 4 * i) * LDA + kk);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 b = *reinterpret_cast<const uint4 *>(sb + (kk + q) * LDB + pair_base);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const uint32_t ai = q == 0 ? av[i].x : q == 1 ? av[i].y : q == 2 ? av[i].z : av[i].w;
+                    acc[i][0] = u16x2_addmin(ai, b.x, acc[i][0]);
+                    acc[i][1] = u16x2_addmin(ai, b.y, acc[i][1]);
+                    acc[i][2] = u16x2_addmin(ai, b.z, acc[i][2]);
+                    acc[i][3] = u16x2_addmin(ai, b.w, acc[i][3]);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+    bool ch = false;
+    int mx = -1;
+    if (a.Ct != nullptr) __syncthreads();  // smem is reused for the transposed tile
+    int *tr = reinterpret_cast<int *>(smem_raw);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int rl = row_base + 4 * i, r = bm + rl;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cl = 2 * (pair_base + j), c = bn + cl;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t u = h ? (acc[i][j] >> 16) : (acc[i][j] & 0xFFFFu);
+                const int v = u >= BTAS_INF_U16 ? kInfI32 : (int)u;
+                if (a.Ct != nullptr) tr[(cl + h) * (BM + 1) + rl] = v;
+                if (r < n && c + h < n) {
+                    if (a.prev != nullptr && v != __ldcg(a.prev + (long long)r * a.ldp + c + h)) ch = true;
+                    if (u < BTAS_INF_U16) mx = max(mx, (int)u);
+                    a.C[(long long)r * a.ldc + c + h] = v;
+                    if (a.Cd != nullptr) {
+                        a.Cd[(long long)r * a.ldcd + c + h] = u * 0x10001u;
+                        a.Cu[(long long)r * a.ldcu + c + h] = (uint16_t)u;
+                    }
+                }
+            }
+        }
+    }
+    if (a.maxfin != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx >= 0) atomicMax(a.maxfin, mx);
+    }
+    if (a.Ct != nullptr) {
+        __syncthreads();
+        for (int idx = tid; idx < BM * 128; idx += NT) {
+            const int c = idx / BM, r = idx % BM;
+            if (bn + c < n && bm + r < n) a.Ct[(long long)(bn + c) * a.ldct + bm + r] = tr[c * (BM + 1) + r];
+        }
+        __syncthreads();
+    }
+    return ch;
+}
+
+}  // namespace btas

@@ -122,3 +122,41 @@ def test_withheld_dependency_times_out(btas):
     ok.wait()
     np.testing.assert_array_equal(host(D), host(btas.apsp(Wd)))
     ok.close()
+
+
+def test_precision_switches_mid_solve(btas, oracle_mod):
+    """Weights near 5000: the first squarings run packed (2*max < 0x7FFF), the
+    later ones must fall back to int32 as distances grow; the batch (device
+    decision) and the server (host decision) both stay exact, and so does the
+    batch with packed squarings disabled."""
+    import os
+    import torch
+    sizes = [40, 130, 257, 300]
+    items = []
+    for i, n in enumerate(sizes):
+        W = gen.random_graph(70 + i, i, n, 0.03, 4000, 5000)
+        items.append((W, dev(W), torch.empty((n, n), dtype=torch.int32, device="cuda")))
+    for no16 in ("0", "1"):
+        os.environ["BTAS_BATCH_NO_U16"] = no16
+        try:
+            b = btas.Batch()
+            for _, Wd, D in items:
+                b.add_apsp(Wd, D)
+            b.launch()
+            b.wait()
+            b.close()
+        finally:
+            os.environ.pop("BTAS_BATCH_NO_U16", None)
+        for W, _, D in items:
+            np.testing.assert_array_equal(host(D), oracle_mod.floyd_warshall(W), err_msg=f"no16={no16}")
+    srv = btas.Server(1 << 30)
+    outs = []
+    for W, _, _ in items:
+        Wh = torch.from_numpy(W).pin_memory()
+        Dh = torch.empty_like(Wh).pin_memory()
+        srv.submit_apsp(Wh, Dh)
+        outs.append((W, Dh))
+    srv.wait_all(120)
+    srv.close()
+    for W, Dh in outs:
+        np.testing.assert_array_equal(Dh.numpy(), oracle_mod.floyd_warshall(W))
