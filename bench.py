@@ -54,9 +54,11 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-graphs", type=int, default=512)
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-tune", action="store_true",
+                   help="skip the autotuner (kernels then come from the built-in defaults)")
     p.add_argument("--serve-requests", type=int, default=300)
     p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
-    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next"],
+    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next", "tune"],
                    help="profiling aids: run one part alone and print its JSON (not a bench line)")
     return p.parse_args()
 
@@ -217,6 +219,21 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------ GPU arm
+def autotune(btas, combos):
+    """Run the library's autotuner once per (semiring, dtype, m, n, k); the
+    library then uses the winners for those size buckets.  Untimed set-up."""
+    names = {btas.I32: "i32", btas.F32: "f32", btas.U16: "u16"}
+    out = {}
+    t0 = time.perf_counter()
+    for sr, dt, m, n, k in combos:
+        r = btas.tune_gemm(sr, dt, m, n, k)
+        key = f"{names[dt]}_{'min' if sr == btas.MINPLUS else 'max'}_{m}x{n}x{k}"
+        out[key] = {"variant": r["variant"], "ns": r["ns"], "cfg": r["cfg"], "tile": [r["tile_m"], r["tile_n"]],
+                    "group_m": r["group_m"], "candidates": r["candidates"],
+                    "top_s": round(r["terms_per_second"] / 1e12, 2)}
+    return out, round(time.perf_counter() - t0, 1)
+
+
 def run_btas(args):
     import numpy as np
     import torch
@@ -235,6 +252,10 @@ def run_btas(args):
     D = torch.empty((n, n), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     n3 = float(n) ** 3
+    tuned, tune_s = ({}, 0.0)
+    if not args.no_tune:
+        tuned, tune_s = autotune(btas, [(sr, dt, n, n, n) for dt in (btas.I32, btas.F32) for sr in (0, 1)] +
+                                 [(0, btas.U16, n, n, n)])
 
     # APSP: squarings actually computed (early exit) for this fixed graph
     _, info = btas.apsp(dev["W"], out=D, info=True)
@@ -355,6 +376,7 @@ def run_btas(args):
         "issue_probe_terms_per_clk_per_sm": probe,
         "clocks": clocks,
         "gpu_launches": launches,
+        "autotune": {"choices": tuned, "tuning_s": tune_s} if tuned else "off (built-in defaults)",
     }
 
     if not args.no_e2e:
@@ -407,11 +429,28 @@ def batched(args, btas, torch):
     def run_batch():
         b.launch()
 
-    def run_loop():
-        for W, D in zip(Ws, Ls):
-            btas.apsp(W, out=D, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32)
-        for A, B_, C in zip(As, Bs, Cl):
-            btas.gemm(A, B_, btas.MAXPLUS, out=C)
+    # two single-call modes: adaptive precision (u16x2 where exact; reads a
+    # flag back after every squaring) and int32 kernels with the device-side
+    # early exit (no host round trips); the baseline is the faster one
+    def loop_with(flags):
+        def run():
+            for W, D in zip(Ws, Ls):
+                btas.apsp(W, out=D, flags=flags)
+            for A, B_, C in zip(As, Bs, Cl):
+                btas.gemm(A, B_, btas.MAXPLUS, out=C)
+        return run
+
+    # the one-call-per-problem baseline runs the autotuner's kernels: one
+    # tuning run per size bucket (largest size of the bucket) and kernel family
+    tuned = 0
+    if not args.no_tune:
+        by_bucket = {}
+        for n in sizes:
+            bkt = int(n - 1).bit_length()
+            by_bucket[bkt] = max(by_bucket.get(bkt, 0), int(n))
+        combos = [(sr, dt, n, n, n) for n in sorted(by_bucket.values())
+                  for sr, dt in ((0, btas.U16), (0, btas.I32), (1, btas.F32))]
+        tuned = len(autotune(btas, combos)[0])
 
     def timed(fn, reps=3):
         fn()
@@ -430,10 +469,18 @@ def batched(args, btas, torch):
 
     t_batch = timed(run_batch)
     b.wait()
-    l0 = btas.btas_kernel_launches()
-    t_loop = timed(run_loop)
-    loop_launches = (btas.btas_kernel_launches() - l0) // 4
-    same = all(torch.equal(x, y) for x, y in zip(Ds, Ls)) and all(torch.equal(x, y) for x, y in zip(Cs, Cl))
+    modes = {"adaptive": btas.APSP_EARLY_EXIT, "int32_device_exit": btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32}
+    loop_t, loop_l, same = {}, {}, True
+    for name, flags in modes.items():
+        l0 = btas.btas_kernel_launches()
+        loop_t[name] = timed(loop_with(flags))
+        loop_l[name] = (btas.btas_kernel_launches() - l0) // 4
+        same = same and all(torch.equal(x, y) for x, y in zip(Ds, Ls)) and \
+            all(torch.equal(x, y) for x, y in zip(Cs, Cl))
+        for L in Ls:
+            L.fill_(-1)
+    best = min(loop_t, key=loop_t.get)
+    t_loop, loop_launches = loop_t[best], loop_l[best]
     gemm_terms = float(sum(int(n) ** 3 for n in sizes))
     tasks = b.tasks
     b.close()
@@ -442,7 +489,9 @@ def batched(args, btas, torch):
             "graphs_per_s": round(G / t_batch, 1), "loop_graphs_per_s": round(G / t_loop, 1),
             "speedup_vs_one_launch_per_problem": round(t_loop / t_batch, 3),
             "batch_launches": 1, "loop_launches": int(loop_launches), "tasks": tasks,
-            "gemm_terms": gemm_terms, "identical_results": bool(same)}
+            "gemm_terms": gemm_terms, "identical_results": bool(same),
+            "loop_kernels": f"autotuned ({tuned} size-bucket entries)" if tuned else "built-in defaults",
+            "loop_apsp_mode": best, "loop_ms_by_mode": {k: round(v * 1e3, 3) for k, v in loop_t.items()}}
 
 
 def serve(args, btas, torch):
@@ -665,6 +714,11 @@ def run_only(args):
         print(json.dumps({"only": "kernels", "n": n, "ms": t}))
     elif args.only == "batched":
         print(json.dumps({"only": "batched", **batched(args, btas, torch)}))
+    elif args.only == "tune":
+        n = args.n
+        combos = [(sr, dt, n, n, n) for dt in (btas.I32, btas.F32) for sr in (0, 1)] + [(0, btas.U16, n, n, n)]
+        choices, secs = autotune(btas, combos)
+        print(json.dumps({"only": "tune", "n": n, "tuning_s": secs, "choices": choices}))
     elif args.only == "next":
         print(json.dumps({"only": "next", **next_rows(args, btas, torch)}))
     else:

@@ -313,6 +313,75 @@ int btas_apsp_squarings(int64_t n);
 btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Autotuner for the tropical product kernels (the product of Eq. 1-4, and
+ * the squarings of the Sec. III APSP that call it).  The paper fixes one
+ * GPU kernel shape; this library has several compiled tile shapes and
+ * inner-loop variants, all with identical results, and picks among them by
+ * measurement on the device at hand.
+ *
+ * Key: (compute capability, SM count, semiring, dtype, size buckets of m, n
+ * and k), where the bucket of x is ceil(log2(x)).  Value: the fastest kernel
+ * (inner-loop variant, IMAD-path column count ns, tile configuration) and
+ * the tile raster group (a schedule parameter).
+ *
+ * Kernel choice in btas_gemm, btas_apsp/_ex, btas_closure, btas_apsp_paths
+ * and btas_apsp_fw, in this order: explicit environment overrides
+ * (BTAS_CFG, BTAS_I32_VARIANT, BTAS_I32_NS, BTAS_F32_VARIANT, BTAS_U16_NS);
+ * then a table entry for the key; then, if the environment sets BTAS_TUNE=1
+ * and the stream is not being captured, a tuning run on the spot (it
+ * synchronises the stream once and allocates scratch); then the built-in
+ * defaults.  BTAS_TUNE_CACHE=<path> loads that file into the table on first
+ * use, and an on-the-spot tuning run appends the table back to it.
+ * btas_apsp_noalloc and the batched/server paths do not consult the table.
+ *
+ * btas_tune_gemm : times every compiled candidate for (semiring, dtype) at
+ *                  m x n x k on `stream` (device scratch operands with
+ *                  seeded values in the dtype's domain, INF entries
+ *                  included; the caller's memory is not touched), checks
+ *                  that every candidate's result equals the first one's bit
+ *                  for bit (BTAS_ERR_INTERNAL otherwise), then times the
+ *                  winner's raster groups, stores the best in the table and
+ *                  fills *out (may be NULL).  Synchronises `stream`; takes
+ *                  about 20 ms per candidate plus four products each.
+ *                  semiring: BTAS_MINPLUS/BTAS_MAXPLUS; dtype: BTAS_I32,
+ *                  BTAS_F32, or BTAS_U16 (min-plus only).  m, n, k >= 1.
+ * btas_tune_lookup: 1 and *out filled if the table has an entry for the
+ *                  key of the current device, else 0.
+ * btas_tune_save : writes the whole table (every device's entries) to
+ *                  `path`, one JSON object per line.
+ * btas_tune_load : reads such a file and adds its entries (replacing equal
+ *                  keys).  A malformed line, or a kernel this build does
+ *                  not have, returns BTAS_ERR_ARG and adds nothing.
+ *                  *loaded (may be NULL) receives the number of entries.
+ * btas_tune_clear / btas_tune_entries: empty / count the table.
+ * Thread safety: the table is guarded by a lock; tuning itself runs
+ * unlocked, so two threads tuning the same key both measure and the later
+ * store wins.
+ * ------------------------------------------------------------------------ */
+#define BTAS_ERR_INTERNAL 8 /* a self-check failed (tuning candidates disagree) */
+
+typedef struct {
+    int variant;             /* inner loop: 0 int32 DPX, 1 int32 IMAD/3-input-min mix,
+                                2 fp32 add.f32x2, 3 fp32 scalar, 4 fp32 two adds + 3-input min,
+                                16 packed u16x2 */
+    int ns;                  /* columns (of 8) on the IMAD path; 0 if not applicable */
+    int cfg;                 /* tile configuration id (u16: 0) */
+    int tile_m, tile_n;      /* CTA output tile */
+    int group_m;             /* tile-raster group height */
+    int candidates;          /* kernels timed */
+    double seconds;          /* best time of one product */
+    double terms_per_second; /* m*n*k / seconds */
+} btas_tune_result;
+
+btas_status btas_tune_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, btas_tune_result *out,
+                           void *stream);
+int btas_tune_lookup(int semiring, int dtype, int64_t m, int64_t n, int64_t k, btas_tune_result *out);
+btas_status btas_tune_save(const char *path);
+btas_status btas_tune_load(const char *path, int *loaded);
+void btas_tune_clear(void);
+int btas_tune_entries(void);
+
+/* ------------------------------------------------------------------------
  * Batched execution: many independent tropical products and APSP solves of
  * uneven sizes in ONE persistent kernel launch (captured once in a CUDA
  * graph and replayed).  Same arithmetic and bit-identical results as the

@@ -37,7 +37,8 @@ I32_FINITE_MAX = 1 << 28
 INF_U16 = 0x7FFF
 
 STATUS = {0: "BTAS_OK", 1: "BTAS_ERR_ARG", 2: "BTAS_ERR_BOUND", 3: "BTAS_ERR_NOMEM", 4: "BTAS_ERR_CUDA",
-          5: "BTAS_ERR_TIMEOUT", 6: "BTAS_ERR_BUDGET", 7: "BTAS_ERR_UNSUPPORTED"}
+          5: "BTAS_ERR_TIMEOUT", 6: "BTAS_ERR_BUDGET", 7: "BTAS_ERR_UNSUPPORTED", 8: "BTAS_ERR_INTERNAL"}
+TUNE_VARIANT_U16 = 16
 
 
 class BtasError(RuntimeError):
@@ -86,7 +87,23 @@ SIGNATURES = {
     "btas_server_wait_all": (_i32, [_vp, ctypes.c_double]),
     "btas_server_stats": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "btas_server_destroy": (_i32, [_vp]),
+    "btas_tune_gemm": (_i32, [_i32, _i32, _i64, _i64, _i64, _vp, _vp]),
+    "btas_tune_lookup": (_i32, [_i32, _i32, _i64, _i64, _i64, _vp]),
+    "btas_tune_save": (_i32, [ctypes.c_char_p]),
+    "btas_tune_load": (_i32, [ctypes.c_char_p, _vp]),
+    "btas_tune_clear": (None, []),
+    "btas_tune_entries": (_i32, []),
 }
+
+
+class TuneResult(ctypes.Structure):
+    """btas_tune_result (include/btas.h)."""
+    _fields_ = [("variant", ctypes.c_int), ("ns", ctypes.c_int), ("cfg", ctypes.c_int), ("tile_m", ctypes.c_int),
+                ("tile_n", ctypes.c_int), ("group_m", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("seconds", ctypes.c_double), ("terms_per_second", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 def lib():
@@ -553,3 +570,61 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ autotuner
+def btas_tune_gemm(semiring, dtype, m, n, k, out_ptr, stream) -> int:
+    return lib().btas_tune_gemm(semiring, dtype, m, n, k, out_ptr, stream)
+
+
+def btas_tune_lookup(semiring, dtype, m, n, k, out_ptr) -> int:
+    return lib().btas_tune_lookup(semiring, dtype, m, n, k, out_ptr)
+
+
+def btas_tune_save(path) -> int:
+    return lib().btas_tune_save(os.fsencode(path))
+
+
+def btas_tune_load(path, loaded_ptr) -> int:
+    return lib().btas_tune_load(os.fsencode(path), loaded_ptr)
+
+
+def btas_tune_clear() -> None:
+    lib().btas_tune_clear()
+
+
+def btas_tune_entries() -> int:
+    return lib().btas_tune_entries()
+
+
+def tune_gemm(semiring, dtype, m, n, k, stream=None) -> dict:
+    """Time every compiled kernel for (semiring, dtype) at m x n x k, keep the
+    fastest in the tuning table and return it as a dict (btas_tune_result)."""
+    r = TuneResult()
+    check(btas_tune_gemm(_sr(semiring), dtype, m, n, k, ctypes.addressof(r), _stream(stream)))
+    return r.as_dict()
+
+
+def tune_lookup(semiring, dtype, m, n, k):
+    """The table's entry for this problem's size buckets on the current
+    device, or None."""
+    r = TuneResult()
+    return r.as_dict() if btas_tune_lookup(_sr(semiring), dtype, m, n, k, ctypes.addressof(r)) else None
+
+
+def tune_save(path) -> None:
+    check(btas_tune_save(path))
+
+
+def tune_load(path) -> int:
+    c = ctypes.c_int()
+    check(btas_tune_load(path, ctypes.addressof(c)))
+    return c.value
+
+
+def tune_clear() -> None:
+    btas_tune_clear()
+
+
+def tune_entries() -> int:
+    return btas_tune_entries()

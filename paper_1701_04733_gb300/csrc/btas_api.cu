@@ -76,14 +76,27 @@ int env_int(const char *name, int dflt) {
     return v && *v ? atoi(v) : dflt;
 }
 
-// Kernel choice.  Defaults come from measurement on GB300 (8192^3: the
-// 2-CTA/SM, 64-bit-fragment tiles reach the measured issue ceilings of their
-// instruction mixes): int32 = IMAD/3-input-min mix on 4 of 8 columns, fp32 =
-// add.f32x2 + 3-input min; 64 x 64 tiles when fewer than 2 waves of 128 x 128
-// tiles exist.  BTAS_I32_VARIANT (0 = DPX, 1 = mixed), BTAS_I32_NS,
-// BTAS_F32_VARIANT (2 = f32x2, 3 = scalar, 4 = two scalar adds + 3-input min)
-// and BTAS_CFG override them.
-const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n) {
+// Kernel choice.  Explicit environment overrides win: BTAS_I32_VARIANT (0 =
+// DPX, 1 = mixed), BTAS_I32_NS, BTAS_F32_VARIANT (2 = f32x2, 3 = scalar, 4 =
+// two scalar adds + 3-input min) and BTAS_CFG.  Otherwise an autotuner entry
+// for the problem's size buckets (tune.cu), else the defaults measured on
+// GB300 at 8192^3, where the 2-CTA/SM, 64-bit-fragment tiles reach the
+// measured issue ceilings of their instruction mixes: int32 = IMAD/3-input-min
+// mix on 4 of 8 columns, fp32 = add.f32x2 + 3-input min; 64 x 64 tiles when
+// fewer than 2 waves of 128 x 128 tiles exist.
+const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n, long long k, cudaStream_t st,
+                                int *group_m) {
+    *group_m = 8;
+    const bool forced = getenv("BTAS_I32_VARIANT") || getenv("BTAS_I32_NS") || getenv("BTAS_F32_VARIANT") ||
+                        getenv("BTAS_CFG");
+    TuneChoice c{};
+    if (!forced && tune_choice(sr, dtype, m, n, k, st, &c)) {
+        const GemmKernel *t = find_gemm_kernel(c.var, sr, c.ns, c.cfg);
+        if (t) {
+            *group_m = c.group_m;
+            return t;
+        }
+    }
     int var, ns = 0;
     if (dtype == BTAS_F32) {
         var = env_int("BTAS_F32_VARIANT", kF32X2);
@@ -93,21 +106,31 @@ const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n) {
     }
     const long long big_tiles = ((m + 127) / 128) * ((n + 127) / 128);
     int cfg = env_int("BTAS_CFG", big_tiles >= 2 * 152 ? 4 : 2);
-    const GemmKernel *k = find_gemm_kernel(var, sr, ns, cfg);
-    if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Mix, sr, 5, cfg);
-    if (!k) k = find_gemm_kernel(var, sr, ns, 0);
-    if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Mix, sr, 5, 0);
-    if (!k && dtype == BTAS_I32) k = find_gemm_kernel(kI32Dpx, sr, 0, 0);
-    if (!k && dtype == BTAS_F32) k = find_gemm_kernel(kF32X2, sr, 0, 0);
-    return k;
+    const GemmKernel *kk = find_gemm_kernel(var, sr, ns, cfg);
+    if (!kk && dtype == BTAS_I32) kk = find_gemm_kernel(kI32Mix, sr, 5, cfg);
+    if (!kk) kk = find_gemm_kernel(var, sr, ns, 0);
+    if (!kk && dtype == BTAS_I32) kk = find_gemm_kernel(kI32Mix, sr, 5, 0);
+    if (!kk && dtype == BTAS_I32) kk = find_gemm_kernel(kI32Dpx, sr, 0, 0);
+    if (!kk && dtype == BTAS_F32) kk = find_gemm_kernel(kF32X2, sr, 0, 0);
+    return kk;
+}
+
+// IMAD/DPX split of the packed u16x2 kernel: BTAS_U16_NS, else the
+// autotuner's entry, else 5.
+int u16_ns(long long m, long long n, long long k, cudaStream_t st) {
+    if (getenv("BTAS_U16_NS")) return env_int("BTAS_U16_NS", 5);
+    TuneChoice c{};
+    if (tune_choice(kMin, BTAS_U16, m, n, k, st, &c)) return c.ns;
+    return 5;
 }
 
 // Run the NT kernel on A (m x k) and Bt (n x k).
 btas_status run_nt(int dtype, int sr, const GemmArgs &a, cudaStream_t st) {
-    const GemmKernel *k = select_kernel(dtype, sr, a.m, a.n);
+    int group_m = 8;
+    const GemmKernel *k = select_kernel(dtype, sr, a.m, a.n, a.k, st, &group_m);
     if (!k) return fail(BTAS_ERR_UNSUPPORTED, "no kernel for dtype %d semiring %d", dtype, sr);
     GemmArgs args = a;
-    args.group_m = 8;
+    args.group_m = group_m;
     args.one = 1;
     BTAS_CUDA(k->launch(args, st), "tropical gemm launch");
     return BTAS_OK;
@@ -124,13 +147,22 @@ namespace btas {
 void record_error(const char *msg) { g_err = msg; }
 
 const GemmKernel *find_gemm_kernel(int var, int sr, int ns, int cfg) {
-    const GemmKernel *tabs[3] = {kGemmI32Dpx, kGemmI32Mix, kGemmF32};
-    const int counts[3] = {kGemmI32DpxCount, kGemmI32MixCount, kGemmF32Count};
-    for (int t = 0; t < 3; ++t)
-        for (int i = 0; i < counts[t]; ++i) {
-            const GemmKernel &k = tabs[t][i];
-            if (k.var == var && k.sr == sr && k.cfg == cfg && (var != kI32Mix || k.ns == ns)) return &k;
-        }
+    for (int i = 0; i < gemm_kernel_count(); ++i) {
+        const GemmKernel &k = *gemm_kernel_at(i);
+        if (k.var == var && k.sr == sr && k.cfg == cfg && (var != kI32Mix || k.ns == ns)) return &k;
+    }
+    return nullptr;
+}
+
+int gemm_kernel_count() { return kGemmI32DpxCount + kGemmI32MixCount + kGemmF32Count; }
+
+const GemmKernel *gemm_kernel_at(int i) {
+    if (i < 0) return nullptr;
+    if (i < kGemmI32DpxCount) return &kGemmI32Dpx[i];
+    i -= kGemmI32DpxCount;
+    if (i < kGemmI32MixCount) return &kGemmI32Mix[i];
+    i -= kGemmI32MixCount;
+    if (i < kGemmF32Count) return &kGemmF32[i];
     return nullptr;
 }
 }  // namespace btas
@@ -190,7 +222,7 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
         if (accumulate) return fail(BTAS_ERR_UNSUPPORTED, "btas_gemm: BTAS_U16 accumulate");
         Workspace ws(st);
         BTAS_CUDA(ws.alloc((size_t)m * ((k + 3) & ~3LL) * 4), "workspace alloc");
-        BTAS_CUDA(launch_tgemm_u16_ws(a, static_cast<uint32_t *>(ws.p), env_int("BTAS_U16_NS", 5), st),
+        BTAS_CUDA(launch_tgemm_u16_ws(a, static_cast<uint32_t *>(ws.p), u16_ns(m, n, k, st), st),
                   "u16 gemm launch");
         return BTAS_OK;
     }
@@ -480,7 +512,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     const bool no_carrier = env_int("BTAS_APSP_NO_CARRIER", 0) != 0;
     int *chg = dflags;
     int *mxs = dflags + S + 4;
-    const int ns16 = env_int("BTAS_U16_NS", 5);
+    int ns16 = -1;  // looked up at the first packed squaring
     auto other = [&](const void *p) -> void * { return p == (const void *)X ? (void *)Y : (void *)X; };
     // convert an n x n matrix between representations (T is free scratch here)
     auto convert = [&](int from, int to, const void *src, void *dst) -> cudaError_t {
@@ -519,6 +551,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
             a.changed = &chg[s];
             a.one = 1;
             a.maxfin = &mxs[s];
+            if (ns16 < 0) ns16 = u16_ns(n, n, n, st);
             BTAS_CUDA(launch_tgemm_u16_ws(a, reinterpret_cast<uint32_t *>(T), ns16, st), "u16 squaring");
         } else {
             const long long ldt = (n + 3) & ~3LL;

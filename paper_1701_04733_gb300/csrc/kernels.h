@@ -23,6 +23,17 @@ struct GemmKernel {
     cudaError_t (*launch)(const GemmArgs &, cudaStream_t);
 };
 const GemmKernel *find_gemm_kernel(int var, int sr, int ns, int cfg);
+int gemm_kernel_count();
+const GemmKernel *gemm_kernel_at(int i);
+
+// ---- autotuner (tune.cu)
+struct TuneChoice {
+    int var, ns, cfg, group_m;  // var 16: packed u16x2 kernel (ns = its IMAD split)
+};
+// Tuned kernel for (sr, dtype, m, n, k) on the current device: a table entry,
+// or -- when BTAS_TUNE=1 and `st` is not capturing -- a tuning run on the
+// spot.  false: no choice (use the defaults).
+bool tune_choice(int sr, int dtype, long long m, long long n, long long k, cudaStream_t st, TuneChoice *out);
 
 // ---- auxiliary kernels (aux.cu)
 // dst (cols x rows, ldd) = transpose of src (rows x cols, lds); 4-byte elements.
