@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-graphs", type=int, default=512)
+    p.add_argument("--batched-profile", action="store_true",
+                   help="also run one profiled launch and report cycles per task kind")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-tune", action="store_true",
                    help="skip the autotuner (kernels then come from the built-in defaults)")
@@ -484,6 +486,22 @@ def batched(args, btas, torch):
     gemm_terms = float(sum(int(n) ** 3 for n in sizes))
     tasks = b.tasks
     b.close()
+    prof = None
+    if args.batched_profile:
+        pb = btas.Batch(profile=True)
+        for W, D in zip(Ws, Ls):
+            pb.add_apsp(W, D)
+        for A, B_, C in zip(As, Bs, Cl):
+            pb.add_gemm(A, B_, C, btas.MAXPLUS)
+        pb.launch()
+        pb.wait()
+        raw = pb.profile()
+        pb.close()
+        total = sum(v["cycles"] for k, v in raw.items() if k != "wait") or 1
+        mhz = peaks().get("sm_max_mhz") or 2070.0
+        prof = {k: {"tasks": v["tasks"], "share_of_task_cycles": round(v["cycles"] / total, 4),
+                    "us_per_task": round(v["cycles"] / max(v["tasks"], 1) / mhz, 2)}
+                for k, v in raw.items() if v["tasks"]}
     return {"workload": f"{G} APSP graphs n~U[32,1024] p=0.1 w[1,100] int32 + {G} fp32 max-plus products same sizes",
             "batch_ms": round(t_batch * 1e3, 3), "loop_ms": round(t_loop * 1e3, 3),
             "graphs_per_s": round(G / t_batch, 1), "loop_graphs_per_s": round(G / t_loop, 1),
@@ -491,6 +509,7 @@ def batched(args, btas, torch):
             "batch_launches": 1, "loop_launches": int(loop_launches), "tasks": tasks,
             "gemm_terms": gemm_terms, "identical_results": bool(same),
             "loop_kernels": f"autotuned ({tuned} size-bucket entries)" if tuned else "built-in defaults",
+            "profile": prof,
             "loop_apsp_mode": best, "loop_ms_by_mode": {k: round(v * 1e3, 3) for k, v in loop_t.items()}}
 
 

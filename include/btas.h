@@ -413,9 +413,31 @@ int btas_tune_entries(void);
  * btas_batch_destroy : frees the plan and the batch (call after the work has
  *                      completed).
  * btas_batch_workspace_bytes / btas_batch_tasks: plan size diagnostics.
+ * btas_batch_profile : tracing.  With BTAS_BATCH_PROFILE at create, every
+ *                      CTA adds, per task, the SM clock cycles its first
+ *                      thread spent on the task to a per-kind slot
+ *                      (BTAS_BATCH_SLOT_*), and the cycles it spent in the
+ *                      dependency wait to BTAS_BATCH_SLOT_WAIT.  Sums run
+ *                      over all launches since the plan was built.  Fills
+ *                      cycles[i] and counts[i] for i < min(slots,
+ *                      BTAS_BATCH_PROFILE_SLOTS) after synchronising the
+ *                      device; BTAS_ERR_ARG if the batch was created without
+ *                      the flag or has not been launched.
  * ------------------------------------------------------------------------ */
 typedef struct btas_batch_t btas_batch_t;
 #define BTAS_BATCH_NO_GRAPH 0x1
+#define BTAS_BATCH_PROFILE 0x2
+#define BTAS_BATCH_PROFILE_SLOTS 10
+#define BTAS_BATCH_SLOT_TRANSPOSE 0   /* level-0 transposes (and 16-bit forms) */
+#define BTAS_BATCH_SLOT_COPY 1        /* n <= 2 APSP: D = W */
+#define BTAS_BATCH_SLOT_APSP_U16 2    /* APSP squaring tile, packed u16x2 */
+#define BTAS_BATCH_SLOT_APSP_I32 3    /* APSP squaring tile, int32 */
+#define BTAS_BATCH_SLOT_APSP_DONE 4   /* APSP squaring tile after convergence (copy through) */
+#define BTAS_BATCH_SLOT_GEMM_I32 5    /* product tile, int32 */
+#define BTAS_BATCH_SLOT_GEMM_F32 6    /* product tile, fp32 */
+#define BTAS_BATCH_SLOT_SQUARE_U16 7  /* server single-squaring tile, u16x2 */
+#define BTAS_BATCH_SLOT_SQUARE_I32 8  /* server single-squaring tile, int32 */
+#define BTAS_BATCH_SLOT_WAIT 9        /* waiting for the previous level */
 btas_status btas_batch_create(btas_batch_t **out, int flags);
 btas_status btas_batch_add_apsp(btas_batch_t *b, int64_t n, const int32_t *W, int32_t *D);
 btas_status btas_batch_add_gemm(btas_batch_t *b, int semiring, int dtype, int64_t m, int64_t n, int64_t k,
@@ -425,6 +447,7 @@ btas_status btas_batch_wait(btas_batch_t *b, void *stream);
 btas_status btas_batch_destroy(btas_batch_t *b);
 int64_t btas_batch_workspace_bytes(btas_batch_t *b);
 int btas_batch_tasks(btas_batch_t *b);
+btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *counts, int slots);
 
 /* ------------------------------------------------------------------------
  * Continuous-batching server: requests with HOST buffers (contiguous

@@ -39,6 +39,10 @@ INF_U16 = 0x7FFF
 STATUS = {0: "BTAS_OK", 1: "BTAS_ERR_ARG", 2: "BTAS_ERR_BOUND", 3: "BTAS_ERR_NOMEM", 4: "BTAS_ERR_CUDA",
           5: "BTAS_ERR_TIMEOUT", 6: "BTAS_ERR_BUDGET", 7: "BTAS_ERR_UNSUPPORTED", 8: "BTAS_ERR_INTERNAL"}
 TUNE_VARIANT_U16 = 16
+BATCH_PROFILE = 0x2
+BATCH_PROFILE_SLOTS = 10
+BATCH_SLOT_NAMES = ("transpose", "copy", "apsp_u16", "apsp_i32", "apsp_done", "gemm_i32", "gemm_f32",
+                    "square_u16", "square_i32", "wait")
 
 
 class BtasError(RuntimeError):
@@ -80,6 +84,7 @@ SIGNATURES = {
     "btas_batch_destroy": (_i32, [_vp]),
     "btas_batch_workspace_bytes": (_i64, [_vp]),
     "btas_batch_tasks": (_i32, [_vp]),
+    "btas_batch_profile": (_i32, [_vp, _vp, _vp, _i32]),
     "btas_server_create": (_i32, [_vp, _i64, _i32]),
     "btas_server_submit_apsp": (_i32, [_vp, _i64, _vp, _vp, _vp]),
     "btas_server_submit_gemm": (_i32, [_vp, _i32, _i32, _i64, _i64, _i64, _vp, _vp, _vp, _vp]),
@@ -311,6 +316,10 @@ def btas_batch_tasks(b) -> int:
     return lib().btas_batch_tasks(b)
 
 
+def btas_batch_profile(b, cycles_ptr, counts_ptr, slots) -> int:
+    return lib().btas_batch_profile(b, cycles_ptr, counts_ptr, slots)
+
+
 # ------------------------------------------------------- torch helpers
 def _torch():
     import torch
@@ -461,9 +470,10 @@ class Batch:
     """Many APSP solves and tropical products in one persistent launch
     (btas_batch_*).  Keep the tensors alive until `wait()` returns."""
 
-    def __init__(self, graph: bool = True):
+    def __init__(self, graph: bool = True, profile: bool = False):
         h = ctypes.c_void_p()
-        check(btas_batch_create(ctypes.addressof(h), 0 if graph else BATCH_NO_GRAPH))
+        flags = (0 if graph else BATCH_NO_GRAPH) | (BATCH_PROFILE if profile else 0)
+        check(btas_batch_create(ctypes.addressof(h), flags))
         self.handle = h.value
         self._keep = []
 
@@ -494,6 +504,15 @@ class Batch:
     @property
     def tasks(self) -> int:
         return btas_batch_tasks(self.handle)
+
+    def profile(self) -> dict:
+        """Per-task-kind SM cycles and task counts, summed over every launch
+        (batch created with profile=True); synchronises the device."""
+        cyc = (ctypes.c_uint64 * BATCH_PROFILE_SLOTS)()
+        cnt = (ctypes.c_uint64 * BATCH_PROFILE_SLOTS)()
+        check(lib().btas_batch_profile(self.handle, ctypes.addressof(cyc), ctypes.addressof(cnt),
+                                       BATCH_PROFILE_SLOTS))
+        return {name: {"cycles": int(cyc[i]), "tasks": int(cnt[i])} for i, name in enumerate(BATCH_SLOT_NAMES)}
 
     @property
     def workspace_bytes(self) -> int:

@@ -14,9 +14,10 @@
 // status word and stops, and the other CTAs see the word and stop too.
 //
 // An APSP squaring tile also stores its output transposed (through shared
-// memory), so the next squaring finds its B operand ready; a squaring whose
-// predecessor changed nothing copies its input through (early exit with an
-// unchanged result).  The launch (counter reset + kernel) is captured once in
+// memory), so the next squaring finds its B operand ready.  Early exit: the
+// first squaring whose predecessor changed nothing copies that fixpoint into
+// D, and the squarings after it do nothing (the result is unchanged).  The
+// launch (counter reset + kernel) is captured once in
 // a CUDA graph and replayed.
 #include <algorithm>
 #include <cstring>
@@ -54,17 +55,32 @@ __device__ __forceinline__ void transpose_tile(const uint32_t *src, long long ld
     const int tiles_c = (cols + kBT - 1) / kBT;
     const int r0 = (tile / tiles_c) * kBT, c0 = (tile % tiles_c) * kBT;
     int mx = -1;
-    for (int idx = tid; idx < kBT * kBT; idx += BCfg::kThreads) {
-        const int r = idx / kBT, c = idx % kBT;
-        if (r0 + r < rows && c0 + c < cols) {
-            const uint32_t v = __ldcg(src + (long long)(r0 + r) * lds + c0 + c);
-            sm[c * (kBT + 1) + r] = v;
-            if (Cd != nullptr) {
-                const int iv = static_cast<int>(v);
-                const uint32_t u = iv >= BTAS_INF_U16 ? BTAS_INF_U16 : (uint32_t)iv;
-                Cd[(long long)(r0 + r) * ldcd + c0 + c] = u * 0x10001u;
-                Cu[(long long)(r0 + r) * ldcu + c0 + c] = (uint16_t)u;
-                if (iv < kInfI32) mx = max(mx, iv);
+    // loads in batches of 16 per thread (coalesced along rows), so several
+    // are in flight before the shared-memory and 16-bit-form stores
+    constexpr int PER = kBT * kBT / BCfg::kThreads, BATCH = 16;
+    static_assert(PER % BATCH == 0, "whole batches");
+#pragma unroll 1
+    for (int b0 = 0; b0 < PER; b0 += BATCH) {
+        uint32_t v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int idx = tid + (b0 + u) * BCfg::kThreads;
+            const int r = idx / kBT, c = idx % kBT;
+            v[u] = (r0 + r < rows && c0 + c < cols) ? __ldcg(src + (long long)(r0 + r) * lds + c0 + c) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int idx = tid + (b0 + u) * BCfg::kThreads;
+            const int r = idx / kBT, c = idx % kBT;
+            if (r0 + r < rows && c0 + c < cols) {
+                sm[c * (kBT + 1) + r] = v[u];
+                if (Cd != nullptr) {
+                    const int iv = static_cast<int>(v[u]);
+                    const uint32_t h = iv >= BTAS_INF_U16 ? BTAS_INF_U16 : (uint32_t)iv;
+                    Cd[(long long)(r0 + r) * ldcd + c0 + c] = h * 0x10001u;
+                    Cu[(long long)(r0 + r) * ldcu + c0 + c] = (uint16_t)h;
+                    if (iv < kInfI32) mx = max(mx, iv);
+                }
             }
         }
     }
@@ -92,7 +108,9 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_task[4];
     __shared__ int s_flag;
+    __shared__ int s_flag2;
     __shared__ int s_m;
+    __shared__ long long s_wait;
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) {
@@ -101,7 +119,9 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             if (t < p.total && ld_acquire(p.status) == 0) w = p.tasks[t];
             s_task[0] = w.x; s_task[1] = w.y; s_task[2] = w.z; s_task[3] = w.w;
             s_flag = 1;
+            s_flag2 = 1;
             s_m = 0x7FFFFFFF;
+            s_wait = 0;
             if (w.x >= 0 && w.z > 0) {
                 // wait until every task of the previous level of this instance is done
                 const BInst &I = p.insts[w.y];
@@ -117,20 +137,27 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                     }
                     __nanosleep(200);
                 }
+                s_wait = clock64() - t0;
                 if (s_task[0] >= 0 && I.kind == kInstApsp && w.z >= 2)
                     s_flag = ld_acquire(p.changed + I.flag_base + w.z - 1);
+                if (s_task[0] >= 0 && I.kind == kInstApsp && w.z >= 3)
+                    s_flag2 = ld_acquire(p.changed + I.flag_base + w.z - 2);
                 if (s_task[0] >= 0 && I.kind == kInstApsp) s_m = ld_acquire(p.maxfin + I.flag_base + w.z - 1);
             }
         }
         __syncthreads();
         const int type = s_task[0], inst = s_task[1], level = s_task[2], tile = s_task[3];
         const int prev_changed = s_flag;
+        const int prev_changed2 = s_flag2;
         const int prev_max = s_m;
         __syncthreads();
         if (type < 0) break;
+        const long long t_task = clock64();
+        int slot = BTAS_BATCH_SLOT_COPY;
         const BInst I = p.insts[inst];
         bool ch = false;
         if (type == kTaskTranspose) {
+            slot = BTAS_BATCH_SLOT_TRANSPOSE;
             const uint32_t *src = static_cast<const uint32_t *>(I.kind == kInstGemm ? I.B : I.A);
             const long long lds = I.kind == kInstGemm ? I.ldb : I.lda;
             const bool forms = I.kind == kInstApsp && I.use_u16;
@@ -164,13 +191,26 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.vec_b = 1;
             // forms of D_{s-1} are in set (s-1) & 1, D_s goes to set s & 1
             const bool more = s < S && I.use_u16;
-            int *Ct = s < S ? static_cast<int *>((s & 1) ? I.Q1 : I.Q0) : nullptr;
+            // every finite entry of D_s is <= 2 max(D_{s-1}); if even 4 max(D_{s-1})
+            // < 0x7FFF, squaring s+1 is certain to run packed and needs no
+            // transposed int32 operand
+            const bool next_u16 = I.use_u16 && 4LL * prev_max < BTAS_INF_U16;
+            int *Ct = (s < S && !next_u16) ? static_cast<int *>((s & 1) ? I.Q1 : I.Q0) : nullptr;
             uint32_t *Cd = more ? ((s & 1) ? I.Ad1 : I.Ad0) : nullptr;
             uint16_t *Cu = more ? ((s & 1) ? I.U1 : I.U0) : nullptr;
             if (more) a.maxfin = p.maxfin + I.flag_base + s;
             if (s >= 2 && prev_changed == 0) {
-                copy_tile<BCfg, int>(a, bm, bn, tid);
+                // D_{s-1} == D_{s-2}: a fixpoint of the squaring.  The first
+                // such level copies it into D; the levels after it have
+                // nothing left to do.
+                slot = BTAS_BATCH_SLOT_APSP_DONE;
+                if (prev_changed2 != 0) {
+                    a.C = I.C;
+                    a.ldc = I.ldc;
+                    copy_tile<BCfg, int>(a, bm, bn, tid);
+                }
             } else if (I.use_u16 && 2LL * prev_max < BTAS_INF_U16) {
+                slot = BTAS_BATCH_SLOT_APSP_U16;
                 // every finite entry of D_{s-1} is < 0x7FFF / 2: the packed squaring is exact
                 U16Tile u{};
                 u.n = I.n;
@@ -184,6 +224,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                 u.maxfin = a.maxfin;
                 ch = u16_tile(u, bm, bn, smem_raw, tid);
             } else {
+                slot = BTAS_BATCH_SLOT_APSP_I32;
                 ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, Ct, I.ldq, Cd, I.ldq, Cu, I.ldu);
             }
         } else if (type == kTaskSquare) {
@@ -199,6 +240,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.vec_b = 1;
             a.maxfin = I.maxfin_ptr;
             if (I.use_u16) {
+                slot = BTAS_BATCH_SLOT_SQUARE_U16;
                 U16Tile u{};
                 u.n = I.n;
                 u.Ad = I.Ad0; u.ldad = I.ldq;
@@ -211,6 +253,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                 u.maxfin = I.maxfin_ptr;
                 ch = u16_tile(u, bm, bn, smem_raw, tid);
             } else {
+                slot = BTAS_BATCH_SLOT_SQUARE_I32;
                 ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, I.Q1, I.ldq, I.Ad1, I.ldq, I.U1, I.ldu);
             }
         } else {  // kTaskGemm
@@ -223,6 +266,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.one = 1;
             a.vec_a = ((reinterpret_cast<uintptr_t>(I.A) & 15) == 0) && ((I.lda & 3) == 0);
             a.vec_b = ((reinterpret_cast<uintptr_t>(a.Bt) & 15) == 0) && ((a.ldb & 3) == 0);
+            slot = I.dtype == BTAS_I32 ? BTAS_BATCH_SLOT_GEMM_I32 : BTAS_BATCH_SLOT_GEMM_F32;
             if (I.dtype == BTAS_I32) {
                 if (I.sr == kMin) gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid);
                 else gemm_tile<kI32Mix, kMax>(a, bm, bn, smem_raw, tid);
@@ -236,7 +280,17 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
         if (type == kTaskSquare && __any_sync(0xffffffffu, ch) && (tid & 31) == 0) atomicOr(I.changed_ptr, 1);
         __threadfence();
         __syncthreads();
-        if (tid == 0) atomicAdd(p.done + I.done_base + level, 1);
+        if (tid == 0) {
+            atomicAdd(p.done + I.done_base + level, 1);
+            if (p.prof != nullptr) {
+                atomicAdd(p.prof + 2 * slot, (unsigned long long)(clock64() - t_task));
+                atomicAdd(p.prof + 2 * slot + 1, 1ULL);
+                if (level > 0) {
+                    atomicAdd(p.prof + 2 * BTAS_BATCH_SLOT_WAIT, (unsigned long long)s_wait);
+                    atomicAdd(p.prof + 2 * BTAS_BATCH_SLOT_WAIT + 1, 1ULL);
+                }
+            }
+        }
     }
 }
 
@@ -285,6 +339,7 @@ struct btas_batch_t {
     size_t dev_bytes = 0;
     int total = 0;
     int *d_counters = nullptr;  // next | status | done[] | changed[]
+    unsigned long long *d_prof = nullptr;  // BTAS_BATCH_PROFILE: (cycles, count) per slot
     size_t counter_bytes = 0;
     BatchParams params{};
     int grid = 0;
@@ -317,6 +372,7 @@ void release_plan(btas_batch_t *b) {
     b->exec = nullptr;
     b->graph = nullptr;
     b->dev_mem = nullptr;
+    b->d_prof = nullptr;
 }
 
 btas_status bfail(btas_status s, const char *msg) {
@@ -393,14 +449,19 @@ btas_status build_plan(btas_batch_t *b) {
     const size_t inst_bytes = al256(ninst * sizeof(BInst));
     b->counter_bytes = al256((size_t)(2 + 3 * counters) * 4);
     b->workspace_bytes = (long long)ws;
-    b->dev_bytes = task_bytes + inst_bytes + b->counter_bytes + ws;
+    const size_t prof_bytes = (b->flags & BTAS_BATCH_PROFILE) ? al256(2 * BTAS_BATCH_PROFILE_SLOTS * 8) : 0;
+    b->dev_bytes = task_bytes + inst_bytes + b->counter_bytes + prof_bytes + ws;
     if (cudaMalloc(&b->dev_mem, b->dev_bytes ? b->dev_bytes : 256) != cudaSuccess)
         return bfail(BTAS_ERR_NOMEM, "btas_batch: workspace allocation failed");
     char *base = static_cast<char *>(b->dev_mem);
     int4 *d_tasks = reinterpret_cast<int4 *>(base);
     BInst *d_insts = reinterpret_cast<BInst *>(base + task_bytes);
     b->d_counters = reinterpret_cast<int *>(base + task_bytes + inst_bytes);
-    char *d_ws = base + task_bytes + inst_bytes + b->counter_bytes;
+    b->d_prof = prof_bytes ? reinterpret_cast<unsigned long long *>(base + task_bytes + inst_bytes + b->counter_bytes)
+                           : nullptr;
+    if (b->d_prof && cudaMemset(b->d_prof, 0, prof_bytes) != cudaSuccess)
+        return bfail(BTAS_ERR_CUDA, "btas_batch: profile reset");
+    char *d_ws = base + task_bytes + inst_bytes + b->counter_bytes + prof_bytes;
     for (size_t i = 0; i < ninst; ++i) {
         BInst &I = insts[i];
         char *w = d_ws + ws_off[i];
@@ -431,6 +492,7 @@ btas_status build_plan(btas_batch_t *b) {
     p.maxfin = b->d_counters + 2 + 2 * counters;
     p.insts = d_insts;
     p.timeout_cycles = batch_timeout_cycles(dev);
+    p.prof = b->d_prof;
     // Fault injection (tests only): BTAS_BATCH_WITHHOLD=i makes the host
     // withhold one completion of instance i (in add order), so its bounded
     // waits run out and the launch ends with BTAS_ERR_TIMEOUT.
@@ -465,7 +527,8 @@ extern "C" {
 
 btas_status btas_batch_create(btas_batch_t **out, int flags) {
     if (!out) return bfail(BTAS_ERR_ARG, "btas_batch_create: NULL out");
-    if (flags & ~BTAS_BATCH_NO_GRAPH) return bfail(BTAS_ERR_ARG, "btas_batch_create: unknown flags");
+    if (flags & ~(BTAS_BATCH_NO_GRAPH | BTAS_BATCH_PROFILE))
+        return bfail(BTAS_ERR_ARG, "btas_batch_create: unknown flags");
     btas_batch_t *b = new btas_batch_t();
     b->flags = flags;
     *out = b;
@@ -581,5 +644,21 @@ btas_status btas_batch_wait(btas_batch_t *b, void *stream) {
 int64_t btas_batch_workspace_bytes(btas_batch_t *b) { return b ? b->workspace_bytes : 0; }
 
 int btas_batch_tasks(btas_batch_t *b) { return b ? b->total : 0; }
+
+btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *counts, int slots) {
+    if (!b || !(b->flags & BTAS_BATCH_PROFILE))
+        return bfail(BTAS_ERR_ARG, "btas_batch_profile: batch created without BTAS_BATCH_PROFILE");
+    if (!b->d_prof) return bfail(BTAS_ERR_ARG, "btas_batch_profile: batch not launched yet");
+    if (slots < 0 || ((!cycles || !counts) && slots > 0)) return bfail(BTAS_ERR_ARG, "btas_batch_profile: outputs");
+    unsigned long long h[2 * BTAS_BATCH_PROFILE_SLOTS];
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(h, b->d_prof, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bfail(BTAS_ERR_CUDA, "btas_batch_profile: read back");
+    for (int i = 0; i < std::min(slots, BTAS_BATCH_PROFILE_SLOTS); ++i) {
+        cycles[i] = h[2 * i];
+        counts[i] = h[2 * i + 1];
+    }
+    return BTAS_OK;
+}
 
 }  // extern "C"

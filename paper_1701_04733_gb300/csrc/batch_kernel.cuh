@@ -58,6 +58,7 @@ struct BatchParams {
     const BInst *insts;
     long long timeout_cycles;
     int withhold_inst;  // fault injection for tests: this instance's level-1+ tasks never become ready
+    unsigned long long *prof;  // optional: (cycles, count) per BTAS_BATCH_SLOT_*
 };
 
 // Dynamic shared memory and CTAs per SM of the persistent kernel.

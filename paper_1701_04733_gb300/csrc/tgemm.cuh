@@ -225,12 +225,53 @@ __device__ __forceinline__ T finish(T v) {
 // Converged squaring (D_{s+1} = D_s): copy one BM x BN tile of P into C.
 template <class Cfg, typename T>
 __device__ __forceinline__ void copy_tile(const GemmArgs &args, int bm, int bn, int tid) {
+    // Bit copy of the 4-byte tile prev -> C.  Each thread issues its loads in
+    // batches of 8 (16-byte vectors where the pointers and pitches allow)
+    // before storing, so several loads are in flight per thread.
+    static_assert(sizeof(T) == 4, "4-byte elements");
     constexpr int BM = Cfg::BM, BN = Cfg::BN, NT = Cfg::kThreads;
-    const T *P = static_cast<const T *>(args.prev);
-    T *C = static_cast<T *>(args.C);
-    for (int idx = tid; idx < BM * BN; idx += NT) {
-        const int r = bm + idx / BN, c = bn + idx % BN;
-        if (r < args.m && c < args.n) C[(long long)r * args.ldc + c] = __ldcg(P + (long long)r * args.ldp + c);
+    constexpr int Q = BN / 4;  // 4-element chunks per tile row
+    static_assert((BM * Q) % NT == 0, "chunks divide evenly among the threads");
+    constexpr int PER = BM * Q / NT;
+    constexpr int BATCH = PER < 8 ? PER : 8;
+    static_assert(PER % BATCH == 0, "whole batches");
+    const uint32_t *P = static_cast<const uint32_t *>(args.prev);
+    uint32_t *C = static_cast<uint32_t *>(args.C);
+    const bool vec = ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(C)) & 15) == 0 &&
+                     ((args.ldp | args.ldc) & 3) == 0;
+#pragma unroll 1
+    for (int b0 = 0; b0 < PER; b0 += BATCH) {
+        uint4 v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int q = tid + (b0 + u) * NT;
+            const int r = bm + q / Q, c = bn + (q % Q) * 4;
+            const uint32_t *src = P + (long long)r * args.ldp + c;
+            if (vec && r < args.m && c + 4 <= args.n) {
+                v[u] = __ldcg(reinterpret_cast<const uint4 *>(src));
+            } else {
+                const bool rr = r < args.m;
+                v[u].x = rr && c < args.n ? __ldcg(src) : 0u;
+                v[u].y = rr && c + 1 < args.n ? __ldcg(src + 1) : 0u;
+                v[u].z = rr && c + 2 < args.n ? __ldcg(src + 2) : 0u;
+                v[u].w = rr && c + 3 < args.n ? __ldcg(src + 3) : 0u;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int q = tid + (b0 + u) * NT;
+            const int r = bm + q / Q, c = bn + (q % Q) * 4;
+            if (r >= args.m) continue;
+            uint32_t *dst = C + (long long)r * args.ldc + c;
+            if (vec && c + 4 <= args.n) {
+                *reinterpret_cast<uint4 *>(dst) = v[u];
+            } else {
+                if (c < args.n) dst[0] = v[u].x;
+                if (c + 1 < args.n) dst[1] = v[u].y;
+                if (c + 2 < args.n) dst[2] = v[u].z;
+                if (c + 3 < args.n) dst[3] = v[u].w;
+            }
+        }
     }
 }
 

@@ -160,3 +160,39 @@ def test_precision_switches_mid_solve(btas, oracle_mod):
     srv.close()
     for W, Dh in outs:
         np.testing.assert_array_equal(Dh.numpy(), oracle_mod.floyd_warshall(W))
+
+
+def test_profile_counts_every_task(btas, oracle_mod):
+    """BTAS_BATCH_PROFILE: every task lands in exactly one slot per launch;
+    the profiled launch still gives the oracle's results."""
+    apsp, gemm = _mixed(btas, seed=3)
+    b = btas.Batch(profile=True)
+    for W, Wd, D in apsp:
+        b.add_apsp(Wd, D)
+    for A, B, Ad, Bd, C, sr, tb in gemm:
+        b.add_gemm(Ad, Bd, C, sr, trans_b=tb)
+    with pytest.raises(btas.BtasError):
+        b.profile()  # not launched yet
+    for _ in range(2):
+        b.launch()
+        b.wait()
+    prof = b.profile()
+    work = {k: v for k, v in prof.items() if k != "wait"}
+    assert sum(v["tasks"] for v in work.values()) == 2 * b.tasks
+    assert all(v["cycles"] > 0 for v in work.values() if v["tasks"] > 0)
+    tiles = lambda x: (x + 127) // 128  # noqa: E731
+    n_transposes = sum(tiles(W.shape[0]) ** 2 for W, _, _ in apsp if W.shape[0] > 2) + \
+        sum(tiles(A.shape[1]) * tiles(B.shape[1]) for A, B, _, _, _, _, tb in gemm if not tb)
+    assert prof["transpose"]["tasks"] == 2 * n_transposes
+    assert prof["copy"]["tasks"] == 2 * 2  # n = 1 and n = 2
+    assert prof["gemm_i32"]["tasks"] > 0 and prof["gemm_f32"]["tasks"] > 0
+    assert prof["apsp_u16"]["tasks"] > 0  # weights <= 100: the packed squaring runs
+    assert prof["square_u16"]["tasks"] == prof["square_i32"]["tasks"] == 0
+    for W, Wd, D in apsp:
+        np.testing.assert_array_equal(host(D), oracle_mod.apsp_squaring(W))
+    for A, B, Ad, Bd, C, sr, tb in gemm:
+        np.testing.assert_array_equal(bits(host(C)), bits(oracle_mod.tgemm(sr, A, B)))
+    plain = btas.Batch()
+    assert btas.btas_batch_profile(plain.handle, None, None, 0) == 1  # created without the flag
+    plain.close()
+    b.close()
