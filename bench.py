@@ -712,6 +712,22 @@ def next_rows(args, btas, torch):
                      W[:np_, :np_].float()).contiguous()
     t_c = timed(lambda: btas.closure(Wf, "min"), reps=1)
     out["closure_fp32_minplus"] = {"n": np_, "ms": round(t_c * 1e3, 3)}
+    # exact packed int32 products (BTAS_GEMM_PACKED): small-range operands
+    # (values in [-4000, 4000]) on the packed kernel vs the int32 kernel
+    del Wp, Wf
+    Ap = torch.from_numpy(gen.uniform_int(s, 28, (n, n), -4000, 4000)).cuda()
+    Bp = torch.from_numpy(gen.uniform_int(s, 29, (n, n), -4000, 4000)).cuda()
+    Cp = torch.empty_like(Ap)
+    Cq = torch.empty_like(Ap)
+    for sr, name in ((0, "min"), (1, "max")):
+        c0 = btas.btas_packed_products()
+        t_pk = timed(lambda: btas.gemm(Ap, Bp, sr, out=Cp, packed=True), reps=2)
+        took = btas.btas_packed_products() - c0
+        t_32 = timed(lambda: btas.gemm(Ap, Bp, sr, out=Cq), reps=2)
+        out[f"gemm_i32_packed_{name}"] = {
+            "ms": round(t_pk * 1e3, 3), "tops": round(float(n) ** 3 / t_pk / 1e12, 2),
+            "int32_kernel_ms": round(t_32 * 1e3, 3), "speedup": round(t_32 / t_pk, 3),
+            "packed_path_taken": took == 3, "identical": bool(torch.equal(Cp, Cq))}
     return out
 
 

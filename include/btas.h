@@ -65,7 +65,10 @@ typedef enum {
 /* Flags OR-ed into the semiring argument of btas_gemm. */
 #define BTAS_GEMM_ACCUMULATE 0x100 /* C <- C (+) A (.) B, the paper's Z <- Z (+) X (.) Y */
 #define BTAS_GEMM_TRANS_B 0x200    /* B is given transposed: an n x k row-major matrix */
-#define BTAS_GEMM_NO_CARRIER 0x400 /* int32: never use the exact FP32-carrier path */
+#define BTAS_GEMM_NO_CARRIER 0x400 /* accepted and ignored: btas_gemm changes representation only
+                                       with BTAS_GEMM_PACKED (the APSP entry points have their own
+                                       switches) */
+#define BTAS_GEMM_PACKED 0x800     /* int32: exact packed 16-bit path when the operand ranges allow */
 
 typedef enum {
     BTAS_I32 = 0, /* int32, encoding above */
@@ -121,10 +124,27 @@ btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_per_sm);
  *            NULL pointers with non-empty extents, unknown semiring/dtype;
  *            BTAS_ERR_UNSUPPORTED for max-plus with BTAS_U16.
  * Results are bit-exact with the definition for every tiling.
+ *
+ * BTAS_GEMM_PACKED (int32 only; ignored for other dtypes): both semirings
+ * commute with a shift of each operand (min-plus: subtract the operand's
+ * smallest finite entry; max-plus: subtract each entry from the largest),
+ * after which every finite operand of A lies in [0, R_A] and of B in
+ * [0, R_B].  When every entry of A and B is finite (|v| <= 2^28) or the
+ * (+)-identity, and R_A + R_B < 0x7FFF, the product is computed exactly on
+ * the packed u16x2 kernel (two terms per instruction) and shifted back;
+ * otherwise on the int32 kernel.  The ranges are scanned and the choice is
+ * made on the device: the call stays asynchronous, the results are
+ * bit-identical either way, and it costs a few passes over A, B and C plus
+ * device workspace of about 4mk + 2kn + 2mn bytes.
  * ------------------------------------------------------------------------ */
 btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k,
                       const void *A, int64_t lda, const void *B, int64_t ldb,
                       void *C, int64_t ldc, void *stream);
+
+/* Diagnostic: number of products the current device has computed through
+ * the packed path of BTAS_GEMM_PACKED since the library was loaded
+ * (synchronises the device; -1 on a CUDA error). */
+int64_t btas_packed_products(void);
 
 /* ------------------------------------------------------------------------
  * Level 2: tropical matrix-vector product (the "standard vector and matrix

@@ -24,6 +24,7 @@ MAXPLUS = 1
 GEMM_ACCUMULATE = 0x100
 GEMM_TRANS_B = 0x200
 GEMM_NO_CARRIER = 0x400
+GEMM_PACKED = 0x800
 I32 = 0
 F32 = 1
 U16 = 2
@@ -62,6 +63,7 @@ SIGNATURES = {
     "btas_kernel_launches": (_i64, []),
     "btas_measure_issue_rate": (_i32, [_i32, _vp]),
     "btas_gemm": (_i32, [_i32, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
+    "btas_packed_products": (_i64, []),
     "btas_dot": (_i32, [_i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp, _vp]),
     "btas_axpy": (_i32, [_i32, _i32, _i64, _vp, _vp, _i64, _vp, _i64, _vp]),
     "btas_add": (_i32, [_i32, _i32, _i64, _vp, _vp, _vp, _vp]),
@@ -144,6 +146,11 @@ def check(status: int) -> None:
 
 
 # ---------------------------------------------------------------- raw ABI
+def btas_packed_products() -> int:
+    """Products the current device computed on the packed path (syncs)."""
+    return lib().btas_packed_products()
+
+
 def btas_version() -> int:
     return lib().btas_version()
 
@@ -357,20 +364,24 @@ def _rowmajor(t, name):
     return max(t.stride(0), 1) if t.shape[0] > 1 else max(t.shape[1], 1)
 
 
-def gemm(A, B, semiring="min", out=None, accumulate=False, trans_b=False, stream=None, no_carrier=False):
+def gemm(A, B, semiring="min", out=None, accumulate=False, trans_b=False, stream=None, no_carrier=False,
+         packed=False):
     """Tropical product C = A (x) B (or C (+)= A (x) B with accumulate).
 
     A, B are CUDA tensors (int32, float32, or int16 holding values in
     [0, 0x7FFF] for the packed min-plus path).  With trans_b, B is given as
-    B^T (n x k).  CPU tensors are copied to the current device and the result
-    is copied back (host -> device -> kernel -> host, the flow of Fig. 1)."""
+    B^T (n x k).  With packed=True (int32) the product runs on the exact
+    packed 16-bit kernel when the operands' finite ranges allow it
+    (BTAS_GEMM_PACKED; decided on the device, same bits either way).  CPU
+    tensors are copied to the current device and the result is copied back
+    (host -> device -> kernel -> host, the flow of Fig. 1)."""
     torch = _torch()
     host = A.device.type == "cpu"
     if host:
         dev = torch.device("cuda", torch.cuda.current_device())
         Ad, Bd = A.to(dev, non_blocking=True), B.to(dev, non_blocking=True)
         od = out.to(dev, non_blocking=True) if (out is not None and accumulate) else None
-        C = gemm(Ad, Bd, semiring, od, accumulate, trans_b, stream, no_carrier)
+        C = gemm(Ad, Bd, semiring, od, accumulate, trans_b, stream, no_carrier, packed)
         if out is None:
             return C.cpu()
         out.copy_(C)
@@ -385,6 +396,7 @@ def gemm(A, B, semiring="min", out=None, accumulate=False, trans_b=False, stream
         out = torch.empty((m, n), dtype=A.dtype, device=A.device)
     flags = _sr(semiring) | (GEMM_ACCUMULATE if accumulate else 0) | (GEMM_TRANS_B if trans_b else 0)
     flags |= GEMM_NO_CARRIER if no_carrier else 0
+    flags |= GEMM_PACKED if packed else 0
     check(btas_gemm(flags, _dtype_code(A), m, n, k, A.data_ptr(), _rowmajor(A, "A"), B.data_ptr(),
                     _rowmajor(B, "B"), out.data_ptr(), _rowmajor(out, "out"), _stream(stream)))
     return out

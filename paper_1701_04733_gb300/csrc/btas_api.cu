@@ -190,7 +190,8 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
     const int sr = semiring & 0xff;
     const bool accumulate = (semiring & BTAS_GEMM_ACCUMULATE) != 0;
     const bool trans_b = (semiring & BTAS_GEMM_TRANS_B) != 0;
-    if (semiring & ~(0xff | BTAS_GEMM_ACCUMULATE | BTAS_GEMM_TRANS_B | BTAS_GEMM_NO_CARRIER))
+    const bool packed = (semiring & BTAS_GEMM_PACKED) != 0;
+    if (semiring & ~(0xff | BTAS_GEMM_ACCUMULATE | BTAS_GEMM_TRANS_B | BTAS_GEMM_NO_CARRIER | BTAS_GEMM_PACKED))
         return fail(BTAS_ERR_ARG, "btas_gemm: unknown flag bits 0x%x", semiring);
     if (sr != BTAS_MINPLUS && sr != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_gemm: unknown semiring %d", sr);
     if (dtype != BTAS_I32 && dtype != BTAS_F32 && dtype != BTAS_U16)
@@ -236,10 +237,42 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
     Workspace ws(st);
     const void *Bt = B;
     long long ldbt = ldb;
+    const long long ldt = (k + 3) & ~3LL;
+    const size_t bt_bytes = trans_b ? 0 : align256((size_t)n * ldt * 4);
+    int *pack_state = nullptr;
+    if (packed && dtype == BTAS_I32) {
+        // exact packed path, chosen on the device (pack.cu); the int32 path
+        // below is enqueued too and bypassed when the packed one runs
+        const long long ldad = (k + 3) & ~3LL, ldbu = (n + 7) & ~7LL;
+        const size_t s_state = align256(kPackStateInts * 4), s_ad = align256((size_t)m * ldad * 4),
+                     s_bu = align256((size_t)k * ldbu * 2), s_cu = align256((size_t)m * ldbu * 2);
+        BTAS_CUDA(ws.alloc(bt_bytes + s_state + s_ad + s_bu + s_cu), "workspace alloc");
+        char *base = static_cast<char *>(ws.p) + bt_bytes;
+        pack_state = reinterpret_cast<int *>(base);
+        uint32_t *adup = reinterpret_cast<uint32_t *>(base + s_state);
+        uint16_t *bu = reinterpret_cast<uint16_t *>(base + s_state + s_ad);
+        uint16_t *cu = reinterpret_cast<uint16_t *>(base + s_state + s_ad + s_bu);
+        BTAS_CUDA(launch_pack_prepare(sr, (int)m, (int)n, (int)k, static_cast<const int *>(A), lda,
+                                      static_cast<const int *>(B), ldb, trans_b, pack_state, adup, bu, ldbu, st),
+                  "packed operands");
+        U16Args a{};
+        a.m = (int)m; a.n = (int)n; a.k = (int)k;
+        a.B = bu; a.ldb = ldbu;
+        a.C = cu; a.ldc = ldbu;
+        a.one = 1;
+        a.gate = pack_state + kPackStateUse;
+        a.adup_ready = true;
+        BTAS_CUDA(launch_tgemm_u16_ws(a, adup, u16_ns(m, n, k, st), st), "packed product");
+        BTAS_CUDA(launch_pack_finish(sr, (int)m, (int)n, cu, ldbu, pack_state, static_cast<int *>(C), ldc,
+                                     accumulate, st),
+                  "packed result");
+    } else if (!trans_b) {
+        BTAS_CUDA(ws.alloc(bt_bytes), "workspace alloc");
+    }
     if (!trans_b) {
-        const long long ldt = (k + 3) & ~3LL;
-        BTAS_CUDA(ws.alloc((size_t)n * ldt * 4), "workspace alloc");
-        BTAS_CUDA(launch_transpose4(B, ldb, (int)k, (int)n, ws.p, ldt, 0, nullptr, st), "transpose B");
+        BTAS_CUDA(launch_transpose4(B, ldb, (int)k, (int)n, ws.p, ldt, 0,
+                                    pack_state ? pack_state + kPackStateNotUse : nullptr, st),
+                  "transpose B");
         Bt = ws.p;
         ldbt = ldt;
     }
@@ -251,7 +284,14 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
     a.accumulate = accumulate ? 1 : 0;
     a.vec_a = aligned16(A, lda);
     a.vec_b = aligned16(Bt, ldbt);
+    a.bypass = pack_state ? pack_state + kPackStateUse : nullptr;
     return run_nt(dtype, sr, a, st);
+}
+
+int64_t btas_packed_products(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    return packed_products(dev);
 }
 
 // ----------------------------------------------------------------- level 2

@@ -88,11 +88,25 @@ struct U16Args {
     const int *skip;
     int one;
     int *maxfin;  // optional: atomicMax of the largest output below INF16
+    const int *gate;    // optional: *gate == 0 => the launches do nothing
+    bool adup_ready;    // `adup` already holds A's duplicated words (no pre-pass)
 };
 // Duplicates A into `adup` (m x round4(k) 32-bit words, caller workspace) and
 // runs the packed product; ns = number of the 8 column pairs per thread that
 // take the IMAD + 3-input-min path (the rest use DPX).
 cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaStream_t st);
+// ---- exact packed path for int32 products (pack.cu).  Device state words:
+// [0] packed? [1] offset of A [2] offset of B [3] !packed [4..7] ranges
+// and out-of-domain count.  All launches are stream-ordered; the choice is
+// made on the device.
+constexpr int kPackStateInts = 16;
+constexpr int kPackStateUse = 0, kPackStateNotUse = 3;
+cudaError_t launch_pack_prepare(int sr, int m, int n, int k, const int *A, long long lda, const int *B, long long ldb,
+                                bool trans_b, int *state, uint32_t *adup, uint16_t *bu, long long ldbu,
+                                cudaStream_t st);
+cudaError_t launch_pack_finish(int sr, int m, int n, const uint16_t *cu, long long ldcu, const int *state, int *C,
+                               long long ldc, bool accumulate, cudaStream_t st);
+long long packed_products(int device);
 cudaError_t launch_narrow_u16(const int *src, long long total, uint16_t *dst, cudaStream_t st);
 cudaError_t launch_widen_u16_i32(const uint16_t *src, long long total, int *dst, cudaStream_t st);
 

@@ -424,6 +424,7 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::MINB) tgemm_nt_kernel(cons
     int tm, tn;
     raster(blockIdx.x, tiles_m, tiles_n, args.group_m, tm, tn);
     const int bm = tm * Cfg::BM, bn = tn * Cfg::BN;
+    if (args.bypass != nullptr && __ldcg(args.bypass) != 0) return;
     if (args.skip != nullptr && __ldcg(args.skip) == 0) {
         copy_tile<Cfg, T>(args, bm, bn, tid);
         return;

@@ -22,6 +22,7 @@ struct GemmArgs {
     int vec_a, vec_b;   // operand rows are 16-byte aligned (cp.async usable)
     int group_m;        // CTA rasterisation: tile rows per group
     int *maxfin;        // optional: atomicMax of the largest finite output (as int)
+    const int *bypass;  // optional: *bypass != 0 => do nothing (another path computes C)
 };
 
 }  // namespace btas

@@ -51,6 +51,7 @@ struct U16KArgs {
     int one;
     int vec_a, vec_b;
     int *maxfin;
+    const int *gate;  // optional: *gate == 0 => do nothing
 };
 
 __global__ void dup_u16_kernel(const uint16_t *__restrict__ A, long long lda, int m, int k, uint32_t *__restrict__ Ad,
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
     const int tn = (pid % per_group) / gsz;
     const int bm = tm * BM, bnp = tn * BNP;  // bnp in pairs; column = 2*pair
 
+    if (args.gate != nullptr && __ldcg(args.gate) == 0) return;
     if (args.skip != nullptr && *args.skip == 0) {
         for (int idx = tid; idx < BM * BNP * 2; idx += NT) {
             const int r = bm + idx / (BNP * 2), c = 2 * bnp + idx % (BNP * 2);
@@ -283,10 +285,12 @@ static cudaError_t launch_ns(const U16KArgs &ka, cudaStream_t st) {
 // workspace) and the packed product.  ns selects the IMAD/DPX split.
 cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaStream_t st) {
     const long long ldad = (a.k + 3) & ~3LL;
-    dup_u16_kernel<<<grid_for((long long)a.m * a.k), 256, 0, st>>>(a.A, a.lda, a.m, a.k, adup, ldad, a.skip);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (!a.adup_ready) {
+        dup_u16_kernel<<<grid_for((long long)a.m * a.k), 256, 0, st>>>(a.A, a.lda, a.m, a.k, adup, ldad, a.skip);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     U16KArgs ka{};
     ka.m = a.m; ka.n = a.n; ka.k = a.k;
     ka.Ad = adup; ka.ldad = ldad;
@@ -297,6 +301,7 @@ cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaSt
     ka.skip = a.skip;
     ka.one = 1;
     ka.maxfin = a.maxfin;
+    ka.gate = a.gate;
     ka.vec_a = (reinterpret_cast<uintptr_t>(adup) & 15) == 0;
     ka.vec_b = (reinterpret_cast<uintptr_t>(a.B) & 15) == 0 && (a.ldb & 7) == 0;
     switch (ns) {

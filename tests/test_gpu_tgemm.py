@@ -151,3 +151,69 @@ def test_full_size_8192_sampled_rows(btas, oracle_mod, dt, sr):
     finally:
         oracle_mod.set_threads(1)
     np.testing.assert_array_equal(bits(C[rows]), bits(ref))
+
+
+def _ranged(seed, shape, lo, hi, sr, p_inf=0.1):
+    return int_matrix(seed, shape, sr, lo=lo, hi=hi, p_inf=p_inf)
+
+
+@pytest.mark.parametrize("sr", [0, 1])
+def test_packed_int32_product(btas, oracle_mod, sr):
+    """BTAS_GEMM_PACKED: operands whose finite ranges add up to less than
+    0x7FFF run on the packed kernel (the device counter moves) and give the
+    oracle's bits, negative values, INF entries, ragged sizes, B transposed
+    and the accumulate form included; wider ranges or an out-of-domain entry
+    keep the int32 kernel, with the same bits."""
+    cases = [((1, 1, 1), (-3, 3), (0, 0)), ((31, 33, 17), (-1000, 1000), (5, 900)),
+             ((200, 300, 129), (-9000, 4000), (100, 16000)), ((257, 130, 513), (0, 16383), (0, 16383))]
+    for si, ((m, n, k), ra, rb) in enumerate(cases):
+        A = _ranged(300 + si, (m, k), *ra, sr)
+        B = _ranged(400 + si, (k, n), *rb, sr)
+        ref = oracle_mod.tgemm(sr, A, B)
+        c0 = btas.btas_packed_products()
+        C = host(btas.gemm(dev(A), dev(B), sr, packed=True))
+        assert btas.btas_packed_products() == c0 + 1, (m, n, k)
+        np.testing.assert_array_equal(C, ref, err_msg=f"{m}x{n}x{k}")
+        Ct = host(btas.gemm(dev(A), dev(np.ascontiguousarray(B.T)), sr, trans_b=True, packed=True))
+        np.testing.assert_array_equal(Ct, ref)
+        C0 = _ranged(500 + si, (m, n), -20000, 20000, sr)
+        out = dev(C0)
+        btas.gemm(dev(A), dev(B), sr, out=out, accumulate=True, packed=True)
+        np.testing.assert_array_equal(host(out), oracle_mod.tgemm(sr, A, B, C0))
+        assert btas.btas_packed_products() == c0 + 3
+    # ranges too wide (about 20000 + 20000 >= 0x7FFF): int32 kernel, same bits
+    A = _ranged(600, (100, 70), 0, 20000, sr)
+    B = _ranged(601, (70, 90), -20000, 0, sr)
+    c0 = btas.btas_packed_products()
+    np.testing.assert_array_equal(host(btas.gemm(dev(A), dev(B), sr, packed=True)), oracle_mod.tgemm(sr, A, B))
+    assert btas.btas_packed_products() == c0
+    # the other semiring's identity is outside the domain: int32 kernel
+    A = _ranged(604, (100, 70), -10, 10, sr)
+    A[3, 4] = NINF if sr == 0 else INF
+    btas.gemm(dev(A), dev(_ranged(602, (70, 90), 0, 10, sr)), sr, packed=True)
+    assert btas.btas_packed_products() == c0
+    # all-identity operand: packed, every output is the identity
+    E = np.full((40, 30), INF if sr == 0 else NINF, np.int32)
+    c0 = btas.btas_packed_products()
+    C = host(btas.gemm(dev(E), dev(_ranged(603, (30, 50), -5, 5, sr)), sr, packed=True))
+    assert btas.btas_packed_products() == c0 + 1
+    assert (C == (INF if sr == 0 else NINF)).all()
+
+
+def test_packed_full_size_sampled_rows(btas, oracle_mod):
+    """n = 8192 int32 min-plus with values in [0, 8000]: packed path at full
+    size, 32 seeded rows recomputed by the oracle."""
+    n = 8192
+    A = gen.uniform_int(gen.BASE_SEED, 71, (n, n), 0, 8000)
+    B = gen.uniform_int(gen.BASE_SEED, 72, (n, n), 0, 8000)
+    c0 = btas.btas_packed_products()
+    C = btas.gemm(dev(A), dev(B), 0, packed=True)
+    assert btas.btas_packed_products() == c0 + 1
+    rows = gen.sample_indices(gen.BASE_SEED, 73, 32, n)
+    ref = oracle_mod.tgemm(0, A[rows], B)
+    np.testing.assert_array_equal(host(C[torch_index(rows)]), ref)
+
+
+def torch_index(rows):
+    import torch
+    return torch.from_numpy(np.asarray(rows, dtype=np.int64)).cuda()
