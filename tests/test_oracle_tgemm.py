@@ -102,6 +102,24 @@ def test_minplus_maxplus_duality(oracle_mod):
     np.testing.assert_array_equal(oracle_mod.tgemm(MAX, Af, Bf), -oracle_mod.tgemm(MIN, -Af, -Bf))
 
 
+@pytest.mark.parametrize("sr", [MIN, MAX])
+def test_translation_invariance_int(oracle_mod, sr):
+    """(A + a) (x) (B + b) = (A (x) B) + a + b on finite entries, identity
+    entries staying the identity (each term shifts by a + b, and min/max
+    commute with a common shift); the law the packed int32 path relies on."""
+    inf = INF if sr == MIN else NINF
+    A = _rand_i32(14, (9, 13), -500, 500, 0.25, inf)
+    B = _rand_i32(15, (13, 7), -500, 500, 0.25, inf)
+    A[2, :] = inf  # a row with no finite term: its outputs stay the identity
+    a, b = -377, 1234
+    As = np.where(A == inf, inf, A + a).astype(np.int32)
+    Bs = np.where(B == inf, inf, B + b).astype(np.int32)
+    C = oracle_mod.tgemm(sr, A, B)
+    Cs = oracle_mod.tgemm(sr, As, Bs)
+    np.testing.assert_array_equal(Cs, np.where(C == inf, inf, C + a + b))
+    assert (C == inf).any() and (C != inf).any()
+
+
 @pytest.mark.parametrize("dt", ["i32", "f32"])
 @pytest.mark.parametrize("sr", [MIN, MAX])
 def test_split_k_partials_combine(oracle_mod, dt, sr):
