@@ -56,11 +56,13 @@ def parse():
     p.add_argument("--batched-profile", action="store_true",
                    help="also run one profiled launch and report cycles per task kind")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the small-config timings (n = 256 solve, n = 4096 packed vs int32, Table II sizes)")
     p.add_argument("--no-tune", action="store_true",
                    help="skip the autotuner (kernels then come from the built-in defaults)")
     p.add_argument("--serve-requests", type=int, default=300)
     p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
-    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next", "tune"],
+    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next", "tune", "configs"],
                    help="profiling aids: run one part alone and print its JSON (not a bench line)")
     return p.parse_args()
 
@@ -186,6 +188,18 @@ def cpu_oracle_rate(inp, budget_s=15.0, threads=None):
     finally:
         oracle.set_threads(1)
     return total / dt / 1e9, threads, f"{R} rows x {n} x {n} of each of the 4 products ({total:.3g} terms, {dt:.1f} s)"
+
+
+def oracle_fw_n256_us():
+    """The oracle's Floyd-Warshall (one thread) on the n = 256 graph of the
+    config timings, in microseconds: the CPU side of that comparison."""
+    import gen
+    import oracle
+    W = gen.random_graph(gen.BASE_SEED, 1, 256, 0.1, 1, 100)
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.floyd_warshall(W)
+    return round((time.perf_counter() - t0) * 1e6, 1)
 
 
 def run_reference(args):
@@ -383,6 +397,8 @@ def run_btas(args):
 
     if not args.no_e2e:
         line["e2e"] = e2e(args, inp, btas, torch, units_per_step)
+    if not args.no_configs:
+        line["config_timings"] = config_timings(args, btas, torch)
     if not args.no_batched:
         del dev, Ci, Cf, D
         torch.cuda.empty_cache()
@@ -393,7 +409,7 @@ def run_btas(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, sample = cpu_oracle_rate(inp)
         line["cpu_baseline"] = {"value": round(rate, 3), "unit": "Gop/s", "cores": threads, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample, "fw_n256_us_1_thread": oracle_fw_n256_us()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -662,6 +678,59 @@ def e2e(args, inp, btas, torch, units_per_step):
             "overlap": "H2D and D2H on their own streams, overlapping the products"}
 
 
+PAPER_TABLE2_MS = {4: (0.008, 0.001062), 16: (0.078, 0.001163999), 32: (0.543, 0.002068), 64: (4.034, 0.0011743),
+                   128: (31.066, 0.004833)}  # Table II: (1-thread CPU FW, Fermi GPU FW), context only
+
+
+def config_timings(args, btas, torch):
+    """The smaller configurations as timings: one APSP solve at n = 256
+    (p = 0.1, w in [1, 100]); the n = 4096 graph with w in [1, 7] on the
+    packed kernel vs the int32 kernel (same bits); and the Floyd-Warshall
+    sizes of the paper's Table II (4 ... 128 vertices), blocked FW and
+    squaring, with the paper's own numbers beside them as context."""
+    import gen
+    s = gen.BASE_SEED
+
+    def lat(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return round(statistics.median(ts), 1)
+
+    out = {}
+    W1h = gen.random_graph(s, 1, 256, 0.1, 1, 100)
+    W1 = torch.from_numpy(W1h).cuda()
+    D1 = torch.empty_like(W1)
+    c1 = {"us_per_solve_adaptive": lat(lambda: btas.apsp(W1, out=D1)),
+          "us_per_solve_int32_device_exit": lat(
+              lambda: btas.apsp(W1, out=D1, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32)),
+          "us_per_solve_noalloc": lat(lambda: btas.btas_apsp_noalloc(256, W1.data_ptr(), D1.data_ptr(),
+                                                                     torch.cuda.current_stream().cuda_stream))}
+    out["n256_p0.1_w1-100"] = c1
+    W3 = torch.from_numpy(gen.random_graph(s, 3, 4096, 0.05, 1, 7)).cuda()
+    D3a, D3b = torch.empty_like(W3), torch.empty_like(W3)
+    t_u16 = lat(lambda: btas.apsp(W3, out=D3a, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_U16), reps=3)
+    t_i32 = lat(lambda: btas.apsp(W3, out=D3b, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32), reps=3)
+    out["n4096_p0.05_w1-7"] = {"packed_u16x2_ms": round(t_u16 / 1e3, 3), "int32_ms": round(t_i32 / 1e3, 3),
+                               "speedup": round(t_i32 / t_u16, 3), "identical": bool(torch.equal(D3a, D3b))}
+    t2 = []
+    for n, (cpu_ms, gpu_ms) in PAPER_TABLE2_MS.items():
+        W = torch.from_numpy(gen.random_graph(s, 200 + n, n, 0.5, 1, 100)).cuda()
+        D = torch.empty_like(W)
+        t2.append({"n": n, "blocked_fw_us": lat(lambda: btas.apsp_fw(W, out=D)),
+                   "squaring_us": lat(lambda: btas.apsp(W, out=D)),
+                   "paper_cpu_fw_us": round(cpu_ms * 1e3, 3), "paper_gpu_fw_us": round(gpu_ms * 1e3, 3)})
+    out["paper_table2_sizes"] = t2
+    return out
+
+
 def next_rows(args, btas, torch):
     """The follow-on routines at the n = 8192 graph: tropical gemv (HBM
     roofline), Bellman-Ford SSSP by repeated vector-matrix products, blocked
@@ -771,6 +840,8 @@ def run_only(args):
         print(json.dumps({"only": "tune", "n": n, "tuning_s": secs, "choices": choices}))
     elif args.only == "next":
         print(json.dumps({"only": "next", **next_rows(args, btas, torch)}))
+    elif args.only == "configs":
+        print(json.dumps({"only": "configs", **config_timings(args, btas, torch)}))
     else:
         print(json.dumps({"only": "serve", **serve(args, btas, torch)}))
     return 0

@@ -13,8 +13,9 @@
  *    a*M+b, Algorithms 2 and 3); leading dimensions are in elements.
  *  - Every array argument is a DEVICE pointer owned by the caller, unless the
  *    argument's description says "host".  The library never frees a caller's
- *    pointer.  Temporary device workspace is taken from the stream-ordered
- *    allocator (cudaMallocAsync on `stream`) and released on the same stream.
+ *    pointer.  Temporary device workspace is taken stream-ordered (on
+ *    `stream`) from a memory pool the library owns per device, and released
+ *    on the same stream; see btas_workspace_reserved.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  All work is enqueued asynchronously on it; a call returns once
  *    the work is enqueued, except where an out-parameter needs a device
@@ -86,6 +87,19 @@ typedef enum {
     BTAS_ERR_BUDGET = 6,      /* request exceeds the configured device-memory budget */
     BTAS_ERR_UNSUPPORTED = 7  /* semiring/dtype combination not offered */
 } btas_status;
+
+/* Workspace pool.  Temporary device memory comes from a stream-ordered
+ * memory pool the library creates for each device (cudaMemPoolCreate).
+ * Freed blocks stay cached for later calls up to a release threshold, set
+ * by the environment variable BTAS_POOL_KEEP_MB when the pool is created
+ * (default 4096 MiB).  Without the cache, blocks would go back to the
+ * driver at every synchronisation and each small call would pay for a
+ * fresh mapping.
+ * btas_workspace_reserved: bytes the current device's pool holds now.
+ * btas_workspace_trim    : synchronises the device and releases every
+ *                          cached block of its pool. */
+int64_t btas_workspace_reserved(void);
+btas_status btas_workspace_trim(void);
 
 /* Library version as 10000*major + 100*minor + patch. */
 int btas_version(void);

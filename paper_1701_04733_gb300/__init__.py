@@ -61,6 +61,8 @@ SIGNATURES = {
     "btas_version": (_i32, []),
     "btas_last_error_string": (ctypes.c_char_p, []),
     "btas_kernel_launches": (_i64, []),
+    "btas_workspace_reserved": (_i64, []),
+    "btas_workspace_trim": (_i32, []),
     "btas_measure_issue_rate": (_i32, [_i32, _vp]),
     "btas_gemm": (_i32, [_i32, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "btas_packed_products": (_i64, []),
@@ -146,6 +148,16 @@ def check(status: int) -> None:
 
 
 # ---------------------------------------------------------------- raw ABI
+def btas_workspace_reserved() -> int:
+    """Bytes the library's workspace pool of the current device holds."""
+    return lib().btas_workspace_reserved()
+
+
+def btas_workspace_trim() -> int:
+    """Release the cached workspace of the current device (syncs)."""
+    return lib().btas_workspace_trim()
+
+
 def btas_packed_products() -> int:
     """Products the current device computed on the packed path (syncs)."""
     return lib().btas_packed_products()

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,42 @@ using namespace btas;
 namespace btas {
 static std::atomic<long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// One workspace pool per device, created on first use, with a release
+// threshold so that freed blocks stay cached between calls.
+static std::mutex g_pool_mu;
+static std::vector<cudaMemPool_t> g_pools;
+
+static cudaError_t device_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        const char *keep = getenv("BTAS_POOL_KEEP_MB");
+        uint64_t thr = (uint64_t)((keep && *keep) ? atoll(keep) : 4096) << 20;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr)) != cudaSuccess) return e;
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+cudaError_t ws_free(void *p, cudaStream_t st) { return cudaFreeAsync(p, st); }
 }  // namespace btas
 
 namespace {
@@ -59,9 +96,9 @@ struct Workspace {
     void *p = nullptr;
     cudaStream_t st;
     explicit Workspace(cudaStream_t s) : st(s) {}
-    cudaError_t alloc(size_t bytes) { return bytes ? cudaMallocAsync(&p, bytes, st) : cudaSuccess; }
+    cudaError_t alloc(size_t bytes) { return bytes ? ws_alloc(&p, bytes, st) : cudaSuccess; }
     ~Workspace() {
-        if (p) cudaFreeAsync(p, st);
+        if (p) ws_free(p, st);
     }
 };
 
@@ -172,6 +209,22 @@ extern "C" {
 int btas_version(void) { return 100; }
 
 int64_t btas_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t btas_workspace_reserved(void) {
+    cudaMemPool_t pool = nullptr;
+    if (device_pool(&pool) != cudaSuccess) return -1;
+    uint64_t v = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v) != cudaSuccess) return -1;
+    return (int64_t)v;
+}
+
+btas_status btas_workspace_trim(void) {
+    cudaMemPool_t pool = nullptr;
+    BTAS_CUDA(device_pool(&pool), "workspace pool");
+    BTAS_CUDA(cudaDeviceSynchronize(), "synchronise");
+    BTAS_CUDA(cudaMemPoolTrimTo(pool, 0), "trim");
+    return BTAS_OK;
+}
 
 const char *btas_last_error_string(void) { return g_err.c_str(); }
 
@@ -466,6 +519,30 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     const int S = btas_apsp_squarings(n);
     const bool early = (flags & BTAS_APSP_EARLY_EXIT) != 0;
     const size_t nn = (size_t)n * (size_t)n;
+
+    // small graphs: the whole solve in one thread block (one launch, one
+    // read-back) on the int32 arithmetic; BTAS_APSP_NO_SMALL=1 disables it
+    if (S >= 1 && n <= apsp_small_max_n() && !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) &&
+        env_int("BTAS_APSP_NO_SMALL", 0) == 0) {
+        Workspace ws(st);
+        BTAS_CUDA(ws.alloc(256), "workspace alloc");
+        int *info = static_cast<int *>(ws.p);
+        int host[3] = {0, 0, 0};
+        BTAS_CUDA(launch_apsp_small(W, n, (int)n, S, early, D, n, info, st), "small apsp");
+        BTAS_CUDA(cudaMemcpyAsync(host, info, 12, cudaMemcpyDeviceToHost, st), "info readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "small apsp sync");
+        if (host[0] != 0) {
+            if (bound_out) *bound_out = -1;
+            return fail(BTAS_ERR_ARG,
+                        "btas_apsp: %d entries outside the domain (negative weight, weight > 2^28, or non-zero "
+                        "diagonal)",
+                        host[0]);
+        }
+        if (bound_out) *bound_out = (long long)(n - 1) * host[1];
+        if (squarings_done) *squarings_done = host[2];
+        if (path_out) *path_out = 1;
+        return BTAS_OK;
+    }
 
     Workspace ws(st);
     const size_t flag_bytes = align256((size_t)(2 * S + 8) * 4);

@@ -12,6 +12,9 @@ namespace btas {
 void note_launch(int n = 1);
 // Sets the calling thread's message returned by btas_last_error_string.
 void record_error(const char *msg);
+// Stream-ordered workspace from the library's pool of the current device.
+cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t st);
+cudaError_t ws_free(void *p, cudaStream_t st);
 
 // ---- tropical GEMM kernel registry (tgemm_*.cu)
 struct GemmKernel {
@@ -64,6 +67,14 @@ cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *D
 // changed (trans 1, optional) is set when some y entry changes.
 cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *A, long long lda, const void *x,
                         void *y, int accumulate, int *changed, cudaStream_t st);
+
+// ---- APSP in one thread block for n <= apsp_small_max_n() (small.cu).
+// info (device, 3 ints): entries outside the domain, largest finite weight,
+// squarings that changed D.  Nothing is written to D if the domain check
+// fails.
+int apsp_small_max_n();
+cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd,
+                              int *info, cudaStream_t st);
 
 // ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
 cudaError_t launch_fw_phase12(int *D, long long n, int kb, cudaStream_t st);

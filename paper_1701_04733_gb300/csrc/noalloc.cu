@@ -2,7 +2,7 @@
 // allocate device memory at call time.
 //
 // btas_apsp takes its scratch (a ping-pong matrix, a transpose buffer and the
-// per-squaring change flags) from cudaMallocAsync on every call.  Some callers
+// per-squaring change flags) from its stream-ordered pool on every call.  Some callers
 // cannot do that: a process whose own memory pool has already reserved the
 // device's free memory, or latency-critical code that must not allocate (an
 // allocation can block or synchronise) inside its loop.  This entry point

@@ -148,7 +148,7 @@ size_t footprint(const Req &r) {
 
 // Allocate the request's device block and start its input copies.
 bool admit(btas_server_t *sv, Req *r) {
-    if (cudaMallocAsync(reinterpret_cast<void **>(&r->dmem), r->bytes, sv->compute) != cudaSuccess) return false;
+    if (ws_alloc(reinterpret_cast<void **>(&r->dmem), r->bytes, sv->compute) != cudaSuccess) return false;
     // the copy stream must see the allocation
     cudaEvent_t ev;
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -198,7 +198,7 @@ bool admit(btas_server_t *sv, Req *r) {
 }
 
 void release(btas_server_t *sv, Req *r) {
-    if (r->dmem) cudaFreeAsync(r->dmem, sv->copy);
+    if (r->dmem) ws_free(r->dmem, sv->copy);
     r->dmem = nullptr;
     if (r->in_ready) cudaEventDestroy(r->in_ready);
     if (r->out_ready) cudaEventDestroy(r->out_ready);

@@ -226,12 +226,12 @@ struct Scratch {
     explicit Scratch(cudaStream_t s) : st(s) {}
     void *get(size_t bytes) {
         void *p = nullptr;
-        if (cudaMallocAsync(&p, bytes ? bytes : 256, st) != cudaSuccess) return nullptr;
+        if (ws_alloc(&p, bytes ? bytes : 256, st) != cudaSuccess) return nullptr;
         ptrs.push_back(p);
         return p;
     }
     ~Scratch() {
-        for (void *p : ptrs) cudaFreeAsync(p, st);
+        for (void *p : ptrs) ws_free(p, st);
     }
 };
 

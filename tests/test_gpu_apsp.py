@@ -155,3 +155,58 @@ def test_config_n8192_sampled(btas, oracle_mod):
     # the int32 kernels agree with the automatically chosen path
     D32 = host(btas.apsp(dev(W), flags=0x2 | 1))
     np.testing.assert_array_equal(D32, D)
+
+
+def test_workspace_pool_caches_and_trims(btas, oracle_mod):
+    """Workspace comes from the library's pool: it stays reserved between
+    calls (later calls reuse it) and btas_workspace_trim releases it."""
+    W = gen.random_graph(91, 1, 300, 0.05, 1, 100)
+    D1 = host(btas.apsp(dev(W)))
+    held = btas.btas_workspace_reserved()
+    assert held > 0
+    D2 = host(btas.apsp(dev(W)))
+    assert btas.btas_workspace_reserved() == held
+    np.testing.assert_array_equal(D1, D2)
+    np.testing.assert_array_equal(D1, oracle_mod.apsp_squaring(W))
+    assert btas.btas_workspace_trim() == 0
+    assert btas.btas_workspace_reserved() < held
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 33, 64, 100, 127, 128])
+def test_small_graph_single_block_path(btas, oracle_mod, n):
+    """n <= 128 runs in one thread block (all squarings in shared memory);
+    distances, squarings count and bound equal the general path's and the
+    oracle's, with and without early exit, in place too."""
+    import os
+    for p, whi in ((0.5 if n < 8 else 0.1, 100), (0.03, 10 ** 6)):
+        W = gen.random_graph(gen.BASE_SEED, 700 + n, n, p, 1, whi)
+        ref = oracle_mod.floyd_warshall(W)
+        for early in (0, 1):
+            D, info = btas.apsp(dev(W), flags=early, info=True)
+            os.environ["BTAS_APSP_NO_SMALL"] = "1"
+            try:
+                D2, info2 = btas.apsp(dev(W), flags=early | btas.APSP_FORCE_I32, info=True)
+            finally:
+                del os.environ["BTAS_APSP_NO_SMALL"]
+            np.testing.assert_array_equal(host(D), ref)
+            np.testing.assert_array_equal(host(D2), ref)
+            assert info["path"] == "int32"
+            assert info["squarings"] == info2["squarings"]
+            assert info["bound"] == info2["bound"] == (n - 1) * int(W[W < INF].max())
+        t = dev(W)
+        btas.apsp(t, out=t)
+        np.testing.assert_array_equal(host(t), ref)
+    # a directed path needs every squaring
+    W = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(W, 0)
+    W[np.arange(n - 1), np.arange(1, n)] = 3
+    D, info = btas.apsp(dev(W), info=True)
+    assert host(D)[0, n - 1] == 3 * (n - 1)
+    assert info["squarings"] == btas.btas_apsp_squarings(n)
+    # domain violations are reported and leave D untouched
+    bad = W.copy()
+    bad[1, 1] = 7
+    out = dev(np.full((n, n), 123, np.int32))
+    with pytest.raises(btas.BtasError):
+        btas.apsp(dev(bad), out=out)
+    assert (host(out) == 123).all()
