@@ -20,13 +20,8 @@ namespace btas {
 
 namespace {
 
-constexpr int FB = 128;  // tile edge
-constexpr int FT = 256;  // threads
-
-__device__ __forceinline__ int relax(int d, int a, int b) {
-    const int s = a + b;  // operands in [0, INF]: no overflow
-    return s < d ? s : d;
-}
+constexpr int FB = 128;   // tile edge
+constexpr int FT = 1024;  // threads: 32 x 32, each owning a 4 x 4 block of the tile
 
 // Load tile (r0, c0) of D into shared memory (INF outside the matrix).
 __device__ __forceinline__ void load_tile(int *sm, const int *D, long long n, int r0, int c0) {
@@ -42,24 +37,54 @@ __device__ __forceinline__ void store_tile(const int *sm, int *D, long long n, i
     }
 }
 
-__global__ void __launch_bounds__(FT) fw_diag_kernel(int *D, long long n, int kb) {
-    extern __shared__ int sm[];
-    const int o = kb * FB;
-    load_tile(sm, D, n, o, o);
-    __syncthreads();
+// The B pivots of one block: blk[i][j] = min(blk[i][j], colsrc[i][k] +
+// rowsrc[k][j]) for k = 0 .. FB-1 in order.  Each thread keeps its 4 x 4
+// outputs in registers and publishes them to shared memory after every
+// pivot, so pivot k+1 reads the current row k+1 and column k+1.  During
+// pivot k the pivot row and column themselves do not change (zero diagonal,
+// non-negative weights), so the reads of one pivot see consistent values.
+// Operands lie in [0, INF]: a + b cannot overflow, and one DPX add-min is one
+// relaxation.
+__device__ __forceinline__ void pivots(int *blk, const int *colsrc, const int *rowsrc) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i0 = ty * 4, j0 = tx * 4;
+    int d[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int4 v = *reinterpret_cast<const int4 *>(blk + (i0 + r) * FB + j0);
+        d[r][0] = v.x; d[r][1] = v.y; d[r][2] = v.z; d[r][3] = v.w;
+    }
     for (int k = 0; k < FB; ++k) {
-        for (int idx = threadIdx.x; idx < FB * FB; idx += FT) {
-            const int r = idx / FB, c = idx % FB;
-            sm[idx] = relax(sm[idx], sm[r * FB + k], sm[k * FB + c]);
+        int a[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = colsrc[(i0 + r) * FB + k];
+        const int4 b = *reinterpret_cast<const int4 *>(rowsrc + k * FB + j0);
+        __syncthreads();  // every read of pivot k precedes every write of it
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            d[r][0] = __viaddmin_s32(a[r], b.x, d[r][0]);
+            d[r][1] = __viaddmin_s32(a[r], b.y, d[r][1]);
+            d[r][2] = __viaddmin_s32(a[r], b.z, d[r][2]);
+            d[r][3] = __viaddmin_s32(a[r], b.w, d[r][3]);
+            *reinterpret_cast<int4 *>(blk + (i0 + r) * FB + j0) = make_int4(d[r][0], d[r][1], d[r][2], d[r][3]);
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(FT, 1) fw_diag_kernel(int *D, long long n, int kb) {
+    extern __shared__ __align__(16) int sm[];
+    const int o = kb * FB;
+    load_tile(sm, D, n, o, o);
+    __syncthreads();
+    pivots(sm, sm, sm);
     store_tile(sm, D, n, o, o);
 }
 
-// blockIdx.x < nb: row panel tile (kb, b); else column panel tile (b, kb).
-__global__ void __launch_bounds__(FT) fw_panel_kernel(int *D, long long n, int kb, int nb) {
-    extern __shared__ int sm[];
+// blockIdx.x < nb: row panel tile (kb, b) relaxes through diag[i][k] +
+// blk[k][j]; else column panel tile (b, kb) through blk[i][k] + diag[k][j].
+__global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, int kb, int nb) {
+    extern __shared__ __align__(16) int sm[];
     int *diag = sm, *blk = sm + FB * FB;
     const bool row = blockIdx.x < (unsigned)nb;
     const int b = row ? blockIdx.x : blockIdx.x - nb;
@@ -69,14 +94,8 @@ __global__ void __launch_bounds__(FT) fw_panel_kernel(int *D, long long n, int k
     load_tile(diag, D, n, o, o);
     load_tile(blk, D, n, r0, c0);
     __syncthreads();
-    for (int k = 0; k < FB; ++k) {
-        for (int idx = threadIdx.x; idx < FB * FB; idx += FT) {
-            const int r = idx / FB, c = idx % FB;
-            blk[idx] = row ? relax(blk[idx], diag[r * FB + k], blk[k * FB + c])
-                           : relax(blk[idx], blk[r * FB + k], diag[k * FB + c]);
-        }
-        __syncthreads();
-    }
+    if (row) pivots(blk, diag, blk);
+    else pivots(blk, blk, diag);
     store_tile(blk, D, n, r0, c0);
 }
 
