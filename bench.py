@@ -720,6 +720,19 @@ def config_timings(args, btas, torch):
     t_i32 = lat(lambda: btas.apsp(W3, out=D3b, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32), reps=3)
     out["n4096_p0.05_w1-7"] = {"packed_u16x2_ms": round(t_u16 / 1e3, 3), "int32_ms": round(t_i32 / 1e3, 3),
                                "speedup": round(t_i32 / t_u16, 3), "identical": bool(torch.equal(D3a, D3b))}
+    mid = []
+    for n in (192, 256, 512, 1024):
+        W = torch.from_numpy(gen.random_graph(s, 300 + n, n, 0.05, 1, 100)).cuda()
+        D = torch.empty_like(W)
+        t_coop = lat(lambda: btas.apsp(W, out=D), reps=5)
+        os.environ["BTAS_APSP_NO_MID"] = "1"
+        try:
+            t_gen = lat(lambda: btas.apsp(W, out=D), reps=5)
+            t_dev = lat(lambda: btas.apsp(W, out=D, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32), reps=5)
+        finally:
+            del os.environ["BTAS_APSP_NO_MID"]
+        mid.append({"n": n, "cooperative_us": t_coop, "tiled_adaptive_us": t_gen, "tiled_int32_device_exit_us": t_dev})
+    out["mid_sizes_p0.05_w1-100"] = mid
     t2 = []
     for n, (cpu_ms, gpu_ms) in PAPER_TABLE2_MS.items():
         W = torch.from_numpy(gen.random_graph(s, 200 + n, n, 0.5, 1, 100)).cuda()

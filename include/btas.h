@@ -223,6 +223,19 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  * `stream`; BTAS_ERR_ARG if violated), enables the early exit, and picks the
  * exact representation per squaring as btas_apsp_ex does without FORCE
  * flags.
+ *
+ * Execution by size (same results and the same squarings count in every
+ * regime; FORCE_U16 / FORCE_CARRIER always take the tiled path):
+ *   n <= 128        one thread block holds D in shared memory and runs the
+ *                   domain check and every squaring (int32): one launch, one
+ *                   read-back;
+ *   128 < n <= 1024 one cooperative launch runs every squaring as split-k
+ *                   work items merged with atomicMin, grid barriers (bounded
+ *                   waits; BTAS_ERR_TIMEOUT if one expires) in between (int32);
+ *   larger n        the tiled product kernels, one launch per squaring, with
+ *                   the per-squaring exact representation described below.
+ * BTAS_APSP_NO_SMALL=1 / BTAS_APSP_NO_MID=1 in the environment send the first
+ * two regimes to the tiled path.
  * ------------------------------------------------------------------------ */
 btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
 

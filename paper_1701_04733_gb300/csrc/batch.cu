@@ -312,9 +312,9 @@ cudaError_t launch_batch_kernel(const BatchParams &p, int grid, cudaStream_t st)
 }
 
 long long batch_timeout_cycles(int device) {
-    int clk_khz = 0;
-    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, device);
-    long long c = (long long)(2.0 * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);
+    (void)device;  // the current device
+    DeviceInfo d{};
+    long long c = (long long)(2.0 * (current_device_info(&d) ? d.clock_khz : 2000000) * 1e3);
     const char *tmo = getenv("BTAS_BATCH_TIMEOUT_CYCLES");
     if (tmo && *tmo) c = atoll(tmo);
     return c;

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -64,6 +65,45 @@ cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t st) {
 }
 
 cudaError_t ws_free(void *p, cudaStream_t st) { return cudaFreeAsync(p, st); }
+
+static std::mutex g_dev_mu;
+static std::vector<DeviceInfo> g_dev_info;
+static std::set<std::pair<int, const void *>> g_smem_set;
+
+bool current_device_info(DeviceInfo *out, int *device) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (device) *device = dev;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if ((int)g_dev_info.size() <= dev) g_dev_info.resize(dev + 1, DeviceInfo{0, 0, 0});
+    DeviceInfo &d = g_dev_info[dev];
+    if (d.sms == 0) {
+        int ma = 0, mi = 0, sms = 0, khz = 0;
+        if (cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess)
+            return false;
+        d = DeviceInfo{ma * 10 + mi, sms, khz > 0 ? khz : 2000000};
+    }
+    *out = d;
+    return true;
+}
+
+cudaError_t set_smem_once(const void *func, int bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_dev_mu);
+        if (g_smem_set.count({dev, func})) return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    g_smem_set.insert({dev, func});
+    return cudaSuccess;
+}
 }  // namespace btas
 
 namespace {
@@ -531,6 +571,33 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         BTAS_CUDA(launch_apsp_small(W, n, (int)n, S, early, D, n, info, st), "small apsp");
         BTAS_CUDA(cudaMemcpyAsync(host, info, 12, cudaMemcpyDeviceToHost, st), "info readback");
         BTAS_CUDA(cudaStreamSynchronize(st), "small apsp sync");
+        if (host[0] != 0) {
+            if (bound_out) *bound_out = -1;
+            return fail(BTAS_ERR_ARG,
+                        "btas_apsp: %d entries outside the domain (negative weight, weight > 2^28, or non-zero "
+                        "diagonal)",
+                        host[0]);
+        }
+        if (bound_out) *bound_out = (long long)(n - 1) * host[1];
+        if (squarings_done) *squarings_done = host[2];
+        if (path_out) *path_out = 1;
+        return BTAS_OK;
+    }
+
+    // mid-size graphs: every squaring in one cooperative launch (one
+    // read-back); BTAS_APSP_NO_MID=1 disables it
+    if (S >= 1 && n > apsp_small_max_n() && n <= apsp_mid_max_n() &&
+        !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) && env_int("BTAS_APSP_NO_MID", 0) == 0) {
+        Workspace ws(st);
+        const size_t mid_bytes = apsp_mid_workspace(n, S);
+        BTAS_CUDA(ws.alloc(mid_bytes + 256), "workspace alloc");
+        int *info = reinterpret_cast<int *>(static_cast<char *>(ws.p) + mid_bytes);
+        BTAS_CUDA(cudaMemsetAsync(info, 0, 256, st), "memset");
+        BTAS_CUDA(launch_apsp_mid(W, (int)n, S, early, D, ws.p, info, st), "mid apsp");
+        int host[4] = {0, 0, 0, 0};
+        BTAS_CUDA(cudaMemcpyAsync(host, info, 16, cudaMemcpyDeviceToHost, st), "info readback");
+        BTAS_CUDA(cudaStreamSynchronize(st), "mid apsp sync");
+        if (host[3] != 0) return fail(BTAS_ERR_TIMEOUT, "btas_apsp: a bounded grid barrier wait expired");
         if (host[0] != 0) {
             if (bound_out) *bound_out = -1;
             return fail(BTAS_ERR_ARG,

@@ -103,9 +103,9 @@ __global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, in
 
 cudaError_t launch_fw_phase12(int *D, long long n, int kb, cudaStream_t st) {
     const int nb = (int)((n + FB - 1) / FB);
-    cudaError_t e = cudaFuncSetAttribute(fw_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FB * FB * 4);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(fw_diag_kernel), FB * FB * 4);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fw_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * FB * FB * 4);
+    e = set_smem_once(reinterpret_cast<const void *>(fw_panel_kernel), 2 * FB * FB * 4);
     if (e != cudaSuccess) return e;
     fw_diag_kernel<<<1, FT, FB * FB * 4, st>>>(D, n, kb);
     note_launch();

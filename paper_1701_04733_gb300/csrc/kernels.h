@@ -12,6 +12,15 @@ namespace btas {
 void note_launch(int n = 1);
 // Sets the calling thread's message returned by btas_last_error_string.
 void record_error(const char *msg);
+// Device facts queried once per device (some attribute queries cost
+// hundreds of microseconds): compute capability major*10+minor, SM count,
+// SM clock in kHz.  Returns false if the device cannot be queried.
+struct DeviceInfo {
+    int arch, sms, clock_khz;
+};
+bool current_device_info(DeviceInfo *out, int *device = nullptr);
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (function, device).
+cudaError_t set_smem_once(const void *func, int bytes);
 // Stream-ordered workspace from the library's pool of the current device.
 cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t st);
 cudaError_t ws_free(void *p, cudaStream_t st);
@@ -75,6 +84,14 @@ cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *
 int apsp_small_max_n();
 cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd,
                               int *info, cudaStream_t st);
+
+// ---- APSP in one cooperative launch for apsp_small_max_n() < n <=
+// apsp_mid_max_n() (mid.cu).  ws: apsp_mid_workspace(n, S) bytes; info
+// (device, 64 ints, zeroed by the caller): [0] entries outside the domain,
+// [1] largest finite weight, [2] squarings that changed D, [3] status.
+int apsp_mid_max_n();
+size_t apsp_mid_workspace(long long n, int S);
+cudaError_t launch_apsp_mid(const int *W, int n, int S, bool early, int *D, void *ws, int *info, cudaStream_t st);
 
 // ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
 cudaError_t launch_fw_phase12(int *D, long long n, int kb, cudaStream_t st);

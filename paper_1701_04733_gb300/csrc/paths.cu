@@ -128,7 +128,7 @@ cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *D
                                 int *D2, int *N2, int *changed, cudaStream_t st) {
     const int tiles = (n + PBM - 1) / PBM;
     const int vec_a = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && ((ldd & 3) == 0);
-    cudaError_t e = cudaFuncSetAttribute(paths_square_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PSMEM);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(paths_square_kernel), PSMEM);
     if (e != cudaSuccess) return e;
     paths_square_kernel<<<tiles * tiles, PNT, PSMEM, st>>>(n, D, ldd, Dt, ldt, N, D2, N2, changed, vec_a);
     note_launch();

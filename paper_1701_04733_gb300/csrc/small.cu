@@ -121,14 +121,8 @@ int apsp_small_max_n() { return kMaxN; }
 
 cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd,
                               int *info, cudaStream_t st) {
-    static bool attr_set[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 64 || !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(apsp_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) attr_set[dev] = true;
-    }
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(apsp_small_kernel), kSmem);
+    if (e != cudaSuccess) return e;
     apsp_small_kernel<<<1, kThreads, kSmem, st>>>(W, ldw, n, S, early ? 1 : 0, D, ldd, info);
     note_launch();
     return cudaGetLastError();

@@ -273,7 +273,7 @@ cudaError_t launch_widen_u16_i32(const uint16_t *src, long long total, int *dst,
 template <int NS>
 static cudaError_t launch_ns(const U16KArgs &ka, cudaStream_t st) {
     auto kern = tgemm_u16_kernel<NS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, u16::SMEM);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(kern), u16::SMEM);
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)((ka.m + u16::BM - 1) / u16::BM) * (((ka.n + 1) / 2 + u16::BNP - 1) / u16::BNP);
     kern<<<(unsigned)tiles, u16::NT, u16::SMEM, st>>>(ka);

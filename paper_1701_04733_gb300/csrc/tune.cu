@@ -55,15 +55,10 @@ int bucket(long long x) {
 }
 
 bool device_key(int *arch, int *sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    int ma = 0, mi = 0, s = 0;
-    if (cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return false;
-    *arch = ma * 10 + mi;
-    *sms = s;
+    DeviceInfo d{};
+    if (!current_device_info(&d)) return false;
+    *arch = d.arch;
+    *sms = d.sms;
     return true;
 }
 

@@ -210,3 +210,42 @@ def test_small_graph_single_block_path(btas, oracle_mod, n):
     with pytest.raises(btas.BtasError):
         btas.apsp(dev(bad), out=out)
     assert (host(out) == 123).all()
+
+
+@pytest.mark.parametrize("n", [129, 200, 256, 333, 512, 777, 1024])
+def test_mid_graph_cooperative_path(btas, oracle_mod, n):
+    """128 < n <= 1024 runs every squaring in one cooperative launch (split-k
+    work items merged with atomicMin, grid barriers between squarings);
+    distances, squarings count and bound equal the general path's and the
+    oracle's, with and without early exit, in place too."""
+    import os
+    for p, whi in ((0.05, 100), (3.0 / n, 10 ** 6)):
+        W = gen.random_graph(gen.BASE_SEED, 800 + n, n, p, 1, whi)
+        ref = oracle_mod.floyd_warshall(W)
+        for early in (0, 1):
+            D, info = btas.apsp(dev(W), flags=early, info=True)
+            os.environ["BTAS_APSP_NO_MID"] = "1"
+            try:
+                D2, info2 = btas.apsp(dev(W), flags=early | btas.APSP_FORCE_I32, info=True)
+            finally:
+                del os.environ["BTAS_APSP_NO_MID"]
+            np.testing.assert_array_equal(host(D), ref)
+            np.testing.assert_array_equal(host(D2), ref)
+            assert info["path"] == "int32"
+            assert info["squarings"] == info2["squarings"]
+            assert info["bound"] == info2["bound"] == (n - 1) * int(W[W < INF].max())
+        t = dev(W)
+        btas.apsp(t, out=t)
+        np.testing.assert_array_equal(host(t), ref)
+    W = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(W, 0)
+    W[np.arange(n - 1), np.arange(1, n)] = 5
+    D, info = btas.apsp(dev(W), info=True)
+    assert host(D)[0, n - 1] == 5 * (n - 1)
+    assert info["squarings"] == btas.btas_apsp_squarings(n)
+    bad = W.copy()
+    bad[3, 7] = -1
+    out = dev(np.full((n, n), 77, np.int32))
+    with pytest.raises(btas.BtasError):
+        btas.apsp(dev(bad), out=out)
+    assert (host(out) == 77).all()
