@@ -208,7 +208,9 @@ def workload_config(n, world):
     return {"workload": f"tropical product {n}^3 (int32 [0,1e6] and f32 [0,1), min-plus and max-plus) + "
                         f"int32 APSP n={n} p=0.01 w[1,1000] ({S} squarings, early exit)",
             "n": n, "b_operand": "supplied transposed (BTAS_GEMM_TRANS_B)",
-            "l2": "inputs (256 MiB per matrix) larger than L2 (129 MB)", "parallelism": f"replicas x{world}"}
+            "l2": (f"inputs ({n * n * 4 >> 20} MiB per matrix) larger than L2 (129 MB)" if n * n * 4 > 129e6
+                   else f"inputs ({n * n * 4 >> 20} MiB per matrix) fit in L2 (129 MB): not an L2-cold number"),
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
