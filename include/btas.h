@@ -504,16 +504,21 @@ btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *coun
  * the next unit of every admitted request (a whole product, or one APSP
  * squaring) in one persistent launch; requests arriving meanwhile join the
  * next step.  A product completes after its step; an APSP solve after its
- * last squaring or as soon as a squaring changed nothing.  Results are
- * bit-identical to btas_gemm / btas_apsp (APSP here always uses the int32
- * kernels).  Buffers must stay valid until the request is done.
+ * last squaring or as soon as a squaring changed nothing.  An APSP request
+ * with n <= 1024 is instead solved whole in one unit, by the one-block
+ * (n <= 128) or the cooperative kernel of btas_apsp, launched in the step
+ * after the persistent kernel (BTAS_SERVER_NO_WHOLE=1 in the environment at
+ * creation turns this off).  Results are bit-identical to btas_gemm /
+ * btas_apsp.  Buffers must stay valid until the request is done.
  *
  * btas_server_create      : budget in bytes (> 0); flags must be 0.  The
  *                           current device is the server's device.
  * btas_server_submit_apsp : n x n int32 W (host) -> D (host); *ticket
  *                           receives the request id.  The domain (zero
  *                           diagonal, weights in [0, 2^28] or INF) is
- *                           assumed.  BTAS_ERR_BUDGET if the request alone
+ *                           checked for whole solves (the request then
+ *                           ends in state 3, failed) and assumed
+ *                           otherwise.  BTAS_ERR_BUDGET if the request alone
  *                           exceeds the budget.
  * btas_server_submit_gemm : C (m x n) = A (m x k) (x) B (k x n), host,
  *                           int32 or fp32, min-plus or max-plus.

@@ -593,7 +593,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         BTAS_CUDA(ws.alloc(mid_bytes + 256), "workspace alloc");
         int *info = reinterpret_cast<int *>(static_cast<char *>(ws.p) + mid_bytes);
         BTAS_CUDA(cudaMemsetAsync(info, 0, 256, st), "memset");
-        BTAS_CUDA(launch_apsp_mid(W, (int)n, S, early, D, ws.p, info, st), "mid apsp");
+        BTAS_CUDA(launch_apsp_mid(W, n, (int)n, S, early, D, n, ws.p, info, st), "mid apsp");
         int host[4] = {0, 0, 0, 0};
         BTAS_CUDA(cudaMemcpyAsync(host, info, 16, cudaMemcpyDeviceToHost, st), "info readback");
         BTAS_CUDA(cudaStreamSynchronize(st), "mid apsp sync");

@@ -91,7 +91,8 @@ cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool ea
 // [1] largest finite weight, [2] squarings that changed D, [3] status.
 int apsp_mid_max_n();
 size_t apsp_mid_workspace(long long n, int S);
-cudaError_t launch_apsp_mid(const int *W, int n, int S, bool early, int *D, void *ws, int *info, cudaStream_t st);
+cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd, void *ws,
+                            int *info, cudaStream_t st);
 
 // ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
 cudaError_t launch_fw_phase12(int *D, long long n, int kb, cudaStream_t st);

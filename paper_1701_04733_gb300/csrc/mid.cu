@@ -13,9 +13,9 @@
 // arithmetic per term is the int32 product's (DPX add-min), so results are
 // bit-identical to the other paths.
 //
-// Squaring s reads X_{s-1} (X_0 = W) and writes X_s into one of three
-// rotating buffers; X_{s+1}'s buffer is reset to INF while squaring s is
-// checked for change.  Every grid barrier wait is bounded (clock64); on
+// Squaring s reads X_{s-1} (X_0 = a pitch-n copy of W) and writes X_s into
+// one of three rotating buffers; X_{s+1}'s buffer is reset to INF while
+// squaring s is checked for change.  Every grid barrier wait is bounded (clock64); on
 // expiry the kernel records BTAS_ERR_TIMEOUT and all blocks return.
 #include <algorithm>
 #include <mutex>
@@ -30,10 +30,12 @@ constexpr int kT = 64, kThreads = 256, kKc = 32;  // tile edge, threads, k step
 
 struct MidArgs {
     const int *W;
+    long long ldw;
     int n;
     int S;
     int early;
     int *D;
+    long long ldd;
     int *buf0, *buf1, *buf2;  // n x n each, pitch n
     int kchunks;      // k-chunks per output tile
     int chunk;        // k-chunk length (multiple of kKc)
@@ -95,15 +97,16 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
     const long long gthreads = (long long)gridDim.x * kThreads;
     const long long gtid = (long long)blockIdx.x * kThreads + tid;
 
-    // phase 0: domain check, X_1's buffer to INF
+    // phase 0: domain check, W -> X_0 (buf2, pitch n), X_1's buffer to INF
     {
         int bad = 0, mx = 0;
         for (long long idx = gtid; idx < nn; idx += gthreads) {
             const int i = (int)(idx / n), j = (int)(idx % n);
-            const int v = a.W[idx];
+            const int v = a.W[(long long)i * a.ldw + j];
             const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
             if ((!fin && v != kInfI32) || (i == j && v != 0)) ++bad;
             if (fin) mx = max(mx, v);
+            a.buf2[idx] = v;
             a.buf0[idx] = kInfI32;
         }
 #pragma unroll
@@ -122,8 +125,8 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
     const int tiles = (n + kT - 1) / kT;
     const int items = tiles * tiles * a.kchunks;
     const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads, 4 x 4 outputs each
-    const int *in = a.W;
-    int cur = 0, done = 0;  // X_s lives in buf[(s - 1) % 3]
+    const int *in = a.buf2;  // X_0
+    int cur = 0, done = 0;   // X_s (s >= 1) lives in buf[(s - 1) % 3]
     for (int s = 1; s <= a.S; ++s) {
         int *out = bufp(a, cur);
         // phase A: partial products merged with atomicMin
@@ -193,8 +196,9 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
         cur = (cur + 1) % 3;
         if (!changed && a.early) break;
     }
-    // result: X_last -> D (W is no longer read, so D may be W)
-    for (long long idx = gtid; idx < nn; idx += gthreads) a.D[idx] = __ldcg(in + idx);
+    // result: X_last -> D (W was read only in phase 0, so D may be W)
+    for (long long idx = gtid; idx < nn; idx += gthreads)
+        a.D[(idx / n) * a.ldd + idx % n] = __ldcg(in + idx);
     if (blockIdx.x == 0 && tid == 0) a.info[2] = done;
 }
 
@@ -206,8 +210,8 @@ size_t apsp_mid_workspace(long long n, int S) {
     return 3 * (((size_t)n * n * 4 + 255) & ~size_t(255)) + 256 + (((size_t)(S + 8) * 4 + 255) & ~size_t(255));
 }
 
-cudaError_t launch_apsp_mid(const int *W, int n, int S, bool early, int *D, void *ws, int *info_out_dev,
-                            cudaStream_t st) {
+cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd, void *ws,
+                            int *info_out_dev, cudaStream_t st) {
     // device facts and the kernel's occupancy, queried once per device
     DeviceInfo di{};
     int dev = 0;
@@ -236,10 +240,12 @@ cudaError_t launch_apsp_mid(const int *W, int n, int S, bool early, int *D, void
     char *base = static_cast<char *>(ws);
     MidArgs a{};
     a.W = W;
+    a.ldw = ldw;
     a.n = n;
     a.S = S;
     a.early = early ? 1 : 0;
     a.D = D;
+    a.ldd = ldd;
     a.buf0 = reinterpret_cast<int *>(base);
     a.buf1 = reinterpret_cast<int *>(base + mat);
     a.buf2 = reinterpret_cast<int *>(base + 2 * mat);

@@ -13,7 +13,9 @@
 //             2 ms; BTAS_SERVER_STEP_TERMS), and these units run together in
 //             ONE launch of the persistent tile-task kernel
 //             (batch_kernel.cuh); short steps let finished requests leave
-//             and new ones join often;
+//             and new ones join often.  An APSP request with n <= 1024 is
+//             one unit instead: the whole solve, by the one-block or the
+//             cooperative kernel, launched after the persistent kernel;
 //   retire  - a product is finished after its step; an APSP solve after its
 //             last squaring or as soon as a squaring changed nothing (early
 //             exit, same result).  Its result is copied back on the copy
@@ -76,6 +78,8 @@ struct Req {
     int state = kQueued;
     int steps = 0;
     bool finished = false;
+    bool whole = false;  // APSP solved in one unit (small / cooperative kernel) in this step
+    bool bad = false;    // W outside the domain (whole-solve check): the request fails
     // terms of this request's next unit of work
     double unit_terms() const { return kind == 0 ? (double)n * n * n : (double)m * n * k; }
 };
@@ -110,6 +114,8 @@ struct btas_server_t {
     int step_parity = 0;
     double step_terms = 3e10;  // work cap of one step (terms), keeps steps short
     int allow_u16 = 1;         // BTAS_SERVER_NO_U16=1 keeps every squaring in int32
+    int allow_whole = 1;       // BTAS_SERVER_NO_WHOLE=1 runs every APSP squaring by squaring
+    double whole_below = 4e9;  // whole solves only when the other pending work is below this (terms)
     int64_t steps = 0;
     int64_t units = 0;
     int64_t completed = 0;
@@ -210,19 +216,30 @@ void release(btas_server_t *sv, Req *r) {
 int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
     // oldest admitted requests first, until the step's work cap (at least one)
     units.clear();
-    double terms = 0;
+    double terms = 0, pending = 0;
+    for (Req *r : sv->active) pending += r->unit_terms();
     for (Req *r : sv->active) {
-        const double w = r->unit_terms();
+        // an APSP request that fits the one-block or cooperative kernel is
+        // solved whole, in one unit, instead of one squaring per step -- when
+        // the rest of the step is light (at low load).  Under load its
+        // squarings are batched with the other requests' work instead, which
+        // keeps the GPU busier than a whole solve's grid barriers do.
+        r->whole = sv->allow_whole && r->kind == 0 && r->s == 1 && r->n <= apsp_mid_max_n() &&
+                   pending - r->unit_terms() < sv->whole_below;
+        const double w = r->whole ? r->unit_terms() * std::min(r->S, 6) : r->unit_terms();
         if (!units.empty() && terms + w > sv->step_terms) continue;
         units.push_back(r);
         terms += w;
     }
     if (units.empty()) return 0;
+    // batched units first (largest first), whole solves after them
     std::stable_sort(units.begin(), units.end(), [](const Req *a, const Req *b) {
+        if (a->whole != b->whole) return !a->whole;
         const long long wa = (long long)a->m * a->n * a->k, wb = (long long)b->m * b->n * b->k;
         return wa > wb;
     });
-    const int ninst = (int)units.size();
+    int ninst = 0;
+    while (ninst < (int)units.size() && !units[ninst]->whole) ++ninst;
     std::vector<BInst> insts(ninst);
     std::vector<int4> tasks;
     for (int i = 0; i < ninst; ++i) {
@@ -279,6 +296,10 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
         }
         insts[i] = I;
     }
+    const int par = sv->step_parity;
+    // the staging buffer of this parity was used two steps ago: that step is done
+    cudaEventSynchronize(sv->step_done[par]);
+    if (ninst > 0) {
     for (int level = 0; level <= 1; ++level)
         for (int i = 0; i < ninst; ++i) {
             const BInst &I = insts[i];
@@ -297,9 +318,6 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
     const size_t inst_bytes = a256((size_t)ninst * sizeof(BInst));
     const size_t task_bytes = a256(tasks.size() * sizeof(int4));
     const size_t need = cnt_bytes + inst_bytes + task_bytes;
-    const int par = sv->step_parity;
-    // the staging buffer of this parity was used two steps ago: that step is done
-    cudaEventSynchronize(sv->step_done[par]);
     if (need > sv->stage_bytes) {
         for (int q = 0; q < 2; ++q) {
             cudaEventSynchronize(sv->step_done[q]);
@@ -342,11 +360,33 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
                         cudaMemcpyDeviceToHost, sv->compute);
     }
     cudaMemcpyAsync(sv->h_flags + sv->flag_slots, p.status, 4, cudaMemcpyDeviceToHost, sv->compute);
+    } else {
+        sv->h_flags[sv->flag_slots] = 0;
+    }
+    // whole solves: domain check and every squaring in one launch each; the
+    // result lands in P[1]; mailbox slot i <- entries outside the domain,
+    // slot flag_slots + 1 + i <- barrier status
+    for (int i = ninst; i < (int)units.size(); ++i) {
+        Req *r = units[i];
+        cudaStreamWaitEvent(sv->compute, r->in_ready, 0);
+        int *info = r->dflag;  // 2S + 4 >= S + 5 ints
+        cudaMemsetAsync(info, 0, (size_t)(2 * r->S + 4) * 4, sv->compute);
+        cudaError_t e;
+        if (r->n <= apsp_small_max_n())
+            e = launch_apsp_small(static_cast<const int *>(r->P[0]), r->ldp, r->n, r->S, true,
+                                  static_cast<int *>(r->P[1]), r->ldp, info, sv->compute);
+        else
+            e = launch_apsp_mid(static_cast<const int *>(r->P[0]), r->ldp, r->n, r->S, true,
+                                static_cast<int *>(r->P[1]), r->ldp, r->Q[0], info, sv->compute);
+        if (e != cudaSuccess) return -1;
+        cudaMemcpyAsync(sv->h_flags + i, info, 4, cudaMemcpyDeviceToHost, sv->compute);
+        cudaMemcpyAsync(sv->h_flags + sv->flag_slots + 1 + i, info + 3, 4, cudaMemcpyDeviceToHost, sv->compute);
+    }
     cudaEventRecord(sv->step_done[par], sv->compute);
     sv->step_parity ^= 1;
     ++sv->steps;
-    sv->units += ninst;
-    return ninst;
+    sv->units += (int)units.size();
+    return (int)units.size();
 }
 
 void start_retire(btas_server_t *sv, Req *r) {
@@ -371,7 +411,7 @@ void poll_retiring(btas_server_t *sv, bool block) {
             release(sv, r);
             std::lock_guard<std::mutex> lk(sv->mu);
             r->t_done = t;
-            r->state = kDone;
+            r->state = r->bad ? kFailed : kDone;
             sv->used -= (long long)r->bytes;
             ++sv->completed;
         } else {
@@ -433,7 +473,12 @@ void worker_loop(btas_server_t *sv) {
             Req *r = units[i];
             ++r->steps;
             bool finished = true;
-            if (r->kind == 0) {
+            if (r->whole) {
+                // the one-block kernel reports no barrier status (its slot stays 0)
+                r->bad = sv->h_flags[i] != 0 || (r->n > apsp_small_max_n() && sv->h_flags[sv->flag_slots + 1 + i] != 0);
+                r->result_buf = 1;
+                r->s = r->S + 1;
+            } else if (r->kind == 0) {
                 const bool changed = sv->h_flags[i] != 0;
                 r->last_max = r->s < r->S ? sv->h_flags[sv->flag_slots + 1 + i] : -1;
                 r->result_buf = r->s & 1;
@@ -476,6 +521,7 @@ btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, in
     sv->grid = std::max(1, per_sm * sms);
     if (const char *e = getenv("BTAS_SERVER_STEP_TERMS")) sv->step_terms = atof(e) > 0 ? atof(e) : sv->step_terms;
     if (const char *e = getenv("BTAS_SERVER_NO_U16")) sv->allow_u16 = (*e && atoi(e) != 0) ? 0 : 1;
+    if (const char *e = getenv("BTAS_SERVER_NO_WHOLE")) sv->allow_whole = (*e && atoi(e) != 0) ? 0 : 1;
     sv->timeout_cycles = batch_timeout_cycles(sv->device);
     sv->flag_slots = 1 << 16;
     if (cudaMallocHost(reinterpret_cast<void **>(&sv->h_flags), (size_t)(2 * sv->flag_slots + 1) * 4) != cudaSuccess) {

@@ -49,9 +49,20 @@ def _alone(btas, r):
     return host(btas.gemm(r[1].cuda(), r[2].cuda(), r[4]))
 
 
-def test_mixed_arrivals_match_single_calls(btas, oracle_mod):
+@pytest.mark.parametrize("whole", [True, False])
+def test_mixed_arrivals_match_single_calls(btas, oracle_mod, whole):
+    """whole=True: APSP requests with n <= 1024 are solved in one unit (the
+    one-block or the cooperative kernel); whole=False
+    (BTAS_SERVER_NO_WHOLE=1): one squaring per step, through the persistent
+    tile-task kernel."""
+    import os
     reqs = _requests(40, 7)
-    srv = btas.Server(40 << 30)
+    if not whole:
+        os.environ["BTAS_SERVER_NO_WHOLE"] = "1"
+    try:
+        srv = btas.Server(40 << 30)
+    finally:
+        os.environ.pop("BTAS_SERVER_NO_WHOLE", None)
     tickets = []
 
     def producer():
@@ -103,3 +114,25 @@ def test_small_budget_queues_and_rejects(btas):
         srv.submit_apsp(big, big.clone())
     assert ei.value.status == 6
     srv.close()
+
+
+def test_whole_solve_domain_violation_fails_alone(btas, oracle_mod):
+    """A whole-solve APSP request whose W is outside the domain (a negative
+    weight) ends in the failed state; the requests around it are unaffected.
+    A graph above the whole-solve limit runs squaring by squaring."""
+    import torch
+    good = gen.random_graph(31, 1, 300, 0.05, 1, 100)
+    bad = good.copy()
+    bad[4, 9] = -2
+    large = gen.random_graph(32, 1, 1100, 0.01, 1, 100)
+    bufs = [(torch.from_numpy(w).pin_memory(), torch.zeros(w.shape, dtype=torch.int32).pin_memory())
+            for w in (good, bad, large, good[:100, :100].copy())]
+    srv = btas.Server(8 << 30)
+    tickets = [srv.submit_apsp(W, D) for W, D in bufs]
+    srv.wait_all(120)
+    states = [srv.poll(t)["state"] for t in tickets]
+    srv.close()
+    assert states == [2, 3, 2, 2]
+    np.testing.assert_array_equal(bufs[0][1].numpy(), oracle_mod.floyd_warshall(good))
+    np.testing.assert_array_equal(bufs[2][1].numpy(), host(btas.apsp(dev(large))))
+    np.testing.assert_array_equal(bufs[3][1].numpy(), oracle_mod.floyd_warshall(good[:100, :100].copy()))
