@@ -37,15 +37,16 @@ __device__ __forceinline__ void store_tile(const int *sm, int *D, long long n, i
     }
 }
 
-// The B pivots of one block: blk[i][j] = min(blk[i][j], colsrc[i][k] +
-// rowsrc[k][j]) for k = 0 .. FB-1 in order.  Each thread keeps its 4 x 4
+// The pivots of one block: blk[i][j] = min(blk[i][j], colsrc[i][k] +
+// rowsrc[k][j]) for k = 0 .. kmax-1 in order (kmax < FB only in the last
+// block, whose padding pivots are INF rows and columns and change nothing).  Each thread keeps its 4 x 4
 // outputs in registers and publishes them to shared memory after every
 // pivot, so pivot k+1 reads the current row k+1 and column k+1.  During
 // pivot k the pivot row and column themselves do not change (zero diagonal,
 // non-negative weights), so the reads of one pivot see consistent values.
 // Operands lie in [0, INF]: a + b cannot overflow, and one DPX add-min is one
 // relaxation.
-__device__ __forceinline__ void pivots(int *blk, const int *colsrc, const int *rowsrc) {
+__device__ __forceinline__ void pivots(int *blk, const int *colsrc, const int *rowsrc, int kmax) {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int i0 = ty * 4, j0 = tx * 4;
     int d[4][4];
@@ -54,7 +55,7 @@ __device__ __forceinline__ void pivots(int *blk, const int *colsrc, const int *r
         const int4 v = *reinterpret_cast<const int4 *>(blk + (i0 + r) * FB + j0);
         d[r][0] = v.x; d[r][1] = v.y; d[r][2] = v.z; d[r][3] = v.w;
     }
-    for (int k = 0; k < FB; ++k) {
+    for (int k = 0; k < kmax; ++k) {  // pivots past the matrix edge are INF rows/columns: no-ops
         int a[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) a[r] = colsrc[(i0 + r) * FB + k];
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(FT, 1) fw_diag_kernel(int *D, long long n, int
     const int o = kb * FB;
     load_tile(sm, D, n, o, o);
     __syncthreads();
-    pivots(sm, sm, sm);
+    pivots(sm, sm, sm, (int)min((long long)FB, n - o));
     store_tile(sm, D, n, o, o);
 }
 
@@ -94,8 +95,9 @@ __global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, in
     load_tile(diag, D, n, o, o);
     load_tile(blk, D, n, r0, c0);
     __syncthreads();
-    if (row) pivots(blk, diag, blk);
-    else pivots(blk, blk, diag);
+    const int kmax = (int)min((long long)FB, n - o);
+    if (row) pivots(blk, diag, blk, kmax);
+    else pivots(blk, blk, diag, kmax);
     store_tile(blk, D, n, r0, c0);
 }
 

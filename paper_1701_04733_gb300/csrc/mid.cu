@@ -36,7 +36,8 @@ struct MidArgs {
     int early;
     int *D;
     long long ldd;
-    int *buf0, *buf1, *buf2;  // n x n each, pitch n
+    int *buf0, *buf1, *buf2;  // n x ldx each; columns n .. ldx-1 always hold INF
+    long long ldx;            // round4(n): 16-byte rows for vector staging
     int kchunks;      // k-chunks per output tile
     int chunk;        // k-chunk length (multiple of kKc)
     unsigned *bar;    // [0] arrivals, [32] generation (separate 128-byte lines)
@@ -93,19 +94,23 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
     __shared__ __align__(16) int sa[kT][kKc + 4];
     __shared__ __align__(16) int sb[kKc][kT];
     const int n = a.n, tid = threadIdx.x;
-    const long long nn = (long long)n * n;
+    const long long ldx = a.ldx;
+    const long long nx = (long long)n * ldx;
     const long long gthreads = (long long)gridDim.x * kThreads;
     const long long gtid = (long long)blockIdx.x * kThreads + tid;
 
-    // phase 0: domain check, W -> X_0 (buf2, pitch n), X_1's buffer to INF
+    // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF
     {
         int bad = 0, mx = 0;
-        for (long long idx = gtid; idx < nn; idx += gthreads) {
-            const int i = (int)(idx / n), j = (int)(idx % n);
-            const int v = a.W[(long long)i * a.ldw + j];
-            const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
-            if ((!fin && v != kInfI32) || (i == j && v != 0)) ++bad;
-            if (fin) mx = max(mx, v);
+        for (long long idx = gtid; idx < nx; idx += gthreads) {
+            const int i = (int)(idx / ldx), j = (int)(idx % ldx);
+            int v = kInfI32;
+            if (j < n) {
+                v = a.W[(long long)i * a.ldw + j];
+                const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
+                if ((!fin && v != kInfI32) || (i == j && v != 0)) ++bad;
+                if (fin) mx = max(mx, v);
+            }
             a.buf2[idx] = v;
             a.buf0[idx] = kInfI32;
         }
@@ -141,16 +146,29 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[r][c] = kInfI32;
             for (int kb = k0; kb < k1; kb += kKc) {
-                // stage A[bm.., kb..] (64 x 32) and B[kb.., bn..] (32 x 64)
-                for (int e = tid; e < kT * kKc; e += kThreads) {
-                    const int r = e / kKc, c = e % kKc;
-                    const int gi = bm + r, gk = kb + c;
-                    sa[r][c] = (gi < n && gk < k1) ? __ldcg(in + (long long)gi * n + gk) : kInfI32;
+                // stage A[bm.., kb..] (64 x 32) and B[kb.., bn..] (32 x 64) with
+                // 16-byte loads, all issued before the shared-memory stores.  A
+                // vector that starts inside the matrix ends inside the row (ldx
+                // is a multiple of 4) and reads INF padding past column n-1;
+                // k-chunks end on multiples of 32, so no vector crosses one.
+                int4 va[2], vb[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e = tid + q * kThreads;
+                    const int ra = e >> 3, ca = (e & 7) * 4;  // A: 8 vectors per row
+                    const int gi = bm + ra, gka = kb + ca;
+                    va[q] = (gi < n && gka < k1) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)gi * ldx + gka))
+                                                 : make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+                    const int rb = e >> 4, cb = (e & 15) * 4;  // B: 16 vectors per row
+                    const int gkb = kb + rb, gj = bn + cb;
+                    vb[q] = (gkb < k1 && gj < n) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)gkb * ldx + gj))
+                                                 : make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
                 }
-                for (int e = tid; e < kKc * kT; e += kThreads) {
-                    const int r = e / kT, c = e % kT;
-                    const int gk = kb + r, gj = bn + c;
-                    sb[r][c] = (gk < k1 && gj < n) ? __ldcg(in + (long long)gk * n + gj) : kInfI32;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e = tid + q * kThreads;
+                    *reinterpret_cast<int4 *>(&sa[e >> 3][(e & 7) * 4]) = va[q];
+                    *reinterpret_cast<int4 *>(&sb[e >> 4][(e & 15) * 4]) = vb[q];
                 }
                 __syncthreads();
 #pragma unroll 4
@@ -175,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
                 for (int c = 0; c < 4; ++c) {
                     const int i = bm + ty * 4 + r, j = bn + tx * 4 + c;
                     const int v = clamp_i32<kMin>(acc[r][c]);
-                    if (i < n && j < n && v < kInfI32) atomicMin(out + (long long)i * n + j, v);
+                    if (i < n && j < n && v < kInfI32) atomicMin(out + (long long)i * ldx + j, v);
                 }
         }
         if (!grid_barrier(a)) return;
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
         {
             int *nxt = bufp(a, (cur + 1) % 3);
             bool ch = false;
-            for (long long idx = gtid; idx < nn; idx += gthreads) {
+            for (long long idx = gtid; idx < nx; idx += gthreads) {
                 ch |= __ldcg(out + idx) != __ldcg(in + idx);
                 if (s < a.S) nxt[idx] = kInfI32;
             }
@@ -197,8 +215,8 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
         if (!changed && a.early) break;
     }
     // result: X_last -> D (W was read only in phase 0, so D may be W)
-    for (long long idx = gtid; idx < nn; idx += gthreads)
-        a.D[(idx / n) * a.ldd + idx % n] = __ldcg(in + idx);
+    for (long long idx = gtid; idx < (long long)n * n; idx += gthreads)
+        a.D[(idx / n) * a.ldd + idx % n] = __ldcg(in + (idx / n) * ldx + idx % n);
     if (blockIdx.x == 0 && tid == 0) a.info[2] = done;
 }
 
@@ -207,7 +225,8 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
 int apsp_mid_max_n() { return 1024; }
 
 size_t apsp_mid_workspace(long long n, int S) {
-    return 3 * (((size_t)n * n * 4 + 255) & ~size_t(255)) + 256 + (((size_t)(S + 8) * 4 + 255) & ~size_t(255));
+    const size_t mat = ((size_t)n * ((n + 3) & ~3LL) * 4 + 255) & ~size_t(255);
+    return 3 * mat + 256 + (((size_t)(S + 8) * 4 + 255) & ~size_t(255));
 }
 
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd, void *ws,
@@ -236,7 +255,8 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     int chunk = ((n + kchunks - 1) / kchunks + kKc - 1) / kKc * kKc;
     kchunks = (n + chunk - 1) / chunk;
     const int grid = std::max(1, std::min(tiles * tiles * kchunks, std::min(want, per_sm * sms)));
-    const size_t mat = ((size_t)n * n * 4 + 255) & ~size_t(255);
+    const long long ldx = (n + 3) & ~3LL;
+    const size_t mat = ((size_t)n * ldx * 4 + 255) & ~size_t(255);
     char *base = static_cast<char *>(ws);
     MidArgs a{};
     a.W = W;
@@ -246,6 +266,7 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     a.early = early ? 1 : 0;
     a.D = D;
     a.ldd = ldd;
+    a.ldx = ldx;
     a.buf0 = reinterpret_cast<int *>(base);
     a.buf1 = reinterpret_cast<int *>(base + mat);
     a.buf2 = reinterpret_cast<int *>(base + 2 * mat);
