@@ -540,6 +540,41 @@ static btas_status squaring_loop(int dtype, long long n, int S, const void *cur0
     return BTAS_OK;
 }
 
+// The cooperative mid-size solve (mid.cu).  Returns a btas_status, or
+// kMidFallback if the grid cannot be co-resident on this device (e.g. a
+// shared device); the tiled path then computes the same result.
+constexpr int kMidFallback = -1;
+
+static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool early, int *squarings_done,
+                          int64_t *bound_out, int *path_out, cudaStream_t st) {
+    Workspace ws(st);
+    const size_t mid_bytes = apsp_mid_workspace(n, S);
+    BTAS_CUDA(ws.alloc(mid_bytes + 256), "workspace alloc");
+    int *info = reinterpret_cast<int *>(static_cast<char *>(ws.p) + mid_bytes);
+    BTAS_CUDA(cudaMemsetAsync(info, 0, 256, st), "memset");
+    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, D, n, ws.p, info, st);
+    if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
+        cudaGetLastError();
+        return kMidFallback;
+    }
+    BTAS_CUDA(le, "mid apsp");
+    int host[4] = {0, 0, 0, 0};
+    BTAS_CUDA(cudaMemcpyAsync(host, info, 16, cudaMemcpyDeviceToHost, st), "info readback");
+    BTAS_CUDA(cudaStreamSynchronize(st), "mid apsp sync");
+    if (host[3] != 0) return fail(BTAS_ERR_TIMEOUT, "btas_apsp: a bounded grid barrier wait expired");
+    if (host[0] != 0) {
+        if (bound_out) *bound_out = -1;
+        return fail(BTAS_ERR_ARG,
+                    "btas_apsp: %d entries outside the domain (negative weight, weight > 2^28, or non-zero "
+                    "diagonal)",
+                    host[0]);
+    }
+    if (bound_out) *bound_out = (long long)(n - 1) * host[1];
+    if (squarings_done) *squarings_done = host[2];
+    if (path_out) *path_out = 1;
+    return BTAS_OK;
+}
+
 static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags, int *squarings_done,
                              int64_t *bound_out, int *path_out, cudaStream_t st) {
     if (n < 0) return fail(BTAS_ERR_ARG, "btas_apsp: negative n");
@@ -588,27 +623,8 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     // read-back); BTAS_APSP_NO_MID=1 disables it
     if (S >= 1 && n > apsp_small_max_n() && n <= apsp_mid_max_n() &&
         !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) && env_int("BTAS_APSP_NO_MID", 0) == 0) {
-        Workspace ws(st);
-        const size_t mid_bytes = apsp_mid_workspace(n, S);
-        BTAS_CUDA(ws.alloc(mid_bytes + 256), "workspace alloc");
-        int *info = reinterpret_cast<int *>(static_cast<char *>(ws.p) + mid_bytes);
-        BTAS_CUDA(cudaMemsetAsync(info, 0, 256, st), "memset");
-        BTAS_CUDA(launch_apsp_mid(W, n, (int)n, S, early, D, n, ws.p, info, st), "mid apsp");
-        int host[4] = {0, 0, 0, 0};
-        BTAS_CUDA(cudaMemcpyAsync(host, info, 16, cudaMemcpyDeviceToHost, st), "info readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "mid apsp sync");
-        if (host[3] != 0) return fail(BTAS_ERR_TIMEOUT, "btas_apsp: a bounded grid barrier wait expired");
-        if (host[0] != 0) {
-            if (bound_out) *bound_out = -1;
-            return fail(BTAS_ERR_ARG,
-                        "btas_apsp: %d entries outside the domain (negative weight, weight > 2^28, or non-zero "
-                        "diagonal)",
-                        host[0]);
-        }
-        if (bound_out) *bound_out = (long long)(n - 1) * host[1];
-        if (squarings_done) *squarings_done = host[2];
-        if (path_out) *path_out = 1;
-        return BTAS_OK;
+        const int r = apsp_mid_solve(n, W, D, S, early, squarings_done, bound_out, path_out, st);
+        if (r != kMidFallback) return static_cast<btas_status>(r);
     }
 
     Workspace ws(st);

@@ -39,13 +39,15 @@ __device__ __forceinline__ void store_tile(const int *sm, int *D, long long n, i
 
 // The pivots of one block: blk[i][j] = min(blk[i][j], colsrc[i][k] +
 // rowsrc[k][j]) for k = 0 .. kmax-1 in order (kmax < FB only in the last
-// block, whose padding pivots are INF rows and columns and change nothing).  Each thread keeps its 4 x 4
-// outputs in registers and publishes them to shared memory after every
-// pivot, so pivot k+1 reads the current row k+1 and column k+1.  During
-// pivot k the pivot row and column themselves do not change (zero diagonal,
-// non-negative weights), so the reads of one pivot see consistent values.
-// Operands lie in [0, INF]: a + b cannot overflow, and one DPX add-min is one
-// relaxation.
+// block, whose padding pivots are INF rows and columns and change nothing).
+// Each thread keeps its 4 x 4 outputs in registers.  Pivot k reads row k of
+// rowsrc and column k of colsrc; during pivot k neither changes (zero
+// diagonal, non-negative weights), so after relaxing, only the owners of
+// row k+1 (when rowsrc is blk: PUB_ROW) and of column k+1 (when colsrc is
+// blk: PUB_COL) publish those values to shared memory, and one barrier per
+// pivot orders them before the next pivot's reads.  Operands lie in [0, INF]:
+// a + b cannot overflow, and one DPX add-min is one relaxation.
+template <bool PUB_ROW, bool PUB_COL>
 __device__ __forceinline__ void pivots(int *blk, const int *colsrc, const int *rowsrc, int kmax) {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int i0 = ty * 4, j0 = tx * 4;
@@ -60,17 +62,31 @@ __device__ __forceinline__ void pivots(int *blk, const int *colsrc, const int *r
 #pragma unroll
         for (int r = 0; r < 4; ++r) a[r] = colsrc[(i0 + r) * FB + k];
         const int4 b = *reinterpret_cast<const int4 *>(rowsrc + k * FB + j0);
-        __syncthreads();  // every read of pivot k precedes every write of it
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             d[r][0] = __viaddmin_s32(a[r], b.x, d[r][0]);
             d[r][1] = __viaddmin_s32(a[r], b.y, d[r][1]);
             d[r][2] = __viaddmin_s32(a[r], b.z, d[r][2]);
             d[r][3] = __viaddmin_s32(a[r], b.w, d[r][3]);
-            *reinterpret_cast<int4 *>(blk + (i0 + r) * FB + j0) = make_int4(d[r][0], d[r][1], d[r][2], d[r][3]);
+        }
+        const int kn = k + 1, q = kn & 3;  // selects by value keep d in registers
+        if (PUB_ROW && (kn >> 2) == ty) {
+            int v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = q == 0 ? d[0][c] : q == 1 ? d[1][c] : q == 2 ? d[2][c] : d[3][c];
+            *reinterpret_cast<int4 *>(blk + (i0 + q) * FB + j0) = make_int4(v[0], v[1], v[2], v[3]);
+        }
+        if (PUB_COL && (kn >> 2) == tx) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                blk[(i0 + r) * FB + j0 + q] = q == 0 ? d[r][0] : q == 1 ? d[r][1] : q == 2 ? d[r][2] : d[r][3];
         }
         __syncthreads();
     }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        *reinterpret_cast<int4 *>(blk + (i0 + r) * FB + j0) = make_int4(d[r][0], d[r][1], d[r][2], d[r][3]);
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(FT, 1) fw_diag_kernel(int *D, long long n, int kb) {
@@ -78,7 +94,7 @@ __global__ void __launch_bounds__(FT, 1) fw_diag_kernel(int *D, long long n, int
     const int o = kb * FB;
     load_tile(sm, D, n, o, o);
     __syncthreads();
-    pivots(sm, sm, sm, (int)min((long long)FB, n - o));
+    pivots<true, true>(sm, sm, sm, (int)min((long long)FB, n - o));
     store_tile(sm, D, n, o, o);
 }
 
@@ -96,8 +112,8 @@ __global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, in
     load_tile(blk, D, n, r0, c0);
     __syncthreads();
     const int kmax = (int)min((long long)FB, n - o);
-    if (row) pivots(blk, diag, blk, kmax);
-    else pivots(blk, blk, diag, kmax);
+    if (row) pivots<true, false>(blk, diag, blk, kmax);
+    else pivots<false, true>(blk, blk, diag, kmax);
     store_tile(blk, D, n, r0, c0);
 }
 
