@@ -76,6 +76,19 @@ def test_gemm(btas, oracle_mod, dt, sr):
     _check(gA, gB, gC)
     assert gA.unchanged() and gB.unchanged()
     np.testing.assert_array_equal(bits(host(gC.t)), bits(ref))
+    if dt == "i32":
+        # exact packed path (small-range operands), plain and B transposed
+        Ap, Bp = int_matrix(13, (m, k), sr, -2000, 2000), int_matrix(14, (k, n), sr, -2000, 2000)
+        refp = oracle_mod.tgemm(sr, Ap, Bp)
+        gAp, gBp, gBpt, gCp = Guarded(Ap), Guarded(Bp), Guarded(np.ascontiguousarray(Bp.T)), _out((m, n), np.int32)
+        c0 = btas.btas_packed_products()
+        btas.gemm(gAp.t, gBp.t, sr, out=gCp.t, packed=True)
+        _check(gAp, gBp, gCp)
+        np.testing.assert_array_equal(host(gCp.t), refp)
+        btas.gemm(gAp.t, gBpt.t, sr, out=gCp.t, packed=True, trans_b=True)
+        _check(gBpt, gCp)
+        np.testing.assert_array_equal(host(gCp.t), refp)
+        assert btas.btas_packed_products() == c0 + 2
     if dt != "u16":
         gBt = Guarded(np.ascontiguousarray(B.T))
         gC2 = Guarded(ref)  # accumulate into the result itself: unchanged (idempotent)

@@ -200,6 +200,26 @@ def test_packed_int32_product(btas, oracle_mod, sr):
     assert (C == (INF if sr == 0 else NINF)).all()
 
 
+def test_packed_strided_operands(btas, oracle_mod):
+    """Packed path with leading dimensions larger than the rows (aligned and
+    unaligned pitch) on A, B and C."""
+    import torch
+    m, n, k = 130, 97, 61
+    for sr in (0, 1):
+        A = _ranged(650 + sr, (m, k), -500, 700, sr)
+        B = _ranged(660 + sr, (k, n), 0, 900, sr)
+        ref = oracle_mod.tgemm(sr, A, B)
+        for pad in (4, 3):
+            Ab = dev(np.pad(A, ((0, 0), (0, pad))))
+            Bb = dev(np.pad(B, ((0, 0), (0, pad))))
+            Cb = torch.zeros((m, n + pad), dtype=torch.int32, device="cuda")
+            c0 = btas.btas_packed_products()
+            btas.gemm(Ab[:, :k], Bb[:, :n], sr, out=Cb[:, :n], packed=True)
+            assert btas.btas_packed_products() == c0 + 1
+            np.testing.assert_array_equal(host(Cb[:, :n]).copy(), ref)
+            assert (host(Cb[:, n:]) == 0).all()
+
+
 def test_packed_full_size_sampled_rows(btas, oracle_mod):
     """n = 8192 int32 min-plus with values in [0, 8000]: packed path at full
     size, 32 seeded rows recomputed by the oracle."""
