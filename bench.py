@@ -62,7 +62,7 @@ def parse():
                    help="skip the autotuner (kernels then come from the built-in defaults)")
     p.add_argument("--serve-requests", type=int, default=300)
     p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
-    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next", "tune", "configs"],
+    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next", "tune", "configs", "probe"],
                    help="profiling aids: run one part alone and print its JSON (not a bench line)")
     return p.parse_args()
 
@@ -200,6 +200,22 @@ def oracle_fw_n256_us():
     t0 = time.perf_counter()
     oracle.floyd_warshall(W)
     return round((time.perf_counter() - t0) * 1e6, 1)
+
+
+PROBE_MIXES = ((0, "int32_dpx"), (4, "int32_iadd_min3"), (5, "int32_imad_min3"), (6, "int32_split_imad5_dpx3"),
+               (1, "fp32_f32x2_min3"), (7, "fp32_2fadd_min3"), (2, "u16x2_dpx"), (3, "ffma_reference"))
+
+
+def issue_probe(btas):
+    """Measured issue ceilings of the inner-loop instruction mixes, in
+    tropical terms per clock per SM (btas_measure_issue_rate)."""
+    probe = {}
+    for mix, name in PROBE_MIXES:
+        try:
+            probe[name] = round(btas.measure_issue_rate(mix), 1)
+        except Exception as exc:  # diagnostic only
+            probe[name] = f"unavailable: {exc}"
+    return probe
 
 
 def workload_config(n, world):
@@ -376,15 +392,12 @@ def run_btas(args):
     roof_i32 = roof("tgemm_nt int32 min-plus 8192^3", n3, t_i32min)
     roof_i32["traffic"] = traffic.get("tgemm_nt int32 min-plus 8192^3")
     # measured issue ceilings of the instruction mixes (terms / clock / SM)
-    probe = {}
-    for mix, name in ((0, "int32_dpx"), (1, "fp32_f32x2_min3"), (2, "u16x2_dpx")):
-        try:
-            probe[name] = round(btas.measure_issue_rate(mix), 1)
-        except Exception as exc:  # diagnostic only
-            probe[name] = f"unavailable: {exc}"
-    if isinstance(probe.get("int32_dpx"), float):
-        ceil = probe["int32_dpx"] * sms * max_mhz * 1e6 / 1e12
+    probe = issue_probe(btas)
+    int_best = max((v for k, v in probe.items() if k.startswith("int32") and isinstance(v, float)), default=None)
+    if int_best:
+        ceil = int_best * sms * max_mhz * 1e6 / 1e12
         roof_i32["measured_issue_ceiling_tops"] = round(ceil, 3)
+        roof_i32["measured_issue_ceiling_basis"] = "best int32 instruction mix of the probe"
         roof_i32["frac_of_measured_ceiling"] = round(n3 / t_i32min / 1e12 / ceil, 4)
 
     line = {
@@ -865,6 +878,8 @@ def run_only(args):
         print(json.dumps({"only": "tune", "n": n, "tuning_s": secs, "choices": choices}))
     elif args.only == "next":
         print(json.dumps({"only": "next", **next_rows(args, btas, torch)}))
+    elif args.only == "probe":
+        print(json.dumps({"only": "probe", "terms_per_clk_per_sm": issue_probe(btas)}))
     elif args.only == "configs":
         print(json.dumps({"only": "configs", **config_timings(args, btas, torch)}))
     else:

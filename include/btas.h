@@ -115,7 +115,10 @@ int64_t btas_kernel_launches(void);
  * instruction mix, in tropical terms (one (i,j,k) add-then-min) per clock per
  * SM, from a register-only kernel with one CTA per SM (synchronises the
  * device).  mix: 0 = int32 DPX fused add-min, 1 = fp32 add.f32x2 + 3-input
- * min, 2 = packed u16x2 DPX add-min, 3 = FFMA (multiply-adds, reference). */
+ * min, 2 = packed u16x2 DPX add-min, 3 = FFMA (multiply-adds, reference),
+ * 4 = int32 IADD + 3-input min, 5 = int32 IMAD (x*1+y) + 3-input min,
+ * 6 = int32 column split (mix 5 on 5 of 8 columns, DPX on 3),
+ * 7 = fp32 two scalar adds + 3-input min. */
 btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_per_sm);
 
 /* ------------------------------------------------------------------------

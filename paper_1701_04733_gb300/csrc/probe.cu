@@ -22,7 +22,7 @@ __device__ __forceinline__ uint64_t pk(float lo, float hi) {
 }
 
 template <int MIX>
-__global__ void __launch_bounds__(256, 1) probe_kernel(const float *in, float *out, int iters, long long *cyc) {
+__global__ void __launch_bounds__(256, 1) probe_kernel(const float *in, float *out, int iters, long long *cyc, int one) {
     uint64_t x[8], y[8];
     float acc[8][8];
 #pragma unroll
@@ -59,6 +59,20 @@ __global__ void __launch_bounds__(256, 1) probe_kernel(const float *in, float *o
                 } else if (MIX == 2) {  // packed 16-bit: two DPX u16x2 add-min (4 terms)
                     const unsigned t = __viaddmin_u16x2(__float_as_uint(a0), __float_as_uint(b0), __float_as_uint(acc[i][j]));
                     acc[i][j] = __uint_as_float(__viaddmin_u16x2(__float_as_uint(a1), __float_as_uint(b1), t));
+                } else if (MIX == 4 || MIX == 5 || (MIX == 6 && j < 5)) {
+                    // int32: two adds (4: IADD on the ALU pipe; 5, 6: IMAD x*1+y on
+                    // the FMA pipe) + one 3-input min (2 terms); 6 uses this on 5
+                    // of 8 columns and DPX on the other 3
+                    const int s0 = MIX == 4 ? __float_as_int(a0) + __float_as_int(b0)
+                                            : imad_add(__float_as_int(a0), one, __float_as_int(b0));
+                    const int s1 = MIX == 4 ? __float_as_int(a1) + __float_as_int(b1)
+                                            : imad_add(__float_as_int(a1), one, __float_as_int(b1));
+                    acc[i][j] = __int_as_float(__vimin3_s32(__float_as_int(acc[i][j]), s0, s1));
+                } else if (MIX == 6) {
+                    const int t = __viaddmin_s32(__float_as_int(a0), __float_as_int(b0), __float_as_int(acc[i][j]));
+                    acc[i][j] = __int_as_float(__viaddmin_s32(__float_as_int(a1), __float_as_int(b1), t));
+                } else if (MIX == 7) {  // fp32: two scalar RN adds + 3-input min (2 terms)
+                    acc[i][j] = fsel3<kMin>(acc[i][j], __fadd_rn(a0, b0), __fadd_rn(a1, b1));
                 } else {  // reference: two FFMA (2 multiply-adds)
                     acc[i][j] = fmaf(a1, b1, fmaf(a0, b0, acc[i][j]));
                 }
@@ -79,9 +93,9 @@ constexpr int kProbeSmem = 120 * 1024;
 
 template <int MIX>
 cudaError_t run_probe(int sms, const float *in, float *out, long long *cyc, int iters) {
-    cudaError_t e = cudaFuncSetAttribute(probe_kernel<MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(probe_kernel<MIX>), kProbeSmem);
     if (e != cudaSuccess) return e;
-    probe_kernel<MIX><<<sms, 256, kProbeSmem>>>(in, out, iters, cyc);
+    probe_kernel<MIX><<<sms, 256, kProbeSmem>>>(in, out, iters, cyc, 1);
     note_launch();
     return cudaGetLastError();
 }
@@ -92,8 +106,8 @@ cudaError_t run_probe(int sms, const float *in, float *out, long long *cyc, int 
 using namespace btas;
 
 extern "C" btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_per_sm) {
-    if (mix < 0 || mix > 3 || !terms_per_clock_per_sm) {
-        record_error("btas_measure_issue_rate: mix must be 0..3");
+    if (mix < 0 || mix > 7 || !terms_per_clock_per_sm) {
+        record_error("btas_measure_issue_rate: mix must be 0..7");
         return BTAS_ERR_ARG;
     }
     int dev = 0, sms = 0;
@@ -119,7 +133,11 @@ extern "C" btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_
             case 0: e = run_probe<0>(sms, in, out, cyc, rep ? iters : 16); break;
             case 1: e = run_probe<1>(sms, in, out, cyc, rep ? iters : 16); break;
             case 2: e = run_probe<2>(sms, in, out, cyc, rep ? iters : 16); break;
-            default: e = run_probe<3>(sms, in, out, cyc, rep ? iters : 16); break;
+            case 3: e = run_probe<3>(sms, in, out, cyc, rep ? iters : 16); break;
+            case 4: e = run_probe<4>(sms, in, out, cyc, rep ? iters : 16); break;
+            case 5: e = run_probe<5>(sms, in, out, cyc, rep ? iters : 16); break;
+            case 6: e = run_probe<6>(sms, in, out, cyc, rep ? iters : 16); break;
+            default: e = run_probe<7>(sms, in, out, cyc, rep ? iters : 16); break;
         }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
