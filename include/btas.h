@@ -350,6 +350,10 @@ int btas_apsp_squarings(int64_t n);
  * this library holds until the process exits; hence n <= BTAS_NOALLOC_MAX_N
  * (larger n returns BTAS_ERR_ARG, nothing enqueued).  The caller still passes
  * W and D (device pointers, n x n int32, row-major, D == W allowed).
+ * n <= 128 runs on the one-block kernel and mid-size n whose three iterates
+ * fit in the array on the cooperative kernel (as btas_apsp does); larger n
+ * runs the tiled int32 squarings.  Nothing is read back: the call does not
+ * synchronise `stream`.
  * The first call on a device looks up the array's device address with that
  * device current (a host-side set-up step); make that first call before any
  * stream capture.  All calls share the array and it keeps the last call's

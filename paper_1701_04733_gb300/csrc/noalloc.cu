@@ -15,6 +15,10 @@
 // that device current, through cudaGetSymbolAddress, on the first call made
 // on that device.  Make that first call before any stream capture.
 //
+// Graphs with n <= 128 run on the one-block kernel and mid-size graphs whose
+// three iterates fit in the scratch run on the cooperative kernel (the same
+// kernels btas_apsp uses); the rest take the tiled int32 squarings below.
+//
 // All calls share the one array, and each call leaves its contents behind.
 // The change flags, which must start at zero, are cleared on the stream at the
 // start of every call.  Calls whose work overlaps on the GPU (different
@@ -118,6 +122,22 @@ extern "C" btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D
 
     e = cudaMemsetAsync(flags, 0, kFlagBytes, st);
     if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+
+    // Small and mid-size graphs: the one-block kernel, or the cooperative
+    // kernel when its three iterates fit in the scratch matrices; both take
+    // their status words from the flag area and need no read-back here.
+    if (n <= apsp_small_max_n()) {
+        e = launch_apsp_small(W, n, (int)n, S, true, D, n, flags, st);
+        if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+        return BTAS_OK;
+    }
+    if (n <= apsp_mid_max_n() && apsp_mid_workspace(n, S) <= 2 * kMatBytes) {
+        e = launch_apsp_mid(W, n, (int)n, S, true, D, n, X, flags, st);
+        if (e == cudaSuccess) return BTAS_OK;
+        if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorNotSupported)
+            return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+        cudaGetLastError();  // the grid cannot be co-resident here: tiled squarings below
+    }
 
     // Outputs alternate so that the last squaring writes D: squaring s writes
     // bufs[(S-1-s) & 1].  In place (D == W) with S odd the first squaring

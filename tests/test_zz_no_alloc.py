@@ -59,3 +59,18 @@ def test_in_place_and_size_limit(btas):
     # beyond the fixed scratch: rejected on the host, nothing enqueued
     assert btas.btas_apsp_noalloc(1025, t.data_ptr(), t.data_ptr(), stream) == 1
     assert "1024" in btas.last_error()
+
+
+def test_small_and_mid_sizes(btas):
+    """The one-block (n <= 128) and cooperative (mid n) kernels behind the
+    allocation-free entry point, out of place and in place."""
+    import torch
+    for n, seed in ((3, 74), (100, 75), (129, 76), (512, 77)):
+        W = gen.random_graph(gen.BASE_SEED, seed, n, 0.5 if n < 8 else 0.05, 1, 100)
+        ref, out = _both(btas, W)
+        np.testing.assert_array_equal(out, ref)
+        t = torch.from_numpy(W).cuda()
+        stream = torch.cuda.current_stream().cuda_stream
+        assert btas.btas_apsp_noalloc(n, t.data_ptr(), t.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(t.cpu().numpy(), ref)
