@@ -940,10 +940,24 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int B = fw_block();
     const size_t nn = (size_t)n * (size_t)n;
+    const int nb = (int)((n + B - 1) / B);
+    // Phase 3 runs on the exact packed u16x2 kernel for every pivot block
+    // whose row and column panels (after phase 2) have all finite entries
+    // below 0x7FFF / 2 -- decided on the device; BTAS_FW_NO_U16=1 keeps it
+    // on the int32 kernel.
+    const bool allow16 = nb > 1 && env_int("BTAS_FW_NO_U16", 0) == 0;
+    const long long ldbu = (n + 7) & ~7LL;
+    const size_t s_rpt = align256((size_t)n * B * 4), s_pmax = align256((size_t)nb * 4);
+    const size_t s_ad = allow16 ? align256((size_t)n * B * 4) : 0, s_bu = allow16 ? align256((size_t)B * ldbu * 2) : 0;
     Workspace ws(st);
-    BTAS_CUDA(ws.alloc(256 + align256((size_t)n * B * 4)), "workspace alloc");
-    int *scan = static_cast<int *>(ws.p);
-    int *RPT = reinterpret_cast<int *>(static_cast<char *>(ws.p) + 256);
+    BTAS_CUDA(ws.alloc(256 + s_rpt + s_pmax + 256 + s_ad + s_bu), "workspace alloc");
+    char *wbase = static_cast<char *>(ws.p);
+    int *scan = reinterpret_cast<int *>(wbase);
+    int *RPT = reinterpret_cast<int *>(wbase + 256);
+    int *pmax = reinterpret_cast<int *>(wbase + 256 + s_rpt);
+    int *state = reinterpret_cast<int *>(wbase + 256 + s_rpt + s_pmax);
+    uint32_t *Ad = reinterpret_cast<uint32_t *>(wbase + 256 + s_rpt + s_pmax + 256);
+    uint16_t *Bu = reinterpret_cast<uint16_t *>(wbase + 256 + s_rpt + s_pmax + 256 + s_ad);
     {
         int host[2] = {0, 0};
         BTAS_CUDA(cudaMemsetAsync(scan, 0, 8, st), "memset");
@@ -953,13 +967,26 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) 
         if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_apsp_fw: %d entries outside the domain", host[1]);
     }
     if (D != W) BTAS_CUDA(cudaMemcpyAsync(D, W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
-    const int nb = (int)((n + B - 1) / B);
+    BTAS_CUDA(cudaMemsetAsync(pmax, 0xFF, (size_t)nb * 4, st), "memset");  // -1: nothing finite yet
     for (int kb = 0; kb < nb; ++kb) {
         const long long o = (long long)kb * B, bw = std::min<long long>(B, n - o);
-        BTAS_CUDA(launch_fw_phase12(D, n, kb, st), "phases 1-2");
+        BTAS_CUDA(launch_fw_phase12(D, n, kb, allow16 ? pmax + kb : nullptr, st), "phases 1-2");
         if (nb == 1) break;
+        if (allow16) {
+            // Ad pitch round4(bw): the pitch the packed kernel reads a pre-duplicated A with
+            BTAS_CUDA(launch_fw_pack(D, n, kb, pmax + kb, state, Ad, (bw + 3) & ~3LL, Bu, ldbu, st), "packed panels");
+            U16Args a{};
+            a.m = (int)n; a.n = (int)n; a.k = (int)bw;
+            a.B = Bu; a.ldb = ldbu;
+            a.one = 1;
+            a.gate = state;
+            a.adup_ready = true;
+            a.Ci = D; a.ldci = n;
+            BTAS_CUDA(launch_tgemm_u16_ws(a, Ad, u16_ns(n, n, bw, st), st), "packed phase 3");
+        }
         // row panel D[o:o+bw, :] transposed into RPT (n x B): the k-contiguous B operand
-        BTAS_CUDA(launch_transpose4(D + o * n, n, (int)bw, (int)n, RPT, B, 0, nullptr, st), "panel transpose");
+        BTAS_CUDA(launch_transpose4(D + o * n, n, (int)bw, (int)n, RPT, B, 0, allow16 ? state + 1 : nullptr, st),
+                  "panel transpose");
         const long long rr[2][2] = {{0, o}, {o + bw, n}};
         for (int ri = 0; ri < 2; ++ri)
             for (int ci = 0; ci < 2; ++ci) {
@@ -975,6 +1002,7 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) 
                 a.accumulate = 1;
                 a.vec_a = aligned16(a.A, n);
                 a.vec_b = aligned16(a.Bt, B);
+                a.bypass = allow16 ? state : nullptr;  // the packed phase 3 ran instead
                 btas_status r = run_nt(BTAS_I32, kMin, a, st);
                 if (r != BTAS_OK) return r;
             }

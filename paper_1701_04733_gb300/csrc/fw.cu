@@ -11,6 +11,7 @@
 // For non-negative weights every relaxation order reaches the same distance
 // matrix, so the result equals Algorithm 2 (and APSP by squaring) exactly,
 // after n^3 terms instead of ceil(log2(n-1)) * n^3.
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -30,10 +31,21 @@ __device__ __forceinline__ void load_tile(int *sm, const int *D, long long n, in
         sm[idx] = (r0 + r < n && c0 + c < n) ? D[(long long)(r0 + r) * n + c0 + c] : kInfI32;
     }
 }
-__device__ __forceinline__ void store_tile(const int *sm, int *D, long long n, int r0, int c0) {
+// Store the tile; with pmax, also atomicMax the largest finite value stored.
+__device__ __forceinline__ void store_tile(const int *sm, int *D, long long n, int r0, int c0, int *pmax) {
+    int mx = -1;
     for (int idx = threadIdx.x; idx < FB * FB; idx += FT) {
         const int r = idx / FB, c = idx % FB;
-        if (r0 + r < n && c0 + c < n) D[(long long)(r0 + r) * n + c0 + c] = sm[idx];
+        if (r0 + r < n && c0 + c < n) {
+            const int v = sm[idx];
+            D[(long long)(r0 + r) * n + c0 + c] = v;
+            if (v < kInfI32) mx = max(mx, v);
+        }
+    }
+    if (pmax != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0 && mx >= 0) atomicMax(pmax, mx);
     }
 }
 
@@ -89,18 +101,18 @@ __device__ __forceinline__ void pivots(int *blk, const int *colsrc, const int *r
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(FT, 1) fw_diag_kernel(int *D, long long n, int kb) {
+__global__ void __launch_bounds__(FT, 1) fw_diag_kernel(int *D, long long n, int kb, int *pmax) {
     extern __shared__ __align__(16) int sm[];
     const int o = kb * FB;
     load_tile(sm, D, n, o, o);
     __syncthreads();
     pivots<true, true>(sm, sm, sm, (int)min((long long)FB, n - o));
-    store_tile(sm, D, n, o, o);
+    store_tile(sm, D, n, o, o, pmax);
 }
 
 // blockIdx.x < nb: row panel tile (kb, b) relaxes through diag[i][k] +
 // blk[k][j]; else column panel tile (b, kb) through blk[i][k] + diag[k][j].
-__global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, int kb, int nb) {
+__global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, int kb, int nb, int *pmax) {
     extern __shared__ __align__(16) int sm[];
     int *diag = sm, *blk = sm + FB * FB;
     const bool row = blockIdx.x < (unsigned)nb;
@@ -114,21 +126,66 @@ __global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, in
     const int kmax = (int)min((long long)FB, n - o);
     if (row) pivots<true, false>(blk, diag, blk, kmax);
     else pivots<false, true>(blk, blk, diag, kmax);
-    store_tile(blk, D, n, r0, c0);
+    store_tile(blk, D, n, r0, c0, pmax);
+}
+
+// Packed phase 3: state[0] = 1 when every finite entry of the pivot row and
+// column panels (after phase 2) is < 0x7FFF / 2, so that every finite term of
+// the phase-3 product is < 0x7FFF and the packed u16x2 product is exact;
+// state[1] = !state[0].
+__global__ void fw_pack_decide_kernel(const int *pmax, int *state) {
+    if (threadIdx.x != 0) return;
+    const int use = 2LL * __ldcg(pmax) < BTAS_INF_U16;
+    state[0] = use;
+    state[1] = !use;
+}
+
+// Column panel D[:, o:o+bw] -> duplicated 16-bit words (n x ldad); row panel
+// D[o:o+bw, :] -> uint16 (bw x ldbu).  INF (or anything >= 0x7FFF, which the
+// decision rules out for finite entries) becomes 0x7FFF.
+__global__ void fw_pack_panels_kernel(const int *D, long long n, long long o, int bw, const int *state,
+                                      uint32_t *Ad, long long ldad, uint16_t *Bu, long long ldbu) {
+    if (__ldcg(state) == 0) return;
+    const long long colp = n * bw, total = colp + (long long)bw * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (idx < colp) {
+            const long long i = idx / bw, k = idx % bw;
+            const int v = D[i * n + o + k];
+            const uint32_t u = v >= BTAS_INF_U16 ? BTAS_INF_U16 : (uint32_t)v;
+            Ad[i * ldad + k] = u * 0x10001u;
+        } else {
+            const long long q = idx - colp, k = q / n, j = q % n;
+            const int v = D[(o + k) * n + j];
+            Bu[k * ldbu + j] = (uint16_t)(v >= BTAS_INF_U16 ? BTAS_INF_U16 : v);
+        }
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_fw_phase12(int *D, long long n, int kb, cudaStream_t st) {
+cudaError_t launch_fw_pack(int *D, long long n, int kb, const int *pmax, int *state, uint32_t *Ad, long long ldad,
+                           uint16_t *Bu, long long ldbu, cudaStream_t st) {
+    const long long o = (long long)kb * FB;
+    const int bw = (int)std::min<long long>(FB, n - o);
+    fw_pack_decide_kernel<<<1, 32, 0, st>>>(pmax, state);
+    const long long total = 2 * n * bw;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 16));
+    fw_pack_panels_kernel<<<grid, 256, 0, st>>>(D, n, o, bw, state, Ad, ldad, Bu, ldbu);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fw_phase12(int *D, long long n, int kb, int *pmax, cudaStream_t st) {
     const int nb = (int)((n + FB - 1) / FB);
     cudaError_t e = set_smem_once(reinterpret_cast<const void *>(fw_diag_kernel), FB * FB * 4);
     if (e != cudaSuccess) return e;
     e = set_smem_once(reinterpret_cast<const void *>(fw_panel_kernel), 2 * FB * FB * 4);
     if (e != cudaSuccess) return e;
-    fw_diag_kernel<<<1, FT, FB * FB * 4, st>>>(D, n, kb);
+    fw_diag_kernel<<<1, FT, FB * FB * 4, st>>>(D, n, kb, pmax);
     note_launch();
     if (nb > 1) {
-        fw_panel_kernel<<<2 * nb, FT, 2 * FB * FB * 4, st>>>(D, n, kb, nb);
+        fw_panel_kernel<<<2 * nb, FT, 2 * FB * FB * 4, st>>>(D, n, kb, nb, pmax);
         note_launch();
     }
     return cudaGetLastError();

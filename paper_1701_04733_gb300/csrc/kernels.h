@@ -95,7 +95,14 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
                             int *info, cudaStream_t st);
 
 // ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
-cudaError_t launch_fw_phase12(int *D, long long n, int kb, cudaStream_t st);
+// pmax (optional): atomicMax of the largest finite value the phases store
+// (the pivot row and column panels).
+cudaError_t launch_fw_phase12(int *D, long long n, int kb, int *pmax, cudaStream_t st);
+// Packed phase 3 set-up for pivot block kb: state[0] = 1 if 2 * *pmax <
+// 0x7FFF (state[1] = !state[0]); when set, the column panel goes to Ad
+// (duplicated words, n x ldad) and the row panel to Bu (uint16, bw x ldbu).
+cudaError_t launch_fw_pack(int *D, long long n, int kb, const int *pmax, int *state, uint32_t *Ad, long long ldad,
+                           uint16_t *Bu, long long ldbu, cudaStream_t st);
 int fw_block();
 
 // ---- vector kernels (tvec.cu)
@@ -119,9 +126,12 @@ struct U16Args {
     int *maxfin;  // optional: atomicMax of the largest output below INF16
     const int *gate;    // optional: *gate == 0 => the launches do nothing
     bool adup_ready;    // `adup` already holds A's duplicated words (no pre-pass)
+    int *Ci;            // optional: int32 accumulate target, Ci = min(Ci, result); C is then not written
+    long long ldci;
 };
-// Duplicates A into `adup` (m x round4(k) 32-bit words, caller workspace) and
-// runs the packed product; ns = number of the 8 column pairs per thread that
+// Duplicates A into `adup` (m x round4(k) 32-bit words, caller workspace;
+// with adup_ready the caller has filled it, with that pitch) and runs the
+// packed product; ns = number of the 8 column pairs per thread that
 // take the IMAD + 3-input-min path (the rest use DPX).
 cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaStream_t st);
 // ---- exact packed path for int32 products (pack.cu).  Device state words:

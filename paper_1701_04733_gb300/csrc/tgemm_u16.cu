@@ -52,6 +52,8 @@ struct U16KArgs {
     int vec_a, vec_b;
     int *maxfin;
     const int *gate;  // optional: *gate == 0 => do nothing
+    int *Ci;          // optional: accumulate into int32 Ci = min(Ci, widened result) instead of writing C
+    long long ldci;
 };
 
 __global__ void dup_u16_kernel(const uint16_t *__restrict__ A, long long lda, int m, int k, uint32_t *__restrict__ Ad,
@@ -218,6 +220,28 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
 
     bool ch = false;
     int mx = -1;
+    if (args.Ci != nullptr) {
+        // int32 accumulate: Ci = min(Ci, result), INF16 read as INF
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = bm + row_base + 4 * i;
+            if (r >= M) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int h = j >> 2, q = j & 3;
+                const int c = 2 * (bnp + pair_base + 32 * h + q);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (c + e >= N) continue;
+                    const uint32_t u = e ? (acc[i][j] >> 16) : (acc[i][j] & 0xFFFFu);
+                    if (u >= BTAS_INF_U16) continue;
+                    int *pc = args.Ci + (long long)r * args.ldci + c + e;
+                    if ((int)u < *pc) *pc = (int)u;
+                }
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int r = bm + row_base + 4 * i;
@@ -302,6 +326,8 @@ cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaSt
     ka.one = 1;
     ka.maxfin = a.maxfin;
     ka.gate = a.gate;
+    ka.Ci = a.Ci;
+    ka.ldci = a.ldci;
     ka.vec_a = (reinterpret_cast<uintptr_t>(adup) & 15) == 0;
     ka.vec_b = (reinterpret_cast<uintptr_t>(a.B) & 15) == 0 && (a.ldb & 7) == 0;
     switch (ns) {
