@@ -221,22 +221,58 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
     bool ch = false;
     int mx = -1;
     if (args.Ci != nullptr) {
-        // int32 accumulate: Ci = min(Ci, result), INF16 read as INF
+        // int32 accumulate: Ci = min(Ci, result), INF16 read as INF.  Each
+        // thread's 8 columns per half (h) are consecutive, so rows are read
+        // and written as 16-byte vectors, two rows' loads in flight at once.
+        const bool vec = ((reinterpret_cast<uintptr_t>(args.Ci) & 15) == 0) && ((args.ldci & 3) == 0);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int r = bm + row_base + 4 * i;
-            if (r >= M) continue;
+        for (int i0 = 0; i0 < 8; i0 += 2) {
+            int4 old[2][2][2];  // [row][h][vector]
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int h = j >> 2, q = j & 3;
-                const int c = 2 * (bnp + pair_base + 32 * h + q);
+            for (int ii = 0; ii < 2; ++ii) {
+                const int r = bm + row_base + 4 * (i0 + ii);
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    if (c + e >= N) continue;
-                    const uint32_t u = e ? (acc[i][j] >> 16) : (acc[i][j] & 0xFFFFu);
-                    if (u >= BTAS_INF_U16) continue;
-                    int *pc = args.Ci + (long long)r * args.ldci + c + e;
-                    if ((int)u < *pc) *pc = (int)u;
+                for (int h = 0; h < 2; ++h) {
+                    const int c0 = 2 * (bnp + pair_base + 32 * h);
+                    const int *pc = args.Ci + (long long)r * args.ldci + c0;
+                    if (vec && r < M && c0 + 8 <= N) {
+                        old[ii][h][0] = *reinterpret_cast<const int4 *>(pc);
+                        old[ii][h][1] = *reinterpret_cast<const int4 *>(pc + 4);
+                    } else {
+                        int t[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) t[e] = (r < M && c0 + e < N) ? pc[e] : kInfI32;
+                        old[ii][h][0] = make_int4(t[0], t[1], t[2], t[3]);
+                        old[ii][h][1] = make_int4(t[4], t[5], t[6], t[7]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int ii = 0; ii < 2; ++ii) {
+                const int i = i0 + ii;
+                const int r = bm + row_base + 4 * i;
+                if (r >= M) continue;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c0 = 2 * (bnp + pair_base + 32 * h);
+                    int v[8] = {old[ii][h][0].x, old[ii][h][0].y, old[ii][h][0].z, old[ii][h][0].w,
+                                old[ii][h][1].x, old[ii][h][1].y, old[ii][h][1].z, old[ii][h][1].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t w = acc[i][4 * h + q];
+                        const uint32_t lo = w & 0xFFFFu, hi = w >> 16;
+                        if (lo < BTAS_INF_U16) v[2 * q] = min(v[2 * q], (int)lo);
+                        if (hi < BTAS_INF_U16) v[2 * q + 1] = min(v[2 * q + 1], (int)hi);
+                    }
+                    int *pc = args.Ci + (long long)r * args.ldci + c0;
+                    if (vec && c0 + 8 <= N) {
+                        *reinterpret_cast<int4 *>(pc) = make_int4(v[0], v[1], v[2], v[3]);
+                        *reinterpret_cast<int4 *>(pc + 4) = make_int4(v[4], v[5], v[6], v[7]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (c0 + e < N) pc[e] = v[e];
+                    }
                 }
             }
         }
