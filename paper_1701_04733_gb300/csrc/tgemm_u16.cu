@@ -278,25 +278,64 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
         }
         return;
     }
+    // Each thread's 8 columns per half (h) are consecutive: 16 bytes of C and
+    // of prev.  Where aligned and inside the matrix, prev is read and C
+    // written as 16-byte vectors, with both halves of two rows read before
+    // any store; elsewhere element by element.
+    const bool vec_c = ((reinterpret_cast<uintptr_t>(args.C) & 15) == 0) && ((args.ldc & 7) == 0) &&
+                       (args.prev == nullptr ||
+                        (((reinterpret_cast<uintptr_t>(args.prev) & 15) == 0) && ((args.ldp & 7) == 0)));
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int r = bm + row_base + 4 * i;
-        if (r >= M) continue;
+    for (int i0 = 0; i0 < 8; i0 += 2) {
+        uint4 pv[2][2];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int h = j >> 2, q = j & 3;
-            const int c = 2 * (bnp + pair_base + 32 * h + q);
-            const uint32_t v = acc[i][j];
-            const uint16_t lo = (uint16_t)(v & 0xFFFF), hi = (uint16_t)(v >> 16);
-            if (c < N) {
-                if (args.prev && lo != args.prev[(long long)r * args.ldp + c]) ch = true;
-                if (lo < BTAS_INF_U16) mx = max(mx, (int)lo);
-                args.C[(long long)r * args.ldc + c] = lo;
+        for (int ii = 0; ii < 2; ++ii) {
+            const int r = bm + row_base + 4 * (i0 + ii);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c0 = 2 * (bnp + pair_base + 32 * h);
+                pv[ii][h] = make_uint4(0, 0, 0, 0);
+                if (args.prev && vec_c && r < M && c0 + 8 <= N)
+                    pv[ii][h] = *reinterpret_cast<const uint4 *>(args.prev + (long long)r * args.ldp + c0);
             }
-            if (c + 1 < N) {
-                if (args.prev && hi != args.prev[(long long)r * args.ldp + c + 1]) ch = true;
-                if (hi < BTAS_INF_U16) mx = max(mx, (int)hi);
-                args.C[(long long)r * args.ldc + c + 1] = hi;
+        }
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii) {
+            const int i = i0 + ii;
+            const int r = bm + row_base + 4 * i;
+            if (r >= M) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c0 = 2 * (bnp + pair_base + 32 * h);
+                if (vec_c && c0 + 8 <= N) {
+                    const uint4 w = make_uint4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+                    if (args.prev)
+                        ch |= (w.x != pv[ii][h].x) | (w.y != pv[ii][h].y) | (w.z != pv[ii][h].z) | (w.w != pv[ii][h].w);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t lo = acc[i][4 * h + q] & 0xFFFFu, hi = acc[i][4 * h + q] >> 16;
+                        if (lo < BTAS_INF_U16) mx = max(mx, (int)lo);
+                        if (hi < BTAS_INF_U16) mx = max(mx, (int)hi);
+                    }
+                    *reinterpret_cast<uint4 *>(args.C + (long long)r * args.ldc + c0) = w;
+                    continue;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = c0 + 2 * q;
+                    const uint32_t v = acc[i][4 * h + q];
+                    const uint16_t lo = (uint16_t)(v & 0xFFFF), hi = (uint16_t)(v >> 16);
+                    if (c < N) {
+                        if (args.prev && lo != args.prev[(long long)r * args.ldp + c]) ch = true;
+                        if (lo < BTAS_INF_U16) mx = max(mx, (int)lo);
+                        args.C[(long long)r * args.ldc + c] = lo;
+                    }
+                    if (c + 1 < N) {
+                        if (args.prev && hi != args.prev[(long long)r * args.ldp + c + 1]) ch = true;
+                        if (hi < BTAS_INF_U16) mx = max(mx, (int)hi);
+                        args.C[(long long)r * args.ldc + c + 1] = hi;
+                    }
+                }
             }
         }
     }
