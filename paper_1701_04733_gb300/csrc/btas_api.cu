@@ -160,7 +160,7 @@ int env_int(const char *name, int dflt) {
 // GB300 at 8192^3, where the 2-CTA/SM, 64-bit-fragment tiles reach the
 // measured issue ceilings of their instruction mixes: int32 = IMAD/3-input-min
 // mix on 4 of 8 columns, fp32 = add.f32x2 + 3-input min; 64 x 64 tiles when
-// fewer than 2 waves of 128 x 128 tiles exist.
+// the 128 x 128 tiles would not fill one wave of 2 CTAs per SM.
 const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n, long long k, cudaStream_t st,
                                 int *group_m) {
     *group_m = 8;
@@ -181,8 +181,11 @@ const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n, lon
         var = env_int("BTAS_I32_VARIANT", kI32Mix);
         ns = var == kI32Mix ? env_int("BTAS_I32_NS", 4) : 0;
     }
+    // 128 x 128 tiles at 2 CTAs/SM once they fill at least one full wave
+    DeviceInfo di{};
+    const int sms = current_device_info(&di) ? di.sms : 152;
     const long long big_tiles = ((m + 127) / 128) * ((n + 127) / 128);
-    int cfg = env_int("BTAS_CFG", big_tiles >= 2 * 152 ? 4 : 2);
+    int cfg = env_int("BTAS_CFG", big_tiles >= 2LL * sms ? 4 : 2);
     const GemmKernel *kk = find_gemm_kernel(var, sr, ns, cfg);
     if (!kk && dtype == BTAS_I32) kk = find_gemm_kernel(kI32Mix, sr, 5, cfg);
     if (!kk) kk = find_gemm_kernel(var, sr, ns, 0);

@@ -80,7 +80,9 @@ int squarings(long long n) {
 
 const GemmKernel *pick_kernel(long long n) {
     const long long tiles = ((n + 127) / 128) * ((n + 127) / 128);
-    const GemmKernel *k = find_gemm_kernel(kI32Mix, kMin, 5, tiles >= 2 * 152 ? 0 : 2);
+    DeviceInfo di{};
+    const int sms = current_device_info(&di) ? di.sms : 152;
+    const GemmKernel *k = find_gemm_kernel(kI32Mix, kMin, 5, tiles >= 2LL * sms ? 0 : 2);
     if (!k) k = find_gemm_kernel(kI32Dpx, kMin, 0, 0);
     return k;
 }
