@@ -25,6 +25,11 @@
  *    and return BTAS_ERR_ARG (nothing is written).  A failed CUDA call returns
  *    BTAS_ERR_CUDA.  btas_last_error_string() describes the most recent
  *    failure of the calling thread.
+ *  - Tracing: every level-2/3 and APSP entry point is an NVTX range named
+ *    after it (visible to Nsight tools).  BTAS_LOG=1 in the environment
+ *    (read once per process) prints each call's execution choices -- the
+ *    product kernel and where its choice came from, the APSP size regime and
+ *    representations -- to stderr.
  *
  * Integer encoding of "no edge" / the semiring zero
  *  The paper marks a missing edge with 0 (Algorithm 2) or -1 (Algorithm 3);

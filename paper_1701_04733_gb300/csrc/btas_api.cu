@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -65,6 +67,26 @@ cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t st) {
 }
 
 cudaError_t ws_free(void *p, cudaStream_t st) { return cudaFreeAsync(p, st); }
+
+// BTAS_LOG=1 (read once) prints each entry point's execution choices to
+// stderr; 0 or unset prints nothing.
+int log_level() {
+    static const int level = [] {
+        const char *v = getenv("BTAS_LOG");
+        return v && *v ? atoi(v) : 0;
+    }();
+    return level;
+}
+
+void log_event(const char *fmt, ...) {
+    if (log_level() <= 0) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    fprintf(stderr, "[btas] %s\n", buf);
+}
 
 static std::mutex g_dev_mu;
 static std::vector<DeviceInfo> g_dev_info;
@@ -142,6 +164,13 @@ struct Workspace {
     }
 };
 
+// An NVTX range around one entry point (visible to Nsight tools; a no-op
+// without one attached).
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+};
+
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 bool aligned16(const void *p, long long ld) {
@@ -171,6 +200,9 @@ const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n, lon
         const GemmKernel *t = find_gemm_kernel(c.var, sr, c.ns, c.cfg);
         if (t) {
             *group_m = c.group_m;
+            log_event("product %lldx%lldx%lld %s %s: variant %d ns %d cfg %d group %d (autotuner)", m, n, k,
+                      dtype == BTAS_F32 ? "fp32" : "int32", sr == kMin ? "min-plus" : "max-plus", t->var, t->ns,
+                      t->cfg, c.group_m);
             return t;
         }
     }
@@ -192,6 +224,10 @@ const GemmKernel *select_kernel(int dtype, int sr, long long m, long long n, lon
     if (!kk && dtype == BTAS_I32) kk = find_gemm_kernel(kI32Mix, sr, 5, 0);
     if (!kk && dtype == BTAS_I32) kk = find_gemm_kernel(kI32Dpx, sr, 0, 0);
     if (!kk && dtype == BTAS_F32) kk = find_gemm_kernel(kF32X2, sr, 0, 0);
+    if (kk)
+        log_event("product %lldx%lldx%lld %s %s: variant %d ns %d cfg %d group 8 (%s)", m, n, k,
+                  dtype == BTAS_F32 ? "fp32" : "int32", sr == kMin ? "min-plus" : "max-plus", kk->var, kk->ns,
+                  kk->cfg, forced ? "environment" : "defaults");
     return kk;
 }
 
@@ -283,6 +319,7 @@ int btas_apsp_squarings(int64_t n) {
 
 btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, const void *A, int64_t lda,
                       const void *B, int64_t ldb, void *C, int64_t ldc, void *stream) {
+    Trace trace_("btas_gemm");
     const int sr = semiring & 0xff;
     const bool accumulate = (semiring & BTAS_GEMM_ACCUMULATE) != 0;
     const bool trans_b = (semiring & BTAS_GEMM_TRANS_B) != 0;
@@ -337,6 +374,8 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
     const size_t bt_bytes = trans_b ? 0 : align256((size_t)n * ldt * 4);
     int *pack_state = nullptr;
     if (packed && dtype == BTAS_I32) {
+        log_event("product %lldx%lldx%lld int32: packed path requested (range check and choice on the device)",
+                  (long long)m, (long long)n, (long long)k);
         // exact packed path, chosen on the device (pack.cu); the int32 path
         // below is enqueued too and bypassed when the packed one runs
         const long long ldad = (k + 3) & ~3LL, ldbu = (n + 7) & ~7LL;
@@ -394,6 +433,7 @@ int64_t btas_packed_products(void) {
 
 btas_status btas_gemv(int semiring, int dtype, int trans, int64_t m, int64_t n, const void *A, int64_t lda,
                       const void *x, void *y, void *stream) {
+    Trace trace_("btas_gemv");
     const int sr = semiring & 0xff;
     const bool accumulate = (semiring & BTAS_GEMM_ACCUMULATE) != 0;
     if (semiring & ~(0xff | BTAS_GEMM_ACCUMULATE)) return fail(BTAS_ERR_ARG, "btas_gemv: unknown flags");
@@ -416,6 +456,7 @@ btas_status btas_gemv(int semiring, int dtype, int trans, int64_t m, int64_t n, 
 }
 
 btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, int *iterations, void *stream) {
+    Trace trace_("btas_sssp");
     if (n < 0 || n > INT32_MAX) return fail(BTAS_ERR_ARG, "btas_sssp: n out of range");
     if (n == 0) {
         if (iterations) *iterations = 0;
@@ -463,6 +504,7 @@ btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, i
 
 btas_status btas_dot(int semiring, int dtype, int64_t n, const void *x, int64_t incx, const void *y,
                      int64_t incy, void *result, void *stream) {
+    Trace trace_("btas_dot");
     if (semiring != BTAS_MINPLUS && semiring != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_dot: semiring");
     if (dtype != BTAS_I32 && dtype != BTAS_F32) return fail(BTAS_ERR_ARG, "btas_dot: dtype");
     if (n < 0 || incx < 1 || incy < 1) return fail(BTAS_ERR_ARG, "btas_dot: size or stride");
@@ -482,6 +524,7 @@ btas_status btas_dot(int semiring, int dtype, int64_t n, const void *x, int64_t 
 
 btas_status btas_axpy(int semiring, int dtype, int64_t n, const void *alpha, const void *x, int64_t incx, void *y,
                       int64_t incy, void *stream) {
+    Trace trace_("btas_axpy");
     if (semiring != BTAS_MINPLUS && semiring != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_axpy: semiring");
     if (dtype != BTAS_I32 && dtype != BTAS_F32) return fail(BTAS_ERR_ARG, "btas_axpy: dtype");
     if (n < 0 || incx < 1 || incy < 1) return fail(BTAS_ERR_ARG, "btas_axpy: size or stride");
@@ -580,6 +623,7 @@ static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool e
 
 static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags, int *squarings_done,
                              int64_t *bound_out, int *path_out, cudaStream_t st) {
+    Trace trace_("btas_apsp");
     if (n < 0) return fail(BTAS_ERR_ARG, "btas_apsp: negative n");
     if (n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp: n too large");
     if (n == 0) {
@@ -619,6 +663,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         if (bound_out) *bound_out = (long long)(n - 1) * host[1];
         if (squarings_done) *squarings_done = host[2];
         if (path_out) *path_out = 1;
+        log_event("apsp n=%lld: one-block kernel, int32, %d changing squarings", (long long)n, host[2]);
         return BTAS_OK;
     }
 
@@ -627,7 +672,11 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     if (S >= 1 && n > apsp_small_max_n() && n <= apsp_mid_max_n() &&
         !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) && env_int("BTAS_APSP_NO_MID", 0) == 0) {
         const int r = apsp_mid_solve(n, W, D, S, early, squarings_done, bound_out, path_out, st);
-        if (r != kMidFallback) return static_cast<btas_status>(r);
+        if (r != kMidFallback) {
+            log_event("apsp n=%lld: cooperative kernel, int32 (status %d)", (long long)n, r);
+            return static_cast<btas_status>(r);
+        }
+        log_event("apsp n=%lld: cooperative launch not possible here, tiled path", (long long)n);
     }
 
     Workspace ws(st);
@@ -789,11 +838,14 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     }
     if (squarings_done) *squarings_done = done;
     if (path_out) *path_out = used;
+    log_event("apsp n=%lld: tiled kernels, representations %s%s%s, %d changing squarings", (long long)n,
+              used & 1 ? "int32 " : "", used & 2 ? "fp32-carrier " : "", used & 4 ? "u16x2" : "", done);
     return BTAS_OK;
 }
 
 btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void *Astar, int flags,
                          int *squarings_done, void *stream) {
+    Trace trace_("btas_closure");
     if (semiring != BTAS_MINPLUS && semiring != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_closure: semiring");
     if (dtype != BTAS_I32 && dtype != BTAS_F32) return fail(BTAS_ERR_ARG, "btas_closure: dtype");
     if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_closure: n out of range");
@@ -885,6 +937,7 @@ btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void
 
 btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Next, int flags, int *squarings_done,
                             void *stream) {
+    Trace trace_("btas_apsp_paths");
     if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp_paths: n out of range");
     if (flags & ~BTAS_APSP_EARLY_EXIT) return fail(BTAS_ERR_ARG, "btas_apsp_paths: unknown flags");
     if (n == 0) {
@@ -937,6 +990,7 @@ btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Ne
 }
 
 btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) {
+    Trace trace_("btas_apsp_fw");
     if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp_fw: n out of range");
     if (n == 0) return BTAS_OK;
     if (!W || !D) return fail(BTAS_ERR_ARG, "btas_apsp_fw: NULL pointer");
@@ -1023,6 +1077,7 @@ btas_status btas_apsp_ex(int64_t n, const int32_t *W, int32_t *D, int flags, int
 }
 
 btas_status btas_apsp_u16(int64_t n, const uint16_t *W, uint16_t *D, int max_w, int flags, void *stream) {
+    Trace trace_("btas_apsp_u16");
     if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp_u16: n out of range");
     if (max_w < 0 || max_w >= BTAS_INF_U16) return fail(BTAS_ERR_ARG, "btas_apsp_u16: max_w out of range");
     if (flags & ~BTAS_APSP_EARLY_EXIT) return fail(BTAS_ERR_ARG, "btas_apsp_u16: unknown flags");

@@ -12,6 +12,10 @@ namespace btas {
 void note_launch(int n = 1);
 // Sets the calling thread's message returned by btas_last_error_string.
 void record_error(const char *msg);
+// BTAS_LOG level (read once from the environment) and a printf-style line
+// to stderr when it is >= 1.
+int log_level();
+void log_event(const char *fmt, ...);
 // Device facts queried once per device (some attribute queries cost
 // hundreds of microseconds): compute capability major*10+minor, SM count,
 // SM clock in kHz.  Returns false if the device cannot be queried.
