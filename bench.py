@@ -190,6 +190,19 @@ def cpu_oracle_rate(inp, budget_s=15.0, threads=None):
     return total / dt / 1e9, threads, f"{R} rows x {n} x {n} of each of the 4 products ({total:.3g} terms, {dt:.1f} s)"
 
 
+def oracle_single_thread_gops(n=1024):
+    """The oracle's int32 min-plus product at n^3 on ONE host thread (the
+    paper's single-thread CPU methodology), in Gop/s."""
+    import gen
+    import oracle
+    A = gen.uniform_int(gen.BASE_SEED, 91, (n, n), 0, 10 ** 6)
+    B = gen.uniform_int(gen.BASE_SEED, 92, (n, n), 0, 10 ** 6)
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.tgemm(0, A, B)
+    return round(float(n) ** 3 / (time.perf_counter() - t0) / 1e9, 3)
+
+
 def oracle_fw_n256_us():
     """The oracle's Floyd-Warshall (one thread) on the n = 256 graph of the
     config timings, in microseconds: the CPU side of that comparison."""
@@ -434,7 +447,8 @@ def run_btas(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, sample = cpu_oracle_rate(inp)
         line["cpu_baseline"] = {"value": round(rate, 3), "unit": "Gop/s", "cores": threads, "kind": "oracle",
-                                "sample": sample, "fw_n256_us_1_thread": oracle_fw_n256_us()}
+                                "sample": sample, "fw_n256_us_1_thread": oracle_fw_n256_us(),
+                                "int32_product_1024_gops_1_thread": oracle_single_thread_gops()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
