@@ -9,10 +9,10 @@
 //
 // Kernel: 64 x 64 output tile, 256 threads with 4 x 4 outputs each, k staged
 // through a cp.async ring (A = D rows, B = D^T rows, both k-contiguous).  Per
-// term: an add, a DPX min that also reports which operand won
-// (__vibmin_s32), and a select of the index -- the running minimum is only
-// replaced by a strictly smaller sum, and k increases monotonically per
-// thread, so the smallest minimising k survives.
+// group of 4 consecutive k: the group minimum by DPX add-min (one per term);
+// only if it is strictly smaller than the running minimum is the first k of
+// the group attaining it recorded.  k increases monotonically per thread, so
+// the smallest minimising k survives.
 #include <cstdint>
 
 #include "common.cuh"
@@ -71,18 +71,27 @@ paths_square_kernel(int n, const int *__restrict__ D, long long ldd, const int *
 #pragma unroll
             for (int j = 0; j < 4; ++j) b[j] = *reinterpret_cast<const int4 *>(sb + (tc + 16 * j) * PLD + kk);
             const int k0 = kt * PBK + kk;
+            // Two levels: the minimum of the 4 sums of this k-group costs one
+            // DPX add-min per term; only when it beats the running minimum
+            // (rarely, once the minimum has settled) is the first k of the
+            // group that attains it looked up.  An equal group minimum keeps
+            // the earlier, smaller k.  Same result as a per-term argmin.
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int av = q == 0 ? a[i].x : q == 1 ? a[i].y : q == 2 ? a[i].z : a[i].w;
-                        const int bv = q == 0 ? b[j].x : q == 1 ? b[j].y : q == 2 ? b[j].z : b[j].w;
-                        bool keep;
-                        val[i][j] = __vibmin_s32(val[i][j], av + bv, &keep);
-                        idx[i][j] = keep ? idx[i][j] : k0 + q;
+                for (int j = 0; j < 4; ++j) {
+                    int cm = __viaddmin_s32(a[i].x, b[j].x, 0x7FFFFFFF);
+                    cm = __viaddmin_s32(a[i].y, b[j].y, cm);
+                    cm = __viaddmin_s32(a[i].z, b[j].z, cm);
+                    cm = __viaddmin_s32(a[i].w, b[j].w, cm);
+                    if (cm < val[i][j]) {
+                        val[i][j] = cm;
+                        idx[i][j] = k0 + (a[i].x + b[j].x == cm   ? 0
+                                          : a[i].y + b[j].y == cm ? 1
+                                          : a[i].z + b[j].z == cm ? 2
+                                                                  : 3);
                     }
+                }
         }
     }
     cp_async_wait<0>();
