@@ -850,11 +850,17 @@ def next_rows(args, btas, torch):
     np_ = min(n, 4096)
     Wp = W[:np_, :np_].contiguous()
     t_p = timed(lambda: btas.apsp_paths(Wp), reps=1)
-    out["apsp_paths"] = {"n": np_, "ms": round(t_p * 1e3, 3)}
+    sq_p = btas.apsp_paths(Wp, info=True)[2]["squarings"]
+    terms_p = min(btas.btas_apsp_squarings(np_), sq_p + 1) * float(np_) ** 3
+    out["apsp_paths"] = {"n": np_, "ms": round(t_p * 1e3, 3), "squarings_computed": int(terms_p / float(np_) ** 3),
+                         "terms_tops": round(terms_p / t_p / 1e12, 2)}
     Wf = torch.where(W[:np_, :np_] == btas.INF_I32, torch.tensor(float("inf"), device="cuda"),
                      W[:np_, :np_].float()).contiguous()
     t_c = timed(lambda: btas.closure(Wf, "min"), reps=1)
-    out["closure_fp32_minplus"] = {"n": np_, "ms": round(t_c * 1e3, 3)}
+    sq_c = btas.closure(Wf, "min", info=True)[1]["squarings"]
+    terms_c = min(btas.btas_apsp_squarings(np_) + 1, sq_c + 1) * float(np_) ** 3
+    out["closure_fp32_minplus"] = {"n": np_, "ms": round(t_c * 1e3, 3), "squarings_computed": int(terms_c / float(np_) ** 3),
+                                   "terms_tops": round(terms_c / t_c / 1e12, 2)}
     # exact packed int32 products (BTAS_GEMM_PACKED): small-range operands
     # (values in [-4000, 4000]) on the packed kernel vs the int32 kernel
     del Wp, Wf

@@ -242,15 +242,17 @@ def btas_apsp_paths(n, W, D, Next, flags, squarings_done_ptr, stream) -> int:
     return lib().btas_apsp_paths(n, W, D, Next, flags, squarings_done_ptr, stream)
 
 
-def apsp_paths(W, early_exit=True, stream=None):
-    """APSP distances and next-hop matrix (int32 CUDA tensors)."""
+def apsp_paths(W, early_exit=True, stream=None, info=False):
+    """APSP distances and next-hop matrix (int32 CUDA tensors); with
+    info=True also {"squarings": squarings that changed D}."""
     torch = _torch()
     n = W.shape[0]
     D = torch.empty_like(W)
     Nx = torch.empty_like(W)
-    check(btas_apsp_paths(n, W.data_ptr(), D.data_ptr(), Nx.data_ptr(), APSP_EARLY_EXIT if early_exit else 0, None,
-                          _stream(stream)))
-    return D, Nx
+    sq = ctypes.c_int(0)
+    check(btas_apsp_paths(n, W.data_ptr(), D.data_ptr(), Nx.data_ptr(), APSP_EARLY_EXIT if early_exit else 0,
+                          ctypes.addressof(sq), _stream(stream)))
+    return (D, Nx, {"squarings": sq.value}) if info else (D, Nx)
 
 
 def btas_apsp_fw(n, W, D, stream) -> int:
