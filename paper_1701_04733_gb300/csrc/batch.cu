@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.one = 1;
             a.vec_a = ((reinterpret_cast<uintptr_t>(cur) & 15) == 0) && ((ldcur & 3) == 0);
             a.vec_b = 1;
+            a.ro_a = s == 1;  // W; later iterates are written by this launch
             // forms of D_{s-1} are in set (s-1) & 1, D_s goes to set s & 1
             const bool more = s < S && I.use_u16;
             // every finite entry of D_s is <= 2 max(D_{s-1}); if even 4 max(D_{s-1})
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.one = 1;
             a.vec_a = ((reinterpret_cast<uintptr_t>(I.A) & 15) == 0) && ((I.lda & 3) == 0);
             a.vec_b = 1;
+            a.ro_a = 1;  // this step's input, written by an earlier launch
             a.maxfin = I.maxfin_ptr;
             if (I.use_u16) {
                 slot = BTAS_BATCH_SLOT_SQUARE_U16;
@@ -266,6 +268,8 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.one = 1;
             a.vec_a = ((reinterpret_cast<uintptr_t>(I.A) & 15) == 0) && ((I.lda & 3) == 0);
             a.vec_b = ((reinterpret_cast<uintptr_t>(a.Bt) & 15) == 0) && ((a.ldb & 3) == 0);
+            a.ro_a = 1;                // the caller's A
+            a.ro_b = I.trans_b ? 1 : 0;  // the caller's B^T, or Q0 from this launch's transposes
             slot = I.dtype == BTAS_I32 ? BTAS_BATCH_SLOT_GEMM_I32 : BTAS_BATCH_SLOT_GEMM_F32;
             if (I.dtype == BTAS_I32) {
                 if (I.sr == kMin) gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid);

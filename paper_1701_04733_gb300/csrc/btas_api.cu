@@ -248,6 +248,8 @@ btas_status run_nt(int dtype, int sr, const GemmArgs &a, cudaStream_t st) {
     GemmArgs args = a;
     args.group_m = group_m;
     args.one = 1;
+    // one standalone launch never writes its own operands
+    args.ro_a = args.ro_b = 1;
     BTAS_CUDA(k->launch(args, st), "tropical gemm launch");
     return BTAS_OK;
 }

@@ -48,8 +48,8 @@ paths_square_kernel(int n, const int *__restrict__ D, long long ldd, const int *
     auto load = [&](int s, int kt) {
         int *sa = smem + s * PSTAGE;
         int *sb = sa + PBM * PLD;
-        stage_rows<int, PBM, PBK, PLD, PNT>(sa, D, ldd, bm, n, kt * PBK, n, vec_a != 0, kInfI32, tid);
-        stage_rows<int, PBM, PBK, PLD, PNT>(sb, Dt, ldt, bn, n, kt * PBK, n, true, kInfI32, tid);
+        stage_rows<int, PBM, PBK, PLD, PNT>(sa, D, ldd, bm, n, kt * PBK, n, vec_a != 0, kInfI32, tid, true);
+        stage_rows<int, PBM, PBK, PLD, PNT>(sb, Dt, ldt, bn, n, kt * PBK, n, true, kInfI32, tid, true);
     };
 #pragma unroll
     for (int s = 0; s < PST - 1; ++s) {

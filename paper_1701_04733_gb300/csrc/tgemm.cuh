@@ -58,7 +58,7 @@ struct TileCfg {
 
 template <typename T, int ROWS, int BK, int LD, int NT>
 __device__ __forceinline__ void stage_rows(T *sm, const T *g, long long ldg, int row0, int rows_total,
-                                           int k0, int K, bool vec, T fill, int tid) {
+                                           int k0, int K, bool vec, T fill, int tid, bool ro = false) {
     constexpr int CPR = BK / 4;
     constexpr int CHUNKS = ROWS * CPR;
     static_assert(CHUNKS % NT == 0, "chunks per thread");
@@ -70,6 +70,13 @@ __device__ __forceinline__ void stage_rows(T *sm, const T *g, long long ldg, int
         T *dst = sm + r * LD + kc;
         if (vec && gr < rows_total && gk + 4 <= K) {
             cp_async16(dst, g + (long long)gr * ldg + gk);
+        } else if (ro) {
+            // asynchronous element copies: unaligned rows do not stall the pipeline
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (gr < rows_total && gk + e < K) cp_async4(dst + e, g + (long long)gr * ldg + gk + e);
+                else dst[e] = fill;
+            }
         } else {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -324,8 +331,8 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
     auto load_stage = [&](int s, int kt) {
         T *sa = smem + s * Cfg::kStageElems;
         T *sb = sa + BM * LD;
-        stage_rows<T, BM, BK, LD, NT>(sa, A, args.lda, bm, M, kt * BK, K, va, ident, tid);
-        stage_rows<T, BN, BK, LD, NT>(sb, Bt, args.ldb, bn, N, kt * BK, K, vb, ident, tid);
+        stage_rows<T, BM, BK, LD, NT>(sa, A, args.lda, bm, M, kt * BK, K, va, ident, tid, args.ro_a != 0);
+        stage_rows<T, BN, BK, LD, NT>(sb, Bt, args.ldb, bn, N, kt * BK, K, vb, ident, tid, args.ro_b != 0);
     };
 
 #pragma unroll

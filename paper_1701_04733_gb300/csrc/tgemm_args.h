@@ -20,6 +20,8 @@ struct GemmArgs {
     const int *skip;    // optional: *skip == 0 => C = prev (converged squaring)
     int one;            // the constant 1, opaque to the compiler
     int vec_a, vec_b;   // operand rows are 16-byte aligned (cp.async usable)
+    int ro_a, ro_b;     // operand not written by any CTA of this launch: unaligned and edge
+                        // elements may then be staged with 4-byte cp.async through L1
     int group_m;        // CTA rasterisation: tile rows per group
     int *maxfin;        // optional: atomicMax of the largest finite output (as int)
     const int *bypass;  // optional: *bypass != 0 => do nothing (another path computes C)
