@@ -593,21 +593,21 @@ static btas_status squaring_loop(int dtype, long long n, int S, const void *cur0
 // shared device); the tiled path then computes the same result.
 constexpr int kMidFallback = -1;
 
-static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool early, int *squarings_done,
-                          int64_t *bound_out, int *path_out, cudaStream_t st) {
+static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool early, bool packed_ok,
+                          int *squarings_done, int64_t *bound_out, int *path_out, cudaStream_t st) {
     Workspace ws(st);
     const size_t mid_bytes = apsp_mid_workspace(n, S);
     BTAS_CUDA(ws.alloc(mid_bytes + 256), "workspace alloc");
     int *info = reinterpret_cast<int *>(static_cast<char *>(ws.p) + mid_bytes);
     BTAS_CUDA(cudaMemsetAsync(info, 0, 256, st), "memset");
-    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, D, n, ws.p, info, st);
+    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, ws.p, info, st);
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
         cudaGetLastError();
         return kMidFallback;
     }
     BTAS_CUDA(le, "mid apsp");
-    int host[4] = {0, 0, 0, 0};
-    BTAS_CUDA(cudaMemcpyAsync(host, info, 16, cudaMemcpyDeviceToHost, st), "info readback");
+    int host[5] = {0, 0, 0, 0, 0};
+    BTAS_CUDA(cudaMemcpyAsync(host, info, 20, cudaMemcpyDeviceToHost, st), "info readback");
     BTAS_CUDA(cudaStreamSynchronize(st), "mid apsp sync");
     if (host[3] != 0) return fail(BTAS_ERR_TIMEOUT, "btas_apsp: a bounded grid barrier wait expired");
     if (host[0] != 0) {
@@ -619,7 +619,9 @@ static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool e
     }
     if (bound_out) *bound_out = (long long)(n - 1) * host[1];
     if (squarings_done) *squarings_done = host[2];
-    if (path_out) *path_out = 1;
+    if (path_out) *path_out = host[4];
+    log_event("apsp n=%lld: cooperative kernel, representations 0x%x, %d changing squarings", (long long)n, host[4],
+              host[2]);
     return BTAS_OK;
 }
 
@@ -646,7 +648,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
 
     // small graphs: the whole solve in one thread block (one launch, one
     // read-back) on the int32 arithmetic; BTAS_APSP_NO_SMALL=1 disables it
-    if (S >= 1 && n <= apsp_small_max_n() && !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) &&
+    if (S >= 1 && n <= apsp_small_limit() && !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) &&
         env_int("BTAS_APSP_NO_SMALL", 0) == 0) {
         Workspace ws(st);
         BTAS_CUDA(ws.alloc(256), "workspace alloc");
@@ -671,13 +673,11 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
 
     // mid-size graphs: every squaring in one cooperative launch (one
     // read-back); BTAS_APSP_NO_MID=1 disables it
-    if (S >= 1 && n > apsp_small_max_n() && n <= apsp_mid_max_n() &&
+    if (S >= 1 && n > apsp_small_limit() && n <= apsp_mid_max_n() &&
         !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) && env_int("BTAS_APSP_NO_MID", 0) == 0) {
-        const int r = apsp_mid_solve(n, W, D, S, early, squarings_done, bound_out, path_out, st);
-        if (r != kMidFallback) {
-            log_event("apsp n=%lld: cooperative kernel, int32 (status %d)", (long long)n, r);
-            return static_cast<btas_status>(r);
-        }
+        const int r = apsp_mid_solve(n, W, D, S, early, !(flags & BTAS_APSP_FORCE_I32), squarings_done, bound_out,
+                                     path_out, st);
+        if (r != kMidFallback) return static_cast<btas_status>(r);
         log_event("apsp n=%lld: cooperative launch not possible here, tiled path", (long long)n);
     }
 

@@ -1,23 +1,41 @@
 // APSP by repeated squaring (Sec. III) for mid-size graphs in ONE
 // cooperative launch.
 //
-// Between the one-block kernel (n <= 128) and the tiled product kernels, a
+// Between the one-block kernel (n <= 128) and the tiled product kernels a
 // solve is bound by launches and host round trips: a few dozen tiles per
 // squaring cannot fill the GPU, and every squaring waits for the previous
 // one's change flag.  Here one cooperative grid runs the domain check and all
-// squarings, separated by grid barriers.  Each squaring is split into (64 x
-// 64 output tile, k-chunk) work items so that every SM has work; an item
-// computes the tile's partial minimum over its k-chunk and merges it into
-// the output with atomicMin -- exact, because (+) = min is associative,
-// commutative and idempotent, and the INF clamp commutes with min.  The
-// arithmetic per term is the int32 product's (DPX add-min), so results are
-// bit-identical to the other paths.
+// squarings, with ONE grid barrier per squaring.
 //
-// Squaring s reads X_{s-1} (X_0 = a pitch-n copy of W) and writes X_s into
-// one of three rotating buffers; X_{s+1}'s buffer is reset to INF while
-// squaring s is checked for change.  Every grid barrier wait is bounded (clock64); on
-// expiry the kernel records BTAS_ERR_TIMEOUT and all blocks return.
+// Work items.  Squaring s is split into (64 x 64 output tile, k-chunk) items
+// so that every SM has work; an item computes the tile's partial minimum p
+// over its k-chunk.
+//
+// Merging without a second pass.  With a zero diagonal and non-negative
+// weights X_s <= X_{s-1} entrywise: the terms k = i and k = j of the product
+// are X_{s-1}[i][j] itself.  So the item whose chunk holds k = j has
+// p <= X_{s-1}[i][j], and X_s[i][j] < X_{s-1}[i][j] exactly when some item
+// finds p < X_{s-1}[i][j].  An item merges p into X_s (reset to INF
+// beforehand) with atomicMin where p < X_{s-1}[i][j], or where p equals it
+// and the item holds k = j; any other p cannot be the minimum.  The same
+// comparison is the change test, so a squaring needs no checking pass, and
+// (+) = min being associative, commutative and idempotent makes the merge
+// exact in any order.
+//
+// Precision per squaring.  Every finite entry of X_s is one of the values
+// merged during squaring s, so their maximum bounds max(X_s).  When the
+// bound is <= 16383 the next squaring runs on packed 16-bit pairs (two terms
+// per DPX add-min, INF as 0x7FFF; sums of operands stay <= 32766, so 0x7FFF
+// still means "no path"), else on int32 (DPX add-min, INF absorbed by the
+// clamp at INF - 2^28).  Both are exact: results are bit-identical to the
+// other paths.
+//
+// Buffers.  X_s lives in buf[(s - 1) % 3] and X_0, a pitch-ldx copy of W, in
+// buf2.  Squaring s reads X_{s-1}, merges into X_s and resets X_{s+1}'s
+// buffer, which held X_{s-2}.  Every grid barrier wait is bounded (clock64);
+// on expiry the kernel records BTAS_ERR_TIMEOUT and all blocks return.
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -27,6 +45,8 @@ namespace btas {
 namespace {
 
 constexpr int kT = 64, kThreads = 256, kKc = 32;  // tile edge, threads, k step
+constexpr int kLdA = kT + 4;                      // k-major A stage row (words)
+constexpr int kU16Max = 16383;                    // operand bound of the packed squaring
 
 struct MidArgs {
     const int *W;
@@ -34,15 +54,22 @@ struct MidArgs {
     int n;
     int S;
     int early;
+    int u16_ok;  // 0: int32 squarings only
     int *D;
     long long ldd;
     int *buf0, *buf1, *buf2;  // n x ldx each; columns n .. ldx-1 always hold INF
     long long ldx;            // round4(n): 16-byte rows for vector staging
-    int kchunks;      // k-chunks per output tile
-    int chunk;        // k-chunk length (multiple of kKc)
-    unsigned *bar;    // [0] arrivals, [32] generation (separate 128-byte lines)
-    int *info;        // [0] bad entries, [1] max weight, [2] squarings that changed, [3] status, [4..] changed[s]
+    int kchunks;              // k-chunks per output tile
+    int chunk;                // k-chunk length (multiple of kKc)
+    unsigned *bar;            // [0] arrivals, [32] generation, [64 + s] largest value merged in squaring s
+    int *info;  // [0] bad entries, [1] max weight, [2] squarings that changed, [3] status,
+                // [4] representations used (1 int32, 4 packed 16-bit), [4 + s] squaring s changed X
     long long timeout_cycles;
+};
+
+struct MidSmem {
+    int a[2][kKc][kLdA];  // A stage, k-major: a[k][row]; packed mode: duplicated 16-bit words
+    int b[2][kKc][kT];    // B stage: b[k][col]; packed mode: b[k][pair] in the first kT / 2 words
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -90,9 +117,147 @@ __device__ bool grid_barrier(const MidArgs &a) {
 
 __device__ __forceinline__ int *bufp(const MidArgs &a, int i) { return i == 0 ? a.buf0 : i == 1 ? a.buf1 : a.buf2; }
 
-__global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
-    __shared__ __align__(16) int sa[kT][kKc + 4];
-    __shared__ __align__(16) int sb[kKc][kT];
+// 16-bit form of an entry of a packed squaring's operand: <= 16383, or 0x7FFF for INF
+__device__ __forceinline__ unsigned u16_of(int v) { return (unsigned)min(v, BTAS_INF_U16); }
+
+// One k-step of operands from global memory (L2: X is written by other
+// blocks), into registers.  A = X[bm.., kb..] (64 x 32) as 16-byte vectors
+// along k, B = X[kb.., bn..] (32 x 64) along columns.  Lane pairs of a warp
+// read 32 contiguous bytes of one of 16 rows, which also makes the
+// transposing shared-memory stores below conflict-free.  A vector that
+// starts inside the matrix ends inside the row (ldx is a multiple of 4) and
+// reads INF padding past column n-1; k-chunks end on multiples of 32, so no
+// vector crosses one.
+__device__ __forceinline__ void fetch(const int *in, long long ldx, int n, int bm, int bn, int kb, int k1, int tid,
+                                      int4 (&va)[2], int4 (&vb)[2]) {
+    const int4 inf4 = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int e = tid + q * kThreads;
+        const int kg = (e & 1) + 2 * ((e >> 5) & 3), r = ((e >> 1) & 15) + 16 * (e >> 7);
+        const int gi = bm + r, gk = kb + 4 * kg;
+        va[q] = (gi < n && gk < k1) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)gi * ldx + gk)) : inf4;
+        const int rk = e >> 4, cb = (e & 15) * 4;
+        const int gkb = kb + rk, gj = bn + cb;
+        vb[q] = (gkb < k1 && gj < n) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)gkb * ldx + gj)) : inf4;
+    }
+}
+
+// Registers -> one shared stage: A transposed to k-major, B as is; the
+// packed form stores A as duplicated 16-bit words and B as column pairs.
+template <bool U16>
+__device__ __forceinline__ void stash(MidSmem &sm, int buf, int tid, const int4 (&va)[2], const int4 (&vb)[2]) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int e = tid + q * kThreads;
+        const int kg = (e & 1) + 2 * ((e >> 5) & 3), r = ((e >> 1) & 15) + 16 * (e >> 7);
+        int *col = &sm.a[buf][4 * kg][r];
+        if (U16) {
+            col[0] = (int)(u16_of(va[q].x) * 0x10001u);
+            col[kLdA] = (int)(u16_of(va[q].y) * 0x10001u);
+            col[2 * kLdA] = (int)(u16_of(va[q].z) * 0x10001u);
+            col[3 * kLdA] = (int)(u16_of(va[q].w) * 0x10001u);
+        } else {
+            col[0] = va[q].x;
+            col[kLdA] = va[q].y;
+            col[2 * kLdA] = va[q].z;
+            col[3 * kLdA] = va[q].w;
+        }
+        const int rk = e >> 4, cb = (e & 15) * 4;
+        if (U16) {
+            const uint2 w = make_uint2(u16_of(vb[q].x) | (u16_of(vb[q].y) << 16),
+                                       u16_of(vb[q].z) | (u16_of(vb[q].w) << 16));
+            *reinterpret_cast<uint2 *>(&sm.b[buf][rk][cb / 2]) = w;
+        } else {
+            *reinterpret_cast<int4 *>(&sm.b[buf][rk][cb]) = vb[q];
+        }
+    }
+}
+
+// One work item: the 64 x 64 tile (bm, bn) of X_{s-1} (x) X_{s-1} over
+// k in [k0, k1), merged into out.  256 threads, 4 x 4 outputs each; the
+// next k-step's operands are in flight while this one is computed.
+template <bool U16>
+__device__ __forceinline__ void run_item(const MidArgs &a, const int *in, int *out, int bm, int bn, int k0, int k1,
+                                         MidSmem &sm, int tid, bool &ch, int &mx) {
+    const int n = a.n;
+    const long long ldx = a.ldx;
+    const int ty = tid >> 4, tx = tid & 15;
+    const int r0 = bm + ty * 4, c0 = bn + tx * 4;
+    // X_{s-1} over this thread's outputs (the merge bound), fetched first
+    int4 old[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        old[r] = (r0 + r < n && c0 < n) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)(r0 + r) * ldx + c0))
+                                        : make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+    int acc[4][4];             // int32 mode
+    unsigned acc16[4][2];      // packed mode: columns (c0 + 2p, c0 + 2p + 1) in (low, high)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = kInfI32;
+        acc16[r][0] = acc16[r][1] = kInfU16x2;
+    }
+    int4 va[2], vb[2];
+    fetch(in, ldx, n, bm, bn, k0, k1, tid, va, vb);
+    stash<U16>(sm, 0, tid, va, vb);
+    __syncthreads();
+    int buf = 0;
+    for (int kb = k0; kb < k1; kb += kKc) {
+        const bool more = kb + kKc < k1;
+        if (more) fetch(in, ldx, n, bm, bn, kb + kKc, k1, tid, va, vb);
+#pragma unroll 8
+        for (int k = 0; k < kKc; ++k) {
+            const int4 av = *reinterpret_cast<const int4 *>(&sm.a[buf][k][ty * 4]);
+            const int ar[4] = {av.x, av.y, av.z, av.w};
+            if (U16) {
+                const uint2 bv = *reinterpret_cast<const uint2 *>(&sm.b[buf][k][tx * 2]);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    acc16[r][0] = u16x2_addmin((unsigned)ar[r], bv.x, acc16[r][0]);
+                    acc16[r][1] = u16x2_addmin((unsigned)ar[r], bv.y, acc16[r][1]);
+                }
+            } else {
+                const int4 bv = *reinterpret_cast<const int4 *>(&sm.b[buf][k][tx * 4]);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    acc[r][0] = __viaddmin_s32(ar[r], bv.x, acc[r][0]);
+                    acc[r][1] = __viaddmin_s32(ar[r], bv.y, acc[r][1]);
+                    acc[r][2] = __viaddmin_s32(ar[r], bv.z, acc[r][2]);
+                    acc[r][3] = __viaddmin_s32(ar[r], bv.w, acc[r][3]);
+                }
+            }
+        }
+        if (more) stash<U16>(sm, buf ^ 1, tid, va, vb);
+        __syncthreads();
+        buf ^= 1;
+    }
+    // merge: p < old (a change), or p == old from the item holding k = j
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = r0 + r;
+        const int o[4] = {old[r].x, old[r].y, old[r].z, old[r].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = c0 + c;
+            int p;
+            if (U16) {
+                const unsigned h = (acc16[r][c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
+                p = h >= (unsigned)BTAS_INF_U16 ? kInfI32 : (int)h;
+            } else {
+                p = clamp_i32<kMin>(acc[r][c]);
+            }
+            if (i < n && j < n && p < kInfI32 && (p < o[c] || (p == o[c] && j >= k0 && j < k1))) {
+                atomicMin(out + (long long)i * ldx + j, p);
+                mx = max(mx, p);
+                ch |= p < o[c];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) {
+    __shared__ __align__(16) MidSmem sm;
     const int n = a.n, tid = threadIdx.x;
     const long long ldx = a.ldx;
     const long long nx = (long long)n * ldx;
@@ -129,86 +294,40 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
 
     const int tiles = (n + kT - 1) / kT;
     const int items = tiles * tiles * a.kchunks;
-    const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads, 4 x 4 outputs each
-    const int *in = a.buf2;  // X_0
-    int cur = 0, done = 0;   // X_s (s >= 1) lives in buf[(s - 1) % 3]
+    const int4 inf4 = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+    const int *in = a.buf2;               // X_0
+    int cur = 0, done = 0, path = 0;      // X_s (s >= 1) lives in buf[(s - 1) % 3]
+    int bound = ld_acquire_i32(a.info + 1);  // >= every finite entry of X_{s-1}
     for (int s = 1; s <= a.S; ++s) {
         int *out = bufp(a, cur);
-        // phase A: partial products merged with atomicMin
+        if (s < a.S) {
+            int4 *nxt = reinterpret_cast<int4 *>(bufp(a, (cur + 1) % 3));
+            for (long long idx = gtid; idx < nx / 4; idx += gthreads) nxt[idx] = inf4;
+        }
+        const bool u16 = a.u16_ok && bound <= kU16Max;
+        path |= u16 ? 4 : 1;
+        bool ch = false;
+        int mx = 0;
         for (int it = blockIdx.x; it < items; it += gridDim.x) {
             const int tile = it / a.kchunks, kc = it % a.kchunks;
             const int bm = (tile / tiles) * kT, bn = (tile % tiles) * kT;
             const int k0 = kc * a.chunk, k1 = min(n, k0 + a.chunk);
             if (k0 >= k1) continue;
-            int acc[4][4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = kInfI32;
-            for (int kb = k0; kb < k1; kb += kKc) {
-                // stage A[bm.., kb..] (64 x 32) and B[kb.., bn..] (32 x 64) with
-                // 16-byte loads, all issued before the shared-memory stores.  A
-                // vector that starts inside the matrix ends inside the row (ldx
-                // is a multiple of 4) and reads INF padding past column n-1;
-                // k-chunks end on multiples of 32, so no vector crosses one.
-                int4 va[2], vb[2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int e = tid + q * kThreads;
-                    const int ra = e >> 3, ca = (e & 7) * 4;  // A: 8 vectors per row
-                    const int gi = bm + ra, gka = kb + ca;
-                    va[q] = (gi < n && gka < k1) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)gi * ldx + gka))
-                                                 : make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
-                    const int rb = e >> 4, cb = (e & 15) * 4;  // B: 16 vectors per row
-                    const int gkb = kb + rb, gj = bn + cb;
-                    vb[q] = (gkb < k1 && gj < n) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)gkb * ldx + gj))
-                                                 : make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
-                }
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int e = tid + q * kThreads;
-                    *reinterpret_cast<int4 *>(&sa[e >> 3][(e & 7) * 4]) = va[q];
-                    *reinterpret_cast<int4 *>(&sb[e >> 4][(e & 15) * 4]) = vb[q];
-                }
-                __syncthreads();
-#pragma unroll 4
-                for (int k = 0; k < kKc; ++k) {
-                    int av[4];
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) av[r] = sa[ty * 4 + r][k];
-                    const int4 b = *reinterpret_cast<const int4 *>(&sb[k][tx * 4]);
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        acc[r][0] = __viaddmin_s32(av[r], b.x, acc[r][0]);
-                        acc[r][1] = __viaddmin_s32(av[r], b.y, acc[r][1]);
-                        acc[r][2] = __viaddmin_s32(av[r], b.z, acc[r][2]);
-                        acc[r][3] = __viaddmin_s32(av[r], b.w, acc[r][3]);
-                    }
-                }
-                __syncthreads();
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int i = bm + ty * 4 + r, j = bn + tx * 4 + c;
-                    const int v = clamp_i32<kMin>(acc[r][c]);
-                    if (i < n && j < n && v < kInfI32) atomicMin(out + (long long)i * ldx + j, v);
-                }
+            if (u16)
+                run_item<true>(a, in, out, bm, bn, k0, k1, sm, tid, ch, mx);
+            else
+                run_item<false>(a, in, out, bm, bn, k0, k1, sm, tid, ch, mx);
         }
-        if (!grid_barrier(a)) return;
-        // phase B: change check of X_s against X_{s-1}; X_{s+1}'s buffer to INF
-        {
-            int *nxt = bufp(a, (cur + 1) % 3);
-            bool ch = false;
-            for (long long idx = gtid; idx < nx; idx += gthreads) {
-                ch |= __ldcg(out + idx) != __ldcg(in + idx);
-                if (s < a.S) nxt[idx] = kInfI32;
-            }
-            if (__any_sync(0xffffffffu, ch) && (tid & 31) == 0) atomicOr(a.info + 4 + s, 1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const bool any = __any_sync(0xffffffffu, ch);
+        if ((tid & 31) == 0) {
+            if (any) atomicOr(a.info + 4 + s, 1);
+            if (mx > 0) atomicMax(reinterpret_cast<int *>(a.bar + 64 + s), mx);
         }
         if (!grid_barrier(a)) return;
         const int changed = ld_acquire_i32(a.info + 4 + s);
+        bound = ld_acquire_i32(reinterpret_cast<const int *>(a.bar + 64 + s));
         done += changed;
         in = out;
         cur = (cur + 1) % 3;
@@ -217,7 +336,31 @@ __global__ void __launch_bounds__(kThreads) apsp_mid_kernel(const MidArgs a) {
     // result: X_last -> D (W was read only in phase 0, so D may be W)
     for (long long idx = gtid; idx < (long long)n * n; idx += gthreads)
         a.D[(idx / n) * a.ldd + idx % n] = __ldcg(in + (idx / n) * ldx + idx % n);
-    if (blockIdx.x == 0 && tid == 0) a.info[2] = done;
+    if (blockIdx.x == 0 && tid == 0) {
+        a.info[2] = done;
+        a.info[4] = path;
+    }
+}
+
+// k-chunk length for n: the number of (tile, chunk) items per SM sets the
+// compute time, the number of waves of co-resident blocks the exposed load
+// latency (about two k-steps per wave).
+int pick_chunk(int n, int sms, int grid_max) {
+    const int tiles = (n + kT - 1) / kT;
+    const int kmax = (n + kKc - 1) / kKc * kKc;
+    int best = kKc;
+    long long best_cost = -1;
+    for (int c = kKc; c < 2 * kmax; c *= 2) {
+        const int len = std::min(c, kmax);
+        const long long items = (long long)tiles * tiles * ((n + len - 1) / len);
+        const long long cost = (items + sms - 1) / sms * len + (items + grid_max - 1) / grid_max * 2 * kKc;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = len;
+        }
+        if (len == kmax) break;
+    }
+    return best;
 }
 
 }  // namespace
@@ -229,8 +372,8 @@ size_t apsp_mid_workspace(long long n, int S) {
     return 3 * mat + 256 + (((size_t)(S + 8) * 4 + 255) & ~size_t(255));
 }
 
-cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd, void *ws,
-                            int *info_out_dev, cudaStream_t st) {
+cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
+                            long long ldd, void *ws, int *info_out_dev, cudaStream_t st) {
     // device facts and the kernel's occupancy, queried once per device
     DeviceInfo di{};
     int dev = 0;
@@ -248,22 +391,24 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
             if (dev < 64) cached_per_sm[dev] = per_sm;
         }
     }
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     const int sms = di.sms, clk_khz = di.clock_khz;
     const int tiles = (n + kT - 1) / kT;
-    const int want = 2 * sms;
-    int kchunks = std::max(1, std::min((n + kKc - 1) / kKc, (want + tiles * tiles - 1) / (tiles * tiles)));
-    int chunk = ((n + kchunks - 1) / kchunks + kKc - 1) / kKc * kKc;
-    kchunks = (n + chunk - 1) / chunk;
-    const int grid = std::max(1, std::min(tiles * tiles * kchunks, std::min(want, per_sm * sms)));
+    const int grid_max = per_sm * sms;
+    const int chunk = pick_chunk(n, sms, grid_max);
+    const int kchunks = (n + chunk - 1) / chunk;
+    const int grid = std::max(1, std::min(tiles * tiles * kchunks, grid_max));
     const long long ldx = (n + 3) & ~3LL;
     const size_t mat = ((size_t)n * ldx * 4 + 255) & ~size_t(255);
     char *base = static_cast<char *>(ws);
+    const char *no_u16 = getenv("BTAS_MID_NO_U16");
     MidArgs a{};
     a.W = W;
     a.ldw = ldw;
     a.n = n;
     a.S = S;
     a.early = early ? 1 : 0;
+    a.u16_ok = (!packed_ok || (no_u16 && *no_u16 && atoi(no_u16) != 0)) ? 0 : 1;
     a.D = D;
     a.ldd = ldd;
     a.ldx = ldx;
@@ -275,7 +420,9 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     a.kchunks = kchunks;
     a.chunk = chunk;
     a.timeout_cycles = (long long)(2.0 * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);  // about 2 s
-    cudaError_t e = cudaMemsetAsync(base + 3 * mat, 0, 256, st);
+    // barrier words and the per-squaring maxima (512 bytes: the workspace
+    // holds 256 + at least 256 bytes after the three matrices)
+    cudaError_t e = cudaMemsetAsync(base + 3 * mat, 0, 512, st);
     if (e != cudaSuccess) return e;
     void *args[] = {&a};
     e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(apsp_mid_kernel), dim3(grid), dim3(kThreads), args, 0,

@@ -128,13 +128,13 @@ extern "C" btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D
     // Small and mid-size graphs: the one-block kernel, or the cooperative
     // kernel when its three iterates fit in the scratch matrices; both take
     // their status words from the flag area and need no read-back here.
-    if (n <= apsp_small_max_n()) {
+    if (n <= apsp_small_limit()) {
         e = launch_apsp_small(W, n, (int)n, S, true, D, n, flags, st);
         if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
         return BTAS_OK;
     }
     if (n <= apsp_mid_max_n() && apsp_mid_workspace(n, S) <= 2 * kMatBytes) {
-        e = launch_apsp_mid(W, n, (int)n, S, true, D, n, X, flags, st);
+        e = launch_apsp_mid(W, n, (int)n, S, true, true, D, n, X, flags, st);
         if (e == cudaSuccess) return BTAS_OK;
         if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorNotSupported)
             return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));

@@ -372,11 +372,11 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
         int *info = r->dflag;  // 2S + 4 >= S + 5 ints
         cudaMemsetAsync(info, 0, (size_t)(2 * r->S + 4) * 4, sv->compute);
         cudaError_t e;
-        if (r->n <= apsp_small_max_n())
+        if (r->n <= apsp_small_limit())
             e = launch_apsp_small(static_cast<const int *>(r->P[0]), r->ldp, r->n, r->S, true,
                                   static_cast<int *>(r->P[1]), r->ldp, info, sv->compute);
         else
-            e = launch_apsp_mid(static_cast<const int *>(r->P[0]), r->ldp, r->n, r->S, true,
+            e = launch_apsp_mid(static_cast<const int *>(r->P[0]), r->ldp, r->n, r->S, true, true,
                                 static_cast<int *>(r->P[1]), r->ldp, r->Q[0], info, sv->compute);
         if (e != cudaSuccess) return -1;
         cudaMemcpyAsync(sv->h_flags + i, info, 4, cudaMemcpyDeviceToHost, sv->compute);
@@ -475,7 +475,7 @@ void worker_loop(btas_server_t *sv) {
             bool finished = true;
             if (r->whole) {
                 // the one-block kernel reports no barrier status (its slot stays 0)
-                r->bad = sv->h_flags[i] != 0 || (r->n > apsp_small_max_n() && sv->h_flags[sv->flag_slots + 1 + i] != 0);
+                r->bad = sv->h_flags[i] != 0 || (r->n > apsp_small_limit() && sv->h_flags[sv->flag_slots + 1 + i] != 0);
                 r->result_buf = 1;
                 r->s = r->S + 1;
             } else if (r->kind == 0) {

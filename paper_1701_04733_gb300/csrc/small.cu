@@ -8,6 +8,8 @@
 // read-back.  The arithmetic is that of the int32 product kernels (DPX
 // add-min, INF absorption by the clamp at INF - 2^28), so the result is
 // bit-identical to the general path.
+#include <cstdlib>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -118,6 +120,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 int apsp_small_max_n() { return kMaxN; }
+
+int apsp_small_limit() {
+    // graphs up to this size take the one-block kernel, larger ones the
+    // cooperative kernel; BTAS_APSP_SMALL_MAX_N overrides it (0 .. 128)
+    static const int dflt = kMaxN;
+    const char *e = getenv("BTAS_APSP_SMALL_MAX_N");
+    if (!e || !*e) return dflt;
+    const int v = atoi(e);
+    return v < 0 ? 0 : v > kMaxN ? kMaxN : v;
+}
 
 cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd,
                               int *info, cudaStream_t st) {

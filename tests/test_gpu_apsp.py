@@ -11,6 +11,26 @@ from gpu_util import INF, dev, host
 
 pytestmark = pytest.mark.gpu
 
+
+class env:
+    """Set environment variables for the duration of a with-block."""
+
+    def __init__(self, **kv):
+        self.kv = kv
+
+    def __enter__(self):
+        import os
+        self.old = {k: os.environ.get(k) for k in self.kv}
+        os.environ.update(self.kv)
+
+    def __exit__(self, *a):
+        import os
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
 PATHS = {"int32": 0x2, "carrier": 0x8, "u16": 0x4}
 
 
@@ -215,24 +235,29 @@ def test_small_graph_single_block_path(btas, oracle_mod, n):
 @pytest.mark.parametrize("n", [129, 200, 256, 333, 512, 777, 1024])
 def test_mid_graph_cooperative_path(btas, oracle_mod, n):
     """128 < n <= 1024 runs every squaring in one cooperative launch (split-k
-    work items merged with atomicMin, grid barriers between squarings);
-    distances, squarings count and bound equal the general path's and the
-    oracle's, with and without early exit, in place too."""
-    import os
-    for p, whi in ((0.05, 100), (3.0 / n, 10 ** 6)):
+    work items merged with atomicMin, one grid barrier per squaring), each
+    squaring on packed 16-bit pairs while the largest merged value allows it
+    (<= 16383), else on int32.  Distances, squarings count and bound equal the
+    general path's and the oracle's, with and without early exit, with the
+    packed squarings disabled (BTAS_MID_NO_U16=1, FORCE_I32), and in place."""
+    for p, whi, expect in ((0.05, 100, "u16x2"), (3.0 / n, 10 ** 6, "int32"), (0.02, 12000, None)):
         W = gen.random_graph(gen.BASE_SEED, 800 + n, n, p, 1, whi)
         ref = oracle_mod.floyd_warshall(W)
         for early in (0, 1):
             D, info = btas.apsp(dev(W), flags=early, info=True)
-            os.environ["BTAS_APSP_NO_MID"] = "1"
-            try:
+            with env(BTAS_APSP_NO_MID="1"):
                 D2, info2 = btas.apsp(dev(W), flags=early | btas.APSP_FORCE_I32, info=True)
-            finally:
-                del os.environ["BTAS_APSP_NO_MID"]
-            np.testing.assert_array_equal(host(D), ref)
-            np.testing.assert_array_equal(host(D2), ref)
-            assert info["path"] == "int32"
-            assert info["squarings"] == info2["squarings"]
+            with env(BTAS_MID_NO_U16="1"):
+                D3, info3 = btas.apsp(dev(W), flags=early, info=True)
+            D4, info4 = btas.apsp(dev(W), flags=early | btas.APSP_FORCE_I32, info=True)
+            for X in (D, D2, D3, D4):
+                np.testing.assert_array_equal(host(X), ref)
+            if expect is None:  # first squaring packed (max w <= 16383), later ones on int32
+                assert "u16x2" in info["path"].split("+")
+            else:
+                assert info["path"] == expect
+            assert info3["path"] == info4["path"] == "int32"
+            assert info["squarings"] == info2["squarings"] == info3["squarings"] == info4["squarings"]
             assert info["bound"] == info2["bound"] == (n - 1) * int(W[W < INF].max())
         t = dev(W)
         btas.apsp(t, out=t)
