@@ -234,16 +234,20 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  *
  * Execution by size (same results and the same squarings count in every
  * regime; FORCE_U16 / FORCE_CARRIER always take the tiled path):
- *   n <= 128        one thread block holds D in shared memory and runs the
+ *   n <= 64         one thread block holds D in shared memory and runs the
  *                   domain check and every squaring (int32): one launch, one
  *                   read-back;
- *   128 < n <= 1024 one cooperative launch runs every squaring as split-k
- *                   work items merged with atomicMin, grid barriers (bounded
- *                   waits; BTAS_ERR_TIMEOUT if one expires) in between (int32);
+ *   64 < n <= 1024  one cooperative launch runs every squaring as split-k
+ *                   pieces merged with atomicMin, one grid barrier (bounded
+ *                   wait; BTAS_ERR_TIMEOUT if it expires) per squaring; each
+ *                   squaring packed 16-bit while every finite entry of its
+ *                   operand is <= 16383 (a bound the previous squaring
+ *                   reports), else int32 (always int32 with FORCE_I32);
  *   larger n        the tiled product kernels, one launch per squaring, with
  *                   the per-squaring exact representation described below.
- * BTAS_APSP_NO_SMALL=1 / BTAS_APSP_NO_MID=1 in the environment send the first
- * two regimes to the tiled path.
+ * BTAS_APSP_SMALL_MAX_N=m (0 .. 128) in the environment moves the first
+ * boundary to m; BTAS_APSP_NO_SMALL=1 / BTAS_APSP_NO_MID=1 send the first two
+ * regimes to the tiled path.
  * ------------------------------------------------------------------------ */
 btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
@@ -355,8 +359,9 @@ int btas_apsp_squarings(int64_t n);
  * this library holds until the process exits; hence n <= BTAS_NOALLOC_MAX_N
  * (larger n returns BTAS_ERR_ARG, nothing enqueued).  The caller still passes
  * W and D (device pointers, n x n int32, row-major, D == W allowed).
- * n <= 128 runs on the one-block kernel and mid-size n whose three iterates
- * fit in the array on the cooperative kernel (as btas_apsp does); larger n
+ * The smallest n run on the one-block kernel and mid-size n whose three
+ * iterates fit in the array on the cooperative kernel (as btas_apsp does,
+ * with the same size boundary); larger n
  * runs the tiled int32 squarings.  Nothing is read back: the call does not
  * synchronise `stream`.
  * The first call on a device looks up the array's device address with that
@@ -517,8 +522,8 @@ btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *coun
  * squaring) in one persistent launch; requests arriving meanwhile join the
  * next step.  A product completes after its step; an APSP solve after its
  * last squaring or as soon as a squaring changed nothing.  An APSP request
- * with n <= 1024 is instead solved whole in one unit, by the one-block
- * (n <= 128) or the cooperative kernel of btas_apsp, launched in the step
+ * with n <= 1024 is instead solved whole in one unit, by the one-block or
+ * the cooperative kernel of btas_apsp (the same size boundary), launched in the step
  * after the persistent kernel (BTAS_SERVER_NO_WHOLE=1 in the environment at
  * creation turns this off).  Results are bit-identical to btas_gemm /
  * btas_apsp.  Buffers must stay valid until the request is done.

@@ -119,6 +119,8 @@ def lib():
     """The loaded libbtas.so.  Raises if it has not been built: there is no
     fallback implementation."""
     global _lib
+    if _lib is not None:
+        return _lib
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
@@ -342,15 +344,27 @@ def btas_batch_profile(b, cycles_ptr, counts_ptr, slots) -> int:
 
 
 # ------------------------------------------------------- torch helpers
+_torch_mod = None
+
+
 def _torch():
-    import torch
-    return torch
+    global _torch_mod
+    if _torch_mod is None:
+        import torch
+        _torch_mod = torch
+    return _torch_mod
 
 
 def _stream(stream=None) -> int:
+    """The cudaStream_t of `stream`, or of the current device's current stream
+    (read without building a Stream object: this is on every call's path)."""
+    if stream is not None:
+        return int(stream.cuda_stream)
     torch = _torch()
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return int(s.cuda_stream)
+    raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+    if raw is not None:
+        return int(raw(torch.cuda.current_device()))
+    return int(torch.cuda.current_stream().cuda_stream)
 
 
 def _sr(semiring) -> int:

@@ -132,6 +132,29 @@ namespace {
 
 thread_local std::string g_err = "no error";
 
+// A small device -> host read-back followed by a wait for the stream, through
+// a per-thread pinned mailbox (a copy into pageable memory is staged by the
+// driver and takes longer).
+cudaError_t read_back(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    struct Mailbox {
+        void *p = nullptr;
+        ~Mailbox() {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    thread_local Mailbox mb;
+    constexpr size_t kCap = 4096;
+    if (bytes <= kCap && !mb.p && cudaMallocHost(&mb.p, kCap) != cudaSuccess) {
+        cudaGetLastError();
+        mb.p = nullptr;
+    }
+    void *tgt = (bytes <= kCap && mb.p) ? mb.p : dst;
+    cudaError_t e = cudaMemcpyAsync(tgt, src, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && tgt != dst) memcpy(dst, tgt, bytes);
+    return e;
+}
+
 btas_status fail(btas_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -477,8 +500,7 @@ btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, i
         int host[2] = {0, 0};
         BTAS_CUDA(cudaMemsetAsync(flag, 0, 256, st), "memset");
         BTAS_CUDA(launch_apsp_scan(W, n, flag + 8, st), "domain scan");
-        BTAS_CUDA(cudaMemcpyAsync(host, flag + 8, 8, cudaMemcpyDeviceToHost, st), "scan readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "scan sync");
+        BTAS_CUDA(read_back(host, flag + 8, 8, st), "scan readback");
         if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_sssp: %d entries outside the domain", host[1]);
     }
     // d_0 = e_src; d_{t+1} = d_t (x) W until unchanged (at most n-1 products)
@@ -491,8 +513,7 @@ btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, i
         BTAS_CUDA(cudaMemsetAsync(flag, 0, 4, st), "flag reset");
         BTAS_CUDA(launch_gemv(kMin, BTAS_I32, 1, (int)n, (int)n, W, n, d[cur], d[cur ^ 1], 1, flag, st), "relax");
         int changed = 0;
-        BTAS_CUDA(cudaMemcpyAsync(&changed, flag, 4, cudaMemcpyDeviceToHost, st), "flag readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "step sync");
+        BTAS_CUDA(read_back(&changed, flag, 4, st), "flag readback");
         cur ^= 1;
         if (!changed) break;
         ++steps;
@@ -596,19 +617,17 @@ constexpr int kMidFallback = -1;
 static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool early, bool packed_ok,
                           int *squarings_done, int64_t *bound_out, int *path_out, cudaStream_t st) {
     Workspace ws(st);
-    const size_t mid_bytes = apsp_mid_workspace(n, S);
-    BTAS_CUDA(ws.alloc(mid_bytes + 256), "workspace alloc");
-    int *info = reinterpret_cast<int *>(static_cast<char *>(ws.p) + mid_bytes);
-    BTAS_CUDA(cudaMemsetAsync(info, 0, 256, st), "memset");
-    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, ws.p, info, st);
+    BTAS_CUDA(ws.alloc(apsp_mid_workspace(n, S)), "workspace alloc");
+    // the status words inside the workspace: zeroed by the launch
+    int *info = apsp_mid_info(ws.p, n);
+    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, ws.p, nullptr, st);
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
         cudaGetLastError();
         return kMidFallback;
     }
     BTAS_CUDA(le, "mid apsp");
     int host[5] = {0, 0, 0, 0, 0};
-    BTAS_CUDA(cudaMemcpyAsync(host, info, 20, cudaMemcpyDeviceToHost, st), "info readback");
-    BTAS_CUDA(cudaStreamSynchronize(st), "mid apsp sync");
+    BTAS_CUDA(read_back(host, info, 20, st), "info readback");
     if (host[3] != 0) return fail(BTAS_ERR_TIMEOUT, "btas_apsp: a bounded grid barrier wait expired");
     if (host[0] != 0) {
         if (bound_out) *bound_out = -1;
@@ -655,8 +674,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         int *info = static_cast<int *>(ws.p);
         int host[3] = {0, 0, 0};
         BTAS_CUDA(launch_apsp_small(W, n, (int)n, S, early, D, n, info, st), "small apsp");
-        BTAS_CUDA(cudaMemcpyAsync(host, info, 12, cudaMemcpyDeviceToHost, st), "info readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "small apsp sync");
+        BTAS_CUDA(read_back(host, info, 12, st), "info readback");
         if (host[0] != 0) {
             if (bound_out) *bound_out = -1;
             return fail(BTAS_ERR_ARG,
@@ -702,8 +720,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         int host[2] = {0, 0};
         int *scan = dflags + S + 1;
         BTAS_CUDA(launch_apsp_scan(W, n, scan, st), "domain scan");
-        BTAS_CUDA(cudaMemcpyAsync(host, scan, 8, cudaMemcpyDeviceToHost, st), "scan readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "scan sync");
+        BTAS_CUDA(read_back(host, scan, 8, st), "scan readback");
         if (host[1] != 0) {
             if (bound_out) *bound_out = -1;
             return fail(BTAS_ERR_ARG,
@@ -736,8 +753,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         if (path_out) *path_out = 1;
         if (squarings_done) {
             int host[64];
-            BTAS_CUDA(cudaMemcpyAsync(host, dflags, (size_t)S * 4, cudaMemcpyDeviceToHost, st), "flags readback");
-            BTAS_CUDA(cudaStreamSynchronize(st), "flags sync");
+            BTAS_CUDA(read_back(host, dflags, (size_t)S * 4, st), "flags readback");
             int done = 0;
             for (int q = 0; q < S; ++q) done += host[q] != 0;
             *squarings_done = done;
@@ -826,8 +842,7 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         used |= 1 << rep;
         int host[2] = {0, 0};
         BTAS_CUDA(cudaMemcpyAsync(&host[0], &chg[s], 4, cudaMemcpyDeviceToHost, st), "flag readback");
-        BTAS_CUDA(cudaMemcpyAsync(&host[1], &mxs[s], 4, cudaMemcpyDeviceToHost, st), "max readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "squaring sync");
+        BTAS_CUDA(read_back(&host[1], &mxs[s], 4, st), "max readback");
         cur = out;
         m = host[1] < 0 ? 0 : host[1];
         if (host[0]) ++done;
@@ -900,8 +915,7 @@ btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void
         btas_status r = square(cur, out, &dflags[s]);
         if (r != BTAS_OK) return r;
         int changed = 1;
-        BTAS_CUDA(cudaMemcpyAsync(&changed, &dflags[s], 4, cudaMemcpyDeviceToHost, st), "flag readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "squaring sync");
+        BTAS_CUDA(read_back(&changed, &dflags[s], 4, st), "flag readback");
         if (!changed) {
             converged = true;
             break;
@@ -967,8 +981,7 @@ btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Ne
     {
         int host[2] = {0, 0};
         BTAS_CUDA(launch_apsp_scan(W, n, dflags + S + 1, st), "domain scan");
-        BTAS_CUDA(cudaMemcpyAsync(host, dflags + S + 1, 8, cudaMemcpyDeviceToHost, st), "scan readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "scan sync");
+        BTAS_CUDA(read_back(host, dflags + S + 1, 8, st), "scan readback");
         if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_apsp_paths: %d entries outside the domain", host[1]);
     }
     BTAS_CUDA(cudaMemcpyAsync(Db[0], W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
@@ -980,8 +993,7 @@ btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Ne
                   "paths squaring");
         cur ^= 1;
         int changed = 1;
-        BTAS_CUDA(cudaMemcpyAsync(&changed, &dflags[s], 4, cudaMemcpyDeviceToHost, st), "flag readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "squaring sync");
+        BTAS_CUDA(read_back(&changed, &dflags[s], 4, st), "flag readback");
         if (changed) ++done;
         if (!changed && (flags & BTAS_APSP_EARLY_EXIT)) break;
     }
@@ -1021,8 +1033,7 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) 
         int host[2] = {0, 0};
         BTAS_CUDA(cudaMemsetAsync(scan, 0, 8, st), "memset");
         BTAS_CUDA(launch_apsp_scan(W, n, scan, st), "domain scan");
-        BTAS_CUDA(cudaMemcpyAsync(host, scan, 8, cudaMemcpyDeviceToHost, st), "scan readback");
-        BTAS_CUDA(cudaStreamSynchronize(st), "scan sync");
+        BTAS_CUDA(read_back(host, scan, 8, st), "scan readback");
         if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_apsp_fw: %d entries outside the domain", host[1]);
     }
     if (D != W) BTAS_CUDA(cudaMemcpyAsync(D, W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");

@@ -90,14 +90,17 @@ int apsp_small_limit();  // the size up to which callers use it (<= apsp_small_m
 cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool early, int *D, long long ldd,
                               int *info, cudaStream_t st);
 
-// ---- APSP in one cooperative launch for apsp_small_max_n() < n <=
+// ---- APSP in one cooperative launch for apsp_small_limit() < n <=
 // apsp_mid_max_n() (mid.cu).  ws: apsp_mid_workspace(n, S) bytes; info
-// (device, zeroed by the caller, S + 5 ints): [0] entries outside the domain,
-// [1] largest finite weight, [2] squarings that changed D, [3] status, [4]
-// representations used (1 int32, 4 packed 16-bit).  packed_ok = false keeps
-// every squaring on int32 (so does BTAS_MID_NO_U16=1 in the environment).
+// (device, 5 ints zeroed by the caller; or null: the words at
+// apsp_mid_info(ws, n), zeroed by the launch): [0] entries outside the
+// domain, [1] largest finite weight, [2] squarings that changed D, [3]
+// status, [4] representations used (1 int32, 4 packed 16-bit).  packed_ok =
+// false keeps every squaring on int32 (so does BTAS_MID_NO_U16=1 in the
+// environment).
 int apsp_mid_max_n();
 size_t apsp_mid_workspace(long long n, int S);
+int *apsp_mid_info(void *ws, long long n);
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
                             long long ldd, void *ws, int *info, cudaStream_t st);
 

@@ -1,23 +1,26 @@
 // APSP by repeated squaring (Sec. III) for mid-size graphs in ONE
 // cooperative launch.
 //
-// Between the one-block kernel (n <= 128) and the tiled product kernels a
+// Between the one-block kernel (n <= 64) and the tiled product kernels a
 // solve is bound by launches and host round trips: a few dozen tiles per
 // squaring cannot fill the GPU, and every squaring waits for the previous
 // one's change flag.  Here one cooperative grid runs the domain check and all
 // squarings, with ONE grid barrier per squaring.
 //
-// Work items.  Squaring s is split into (64 x 64 output tile, k-chunk) items
-// so that every SM has work; an item computes the tile's partial minimum p
-// over its k-chunk.
+// Work split.  Squaring s is a space of units (64 x 64 output tile, 32-wide
+// k-step), cut into equal contiguous shares, one per block ("stream-K"): a
+// block's share covers the end of one tile's k-range, whole tiles, and the
+// start of another, so the blocks finish together whatever n is.  The
+// consecutive units of one tile in a share form a piece (a tile and a
+// k-range) whose partial minimum p the block merges into X_s.
 //
 // Merging without a second pass.  With a zero diagonal and non-negative
 // weights X_s <= X_{s-1} entrywise: the terms k = i and k = j of the product
-// are X_{s-1}[i][j] itself.  So the item whose chunk holds k = j has
-// p <= X_{s-1}[i][j], and X_s[i][j] < X_{s-1}[i][j] exactly when some item
-// finds p < X_{s-1}[i][j].  An item merges p into X_s (reset to INF
+// are X_{s-1}[i][j] itself.  So the piece holding k = j has
+// p <= X_{s-1}[i][j], and X_s[i][j] < X_{s-1}[i][j] exactly when some piece
+// finds p < X_{s-1}[i][j].  A piece merges p into X_s (reset to INF
 // beforehand) with atomicMin where p < X_{s-1}[i][j], or where p equals it
-// and the item holds k = j; any other p cannot be the minimum.  The same
+// and the piece holds k = j; any other p cannot be the minimum.  The same
 // comparison is the change test, so a squaring needs no checking pass, and
 // (+) = min being associative, commutative and idempotent makes the merge
 // exact in any order.
@@ -32,8 +35,10 @@
 //
 // Buffers.  X_s lives in buf[(s - 1) % 3] and X_0, a pitch-ldx copy of W, in
 // buf2.  Squaring s reads X_{s-1}, merges into X_s and resets X_{s+1}'s
-// buffer, which held X_{s-2}.  Every grid barrier wait is bounded (clock64);
-// on expiry the kernel records BTAS_ERR_TIMEOUT and all blocks return.
+// buffer, which held X_{s-2}.  The grid barrier after a squaring also
+// carries its change flag and merged maximum to every block.  Every barrier
+// wait is bounded (clock64); on expiry the kernel records BTAS_ERR_TIMEOUT
+// and all blocks return.
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
@@ -59,11 +64,9 @@ struct MidArgs {
     long long ldd;
     int *buf0, *buf1, *buf2;  // n x ldx each; columns n .. ldx-1 always hold INF
     long long ldx;            // round4(n): 16-byte rows for vector staging
-    int kchunks;              // k-chunks per output tile
-    int chunk;                // k-chunk length (multiple of kKc)
-    unsigned *bar;            // [0] arrivals, [32] generation, [64 + s] largest value merged in squaring s
-    int *info;  // [0] bad entries, [1] max weight, [2] squarings that changed, [3] status,
-                // [4] representations used (1 int32, 4 packed 16-bit), [4 + s] squaring s changed X
+    unsigned *bar;  // [2g, 2g + 1] barrier g's counter, [32, 33] release word, [64 + s] largest merged value
+    int *info;      // [0] bad entries, [1] max weight, [2] squarings that changed, [3] status,
+                    // [4] representations used (1 int32, 4 packed 16-bit)
     long long timeout_cycles;
 };
 
@@ -72,35 +75,62 @@ struct MidSmem {
     int b[2][kKc][kT];    // B stage: b[k][col]; packed mode: b[k][pair] in the first kT / 2 words
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ int ld_acquire_i32(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-// Bounded grid barrier (sense by generation).  Returns false if the status
-// word is set (timeout here or elsewhere): the caller returns.
-__device__ bool grid_barrier(const MidArgs &a) {
-    __syncthreads();
-    __shared__ int s_ok;
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr int kMaxBarriers = 16;  // phase 0 + at most 15 squarings (n <= 2^15)
+
+// Bounded grid barrier that also ORs a per-block flag over the grid and
+// reads one word (*pval, in [0, 2^30)) once all blocks have arrived.  Barrier
+// g has its own 64-bit counter bar[2g .. 2g+1]: each block adds 1 (arrival)
+// plus 2^32 if its flag is set, so the last block to arrive learns the
+// grid's flag from the value its add returns.  It then reads *pval and
+// publishes barrier number, flag and value in one 64-bit word on a line of
+// its own (bar[32 .. 33]); the other blocks poll that word, so one load gives
+// them the release and both results.  Returns false if the status word is
+// set (timeout here or elsewhere): the caller returns.
+__device__ bool grid_barrier(const MidArgs &a, unsigned &gen, bool flag, const int *pval, int &v0, int &v1) {
+    __shared__ int s_ok, s_v0, s_v1;
+    const int any = __syncthreads_or(flag ? 1 : 0);
+    ++gen;
     if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = ld_acquire_u32(a.bar + 32);
+        unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.bar) + (gen - 1);
+        unsigned long long *pub = reinterpret_cast<unsigned long long *>(a.bar + 32);
+        unsigned long long word = 0;
         __threadfence();
-        if (atomicAdd(a.bar, 1u) == gridDim.x - 1) {
-            atomicExch(a.bar, 0u);
+        const unsigned long long prev = atomicAdd(ctr, 1ull | ((unsigned long long)(any != 0) << 32));
+        if ((unsigned)prev == gridDim.x - 1) {
             __threadfence();
-            atomicAdd(a.bar + 32, 1u);
+            const unsigned f = ((prev >> 32) != 0 || any != 0) ? 1u : 0u;
+            const unsigned v = pval ? (unsigned)ld_relaxed_i32(pval) & 0x3FFFFFFFu : 0u;
+            word = (unsigned long long)gen | ((unsigned long long)f << 32) | ((unsigned long long)v << 33);
+            st_release_u64(pub, word);
         } else {
             const long long t0 = clock64();
-            while (ld_acquire_u32(a.bar + 32) == g) {
-                if (ld_acquire_i32(a.info + 3) != 0) break;
+            for (unsigned it = 1;; ++it) {
+                word = ld_acquire_u64(pub);
+                if ((unsigned)word == gen) break;
+                // another block gave up (status set) or this wait expires
+                if ((it & 15) == 0 && ld_acquire_i32(a.info + 3) != 0) break;
                 if (clock64() - t0 > a.timeout_cycles) {
                     atomicCAS(a.info + 3, 0, BTAS_ERR_TIMEOUT);
                     break;
@@ -108,10 +138,13 @@ __device__ bool grid_barrier(const MidArgs &a) {
                 __nanosleep(32);
             }
         }
-        if (ld_acquire_i32(a.info + 3) != 0) ok = 0;
-        s_ok = ok;
+        s_ok = (unsigned)word == gen;
+        s_v0 = (int)((word >> 32) & 1u);
+        s_v1 = (int)(word >> 33);
     }
     __syncthreads();
+    v0 = s_v0;
+    v1 = s_v1;
     return s_ok != 0;
 }
 
@@ -174,9 +207,9 @@ __device__ __forceinline__ void stash(MidSmem &sm, int buf, int tid, const int4 
     }
 }
 
-// One work item: the 64 x 64 tile (bm, bn) of X_{s-1} (x) X_{s-1} over
-// k in [k0, k1), merged into out.  256 threads, 4 x 4 outputs each; the
-// next k-step's operands are in flight while this one is computed.
+// One piece: the 64 x 64 tile (bm, bn) of X_{s-1} (x) X_{s-1} over k in
+// [k0, k1), merged into out.  256 threads, 4 x 4 outputs each; the next
+// k-step's operands are in flight while this one is computed.
 template <bool U16>
 __device__ __forceinline__ void run_item(const MidArgs &a, const int *in, int *out, int bm, int bn, int k0, int k1,
                                          MidSmem &sm, int tid, bool &ch, int &mx) {
@@ -190,8 +223,8 @@ __device__ __forceinline__ void run_item(const MidArgs &a, const int *in, int *o
     for (int r = 0; r < 4; ++r)
         old[r] = (r0 + r < n && c0 < n) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)(r0 + r) * ldx + c0))
                                         : make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
-    int acc[4][4];             // int32 mode
-    unsigned acc16[4][2];      // packed mode: columns (c0 + 2p, c0 + 2p + 1) in (low, high)
+    int acc[4][4];         // int32 mode
+    unsigned acc16[4][2];  // packed mode: columns (c0 + 2p, c0 + 2p + 1) in (low, high)
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
 #pragma unroll
@@ -232,7 +265,7 @@ __device__ __forceinline__ void run_item(const MidArgs &a, const int *in, int *o
         __syncthreads();
         buf ^= 1;
     }
-    // merge: p < old (a change), or p == old from the item holding k = j
+    // merge: p < old (a change), or p == old from the piece holding k = j
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int i = r0 + r;
@@ -256,6 +289,22 @@ __device__ __forceinline__ void run_item(const MidArgs &a, const int *in, int *o
     }
 }
 
+// A block's share [u0, u1) of squaring s, unit u = k-step u % KS of tile
+// u / KS, as pieces of consecutive units of one tile.
+template <bool U16>
+__device__ __forceinline__ void squaring(const MidArgs &a, const int *in, int *out, int tiles, int KS, long long u0,
+                                         long long u1, MidSmem &sm, int tid, bool &ch, int &mx) {
+    const int n = a.n;
+    long long u = u0;
+    while (u < u1) {
+        const int tile = (int)(u / KS), ks = (int)(u % KS);
+        const long long pe = min(u1, (long long)(tile + 1) * KS);
+        const int k0 = ks * kKc, k1 = min(n, (int)(pe - (long long)tile * KS) * kKc);
+        run_item<U16>(a, in, out, (tile / tiles) * kT, (tile % tiles) * kT, k0, k1, sm, tid, ch, mx);
+        u = pe;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) {
     __shared__ __align__(16) MidSmem sm;
     const int n = a.n, tid = threadIdx.x;
@@ -263,8 +312,10 @@ __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) 
     const long long nx = (long long)n * ldx;
     const long long gthreads = (long long)gridDim.x * kThreads;
     const long long gtid = (long long)blockIdx.x * kThreads + tid;
+    unsigned gen = 0;
 
     // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF
+    bool bad_block = false;
     {
         int bad = 0, mx = 0;
         for (long long idx = gtid; idx < nx; idx += gthreads) {
@@ -288,16 +339,19 @@ __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) 
             if (bad) atomicAdd(a.info + 0, bad);
             atomicMax(a.info + 1, mx);
         }
+        bad_block = bad != 0;
     }
-    if (!grid_barrier(a)) return;
-    if (ld_acquire_i32(a.info + 0) != 0) return;  // D untouched
+    int nbad = 0, bound = 0;  // bound: >= every finite entry of X_{s-1}
+    if (!grid_barrier(a, gen, bad_block, a.info + 1, nbad, bound)) return;
+    if (nbad != 0) return;  // D untouched
 
-    const int tiles = (n + kT - 1) / kT;
-    const int items = tiles * tiles * a.kchunks;
+    // stream-K split of the (tile, k-step) units: equal shares, +-1 unit
+    const int tiles = (n + kT - 1) / kT, KS = (n + kKc - 1) / kKc;
+    const long long U = (long long)tiles * tiles * KS;
+    const long long u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
     const int4 inf4 = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
-    const int *in = a.buf2;               // X_0
-    int cur = 0, done = 0, path = 0;      // X_s (s >= 1) lives in buf[(s - 1) % 3]
-    int bound = ld_acquire_i32(a.info + 1);  // >= every finite entry of X_{s-1}
+    const int *in = a.buf2;           // X_0
+    int cur = 0, done = 0, path = 0;  // X_s (s >= 1) lives in buf[(s - 1) % 3]
     for (int s = 1; s <= a.S; ++s) {
         int *out = bufp(a, cur);
         if (s < a.S) {
@@ -308,27 +362,16 @@ __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) 
         path |= u16 ? 4 : 1;
         bool ch = false;
         int mx = 0;
-        for (int it = blockIdx.x; it < items; it += gridDim.x) {
-            const int tile = it / a.kchunks, kc = it % a.kchunks;
-            const int bm = (tile / tiles) * kT, bn = (tile % tiles) * kT;
-            const int k0 = kc * a.chunk, k1 = min(n, k0 + a.chunk);
-            if (k0 >= k1) continue;
-            if (u16)
-                run_item<true>(a, in, out, bm, bn, k0, k1, sm, tid, ch, mx);
-            else
-                run_item<false>(a, in, out, bm, bn, k0, k1, sm, tid, ch, mx);
-        }
+        if (u16)
+            squaring<true>(a, in, out, tiles, KS, u0, u1, sm, tid, ch, mx);
+        else
+            squaring<false>(a, in, out, tiles, KS, u0, u1, sm, tid, ch, mx);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const bool any = __any_sync(0xffffffffu, ch);
-        if ((tid & 31) == 0) {
-            if (any) atomicOr(a.info + 4 + s, 1);
-            if (mx > 0) atomicMax(reinterpret_cast<int *>(a.bar + 64 + s), mx);
-        }
-        if (!grid_barrier(a)) return;
-        const int changed = ld_acquire_i32(a.info + 4 + s);
-        bound = ld_acquire_i32(reinterpret_cast<const int *>(a.bar + 64 + s));
-        done += changed;
+        if ((tid & 31) == 0 && mx > 0) atomicMax(reinterpret_cast<int *>(a.bar + 64 + s), mx);
+        int changed = 0;
+        if (!grid_barrier(a, gen, ch, reinterpret_cast<const int *>(a.bar + 64 + s), changed, bound)) return;
+        done += changed != 0;
         in = out;
         cur = (cur + 1) % 3;
         if (!changed && a.early) break;
@@ -342,34 +385,21 @@ __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) 
     }
 }
 
-// k-chunk length for n: the number of (tile, chunk) items per SM sets the
-// compute time, the number of waves of co-resident blocks the exposed load
-// latency (about two k-steps per wave).
-int pick_chunk(int n, int sms, int grid_max) {
-    const int tiles = (n + kT - 1) / kT;
-    const int kmax = (n + kKc - 1) / kKc * kKc;
-    int best = kKc;
-    long long best_cost = -1;
-    for (int c = kKc; c < 2 * kmax; c *= 2) {
-        const int len = std::min(c, kmax);
-        const long long items = (long long)tiles * tiles * ((n + len - 1) / len);
-        const long long cost = (items + sms - 1) / sms * len + (items + grid_max - 1) / grid_max * 2 * kKc;
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            best = len;
-        }
-        if (len == kmax) break;
-    }
-    return best;
-}
-
 }  // namespace
 
 int apsp_mid_max_n() { return 1024; }
 
+// workspace: three n x ldx matrices, then 512 bytes of barrier words and
+// 256 bytes for the status words of a caller that passes info = null
 size_t apsp_mid_workspace(long long n, int S) {
+    (void)S;
     const size_t mat = ((size_t)n * ((n + 3) & ~3LL) * 4 + 255) & ~size_t(255);
-    return 3 * mat + 256 + (((size_t)(S + 8) * 4 + 255) & ~size_t(255));
+    return 3 * mat + 1024;
+}
+
+int *apsp_mid_info(void *ws, long long n) {
+    const size_t mat = ((size_t)n * ((n + 3) & ~3LL) * 4 + 255) & ~size_t(255);
+    return reinterpret_cast<int *>(static_cast<char *>(ws) + 3 * mat + 512);
 }
 
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
@@ -392,12 +422,11 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
         }
     }
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    if (S + 1 > kMaxBarriers) return cudaErrorInvalidValue;
     const int sms = di.sms, clk_khz = di.clock_khz;
-    const int tiles = (n + kT - 1) / kT;
-    const int grid_max = per_sm * sms;
-    const int chunk = pick_chunk(n, sms, grid_max);
-    const int kchunks = (n + chunk - 1) / chunk;
-    const int grid = std::max(1, std::min(tiles * tiles * kchunks, grid_max));
+    const long long tiles = (n + kT - 1) / kT, KS = (n + kKc - 1) / kKc;
+    const long long units = tiles * tiles * KS;
+    const int grid = (int)std::max(1LL, std::min(units, (long long)per_sm * sms));
     const long long ldx = (n + 3) & ~3LL;
     const size_t mat = ((size_t)n * ldx * 4 + 255) & ~size_t(255);
     char *base = static_cast<char *>(ws);
@@ -416,13 +445,11 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     a.buf1 = reinterpret_cast<int *>(base + mat);
     a.buf2 = reinterpret_cast<int *>(base + 2 * mat);
     a.bar = reinterpret_cast<unsigned *>(base + 3 * mat);
-    a.info = info_out_dev;
-    a.kchunks = kchunks;
-    a.chunk = chunk;
+    a.info = info_out_dev ? info_out_dev : apsp_mid_info(ws, n);
     a.timeout_cycles = (long long)(2.0 * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);  // about 2 s
-    // barrier words and the per-squaring maxima (512 bytes: the workspace
-    // holds 256 + at least 256 bytes after the three matrices)
-    cudaError_t e = cudaMemsetAsync(base + 3 * mat, 0, 512, st);
+    // barrier words and per-squaring maxima, and the internal status words
+    // when the caller passes none: one memset
+    cudaError_t e = cudaMemsetAsync(base + 3 * mat, 0, info_out_dev ? 512 : 768, st);
     if (e != cudaSuccess) return e;
     void *args[] = {&a};
     e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(apsp_mid_kernel), dim3(grid), dim3(kThreads), args, 0,

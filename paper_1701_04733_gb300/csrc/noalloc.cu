@@ -15,9 +15,9 @@
 // that device current, through cudaGetSymbolAddress, on the first call made
 // on that device.  Make that first call before any stream capture.
 //
-// Graphs with n <= 128 run on the one-block kernel and mid-size graphs whose
-// three iterates fit in the scratch run on the cooperative kernel (the same
-// kernels btas_apsp uses); the rest take the tiled int32 squarings below.
+// The smallest graphs run on the one-block kernel and mid-size graphs whose
+// three iterates fit in the scratch on the cooperative kernel (the same
+// kernels and size boundary as btas_apsp); the rest take the tiled int32 squarings below.
 //
 // All calls share the one array, and each call leaves its contents behind.
 // The change flags, which must start at zero, are cleared on the stream at the

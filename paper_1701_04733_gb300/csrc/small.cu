@@ -1,4 +1,5 @@
-// APSP by repeated squaring (Sec. III) for n <= 128 in ONE thread block.
+// APSP by repeated squaring (Sec. III) for n <= 128 in ONE thread block
+// (by default the library sends it n <= 64; see apsp_small_limit).
 //
 // For a small graph the general path is latency-bound: every squaring is a
 // separate launch over a handful of tiles, with a host round trip for the
@@ -123,8 +124,10 @@ int apsp_small_max_n() { return kMaxN; }
 
 int apsp_small_limit() {
     // graphs up to this size take the one-block kernel, larger ones the
-    // cooperative kernel; BTAS_APSP_SMALL_MAX_N overrides it (0 .. 128)
-    static const int dflt = kMaxN;
+    // cooperative kernel, which is faster from n of about 72 on (one SM's DPX
+    // rate against a few grid barriers per squaring); BTAS_APSP_SMALL_MAX_N
+    // overrides it (0 .. 128)
+    static const int dflt = 64;
     const char *e = getenv("BTAS_APSP_SMALL_MAX_N");
     if (!e || !*e) return dflt;
     const int v = atoi(e);

@@ -192,8 +192,16 @@ def test_workspace_pool_caches_and_trims(btas, oracle_mod):
     assert btas.btas_workspace_reserved() < held
 
 
+@pytest.fixture
+def one_block_up_to_128():
+    """Send every n <= 128 to the one-block kernel (by default only the
+    smallest graphs take it, the rest the cooperative kernel)."""
+    with env(BTAS_APSP_SMALL_MAX_N="128"):
+        yield
+
+
 @pytest.mark.parametrize("n", [3, 4, 7, 33, 64, 100, 127, 128])
-def test_small_graph_single_block_path(btas, oracle_mod, n):
+def test_small_graph_single_block_path(btas, oracle_mod, n, one_block_up_to_128):
     """n <= 128 runs in one thread block (all squarings in shared memory);
     distances, squarings count and bound equal the general path's and the
     oracle's, with and without early exit, in place too."""
@@ -232,10 +240,17 @@ def test_small_graph_single_block_path(btas, oracle_mod, n):
     assert (host(out) == 123).all()
 
 
-@pytest.mark.parametrize("n", [129, 200, 256, 333, 512, 777, 1024])
-def test_mid_graph_cooperative_path(btas, oracle_mod, n):
-    """128 < n <= 1024 runs every squaring in one cooperative launch (split-k
-    work items merged with atomicMin, one grid barrier per squaring), each
+@pytest.fixture
+def cooperative_from_3():
+    """Send every n >= 3 up to the cooperative kernel's limit to it."""
+    with env(BTAS_APSP_SMALL_MAX_N="0"):
+        yield
+
+
+@pytest.mark.parametrize("n", [3, 7, 33, 100, 129, 200, 256, 333, 512, 777, 1024])
+def test_mid_graph_cooperative_path(btas, oracle_mod, n, cooperative_from_3):
+    """Up to n = 1024 every squaring can run in one cooperative launch (split-k
+    pieces merged with atomicMin, one grid barrier per squaring), each
     squaring on packed 16-bit pairs while the largest merged value allows it
     (<= 16383), else on int32.  Distances, squarings count and bound equal the
     general path's and the oracle's, with and without early exit, with the
@@ -269,7 +284,7 @@ def test_mid_graph_cooperative_path(btas, oracle_mod, n):
     assert host(D)[0, n - 1] == 5 * (n - 1)
     assert info["squarings"] == btas.btas_apsp_squarings(n)
     bad = W.copy()
-    bad[3, 7] = -1
+    bad[1, n - 1] = -1
     out = dev(np.full((n, n), 77, np.int32))
     with pytest.raises(btas.BtasError):
         btas.apsp(dev(bad), out=out)

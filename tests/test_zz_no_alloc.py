@@ -62,8 +62,8 @@ def test_in_place_and_size_limit(btas):
 
 
 def test_small_and_mid_sizes(btas):
-    """The one-block (n <= 128) and cooperative (mid n) kernels behind the
-    allocation-free entry point, out of place and in place."""
+    """The one-block (smallest n) and cooperative (up to n = 1024) kernels
+    behind the allocation-free entry point, out of place and in place."""
     import torch
     for n, seed in ((3, 74), (100, 75), (129, 76), (512, 77)):
         W = gen.random_graph(gen.BASE_SEED, seed, n, 0.5 if n < 8 else 0.05, 1, 100)
