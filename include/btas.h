@@ -359,11 +359,11 @@ int btas_apsp_squarings(int64_t n);
  * this library holds until the process exits; hence n <= BTAS_NOALLOC_MAX_N
  * (larger n returns BTAS_ERR_ARG, nothing enqueued).  The caller still passes
  * W and D (device pointers, n x n int32, row-major, D == W allowed).
- * The smallest n run on the one-block kernel and mid-size n whose three
- * iterates fit in the array on the cooperative kernel (as btas_apsp does,
- * with the same size boundary); larger n
- * runs the tiled int32 squarings.  Nothing is read back: the call does not
- * synchronise `stream`.
+ * The smallest n run on the one-block kernel and the others on the
+ * cooperative kernel, as in btas_apsp (the same size boundary); only if a
+ * cooperative launch is not possible on the device do they take the tiled
+ * int32 squarings.  Nothing is read back: the call does not synchronise
+ * `stream`.
  * The first call on a device looks up the array's device address with that
  * device current (a host-side set-up step); make that first call before any
  * stream capture.  All calls share the array and it keeps the last call's
@@ -373,7 +373,7 @@ int btas_apsp_squarings(int64_t n);
  * [0, 2^28] or BTAS_INF_I32) is assumed, not checked.
  * ------------------------------------------------------------------------ */
 #define BTAS_NOALLOC_MAX_N 1024
-#define BTAS_NOALLOC_SCRATCH_BYTES (256 + 2 * 4 * BTAS_NOALLOC_MAX_N * BTAS_NOALLOC_MAX_N)
+#define BTAS_NOALLOC_SCRATCH_BYTES (256 + 3 * 4 * BTAS_NOALLOC_MAX_N * BTAS_NOALLOC_MAX_N + 1024)
 btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
 /* ------------------------------------------------------------------------

@@ -15,15 +15,16 @@
 // that device current, through cudaGetSymbolAddress, on the first call made
 // on that device.  Make that first call before any stream capture.
 //
-// The smallest graphs run on the one-block kernel and mid-size graphs whose
-// three iterates fit in the scratch on the cooperative kernel (the same
-// kernels and size boundary as btas_apsp); the rest take the tiled int32 squarings below.
+// The smallest graphs run on the one-block kernel and the others on the
+// cooperative kernel (the same kernels and size boundary as btas_apsp); the
+// tiled int32 squarings below serve where a cooperative launch is refused.
 //
 // All calls share the one array, and each call leaves its contents behind.
 // The change flags, which must start at zero, are cleared on the stream at the
 // start of every call.  Calls whose work overlaps on the GPU (different
 // streams, or different host threads without ordering) race on the array.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -37,9 +38,11 @@ namespace {
 constexpr long long kMaxN = BTAS_NOALLOC_MAX_N;
 constexpr size_t kFlagBytes = 256;                                  // change flags (<= 64 ints)
 constexpr size_t kMatBytes = (size_t)kMaxN * (size_t)kMaxN * 4;     // one n x n int32 matrix
-static_assert(BTAS_NOALLOC_SCRATCH_BYTES == kFlagBytes + 2 * kMatBytes, "scratch layout");
+static_assert(BTAS_NOALLOC_SCRATCH_BYTES == kFlagBytes + 3 * kMatBytes + 1024, "scratch layout");
 
-// The scratch: [flags | X (ping-pong output) | T (transpose, row pitch round4(n))].
+// The scratch: [flags | X (ping-pong output) | T (transpose, row pitch
+// round4(n)) | one more matrix + 1 KiB]; the cooperative kernel takes
+// everything after the flags as its workspace.
 static __device__ __align__(256) unsigned char g_scratch[BTAS_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
@@ -126,14 +129,16 @@ extern "C" btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D
     if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
 
     // Small and mid-size graphs: the one-block kernel, or the cooperative
-    // kernel when its three iterates fit in the scratch matrices; both take
+    // kernel (its three iterates fit in the scratch for every n); both take
     // their status words from the flag area and need no read-back here.
     if (n <= apsp_small_limit()) {
         e = launch_apsp_small(W, n, (int)n, S, true, D, n, flags, st);
         if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
         return BTAS_OK;
     }
-    if (n <= apsp_mid_max_n() && apsp_mid_workspace(n, S) <= 2 * kMatBytes) {
+    const char *no_mid = getenv("BTAS_APSP_NO_MID");  // as in btas_apsp: tiled squarings
+    if (n <= apsp_mid_max_n() && apsp_mid_workspace(n, S) <= 3 * kMatBytes + 1024 &&
+        !(no_mid && *no_mid && atoi(no_mid) != 0)) {
         e = launch_apsp_mid(W, n, (int)n, S, true, true, D, n, X, flags, st);
         if (e == cudaSuccess) return BTAS_OK;
         if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorNotSupported)

@@ -47,6 +47,27 @@ def test_two_calls_match_allocating_entry_point(btas):
     np.testing.assert_array_equal(out2, ref2)
 
 
+def test_tiled_fallback(btas):
+    """The tiled int32 squarings, which serve where a cooperative launch is
+    refused (forced here with BTAS_APSP_NO_MID=1), out of place and in place,
+    twice in a row."""
+    import os
+    import torch
+    os.environ["BTAS_APSP_NO_MID"] = "1"
+    try:
+        for n, seed in ((1000, 79), (333, 80)):
+            W = gen.random_graph(gen.BASE_SEED, seed, n, 0.05, 1, 100)
+            ref, out = _both(btas, W)
+            np.testing.assert_array_equal(out, ref)
+            t = torch.from_numpy(W).cuda()
+            stream = torch.cuda.current_stream().cuda_stream
+            assert btas.btas_apsp_noalloc(n, t.data_ptr(), t.data_ptr(), stream) == 0
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(t.cpu().numpy(), ref)
+    finally:
+        del os.environ["BTAS_APSP_NO_MID"]
+
+
 def test_in_place_and_size_limit(btas):
     import torch
     W = gen.random_graph(gen.BASE_SEED, 73, 300, 0.05, 1, 50)
