@@ -1038,13 +1038,47 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) 
     }
     if (D != W) BTAS_CUDA(cudaMemcpyAsync(D, W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
     BTAS_CUDA(cudaMemsetAsync(pmax, 0xFF, (size_t)nb * 4, st), "memset");  // -1: nothing finite yet
-    for (int kb = 0; kb < nb; ++kb) {
+    // Lookahead: phases 1-2 of pivot block kb + 1, preceded by pivot block
+    // kb's phase-3 terms on block row and column kb + 1, run on a second
+    // stream of higher priority while the rest of phase 3 of kb -- which
+    // leaves block row and column kb + 1 alone -- runs on `st`.  The serial
+    // phases then hide behind the product.  BTAS_FW_NO_LOOKAHEAD=1 runs the
+    // three phases one after another on `st`.
+    const bool ahead = nb > 2 && env_int("BTAS_FW_NO_LOOKAHEAD", 0) == 0;
+    struct Side {
+        cudaStream_t s = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Side() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+            if (s) cudaStreamDestroy(s);
+        }
+    } side;
+    if (ahead) {
+        int least = 0, greatest = 0;
+        BTAS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+        BTAS_CUDA(cudaStreamCreateWithPriority(&side.s, cudaStreamNonBlocking, greatest), "side stream");
+        BTAS_CUDA(cudaEventCreateWithFlags(&side.a, cudaEventDisableTiming), "event");
+        BTAS_CUDA(cudaEventCreateWithFlags(&side.b, cudaEventDisableTiming), "event");
+    }
+    BTAS_CUDA(launch_fw_phase12(D, n, 0, allow16 ? pmax : nullptr, st), "phases 1-2");
+    for (int kb = 0; nb > 1 && kb < nb; ++kb) {
         const long long o = (long long)kb * B, bw = std::min<long long>(B, n - o);
-        BTAS_CUDA(launch_fw_phase12(D, n, kb, allow16 ? pmax + kb : nullptr, st), "phases 1-2");
-        if (nb == 1) break;
+        const bool next = kb + 1 < nb, ahead_now = ahead && next;
+        const long long o1 = o + bw;  // next pivot block
+        const long long bw1 = ahead_now ? std::min<long long>(B, n - o1) : 0;  // its width, if it runs ahead
         if (allow16) {
             // Ad pitch round4(bw): the pitch the packed kernel reads a pre-duplicated A with
             BTAS_CUDA(launch_fw_pack(D, n, kb, pmax + kb, state, Ad, (bw + 3) & ~3LL, Bu, ldbu, st), "packed panels");
+        }
+        if (ahead_now) {
+            BTAS_CUDA(cudaEventRecord(side.a, st), "event");
+            BTAS_CUDA(cudaStreamWaitEvent(side.s, side.a, 0), "event wait");
+            BTAS_CUDA(launch_fw_cross(D, n, kb, side.s), "lookahead update");
+            BTAS_CUDA(launch_fw_phase12(D, n, kb + 1, allow16 ? pmax + kb + 1 : nullptr, side.s), "phases 1-2");
+            BTAS_CUDA(cudaEventRecord(side.b, side.s), "event");
+        }
+        if (allow16) {
             U16Args a{};
             a.m = (int)n; a.n = (int)n; a.k = (int)bw;
             a.B = Bu; a.ldb = ldbu;
@@ -1052,12 +1086,16 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) 
             a.gate = state;
             a.adup_ready = true;
             a.Ci = D; a.ldci = n;
+            a.xr0 = a.xc0 = (int)o1;  // block row and column kb + 1 belong to the other stream
+            a.xr1 = a.xc1 = (int)(o1 + bw1);
             BTAS_CUDA(launch_tgemm_u16_ws(a, Ad, u16_ns(n, n, bw, st), st), "packed phase 3");
         }
         // row panel D[o:o+bw, :] transposed into RPT (n x B): the k-contiguous B operand
         BTAS_CUDA(launch_transpose4(D + o * n, n, (int)bw, (int)n, RPT, B, 0, allow16 ? state + 1 : nullptr, st),
                   "panel transpose");
-        const long long rr[2][2] = {{0, o}, {o + bw, n}};
+        // int32 phase 3 on the rectangles around the pivot block (and around
+        // block kb + 1 when it runs ahead)
+        const long long rr[2][2] = {{0, o}, {o1 + bw1, n}};
         for (int ri = 0; ri < 2; ++ri)
             for (int ci = 0; ci < 2; ++ci) {
                 const long long r0 = rr[ri][0], r1 = rr[ri][1], c0 = rr[ci][0], c1 = rr[ci][1];
@@ -1076,6 +1114,10 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) 
                 btas_status r = run_nt(BTAS_I32, kMin, a, st);
                 if (r != BTAS_OK) return r;
             }
+        if (ahead_now)
+            BTAS_CUDA(cudaStreamWaitEvent(st, side.b, 0), "event wait");
+        else if (next)
+            BTAS_CUDA(launch_fw_phase12(D, n, kb + 1, allow16 ? pmax + kb + 1 : nullptr, st), "phases 1-2");
     }
     return BTAS_OK;
 }

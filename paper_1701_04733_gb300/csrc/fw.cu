@@ -129,6 +129,57 @@ __global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, in
     store_tile(blk, D, n, r0, c0, pmax);
 }
 
+// Lookahead: the phase-3 update of pivot block kb applied to block row and
+// block column kb + 1 only -- the tiles that pivot block kb + 1's phases 1-2
+// read and write -- so that those phases can run while the rest of phase 3
+// (which leaves block row and column kb + 1 alone) is still going on.
+// blockIdx.x < nb: tile (kb + 1, b), b != kb (b = kb + 1 is the diagonal
+// tile); else tile (b, kb + 1), b != kb, kb + 1.  Each CTA takes
+// T = min(T, D[rows of T, pivots of kb] (x) D[pivots of kb, columns of T]),
+// the same terms phase 3 would, with the pivot tiles final after phases 1-2
+// of kb.
+__global__ void __launch_bounds__(FT, 1) fw_cross_kernel(int *D, long long n, int kb, int nb) {
+    extern __shared__ __align__(16) int sm[];
+    int *colsrc = sm, *rowsrc = sm + FB * FB;
+    const bool row = blockIdx.x < (unsigned)nb;
+    const int b = row ? blockIdx.x : blockIdx.x - nb;
+    const int kn = kb + 1;
+    if (b == kb || (!row && b == kn)) return;
+    const int o = kb * FB;
+    const int r0 = row ? kn * FB : b * FB, c0 = row ? b * FB : kn * FB;
+    load_tile(colsrc, D, n, r0, o);
+    load_tile(rowsrc, D, n, o, c0);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i0 = ty * 4, j0 = tx * 4;
+    int d[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            d[r][c] = (r0 + i0 + r < n && c0 + j0 + c < n) ? D[(long long)(r0 + i0 + r) * n + c0 + j0 + c] : kInfI32;
+    __syncthreads();
+    const int kmax = (int)min((long long)FB, n - o);
+#pragma unroll 4
+    for (int k = 0; k < kmax; ++k) {
+        int a[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = colsrc[(i0 + r) * FB + k];
+        const int4 bv = *reinterpret_cast<const int4 *>(rowsrc + k * FB + j0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            d[r][0] = __viaddmin_s32(a[r], bv.x, d[r][0]);
+            d[r][1] = __viaddmin_s32(a[r], bv.y, d[r][1]);
+            d[r][2] = __viaddmin_s32(a[r], bv.z, d[r][2]);
+            d[r][3] = __viaddmin_s32(a[r], bv.w, d[r][3]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (r0 + i0 + r < n && c0 + j0 + c < n) D[(long long)(r0 + i0 + r) * n + c0 + j0 + c] = d[r][c];
+}
+
 // Packed phase 3: state[0] = 1 when every finite entry of the pivot row and
 // column panels (after phase 2) is < 0x7FFF / 2, so that every finite term of
 // the phase-3 product is < 0x7FFF and the packed u16x2 product is exact;
@@ -188,6 +239,16 @@ cudaError_t launch_fw_phase12(int *D, long long n, int kb, int *pmax, cudaStream
         fw_panel_kernel<<<2 * nb, FT, 2 * FB * FB * 4, st>>>(D, n, kb, nb, pmax);
         note_launch();
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fw_cross(int *D, long long n, int kb, cudaStream_t st) {
+    const int nb = (int)((n + FB - 1) / FB);
+    if (kb + 1 >= nb) return cudaSuccess;
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(fw_cross_kernel), 2 * FB * FB * 4);
+    if (e != cudaSuccess) return e;
+    fw_cross_kernel<<<2 * nb, FT, 2 * FB * FB * 4, st>>>(D, n, kb, nb);
+    note_launch();
     return cudaGetLastError();
 }
 

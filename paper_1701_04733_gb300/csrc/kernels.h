@@ -107,6 +107,9 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
 // ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
 // pmax (optional): atomicMax of the largest finite value the phases store
 // (the pivot row and column panels).
+// Lookahead update: pivot block kb's phase-3 terms applied to block row and
+// column kb + 1 only (nothing when kb is the last block).
+cudaError_t launch_fw_cross(int *D, long long n, int kb, cudaStream_t st);
 cudaError_t launch_fw_phase12(int *D, long long n, int kb, int *pmax, cudaStream_t st);
 // Packed phase 3 set-up for pivot block kb: state[0] = 1 if 2 * *pmax <
 // 0x7FFF (state[1] = !state[0]); when set, the column panel goes to Ad
@@ -138,6 +141,7 @@ struct U16Args {
     bool adup_ready;    // `adup` already holds A's duplicated words (no pre-pass)
     int *Ci;            // optional: int32 accumulate target, Ci = min(Ci, result); C is then not written
     long long ldci;
+    int xr0, xr1, xc0, xc1;  // with Ci: rows [xr0, xr1) and columns [xc0, xc1) of Ci are left untouched
 };
 // Duplicates A into `adup` (m x round4(k) 32-bit words, caller workspace;
 // with adup_ready the caller has filled it, with that pitch) and runs the

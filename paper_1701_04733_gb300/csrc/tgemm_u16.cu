@@ -54,6 +54,7 @@ struct U16KArgs {
     const int *gate;  // optional: *gate == 0 => do nothing
     int *Ci;          // optional: accumulate into int32 Ci = min(Ci, widened result) instead of writing C
     long long ldci;
+    int xr0, xr1, xc0, xc1;  // rows / columns of Ci not to write (another stream owns them)
 };
 
 __global__ void dup_u16_kernel(const uint16_t *__restrict__ A, long long lda, int m, int k, uint32_t *__restrict__ Ad,
@@ -103,6 +104,16 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
     const int bm = tm * BM, bnp = tn * BNP;  // bnp in pairs; column = 2*pair
 
     if (args.gate != nullptr && __ldcg(args.gate) == 0) return;
+    if (args.Ci != nullptr) {
+        // Pull this CTA's tile of Ci into L2 while its products run: the
+        // min-accumulate epilogue then reads it from L2.  With a short k (128
+        // in blocked Floyd-Warshall) that read is a third of the kernel time
+        // otherwise, since one CTA per SM leaves nothing to overlap it with.
+        for (int l = tid; l < BM * 8; l += NT) {  // 8 lines of 32 words per tile row
+            const int r = bm + (l >> 3), c = 2 * bnp + (l & 7) * 32;
+            if (r < M && c < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(args.Ci + (long long)r * args.ldci + c));
+        }
+    }
     if (args.skip != nullptr && *args.skip == 0) {
         for (int idx = tid; idx < BM * BNP * 2; idx += NT) {
             const int r = bm + idx / (BNP * 2), c = 2 * bnp + idx % (BNP * 2);
@@ -251,7 +262,7 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
             for (int ii = 0; ii < 2; ++ii) {
                 const int i = i0 + ii;
                 const int r = bm + row_base + 4 * i;
-                if (r >= M) continue;
+                if (r >= M || (r >= args.xr0 && r < args.xr1)) continue;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int c0 = 2 * (bnp + pair_base + 32 * h);
@@ -265,13 +276,14 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
                         if (hi < BTAS_INF_U16) v[2 * q + 1] = min(v[2 * q + 1], (int)hi);
                     }
                     int *pc = args.Ci + (long long)r * args.ldci + c0;
-                    if (vec && c0 + 8 <= N) {
+                    const bool clear = c0 + 8 <= args.xc0 || c0 >= args.xc1;  // none of the 8 excluded
+                    if (vec && c0 + 8 <= N && clear) {
                         *reinterpret_cast<int4 *>(pc) = make_int4(v[0], v[1], v[2], v[3]);
                         *reinterpret_cast<int4 *>(pc + 4) = make_int4(v[4], v[5], v[6], v[7]);
                     } else {
 #pragma unroll
                         for (int e = 0; e < 8; ++e)
-                            if (c0 + e < N) pc[e] = v[e];
+                            if (c0 + e < N && (c0 + e < args.xc0 || c0 + e >= args.xc1)) pc[e] = v[e];
                     }
                 }
             }
@@ -403,6 +415,10 @@ cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaSt
     ka.gate = a.gate;
     ka.Ci = a.Ci;
     ka.ldci = a.ldci;
+    ka.xr0 = a.xr0;
+    ka.xr1 = a.xr1;
+    ka.xc0 = a.xc0;
+    ka.xc1 = a.xc1;
     ka.vec_a = (reinterpret_cast<uintptr_t>(adup) & 15) == 0;
     ka.vec_b = (reinterpret_cast<uintptr_t>(a.B) & 15) == 0 && (a.ldb & 7) == 0;
     switch (ns) {

@@ -36,16 +36,19 @@ class env:
                 os.environ[k] = v
 
 
+@pytest.mark.parametrize("ahead", ["0", "1"])
 @pytest.mark.parametrize("packed", ["0", "1"])
 @pytest.mark.parametrize("whi", [100, 10 ** 6])
 @pytest.mark.parametrize("n", [1, 2, 5, 127, 128, 129, 255, 300, 513])
-def test_blocked_fw_equals_oracle(btas, oracle_mod, n, whi, packed):
+def test_blocked_fw_equals_oracle(btas, oracle_mod, n, whi, packed, ahead):
     """Small weights: phase 3 runs packed (u16x2) where the panels allow it;
     weights up to 10^6: it stays on the int32 kernel; BTAS_FW_NO_U16=1
-    forces int32 throughout.  Same bits every time."""
+    forces int32 throughout.  With three or more pivot blocks, phases 1-2 of
+    the next block run ahead on a second stream (BTAS_FW_NO_LOOKAHEAD=1: one
+    stream, phases in order).  Same bits every time."""
     W = gen.random_graph(31, n, n, 0.05 if n > 10 else 0.5, 0, whi)
     ref = oracle_mod.floyd_warshall(W)
-    with env(BTAS_FW_NO_U16="0" if packed == "1" else "1"):
+    with env(BTAS_FW_NO_U16="0" if packed == "1" else "1", BTAS_FW_NO_LOOKAHEAD="0" if ahead == "1" else "1"):
         np.testing.assert_array_equal(host(btas.apsp_fw(dev(W))), ref)
         t = dev(W)
         btas.apsp_fw(t, out=t)
