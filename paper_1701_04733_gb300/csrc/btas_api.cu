@@ -965,38 +965,70 @@ btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Ne
     const int S = btas_apsp_squarings(n);
     const size_t nn = (size_t)n * (size_t)n;
     const long long ldt = (n + 3) & ~3LL;
+    // Keyed squarings (one int32 min-plus product carries distance and
+    // smallest minimising k, see paths.cu) while the entries allow it;
+    // BTAS_PATHS_NO_KEYED=1 keeps every squaring on the argmin kernel.
+    const bool keyed_ok = n <= paths_key_max_n() && env_int("BTAS_PATHS_NO_KEYED", 0) == 0;
     Workspace ws(st);
-    const size_t flag_bytes = align256((size_t)(S + 4) * 4);
-    BTAS_CUDA(ws.alloc(flag_bytes + 4 * align256(nn * 4) + align256((size_t)n * ldt * 4)), "workspace alloc");
+    const size_t flag_bytes = align256((size_t)(2 * S + 4) * 4);
+    const size_t ak_bytes = keyed_ok ? align256(nn * 4) : 0;
+    BTAS_CUDA(ws.alloc(flag_bytes + 4 * align256(nn * 4) + align256((size_t)n * ldt * 4) + ak_bytes),
+              "workspace alloc");
     char *base = static_cast<char *>(ws.p);
-    int *dflags = reinterpret_cast<int *>(base);
+    int *dflags = reinterpret_cast<int *>(base);  // [2s] changed, [2s + 1] largest finite entry after squaring s
     int *Db[2], *Nb[2];
     Db[0] = reinterpret_cast<int *>(base + flag_bytes);
     Db[1] = reinterpret_cast<int *>(reinterpret_cast<char *>(Db[0]) + align256(nn * 4));
     Nb[0] = reinterpret_cast<int *>(reinterpret_cast<char *>(Db[1]) + align256(nn * 4));
     Nb[1] = reinterpret_cast<int *>(reinterpret_cast<char *>(Nb[0]) + align256(nn * 4));
     int *T = reinterpret_cast<int *>(reinterpret_cast<char *>(Nb[1]) + align256(nn * 4));
+    int *Ak = keyed_ok ? reinterpret_cast<int *>(reinterpret_cast<char *>(T) + align256((size_t)n * ldt * 4)) : nullptr;
     BTAS_CUDA(cudaMemsetAsync(dflags, 0, flag_bytes, st), "memset");
     // domain: zero diagonal, weights in [0, 2^28] or INF
+    long long mval = 0;  // bound on the finite entries of the current D
     {
         int host[2] = {0, 0};
-        BTAS_CUDA(launch_apsp_scan(W, n, dflags + S + 1, st), "domain scan");
-        BTAS_CUDA(read_back(host, dflags + S + 1, 8, st), "scan readback");
+        BTAS_CUDA(launch_apsp_scan(W, n, dflags + 2 * S + 1, st), "domain scan");
+        BTAS_CUDA(read_back(host, dflags + 2 * S + 1, 8, st), "scan readback");
         if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_apsp_paths: %d entries outside the domain", host[1]);
+        mval = host[0];
     }
     BTAS_CUDA(cudaMemcpyAsync(Db[0], W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
     BTAS_CUDA(launch_next_init(W, n, Nb[0], st), "next-hop init");
-    int cur = 0, done = 0;
+    int cur = 0, done = 0, keyed_count = 0;
     for (int s = 0; s < S; ++s) {
-        BTAS_CUDA(launch_transpose4(Db[cur], n, (int)n, (int)n, T, ldt, 0, nullptr, st), "transpose");
-        BTAS_CUDA(launch_paths_square((int)n, Db[cur], n, T, ldt, Nb[cur], Db[cur ^ 1], Nb[cur ^ 1], &dflags[s], st),
-                  "paths squaring");
+        const bool keyed = keyed_ok && mval <= paths_key_max();
+        if (keyed) {
+            // keys in Db[cur ^ 1], decoded there in place
+            BTAS_CUDA(launch_paths_encode(Db[cur], (int)n, Ak, T, ldt, st), "key encode");
+            GemmArgs a{};
+            a.m = a.n = a.k = (int)n;
+            a.A = Ak; a.lda = n;
+            a.Bt = T; a.ldb = ldt;
+            a.C = Db[cur ^ 1]; a.ldc = n;
+            a.vec_a = aligned16(Ak, n);
+            a.vec_b = aligned16(T, ldt);
+            btas_status r = run_nt(BTAS_I32, kMin, a, st);
+            if (r != BTAS_OK) return r;
+            BTAS_CUDA(launch_paths_decode(Db[cur ^ 1], Db[cur], Nb[cur], n, Db[cur ^ 1], Nb[cur ^ 1], &dflags[2 * s],
+                                          &dflags[2 * s + 1], st),
+                      "key decode");
+            ++keyed_count;
+        } else {
+            BTAS_CUDA(launch_transpose4(Db[cur], n, (int)n, (int)n, T, ldt, 0, nullptr, st), "transpose");
+            BTAS_CUDA(launch_paths_square((int)n, Db[cur], n, T, ldt, Nb[cur], Db[cur ^ 1], Nb[cur ^ 1],
+                                          &dflags[2 * s], st),
+                      "paths squaring");
+        }
         cur ^= 1;
-        int changed = 1;
-        BTAS_CUDA(read_back(&changed, &dflags[s], 4, st), "flag readback");
-        if (changed) ++done;
-        if (!changed && (flags & BTAS_APSP_EARLY_EXIT)) break;
+        int host[2] = {1, 0};
+        BTAS_CUDA(read_back(host, &dflags[2 * s], 8, st), "flag readback");
+        // every finite entry of the new D is a sum of two of the old
+        mval = keyed ? host[1] : 2 * mval;
+        if (host[0]) ++done;
+        if (!host[0] && (flags & BTAS_APSP_EARLY_EXIT)) break;
     }
+    log_event("apsp paths n=%lld: %d of the squarings keyed (one int32 product each)", (long long)n, keyed_count);
     BTAS_CUDA(cudaMemcpyAsync(D, Db[cur], nn * 4, cudaMemcpyDeviceToDevice, st), "copy D");
     BTAS_CUDA(cudaMemcpyAsync(Next, Nb[cur], nn * 4, cudaMemcpyDeviceToDevice, st), "copy Next");
     if (squarings_done) *squarings_done = done;

@@ -71,6 +71,16 @@ cudaError_t launch_ident_oplus(const void *src, long long lds, int n, void *dst,
 cudaError_t launch_apsp_scan(const int *W, long long n, int *out, cudaStream_t st);
 
 // ---- APSP with next-hop matrix (paths.cu)
+// Keyed path squaring (paths.cu): while every finite entry of D is <=
+// paths_key_max() and n <= paths_key_max_n(), one int32 min-plus product of
+// A' = D << 13 and B' = (D << 13) | k gives distances and smallest
+// minimising k together.  encode: A' (pitch n) and B'^T (pitch ldt);
+// decode: keys -> D', N' (K may be Dn), change flag, largest finite entry.
+int paths_key_max();
+int paths_key_max_n();
+cudaError_t launch_paths_encode(const int *D, int n, int *Ak, int *BkT, long long ldt, cudaStream_t st);
+cudaError_t launch_paths_decode(const int *K, const int *D, const int *N, long long n, int *Dn, int *Nn, int *changed,
+                                int *maxfin, cudaStream_t st);
 cudaError_t launch_next_init(const int *W, long long n, int *N, cudaStream_t st);
 cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *Dt, long long ldt, const int *N,
                                 int *D2, int *N2, int *changed, cudaStream_t st);

@@ -113,6 +113,74 @@ paths_square_kernel(int n, const int *__restrict__ D, long long ldd, const int *
     if (__any_sync(0xffffffffu, ch) && (tid & 31) == 0) atomicOr(changed, 1);
 }
 
+// Keyed squaring.  While every finite entry of D is <= kKeyMax and n <=
+// 2^13, the pair (value, k) of one term is encoded as the single int32 key
+// (value << 13) | k, so that the minimum key holds the minimum value and,
+// among equal values, the smallest k.  The key of term (i, k, j) is the sum
+// A'[i][k] + B'[k][j] with A' = D << 13 and B' = (D << 13) | k (row index),
+// so one plain min-plus product of A' and B' -- the tuned int32 kernels --
+// computes distances and argmins at once.  Finite keys stay below the
+// product kernel's INF clamp (2 * 49151 << 13 | 8191 < INF - 2^28); INF
+// entries encode as INF, and every key with an INF term is clamped to INF.
+constexpr int kKeyShift = 13;
+constexpr int kKeyMaxN = 1 << kKeyShift;
+
+__device__ __forceinline__ int key_a(int v) { return v >= kInfI32 ? kInfI32 : v << kKeyShift; }
+__device__ __forceinline__ int key_b(int v, int k) { return v >= kInfI32 ? kInfI32 : (v << kKeyShift) | k; }
+
+// A' (same layout as D) and B'^T (ldt pitch: B'^T[j][k] = key_b(D[k][j], k)),
+// through 32 x 32 shared tiles so that both are written coalesced.
+__global__ void paths_encode_kernel(const int *__restrict__ D, int n, int *__restrict__ Ak, int *__restrict__ BkT,
+                                    long long ldt) {
+    __shared__ int tile[32][33];
+    const int k0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int k = k0 + r, j = j0 + threadIdx.x;
+        if (k < n && j < n) {
+            const int v = D[(long long)k * n + j];
+            Ak[(long long)k * n + j] = key_a(v);
+            tile[r][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int j = j0 + r, k = k0 + threadIdx.x;
+        if (j < n && k < n) BkT[(long long)j * ldt + k] = key_b(tile[threadIdx.x][r], k);
+    }
+}
+
+// Keys -> D' and N' (K may be D'), the change flag and the largest finite
+// entry of D'.  N'[i][j] = -1 for INF, N[i][j] if the minimising k is i,
+// else N[i][k] -- the rule of the unkeyed kernel.
+__global__ void paths_decode_kernel(const int *K, const int *__restrict__ D, const int *__restrict__ N, long long n,
+                                    int *Dn, int *__restrict__ Nn, int *changed, int *maxfin) {
+    const long long total = n * n;
+    bool ch = false;
+    int mx = 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int key = K[idx];
+        int d = kInfI32, nx = -1;
+        if (key < kInfI32) {
+            const long long i = idx / n;
+            const int k = key & (kKeyMaxN - 1);
+            d = key >> kKeyShift;
+            nx = k == i ? N[idx] : N[i * n + k];
+            mx = max(mx, d);
+        }
+        ch |= d != D[idx] || nx != N[idx];
+        Dn[idx] = d;
+        Nn[idx] = nx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const bool any = __any_sync(0xffffffffu, ch);
+    if ((threadIdx.x & 31) == 0) {
+        if (any) atomicOr(changed, 1);
+        atomicMax(maxfin, mx);
+    }
+}
+
 __global__ void next_init_kernel(const int *__restrict__ W, long long n, int *__restrict__ N) {
     const long long total = n * n;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -129,6 +197,27 @@ cudaError_t launch_next_init(const int *W, long long n, int *N, cudaStream_t st)
     long long b = (n * n + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
     next_init_kernel<<<(int)b, 256, 0, st>>>(W, n, N);
+    note_launch();
+    return cudaGetLastError();
+}
+
+int paths_key_max() { return 49151; }
+int paths_key_max_n() { return kKeyMaxN; }
+
+cudaError_t launch_paths_encode(const int *D, int n, int *Ak, int *BkT, long long ldt, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid((n + 31) / 32, (n + 31) / 32);
+    paths_encode_kernel<<<grid, dim3(32, 8), 0, st>>>(D, n, Ak, BkT, ldt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_paths_decode(const int *K, const int *D, const int *N, long long n, int *Dn, int *Nn, int *changed,
+                                int *maxfin, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long b = (n * n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    paths_decode_kernel<<<(int)b, 256, 0, st>>>(K, D, N, n, Dn, Nn, changed, maxfin);
     note_launch();
     return cudaGetLastError();
 }

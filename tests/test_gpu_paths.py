@@ -27,12 +27,38 @@ def test_hand_worked(btas):
     np.testing.assert_array_equal(host(Nx), as_i32(g["N"]))
 
 
+class env:
+    """Set environment variables for the duration of a with-block."""
+
+    def __init__(self, **kv):
+        self.kv = kv
+
+    def __enter__(self):
+        import os
+        self.old = {k: os.environ.get(k) for k in self.kv}
+        os.environ.update(self.kv)
+
+    def __exit__(self, *a):
+        import os
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+@pytest.mark.parametrize("keyed", ["1", "0"])
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 64, 65, 200, 513])
-def test_matches_oracle_and_walks_are_shortest(btas, oracle_mod, n):
+def test_matches_oracle_and_walks_are_shortest(btas, oracle_mod, n, keyed):
+    """Weights 1..20, so equal-length alternatives are common and the
+    smallest-k rule decides many next hops.  keyed = 1: each squaring is one
+    int32 product of (value << 13 | k) keys; keyed = 0
+    (BTAS_PATHS_NO_KEYED=1): the argmin kernel."""
     W = gen.random_graph(21, n, n, 0.08 if n > 10 else 0.5, 1, 20)
     ref_d, ref_n = oracle_mod.apsp_paths(W)
     for early in (True, False):
-        D, Nx = btas.apsp_paths(dev(W), early_exit=early)
+        with env(BTAS_PATHS_NO_KEYED="0" if keyed == "1" else "1"):
+            D, Nx = btas.apsp_paths(dev(W), early_exit=early)
         np.testing.assert_array_equal(host(D), ref_d)
         np.testing.assert_array_equal(host(Nx), ref_n)
     D, Nx = host(D), host(Nx)
@@ -50,3 +76,20 @@ def test_matches_oracle_and_walks_are_shortest(btas, oracle_mod, n):
             steps += 1
             assert steps <= n
         assert tot == D[i, j]
+
+
+@pytest.mark.parametrize("whi", [30000, 10 ** 6])
+def test_large_weights(btas, oracle_mod, whi):
+    """Weights up to 30000: the first squaring is keyed (every entry <=
+    49151), later ones, whose sums may exceed the key range, run on the
+    argmin kernel; weights up to 10^6: the argmin kernel throughout.  Same
+    bits as the oracle either way, with ties among the 10^6 weights made by
+    repeated weights."""
+    n = 300
+    W = gen.random_graph(22, whi % 97, n, 0.05, 1, whi)
+    W[(W != INF) & (W > 0)] = (W[(W != INF) & (W > 0)] // 7) * 7 + 7  # coarser weights: more ties
+    np.fill_diagonal(W, 0)
+    ref_d, ref_n = oracle_mod.apsp_paths(W)
+    D, Nx = btas.apsp_paths(dev(W))
+    np.testing.assert_array_equal(host(D), ref_d)
+    np.testing.assert_array_equal(host(Nx), ref_n)
