@@ -151,31 +151,37 @@ __global__ void paths_encode_kernel(const int *__restrict__ D, int n, int *__res
 
 // Keys -> D' and N' (K may be D'), the change flag and the largest finite
 // entry of D'.  N'[i][j] = -1 for INF, N[i][j] if the minimising k is i,
-// else N[i][k] -- the rule of the unkeyed kernel.
-__global__ void paths_decode_kernel(const int *K, const int *__restrict__ D, const int *__restrict__ N, long long n,
-                                    int *Dn, int *__restrict__ Nn, int *changed, int *maxfin) {
-    const long long total = n * n;
+// else N[i][k] -- the rule of the unkeyed kernel.  One block per row: the
+// gathers N[i][k] stay within one row, and the flag and maximum cost one
+// atomic each per row.
+__global__ void __launch_bounds__(256) paths_decode_kernel(const int *K, const int *__restrict__ D,
+                                                           const int *__restrict__ N, int n, int *Dn,
+                                                           int *__restrict__ Nn, int *changed, int *maxfin) {
+    __shared__ int s_mx[8];
+    const int i = blockIdx.x;
+    const long long row = (long long)i * n;
     bool ch = false;
     int mx = 0;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int key = K[idx];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int key = K[row + j];
         int d = kInfI32, nx = -1;
         if (key < kInfI32) {
-            const long long i = idx / n;
             const int k = key & (kKeyMaxN - 1);
             d = key >> kKeyShift;
-            nx = k == i ? N[idx] : N[i * n + k];
+            nx = N[row + (k == i ? j : k)];
             mx = max(mx, d);
         }
-        ch |= d != D[idx] || nx != N[idx];
-        Dn[idx] = d;
-        Nn[idx] = nx;
+        ch |= d != D[row + j] || nx != N[row + j];
+        Dn[row + j] = d;
+        Nn[row + j] = nx;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const bool any = __any_sync(0xffffffffu, ch);
-    if ((threadIdx.x & 31) == 0) {
+    if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+    const int any = __syncthreads_or(ch ? 1 : 0);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, s_mx[w]);
+        mx = max(mx, s_mx[0]);
         if (any) atomicOr(changed, 1);
         atomicMax(maxfin, mx);
     }
@@ -215,9 +221,7 @@ cudaError_t launch_paths_encode(const int *D, int n, int *Ak, int *BkT, long lon
 cudaError_t launch_paths_decode(const int *K, const int *D, const int *N, long long n, int *Dn, int *Nn, int *changed,
                                 int *maxfin, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    long long b = (n * n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
-    paths_decode_kernel<<<(int)b, 256, 0, st>>>(K, D, N, n, Dn, Nn, changed, maxfin);
+    paths_decode_kernel<<<(int)n, 256, 0, st>>>(K, D, N, (int)n, Dn, Nn, changed, maxfin);
     note_launch();
     return cudaGetLastError();
 }
