@@ -21,8 +21,13 @@ namespace btas {
 
 namespace {
 
-constexpr int FB = 128;   // tile edge
-constexpr int FT = 1024;  // threads: 32 x 32, each owning a 4 x 4 block of the tile
+constexpr int FB = 128;  // tile edge
+constexpr int FT = 256;  // threads: 16 x 16, each owning 8 rows x 8 columns of the tile
+
+// A thread's tile coordinates: rows ty*8 .. ty*8+7 (contiguous) and columns
+// tx*4 + {0..3} and 64 + tx*4 + {0..3} (two groups, so that a warp's row
+// loads are contiguous 16-byte chunks: no bank conflicts).
+__device__ __forceinline__ int fw_col(int tx, int c) { return (c < 4 ? 0 : 64 - 4) + tx * 4 + c; }
 
 // Load tile (r0, c0) of D into shared memory (INF outside the matrix).
 __device__ __forceinline__ void load_tile(int *sm, const int *D, long long n, int r0, int c0) {
@@ -49,55 +54,73 @@ __device__ __forceinline__ void store_tile(const int *sm, int *D, long long n, i
     }
 }
 
+// d[r][c] = min(d[r][c], colsrc[row r][k] + rowsrc[k][column c]) for the
+// thread's 8 x 8 outputs: 8 broadcast loads of the column, two 16-byte loads
+// of the row, 64 DPX add-min.
+__device__ __forceinline__ void relax8(int (&d)[8][8], const int *colsrc, const int *rowsrc, int i0, int tx, int k) {
+    int a[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = colsrc[(i0 + r) * FB + k];
+    const int4 b0 = *reinterpret_cast<const int4 *>(rowsrc + k * FB + tx * 4);
+    const int4 b1 = *reinterpret_cast<const int4 *>(rowsrc + k * FB + 64 + tx * 4);
+    const int b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) d[r][c] = __viaddmin_s32(a[r], b[c], d[r][c]);
+}
+
 // The pivots of one block: blk[i][j] = min(blk[i][j], colsrc[i][k] +
 // rowsrc[k][j]) for k = 0 .. kmax-1 in order (kmax < FB only in the last
 // block, whose padding pivots are INF rows and columns and change nothing).
-// Each thread keeps its 4 x 4 outputs in registers.  Pivot k reads row k of
+// Each thread keeps its 8 x 8 outputs in registers.  Pivot k reads row k of
 // rowsrc and column k of colsrc; during pivot k neither changes (zero
 // diagonal, non-negative weights), so after relaxing, only the owners of
 // row k+1 (when rowsrc is blk: PUB_ROW) and of column k+1 (when colsrc is
 // blk: PUB_COL) publish those values to shared memory, and one barrier per
-// pivot orders them before the next pivot's reads.  Operands lie in [0, INF]:
+// pivot orders them before the next pivot's reads.  Pivots go in groups of
+// 8, unrolled, so the published row and column of each are known at compile
+// time (registers are not indexed at run time).  Operands lie in [0, INF]:
 // a + b cannot overflow, and one DPX add-min is one relaxation.
 template <bool PUB_ROW, bool PUB_COL>
 __device__ __forceinline__ void pivots(int *blk, const int *colsrc, const int *rowsrc, int kmax) {
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int i0 = ty * 4, j0 = tx * 4;
-    int d[4][4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = ty * 8;
+    int d[8][8];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int4 v = *reinterpret_cast<const int4 *>(blk + (i0 + r) * FB + j0);
-        d[r][0] = v.x; d[r][1] = v.y; d[r][2] = v.z; d[r][3] = v.w;
-    }
-    for (int k = 0; k < kmax; ++k) {  // pivots past the matrix edge are INF rows/columns: no-ops
-        int a[4];
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = colsrc[(i0 + r) * FB + k];
-        const int4 b = *reinterpret_cast<const int4 *>(rowsrc + k * FB + j0);
+        for (int c = 0; c < 8; ++c) d[r][c] = blk[(i0 + r) * FB + fw_col(tx, c)];
+    for (int kg = 0; kg < kmax; kg += 8) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            d[r][0] = __viaddmin_s32(a[r], b.x, d[r][0]);
-            d[r][1] = __viaddmin_s32(a[r], b.y, d[r][1]);
-            d[r][2] = __viaddmin_s32(a[r], b.z, d[r][2]);
-            d[r][3] = __viaddmin_s32(a[r], b.w, d[r][3]);
+        for (int q = 0; q < 8; ++q) {
+            const int k = kg + q;
+            if (k < kmax) {  // pivots past the matrix edge are INF rows/columns: no-ops
+                relax8(d, colsrc, rowsrc, i0, tx, k);
+                const int kn = k + 1;
+                const int qr = (q + 1) & 7;  // row of kn within its owner (compile time)
+                if (PUB_ROW && (kn >> 3) == ty) {
+                    *reinterpret_cast<int4 *>(blk + (i0 + qr) * FB + tx * 4) =
+                        make_int4(d[qr][0], d[qr][1], d[qr][2], d[qr][3]);
+                    *reinterpret_cast<int4 *>(blk + (i0 + qr) * FB + 64 + tx * 4) =
+                        make_int4(d[qr][4], d[qr][5], d[qr][6], d[qr][7]);
+                }
+                // column kn: group h = kn >= 64, owner tx = (kn & 63) >> 2, slot (kn & 3) = (q + 1) & 3
+                const int qc = (q + 1) & 3;
+                if (PUB_COL && ((kn & 63) >> 2) == tx && kn < FB) {
+                    const bool hi = kn >= 64;
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) blk[(i0 + r) * FB + kn] = hi ? d[r][4 + qc] : d[r][qc];
+                }
+                __syncthreads();
+            }
         }
-        const int kn = k + 1, q = kn & 3;  // selects by value keep d in registers
-        if (PUB_ROW && (kn >> 2) == ty) {
-            int v[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = q == 0 ? d[0][c] : q == 1 ? d[1][c] : q == 2 ? d[2][c] : d[3][c];
-            *reinterpret_cast<int4 *>(blk + (i0 + q) * FB + j0) = make_int4(v[0], v[1], v[2], v[3]);
-        }
-        if (PUB_COL && (kn >> 2) == tx) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                blk[(i0 + r) * FB + j0 + q] = q == 0 ? d[r][0] : q == 1 ? d[r][1] : q == 2 ? d[r][2] : d[r][3];
-        }
-        __syncthreads();
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-        *reinterpret_cast<int4 *>(blk + (i0 + r) * FB + j0) = make_int4(d[r][0], d[r][1], d[r][2], d[r][3]);
+    for (int r = 0; r < 8; ++r) {
+        *reinterpret_cast<int4 *>(blk + (i0 + r) * FB + tx * 4) = make_int4(d[r][0], d[r][1], d[r][2], d[r][3]);
+        *reinterpret_cast<int4 *>(blk + (i0 + r) * FB + 64 + tx * 4) = make_int4(d[r][4], d[r][5], d[r][6], d[r][7]);
+    }
     __syncthreads();
 }
 
@@ -149,35 +172,27 @@ __global__ void __launch_bounds__(FT, 1) fw_cross_kernel(int *D, long long n, in
     const int r0 = row ? kn * FB : b * FB, c0 = row ? b * FB : kn * FB;
     load_tile(colsrc, D, n, r0, o);
     load_tile(rowsrc, D, n, o, c0);
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int i0 = ty * 4, j0 = tx * 4;
-    int d[4][4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = ty * 8;
+    int d[8][8];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-            d[r][c] = (r0 + i0 + r < n && c0 + j0 + c < n) ? D[(long long)(r0 + i0 + r) * n + c0 + j0 + c] : kInfI32;
+        for (int c = 0; c < 8; ++c) {
+            const int gi = r0 + i0 + r, gj = c0 + fw_col(tx, c);
+            d[r][c] = (gi < n && gj < n) ? D[(long long)gi * n + gj] : kInfI32;
+        }
     __syncthreads();
     const int kmax = (int)min((long long)FB, n - o);
-#pragma unroll 4
-    for (int k = 0; k < kmax; ++k) {
-        int a[4];
+#pragma unroll 2
+    for (int k = 0; k < kmax; ++k) relax8(d, colsrc, rowsrc, i0, tx, k);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = colsrc[(i0 + r) * FB + k];
-        const int4 bv = *reinterpret_cast<const int4 *>(rowsrc + k * FB + j0);
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            d[r][0] = __viaddmin_s32(a[r], bv.x, d[r][0]);
-            d[r][1] = __viaddmin_s32(a[r], bv.y, d[r][1]);
-            d[r][2] = __viaddmin_s32(a[r], bv.z, d[r][2]);
-            d[r][3] = __viaddmin_s32(a[r], bv.w, d[r][3]);
+        for (int c = 0; c < 8; ++c) {
+            const int gi = r0 + i0 + r, gj = c0 + fw_col(tx, c);
+            if (gi < n && gj < n) D[(long long)gi * n + gj] = d[r][c];
         }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (r0 + i0 + r < n && c0 + j0 + c < n) D[(long long)(r0 + i0 + r) * n + c0 + j0 + c] = d[r][c];
 }
 
 // Packed phase 3: state[0] = 1 when every finite entry of the pivot row and
