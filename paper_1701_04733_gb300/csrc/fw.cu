@@ -29,22 +29,47 @@ constexpr int FT = 256;  // threads: 16 x 16, each owning 8 rows x 8 columns of 
 // loads are contiguous 16-byte chunks: no bank conflicts).
 __device__ __forceinline__ int fw_col(int tx, int c) { return (c < 4 ? 0 : 64 - 4) + tx * 4 + c; }
 
-// Load tile (r0, c0) of D into shared memory (INF outside the matrix).
+// Load tile (r0, c0) of D into shared memory (INF outside the matrix), in
+// 16-byte vectors where the rows allow (n a multiple of 4).
 __device__ __forceinline__ void load_tile(int *sm, const int *D, long long n, int r0, int c0) {
-    for (int idx = threadIdx.x; idx < FB * FB; idx += FT) {
-        const int r = idx / FB, c = idx % FB;
-        sm[idx] = (r0 + r < n && c0 + c < n) ? D[(long long)(r0 + r) * n + c0 + c] : kInfI32;
+    const bool vec = (n & 3) == 0;
+    for (int idx = threadIdx.x; idx < FB * FB / 4; idx += blockDim.x) {
+        const int r = idx / (FB / 4), c = (idx % (FB / 4)) * 4;
+        const long long gr = r0 + r, gc = c0 + c;
+        int4 v;
+        if (vec && gr < n && gc + 4 <= n) {
+            v = *reinterpret_cast<const int4 *>(D + gr * n + gc);
+        } else {
+            int t[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) t[e] = (gr < n && gc + e < n) ? D[gr * n + gc + e] : kInfI32;
+            v = make_int4(t[0], t[1], t[2], t[3]);
+        }
+        *reinterpret_cast<int4 *>(sm + r * FB + c) = v;
     }
 }
 // Store the tile; with pmax, also atomicMax the largest finite value stored.
 __device__ __forceinline__ void store_tile(const int *sm, int *D, long long n, int r0, int c0, int *pmax) {
+    const bool vec = (n & 3) == 0;
     int mx = -1;
-    for (int idx = threadIdx.x; idx < FB * FB; idx += FT) {
-        const int r = idx / FB, c = idx % FB;
-        if (r0 + r < n && c0 + c < n) {
-            const int v = sm[idx];
-            D[(long long)(r0 + r) * n + c0 + c] = v;
-            if (v < kInfI32) mx = max(mx, v);
+    for (int idx = threadIdx.x; idx < FB * FB / 4; idx += blockDim.x) {
+        const int r = idx / (FB / 4), c = (idx % (FB / 4)) * 4;
+        const long long gr = r0 + r, gc = c0 + c;
+        if (gr >= n) continue;
+        const int4 v = *reinterpret_cast<const int4 *>(sm + r * FB + c);
+        const int t[4] = {v.x, v.y, v.z, v.w};
+        if (vec && gc + 4 <= n) {
+            *reinterpret_cast<int4 *>(D + gr * n + gc) = v;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (t[e] < kInfI32) mx = max(mx, t[e]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (gc + e < n) {
+                    D[gr * n + gc + e] = t[e];
+                    if (t[e] < kInfI32) mx = max(mx, t[e]);
+                }
         }
     }
     if (pmax != nullptr) {
@@ -161,9 +186,11 @@ __global__ void __launch_bounds__(FT, 1) fw_panel_kernel(int *D, long long n, in
 // T = min(T, D[rows of T, pivots of kb] (x) D[pivots of kb, columns of T]),
 // the same terms phase 3 would, with the pivot tiles final after phases 1-2
 // of kb.
-__global__ void __launch_bounds__(FT, 1) fw_cross_kernel(int *D, long long n, int kb, int nb) {
+constexpr int FXT = 1024;  // lookahead update: 32 x 32 threads, 4 x 4 outputs each (no barriers, many warps)
+
+__global__ void __launch_bounds__(FXT, 1) fw_cross_kernel(int *D, long long n, int kb, int nb) {
     extern __shared__ __align__(16) int sm[];
-    int *colsrc = sm, *rowsrc = sm + FB * FB;
+    int *colsrc = sm, *rowsrc = sm + FB * FB, *blk = sm + 2 * FB * FB;
     const bool row = blockIdx.x < (unsigned)nb;
     const int b = row ? blockIdx.x : blockIdx.x - nb;
     const int kn = kb + 1;
@@ -172,27 +199,37 @@ __global__ void __launch_bounds__(FT, 1) fw_cross_kernel(int *D, long long n, in
     const int r0 = row ? kn * FB : b * FB, c0 = row ? b * FB : kn * FB;
     load_tile(colsrc, D, n, r0, o);
     load_tile(rowsrc, D, n, o, c0);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int i0 = ty * 8;
-    int d[8][8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int gi = r0 + i0 + r, gj = c0 + fw_col(tx, c);
-            d[r][c] = (gi < n && gj < n) ? D[(long long)gi * n + gj] : kInfI32;
-        }
+    load_tile(blk, D, n, r0, c0);
     __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i0 = ty * 4, j0 = tx * 4;
+    int d[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int4 v = *reinterpret_cast<const int4 *>(blk + (i0 + r) * FB + j0);
+        d[r][0] = v.x; d[r][1] = v.y; d[r][2] = v.z; d[r][3] = v.w;
+    }
     const int kmax = (int)min((long long)FB, n - o);
-#pragma unroll 2
-    for (int k = 0; k < kmax; ++k) relax8(d, colsrc, rowsrc, i0, tx, k);
+#pragma unroll 4
+    for (int k = 0; k < kmax; ++k) {
+        int a[4];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < 4; ++r) a[r] = colsrc[(i0 + r) * FB + k];
+        const int4 bv = *reinterpret_cast<const int4 *>(rowsrc + k * FB + j0);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int gi = r0 + i0 + r, gj = c0 + fw_col(tx, c);
-            if (gi < n && gj < n) D[(long long)gi * n + gj] = d[r][c];
+        for (int r = 0; r < 4; ++r) {
+            d[r][0] = __viaddmin_s32(a[r], bv.x, d[r][0]);
+            d[r][1] = __viaddmin_s32(a[r], bv.y, d[r][1]);
+            d[r][2] = __viaddmin_s32(a[r], bv.z, d[r][2]);
+            d[r][3] = __viaddmin_s32(a[r], bv.w, d[r][3]);
         }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        *reinterpret_cast<int4 *>(blk + (i0 + r) * FB + j0) = make_int4(d[r][0], d[r][1], d[r][2], d[r][3]);
+    __syncthreads();
+    store_tile(blk, D, n, r0, c0, nullptr);
 }
 
 // Packed phase 3: state[0] = 1 when every finite entry of the pivot row and
@@ -260,9 +297,9 @@ cudaError_t launch_fw_phase12(int *D, long long n, int kb, int *pmax, cudaStream
 cudaError_t launch_fw_cross(int *D, long long n, int kb, cudaStream_t st) {
     const int nb = (int)((n + FB - 1) / FB);
     if (kb + 1 >= nb) return cudaSuccess;
-    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(fw_cross_kernel), 2 * FB * FB * 4);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(fw_cross_kernel), 3 * FB * FB * 4);
     if (e != cudaSuccess) return e;
-    fw_cross_kernel<<<2 * nb, FT, 2 * FB * FB * 4, st>>>(D, n, kb, nb);
+    fw_cross_kernel<<<2 * nb, FXT, 3 * FB * FB * 4, st>>>(D, n, kb, nb);
     note_launch();
     return cudaGetLastError();
 }
