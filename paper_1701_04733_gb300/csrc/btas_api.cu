@@ -490,10 +490,15 @@ btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, i
     if (src < 0 || src >= n) return fail(BTAS_ERR_ARG, "btas_sssp: source out of range");
     if (!W || !dist) return fail(BTAS_ERR_ARG, "btas_sssp: NULL pointer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Relaxations are enqueued in groups of kGroup with one read-back per
+    // group: relaxation t does nothing unless t - 1 changed d (its flag is
+    // the next launch's gate), so the group's tail after the fixpoint costs
+    // only empty launches and copies of an unchanged d.
+    constexpr int kGroup = 8;
     Workspace ws(st);
     const size_t vb = align256((size_t)n * 4);
     BTAS_CUDA(ws.alloc(256 + 2 * vb), "workspace alloc");
-    int *flag = static_cast<int *>(ws.p);
+    int *flag = static_cast<int *>(ws.p);  // [0, kGroup) change flags of a group, [8, 10) scan, [16] the constant 1
     int *d[2] = {reinterpret_cast<int *>(static_cast<char *>(ws.p) + 256),
                  reinterpret_cast<int *>(static_cast<char *>(ws.p) + 256 + vb)};
     {
@@ -505,18 +510,31 @@ btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, i
     }
     // d_0 = e_src; d_{t+1} = d_t (x) W until unchanged (at most n-1 products)
     BTAS_CUDA(launch_fill4(d[0], n, 1, (int)n, static_cast<uint32_t>(kInfI32), st), "init");
+    BTAS_CUDA(launch_fill4(flag + 16, 1, 1, 1, 1u, st), "init");
     const int zero = 0;
     BTAS_CUDA(cudaMemcpyAsync(d[0] + src, &zero, 4, cudaMemcpyHostToDevice, st), "init source");
     int cur = 0, steps = 0;
-    for (int64_t t = 0; t + 1 < n; ++t) {
-        BTAS_CUDA(cudaMemcpyAsync(d[cur ^ 1], d[cur], (size_t)n * 4, cudaMemcpyDeviceToDevice, st), "copy");
-        BTAS_CUDA(cudaMemsetAsync(flag, 0, 4, st), "flag reset");
-        BTAS_CUDA(launch_gemv(kMin, BTAS_I32, 1, (int)n, (int)n, W, n, d[cur], d[cur ^ 1], 1, flag, st), "relax");
-        int changed = 0;
-        BTAS_CUDA(read_back(&changed, flag, 4, st), "flag readback");
-        cur ^= 1;
-        if (!changed) break;
-        ++steps;
+    bool done = false;
+    for (int64_t t0 = 0; t0 + 1 < n && !done; t0 += kGroup) {
+        const int g = (int)std::min<int64_t>(kGroup, n - 1 - t0);
+        BTAS_CUDA(cudaMemsetAsync(flag, 0, kGroup * 4, st), "flag reset");
+        for (int q = 0; q < g; ++q) {
+            // the first relaxation of a group runs: the host saw the last one change d
+            const int *gate = q == 0 ? flag + 16 : flag + q - 1;
+            BTAS_CUDA(cudaMemcpyAsync(d[cur ^ 1], d[cur], (size_t)n * 4, cudaMemcpyDeviceToDevice, st), "copy");
+            BTAS_CUDA(launch_gemv(kMin, BTAS_I32, 1, (int)n, (int)n, W, n, d[cur], d[cur ^ 1], 1, flag + q, st, gate),
+                      "relax");
+            cur ^= 1;
+        }
+        int host[kGroup] = {};
+        BTAS_CUDA(read_back(host, flag, (size_t)g * 4, st), "flag readback");
+        for (int q = 0; q < g; ++q) {
+            if (!host[q]) {
+                done = true;
+                break;
+            }
+            ++steps;
+        }
     }
     BTAS_CUDA(cudaMemcpyAsync(dist, d[cur], (size_t)n * 4, cudaMemcpyDeviceToDevice, st), "copy out");
     if (iterations) *iterations = steps;

@@ -106,7 +106,8 @@ constexpr int kColThreads = 256, kRowChunk = 64;
 // or the accumulate start values.  *changed is set if some y entry changed.
 template <typename T, int SR>
 __global__ void gemv_cols_kernel(int m, int n, const T *__restrict__ A, long long lda, const T *__restrict__ x,
-                                 T *y, int *changed, int vec) {
+                                 T *y, int *changed, const int *skip, int vec) {
+    if (skip != nullptr && __ldcg(skip) == 0) return;  // the previous relaxation changed nothing
     const int j0 = (blockIdx.x * kColThreads + threadIdx.x) * 4;
     const int i0 = blockIdx.y * kRowChunk, i1 = min(m, i0 + kRowChunk);
     if (j0 >= n) return;
@@ -147,7 +148,7 @@ __global__ void fill_kernel(T *y, int n, T v) {
 
 template <typename T, int SR>
 cudaError_t gemv_t(int trans, int m, int n, const void *A, long long lda, const void *x, void *y, int accumulate,
-                   int *changed, cudaStream_t st) {
+                   int *changed, const int *skip, cudaStream_t st) {
     const T *a = static_cast<const T *>(A);
     const T *xx = static_cast<const T *>(x);
     T *yy = static_cast<T *>(y);
@@ -165,7 +166,7 @@ cudaError_t gemv_t(int trans, int m, int n, const void *A, long long lda, const 
         }
         const int vec = (reinterpret_cast<uintptr_t>(a) & 15) == 0 && (lda & 3) == 0;
         dim3 grid((n + 4 * kColThreads - 1) / (4 * kColThreads), (m + kRowChunk - 1) / kRowChunk);
-        gemv_cols_kernel<T, SR><<<grid, kColThreads, 0, st>>>(m, n, a, lda, xx, yy, changed, vec);
+        gemv_cols_kernel<T, SR><<<grid, kColThreads, 0, st>>>(m, n, a, lda, xx, yy, changed, skip, vec);
         note_launch();
     }
     return cudaGetLastError();
@@ -174,12 +175,12 @@ cudaError_t gemv_t(int trans, int m, int n, const void *A, long long lda, const 
 }  // namespace
 
 cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *A, long long lda, const void *x,
-                        void *y, int accumulate, int *changed, cudaStream_t st) {
+                        void *y, int accumulate, int *changed, cudaStream_t st, const int *skip) {
     if (dtype == BTAS_I32)
-        return sr == kMin ? gemv_t<int, kMin>(trans, m, n, A, lda, x, y, accumulate, changed, st)
-                          : gemv_t<int, kMax>(trans, m, n, A, lda, x, y, accumulate, changed, st);
-    return sr == kMin ? gemv_t<float, kMin>(trans, m, n, A, lda, x, y, accumulate, changed, st)
-                      : gemv_t<float, kMax>(trans, m, n, A, lda, x, y, accumulate, changed, st);
+        return sr == kMin ? gemv_t<int, kMin>(trans, m, n, A, lda, x, y, accumulate, changed, skip, st)
+                          : gemv_t<int, kMax>(trans, m, n, A, lda, x, y, accumulate, changed, skip, st);
+    return sr == kMin ? gemv_t<float, kMin>(trans, m, n, A, lda, x, y, accumulate, changed, skip, st)
+                      : gemv_t<float, kMax>(trans, m, n, A, lda, x, y, accumulate, changed, skip, st);
 }
 
 }  // namespace btas

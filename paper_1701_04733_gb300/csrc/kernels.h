@@ -87,9 +87,10 @@ cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *D
 
 // ---- level 2 (gemv.cu): trans 0: y_i = (+)_j A[i][j] (.) x_j; trans 1:
 // y_j = (+)_i x_i (.) A[i][j]; accumulate keeps y as a (+) start value;
-// changed (trans 1, optional) is set when some y entry changes.
+// changed (trans 1, optional) is set when some y entry changes; skip
+// (trans 1 with accumulate, optional): *skip == 0 makes the launch a no-op.
 cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *A, long long lda, const void *x,
-                        void *y, int accumulate, int *changed, cudaStream_t st);
+                        void *y, int accumulate, int *changed, cudaStream_t st, const int *skip = nullptr);
 
 // ---- APSP in one thread block for n <= apsp_small_max_n() (small.cu).
 // info (device, 3 ints): entries outside the domain, largest finite weight,

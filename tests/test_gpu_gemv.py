@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import gen
-from gpu_util import bits, dev, f32_matrix, host, int_matrix
+from gpu_util import INF, bits, dev, f32_matrix, host, int_matrix
 
 pytestmark = pytest.mark.gpu
 
@@ -56,3 +56,21 @@ def test_sssp_matches_dijkstra_and_oracle(btas, oracle_mod, n):
             ref, steps = oracle_mod.sssp(W, src)
             np.testing.assert_array_equal(d, ref)
             assert info["iterations"] == steps
+
+
+@pytest.mark.parametrize("n", [2, 9, 17, 20, 33])
+def test_sssp_long_chains(btas, oracle_mod, n):
+    """A directed path needs n - 1 changing relaxations: several groups of
+    relaxations enqueued between read-backs, the last one partial."""
+    W = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(W, 0)
+    W[np.arange(n - 1), np.arange(1, n)] = 3
+    W[n - 1, 0] = 5  # a back edge closes a cycle and changes nothing from source 0
+    d, info = btas.sssp(dev(W), 0, info=True)
+    ref, steps = oracle_mod.sssp(W, 0)
+    np.testing.assert_array_equal(host(d), ref)
+    assert info["iterations"] == steps
+    d, info = btas.sssp(dev(W), n - 1, info=True)
+    ref, steps = oracle_mod.sssp(W, n - 1)
+    np.testing.assert_array_equal(host(d), ref)
+    assert info["iterations"] == steps
