@@ -237,7 +237,7 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  *   n <= 64         one thread block holds D in shared memory and runs the
  *                   domain check and every squaring (int32): one launch, one
  *                   read-back;
- *   64 < n <= 1024  one cooperative launch runs every squaring as split-k
+ *   64 < n <= 1792  one cooperative launch runs every squaring as split-k
  *                   pieces merged with atomicMin, one grid barrier (bounded
  *                   wait; BTAS_ERR_TIMEOUT if it expires) per squaring; each
  *                   squaring packed 16-bit while every finite entry of its
@@ -245,9 +245,9 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  *                   reports), else int32 (always int32 with FORCE_I32);
  *   larger n        the tiled product kernels, one launch per squaring, with
  *                   the per-squaring exact representation described below.
- * BTAS_APSP_SMALL_MAX_N=m (0 .. 128) in the environment moves the first
- * boundary to m; BTAS_APSP_NO_SMALL=1 / BTAS_APSP_NO_MID=1 send the first two
- * regimes to the tiled path.
+ * BTAS_APSP_SMALL_MAX_N=m (0 .. 128) and BTAS_APSP_MID_MAX_N=m (0 .. 4096) in
+ * the environment move the two boundaries; BTAS_APSP_NO_SMALL=1 /
+ * BTAS_APSP_NO_MID=1 send the first two regimes to the tiled path.
  * ------------------------------------------------------------------------ */
 btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
@@ -522,7 +522,7 @@ btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *coun
  * squaring) in one persistent launch; requests arriving meanwhile join the
  * next step.  A product completes after its step; an APSP solve after its
  * last squaring or as soon as a squaring changed nothing.  An APSP request
- * with n <= 1024 is instead solved whole in one unit, by the one-block or
+ * with n <= 1792 is instead solved whole in one unit, by the one-block or
  * the cooperative kernel of btas_apsp (the same size boundary), launched in the step
  * after the persistent kernel (BTAS_SERVER_NO_WHOLE=1 in the environment at
  * creation turns this off).  Results are bit-identical to btas_gemm /
@@ -533,10 +533,11 @@ btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *coun
  * btas_server_submit_apsp : n x n int32 W (host) -> D (host); *ticket
  *                           receives the request id.  The domain (zero
  *                           diagonal, weights in [0, 2^28] or INF) is
- *                           checked for whole solves (the request then
- *                           ends in state 3, failed) and assumed
- *                           otherwise.  BTAS_ERR_BUDGET if the request alone
- *                           exceeds the budget.
+ *                           checked on the device in the request's first
+ *                           step (whole solve or first squaring); a
+ *                           violation ends the request in state 3, failed,
+ *                           with D not written.  BTAS_ERR_BUDGET if the
+ *                           request alone exceeds the budget.
  * btas_server_submit_gemm : C (m x n) = A (m x k) (x) B (k x n), host,
  *                           int32 or fp32, min-plus or max-plus.
  * btas_server_poll        : state (0 queued, 1 running, 2 done, 3 failed)

@@ -72,14 +72,15 @@ __global__ void fill4_kernel(uint32_t *dst, long long ldd, int rows, int cols, u
     }
 }
 
-// out[0] = max finite weight, out[1] = count of out-of-domain entries.
-__global__ void apsp_scan_kernel(const int *__restrict__ W, long long n, int *out) {
+// out[0] = max finite weight, out[1] = count of out-of-domain entries
+// (W: n x n, row pitch ldw).
+__global__ void apsp_scan_kernel(const int *__restrict__ W, long long ldw, long long n, int *out) {
     const long long total = n * n;
     int mx = 0, bad = 0;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int v = W[idx];
         const long long r = idx / n, c = idx % n;
+        const int v = W[r * ldw + c];
         if (r == c) {
             bad += v != 0;
         } else if (v != kInfI32) {
@@ -163,9 +164,9 @@ cudaError_t launch_ident_oplus(const void *src, long long lds, int n, void *dst,
     return cudaGetLastError();
 }
 
-cudaError_t launch_apsp_scan(const int *W, long long n, int *out, cudaStream_t st) {
+cudaError_t launch_apsp_scan(const int *W, long long n, int *out, cudaStream_t st, long long ldw) {
     if (n <= 0) return cudaSuccess;
-    apsp_scan_kernel<<<grid_for(n * n, 256), 256, 0, st>>>(W, n, out);
+    apsp_scan_kernel<<<grid_for(n * n, 256), 256, 0, st>>>(W, ldw > 0 ? ldw : n, n, out);
     note_launch();
     return cudaGetLastError();
 }

@@ -68,7 +68,7 @@ cudaError_t launch_ident_oplus(const void *src, long long lds, int n, void *dst,
 // APSP domain scan of an n x n int32 matrix: out[0] = max finite weight,
 // out[1] = number of entries out of the domain (negative, > 2^28 and not INF,
 // or a non-zero diagonal).  out must be zeroed first.
-cudaError_t launch_apsp_scan(const int *W, long long n, int *out, cudaStream_t st);
+cudaError_t launch_apsp_scan(const int *W, long long n, int *out, cudaStream_t st, long long ldw = 0);  // ldw 0: n
 
 // ---- APSP with next-hop matrix (paths.cu)
 // Keyed path squaring (paths.cu): while every finite entry of D is <=

@@ -1,10 +1,10 @@
 // APSP by repeated squaring (Sec. III) for mid-size graphs in ONE
 // cooperative launch.
 //
-// Between the one-block kernel (n <= 64) and the tiled product kernels a
-// solve is bound by launches and host round trips: a few dozen tiles per
-// squaring cannot fill the GPU, and every squaring waits for the previous
-// one's change flag.  Here one cooperative grid runs the domain check and all
+// Between the one-block kernel (n <= 64) and the tiled product kernels (n >
+// 1792) a solve is bound by launches and host round trips: a few dozen
+// tiles per squaring cannot fill the GPU, and every squaring waits for the
+// previous one's change flag.  Here one cooperative grid runs the domain check and all
 // squarings, with ONE grid barrier per squaring.
 //
 // Work split.  Squaring s is a space of units (64 x 64 output tile, 32-wide
@@ -387,7 +387,17 @@ __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) 
 
 }  // namespace
 
-int apsp_mid_max_n() { return 1024; }
+int apsp_mid_max_n() {
+    // largest n btas_apsp sends here: above about 1800 vertices the tiled
+    // product kernels have enough tiles to fill the GPU and win (measured:
+    // 937 vs 1290 us at n = 1536, 2134 vs 1666 us at 2048);
+    // BTAS_APSP_MID_MAX_N overrides it (up to 4096)
+    static const int dflt = 1792;
+    const char *e = getenv("BTAS_APSP_MID_MAX_N");
+    if (!e || !*e) return dflt;
+    const int v = atoi(e);
+    return v < 0 ? 0 : v > 4096 ? 4096 : v;
+}
 
 // workspace: three n x ldx matrices, then 512 bytes of barrier words and
 // 256 bytes for the status words of a caller that passes info = null

@@ -13,7 +13,7 @@
 //             2 ms; BTAS_SERVER_STEP_TERMS), and these units run together in
 //             ONE launch of the persistent tile-task kernel
 //             (batch_kernel.cuh); short steps let finished requests leave
-//             and new ones join often.  An APSP request with n <= 1024 is
+//             and new ones join often.  An APSP request with n <= 1792 is
 //             one unit instead: the whole solve, by the one-block or the
 //             cooperative kernel, launched after the persistent kernel;
 //   retire  - a product is finished after its step; an APSP solve after its
@@ -79,7 +79,7 @@ struct Req {
     int steps = 0;
     bool finished = false;
     bool whole = false;  // APSP solved in one unit (small / cooperative kernel) in this step
-    bool bad = false;    // W outside the domain (whole-solve check): the request fails
+    bool bad = false;    // W outside the domain (checked on the device before the first squaring): the request fails
     // terms of this request's next unit of work
     double unit_terms() const { return kind == 0 ? (double)n * n * n : (double)m * n * k; }
 };
@@ -105,7 +105,7 @@ struct btas_server_t {
     void *d_stage[2] = {nullptr, nullptr};
     void *h_stage[2] = {nullptr, nullptr};
     size_t stage_bytes = 0;
-    int *h_flags = nullptr;  // pinned mailbox for change flags
+    int *h_flags = nullptr;  // pinned mailbox: change flags, maxima or barrier status, domain-scan results
     int *d_flag_slots = nullptr;
     int flag_slots = 0;
     cudaEvent_t step_done[2] = {nullptr, nullptr};
@@ -146,7 +146,7 @@ int squarings_of(long long n) {
 size_t footprint(const Req &r) {
     if (r.kind == 0) {
         const long long ld = r4(r.n), ldu = (r.n + 7) & ~7LL;
-        return 6 * a256((size_t)r.n * ld * 4) + 2 * a256((size_t)r.n * ldu * 2) + a256((size_t)(2 * r.S + 4) * 4);
+        return 6 * a256((size_t)r.n * ld * 4) + 2 * a256((size_t)r.n * ldu * 2) + a256((size_t)(2 * r.S + 6) * 4);
     }
     return a256((size_t)r.m * r4(r.k) * 4) + a256((size_t)r.k * r4(r.n) * 4) + a256((size_t)r.n * r4(r.k) * 4) +
            a256((size_t)r.m * r4(r.n) * 4);
@@ -176,9 +176,10 @@ bool admit(btas_server_t *sv, Req *r) {
         const size_t ublk = a256((size_t)r->n * r->ldu * 2);
         r->U[0] = reinterpret_cast<uint16_t *>(p + 6 * blk);
         r->U[1] = reinterpret_cast<uint16_t *>(p + 6 * blk + ublk);
-        // change flags [0, S+2) and largest finite entries [S+2, 2S+4)
+        // change flags [0, S+2), largest finite entries [S+2, 2S+4), the
+        // domain scan of W [2S+4, 2S+6)
         r->dflag = reinterpret_cast<int *>(p + 6 * blk + 2 * ublk);
-        cudaMemsetAsync(r->dflag, 0, (size_t)(2 * r->S + 4) * 4, sv->copy);
+        cudaMemsetAsync(r->dflag, 0, (size_t)(2 * r->S + 6) * 4, sv->copy);
         cudaMemcpy2DAsync(r->P[0], ld * 4, r->hA, (size_t)r->n * 4, (size_t)r->n * 4, r->n, cudaMemcpyHostToDevice,
                           sv->copy);
     } else {
@@ -264,7 +265,13 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
             I.Q1 = s < r->S ? r->Q[s & 1] : nullptr;
             I.ldq = r->ldp;
             I.changed_ptr = r->dflag + s;
-            if (s == 1) I.t0_rows = I.t0_cols = r->n;  // transpose W into Q[0] first
+            if (s == 1) {
+                I.t0_rows = I.t0_cols = r->n;  // transpose W into Q[0] first
+                // the weight domain, checked on the device; a violation fails the request
+                if (launch_apsp_scan(static_cast<const int *>(r->P[0]), r->n, r->dflag + 2 * r->S + 4, sv->compute,
+                                     r->ldp) != cudaSuccess)
+                    return -1;
+            }
             // packed squaring when every finite entry of D_{s-1} is < 0x7FFF / 2
             // (exact); the forms of D_s are written for the next squaring
             I.use_u16 = (s >= 2 && r->last_max >= 0 && 2LL * r->last_max < BTAS_INF_U16 && sv->allow_u16) ? 1 : 0;
@@ -355,6 +362,10 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
     // pinned mailbox
     for (int i = 0; i < ninst; ++i) {
         if (units[i]->kind != 0) continue;
+        sv->h_flags[2 * sv->flag_slots + 1 + i] = 0;
+        if (units[i]->s == 1)
+            cudaMemcpyAsync(sv->h_flags + 2 * sv->flag_slots + 1 + i, units[i]->dflag + 2 * units[i]->S + 5, 4,
+                            cudaMemcpyDeviceToHost, sv->compute);
         cudaMemcpyAsync(sv->h_flags + i, units[i]->dflag + units[i]->s, 4, cudaMemcpyDeviceToHost, sv->compute);
         cudaMemcpyAsync(sv->h_flags + sv->flag_slots + 1 + i, units[i]->dflag + units[i]->S + 2 + units[i]->s, 4,
                         cudaMemcpyDeviceToHost, sv->compute);
@@ -390,7 +401,9 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
 }
 
 void start_retire(btas_server_t *sv, Req *r) {
-    if (r->kind == 0) {
+    if (r->bad) {
+        // failed (W outside the domain): the caller's D is not written
+    } else if (r->kind == 0) {
         cudaMemcpy2DAsync(r->hC, (size_t)r->n * 4, r->P[r->result_buf], r->ldp * 4, (size_t)r->n * 4, r->n,
                           cudaMemcpyDeviceToHost, sv->copy);
     } else {
@@ -482,7 +495,8 @@ void worker_loop(btas_server_t *sv) {
                 const bool changed = sv->h_flags[i] != 0;
                 r->last_max = r->s < r->S ? sv->h_flags[sv->flag_slots + 1 + i] : -1;
                 r->result_buf = r->s & 1;
-                finished = !changed || r->s >= r->S;
+                r->bad = r->s == 1 && sv->h_flags[2 * sv->flag_slots + 1 + i] != 0;
+                finished = r->bad || !changed || r->s >= r->S;
                 ++r->s;
             }
             if (finished) {
@@ -524,7 +538,7 @@ btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, in
     if (const char *e = getenv("BTAS_SERVER_NO_WHOLE")) sv->allow_whole = (*e && atoi(e) != 0) ? 0 : 1;
     sv->timeout_cycles = batch_timeout_cycles(sv->device);
     sv->flag_slots = 1 << 16;
-    if (cudaMallocHost(reinterpret_cast<void **>(&sv->h_flags), (size_t)(2 * sv->flag_slots + 1) * 4) != cudaSuccess) {
+    if (cudaMallocHost(reinterpret_cast<void **>(&sv->h_flags), (size_t)(3 * sv->flag_slots + 1) * 4) != cudaSuccess) {
         delete sv;
         return sfail(BTAS_ERR_NOMEM, "btas_server_create: pinned mailbox");
     }

@@ -289,3 +289,17 @@ def test_mid_graph_cooperative_path(btas, oracle_mod, n, cooperative_from_3):
     with pytest.raises(btas.BtasError):
         btas.apsp(dev(bad), out=out)
     assert (host(out) == 77).all()
+
+
+def test_cooperative_path_above_1024(btas, oracle_mod):
+    """The cooperative kernel serves btas_apsp up to n = 1792 by default; at
+    n = 1536 it equals the oracle and counts the tiled path's squarings."""
+    n = 1536
+    W = gen.random_graph(gen.BASE_SEED, 950, n, 0.02, 1, 100)
+    ref = oracle_mod.floyd_warshall(W)
+    D, info = btas.apsp(dev(W), info=True)
+    with env(BTAS_APSP_NO_MID="1"):
+        _, info2 = btas.apsp(dev(W), flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32, info=True)
+    np.testing.assert_array_equal(host(D), ref)
+    assert info["path"] == "u16x2"
+    assert info["squarings"] == info2["squarings"]

@@ -25,7 +25,7 @@ torch.cuda.synchronize()
 """
 
 
-@pytest.mark.parametrize("n,regime", [(48, "one-block kernel"), (300, "cooperative kernel"), (1500, "tiled kernels")])
+@pytest.mark.parametrize("n,regime", [(48, "one-block kernel"), (300, "cooperative kernel"), (2000, "tiled kernels")])
 def test_log_reports_regime_and_kernel_choice(n, regime):
     env = dict(os.environ, BTAS_LOG="1")
     r = subprocess.run([sys.executable, "-c", SCRIPT.format(root=ROOT, n=n)], env=env, capture_output=True,

@@ -117,22 +117,47 @@ def test_small_budget_queues_and_rejects(btas):
 
 
 def test_whole_solve_domain_violation_fails_alone(btas, oracle_mod):
-    """A whole-solve APSP request whose W is outside the domain (a negative
-    weight) ends in the failed state; the requests around it are unaffected.
-    A graph above the whole-solve limit runs squaring by squaring."""
+    """An APSP request whose W is outside the domain (a negative weight) ends
+    in the failed state; the requests around it are unaffected.  The graph
+    above the whole-solve limit runs squaring by squaring, and while it is
+    pending the others do too, so the bad request is caught by the domain
+    scan of its first squaring step (test_whole_solve_domain_check_alone
+    covers the whole-solve check)."""
     import torch
     good = gen.random_graph(31, 1, 300, 0.05, 1, 100)
     bad = good.copy()
     bad[4, 9] = -2
-    large = gen.random_graph(32, 1, 1100, 0.01, 1, 100)
+    large = gen.random_graph(32, 1, 1900, 0.01, 1, 100)
     bufs = [(torch.from_numpy(w).pin_memory(), torch.zeros(w.shape, dtype=torch.int32).pin_memory())
             for w in (good, bad, large, good[:100, :100].copy())]
+    bufs[1][1].fill_(77)
     srv = btas.Server(8 << 30)
     tickets = [srv.submit_apsp(W, D) for W, D in bufs]
     srv.wait_all(120)
     states = [srv.poll(t)["state"] for t in tickets]
     srv.close()
     assert states == [2, 3, 2, 2]
+    assert (bufs[1][1].numpy() == 77).all()  # a failed request leaves D alone
     np.testing.assert_array_equal(bufs[0][1].numpy(), oracle_mod.floyd_warshall(good))
     np.testing.assert_array_equal(bufs[2][1].numpy(), host(btas.apsp(dev(large))))
     np.testing.assert_array_equal(bufs[3][1].numpy(), oracle_mod.floyd_warshall(good[:100, :100].copy()))
+
+
+def test_whole_solve_domain_check_alone(btas, oracle_mod):
+    """With no other pending work the bad request is solved whole, and the
+    whole-solve kernel's own domain check fails it."""
+    import torch
+    good = gen.random_graph(33, 1, 300, 0.05, 1, 100)
+    bad = good.copy()
+    bad[7, 2] = -5
+    bufs = [(torch.from_numpy(w).pin_memory(), torch.zeros(w.shape, dtype=torch.int32).pin_memory())
+            for w in (bad, good)]
+    bufs[0][1].fill_(77)
+    srv = btas.Server(8 << 30)
+    tickets = [srv.submit_apsp(W, D) for W, D in bufs]
+    srv.wait_all(120)
+    states = [srv.poll(t)["state"] for t in tickets]
+    srv.close()
+    assert states == [3, 2]
+    assert (bufs[0][1].numpy() == 77).all()  # a failed request leaves D alone
+    np.testing.assert_array_equal(bufs[1][1].numpy(), oracle_mod.floyd_warshall(good))
