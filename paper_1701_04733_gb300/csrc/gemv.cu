@@ -7,9 +7,12 @@
 //               row chunks spread over the grid, partial results combined
 //               with atomic min/max (order-independent, so exact)
 // Both stream A once: HBM-bound (4 bytes of A per term).
+#include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "common.cuh"
+#include "grid_sync.cuh"
 #include "kernels.h"
 
 namespace btas {
@@ -172,6 +175,110 @@ cudaError_t gemv_t(int trans, int m, int n, const void *A, long long lda, const 
     return cudaGetLastError();
 }
 
+// ---- Bellman-Ford SSSP (repeated vector-matrix products) in ONE
+// cooperative launch.  d_0 = e_src; d_{t+1}[j] = min_i d_t[i] + W[i][j] until
+// d stops changing (at most n - 1 products), with one grid barrier per
+// product instead of a launch, a copy and a host read-back.
+//
+// A product is split into items of 64 rows x 1024 columns (256 threads, 4
+// columns each); an item's partial minimum p over its rows is merged into
+// d_{t+1} (reset to INF beforehand) with atomicMin.  W has a zero diagonal,
+// so d_{t+1} <= d_t entrywise and the item holding row i = j has
+// p <= d_t[j]: an item merges p only where p < d_t[j] (a change) or p equals
+// it and it holds row j -- the same comparison is the change test.  Three
+// rotating buffers: product t reads d_t, merges into d_{t+1} and resets
+// d_{t+2}'s buffer.
+constexpr int kSsspRows = 64, kSsspCols = 1024;
+
+struct SsspArgs {
+    const int *W;
+    long long ldw;
+    int n;
+    int src;
+    int vec;                  // W rows 16-byte aligned (int4 loads)
+    int *buf0, *buf1, *buf2;  // n ints each
+    int *dist;
+    GridSync sync;            // status: info[1]
+    int *info;                // [0] products that changed d, [1] status
+};
+
+__device__ __forceinline__ int *sssp_buf(const SsspArgs &a, int i) { return i == 0 ? a.buf0 : i == 1 ? a.buf1 : a.buf2; }
+
+__global__ void __launch_bounds__(kColThreads) sssp_coop_kernel(const SsspArgs a) {
+    const int n = a.n, tid = threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * blockDim.x;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+    unsigned gen = 0;
+    for (long long j = gtid; j < n; j += gthreads) {
+        a.buf0[j] = j == a.src ? 0 : kInfI32;
+        a.buf1[j] = kInfI32;
+    }
+    int v0 = 0, v1 = 0;
+    if (!grid_barrier(a.sync, gen, false, nullptr, v0, v1)) return;
+    const int cchunks = (n + kSsspCols - 1) / kSsspCols, rchunks = (n + kSsspRows - 1) / kSsspRows;
+    const long long items = (long long)cchunks * rchunks;
+    const long long it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
+    int cur = 0, done = 0;
+    const int *in = a.buf0;
+    for (int t = 0; t + 1 < n; ++t) {
+        int *out = sssp_buf(a, (cur + 1) % 3);
+        int *nxt = sssp_buf(a, (cur + 2) % 3);
+        for (long long j = gtid; j < n; j += gthreads) nxt[j] = kInfI32;
+        bool ch = false;
+        __shared__ int s_x[kSsspRows];  // d_t over the item's rows
+        for (long long it = it0; it < it1; ++it) {
+            const int i0 = (int)(it / cchunks) * kSsspRows, i1 = min(n, i0 + kSsspRows);
+            const int j0 = (int)(it % cchunks) * kSsspCols + tid * 4;
+            __syncthreads();  // the previous item's reads of s_x are done
+            if (tid < kSsspRows) s_x[tid] = i0 + tid < n ? __ldcg(in + i0 + tid) : kInfI32;
+            __syncthreads();
+            if (j0 >= n) continue;
+            int4 acc = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+            if (a.vec && j0 + 4 <= n) {
+#pragma unroll 8
+                for (int i = i0; i < i1; ++i) {
+                    const int xi = s_x[i - i0];
+                    const int4 w = __ldg(reinterpret_cast<const int4 *>(a.W + (long long)i * a.ldw + j0));
+                    acc.x = __viaddmin_s32(xi, w.x, acc.x);
+                    acc.y = __viaddmin_s32(xi, w.y, acc.y);
+                    acc.z = __viaddmin_s32(xi, w.z, acc.z);
+                    acc.w = __viaddmin_s32(xi, w.w, acc.w);
+                }
+            } else {
+                for (int i = i0; i < i1; ++i) {
+                    const int xi = s_x[i - i0];
+                    const int *row = a.W + (long long)i * a.ldw + j0;
+                    // columns past n read as INF
+                    acc.x = __viaddmin_s32(xi, row[0], acc.x);
+                    acc.y = __viaddmin_s32(xi, j0 + 1 < n ? row[1] : kInfI32, acc.y);
+                    acc.z = __viaddmin_s32(xi, j0 + 2 < n ? row[2] : kInfI32, acc.z);
+                    acc.w = __viaddmin_s32(xi, j0 + 3 < n ? row[3] : kInfI32, acc.w);
+                }
+            }
+            const int accv[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + c;
+                if (j >= n) continue;
+                const int p = clamp_i32<kMin>(accv[c]);
+                const int o = __ldcg(in + j);
+                if (p < kInfI32 && (p < o || (p == o && j >= i0 && j < i1))) {
+                    atomicMin(out + j, p);
+                    ch |= p < o;
+                }
+            }
+        }
+        int changed = 0;
+        if (!grid_barrier(a.sync, gen, ch, nullptr, changed, v1)) return;
+        in = out;
+        cur = (cur + 1) % 3;
+        if (!changed) break;
+        ++done;
+    }
+    for (long long j = gtid; j < n; j += gthreads) a.dist[j] = __ldcg(in + j);
+    if (blockIdx.x == 0 && tid == 0) a.info[0] = done;
+}
+
 }  // namespace
 
 cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *A, long long lda, const void *x,
@@ -181,6 +288,53 @@ cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *
                           : gemv_t<int, kMax>(trans, m, n, A, lda, x, y, accumulate, changed, skip, st);
     return sr == kMin ? gemv_t<float, kMin>(trans, m, n, A, lda, x, y, accumulate, changed, skip, st)
                       : gemv_t<float, kMax>(trans, m, n, A, lda, x, y, accumulate, changed, skip, st);
+}
+
+size_t sssp_coop_workspace(long long n) { return 3 * (((size_t)n * 4 + 255) & ~size_t(255)) + 512; }
+
+cudaError_t launch_sssp_coop(const int *W, long long n, int src, int *dist, void *ws, int *info, cudaStream_t st) {
+    DeviceInfo di{};
+    int dev = 0;
+    if (!current_device_info(&di, &dev)) return cudaErrorInvalidDevice;
+    static std::mutex mu;
+    static int cached[64];
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 64 && cached[dev] > 0) {
+            per_sm = cached[dev];
+        } else {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sssp_coop_kernel, kColThreads, 0);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) cached[dev] = per_sm;
+        }
+    }
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const size_t vb = ((size_t)n * 4 + 255) & ~size_t(255);
+    char *base = static_cast<char *>(ws);
+    SsspArgs a{};
+    a.W = W;
+    a.ldw = n;
+    a.n = (int)n;
+    a.src = src;
+    a.vec = ((reinterpret_cast<uintptr_t>(W) & 15) == 0) && (n & 3) == 0;
+    a.buf0 = reinterpret_cast<int *>(base);
+    a.buf1 = reinterpret_cast<int *>(base + vb);
+    a.buf2 = reinterpret_cast<int *>(base + 2 * vb);
+    a.dist = dist;
+    a.info = info;
+    a.sync.bar = reinterpret_cast<unsigned *>(base + 3 * vb);
+    a.sync.status = info + 1;
+    a.sync.timeout_cycles = (long long)(2.0 * (di.clock_khz > 0 ? di.clock_khz : 2000000) * 1e3);  // about 2 s
+    cudaError_t e = cudaMemsetAsync(base + 3 * vb, 0, 256, st);
+    if (e != cudaSuccess) return e;
+    const long long items = ((n + kSsspCols - 1) / kSsspCols) * ((n + kSsspRows - 1) / kSsspRows);
+    const int grid = (int)std::max(1LL, std::min(items, (long long)per_sm * di.sms));
+    void *args[] = {&a};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(sssp_coop_kernel), dim3(grid), dim3(kColThreads),
+                                    args, 0, st);
+    note_launch();
+    return e;
 }
 
 }  // namespace btas

@@ -92,6 +92,13 @@ cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *D
 cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *A, long long lda, const void *x,
                         void *y, int accumulate, int *changed, cudaStream_t st, const int *skip = nullptr);
 
+// ---- Bellman-Ford SSSP in one cooperative launch (gemv.cu): W n x n
+// (pitch n, zero diagonal, domain checked by the caller), dist (n ints,
+// device); ws: sssp_coop_workspace(n) bytes; info (device, 2 ints, zeroed by
+// the caller): [0] products that changed d, [1] status (BTAS_ERR_TIMEOUT).
+size_t sssp_coop_workspace(long long n);
+cudaError_t launch_sssp_coop(const int *W, long long n, int src, int *dist, void *ws, int *info, cudaStream_t st);
+
 // ---- APSP in one thread block for n <= apsp_small_max_n() (small.cu).
 // info (device, 3 ints): entries outside the domain, largest finite weight,
 // squarings that changed D.  Nothing is written to D if the domain check

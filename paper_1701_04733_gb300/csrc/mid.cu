@@ -44,6 +44,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "grid_sync.cuh"
 #include "kernels.h"
 
 namespace btas {
@@ -64,7 +65,7 @@ struct MidArgs {
     long long ldd;
     int *buf0, *buf1, *buf2;  // n x ldx each; columns n .. ldx-1 always hold INF
     long long ldx;            // round4(n): 16-byte rows for vector staging
-    unsigned *bar;  // [2g, 2g + 1] barrier g's counter, [32, 33] release word, [64 + s] largest merged value
+    unsigned *bar;  // [0, 16) barrier counters, [32, 33] release word (grid_sync.cuh), [64 + s] largest merged value
     int *info;      // [0] bad entries, [1] max weight, [2] squarings that changed, [3] status,
                     // [4] representations used (1 int32, 4 packed 16-bit)
     long long timeout_cycles;
@@ -75,77 +76,9 @@ struct MidSmem {
     int b[2][kKc][kT];    // B stage: b[k][col]; packed mode: b[k][pair] in the first kT / 2 words
 };
 
-__device__ __forceinline__ int ld_acquire_i32(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ int ld_relaxed_i32(const int *p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-constexpr int kMaxBarriers = 16;  // phase 0 + at most 15 squarings (n <= 2^15)
-
-// Bounded grid barrier that also ORs a per-block flag over the grid and
-// reads one word (*pval, in [0, 2^30)) once all blocks have arrived.  Barrier
-// g has its own 64-bit counter bar[2g .. 2g+1]: each block adds 1 (arrival)
-// plus 2^32 if its flag is set, so the last block to arrive learns the
-// grid's flag from the value its add returns.  It then reads *pval and
-// publishes barrier number, flag and value in one 64-bit word on a line of
-// its own (bar[32 .. 33]); the other blocks poll that word, so one load gives
-// them the release and both results.  Returns false if the status word is
-// set (timeout here or elsewhere): the caller returns.
-__device__ bool grid_barrier(const MidArgs &a, unsigned &gen, bool flag, const int *pval, int &v0, int &v1) {
-    __shared__ int s_ok, s_v0, s_v1;
-    const int any = __syncthreads_or(flag ? 1 : 0);
-    ++gen;
-    if (threadIdx.x == 0) {
-        unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.bar) + (gen - 1);
-        unsigned long long *pub = reinterpret_cast<unsigned long long *>(a.bar + 32);
-        unsigned long long word = 0;
-        __threadfence();
-        const unsigned long long prev = atomicAdd(ctr, 1ull | ((unsigned long long)(any != 0) << 32));
-        if ((unsigned)prev == gridDim.x - 1) {
-            __threadfence();
-            const unsigned f = ((prev >> 32) != 0 || any != 0) ? 1u : 0u;
-            const unsigned v = pval ? (unsigned)ld_relaxed_i32(pval) & 0x3FFFFFFFu : 0u;
-            word = (unsigned long long)gen | ((unsigned long long)f << 32) | ((unsigned long long)v << 33);
-            st_release_u64(pub, word);
-        } else {
-            const long long t0 = clock64();
-            for (unsigned it = 1;; ++it) {
-                word = ld_acquire_u64(pub);
-                if ((unsigned)word == gen) break;
-                // another block gave up (status set) or this wait expires
-                if ((it & 15) == 0 && ld_acquire_i32(a.info + 3) != 0) break;
-                if (clock64() - t0 > a.timeout_cycles) {
-                    atomicCAS(a.info + 3, 0, BTAS_ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        s_ok = (unsigned)word == gen;
-        s_v0 = (int)((word >> 32) & 1u);
-        s_v1 = (int)(word >> 33);
-    }
-    __syncthreads();
-    v0 = s_v0;
-    v1 = s_v1;
-    return s_ok != 0;
+__device__ __forceinline__ bool grid_barrier(const MidArgs &a, unsigned &gen, bool flag, const int *pval, int &v0,
+                                             int &v1) {
+    return btas::grid_barrier(GridSync{a.bar, a.info + 3, a.timeout_cycles}, gen, flag, pval, v0, v1);
 }
 
 __device__ __forceinline__ int *bufp(const MidArgs &a, int i) { return i == 0 ? a.buf0 : i == 1 ? a.buf1 : a.buf2; }
@@ -432,7 +365,7 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
         }
     }
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    if (S + 1 > kMaxBarriers) return cudaErrorInvalidValue;
+    if (S > 63) return cudaErrorInvalidValue;  // per-squaring maxima at bar[64 + s]
     const int sms = di.sms, clk_khz = di.clock_khz;
     const long long tiles = (n + kT - 1) / kT, KS = (n + kKc - 1) / kKc;
     const long long units = tiles * tiles * KS;

@@ -44,8 +44,22 @@ def test_gemv_strided_and_unaligned(btas, oracle_mod):
     np.testing.assert_array_equal(host(btas.gemv(Abig[:, :91], dev(x), 0)), ref)
 
 
-@pytest.mark.parametrize("n", [1, 2, 50, 777, 4096])
-def test_sssp_matches_dijkstra_and_oracle(btas, oracle_mod, n):
+@pytest.fixture(params=["coop", "grouped"])
+def sssp_mode(request):
+    """coop: all relaxations in one cooperative launch (the default);
+    grouped: BTAS_SSSP_NO_COOP=1, one launch per relaxation in gated groups."""
+    import os
+    old = os.environ.get("BTAS_SSSP_NO_COOP")
+    os.environ["BTAS_SSSP_NO_COOP"] = "1" if request.param == "grouped" else "0"
+    yield request.param
+    if old is None:
+        del os.environ["BTAS_SSSP_NO_COOP"]
+    else:
+        os.environ["BTAS_SSSP_NO_COOP"] = old
+
+
+@pytest.mark.parametrize("n", [1, 2, 50, 777, 1027, 4096])
+def test_sssp_matches_dijkstra_and_oracle(btas, oracle_mod, n, sssp_mode):
     W = gen.random_graph(gen.BASE_SEED, 90 + n % 7, n, 0.01 if n > 1000 else 0.1, 1, 1000)
     Wd = dev(W)
     for src in sorted({0, n // 3, n - 1}):
@@ -59,9 +73,10 @@ def test_sssp_matches_dijkstra_and_oracle(btas, oracle_mod, n):
 
 
 @pytest.mark.parametrize("n", [2, 9, 17, 20, 33])
-def test_sssp_long_chains(btas, oracle_mod, n):
-    """A directed path needs n - 1 changing relaxations: several groups of
-    relaxations enqueued between read-backs, the last one partial."""
+def test_sssp_long_chains(btas, oracle_mod, n, sssp_mode):
+    """A directed path needs n - 1 changing relaxations: as many grid
+    barriers in the cooperative kernel; several groups of relaxations
+    enqueued between read-backs, the last one partial, in the grouped mode."""
     W = np.full((n, n), INF, np.int32)
     np.fill_diagonal(W, 0)
     W[np.arange(n - 1), np.arange(1, n)] = 3
