@@ -501,26 +501,21 @@ btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, i
     int *flag = static_cast<int *>(ws.p);  // [0, kGroup) change flags of a group, [8, 10) scan, [16] the constant 1
     int *d[2] = {reinterpret_cast<int *>(static_cast<char *>(ws.p) + 256),
                  reinterpret_cast<int *>(static_cast<char *>(ws.p) + 256 + vb)};
-    {
-        int host[2] = {0, 0};
-        BTAS_CUDA(cudaMemsetAsync(flag, 0, 256, st), "memset");
-        BTAS_CUDA(launch_apsp_scan(W, n, flag + 8, st), "domain scan");
-        BTAS_CUDA(read_back(host, flag + 8, 8, st), "scan readback");
-        if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_sssp: %d entries outside the domain", host[1]);
-    }
     // d_0 = e_src; d_{t+1} = d_t (x) W until unchanged (at most n-1 products):
-    // in one cooperative launch (one grid barrier per product), else
+    // in one cooperative launch (one grid barrier per product; the first
+    // product checks the domain on its way through W), else
     // (BTAS_SSSP_NO_COOP=1, or no cooperative launch on this device) below
-    if (n <= INT32_MAX / 4 && env_int("BTAS_SSSP_NO_COOP", 0) == 0) {
+    if (n > 1 && n <= INT32_MAX / 4 && env_int("BTAS_SSSP_NO_COOP", 0) == 0) {
         Workspace cw(st);
         BTAS_CUDA(cw.alloc(sssp_coop_workspace(n) + 256), "workspace alloc");
         int *info = reinterpret_cast<int *>(static_cast<char *>(cw.p) + sssp_coop_workspace(n));
-        BTAS_CUDA(cudaMemsetAsync(info, 0, 8, st), "memset");
+        BTAS_CUDA(cudaMemsetAsync(info, 0, 16, st), "memset");
         const cudaError_t le = launch_sssp_coop(W, n, (int)src, dist, cw.p, info, st);
         if (le == cudaSuccess) {
-            int host[2] = {0, 0};
-            BTAS_CUDA(read_back(host, info, 8, st), "info readback");
+            int host[4] = {0, 0, 0, 0};
+            BTAS_CUDA(read_back(host, info, 16, st), "info readback");
             if (host[1] != 0) return fail(BTAS_ERR_TIMEOUT, "btas_sssp: a bounded grid barrier wait expired");
+            if (host[2] != 0) return fail(BTAS_ERR_ARG, "btas_sssp: %d entries outside the domain", host[2]);
             if (iterations) *iterations = host[0];
             log_event("sssp n=%lld: cooperative kernel, %d changing products", (long long)n, host[0]);
             return BTAS_OK;
@@ -528,6 +523,13 @@ btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, i
         if (le != cudaErrorCooperativeLaunchTooLarge && le != cudaErrorNotSupported)
             return fail(BTAS_ERR_CUDA, "btas_sssp: %s", cudaGetErrorString(le));
         cudaGetLastError();
+    }
+    {
+        int host[2] = {0, 0};
+        BTAS_CUDA(cudaMemsetAsync(flag, 0, 256, st), "memset");
+        BTAS_CUDA(launch_apsp_scan(W, n, flag + 8, st), "domain scan");
+        BTAS_CUDA(read_back(host, flag + 8, 8, st), "scan readback");
+        if (host[1] != 0) return fail(BTAS_ERR_ARG, "btas_sssp: %d entries outside the domain", host[1]);
     }
     BTAS_CUDA(launch_fill4(d[0], n, 1, (int)n, static_cast<uint32_t>(kInfI32), st), "init");
     BTAS_CUDA(launch_fill4(flag + 16, 1, 1, 1, 1u, st), "init");

@@ -199,7 +199,7 @@ struct SsspArgs {
     int *buf0, *buf1, *buf2;  // n ints each
     int *dist;
     GridSync sync;            // status: info[1]
-    int *info;                // [0] products that changed d, [1] status
+    int *info;                // [0] products that changed d, [1] status, [2] entries of W outside the domain, [3] any
 };
 
 __device__ __forceinline__ int *sssp_buf(const SsspArgs &a, int i) { return i == 0 ? a.buf0 : i == 1 ? a.buf1 : a.buf2; }
@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(kColThreads) sssp_coop_kernel(const SsspArgs a
         int *nxt = sssp_buf(a, (cur + 2) % 3);
         for (long long j = gtid; j < n; j += gthreads) nxt[j] = kInfI32;
         bool ch = false;
+        int bad = 0;
         __shared__ int s_x[kSsspRows];  // d_t over the item's rows
         for (long long it = it0; it < it1; ++it) {
             const int i0 = (int)(it / cchunks) * kSsspRows, i1 = min(n, i0 + kSsspRows);
@@ -234,7 +235,25 @@ __global__ void __launch_bounds__(kColThreads) sssp_coop_kernel(const SsspArgs a
             __syncthreads();
             if (j0 >= n) continue;
             int4 acc = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
-            if (a.vec && j0 + 4 <= n) {
+            if (t == 0) {
+                // the first product reads every entry of W: check the domain
+                // (zero diagonal, weights in [0, 2^28] or INF) on the way
+                for (int i = i0; i < i1; ++i) {
+                    const int xi = s_x[i - i0];
+                    const int *row = a.W + (long long)i * a.ldw + j0;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (j0 + c >= n) break;
+                        const int v = row[c];
+                        const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
+                        bad += ((!fin && v != kInfI32) || (i == j0 + c && v != 0)) ? 1 : 0;
+                        if (c == 0) acc.x = __viaddmin_s32(xi, v, acc.x);
+                        if (c == 1) acc.y = __viaddmin_s32(xi, v, acc.y);
+                        if (c == 2) acc.z = __viaddmin_s32(xi, v, acc.z);
+                        if (c == 3) acc.w = __viaddmin_s32(xi, v, acc.w);
+                    }
+                }
+            } else if (a.vec && j0 + 4 <= n) {
 #pragma unroll 8
                 for (int i = i0; i < i1; ++i) {
                     const int xi = s_x[i - i0];
@@ -269,7 +288,16 @@ __global__ void __launch_bounds__(kColThreads) sssp_coop_kernel(const SsspArgs a
             }
         }
         int changed = 0;
-        if (!grid_barrier(a.sync, gen, ch, nullptr, changed, v1)) return;
+        if (t == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+            if ((tid & 31) == 0 && bad) {
+                atomicAdd(a.info + 2, bad);
+                atomicExch(a.info + 3, 1);
+            }
+        }
+        if (!grid_barrier(a.sync, gen, ch, t == 0 ? a.info + 3 : nullptr, changed, v1)) return;
+        if (t == 0 && v1 != 0) return;  // W outside the domain: dist untouched
         in = out;
         cur = (cur + 1) % 3;
         if (!changed) break;

@@ -93,9 +93,10 @@ cudaError_t launch_gemv(int sr, int dtype, int trans, int m, int n, const void *
                         void *y, int accumulate, int *changed, cudaStream_t st, const int *skip = nullptr);
 
 // ---- Bellman-Ford SSSP in one cooperative launch (gemv.cu): W n x n
-// (pitch n, zero diagonal, domain checked by the caller), dist (n ints,
-// device); ws: sssp_coop_workspace(n) bytes; info (device, 2 ints, zeroed by
-// the caller): [0] products that changed d, [1] status (BTAS_ERR_TIMEOUT).
+// (pitch n), dist (n ints, device); ws: sssp_coop_workspace(n) bytes; info
+// (device, 4 ints, zeroed by the caller): [0] products that changed d, [1]
+// status (BTAS_ERR_TIMEOUT), [2] entries of W outside the domain (checked
+// during the first product; dist is then not written), [3] scratch.
 size_t sssp_coop_workspace(long long n);
 cudaError_t launch_sssp_coop(const int *W, long long n, int src, int *dist, void *ws, int *info, cudaStream_t st);
 

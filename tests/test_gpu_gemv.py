@@ -89,3 +89,25 @@ def test_sssp_long_chains(btas, oracle_mod, n, sssp_mode):
     ref, steps = oracle_mod.sssp(W, n - 1)
     np.testing.assert_array_equal(host(d), ref)
     assert info["iterations"] == steps
+
+
+@pytest.mark.parametrize("where", ["weight", "diagonal"])
+def test_sssp_domain_violation(btas, sssp_mode, where):
+    """A negative weight or a non-zero diagonal entry is reported
+    (BTAS_ERR_ARG) and dist is left as it was; the cooperative kernel finds it
+    during its first product."""
+    import torch
+    n = 300
+    W = gen.random_graph(gen.BASE_SEED, 97, n, 0.05, 1, 100)
+    if where == "weight":
+        W[17, 250] = -4
+    else:
+        W[123, 123] = 9
+    Wd = dev(W)
+    dist = torch.full((n,), 55, dtype=torch.int32, device="cuda")
+    it = __import__("ctypes").c_int(0)
+    st = torch.cuda.current_stream().cuda_stream
+    rc = btas.lib().btas_sssp(n, Wd.data_ptr(), 0, dist.data_ptr(), __import__("ctypes").addressof(it), st)
+    torch.cuda.synchronize()
+    assert rc == 1 and "outside the domain" in btas.last_error()
+    assert (host(dist) == 55).all()
