@@ -185,9 +185,14 @@ btas_status btas_gemv(int semiring, int dtype, int trans, int64_t m, int64_t n, 
  * vector-matrix products d_{t+1} = d_t (x) W (Bellman-Ford; W[j][j] = 0
  * keeps d_t[j]) until d stops changing, at most n-1 products.  W: n x n int32
  * device matrix (domain as btas_apsp, checked); dist: n int32 device vector
- * (INF = unreachable) = row `src` of btas_apsp's result.  iterations: HOST
- * pointer or NULL, receives the number of products that changed d.
- * Synchronises `stream` once per product. */
+ * (INF = unreachable) = row `src` of btas_apsp's result; not written if the
+ * domain check fails (BTAS_ERR_ARG).  iterations: HOST pointer or NULL,
+ * receives the number of products that changed d.  All products run in one
+ * cooperative launch with one bounded grid barrier each (BTAS_ERR_TIMEOUT if
+ * a wait expires; the first product also checks the domain), and the call
+ * synchronises `stream` once.  Where a cooperative launch is refused (or
+ * with BTAS_SSSP_NO_COOP=1 in the environment) it launches the products in
+ * gated groups of 8 and synchronises once per group. */
 btas_status btas_sssp(int64_t n, const int32_t *W, int64_t src, int32_t *dist, int *iterations, void *stream);
 
 /* ------------------------------------------------------------------------
