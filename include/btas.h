@@ -334,7 +334,11 @@ btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void
  * overlap D or Next).  Domain as btas_apsp (checked: BTAS_ERR_ARG).
  * flags: BTAS_APSP_EARLY_EXIT stops once a squaring changes neither D nor
  * Next (same result).  squarings_done: HOST pointer or NULL.  The call
- * synchronises `stream` once per squaring.  int32 kernels only. */
+ * synchronises `stream` once per squaring.  int32 only: while every
+ * distance is <= 49151 and n <= 8192 a squaring is one int32 min-plus
+ * product of the keys (D << 13) | k (minimum key = minimum distance with
+ * the smallest k), else an argmin kernel; BTAS_PATHS_NO_KEYED=1 forces the
+ * latter. */
 btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Next, int flags, int *squarings_done,
                             void *stream);
 
@@ -345,7 +349,12 @@ btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Ne
  * block's pivots (the semiring GEMM kernel).  n^3 terms instead of
  * ceil(log2(n-1)) * n^3; int32 results identical to btas_apsp.  W, D as
  * btas_apsp (D == W allowed, any other overlap not); domain checked
- * (synchronises `stream` once). */
+ * (synchronises `stream` once).  With three or more pivot blocks, phases
+ * 1-2 of the next block run on an internal stream of higher priority,
+ * forked from and joined back to `stream` with events, so the call's work
+ * is still ordered after earlier work on `stream` and before later work
+ * (stream capture included); BTAS_FW_NO_LOOKAHEAD=1 keeps everything on
+ * `stream`. */
 btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
 /* Number of squarings btas_apsp performs for n vertices: ceil(log2(n-1)). */
