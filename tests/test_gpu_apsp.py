@@ -303,3 +303,22 @@ def test_cooperative_path_above_1024(btas, oracle_mod):
     np.testing.assert_array_equal(host(D), ref)
     assert info["path"] == "u16x2"
     assert info["squarings"] == info2["squarings"]
+
+
+def test_cooperative_barrier_timeout_is_reported(btas, oracle_mod):
+    """Failure detection without a fault: with BTAS_MID_WITHHOLD=1 one block of
+    the cooperative kernel never arrives at its first grid barrier, the
+    others' bounded waits expire (about 2 s), and the call returns
+    BTAS_ERR_TIMEOUT with D untouched; the next call on the same context
+    succeeds."""
+    import torch
+    n = 300
+    W = gen.random_graph(gen.BASE_SEED, 960, n, 0.05, 1, 100)
+    out = dev(np.full((n, n), 41, np.int32))
+    with env(BTAS_MID_WITHHOLD="1"):
+        with pytest.raises(btas.BtasError) as ei:
+            btas.apsp(dev(W), out=out)
+    assert ei.value.status == 5
+    assert (host(out) == 41).all()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(btas.apsp(dev(W))), oracle_mod.floyd_warshall(W))
