@@ -60,6 +60,9 @@ def parse():
                    help="skip the small-config timings (n = 256 solve, n = 4096 packed vs int32, Table II sizes)")
     p.add_argument("--no-tune", action="store_true",
                    help="skip the autotuner (kernels then come from the built-in defaults)")
+    p.add_argument("--probe-mix", type=int, default=None,
+                   help="with --only probe: run this one mix (btas_measure_issue_rate_ex) and nothing else")
+    p.add_argument("--probe-ctas", type=int, default=1, help="with --probe-mix: CTAs per SM (1 or 2)")
     p.add_argument("--serve-requests", type=int, default=300)
     p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
     p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next", "tune", "configs", "probe"],
@@ -216,18 +219,26 @@ def oracle_fw_n256_us():
 
 
 PROBE_MIXES = ((0, "int32_dpx"), (4, "int32_iadd_min3"), (5, "int32_imad_min3"), (6, "int32_split_imad5_dpx3"),
-               (1, "fp32_f32x2_min3"), (7, "fp32_2fadd_min3"), (2, "u16x2_dpx"), (3, "ffma_reference"))
+               (1, "fp32_f32x2_min3"), (7, "fp32_2fadd_min3"), (2, "u16x2_dpx"), (3, "ffma_reference"),
+               (8, "ffma_imm_operand"))
+PROBE_DIAG_MIXES = ((9, "fp32_2fadd_imm_min3"), (10, "int32_iadd_imm_min3"),
+                    (11, "int32_dpx_imm"), (12, "int32_3pipe_dpx3_imad3_fadd2"), (13, "dpx3_f32x2_5"),
+                    (14, "int32_imad_imm_min3"))
 
 
-def issue_probe(btas):
+def issue_probe(btas, full=False):
     """Measured issue ceilings of the inner-loop instruction mixes, in
-    tropical terms per clock per SM (btas_measure_issue_rate)."""
+    tropical terms per clock per SM (btas_measure_issue_rate).  With `full`,
+    also the diagnostic mixes, each at 1 and 2 CTAs per SM."""
     probe = {}
-    for mix, name in PROBE_MIXES:
-        try:
-            probe[name] = round(btas.measure_issue_rate(mix), 1)
-        except Exception as exc:  # diagnostic only
-            probe[name] = f"unavailable: {exc}"
+    mixes = PROBE_MIXES + (PROBE_DIAG_MIXES if full else ())
+    for ctas in ((1, 2) if full else (1,)):
+        for mix, name in mixes:
+            key = name if ctas == 1 else f"{name}@2cta"
+            try:
+                probe[key] = round(btas.measure_issue_rate(mix, ctas), 1)
+            except Exception as exc:  # diagnostic only
+                probe[key] = f"unavailable: {exc}"
     return probe
 
 
@@ -412,6 +423,13 @@ def run_btas(args):
         roof_i32["measured_issue_ceiling_tops"] = round(ceil, 3)
         roof_i32["measured_issue_ceiling_basis"] = "best int32 instruction mix of the probe"
         roof_i32["frac_of_measured_ceiling"] = round(n3 / t_i32min / 1e12 / ceil, 4)
+    if isinstance(probe.get("ffma_reference"), float) and isinstance(probe.get("ffma_imm_operand"), float):
+        # the same FFMA stream with one register operand replaced by an
+        # immediate: the speed-up shows the register-operand read limit
+        roof_i32["limiter"] = ("register-operand reads, about 2 warp-wide 32-bit operands per scheduler per "
+                               "clock: FFMA with 3 register operands "
+                               f"{probe['ffma_reference']} vs 2 register operands {probe['ffma_imm_operand']} "
+                               "terms/clk/SM; a product term reads >= 3 registers (A, B, accumulator)")
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Gop/s", "n_gpus": world, "steps": args.steps,
@@ -930,7 +948,12 @@ def run_only(args):
     elif args.only == "next":
         print(json.dumps({"only": "next", **next_rows(args, btas, torch)}))
     elif args.only == "probe":
-        print(json.dumps({"only": "probe", "terms_per_clk_per_sm": issue_probe(btas)}))
+        if args.probe_mix is not None:
+            r = btas.measure_issue_rate(args.probe_mix, args.probe_ctas)
+            print(json.dumps({"only": "probe", "mix": args.probe_mix, "ctas_per_sm": args.probe_ctas,
+                              "terms_per_clk_per_sm": round(r, 1)}))
+        else:
+            print(json.dumps({"only": "probe", "terms_per_clk_per_sm": issue_probe(btas, full=True)}))
     elif args.only == "configs":
         print(json.dumps({"only": "configs", **config_timings(args, btas, torch)}))
     else:

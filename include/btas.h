@@ -88,7 +88,8 @@ typedef enum {
     BTAS_ERR_BOUND = 2,       /* a requested exact reduced-precision path is not provably exact */
     BTAS_ERR_NOMEM = 3,       /* device workspace allocation failed */
     BTAS_ERR_CUDA = 4,        /* a CUDA runtime call failed */
-    BTAS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (batched scheduler) */
+    BTAS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (batched/server scheduler,
+                                 grid barriers of the cooperative APSP and SSSP kernels) */
     BTAS_ERR_BUDGET = 6,      /* request exceeds the configured device-memory budget */
     BTAS_ERR_UNSUPPORTED = 7  /* semiring/dtype combination not offered */
 } btas_status;
@@ -125,6 +126,22 @@ int64_t btas_kernel_launches(void);
  * 6 = int32 column split (mix 5 on 5 of 8 columns, DPX on 3),
  * 7 = fp32 two scalar adds + 3-input min. */
 btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_per_sm);
+
+/* Diagnostic: the same probe with ctas_per_sm (1 or 2) CTAs of 256 threads
+ * per SM, and the diagnostic mixes that separate pipe throughput from
+ * register-operand reads:
+ *   8  = FFMA x2 with the multiplier an immediate (two register operands),
+ *   9  = fp32 two adds of an immediate + 3-input min,
+ *   10 = int32 two IADD of an immediate + 3-input min,
+ *   11 = int32 DPX add-min with an immediate addend,
+ *   12 = int32 three-pipe split (DPX on 3 of 8 columns, IMAD + 3-input min
+ *        on 3, FADD + 3-input min on 2),
+ *   13 = DPX on 3 of 8 columns, add.f32x2 + 3-input min on 5,
+ *   14 = int32 two IMAD of an immediate addend + 3-input min.
+ * The rate of an SM is taken from its first CTA's start to its last CTA's
+ * end; the slowest SM is reported.  Errors: BTAS_ERR_ARG for a mix outside
+ * 0..14 or ctas_per_sm outside {1, 2}. */
+btas_status btas_measure_issue_rate_ex(int mix, int ctas_per_sm, double *terms_per_clock_per_sm);
 
 /* ------------------------------------------------------------------------
  * Level 3: tropical matrix product (the product listing of Sec. IV, titled
@@ -361,7 +378,8 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream);
 int btas_apsp_squarings(int64_t n);
 
 /* ------------------------------------------------------------------------
- * btas_apsp_noalloc: the same APSP as btas_apsp (int32 kernels, early exit),
+ * btas_apsp_noalloc: the same APSP as btas_apsp (int32 or exact packed
+ * 16-bit squarings as btas_apsp chooses them, early exit),
  * for callers that cannot allocate device memory when they call -- e.g. a
  * process whose own memory pool already holds the device's free memory, or
  * latency-critical code that must not allocate (an allocation can block or
@@ -378,17 +396,35 @@ int btas_apsp_squarings(int64_t n);
  * cooperative launch is not possible on the device do they take the tiled
  * int32 squarings.  Nothing is read back: the call does not synchronise
  * `stream`.
- * The first call on a device looks up the array's device address with that
- * device current (a host-side set-up step); make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents; the change flags are cleared on `stream` at the start of each
- * call.  Calls whose work overlaps on the GPU race on the array: order them
- * (one stream, or events).  The weight domain (zero diagonal, weights in
- * [0, 2^28] or BTAS_INF_I32) is assumed, not checked.
+ * Every call looks up the array's device address in the current context
+ * (a host-side lookup that does not synchronise), so it stays valid after a
+ * context is torn down and recreated.  The first call on a device may load
+ * the library's device code there: make it before any stream capture.  All
+ * calls share the array and it keeps the last call's contents; the status
+ * words are cleared on `stream` at the start of each call.  Calls whose work
+ * overlaps on the GPU race on the array: order them (one stream, or events).
+ * The one-block and cooperative kernels check the weight domain (zero
+ * diagonal, weights in [0, 2^28] or BTAS_INF_I32) and leave D unwritten when
+ * it fails, and so does the cooperative kernel when a bounded grid-barrier
+ * wait expires; the call itself cannot see either (it reads nothing back):
+ * btas_apsp_noalloc_status reports them.  The tiled fallback assumes the
+ * domain.
  * ------------------------------------------------------------------------ */
 #define BTAS_NOALLOC_MAX_N 1024
 #define BTAS_NOALLOC_SCRATCH_BYTES (256 + 3 * 4 * BTAS_NOALLOC_MAX_N * BTAS_NOALLOC_MAX_N + 1024)
 btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D, void *stream);
+
+/* Outcome of the most recent btas_apsp_noalloc call on the current device,
+ * read from the status words that call left in the fixed array.  The read is
+ * enqueued on `stream` (so it follows that call's work when both use the same
+ * stream) and the stream is synchronised; it copies into host memory of the
+ * call's own and allocates nothing.  Returns BTAS_OK (D holds the result),
+ * BTAS_ERR_ARG (W outside the weight domain, D not written; also when no call
+ * has been made on this device), BTAS_ERR_TIMEOUT (a grid-barrier wait of the
+ * cooperative kernel expired, D not written) or BTAS_ERR_CUDA.
+ * squarings_done: HOST pointer or NULL; squarings that changed D.  Another
+ * btas_apsp_noalloc call enqueued in between overwrites the words. */
+btas_status btas_apsp_noalloc_status(void *stream, int *squarings_done);
 
 /* ------------------------------------------------------------------------
  * Autotuner for the tropical product kernels (the product of Eq. 1-4, and

@@ -64,6 +64,7 @@ SIGNATURES = {
     "btas_workspace_reserved": (_i64, []),
     "btas_workspace_trim": (_i32, []),
     "btas_measure_issue_rate": (_i32, [_i32, _vp]),
+    "btas_measure_issue_rate_ex": (_i32, [_i32, _i32, _vp]),
     "btas_gemm": (_i32, [_i32, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "btas_packed_products": (_i64, []),
     "btas_dot": (_i32, [_i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp, _vp]),
@@ -80,6 +81,7 @@ SIGNATURES = {
     "btas_apsp_fw": (_i32, [_i64, _vp, _vp, _vp]),
     "btas_sssp": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp]),
     "btas_apsp_noalloc": (_i32, [_i64, _vp, _vp, _vp]),
+    "btas_apsp_noalloc_status": (_i32, [_vp, _vp]),
     "btas_batch_create": (_i32, [_vp, _i32]),
     "btas_batch_add_apsp": (_i32, [_vp, _i64, _vp, _vp]),
     "btas_batch_add_gemm": (_i32, [_vp, _i32, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64]),
@@ -177,11 +179,15 @@ def btas_measure_issue_rate(mix, out_ptr) -> int:
     return lib().btas_measure_issue_rate(mix, out_ptr)
 
 
-def measure_issue_rate(mix: int) -> float:
+def measure_issue_rate(mix: int, ctas_per_sm: int = 1) -> float:
     """Terms per clock per SM of instruction mix `mix` (see btas.h)."""
     v = ctypes.c_double()
-    check(btas_measure_issue_rate(mix, ctypes.addressof(v)))
+    check(btas_measure_issue_rate_ex(mix, ctas_per_sm, ctypes.addressof(v)))
     return v.value
+
+
+def btas_measure_issue_rate_ex(mix, ctas_per_sm, out_ptr) -> int:
+    return lib().btas_measure_issue_rate_ex(mix, ctas_per_sm, out_ptr)
 
 
 def btas_gemm(semiring, dtype, m, n, k, A, lda, B, ldb, C, ldc, stream) -> int:
@@ -305,6 +311,10 @@ def sssp(W, src, stream=None, info=False):
 
 def btas_apsp_noalloc(n, W, D, stream) -> int:
     return lib().btas_apsp_noalloc(n, W, D, stream)
+
+
+def btas_apsp_noalloc_status(stream, squarings_done_ptr) -> int:
+    return lib().btas_apsp_noalloc_status(stream, squarings_done_ptr)
 
 
 def btas_batch_create(out_ptr, flags) -> int:

@@ -1,11 +1,19 @@
 // Issue-rate probe: how many tropical terms one SM completes per clock for a
 // given register-only instruction mix.  It measures the empirical ceiling
 // that the tropical GEMM kernels are compared against (their roofline is set
-// by ALU issue, not by memory or tensor cores).  One CTA of 256 threads per
-// SM keeps 64 independent accumulators per thread; the 8 + 8 operand
-// registers change every iteration, so no two terms share a sum.  The
-// launch reserves 120 KiB of shared memory per CTA so that exactly one CTA
-// runs on each SM.
+// by ALU issue, not by memory or tensor cores).  CTAs of 256 threads keep 64
+// independent accumulators per thread; the 8 + 8 operand registers change
+// every iteration, so no two terms share a sum.  The launch reserves enough
+// shared memory per CTA that exactly `ctas_per_sm` CTAs run on each SM, and
+// the rate of an SM is taken over the span from its first CTA's start to its
+// last CTA's end (clock64 is a per-SM counter).
+//
+// Besides the mixes the kernels use, the probe carries diagnostic mixes that
+// separate three candidate limits of 32-bit tropical terms:
+//   * pipe throughput (ALU, FMA-heavy, FMA-lite lanes per clock);
+//   * register-operand reads per clock (the same instruction with one operand
+//     an immediate, so one register read fewer per instruction);
+//   * warps available to hide latency (1 or 2 CTAs per SM).
 #include <cstdint>
 #include <vector>
 
@@ -21,8 +29,66 @@ __device__ __forceinline__ uint64_t pk(float lo, float hi) {
     return d;
 }
 
-template <int MIX>
-__global__ void __launch_bounds__(256, 1) probe_kernel(const float *in, float *out, int iters, long long *cyc, int one) {
+__device__ __forceinline__ int fi(float v) { return __float_as_int(v); }
+__device__ __forceinline__ float if_(int v) { return __int_as_float(v); }
+
+// One (i, j) update of mix MIX: two terms (four for the packed u16x2 mix).
+// Operands are bit patterns; only the instruction stream matters here.
+template <int MIX, int J>
+__device__ __forceinline__ float probe_term(float acc, uint64_t xi, uint64_t yj, int one) {
+    float a0, a1, b0, b1;
+    unpack2(xi, a0, a1);
+    unpack2(yj, b0, b1);
+    if constexpr (MIX == 0) {  // int32: two DPX fused add-min
+        const int t = __viaddmin_s32(fi(a0), fi(b0), fi(acc));
+        return if_(__viaddmin_s32(fi(a1), fi(b1), t));
+    } else if constexpr (MIX == 1) {  // fp32: add.f32x2 + 3-input min
+        float lo, hi;
+        unpack2(fadd2(xi, yj), lo, hi);
+        return fsel3<kMin>(acc, lo, hi);
+    } else if constexpr (MIX == 2) {  // packed 16-bit: two DPX u16x2 add-min (4 terms)
+        const unsigned t = __viaddmin_u16x2(__float_as_uint(a0), __float_as_uint(b0), __float_as_uint(acc));
+        return __uint_as_float(__viaddmin_u16x2(__float_as_uint(a1), __float_as_uint(b1), t));
+    } else if constexpr (MIX == 3) {  // reference: two FFMA
+        return fmaf(a1, b1, fmaf(a0, b0, acc));
+    } else if constexpr (MIX == 4) {  // int32: IADD x2 + 3-input min
+        return if_(__vimin3_s32(fi(acc), fi(a0) + fi(b0), fi(a1) + fi(b1)));
+    } else if constexpr (MIX == 5 || (MIX == 6 && J < 5)) {  // int32: IMAD x2 + 3-input min
+        return if_(__vimin3_s32(fi(acc), imad_add(fi(a0), one, fi(b0)), imad_add(fi(a1), one, fi(b1))));
+    } else if constexpr (MIX == 6) {
+        return probe_term<0, J>(acc, xi, yj, one);
+    } else if constexpr (MIX == 7) {  // fp32: two scalar RN adds + 3-input min
+        return fsel3<kMin>(acc, __fadd_rn(a0, b0), __fadd_rn(a1, b1));
+    } else if constexpr (MIX == 8) {  // FFMA x2, second operand an immediate (2 register reads)
+        return fmaf(a1, 1.25f + J, fmaf(a0, 0.75f + J, acc));
+    } else if constexpr (MIX == 9) {  // fp32: two scalar adds of an immediate + 3-input min
+        return fsel3<kMin>(acc, __fadd_rn(a0, 0.5f + J), __fadd_rn(a1, 0.25f + J));
+    } else if constexpr (MIX == 10) {  // int32: IADD of an immediate x2 + 3-input min
+        return if_(__vimin3_s32(fi(acc), fi(a0) + (7 + J), fi(a1) + (13 + J)));
+    } else if constexpr (MIX == 11) {  // int32: DPX add-min with an immediate addend
+        const int t = __viaddmin_s32(fi(a0), 7 + J, fi(acc));
+        return if_(__viaddmin_s32(fi(a1), 13 + J, t));
+    } else if constexpr (MIX == 12) {  // three pipes: DPX on 3 of 8 columns, IMAD+min3 on 3, FADD+min3 on 2
+        if constexpr (J < 3) return probe_term<0, J>(acc, xi, yj, one);
+        else if constexpr (J < 6) return probe_term<5, J>(acc, xi, yj, one);
+        else return probe_term<7, J>(acc, xi, yj, one);
+    } else if constexpr (MIX == 13) {  // DPX on 3 of 8 columns, f32x2 + min3 on 5
+        if constexpr (J < 3) return probe_term<0, J>(acc, xi, yj, one);
+        else return probe_term<1, J>(acc, xi, yj, one);
+    } else {  // 14: IMAD with an immediate addend x2 + 3-input min (x*one + imm)
+        return if_(__vimin3_s32(fi(acc), imad_add(fi(a0), one, 7 + J), imad_add(fi(a1), one, 13 + J)));
+    }
+}
+
+template <int MIX, int J>
+__device__ __forceinline__ void probe_row(float (&acc)[8], uint64_t xi, const uint64_t (&y)[8], int one) {
+    acc[J] = probe_term<MIX, J>(acc[J], xi, y[J], one);
+    if constexpr (J + 1 < 8) probe_row<MIX, J + 1>(acc, xi, y, one);
+}
+
+template <int MIX, int MINB>
+__global__ void __launch_bounds__(256, MINB) probe_kernel(const float *in, float *out, int iters, long long *cyc,
+                                                        int one) {
     uint64_t x[8], y[8];
     float acc[8][8];
 #pragma unroll
@@ -43,41 +109,9 @@ __global__ void __launch_bounds__(256, 1) probe_kernel(const float *in, float *o
 #pragma unroll
         for (int j = 0; j < 8; ++j) y[j] = fadd2(y[j], inc);
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float a0, a1, b0, b1;
-                unpack2(x[i], a0, a1);
-                unpack2(y[j], b0, b1);
-                if (MIX == 0) {  // int32: two DPX fused add-min (2 terms)
-                    const int t = __viaddmin_s32(__float_as_int(a0), __float_as_int(b0), __float_as_int(acc[i][j]));
-                    acc[i][j] = __int_as_float(__viaddmin_s32(__float_as_int(a1), __float_as_int(b1), t));
-                } else if (MIX == 1) {  // fp32: add.f32x2 + 3-input min (2 terms)
-                    float lo, hi;
-                    unpack2(fadd2(x[i], y[j]), lo, hi);
-                    acc[i][j] = fsel3<kMin>(acc[i][j], lo, hi);
-                } else if (MIX == 2) {  // packed 16-bit: two DPX u16x2 add-min (4 terms)
-                    const unsigned t = __viaddmin_u16x2(__float_as_uint(a0), __float_as_uint(b0), __float_as_uint(acc[i][j]));
-                    acc[i][j] = __uint_as_float(__viaddmin_u16x2(__float_as_uint(a1), __float_as_uint(b1), t));
-                } else if (MIX == 4 || MIX == 5 || (MIX == 6 && j < 5)) {
-                    // int32: two adds (4: IADD on the ALU pipe; 5, 6: IMAD x*1+y on
-                    // the FMA pipe) + one 3-input min (2 terms); 6 uses this on 5
-                    // of 8 columns and DPX on the other 3
-                    const int s0 = MIX == 4 ? __float_as_int(a0) + __float_as_int(b0)
-                                            : imad_add(__float_as_int(a0), one, __float_as_int(b0));
-                    const int s1 = MIX == 4 ? __float_as_int(a1) + __float_as_int(b1)
-                                            : imad_add(__float_as_int(a1), one, __float_as_int(b1));
-                    acc[i][j] = __int_as_float(__vimin3_s32(__float_as_int(acc[i][j]), s0, s1));
-                } else if (MIX == 6) {
-                    const int t = __viaddmin_s32(__float_as_int(a0), __float_as_int(b0), __float_as_int(acc[i][j]));
-                    acc[i][j] = __int_as_float(__viaddmin_s32(__float_as_int(a1), __float_as_int(b1), t));
-                } else if (MIX == 7) {  // fp32: two scalar RN adds + 3-input min (2 terms)
-                    acc[i][j] = fsel3<kMin>(acc[i][j], __fadd_rn(a0, b0), __fadd_rn(a1, b1));
-                } else {  // reference: two FFMA (2 multiply-adds)
-                    acc[i][j] = fmaf(a1, b1, fmaf(a0, b0, acc[i][j]));
-                }
-            }
+        for (int i = 0; i < 8; ++i) probe_row<MIX, 0>(acc[i], x[i], y, one);
     }
+    __syncthreads();
     const long long t1 = clock64();
     float s = 0.f;
 #pragma unroll
@@ -85,19 +119,35 @@ __global__ void __launch_bounds__(256, 1) probe_kernel(const float *in, float *o
 #pragma unroll
         for (int j = 0; j < 8; ++j) s += acc[i][j];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
-    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        cyc[3 * blockIdx.x] = t0;
+        cyc[3 * blockIdx.x + 1] = t1;
+        cyc[3 * blockIdx.x + 2] = smid;
+    }
 }
 
-// Dynamic shared memory large enough that only one probe CTA fits per SM.
-constexpr int kProbeSmem = 120 * 1024;
+constexpr int kMaxMix = 14;
 
-template <int MIX>
-cudaError_t run_probe(int sms, const float *in, float *out, long long *cyc, int iters) {
-    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(probe_kernel<MIX>), kProbeSmem);
+// Dynamic shared memory that lets exactly MINB probe CTAs share an SM.
+template <int MINB>
+constexpr int probe_smem() { return MINB == 1 ? 120 * 1024 : 100 * 1024; }
+
+template <int MIX, int MINB>
+cudaError_t run_probe_t(int blocks, const float *in, float *out, long long *cyc, int iters) {
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(probe_kernel<MIX, MINB>), probe_smem<MINB>());
     if (e != cudaSuccess) return e;
-    probe_kernel<MIX><<<sms, 256, kProbeSmem>>>(in, out, iters, cyc, 1);
+    probe_kernel<MIX, MINB><<<blocks, 256, probe_smem<MINB>()>>>(in, out, iters, cyc, 1);
     note_launch();
     return cudaGetLastError();
+}
+
+template <int MINB, int MIX = 0>
+cudaError_t run_probe(int mix, int blocks, const float *in, float *out, long long *cyc, int iters) {
+    if (mix == MIX) return run_probe_t<MIX, MINB>(blocks, in, out, cyc, iters);
+    if constexpr (MIX < kMaxMix) return run_probe<MINB, MIX + 1>(mix, blocks, in, out, cyc, iters);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -105,44 +155,37 @@ cudaError_t run_probe(int sms, const float *in, float *out, long long *cyc, int 
 
 using namespace btas;
 
-extern "C" btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_per_sm) {
-    if (mix < 0 || mix > 7 || !terms_per_clock_per_sm) {
-        record_error("btas_measure_issue_rate: mix must be 0..7");
+extern "C" btas_status btas_measure_issue_rate_ex(int mix, int ctas_per_sm, double *terms_per_clock_per_sm) {
+    if (mix < 0 || mix > kMaxMix || (ctas_per_sm != 1 && ctas_per_sm != 2) || !terms_per_clock_per_sm) {
+        record_error("btas_measure_issue_rate_ex: mix must be 0..14 and ctas_per_sm 1 or 2");
         return BTAS_ERR_ARG;
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * ctas_per_sm;
     float *in = nullptr, *out = nullptr;
     long long *cyc = nullptr;
     if (cudaMalloc(&in, 1024 * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&out, (size_t)sms * 256 * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&cyc, (size_t)sms * sizeof(long long)) != cudaSuccess) {
+        cudaMalloc(&out, (size_t)blocks * 256 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&cyc, (size_t)blocks * 3 * sizeof(long long)) != cudaSuccess) {
         cudaFree(in);
         cudaFree(out);
-        record_error("btas_measure_issue_rate: allocation failed");
+        record_error("btas_measure_issue_rate_ex: allocation failed");
         return BTAS_ERR_NOMEM;
     }
     std::vector<float> h(1024);
     for (int i = 0; i < 1024; ++i) h[i] = (float)((i * 37) % 101) * 0.01f;
-    cudaMemcpy(in, h.data(), 1024 * sizeof(float), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(in, h.data(), 1024 * sizeof(float), cudaMemcpyHostToDevice);
     const int iters = 4000;
-    cudaError_t e = cudaSuccess;
-    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
-        switch (mix) {
-            case 0: e = run_probe<0>(sms, in, out, cyc, rep ? iters : 16); break;
-            case 1: e = run_probe<1>(sms, in, out, cyc, rep ? iters : 16); break;
-            case 2: e = run_probe<2>(sms, in, out, cyc, rep ? iters : 16); break;
-            case 3: e = run_probe<3>(sms, in, out, cyc, rep ? iters : 16); break;
-            case 4: e = run_probe<4>(sms, in, out, cyc, rep ? iters : 16); break;
-            case 5: e = run_probe<5>(sms, in, out, cyc, rep ? iters : 16); break;
-            case 6: e = run_probe<6>(sms, in, out, cyc, rep ? iters : 16); break;
-            default: e = run_probe<7>(sms, in, out, cyc, rep ? iters : 16); break;
-        }
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
+        const int it = rep ? iters : 16;
+        e = ctas_per_sm == 1 ? run_probe<1>(mix, blocks, in, out, cyc, it) : run_probe<2>(mix, blocks, in, out, cyc, it);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
-    std::vector<long long> hc(sms);
-    if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, (size_t)sms * sizeof(long long), cudaMemcpyDeviceToHost);
+    std::vector<long long> hc((size_t)blocks * 3);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hc.data(), cyc, hc.size() * sizeof(long long), cudaMemcpyDeviceToHost);
     cudaFree(in);
     cudaFree(out);
     cudaFree(cyc);
@@ -150,9 +193,38 @@ extern "C" btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_
         record_error(cudaGetErrorString(e));
         return BTAS_ERR_CUDA;
     }
-    long long mx = 1;
-    for (long long c : hc) mx = c > mx ? c : mx;
+    // per SM: span from its first CTA's start to its last CTA's end; the
+    // slowest SM sets the rate
+    std::vector<long long> lo(sms, -1), hi(sms, -1);
+    std::vector<int> cnt(sms, 0);
+    for (int b = 0; b < blocks; ++b) {
+        const long long s = hc[3 * b + 2];
+        if (s < 0 || s >= sms) continue;
+        if (lo[s] < 0 || hc[3 * b] < lo[s]) lo[s] = hc[3 * b];
+        if (hc[3 * b + 1] > hi[s]) hi[s] = hc[3 * b + 1];
+        ++cnt[s];
+    }
     const double terms_per_thread = (double)iters * 64 * (mix == 2 ? 4 : 2);
-    *terms_per_clock_per_sm = terms_per_thread * 256.0 / (double)mx;
+    double worst = 0.0;
+    bool any = false;
+    for (int s = 0; s < sms; ++s) {
+        if (cnt[s] == 0 || hi[s] <= lo[s]) continue;
+        const double r = terms_per_thread * 256.0 * cnt[s] / (double)(hi[s] - lo[s]);
+        if (!any || r < worst) worst = r;
+        any = true;
+    }
+    if (!any) {
+        record_error("btas_measure_issue_rate_ex: no timing recorded");
+        return (btas_status)BTAS_ERR_INTERNAL;
+    }
+    *terms_per_clock_per_sm = worst;
     return BTAS_OK;
+}
+
+extern "C" btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_per_sm) {
+    if (mix < 0 || mix > 7) {
+        record_error("btas_measure_issue_rate: mix must be 0..7");
+        return BTAS_ERR_ARG;
+    }
+    return btas_measure_issue_rate_ex(mix, 1, terms_per_clock_per_sm);
 }
