@@ -75,6 +75,7 @@ typedef enum {
                                        with BTAS_GEMM_PACKED (the APSP entry points have their own
                                        switches) */
 #define BTAS_GEMM_PACKED 0x800     /* int32: exact packed 16-bit path when the operand ranges allow */
+#define BTAS_GEMM_CHECKED 0x1000   /* int32/fp32: check the operand domain on the device (btas_sync_status) */
 
 typedef enum {
     BTAS_I32 = 0, /* int32, encoding above */
@@ -175,10 +176,37 @@ btas_status btas_measure_issue_rate_ex(int mix, int ctas_per_sm, double *terms_p
  * made on the device: the call stays asynchronous, the results are
  * bit-identical either way, and it costs a few passes over A, B and C plus
  * device workspace of about 4mk + 2kn + 2mn bytes.
+ *
+ * BTAS_GEMM_CHECKED (BTAS_I32 and BTAS_F32; BTAS_ERR_UNSUPPORTED with
+ * BTAS_U16): without it, operands outside the domain above are not detected
+ * (an int32 entry beyond 2^28 that is not the (+)-identity can be clamped to
+ * INF without notice).  With it, the call scans A, B (and C with
+ * BTAS_GEMM_ACCUMULATE) on the device before the product: int32 entries must
+ * satisfy |v| <= 2^28 or equal the semiring's (+)-identity; fp32 entries must
+ * not be NaN or the other semiring's infinity.  A call that finds any entry
+ * outside leaves C unwritten and adds the count to the device's status
+ * words; the call itself stays asynchronous and returns BTAS_OK.
+ * btas_sync_status reports (and clears) the words.  Cost: one extra read of
+ * the operands (HBM-bound).
  * ------------------------------------------------------------------------ */
 btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k,
                       const void *A, int64_t lda, const void *B, int64_t ldb,
                       void *C, int64_t ldc, void *stream);
+
+/* Device-side errors of asynchronous calls.  Reads the current device's
+ * status words after the work enqueued on `stream` (synchronises `stream`)
+ * and clears them.  The words accumulate, across calls and streams, the
+ * operand entries outside the domain that BTAS_GEMM_CHECKED products found;
+ * synchronise other streams that ran checked products first.
+ * out_of_domain, calls: HOST pointers or NULL; entries found and checked
+ * calls that found any (each of those left its C unwritten).
+ * Returns BTAS_ERR_ARG if any entry was found, else BTAS_OK (BTAS_ERR_CUDA on
+ * a CUDA failure).  Calls that synchronise on their own report device-side
+ * errors themselves (btas_apsp, btas_sssp and the other APSP entry points
+ * return BTAS_ERR_ARG for a weight outside the domain and BTAS_ERR_TIMEOUT
+ * when a bounded grid-barrier wait expires; btas_batch_wait and the server
+ * report theirs); btas_apsp_noalloc has btas_apsp_noalloc_status. */
+btas_status btas_sync_status(void *stream, int64_t *out_of_domain, int64_t *calls);
 
 /* Diagnostic: number of products the current device has computed through
  * the packed path of BTAS_GEMM_PACKED since the library was loaded

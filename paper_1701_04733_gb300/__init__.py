@@ -66,6 +66,7 @@ SIGNATURES = {
     "btas_measure_issue_rate": (_i32, [_i32, _vp]),
     "btas_measure_issue_rate_ex": (_i32, [_i32, _i32, _vp]),
     "btas_gemm": (_i32, [_i32, _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
+    "btas_sync_status": (_i32, [_vp, _vp, _vp]),
     "btas_packed_products": (_i64, []),
     "btas_dot": (_i32, [_i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp, _vp]),
     "btas_axpy": (_i32, [_i32, _i32, _i64, _vp, _vp, _i64, _vp, _i64, _vp]),

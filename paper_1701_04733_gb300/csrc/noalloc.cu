@@ -11,9 +11,12 @@
 // (BTAS_NOALLOC_SCRATCH_BYTES) until the process exits.
 //
 // Host code cannot use the array's name as a device address: in host code it
-// names a host-side stand-in.  The address is obtained once per device, with
-// that device current, through cudaGetSymbolAddress, on the first call made
-// on that device.  Make that first call before any stream capture.
+// names a host-side stand-in.  Every call looks the address up with
+// cudaGetSymbolAddress for the current device (a host-side lookup, no
+// synchronisation), so a context that was torn down and recreated (for
+// example after cudaDeviceReset) gets the array's new address.  The first
+// call on a device may load the library's device code there: make it before
+// any stream capture.
 //
 // The smallest graphs run on the one-block kernel and the others on the
 // cooperative kernel (the same kernels and size boundary as btas_apsp); the
@@ -23,6 +26,11 @@
 // The change flags, which must start at zero, are cleared on the stream at the
 // start of every call.  Calls whose work overlaps on the GPU (different
 // streams, or different host threads without ordering) race on the array.
+//
+// The call reads nothing back.  The kernels leave their outcome (weight
+// domain violations, a grid-barrier timeout, squarings that changed D) in the
+// status words at the start of the array, and btas_apsp_noalloc_status reads
+// them once the call's work has finished.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -45,30 +53,34 @@ static_assert(BTAS_NOALLOC_SCRATCH_BYTES == kFlagBytes + 3 * kMatBytes + 1024, "
 // everything after the flags as its workspace.
 static __device__ __align__(256) unsigned char g_scratch[BTAS_NOALLOC_SCRATCH_BYTES];
 
+// How the most recent call on each device ran, so that the status query
+// knows which words hold its outcome.
+enum Regime : int { kNone = 0, kTrivial, kOneBlock, kCooperative, kTiled };
+struct LastCall {
+    int regime;
+    int S;
+};
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_dev_ptr[kMaxDevices] = {};
+LastCall g_last[kMaxDevices] = {};
 
 btas_status set_error(btas_status s, const char *msg) {
     record_error(msg);
     return s;
 }
 
-// Device address of g_scratch for the current device (set up on first use).
-cudaError_t scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+cudaError_t current_device(int *dev) {
+    cudaError_t e = cudaGetDevice(dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    return (*dev < 0 || *dev >= kMaxDevices) ? cudaErrorInvalidDevice : cudaSuccess;
+}
+
+// Device address of g_scratch in the current context.
+cudaError_t scratch_address(void **out) { return cudaGetSymbolAddress(out, g_scratch); }
+
+void note_regime(int dev, int regime, int S) {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_dev_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_dev_ptr[dev] = p;
-    }
-    *out = g_dev_ptr[dev];
-    return cudaSuccess;
+    g_last[dev] = LastCall{regime, S};
 }
 
 int squarings(long long n) {
@@ -104,17 +116,19 @@ extern "C" btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D
                  (long long)n, kMaxN);
         return set_error(BTAS_ERR_ARG, buf);
     }
-    if (n == 0) return BTAS_OK;
-    if (!W || !D) return set_error(BTAS_ERR_ARG, "btas_apsp_noalloc: NULL pointer");
+    if (n > 0 && (!W || !D)) return set_error(BTAS_ERR_ARG, "btas_apsp_noalloc: NULL pointer");
+    int dev = 0;
+    cudaError_t e = current_device(&dev);
+    if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t nn = (size_t)n * (size_t)n;
     const int S = squarings(n);
-    cudaError_t e;
     if (S == 0) {
-        if (D != W) {
+        if (n > 0 && D != W) {
             e = cudaMemcpyAsync(D, W, nn * 4, cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
         }
+        note_regime(dev, kTrivial, 0);
         return BTAS_OK;
     }
     void *base = nullptr;
@@ -134,13 +148,17 @@ extern "C" btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D
     if (n <= apsp_small_limit()) {
         e = launch_apsp_small(W, n, (int)n, S, true, D, n, flags, st);
         if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+        note_regime(dev, kOneBlock, S);
         return BTAS_OK;
     }
     const char *no_mid = getenv("BTAS_APSP_NO_MID");  // as in btas_apsp: tiled squarings
     if (n <= apsp_mid_max_n() && apsp_mid_workspace(n, S) <= 3 * kMatBytes + 1024 &&
         !(no_mid && *no_mid && atoi(no_mid) != 0)) {
         e = launch_apsp_mid(W, n, (int)n, S, true, true, D, n, X, flags, st);
-        if (e == cudaSuccess) return BTAS_OK;
+        if (e == cudaSuccess) {
+            note_regime(dev, kCooperative, S);
+            return BTAS_OK;
+        }
         if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorNotSupported)
             return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
         cudaGetLastError();  // the grid cannot be co-resident here: tiled squarings below
@@ -183,5 +201,52 @@ extern "C" btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D
         if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
         cur = out;
     }
+    note_regime(dev, kTiled, S);
+    return BTAS_OK;
+}
+
+extern "C" btas_status btas_apsp_noalloc_status(void *stream, int *squarings_done) {
+    int dev = 0;
+    cudaError_t e = current_device(&dev);
+    if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+    LastCall last;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        last = g_last[dev];
+    }
+    if (last.regime == kNone)
+        return set_error(BTAS_ERR_ARG, "btas_apsp_noalloc_status: no btas_apsp_noalloc call on this device yet");
+    if (squarings_done) *squarings_done = 0;
+    if (last.regime == kTrivial) return BTAS_OK;
+    void *base = nullptr;
+    e = scratch_address(&base);
+    if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+    // the status words (at most 64 ints), copied into pageable host memory:
+    // ordered after the call's work on `stream`, nothing allocated
+    int words[64] = {};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(words, base, sizeof words, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(BTAS_ERR_CUDA, cudaGetErrorString(e));
+    if (last.regime == kTiled) {
+        // one change flag per squaring; the weight domain is not checked here
+        int done = 0;
+        for (int s = 0; s < last.S && s < 64; ++s) done += words[s] != 0;
+        if (squarings_done) *squarings_done = done;
+        return BTAS_OK;
+    }
+    // one-block kernel: [0] entries outside the domain, [1] largest weight,
+    // [2] squarings that changed D; the cooperative kernel adds [3] status
+    if (last.regime == kCooperative && words[3] != 0) {
+        record_error("btas_apsp_noalloc: a bounded grid-barrier wait expired; D was not written");
+        return static_cast<btas_status>(words[3]);
+    }
+    if (words[0] != 0) {
+        char buf[160];
+        snprintf(buf, sizeof buf,
+                 "btas_apsp_noalloc: %d entries of W outside the weight domain; D was not written", words[0]);
+        return set_error(BTAS_ERR_ARG, buf);
+    }
+    if (squarings_done) *squarings_done = words[2];
     return BTAS_OK;
 }

@@ -55,7 +55,7 @@ def test_tiled_fallback(btas):
     import torch
     os.environ["BTAS_APSP_NO_MID"] = "1"
     try:
-        for n, seed in ((1000, 79), (333, 80)):
+        for n, seed in ((1000, 79), (333, 80), (1024, 81)):
             W = gen.random_graph(gen.BASE_SEED, seed, n, 0.05, 1, 100)
             ref, out = _both(btas, W)
             np.testing.assert_array_equal(out, ref)
@@ -84,9 +84,11 @@ def test_in_place_and_size_limit(btas):
 
 def test_small_and_mid_sizes(btas):
     """The one-block (smallest n) and cooperative (up to n = 1024) kernels
-    behind the allocation-free entry point, out of place and in place."""
+    behind the allocation-free entry point, out of place and in place.
+    n = 1024 fills the fixed array exactly (three iterates plus the barrier
+    and status words)."""
     import torch
-    for n, seed in ((3, 74), (100, 75), (129, 76), (512, 77)):
+    for n, seed in ((3, 74), (100, 75), (129, 76), (512, 77), (1024, 78)):
         W = gen.random_graph(gen.BASE_SEED, seed, n, 0.5 if n < 8 else 0.05, 1, 100)
         ref, out = _both(btas, W)
         np.testing.assert_array_equal(out, ref)
@@ -95,3 +97,81 @@ def test_small_and_mid_sizes(btas):
         assert btas.btas_apsp_noalloc(n, t.data_ptr(), t.data_ptr(), stream) == 0
         torch.cuda.synchronize()
         np.testing.assert_array_equal(t.cpu().numpy(), ref)
+
+
+def _status(btas):
+    import ctypes
+    import torch
+    sq = ctypes.c_int(-1)
+    st = btas.btas_apsp_noalloc_status(torch.cuda.current_stream().cuda_stream, ctypes.addressof(sq))
+    return st, sq.value
+
+
+def test_status_reports_squarings(btas):
+    """The status query reads what the last call left in the fixed array: for
+    every regime (one block, cooperative, tiled fallback) the squarings that
+    changed D equal those btas_apsp reports for the same graph."""
+    import os
+    import torch
+    for n, seed, no_mid in ((40, 82, False), (700, 83, False), (700, 83, True)):
+        W = gen.random_graph(gen.BASE_SEED, seed, n, 0.05, 1, 100)
+        Wd = torch.from_numpy(W).cuda()
+        ref, info = btas.apsp(Wd, info=True)
+        out = torch.empty_like(Wd)
+        if no_mid:
+            os.environ["BTAS_APSP_NO_MID"] = "1"
+        try:
+            assert btas.btas_apsp_noalloc(n, Wd.data_ptr(), out.data_ptr(),
+                                          torch.cuda.current_stream().cuda_stream) == 0
+        finally:
+            os.environ.pop("BTAS_APSP_NO_MID", None)
+        st, sq = _status(btas)
+        assert st == 0, btas.last_error()
+        assert sq == info["squarings"]
+        np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+
+
+def test_status_reports_domain_violation(btas):
+    """A weight outside the domain: the kernel leaves D unwritten and the
+    status query returns BTAS_ERR_ARG; the next call succeeds."""
+    import torch
+    for n, seed in ((40, 84), (300, 85)):
+        W = gen.random_graph(gen.BASE_SEED, seed, n, 0.05, 1, 100)
+        bad = W.copy()
+        bad[1, 2] = -5
+        out = torch.full((n, n), 41, dtype=torch.int32, device="cuda")
+        b = torch.from_numpy(bad).cuda()
+        stream = torch.cuda.current_stream().cuda_stream
+        assert btas.btas_apsp_noalloc(n, b.data_ptr(), out.data_ptr(), stream) == 0
+        st, _ = _status(btas)
+        assert st == 1 and "domain" in btas.last_error()
+        assert (out.cpu().numpy() == 41).all()
+        ref, got = _both(btas, W)
+        np.testing.assert_array_equal(got, ref)
+        assert _status(btas)[0] == 0
+
+
+def test_status_reports_barrier_timeout(btas):
+    """Failure detection without a fault: with BTAS_MID_WITHHOLD=1 one block
+    of the cooperative kernel never reaches its first grid barrier, the other
+    blocks' bounded waits expire (about 2 s), D is left unwritten, and the
+    status query returns BTAS_ERR_TIMEOUT.  The next call on the same context
+    succeeds."""
+    import os
+    import torch
+    n = 300
+    W = gen.random_graph(gen.BASE_SEED, 86, n, 0.05, 1, 100)
+    Wd = torch.from_numpy(W).cuda()
+    out = torch.full((n, n), 41, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    os.environ["BTAS_MID_WITHHOLD"] = "1"
+    try:
+        assert btas.btas_apsp_noalloc(n, Wd.data_ptr(), out.data_ptr(), stream) == 0
+    finally:
+        del os.environ["BTAS_MID_WITHHOLD"]
+    st, _ = _status(btas)
+    assert st == 5, btas.last_error()
+    assert (out.cpu().numpy() == 41).all()
+    ref, got = _both(btas, W)
+    np.testing.assert_array_equal(got, ref)
+    assert _status(btas)[0] == 0
