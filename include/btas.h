@@ -527,10 +527,12 @@ int btas_tune_entries(void);
  * Batched execution: many independent tropical products and APSP solves of
  * uneven sizes in ONE persistent kernel launch (captured once in a CUDA
  * graph and replayed).  Same arithmetic and bit-identical results as the
- * single calls; the batch only changes scheduling: 128 x 128 tile tasks are
- * ordered by level (transposes, then squaring 1, 2, ...) and, within a level,
- * largest instance first; persistent CTAs claim tasks from a global counter
- * and wait (bounded) for the previous level of their own instance.
+ * single calls; the batch only changes scheduling: output tile tasks
+ * (128 x 128, or 64 x 64 for instances the tile autotuner gives the small
+ * tile) are ordered by level (transposes, then squaring 1, 2, ...) and,
+ * within a level, largest instance first; persistent CTAs claim tasks from a
+ * global counter and wait (bounded) for the previous level of their own
+ * instance.
  *
  * btas_batch_create  : *out receives a new empty batch.  flags:
  *                      BTAS_BATCH_NO_GRAPH launches the kernel directly
@@ -590,6 +592,36 @@ btas_status btas_batch_destroy(btas_batch_t *b);
 int64_t btas_batch_workspace_bytes(btas_batch_t *b);
 int btas_batch_tasks(btas_batch_t *b);
 btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *counts, int slots);
+
+/* Autotuner of the batched launch's output tile shape (the "tile shapes ...
+ * picked by an autotuner" of the batched form).  For each instance kind
+ * (0: APSP, 1: int32 min-plus product, 2: fp32 max-plus product) and each
+ * size bucket of 32 up to n_max (1 .. 2048), it times one synthetic batch of
+ * that bucket (three sizes, enough instances for about 1.5e10 terms; best of
+ * 3 graph-captured launches after a warm-up) with the 128 x 128 tile and with
+ * the 64 x 64 tile (4 x 4 outputs per thread) and records the 64 x 64 tile
+ * where it is at least 3 % faster.  Plans built afterwards on the current
+ * device use the table (an instance takes the entry of its larger output
+ * side); BTAS_BATCH_TILE=64|128 in the environment overrides it.  Both tiles
+ * compute bit-identical results.  Synchronises `stream`; allocates its
+ * inputs with cudaMalloc (call it outside stream capture).  ms_out: HOST
+ * array or NULL; entry 2*(kind*B + b) (+1) receives the 128 (64) tile's time
+ * in ms of bucket b of kind, B = ceil(n_max / 32), for entries < max_entries.
+ * btas_batch_tile: the table's tile for (kind, n) on the current device,
+ * 128 or 64, or 0 if it has no entry.  btas_batch_tune_clear empties it. */
+btas_status btas_batch_tune(int64_t n_max, void *stream, double *ms_out, int max_entries);
+int btas_batch_tile(int kind, int64_t n);
+void btas_batch_tune_clear(void);
+
+/* Tile choice tuned on one batch itself: times the batch (best of 3
+ * launches after a warm-up, on `stream`, synchronising) planned three ways
+ * -- mode 0: each instance's tile from the table above (and
+ * BTAS_BATCH_TILE); mode 1: 128 x 128 for every instance; mode 2: 64 x 64
+ * for every instance -- and keeps the fastest for the batch's later
+ * launches.  Results are bit-identical in every mode.  The batch's buffers
+ * are read and written by the timing launches.  mode: HOST, receives the
+ * choice; ms_out: HOST array of 3 or NULL, the three times in ms. */
+btas_status btas_batch_select_tiles(btas_batch_t *b, void *stream, int *mode, double *ms_out);
 
 /* ------------------------------------------------------------------------
  * Continuous-batching server: requests with HOST buffers (contiguous

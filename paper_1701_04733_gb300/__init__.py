@@ -25,6 +25,7 @@ GEMM_ACCUMULATE = 0x100
 GEMM_TRANS_B = 0x200
 GEMM_NO_CARRIER = 0x400
 GEMM_PACKED = 0x800
+GEMM_CHECKED = 0x1000
 I32 = 0
 F32 = 1
 U16 = 2
@@ -92,6 +93,10 @@ SIGNATURES = {
     "btas_batch_workspace_bytes": (_i64, [_vp]),
     "btas_batch_tasks": (_i32, [_vp]),
     "btas_batch_profile": (_i32, [_vp, _vp, _vp, _i32]),
+    "btas_batch_tune": (_i32, [_i64, _vp, _vp, _i32]),
+    "btas_batch_tile": (_i32, [_i32, _i64]),
+    "btas_batch_tune_clear": (None, []),
+    "btas_batch_select_tiles": (_i32, [_vp, _vp, _vp, _vp]),
     "btas_server_create": (_i32, [_vp, _i64, _i32]),
     "btas_server_submit_apsp": (_i32, [_vp, _i64, _vp, _vp, _vp]),
     "btas_server_submit_gemm": (_i32, [_vp, _i32, _i32, _i64, _i64, _i64, _vp, _vp, _vp, _vp]),
@@ -354,6 +359,42 @@ def btas_batch_profile(b, cycles_ptr, counts_ptr, slots) -> int:
     return lib().btas_batch_profile(b, cycles_ptr, counts_ptr, slots)
 
 
+def btas_batch_tune(n_max, stream, ms_ptr, max_entries) -> int:
+    return lib().btas_batch_tune(n_max, stream, ms_ptr, max_entries)
+
+
+def btas_batch_tile(kind, n) -> int:
+    return lib().btas_batch_tile(kind, n)
+
+
+def btas_batch_tune_clear() -> None:
+    lib().btas_batch_tune_clear()
+
+
+def btas_batch_select_tiles(b, stream, mode_ptr, ms_ptr) -> int:
+    return lib().btas_batch_select_tiles(b, stream, mode_ptr, ms_ptr)
+
+
+BATCH_TILE_KINDS = ("apsp", "i32_product", "f32_product")
+
+
+def batch_tune(n_max=1024, stream=None):
+    """Tile autotuner of the batched launch (btas_batch_tune).  Returns
+    {kind: [(bucket_lo, bucket_hi, tile, ms_128, ms_64), ...]}."""
+    buckets = (n_max + 31) // 32
+    ms = (ctypes.c_double * (2 * 3 * buckets))()
+    check(btas_batch_tune(n_max, _stream(stream), ctypes.addressof(ms), 2 * 3 * buckets))
+    out = {}
+    for kind, name in enumerate(BATCH_TILE_KINDS):
+        rows = []
+        for b in range(buckets):
+            lo, hi = 32 * b + 1, min(n_max, 32 * b + 32)
+            rows.append((lo, hi, btas_batch_tile(kind, hi), round(ms[2 * (kind * buckets + b)], 4),
+                         round(ms[2 * (kind * buckets + b) + 1], 4)))
+        out[name] = rows
+    return out
+
+
 # ------------------------------------------------------- torch helpers
 _torch_mod = None
 
@@ -404,14 +445,17 @@ def _rowmajor(t, name):
 
 
 def gemm(A, B, semiring="min", out=None, accumulate=False, trans_b=False, stream=None, no_carrier=False,
-         packed=False):
+         packed=False, checked=False):
     """Tropical product C = A (x) B (or C (+)= A (x) B with accumulate).
 
     A, B are CUDA tensors (int32, float32, or int16 holding values in
     [0, 0x7FFF] for the packed min-plus path).  With trans_b, B is given as
     B^T (n x k).  With packed=True (int32) the product runs on the exact
     packed 16-bit kernel when the operands' finite ranges allow it
-    (BTAS_GEMM_PACKED; decided on the device, same bits either way).  CPU
+    (BTAS_GEMM_PACKED; decided on the device, same bits either way).  With
+    checked=True the operand domain is checked on the device
+    (BTAS_GEMM_CHECKED): a violation leaves `out` unwritten and is reported
+    by sync_status().  CPU
     tensors are copied to the current device and the result is copied back
     (host -> device -> kernel -> host, the flow of Fig. 1)."""
     torch = _torch()
@@ -420,7 +464,7 @@ def gemm(A, B, semiring="min", out=None, accumulate=False, trans_b=False, stream
         dev = torch.device("cuda", torch.cuda.current_device())
         Ad, Bd = A.to(dev, non_blocking=True), B.to(dev, non_blocking=True)
         od = out.to(dev, non_blocking=True) if (out is not None and accumulate) else None
-        C = gemm(Ad, Bd, semiring, od, accumulate, trans_b, stream, no_carrier, packed)
+        C = gemm(Ad, Bd, semiring, od, accumulate, trans_b, stream, no_carrier, packed, checked)
         if out is None:
             return C.cpu()
         out.copy_(C)
@@ -436,9 +480,23 @@ def gemm(A, B, semiring="min", out=None, accumulate=False, trans_b=False, stream
     flags = _sr(semiring) | (GEMM_ACCUMULATE if accumulate else 0) | (GEMM_TRANS_B if trans_b else 0)
     flags |= GEMM_NO_CARRIER if no_carrier else 0
     flags |= GEMM_PACKED if packed else 0
+    flags |= GEMM_CHECKED if checked else 0
     check(btas_gemm(flags, _dtype_code(A), m, n, k, A.data_ptr(), _rowmajor(A, "A"), B.data_ptr(),
                     _rowmajor(B, "B"), out.data_ptr(), _rowmajor(out, "out"), _stream(stream)))
     return out
+
+
+def btas_sync_status(stream, out_of_domain_ptr, calls_ptr) -> int:
+    return lib().btas_sync_status(stream, out_of_domain_ptr, calls_ptr)
+
+
+def sync_status(stream=None):
+    """Device-side errors of asynchronous calls (btas_sync_status):
+    synchronises the stream, clears the device's status words and returns
+    (status, out_of_domain_entries, checked_calls_that_found_any)."""
+    e, c = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = btas_sync_status(_stream(stream), ctypes.addressof(e), ctypes.addressof(c))
+    return st, e.value, c.value
 
 
 def apsp(W, out=None, flags=APSP_EARLY_EXIT, stream=None, info=False):
@@ -555,6 +613,16 @@ class Batch:
     @property
     def tasks(self) -> int:
         return btas_batch_tasks(self.handle)
+
+    def select_tiles(self, stream=None):
+        """btas_batch_select_tiles: times the batch with the tuned table's
+        tiles, all 128 x 128 and all 64 x 64, keeps the fastest; returns
+        (mode name, {mode: ms})."""
+        mode = ctypes.c_int(0)
+        ms = (ctypes.c_double * 3)()
+        check(btas_batch_select_tiles(self.handle, _stream(stream), ctypes.addressof(mode), ctypes.addressof(ms)))
+        names = ("table", "all_128x128", "all_64x64")
+        return names[mode.value], {nm: round(ms[i], 3) for i, nm in enumerate(names)}
 
     def profile(self) -> dict:
         """Per-task-kind SM cycles and task counts, summed over every launch

@@ -5,6 +5,8 @@
 // coalesced.
 #include <cstdint>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -122,6 +124,50 @@ __global__ void ident_oplus_kernel(const uint32_t *__restrict__ src, long long l
     }
 }
 
+// BTAS_GEMM_CHECKED: the entries of a rows x cols operand outside the
+// product's domain -- int32: neither |v| <= 2^28 nor the semiring's
+// (+)-identity; fp32: NaN, or the infinity of the other semiring (-inf in a
+// min-plus operand, +inf in a max-plus one) -- are added to *count (this
+// call) and to status[0] (the device's running total).
+__global__ void domain_check_kernel(const uint32_t *__restrict__ X, long long ld, int rows, int cols, int is_float,
+                                    int sr, int *count, unsigned long long *status) {
+    const long long total = (long long)rows * cols;
+    int bad = 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long r = idx / cols, c = idx % cols;
+        const uint32_t bits = X[r * ld + c];
+        if (is_float) {
+            const float f = __uint_as_float(bits);
+            const bool wrong_inf = sr == kMin ? (f == -__int_as_float(0x7f800000)) : (f == __int_as_float(0x7f800000));
+            bad += (f != f) || wrong_inf;
+        } else {
+            const int v = static_cast<int>(bits);
+            const bool fin = v >= -BTAS_I32_FINITE_MAX && v <= BTAS_I32_FINITE_MAX;
+            bad += !(fin || v == (sr == kMin ? kInfI32 : kNinfI32));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) {
+        atomicAdd(count, bad);
+        atomicAdd(status, (unsigned long long)bad);
+    }
+}
+
+// After the domain checks of one call: *skip = 1 when the call found an
+// entry outside the domain (the product kernels then return without
+// writing C) or, on the packed path, when the packed kernels run instead
+// (the packed decision already saw the count); a violation counts the call
+// in status[1].
+__global__ void checked_gate_kernel(const int *count, const int *pack_state, int *skip,
+                                    unsigned long long *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const bool bad = *count != 0;
+    if (bad) atomicAdd(status + 1, 1ULL);
+    *skip = (bad || (pack_state != nullptr && pack_state[kPackStateUse] != 0)) ? 1 : 0;
+}
+
 static int grid_for(long long total, int threads) {
     long long b = (total + threads - 1) / threads;
     if (b > 152 * 16) b = 152 * 16;
@@ -160,6 +206,40 @@ cudaError_t launch_ident_oplus(const void *src, long long lds, int n, void *dst,
     if (n <= 0) return cudaSuccess;
     ident_oplus_kernel<<<grid_for((long long)n * n, 256), 256, 0, st>>>(
         static_cast<const uint32_t *>(src), lds, n, static_cast<uint32_t *>(dst), ldd, sr, is_float);
+    note_launch();
+    return cudaGetLastError();
+}
+
+unsigned long long *device_status_words() {
+    static std::mutex mu;
+    static unsigned long long *words[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (words[dev] == nullptr) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, 256) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, 256) != cudaSuccess) {
+            cudaFree(p);
+            return nullptr;
+        }
+        words[dev] = static_cast<unsigned long long *>(p);
+    }
+    return words[dev];
+}
+
+cudaError_t launch_domain_check(const void *X, long long ld, int rows, int cols, int is_float, int sr, int *count,
+                                unsigned long long *status, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    domain_check_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, st>>>(
+        static_cast<const uint32_t *>(X), ld, rows, cols, is_float, sr, count, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_checked_gate(const int *count, const int *pack_state, int *skip, unsigned long long *status,
+                                cudaStream_t st) {
+    checked_gate_kernel<<<1, 32, 0, st>>>(count, pack_state, skip, status);
     note_launch();
     return cudaGetLastError();
 }

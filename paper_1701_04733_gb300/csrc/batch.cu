@@ -20,6 +20,8 @@
 // launch (counter reset + kernel) is captured once in
 // a CUDA graph and replayed.
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -33,6 +35,9 @@
 namespace btas {
 
 using BCfg = TileCfg<128, 128, 32, 3, 2, 2, 1>;  // 2 CTAs/SM, <= 128 registers
+// the small output tile: 64 x 64, 4 x 4 outputs per thread, same 256 threads
+using BCfgS = TileCfg<kBTSmall, kBTSmall, 32, 3, 2, 2, 1, 4, 4>;
+static_assert(BCfgS::kThreads == BCfg::kThreads, "both task tiles run on the same CTA");
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
@@ -97,11 +102,26 @@ __device__ __forceinline__ void transpose_tile(const uint32_t *src, long long ld
     __syncthreads();
 }
 
+// One output tile of a product or an int32 squaring, of either task tile
+// size (the IMAD path on half of the thread's columns, as in the
+// standalone kernels).
 template <int VAR, int SR>
-__device__ __forceinline__ bool gemm_tile(const GemmArgs &a, int bm, int bn, unsigned char *smem, int tid,
+__device__ __forceinline__ bool gemm_tile(bool small, const GemmArgs &a, int bm, int bn, unsigned char *smem, int tid,
                                           void *Ct = nullptr, long long ldct = 0, uint32_t *Cd = nullptr,
                                           long long ldcd = 0, uint16_t *Cu = nullptr, long long ldcu = 0) {
+    if (small) return nt_tile<BCfgS, VAR, SR, 2>(a, bm, bn, smem, tid, Ct, ldct, Cd, ldcd, Cu, ldcu);
     return nt_tile<BCfg, VAR, SR, 4>(a, bm, bn, smem, tid, Ct, ldct, Cd, ldcd, Cu, ldcu);
+}
+
+__device__ __forceinline__ void copy_task_tile(bool small, const GemmArgs &a, int bm, int bn, int tid) {
+    if (small) copy_tile<BCfgS, int>(a, bm, bn, tid);
+    else copy_tile<BCfg, int>(a, bm, bn, tid);
+}
+
+__device__ __forceinline__ bool u16_task_tile(bool small, const U16Tile &u, int bm, int bn, unsigned char *smem,
+                                              int tid) {
+    if (small) return u16_tile_t<u16t::Small>(u, bm, bn, smem, tid);
+    return u16_tile_t<u16t::Big>(u, bm, bn, smem, tid);
 }
 
 __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const BatchParams p) {
@@ -155,23 +175,26 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
         const long long t_task = clock64();
         int slot = BTAS_BATCH_SLOT_COPY;
         const BInst I = p.insts[inst];
+        const bool small = I.tile == kBTSmall;
+        const int TT = small ? kBTSmall : kBT;  // output tile edge of this instance
         bool ch = false;
         if (type == kTaskTranspose) {
             slot = BTAS_BATCH_SLOT_TRANSPOSE;
             const uint32_t *src = static_cast<const uint32_t *>(I.kind == kInstGemm ? I.B : I.A);
             const long long lds = I.kind == kInstGemm ? I.ldb : I.lda;
-            const bool forms = I.kind == kInstApsp && I.use_u16;
+            const bool forms = (I.kind == kInstApsp && I.use_u16) || (I.kind == kInstSquare && I.use_u16 == 2);
             transpose_tile(src, lds, I.t0_rows, I.t0_cols, static_cast<uint32_t *>(I.Q0), I.ldq, tile,
                            reinterpret_cast<uint32_t *>(smem_raw), tid, forms ? I.Ad0 : nullptr,
-                           forms ? I.U0 : nullptr, I.ldq, I.ldu, forms ? p.maxfin + I.flag_base : nullptr);
+                           forms ? I.U0 : nullptr, I.ldq, I.ldu,
+                           (forms && I.kind == kInstApsp) ? p.maxfin + I.flag_base : nullptr);
         } else if (type == kTaskCopy) {
             // n <= 2: D = W
-            const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
+            const int bm = (tile / I.tiles_n) * TT, bn = (tile % I.tiles_n) * TT;
             GemmArgs a{};
             a.m = I.n; a.n = I.n;
             a.prev = I.A; a.ldp = I.lda;
             a.C = I.C; a.ldc = I.ldc;
-            copy_tile<BCfg, int>(a, bm, bn, tid);
+            copy_task_tile(small, a, bm, bn, tid);
         } else if (type == kTaskApsp) {
             const int S = I.levels, s = level;  // squaring s (1-based) of S
             // D_1..D_{S-1} alternate between X0 and X1 (aligned pitch ldx);
@@ -179,7 +202,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             const void *cur = s == 1 ? I.A : ((s - 1) & 1 ? I.X0 : I.X1);
             const long long ldcur = s == 1 ? I.lda : I.ldx;
             void *out = s == S ? I.C : (s & 1 ? I.X0 : I.X1);
-            const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
+            const int bm = (tile / I.tiles_n) * TT, bn = (tile % I.tiles_n) * TT;
             GemmArgs a{};
             a.m = a.n = a.k = I.n;
             a.A = cur; a.lda = ldcur;
@@ -208,7 +231,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                 if (prev_changed2 != 0) {
                     a.C = I.C;
                     a.ldc = I.ldc;
-                    copy_tile<BCfg, int>(a, bm, bn, tid);
+                    copy_task_tile(small, a, bm, bn, tid);
                 }
             } else if (I.use_u16 && 2LL * prev_max < BTAS_INF_U16) {
                 slot = BTAS_BATCH_SLOT_APSP_U16;
@@ -223,13 +246,13 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                 u.Cd = Cd; u.ldcd = I.ldq;
                 u.Cu = Cu; u.ldcu = I.ldu;
                 u.maxfin = a.maxfin;
-                ch = u16_tile(u, bm, bn, smem_raw, tid);
+                ch = u16_task_tile(small, u, bm, bn, smem_raw, tid);
             } else {
                 slot = BTAS_BATCH_SLOT_APSP_I32;
-                ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, Ct, I.ldq, Cd, I.ldq, Cu, I.ldu);
+                ch = gemm_tile<kI32Mix, kMin>(small, a, bm, bn, smem_raw, tid, Ct, I.ldq, Cd, I.ldq, Cu, I.ldu);
             }
         } else if (type == kTaskSquare) {
-            const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
+            const int bm = (tile / I.tiles_n) * TT, bn = (tile % I.tiles_n) * TT;
             GemmArgs a{};
             a.m = a.n = a.k = I.n;
             a.A = I.A; a.lda = I.lda;
@@ -241,7 +264,10 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.vec_b = 1;
             a.ro_a = 1;  // this step's input, written by an earlier launch
             a.maxfin = I.maxfin_ptr;
-            if (I.use_u16) {
+            // packed when asked, or (use_u16 == 2) when every finite entry of the
+            // input is < 0x7FFF / 2 (exact; the forms were written at level 0)
+            const bool packed = I.use_u16 == 1 || (I.use_u16 == 2 && 2LL * __ldcg(I.maxfin_in) < BTAS_INF_U16);
+            if (packed) {
                 slot = BTAS_BATCH_SLOT_SQUARE_U16;
                 U16Tile u{};
                 u.n = I.n;
@@ -253,13 +279,13 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                 u.Cd = I.Ad1; u.ldcd = I.ldq;
                 u.Cu = I.U1; u.ldcu = I.ldu;
                 u.maxfin = I.maxfin_ptr;
-                ch = u16_tile(u, bm, bn, smem_raw, tid);
+                ch = u16_task_tile(small, u, bm, bn, smem_raw, tid);
             } else {
                 slot = BTAS_BATCH_SLOT_SQUARE_I32;
-                ch = gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid, I.Q1, I.ldq, I.Ad1, I.ldq, I.U1, I.ldu);
+                ch = gemm_tile<kI32Mix, kMin>(small, a, bm, bn, smem_raw, tid, I.Q1, I.ldq, I.Ad1, I.ldq, I.U1, I.ldu);
             }
         } else {  // kTaskGemm
-            const int bm = (tile / I.tiles_n) * kBT, bn = (tile % I.tiles_n) * kBT;
+            const int bm = (tile / I.tiles_n) * TT, bn = (tile % I.tiles_n) * TT;
             GemmArgs a{};
             a.m = I.m; a.n = I.n; a.k = I.k;
             a.A = I.A; a.lda = I.lda;
@@ -272,11 +298,11 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             a.ro_b = I.trans_b ? 1 : 0;  // the caller's B^T, or Q0 from this launch's transposes
             slot = I.dtype == BTAS_I32 ? BTAS_BATCH_SLOT_GEMM_I32 : BTAS_BATCH_SLOT_GEMM_F32;
             if (I.dtype == BTAS_I32) {
-                if (I.sr == kMin) gemm_tile<kI32Mix, kMin>(a, bm, bn, smem_raw, tid);
-                else gemm_tile<kI32Mix, kMax>(a, bm, bn, smem_raw, tid);
+                if (I.sr == kMin) gemm_tile<kI32Mix, kMin>(small, a, bm, bn, smem_raw, tid);
+                else gemm_tile<kI32Mix, kMax>(small, a, bm, bn, smem_raw, tid);
             } else {
-                if (I.sr == kMin) gemm_tile<kF32X2, kMin>(a, bm, bn, smem_raw, tid);
-                else gemm_tile<kF32X2, kMax>(a, bm, bn, smem_raw, tid);
+                if (I.sr == kMin) gemm_tile<kF32X2, kMin>(small, a, bm, bn, smem_raw, tid);
+                else gemm_tile<kF32X2, kMax>(small, a, bm, bn, smem_raw, tid);
             }
         }
         if (type == kTaskApsp && __any_sync(0xffffffffu, ch) && (tid & 31) == 0)
@@ -324,6 +350,36 @@ long long batch_timeout_cycles(int device) {
     return c;
 }
 
+namespace {
+
+// Synthetic inputs of the tile autotuner (timing only): kind 0 a random
+// digraph (edge probability 0.1, weights 1..100, zero diagonal, INF
+// elsewhere), kind 1 int32 values in [0, 10^6], kind 2 fp32 values in [0, 1).
+__global__ void tile_tune_fill_kernel(uint32_t *X, long long n, int kind, unsigned long long seed) {
+    const long long total = n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        unsigned long long h = seed + (unsigned long long)idx * 0x9e3779b97f4a7c15ULL;
+        h = (h ^ (h >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        h = (h ^ (h >> 27)) * 0x94d049bb133111ebULL;
+        h ^= h >> 31;
+        uint32_t v;
+        if (kind == 0) {
+            const long long r = idx / n, c = idx % n;
+            v = r == c ? 0u : ((h & 1023) < 102 ? 1u + (uint32_t)((h >> 16) % 100) : (uint32_t)kInfI32);
+        } else if (kind == 1) {
+            v = (uint32_t)((h >> 20) % 1000001ULL);
+        } else {
+            v = __float_as_uint((float)(h >> 40) * 5.9604644775390625e-8f);
+        }
+        X[idx] = v;
+    }
+}
+
+}  // namespace
+
+// The batch tuner below needs the batch object's internals.
+btas_status batch_tune_impl(int64_t n_max, cudaStream_t st, double *ms_out, int max_entries);
 }  // namespace btas
 
 using namespace btas;
@@ -353,6 +409,7 @@ struct btas_batch_t {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
     long long workspace_bytes = 0;
+    int force_tile = 0;  // the tuner's timing batches: this output tile for every instance
 };
 
 namespace {
@@ -367,6 +424,30 @@ int squarings_of(long long n) {
         ++s;
     }
     return s;
+}
+
+// Output task tile per instance: the autotuner's table, keyed by (device,
+// kind, size bucket of 32), with BTAS_BATCH_TILE=64|128 overriding it and
+// 128 x 128 when neither says otherwise.  kind: 0 APSP, 1 int32 product,
+// 2 fp32 product; the bucket is that of the larger output side.
+std::mutex g_tile_mu;
+std::map<std::tuple<int, int, int>, int> g_tile_table;
+
+int tile_kind(const BInst &I) { return I.kind == kInstApsp ? 0 : (I.dtype == BTAS_I32 ? 1 : 2); }
+int tile_bucket(long long n) { return (int)((std::max(1LL, n) - 1) / 32); }
+
+int table_tile(int dev, int kind, long long n) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile_table.find(std::make_tuple(dev, kind, tile_bucket(n)));
+    return it == g_tile_table.end() ? 0 : it->second;
+}
+
+int choose_tile(const btas_batch_t *b, int dev, const BInst &I) {
+    if (b->force_tile) return b->force_tile;
+    const char *e = getenv("BTAS_BATCH_TILE");
+    if (e && *e) return atoi(e) == kBTSmall ? kBTSmall : kBT;
+    const int t = table_tile(dev, tile_kind(I), std::max(I.m, I.n));
+    return t == kBTSmall ? kBTSmall : kBT;
 }
 
 void release_plan(btas_batch_t *b) {
@@ -405,6 +486,9 @@ btas_status build_plan(btas_batch_t *b) {
     const int allow16 = (no16 && *no16 && atoi(no16) != 0) ? 0 : 1;
     for (size_t i = 0; i < ninst; ++i) {
         BInst I = b->reqs[i].inst;
+        I.tile = choose_tile(b, dev, I);
+        I.tiles_m = (I.m + I.tile - 1) / I.tile;
+        I.tiles_n = (I.n + I.tile - 1) / I.tile;
         ws_off[i] = ws;
         if (I.kind == kInstApsp) {
             if (I.levels > 0) {
@@ -649,6 +733,68 @@ int64_t btas_batch_workspace_bytes(btas_batch_t *b) { return b ? b->workspace_by
 
 int btas_batch_tasks(btas_batch_t *b) { return b ? b->total : 0; }
 
+btas_status btas_batch_tune(int64_t n_max, void *stream, double *ms_out, int max_entries) {
+    return batch_tune_impl(n_max, static_cast<cudaStream_t>(stream), ms_out, max_entries);
+}
+
+btas_status btas_batch_select_tiles(btas_batch_t *b, void *stream, int *mode, double *ms_out) {
+    if (!b) return bfail(BTAS_ERR_ARG, "btas_batch_select_tiles: NULL batch");
+    if (b->reqs.empty()) {
+        if (mode) *mode = 0;
+        return BTAS_OK;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // mode 0: the table (and BTAS_BATCH_TILE), 1: 128 x 128, 2: 64 x 64 for every instance
+    const int force[3] = {0, kBT, kBTSmall};
+    double ms[3] = {0, 0, 0};
+    btas_status r = BTAS_OK;
+    for (int m = 0; m < 3 && r == BTAS_OK; ++m) {
+        b->force_tile = force[m];
+        b->dirty = true;
+        float best = 1e30f;
+        for (int rep = 0; rep < 4 && r == BTAS_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            r = btas_batch_launch(b, st);
+            cudaEventRecord(e1, st);
+            if (r == BTAS_OK) r = btas_batch_wait(b, st);
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) best = std::min(best, t);
+        }
+        ms[m] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != BTAS_OK) {
+        b->force_tile = 0;
+        b->dirty = true;
+        return r;
+    }
+    int best = 0;
+    for (int m = 1; m < 3; ++m)
+        if (ms[m] < ms[best]) best = m;
+    b->force_tile = force[best];
+    b->dirty = true;  // the next launch plans with the chosen tiles
+    if (mode) *mode = best;
+    if (ms_out)
+        for (int m = 0; m < 3; ++m) ms_out[m] = ms[m];
+    return BTAS_OK;
+}
+
+int btas_batch_tile(int kind, int64_t n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || kind < 0 || kind > 2 || n < 1) return 0;
+    return table_tile(dev, kind, n);
+}
+
+void btas_batch_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    g_tile_table.clear();
+}
+
 btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *counts, int slots) {
     if (!b || !(b->flags & BTAS_BATCH_PROFILE))
         return bfail(BTAS_ERR_ARG, "btas_batch_profile: batch created without BTAS_BATCH_PROFILE");
@@ -666,3 +812,118 @@ btas_status btas_batch_profile(btas_batch_t *b, uint64_t *cycles, uint64_t *coun
 }
 
 }  // extern "C"
+
+namespace btas {
+
+// For each kind and size bucket of 32 vertices (rows) up to n_max: one
+// synthetic batch of three sizes in the bucket, with enough instances that
+// every level holds several waves of 128 x 128 tasks (4 waves of the
+// persistent grid per squaring level, 8 for products) -- the regime of a
+// large batch, where per-term speed and padding decide, not the number of
+// tasks -- timed (best of 3 graph-captured launches, after one warm-up)
+// with the 128 x 128 and with the 64 x 64 output tile.  The small tile is
+// kept only if it is at least 3 % faster.
+btas_status batch_tune_impl(int64_t n_max, cudaStream_t st, double *ms_out, int max_entries) {
+    if (n_max < 1 || n_max > 2048) return bfail(BTAS_ERR_ARG, "btas_batch_tune: n_max must be in [1, 2048]");
+    if (max_entries < 0 || (max_entries > 0 && !ms_out)) return bfail(BTAS_ERR_ARG, "btas_batch_tune: ms_out");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return bfail(BTAS_ERR_CUDA, "btas_batch_tune: cudaGetDevice failed");
+    const int buckets = (int)((n_max + 31) / 32);
+    int per_sm = 0;
+    DeviceInfo di{};
+    if (batch_kernel_prepare(&per_sm) != cudaSuccess || !current_device_info(&di))
+        return bfail(BTAS_ERR_CUDA, "btas_batch_tune: device query failed");
+    const double grid = std::max(1, per_sm) * (double)di.sms;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    btas_status result = BTAS_OK;
+    for (int kind = 0; kind < 3 && result == BTAS_OK; ++kind) {
+        for (int bk = 0; bk < buckets && result == BTAS_OK; ++bk) {
+            std::vector<long long> sizes;
+            for (int off : {8, 20, 32}) {
+                const long long n = std::min<long long>(n_max, 32LL * bk + off);
+                if (n >= 3 && (sizes.empty() || sizes.back() != n)) sizes.push_back(n);
+            }
+            if (sizes.empty()) continue;
+            // instances per size: several waves of 128 x 128 tasks per level
+            std::vector<int> count;
+            size_t bytes = 0;
+            for (long long n : sizes) {
+                const double tiles = (double)((n + kBT - 1) / kBT) * ((n + kBT - 1) / kBT);
+                const double waves = kind == 0 ? 4.0 : 8.0;
+                const int c = (int)std::max(2.0, std::min(4096.0, std::ceil(waves * grid / (sizes.size() * tiles))));
+                count.push_back(c);
+                bytes += (size_t)c * (kind == 0 ? 2 : 3) * al256((size_t)n * n * 4);
+            }
+            void *buf = nullptr;
+            if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+                result = bfail(BTAS_ERR_NOMEM, "btas_batch_tune: allocation failed");
+                break;
+            }
+            char *p = static_cast<char *>(buf);
+            std::vector<std::pair<long long, char *>> mats;
+            unsigned long long seed = 0x170104733ULL + 977ULL * (kind * 64 + bk);
+            for (size_t z = 0; z < sizes.size(); ++z)
+                for (int c = 0; c < count[z]; ++c) {
+                    const long long n = sizes[z];
+                    const size_t mb = al256((size_t)n * n * 4);
+                    const int inputs = kind == 0 ? 1 : 2;
+                    for (int q = 0; q < inputs; ++q) {
+                        const long long blocks = std::min<long long>(1024, (n * n + 255) / 256);
+                        tile_tune_fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<uint32_t *>(p + q * mb),
+                                                                               n, kind, seed++);
+                        note_launch();
+                    }
+                    mats.push_back({n, p});
+                    p += (kind == 0 ? 2 : 3) * mb;
+                }
+            double ms[2] = {0, 0};
+            for (int ti = 0; ti < 2 && result == BTAS_OK; ++ti) {
+                btas_batch_t *b = nullptr;
+                btas_batch_create(&b, 0);
+                b->force_tile = ti == 0 ? kBT : kBTSmall;
+                for (auto &m : mats) {
+                    const long long n = m.first;
+                    const size_t mb = al256((size_t)n * n * 4);
+                    if (kind == 0)
+                        btas_batch_add_apsp(b, n, reinterpret_cast<const int32_t *>(m.second),
+                                            reinterpret_cast<int32_t *>(m.second + mb));
+                    else
+                        btas_batch_add_gemm(b, kind == 1 ? BTAS_MINPLUS : BTAS_MAXPLUS, kind == 1 ? BTAS_I32 : BTAS_F32,
+                                            n, n, n, m.second, n, m.second + mb, n, m.second + 2 * mb, n);
+                }
+                float best = 1e30f;
+                for (int rep = 0; rep < 4 && result == BTAS_OK; ++rep) {
+                    cudaEventRecord(e0, st);
+                    result = btas_batch_launch(b, st);
+                    cudaEventRecord(e1, st);
+                    if (result == BTAS_OK) result = btas_batch_wait(b, st);
+                    float t = 0;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0) best = std::min(best, t);
+                }
+                ms[ti] = best;
+                btas_batch_destroy(b);
+            }
+            cudaStreamSynchronize(st);
+            cudaFree(buf);
+            if (result != BTAS_OK) break;
+            const int choice = ms[1] < 0.97 * ms[0] ? kBTSmall : kBT;
+            {
+                std::lock_guard<std::mutex> lk(g_tile_mu);
+                g_tile_table[std::make_tuple(dev, kind, bk)] = choice;
+            }
+            const int slot = kind * buckets + bk;
+            if (2 * slot + 1 < max_entries) {
+                ms_out[2 * slot] = ms[0];
+                ms_out[2 * slot + 1] = ms[1];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return result;
+}
+
+}  // namespace btas

@@ -7,7 +7,8 @@
 
 namespace btas {
 
-constexpr int kBT = 128;  // task tile edge
+constexpr int kBT = 128;  // task tile edge (level-0 transposes, and the default output tile)
+constexpr int kBTSmall = 64;  // the smaller output tile an instance can take instead
 
 enum TaskType : int { kTaskTranspose = 0, kTaskApsp = 1, kTaskGemm = 2, kTaskCopy = 3, kTaskSquare = 4 };
 enum InstKind : int { kInstApsp = 0, kInstGemm = 1, kInstSquare = 2 };
@@ -19,6 +20,7 @@ enum InstKind : int { kInstApsp = 0, kInstGemm = 1, kInstSquare = 2 };
 // at changed_ptr.
 struct BInst {
     int kind, sr, dtype;
+    int tile;             // output tile edge of the level >= 1 tasks: kBT or kBTSmall (0 = kBT)
     int m, n, k;
     int levels;           // APSP: S (>= 1); GEMM / square: 1
     int tiles_m, tiles_n; // output tiles
@@ -43,8 +45,13 @@ struct BInst {
     uint32_t *Ad0, *Ad1;
     uint16_t *U0, *U1;
     long long ldu;
-    int use_u16;          // APSP: packed squarings allowed; square: run this one packed
+    int use_u16;          // APSP: packed squarings allowed; square: 1 = run this one packed,
+                          // 2 = decide on the device from *maxfin_in (packed when
+                          // 2 * max < 0x7FFF; level-0 transposes then also write the
+                          // 16-bit forms of the input into Ad0 / U0)
     int *maxfin_ptr;      // square: atomicMax of the largest finite output
+    const int *maxfin_in; // square with use_u16 == 2: largest finite entry of the input,
+                          // written before the launch
 };
 
 struct BatchParams {

@@ -349,7 +349,9 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
     const bool accumulate = (semiring & BTAS_GEMM_ACCUMULATE) != 0;
     const bool trans_b = (semiring & BTAS_GEMM_TRANS_B) != 0;
     const bool packed = (semiring & BTAS_GEMM_PACKED) != 0;
-    if (semiring & ~(0xff | BTAS_GEMM_ACCUMULATE | BTAS_GEMM_TRANS_B | BTAS_GEMM_NO_CARRIER | BTAS_GEMM_PACKED))
+    const bool checked = (semiring & BTAS_GEMM_CHECKED) != 0;
+    if (semiring & ~(0xff | BTAS_GEMM_ACCUMULATE | BTAS_GEMM_TRANS_B | BTAS_GEMM_NO_CARRIER | BTAS_GEMM_PACKED |
+                     BTAS_GEMM_CHECKED))
         return fail(BTAS_ERR_ARG, "btas_gemm: unknown flag bits 0x%x", semiring);
     if (sr != BTAS_MINPLUS && sr != BTAS_MAXPLUS) return fail(BTAS_ERR_ARG, "btas_gemm: unknown semiring %d", sr);
     if (dtype != BTAS_I32 && dtype != BTAS_F32 && dtype != BTAS_U16)
@@ -364,6 +366,8 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
     if (!C || (k > 0 && (!A || !B))) return fail(BTAS_ERR_ARG, "btas_gemm: NULL pointer");
     if (dtype == BTAS_U16 && sr != BTAS_MINPLUS)
         return fail(BTAS_ERR_UNSUPPORTED, "btas_gemm: BTAS_U16 is min-plus only");
+    if (checked && dtype == BTAS_U16)
+        return fail(BTAS_ERR_UNSUPPORTED, "btas_gemm: BTAS_GEMM_CHECKED takes BTAS_I32 or BTAS_F32");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     if (dtype == BTAS_U16) {
@@ -392,6 +396,28 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
         return BTAS_OK;
     }
 
+    // BTAS_GEMM_CHECKED: count the operand entries outside the domain on the
+    // device; a call that finds any leaves C unwritten, and btas_sync_status
+    // reports it.  chk[0] = this call's count, chk[1] = skip word of the
+    // product kernels.
+    Workspace chk_ws(st);
+    int *chk = nullptr;
+    unsigned long long *status = nullptr;
+    if (checked) {
+        status = device_status_words();
+        if (!status) return fail(BTAS_ERR_CUDA, "btas_gemm: device status words unavailable");
+        BTAS_CUDA(chk_ws.alloc(256), "workspace alloc");
+        chk = static_cast<int *>(chk_ws.p);
+        BTAS_CUDA(cudaMemsetAsync(chk, 0, 8, st), "memset");
+        const int is_f = dtype == BTAS_F32 ? 1 : 0;
+        BTAS_CUDA(launch_domain_check(A, lda, (int)m, (int)k, is_f, sr, chk, status, st), "domain check");
+        BTAS_CUDA(launch_domain_check(B, ldb, trans_b ? (int)n : (int)k, trans_b ? (int)k : (int)n, is_f, sr, chk,
+                                      status, st),
+                  "domain check");
+        if (accumulate)
+            BTAS_CUDA(launch_domain_check(C, ldc, (int)m, (int)n, is_f, sr, chk, status, st), "domain check");
+    }
+
     Workspace ws(st);
     const void *Bt = B;
     long long ldbt = ldb;
@@ -413,8 +439,10 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
         uint16_t *bu = reinterpret_cast<uint16_t *>(base + s_state + s_ad);
         uint16_t *cu = reinterpret_cast<uint16_t *>(base + s_state + s_ad + s_bu);
         BTAS_CUDA(launch_pack_prepare(sr, (int)m, (int)n, (int)k, static_cast<const int *>(A), lda,
-                                      static_cast<const int *>(B), ldb, trans_b, pack_state, adup, bu, ldbu, st),
+                                      static_cast<const int *>(B), ldb, trans_b, pack_state, adup, bu, ldbu, st,
+                                      chk),
                   "packed operands");
+        if (checked) BTAS_CUDA(launch_checked_gate(chk, pack_state, chk + 1, status, st), "checked gate");
         U16Args a{};
         a.m = (int)m; a.n = (int)n; a.k = (int)k;
         a.B = bu; a.ldb = ldbu;
@@ -445,7 +473,27 @@ btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k, 
     a.vec_a = aligned16(A, lda);
     a.vec_b = aligned16(Bt, ldbt);
     a.bypass = pack_state ? pack_state + kPackStateUse : nullptr;
+    if (checked) {
+        if (!pack_state) BTAS_CUDA(launch_checked_gate(chk, nullptr, chk + 1, status, st), "checked gate");
+        a.bypass = chk + 1;
+    }
     return run_nt(dtype, sr, a, st);
+}
+
+btas_status btas_sync_status(void *stream, int64_t *out_of_domain, int64_t *calls) {
+    unsigned long long *status = device_status_words();
+    if (!status) return fail(BTAS_ERR_CUDA, "btas_sync_status: device status words unavailable");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long h[2] = {0, 0};
+    BTAS_CUDA(cudaMemcpyAsync(h, status, sizeof h, cudaMemcpyDeviceToHost, st), "status read");
+    BTAS_CUDA(cudaStreamSynchronize(st), "synchronise");
+    BTAS_CUDA(cudaMemsetAsync(status, 0, sizeof h, st), "status clear");
+    if (out_of_domain) *out_of_domain = (int64_t)h[0];
+    if (calls) *calls = (int64_t)h[1];
+    if (h[0] != 0)
+        return fail(BTAS_ERR_ARG, "btas_sync_status: %llu checked product(s) found %llu operand entries outside the "
+                    "domain and left C unwritten", h[1], h[0]);
+    return BTAS_OK;
 }
 
 int64_t btas_packed_products(void) {

@@ -52,6 +52,18 @@ struct TuneChoice {
 bool tune_choice(int sr, int dtype, long long m, long long n, long long k, cudaStream_t st, TuneChoice *out);
 
 // ---- auxiliary kernels (aux.cu)
+// Per-device status words of asynchronous checks (allocated on first use):
+// [0] entries outside the domain found by BTAS_GEMM_CHECKED products,
+// [1] checked products that found any.  Read and cleared by btas_sync_status.
+unsigned long long *device_status_words();
+// BTAS_GEMM_CHECKED: count the entries of X outside the product's domain into
+// *count and status[0].
+cudaError_t launch_domain_check(const void *X, long long ld, int rows, int cols, int is_float, int sr, int *count,
+                                unsigned long long *status, cudaStream_t st);
+// *skip = (*count != 0) || packed path chosen (pack_state may be null); a
+// violation counts the call in status[1].
+cudaError_t launch_checked_gate(const int *count, const int *pack_state, int *skip, unsigned long long *status,
+                                cudaStream_t st);
 // dst (cols x rows, ldd) = transpose of src (rows x cols, lds); 4-byte elements.
 // mode: 0 = copy, 1 = int32 -> fp32 carrier (INF -> +inf, -INF -> -inf),
 // 2 = fp32 carrier -> int32 (inverse).
@@ -170,12 +182,14 @@ cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaSt
 // ---- exact packed path for int32 products (pack.cu).  Device state words:
 // [0] packed? [1] offset of A [2] offset of B [3] !packed [4..7] ranges
 // and out-of-domain count.  All launches are stream-ordered; the choice is
-// made on the device.
+// made on the device.  extra_bad (optional, device): a count of entries
+// outside the domain from the caller's own check; non-zero withdraws the
+// packed path.
 constexpr int kPackStateInts = 16;
 constexpr int kPackStateUse = 0, kPackStateNotUse = 3;
 cudaError_t launch_pack_prepare(int sr, int m, int n, int k, const int *A, long long lda, const int *B, long long ldb,
                                 bool trans_b, int *state, uint32_t *adup, uint16_t *bu, long long ldbu,
-                                cudaStream_t st);
+                                cudaStream_t st, const int *extra_bad = nullptr);
 cudaError_t launch_pack_finish(int sr, int m, int n, const uint16_t *cu, long long ldcu, const int *state, int *C,
                                long long ldc, bool accumulate, cudaStream_t st);
 long long packed_products(int device);

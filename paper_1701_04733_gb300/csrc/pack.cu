@@ -68,12 +68,14 @@ __global__ void pack_range_kernel(const int *__restrict__ X, long long rows, lon
     }
 }
 
-__global__ void pack_decide_kernel(int sr, int *state) {
+// extra_bad (optional): entries outside the domain found by the caller's
+// own check (BTAS_GEMM_CHECKED); any withdraws the packed path.
+__global__ void pack_decide_kernel(int sr, int *state, const int *extra_bad) {
     if (threadIdx.x != 0) return;
     const bool any_a = state[kLoA] <= state[kHiA], any_b = state[kLoB] <= state[kHiB];
     const long long ra = any_a ? (long long)state[kHiA] - state[kLoA] : 0;
     const long long rb = any_b ? (long long)state[kHiB] - state[kLoB] : 0;
-    const int use = state[kBad] == 0 && ra + rb < BTAS_INF_U16;
+    const int use = state[kBad] == 0 && (extra_bad == nullptr || *extra_bad == 0) && ra + rb < BTAS_INF_U16;
     state[kUse] = use;
     state[kNotUse] = !use;
     state[kOffA] = any_a ? (sr == kMin ? state[kLoA] : state[kHiA]) : 0;
@@ -157,7 +159,7 @@ unsigned grid_of(long long total) {
 
 cudaError_t launch_pack_prepare(int sr, int m, int n, int k, const int *A, long long lda, const int *B, long long ldb,
                                 bool trans_b, int *state, uint32_t *adup, uint16_t *bu, long long ldbu,
-                                cudaStream_t st) {
+                                cudaStream_t st, const int *extra_bad) {
     const int ident = sr == kMin ? kInfI32 : kNinfI32;
     pack_init_kernel<<<1, 32, 0, st>>>(state);
     pack_range_kernel<<<grid_of((long long)m * k), 256, 0, st>>>(A, m, k, lda, ident, state + kLoA, state + kHiA,
@@ -168,7 +170,7 @@ cudaError_t launch_pack_prepare(int sr, int m, int n, int k, const int *A, long 
     else
         pack_range_kernel<<<grid_of((long long)k * n), 256, 0, st>>>(B, k, n, ldb, ident, state + kLoB,
                                                                     state + kHiB, state + kBad);
-    pack_decide_kernel<<<1, 32, 0, st>>>(sr, state);
+    pack_decide_kernel<<<1, 32, 0, st>>>(sr, state, extra_bad);
     const long long ldad = (k + 3) & ~3LL;
     pack_a_kernel<<<grid_of((long long)m * k), 256, 0, st>>>(A, lda, m, k, sr, state, adup, ldad);
     if (trans_b) {

@@ -9,20 +9,35 @@
 //             on a copy stream;
 //   step    - active requests contribute their next unit of work (a
 //             product: the whole product; APSP: its next squaring), oldest
-//             first, up to a work cap per step (default 3e10 terms, about
-//             2 ms; BTAS_SERVER_STEP_TERMS), and these units run together in
+//             first, up to a work cap per step (default 1.5e10 terms, about
+//             1 ms; BTAS_SERVER_STEP_TERMS), and these units run together in
 //             ONE launch of the persistent tile-task kernel
-//             (batch_kernel.cuh); short steps let finished requests leave
-//             and new ones join often.  An APSP request with n <= 1792 is
-//             one unit instead: the whole solve, by the one-block or the
-//             cooperative kernel, launched after the persistent kernel;
+//             (batch_kernel.cuh).  A unit larger than what is left of the
+//             cap contributes a chunk of its 128 x 128 output tiles and
+//             continues in the next step, so every step stays short; units
+//             below 5 % of the cap always join.  Short steps let finished
+//             requests leave and new ones join often.  An APSP request with
+//             n <= 1792 is one unit instead when the rest of the work is
+//             light: the whole solve, by the one-block or the cooperative
+//             kernel, launched after the persistent kernel;
 //   retire  - a product is finished after its step; an APSP solve after its
 //             last squaring or as soon as a squaring changed nothing (early
 //             exit, same result).  Its result is copied back on the copy
 //             stream and its memory returned once the copy has completed.
-// Requests that arrive while a step runs are admitted for the next step, so
-// their work overlaps with the squarings of requests already in flight
-// (iteration-level continuous batching).  The arithmetic is the library's
+// Requests too large for one launch of either kind of kernel to bring any
+// batching gain -- APSP above the cooperative kernel's size limit, products
+// of more than BTAS_SERVER_BULK_TERMS terms (default 4e9) -- take a second
+// lane instead: a bulk thread runs them one at a time, in arrival order,
+// through the library's single calls (btas_apsp, btas_gemm) on a stream of
+// higher priority than the step loop's: the large requests set the latency
+// tail, and the small ones, batched in the step loop, never queue behind
+// them but take the SMs the large kernels leave free.  While the bulk lane
+// is busy the step loop does not use the cooperative whole-solve kernel,
+// whose grid must be co-resident on every SM.
+// Requests that arrive while a step runs are admitted at once (their device
+// memory is taken on the copy stream, so their input copies overlap the
+// step) and join the next step, so their work overlaps with the squarings
+// of requests already in flight (iteration-level continuous batching).  The arithmetic is the library's
 // single-call arithmetic: every result is bit-identical to the one computed
 // alone.
 #include <algorithm>
@@ -77,11 +92,17 @@ struct Req {
     double t_submit = 0, t_admit = 0, t_done = 0;
     int state = kQueued;
     int steps = 0;
+    int tile_next = 0;   // output tiles of the current unit done in earlier steps
+    int take = 0;        // output tiles of the current unit in this step
     bool finished = false;
     bool whole = false;  // APSP solved in one unit (small / cooperative kernel) in this step
+    bool bulk = false;   // large request: runs in the bulk lane through the single calls
     bool bad = false;    // W outside the domain (checked on the device before the first squaring): the request fails
     // terms of this request's next unit of work
     double unit_terms() const { return kind == 0 ? (double)n * n * n : (double)m * n * k; }
+    int unit_tiles() const { return ((m + 127) / 128) * ((n + 127) / 128); }
+    double tile_terms() const { return 128.0 * 128.0 * (double)k; }
+    double remaining_terms() const { return unit_terms() * (1.0 - (double)tile_next / unit_tiles()); }
 };
 
 }  // namespace
@@ -93,14 +114,18 @@ struct btas_server_t {
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Req *> queue;             // waiting for admission
+    std::deque<Req *> bulk_queue;        // large requests waiting for the bulk lane
     std::vector<Req *> active;           // admitted, work remaining
     std::vector<Req *> retiring;         // result copy in flight
     std::map<int64_t, Req *> all;        // every request ever submitted
     int64_t next_id = 1;
     bool stop = false;
-    std::thread worker;
+    std::thread worker, bulk_worker;
     std::chrono::steady_clock::time_point t0;
-    cudaStream_t compute = nullptr, copy = nullptr;
+    cudaStream_t compute = nullptr, copy = nullptr, bulk = nullptr;
+    double bulk_terms = 4e9;   // products above this many terms take the bulk lane
+    int64_t bulk_runs = 0;
+    bool bulk_busy = false;    // the bulk lane holds a request
     // per-step device/pinned staging (double-buffered by step parity)
     void *d_stage[2] = {nullptr, nullptr};
     void *h_stage[2] = {nullptr, nullptr};
@@ -112,10 +137,10 @@ struct btas_server_t {
     int grid = 0;
     long long timeout_cycles = 0;
     int step_parity = 0;
-    double step_terms = 3e10;  // work cap of one step (terms), keeps steps short
+    double step_terms = 1.5e10;  // work cap of one step (terms), keeps steps short
     int allow_u16 = 1;         // BTAS_SERVER_NO_U16=1 keeps every squaring in int32
     int allow_whole = 1;       // BTAS_SERVER_NO_WHOLE=1 runs every APSP squaring by squaring
-    double whole_below = 4e9;  // whole solves only when the other pending work is below this (terms)
+    double whole_below = 1.5e10;  // whole solves only when the other pending work is below this (terms)
     int64_t steps = 0;
     int64_t units = 0;
     int64_t completed = 0;
@@ -153,14 +178,11 @@ size_t footprint(const Req &r) {
 }
 
 // Allocate the request's device block and start its input copies.
+// The block is taken on the copy stream, so the copies start at once even
+// while a step runs on the compute stream; the compute stream waits for
+// in_ready before it touches the block.
 bool admit(btas_server_t *sv, Req *r) {
-    if (ws_alloc(reinterpret_cast<void **>(&r->dmem), r->bytes, sv->compute) != cudaSuccess) return false;
-    // the copy stream must see the allocation
-    cudaEvent_t ev;
-    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    cudaEventRecord(ev, sv->compute);
-    cudaStreamWaitEvent(sv->copy, ev, 0);
-    cudaEventDestroy(ev);
+    if (ws_alloc(reinterpret_cast<void **>(&r->dmem), r->bytes, sv->copy) != cudaSuccess) return false;
     char *p = r->dmem;
     if (r->kind == 0) {
         const long long ld = r4(r->n);
@@ -218,19 +240,41 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
     // oldest admitted requests first, until the step's work cap (at least one)
     units.clear();
     double terms = 0, pending = 0;
-    for (Req *r : sv->active) pending += r->unit_terms();
+    for (Req *r : sv->active) pending += r->remaining_terms();
+    const double small = 0.05 * sv->step_terms;
+    bool bulk_busy;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        bulk_busy = sv->bulk_busy || !sv->bulk_queue.empty();
+    }
     for (Req *r : sv->active) {
         // an APSP request that fits the one-block or cooperative kernel is
         // solved whole, in one unit, instead of one squaring per step -- when
-        // the rest of the step is light (at low load).  Under load its
-        // squarings are batched with the other requests' work instead, which
-        // keeps the GPU busier than a whole solve's grid barriers do.
-        r->whole = sv->allow_whole && r->kind == 0 && r->s == 1 && r->n <= apsp_mid_max_n() &&
-                   pending - r->unit_terms() < sv->whole_below;
-        const double w = r->whole ? r->unit_terms() * std::min(r->S, 6) : r->unit_terms();
-        if (!units.empty() && terms + w > sv->step_terms) continue;
+        // the rest of the work is light.  Under load its squarings are
+        // batched with the other requests' work instead, which keeps the GPU
+        // busier than a whole solve's grid barriers do.
+        r->whole = sv->allow_whole && r->kind == 0 && r->s == 1 && r->tile_next == 0 && r->n <= apsp_mid_max_n() &&
+                   pending - r->unit_terms() < sv->whole_below && (r->n <= apsp_small_limit() || !bulk_busy);
+        r->take = 0;
+        if (r->whole) {
+            const double w = r->unit_terms() * std::min(r->S, 6);
+            if (!units.empty() && terms + w > sv->step_terms && w >= small) continue;
+            units.push_back(r);
+            terms += w;
+            continue;
+        }
+        // the rest of the current unit, or the chunk of its output tiles that
+        // fits what is left of the cap; small units always join
+        const int rem = r->unit_tiles() - r->tile_next;
+        const double tt = r->tile_terms(), rem_terms = rem * tt, left = sv->step_terms - terms;
+        int take;
+        if (rem_terms <= left || rem_terms < small) take = rem;
+        else if (left >= tt) take = std::min(rem, std::max(1, (int)(left / tt)));
+        else if (units.empty()) take = 1;
+        else continue;
+        r->take = take;
         units.push_back(r);
-        terms += w;
+        terms += take * tt;
     }
     if (units.empty()) return 0;
     // batched units first (largest first), whole solves after them
@@ -250,6 +294,7 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
         I.done_base = 2 * i;
         I.flag_base = 2 * i;
         I.levels = 1;
+        const bool first_chunk = r->tile_next == 0;
         if (r->kind == 0) {
             const int s = r->s;
             I.kind = kInstSquare;
@@ -265,16 +310,24 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
             I.Q1 = s < r->S ? r->Q[s & 1] : nullptr;
             I.ldq = r->ldp;
             I.changed_ptr = r->dflag + s;
-            if (s == 1) {
+            if (s == 1 && first_chunk) {
                 I.t0_rows = I.t0_cols = r->n;  // transpose W into Q[0] first
-                // the weight domain, checked on the device; a violation fails the request
+                // the weight domain, checked on the device; a violation fails the
+                // request.  The scan also finds W's largest weight.
                 if (launch_apsp_scan(static_cast<const int *>(r->P[0]), r->n, r->dflag + 2 * r->S + 4, sv->compute,
                                      r->ldp) != cudaSuccess)
                     return -1;
             }
             // packed squaring when every finite entry of D_{s-1} is < 0x7FFF / 2
-            // (exact); the forms of D_s are written for the next squaring
-            I.use_u16 = (s >= 2 && r->last_max >= 0 && 2LL * r->last_max < BTAS_INF_U16 && sv->allow_u16) ? 1 : 0;
+            // (exact); the forms of D_s are written for the next squaring.  For
+            // the first squaring the device decides from W's largest weight (the
+            // level-0 transposes also write W's 16-bit forms).
+            if (s == 1) {
+                I.use_u16 = sv->allow_u16 ? 2 : 0;
+                I.maxfin_in = r->dflag + 2 * r->S + 4;
+            } else {
+                I.use_u16 = (r->last_max >= 0 && 2LL * r->last_max < BTAS_INF_U16 && sv->allow_u16) ? 1 : 0;
+            }
             I.Ad0 = r->Ad[(s - 1) & 1];
             I.U0 = r->U[(s - 1) & 1];
             I.Ad1 = s < r->S ? r->Ad[s & 1] : nullptr;
@@ -298,8 +351,10 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
             I.ldc = r->ldc_d;
             I.Q0 = r->dBt;
             I.ldq = r->ldq;
-            I.t0_rows = r->k;
-            I.t0_cols = r->n;
+            if (first_chunk) {  // B^T into Q0 with the first chunk
+                I.t0_rows = r->k;
+                I.t0_cols = r->n;
+            }
         }
         insts[i] = I;
     }
@@ -316,8 +371,10 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
                     for (int t = 0; t < nt; ++t) tasks.push_back(make_int4(kTaskTranspose, i, 0, t));
                 }
             } else {
+                // this step's chunk of the unit's output tiles
                 const int type = I.kind == kInstSquare ? kTaskSquare : kTaskGemm;
-                for (int t = 0; t < I.tiles_m * I.tiles_n; ++t) tasks.push_back(make_int4(type, i, 1, t));
+                const int t0 = units[i]->tile_next, t1 = t0 + units[i]->take;
+                for (int t = t0; t < t1; ++t) tasks.push_back(make_int4(type, i, 1, t));
             }
         }
     // staging: [counters (next, status, done[2*ninst], changed[2*ninst]) | insts | tasks]
@@ -435,40 +492,110 @@ void poll_retiring(btas_server_t *sv, bool block) {
     sv->cv.notify_all();
 }
 
+// The bulk lane: one large request at a time, in arrival order and within
+// the budget, through the library's single calls on the bulk stream.  The
+// result is the single call's result by construction.
+void bulk_loop(btas_server_t *sv) {
+    cudaSetDevice(sv->device);
+    for (;;) {
+        Req *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait(lk, [&] {
+                return (sv->stop && sv->bulk_queue.empty()) ||
+                       (!sv->bulk_queue.empty() &&
+                        sv->used + (long long)sv->bulk_queue.front()->bytes <= sv->budget);
+            });
+            if (sv->bulk_queue.empty()) break;
+            r = sv->bulk_queue.front();
+            sv->bulk_queue.pop_front();
+            sv->bulk_busy = true;
+            sv->used += (long long)r->bytes;
+            r->state = kRunning;
+            r->t_admit = sv->now();
+        }
+        const cudaStream_t st = sv->bulk;
+        bool ok = true;
+        void *dmem = nullptr;
+        if (r->kind == 0) {
+            const size_t nn = (size_t)r->n * r->n * 4;
+            ok = ws_alloc(&dmem, 2 * a256(nn), st) == cudaSuccess;
+            if (ok) {
+                int32_t *W = static_cast<int32_t *>(dmem);
+                int32_t *D = reinterpret_cast<int32_t *>(static_cast<char *>(dmem) + a256(nn));
+                ok = cudaMemcpyAsync(W, r->hA, nn, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                     btas_apsp(r->n, W, D, st) == BTAS_OK &&
+                     cudaMemcpyAsync(r->hC, D, nn, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+            }
+        } else {
+            const size_t ba = (size_t)r->m * r->k * 4, bb = (size_t)r->k * r->n * 4, bc = (size_t)r->m * r->n * 4;
+            ok = ws_alloc(&dmem, a256(ba) + a256(bb) + a256(bc), st) == cudaSuccess;
+            if (ok) {
+                char *p = static_cast<char *>(dmem);
+                void *A = p, *B = p + a256(ba), *C = p + a256(ba) + a256(bb);
+                ok = cudaMemcpyAsync(A, r->hA, ba, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                     cudaMemcpyAsync(B, r->hB, bb, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                     btas_gemm(r->sr, r->dtype, r->m, r->n, r->k, A, r->k, B, r->n, C, r->n, st) == BTAS_OK &&
+                     cudaMemcpyAsync(r->hC, C, bc, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+            }
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess) ok = false;
+        if (dmem) ws_free(dmem, st);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r->t_done = sv->now();
+            r->state = ok ? kDone : kFailed;
+            sv->used -= (long long)r->bytes;
+            ++sv->completed;
+            ++sv->bulk_runs;
+            sv->bulk_busy = false;
+        }
+        sv->cv.notify_all();
+    }
+}
+
+// Admission: queued requests in arrival order while their device footprint
+// fits the budget.  Worker thread only.
+void admit_queued(btas_server_t *sv, bool wait_if_idle) {
+    std::vector<Req *> admitted;
+    {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        if (wait_if_idle && sv->queue.empty() && sv->active.empty() && sv->retiring.empty() && !sv->stop)
+            sv->cv.wait_for(lk, std::chrono::milliseconds(2));
+        while (!sv->queue.empty() && sv->used + (long long)sv->queue.front()->bytes <= sv->budget) {
+            Req *r = sv->queue.front();
+            sv->queue.pop_front();
+            sv->used += (long long)r->bytes;
+            admitted.push_back(r);
+        }
+    }
+    for (Req *r : admitted) {
+        const double t = sv->now();
+        const bool ok = admit(sv, r);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r->t_admit = t;
+            if (!ok) {
+                r->state = kFailed;
+                sv->used -= (long long)r->bytes;
+            } else {
+                r->state = kRunning;
+            }
+        }
+        if (ok) sv->active.push_back(r);
+    }
+    if (!admitted.empty()) sv->cv.notify_all();
+}
+
 void worker_loop(btas_server_t *sv) {
     cudaSetDevice(sv->device);
     std::vector<Req *> units;
     for (;;) {
-        // admission (FIFO within the budget)
-        std::vector<Req *> admitted;
         {
-            std::unique_lock<std::mutex> lk(sv->mu);
-            if (sv->queue.empty() && sv->active.empty() && sv->retiring.empty()) {
-                if (sv->stop) break;
-                sv->cv.wait_for(lk, std::chrono::milliseconds(2));
-            }
-            while (!sv->queue.empty() && sv->used + (long long)sv->queue.front()->bytes <= sv->budget) {
-                Req *r = sv->queue.front();
-                sv->queue.pop_front();
-                sv->used += (long long)r->bytes;
-                admitted.push_back(r);
-            }
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (sv->stop && sv->queue.empty() && sv->active.empty() && sv->retiring.empty()) break;
         }
-        for (Req *r : admitted) {
-            const double t = sv->now();
-            const bool ok = admit(sv, r);
-            {
-                std::lock_guard<std::mutex> lk(sv->mu);
-                r->t_admit = t;
-                if (!ok) {
-                    r->state = kFailed;
-                    sv->used -= (long long)r->bytes;
-                } else {
-                    r->state = kRunning;
-                }
-            }
-            if (ok) sv->active.push_back(r);
-        }
+        admit_queued(sv, true);
         const int launched = launch_step(sv, units);
         poll_retiring(sv, false);
         if (launched < 0) {
@@ -476,11 +603,18 @@ void worker_loop(btas_server_t *sv) {
             break;
         }
         if (launched == 0) {
-            if (!sv->retiring.empty()) std::this_thread::sleep_for(std::chrono::microseconds(50));
+            // nothing to launch: result copies may still be in flight
+            if (!sv->retiring.empty()) std::this_thread::yield();
             continue;
         }
-        // wait for the step, then advance every unit
-        cudaEventSynchronize(sv->step_done[sv->step_parity ^ 1]);
+        // while the step runs: admit arrivals (their input copies overlap the
+        // step) and retire finished copies; then advance every unit
+        const cudaEvent_t step_ev = sv->step_done[sv->step_parity ^ 1];
+        while (cudaEventQuery(step_ev) == cudaErrorNotReady) {
+            admit_queued(sv, false);
+            poll_retiring(sv, false);
+            std::this_thread::yield();
+        }
         if (sv->h_flags[sv->flag_slots] != 0) sv->last_error = sv->h_flags[sv->flag_slots];
         for (int i = 0; i < (int)units.size(); ++i) {
             Req *r = units[i];
@@ -491,13 +625,21 @@ void worker_loop(btas_server_t *sv) {
                 r->bad = sv->h_flags[i] != 0 || (r->n > apsp_small_limit() && sv->h_flags[sv->flag_slots + 1 + i] != 0);
                 r->result_buf = 1;
                 r->s = r->S + 1;
-            } else if (r->kind == 0) {
-                const bool changed = sv->h_flags[i] != 0;
-                r->last_max = r->s < r->S ? sv->h_flags[sv->flag_slots + 1 + i] : -1;
-                r->result_buf = r->s & 1;
-                r->bad = r->s == 1 && sv->h_flags[2 * sv->flag_slots + 1 + i] != 0;
-                finished = r->bad || !changed || r->s >= r->S;
-                ++r->s;
+            } else {
+                // a unit that ran a chunk of its tiles continues in the next step
+                // (a domain violation ends the request at once)
+                const bool bad = r->kind == 0 && r->s == 1 && sv->h_flags[2 * sv->flag_slots + 1 + i] != 0;
+                r->tile_next += r->take;
+                if (!bad && r->tile_next < r->unit_tiles()) continue;
+                r->tile_next = 0;
+                if (r->kind == 0) {
+                    const bool changed = sv->h_flags[i] != 0;
+                    r->last_max = r->s < r->S ? sv->h_flags[sv->flag_slots + 1 + i] : -1;
+                    r->result_buf = r->s & 1;
+                    r->bad = bad;
+                    finished = r->bad || !changed || r->s >= r->S;
+                    ++r->s;
+                }
             }
             if (finished) {
                 r->finished = true;
@@ -525,10 +667,14 @@ btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, in
     sv->t0 = std::chrono::steady_clock::now();
     cudaGetDevice(&sv->device);
     int per_sm = 0, sms = 0;
+    // the bulk lane's stream gets the highest priority, the step loop's the lowest
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (batch_kernel_prepare(&per_sm) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&sv->compute, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&sv->copy, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithPriority(&sv->compute, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&sv->copy, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&sv->bulk, cudaStreamNonBlocking, prio_high) != cudaSuccess) {
         delete sv;
         return sfail(BTAS_ERR_CUDA, "btas_server_create: CUDA set-up failed");
     }
@@ -536,6 +682,7 @@ btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, in
     if (const char *e = getenv("BTAS_SERVER_STEP_TERMS")) sv->step_terms = atof(e) > 0 ? atof(e) : sv->step_terms;
     if (const char *e = getenv("BTAS_SERVER_NO_U16")) sv->allow_u16 = (*e && atoi(e) != 0) ? 0 : 1;
     if (const char *e = getenv("BTAS_SERVER_NO_WHOLE")) sv->allow_whole = (*e && atoi(e) != 0) ? 0 : 1;
+    if (const char *e = getenv("BTAS_SERVER_BULK_TERMS")) sv->bulk_terms = atof(e);
     sv->timeout_cycles = batch_timeout_cycles(sv->device);
     sv->flag_slots = 1 << 16;
     if (cudaMallocHost(reinterpret_cast<void **>(&sv->h_flags), (size_t)(3 * sv->flag_slots + 1) * 4) != cudaSuccess) {
@@ -547,6 +694,7 @@ btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, in
         cudaEventRecord(sv->step_done[q], sv->compute);
     }
     sv->worker = std::thread(worker_loop, sv);
+    sv->bulk_worker = std::thread(bulk_loop, sv);
     *out = sv;
     return BTAS_OK;
 }
@@ -562,13 +710,16 @@ static btas_status enqueue(btas_server_t *sv, Req *r, int64_t *ticket) {
         delete r;
         return sfail(BTAS_ERR_ARG, "btas_server: server is stopping");
     }
-    if ((int64_t)sv->active.size() + (int64_t)sv->queue.size() >= sv->flag_slots) {
+    if ((int64_t)sv->active.size() + (int64_t)sv->queue.size() + (int64_t)sv->bulk_queue.size() >= sv->flag_slots) {
         delete r;
         return sfail(BTAS_ERR_BUDGET, "btas_server: too many requests in flight");
     }
     r->id = sv->next_id++;
     r->t_submit = sv->now();
-    sv->queue.push_back(r);
+    // large requests take the bulk lane (BTAS_SERVER_BULK_TERMS <= 0 turns it off)
+    r->bulk = sv->bulk_terms > 0 && (r->kind == 0 ? r->n > apsp_mid_max_n() : r->unit_terms() > sv->bulk_terms);
+    if (r->bulk) sv->bulk_queue.push_back(r);
+    else sv->queue.push_back(r);
     sv->all[r->id] = r;
     if (ticket) *ticket = r->id;
     sv->cv.notify_all();
@@ -625,7 +776,7 @@ btas_status btas_server_wait_all(btas_server_t *sv, double timeout_s) {
     std::unique_lock<std::mutex> lk(sv->mu);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
     for (;;) {
-        bool busy = !sv->queue.empty();
+        bool busy = !sv->queue.empty() || !sv->bulk_queue.empty();
         for (auto &kv : sv->all)
             if (kv.second->state == kQueued || kv.second->state == kRunning) busy = true;
         if (!busy) break;
@@ -656,8 +807,10 @@ btas_status btas_server_destroy(btas_server_t *sv) {
     }
     sv->cv.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
+    if (sv->bulk_worker.joinable()) sv->bulk_worker.join();
     cudaStreamSynchronize(sv->compute);
     cudaStreamSynchronize(sv->copy);
+    cudaStreamSynchronize(sv->bulk);
     for (auto &kv : sv->all) {
         release(sv, kv.second);
         delete kv.second;
@@ -671,6 +824,7 @@ btas_status btas_server_destroy(btas_server_t *sv) {
     cudaStreamSynchronize(sv->copy);
     cudaStreamDestroy(sv->compute);
     cudaStreamDestroy(sv->copy);
+    cudaStreamDestroy(sv->bulk);
     delete sv;
     return BTAS_OK;
 }

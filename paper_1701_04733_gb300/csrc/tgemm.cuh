@@ -11,11 +11,13 @@
 // consecutive registers, which the paired instructions below consume without
 // register moves.
 //
-// CTA tile BM x BN x BK, 8 x 8 outputs per thread, warps of 4 x 8 threads
-// covering 32 x 64 outputs.  Thread (ty, tx) of warp (wm, wn) owns rows
-// wm*32 + 4*i + ty and columns wn*64 + 8*j + tx: for every fragment load the
-// warp reads 4 (A) or 8 (B) consecutive smem rows, and rows are padded to
-// BK + 4 words, so every 128-bit load is a single conflict-free wavefront.
+// CTA tile BM x BN x BK, TM x TN outputs per thread (8 x 8 for the product
+// kernels, 4 x 4 for the small task tile of the persistent kernel), warps
+// of 4 x 8 threads covering 4TM x 8TN outputs.  Thread (ty, tx) of warp
+// (wm, wn) owns rows wm*4TM + 4*i + ty and columns wn*8TN + 8*j + tx: for
+// every fragment load the warp reads 4 (A) or 8 (B) consecutive smem rows,
+// and rows are padded to BK + 4 words, so every 128-bit load is a single
+// conflict-free wavefront.
 // Tiles stream through a STAGES-deep cp.async ring (16-byte copies; edge
 // chunks are filled element-wise with the semiring's absorbing value).
 //
@@ -43,16 +45,18 @@ namespace btas {
 // MINB: CTAs per SM the register budget is sized for (1: <= 255 registers,
 // 2: <= 128).  FK: k depth of one register fragment (4 = 128-bit smem loads,
 // 2 = 64-bit loads and half the fragment registers).
-// UNR: unroll factor of the k-slice loop inside one smem stage.
-template <int BM_, int BN_, int BK_, int STAGES_, int MINB_ = 1, int FK_ = 4, int UNR_ = 2>
+// UNR: unroll factor of the k-slice loop inside one smem stage.  TM x TN:
+// outputs per thread.
+template <int BM_, int BN_, int BK_, int STAGES_, int MINB_ = 1, int FK_ = 4, int UNR_ = 2, int TM_ = 8, int TN_ = 8>
 struct TileCfg {
     static constexpr int BM = BM_, BN = BN_, BK = BK_, STAGES = STAGES_, MINB = MINB_, FK = FK_, UNR = UNR_;
-    static constexpr int WARPS_M = BM / 32, WARPS_N = BN / 64;
+    static constexpr int TM = TM_, TN = TN_;
+    static constexpr int WARPS_M = BM / (4 * TM), WARPS_N = BN / (8 * TN);
     static constexpr int kThreads = WARPS_M * WARPS_N * 32;
     static constexpr int kLd = BK + 4;
     static constexpr int kStageElems = (BM + BN) * kLd;
     static constexpr int kSmemBytes = STAGES * kStageElems * 4;
-    static_assert(BM % 32 == 0 && BN % 64 == 0 && BK % 8 == 0, "tile shape");
+    static_assert(BM % (4 * TM) == 0 && BN % (8 * TN) == 0 && BK % 8 == 0, "tile shape");
     static_assert(FK == 2 || FK == 4, "fragment depth");
 };
 
@@ -88,7 +92,7 @@ __device__ __forceinline__ void stage_rows(T *sm, const T *g, long long ldg, int
     }
 }
 
-// Register fragments: for each of the 8 rows (A) or 8 columns (B) of a
+// Register fragments: for each of the TM rows (A) or TN columns (B) of a
 // thread, FK consecutive k values.  Integer and scalar-fp32 variants view
 // them as 32-bit words; the f32x2 variant as FK/2 64-bit pairs.
 template <int FK>
@@ -117,33 +121,33 @@ __device__ __forceinline__ uint64_t pack64(uint32_t lo, uint32_t hi) {
     return d;
 }
 
-// One FK-deep k slice of the 8x8 register tile.
-template <int VAR, int SR, int NS, int FK>
+// One FK-deep k slice of the TM x TN register tile.
+template <int VAR, int SR, int NS, int FK, int TM, int TN>
 struct Step;
 
-template <int SR, int NS, int FK>
-struct Step<kI32Dpx, SR, NS, FK> {
-    static __device__ __forceinline__ void run(int (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
-                                               int) {
+template <int SR, int NS, int FK, int TM, int TN>
+struct Step<kI32Dpx, SR, NS, FK, TM, TN> {
+    static __device__ __forceinline__ void run(int (&acc)[TM][TN], const Frag32<FK> (&a)[TM],
+                                               const Frag32<FK> (&b)[TN], int) {
 #pragma unroll
         for (int q = 0; q < FK; ++q)
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = iaddsel<SR>((int)a[i].v[q], (int)b[j].v[q], acc[i][j]);
+                for (int j = 0; j < TN; ++j) acc[i][j] = iaddsel<SR>((int)a[i].v[q], (int)b[j].v[q], acc[i][j]);
     }
 };
 
-template <int SR, int NS, int FK>
-struct Step<kI32Mix, SR, NS, FK> {
-    static __device__ __forceinline__ void run(int (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
-                                               int one) {
+template <int SR, int NS, int FK, int TM, int TN>
+struct Step<kI32Mix, SR, NS, FK, TM, TN> {
+    static __device__ __forceinline__ void run(int (&acc)[TM][TN], const Frag32<FK> (&a)[TM],
+                                               const Frag32<FK> (&b)[TN], int one) {
 #pragma unroll
         for (int p = 0; p < FK / 2; ++p)
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < TN; ++j) {
                     const int a0 = (int)a[i].v[2 * p], a1 = (int)a[i].v[2 * p + 1];
                     const int b0 = (int)b[j].v[2 * p], b1 = (int)b[j].v[2 * p + 1];
                     if (j < NS) {
@@ -157,16 +161,16 @@ struct Step<kI32Mix, SR, NS, FK> {
     }
 };
 
-template <int SR, int NS, int FK>
-struct Step<kF32X2, SR, NS, FK> {
-    static __device__ __forceinline__ void run(float (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
-                                               int) {
+template <int SR, int NS, int FK, int TM, int TN>
+struct Step<kF32X2, SR, NS, FK, TM, TN> {
+    static __device__ __forceinline__ void run(float (&acc)[TM][TN], const Frag32<FK> (&a)[TM],
+                                               const Frag32<FK> (&b)[TN], int) {
 #pragma unroll
         for (int p = 0; p < FK / 2; ++p)
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < TN; ++j) {
                     const uint64_t s = fadd2(pack64(a[i].v[2 * p], a[i].v[2 * p + 1]),
                                              pack64(b[j].v[2 * p], b[j].v[2 * p + 1]));
                     float lo, hi;
@@ -177,16 +181,16 @@ struct Step<kF32X2, SR, NS, FK> {
 };
 
 // Two scalar RN adds + one 3-input min/max per k pair.
-template <int SR, int NS, int FK>
-struct Step<kF32Add2, SR, NS, FK> {
-    static __device__ __forceinline__ void run(float (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
-                                               int) {
+template <int SR, int NS, int FK, int TM, int TN>
+struct Step<kF32Add2, SR, NS, FK, TM, TN> {
+    static __device__ __forceinline__ void run(float (&acc)[TM][TN], const Frag32<FK> (&a)[TM],
+                                               const Frag32<FK> (&b)[TN], int) {
 #pragma unroll
         for (int p = 0; p < FK / 2; ++p)
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < TN; ++j) {
                     const float s0 = __fadd_rn(__uint_as_float(a[i].v[2 * p]), __uint_as_float(b[j].v[2 * p]));
                     const float s1 = __fadd_rn(__uint_as_float(a[i].v[2 * p + 1]), __uint_as_float(b[j].v[2 * p + 1]));
                     acc[i][j] = fsel3<SR>(acc[i][j], s0, s1);
@@ -194,16 +198,16 @@ struct Step<kF32Add2, SR, NS, FK> {
     }
 };
 
-template <int SR, int NS, int FK>
-struct Step<kF32Scalar, SR, NS, FK> {
-    static __device__ __forceinline__ void run(float (&acc)[8][8], const Frag32<FK> (&a)[8], const Frag32<FK> (&b)[8],
-                                               int) {
+template <int SR, int NS, int FK, int TM, int TN>
+struct Step<kF32Scalar, SR, NS, FK, TM, TN> {
+    static __device__ __forceinline__ void run(float (&acc)[TM][TN], const Frag32<FK> (&a)[TM],
+                                               const Frag32<FK> (&b)[TN], int) {
 #pragma unroll
         for (int q = 0; q < FK; ++q)
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
+                for (int j = 0; j < TN; ++j)
                     acc[i][j] = fsel2<SR>(acc[i][j], __fadd_rn(__uint_as_float(a[i].v[q]), __uint_as_float(b[j].v[q])));
     }
 };
@@ -296,7 +300,7 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
                                         void *Ct = nullptr, long long ldct = 0, uint32_t *Cd = nullptr,
                                         long long ldcd = 0, uint16_t *Cu = nullptr, long long ldcu = 0) {
     using T = typename VarTypes<VAR>::T;
-    constexpr int FK = Cfg::FK;
+    constexpr int FK = Cfg::FK, TM = Cfg::TM, TN = Cfg::TN;
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, LD = Cfg::kLd, ST = Cfg::STAGES;
     constexpr int NT = Cfg::kThreads;
     T *smem = reinterpret_cast<T *>(smem_raw);
@@ -309,15 +313,15 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
     const int warp = tid >> 5, lane = tid & 31;
     const int wm = warp / Cfg::WARPS_N, wn = warp % Cfg::WARPS_N;
     const int ty = lane >> 3, tx = lane & 7;
-    const int row_base = wm * 32 + ty;  // + 4*i
-    const int col_base = wn * 64 + tx;  // + 8*j
+    const int row_base = wm * (4 * TM) + ty;  // + 4*i
+    const int col_base = wn * (8 * TN) + tx;  // + 8*j
 
     const T ident = Ident<T, SR>::v();
-    T acc[8][8];
+    T acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < TN; ++j) {
             T v = ident;
             if (args.accumulate) {
                 const int r = bm + row_base + 4 * i, c = bn + col_base + 8 * j;
@@ -353,12 +357,12 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
         const T *sb = sa + BM * LD;
 #pragma unroll Cfg::UNR
         for (int kk = 0; kk < BK; kk += FK) {
-            Frag32<FK> a[8], b[8];
+            Frag32<FK> a[TM], b[TN];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) a[i] = lds_frag<FK>(sa + (row_base + 4 * i) * LD + kk);
+            for (int i = 0; i < TM; ++i) a[i] = lds_frag<FK>(sa + (row_base + 4 * i) * LD + kk);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) b[j] = lds_frag<FK>(sb + (col_base + 8 * j) * LD + kk);
-            Step<VAR, SR, NS, FK>::run(acc, a, b, args.one);
+            for (int j = 0; j < TN; ++j) b[j] = lds_frag<FK>(sb + (col_base + 8 * j) * LD + kk);
+            Step<VAR, SR, NS, FK, TM, TN>::run(acc, a, b, args.one);
         }
     }
     cp_async_wait<0>();
@@ -366,9 +370,9 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
     bool ch = false;
     int mx = -1;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < TN; ++j) {
             const int r = bm + row_base + 4 * i, c = bn + col_base + 8 * j;
             acc[i][j] = finish<T, SR>(acc[i][j]);
             if (r < M && c < N) {
@@ -397,9 +401,9 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
         static_assert(BN * (BM + 1) <= Cfg::STAGES * Cfg::kStageElems, "transpose staging fits");
         __syncthreads();  // every warp is done reading the last k stage
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) smem[(col_base + 8 * j) * (BM + 1) + row_base + 4 * i] = acc[i][j];
+            for (int j = 0; j < TN; ++j) smem[(col_base + 8 * j) * (BM + 1) + row_base + 4 * i] = acc[i][j];
         __syncthreads();
         T *CT = static_cast<T *>(Ct);
         for (int idx = tid; idx < BM * BN; idx += NT) {

@@ -60,6 +60,12 @@ def test_host_side_argument_errors(libpath):
     assert "lda" in btas.last_error()
     # max-plus on the 16-bit path is not offered
     assert btas.btas_gemm(1, 2, 4, 4, 4, 1, 4, 1, 4, 1, 4, None) == 7
+    # the batched launch's tile tuner takes 1 <= n_max <= 2048
+    assert btas.btas_batch_tune(0, None, None, 0) == 1
+    assert btas.btas_batch_tune(4096, None, None, 0) == 1
+    # the domain check covers int32 and fp32 only
+    assert btas.btas_gemm(0x1000, 2, 4, 4, 4, 1, 4, 1, 4, 1, 4, None) == 7
+    assert "CHECKED" in btas.last_error()
     # empty problems are no-ops
     assert btas.btas_gemm(0, 0, 0, 4, 4, None, 4, None, 4, None, 4, None) == 0
     assert btas.btas_apsp(0, None, None, None) == 0

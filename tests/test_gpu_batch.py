@@ -43,8 +43,31 @@ def _mixed(btas, seed=0):
     return apsp, gemm
 
 
+class _tile:
+    """BTAS_BATCH_TILE for the plans built inside (None: the default)."""
+
+    def __init__(self, tile):
+        self.tile = tile
+
+    def __enter__(self):
+        if self.tile:
+            os.environ["BTAS_BATCH_TILE"] = self.tile
+
+    def __exit__(self, *a):
+        os.environ.pop("BTAS_BATCH_TILE", None)
+
+
+@pytest.mark.parametrize("tile", [None, "64"])
 @pytest.mark.parametrize("graph", [True, False])
-def test_mixed_batch_matches_single_calls_and_oracle(btas, oracle_mod, graph):
+def test_mixed_batch_matches_single_calls_and_oracle(btas, oracle_mod, graph, tile):
+    """Every instance against the oracle and the single call, with the
+    default 128 x 128 output tile and with the 64 x 64 tile (4 x 4 outputs
+    per thread) for every instance."""
+    with _tile(tile):
+        _mixed_batch_check(btas, oracle_mod, graph)
+
+
+def _mixed_batch_check(btas, oracle_mod, graph):
     import torch
     apsp, gemm = _mixed(btas)
     b = btas.Batch(graph=graph)
@@ -136,19 +159,20 @@ def test_precision_switches_mid_solve(btas, oracle_mod):
     for i, n in enumerate(sizes):
         W = gen.random_graph(70 + i, i, n, 0.03, 4000, 5000)
         items.append((W, dev(W), torch.empty((n, n), dtype=torch.int32, device="cuda")))
-    for no16 in ("0", "1"):
+    for no16, tile in (("0", None), ("1", None), ("0", "64"), ("1", "64")):
         os.environ["BTAS_BATCH_NO_U16"] = no16
         try:
-            b = btas.Batch()
-            for _, Wd, D in items:
-                b.add_apsp(Wd, D)
-            b.launch()
-            b.wait()
-            b.close()
+            with _tile(tile):
+                b = btas.Batch()
+                for _, Wd, D in items:
+                    b.add_apsp(Wd, D)
+                b.launch()
+                b.wait()
+                b.close()
         finally:
             os.environ.pop("BTAS_BATCH_NO_U16", None)
         for W, _, D in items:
-            np.testing.assert_array_equal(host(D), oracle_mod.floyd_warshall(W), err_msg=f"no16={no16}")
+            np.testing.assert_array_equal(host(D), oracle_mod.floyd_warshall(W), err_msg=f"no16={no16} tile={tile}")
     srv = btas.Server(1 << 30)
     outs = []
     for W, _, _ in items:
@@ -196,3 +220,44 @@ def test_profile_counts_every_task(btas, oracle_mod):
     assert btas.btas_batch_profile(plain.handle, None, None, 0) == 1  # created without the flag
     plain.close()
     b.close()
+
+
+def test_tile_autotuner_table_and_results(btas, oracle_mod):
+    """btas_batch_tune times both output tiles per kind and size bucket and
+    fills the table; a batch planned afterwards (sizes from several buckets)
+    matches the oracle whichever tile each instance took."""
+    import torch
+    btas.btas_batch_tune_clear()
+    assert btas.btas_batch_tile(0, 100) == 0
+    res = btas.batch_tune(256)
+    for kind in btas.BATCH_TILE_KINDS:
+        rows = res[kind]
+        assert len(rows) == 8
+        for lo, hi, tile, ms128, ms64 in rows:
+            assert tile in (64, 128) and ms128 > 0 and ms64 > 0
+            assert tile == (64 if ms64 < 0.97 * ms128 else 128)
+    assert btas.btas_batch_tile(0, 70) == res["apsp"][2][2]
+    apsp, gemm = _mixed(btas, seed=5)
+    b = btas.Batch()
+    for W, Wd, D in apsp:
+        b.add_apsp(Wd, D)
+    for A, B, Ad, Bd, C, sr, tb in gemm:
+        b.add_gemm(Ad, Bd, C, sr, trans_b=tb)
+    b.launch()
+    b.wait()
+    for W, Wd, D in apsp:
+        np.testing.assert_array_equal(host(D), oracle_mod.floyd_warshall(W))
+    for A, B, Ad, Bd, C, sr, tb in gemm:
+        np.testing.assert_array_equal(bits(host(C)), bits(oracle_mod.tgemm(sr, A, B)))
+    # the per-batch choice between the table, all 128 x 128 and all 64 x 64
+    mode, ms = b.select_tiles()
+    assert mode in ms and ms[mode] == min(ms.values())
+    for _, _, D in apsp:
+        D.fill_(-5)
+    b.launch()
+    b.wait()
+    for W, Wd, D in apsp:
+        np.testing.assert_array_equal(host(D), oracle_mod.floyd_warshall(W))
+    b.close()
+    btas.btas_batch_tune_clear()
+    torch.cuda.synchronize()

@@ -237,3 +237,60 @@ def test_packed_full_size_sampled_rows(btas, oracle_mod):
 def torch_index(rows):
     import torch
     return torch.from_numpy(np.asarray(rows, dtype=np.int64)).cuda()
+
+
+@pytest.mark.parametrize("sr", [0, 1])
+@pytest.mark.parametrize("dt", ["i32", "f32"])
+def test_checked_in_domain(btas, oracle_mod, dt, sr):
+    """BTAS_GEMM_CHECKED on operands inside the domain (INF entries
+    included): the same bits as the oracle, and btas_sync_status reports
+    nothing -- plain, accumulate, B transposed and (int32) packed."""
+    m, n, k = 200, 150, 90
+    A, B = _inputs(dt, sr, m, n, k, 4100 + sr)
+    ref = oracle_mod.tgemm(sr, A, B)
+    np.testing.assert_array_equal(bits(host(btas.gemm(dev(A), dev(B), sr, checked=True))), bits(ref))
+    np.testing.assert_array_equal(
+        bits(host(btas.gemm(dev(A), dev(np.ascontiguousarray(B.T)), sr, trans_b=True, checked=True))), bits(ref))
+    C0 = _inputs(dt, sr, m, n, 1, 4200 + sr)[0][:, :1].repeat(n, axis=1)
+    acc = host(btas.gemm(dev(A), dev(B), sr, out=dev(C0), accumulate=True, checked=True))
+    np.testing.assert_array_equal(bits(acc), bits(oracle_mod.tgemm(sr, A, B, C0)))
+    if dt == "i32":
+        Ap = gen.uniform_int(gen.BASE_SEED, 4300, (m, k), -2000, 2000)
+        Bp = gen.uniform_int(gen.BASE_SEED, 4301, (k, n), -2000, 2000)
+        np.testing.assert_array_equal(host(btas.gemm(dev(Ap), dev(Bp), sr, packed=True, checked=True)),
+                                      oracle_mod.tgemm(sr, Ap, Bp))
+    assert btas.sync_status() == (0, 0, 0)
+
+
+@pytest.mark.parametrize("sr", [0, 1])
+@pytest.mark.parametrize("dt", ["i32", "f32"])
+def test_checked_out_of_domain(btas, dt, sr):
+    """An operand entry outside the domain: the checked product leaves C
+    unwritten, the call itself returns BTAS_OK (it stays asynchronous), and
+    btas_sync_status reports the entries and calls once, then clears."""
+    import torch
+    m, n, k = 130, 70, 50
+    A, B = _inputs(dt, sr, m, n, k, 4400 + sr)
+    A, B = A.copy(), B.copy()
+    if dt == "i32":
+        A[3, 4] = 1 << 29  # beyond 2^28 and not INF
+        B[7, 1] = NINF if sr == 0 else INF  # the other semiring's identity
+    else:
+        A[3, 4] = np.float32("nan")
+        B[7, 1] = np.float32("-inf") if sr == 0 else np.float32("inf")
+    sentinel = np.full((m, n), 41, dtype=A.dtype)
+    for packed in ((False, True) if dt == "i32" else (False,)):
+        out = dev(sentinel)
+        btas.gemm(dev(A), dev(B), sr, out=out, packed=packed, checked=True)
+        assert btas.sync_status() == (1, 2, 1)
+        np.testing.assert_array_equal(host(out), sentinel)
+    # accumulate: an out-of-domain entry of C is found too
+    good_a, good_b = _inputs(dt, sr, m, n, k, 4500 + sr)
+    C0 = np.array(sentinel)
+    C0[0, 0] = (1 << 29) if dt == "i32" else np.float32("nan")
+    out = dev(C0)
+    btas.gemm(dev(good_a), dev(good_b), sr, out=out, accumulate=True, checked=True)
+    assert btas.sync_status() == (1, 1, 1)
+    np.testing.assert_array_equal(bits(host(out)), bits(C0))
+    assert btas.sync_status() == (0, 0, 0)
+    torch.cuda.synchronize()
