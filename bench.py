@@ -783,10 +783,12 @@ def serve(args, btas, torch):
                              f"reused in completion order; set-up {t_pool:.1f} s",
            "rates": []}
     checked = mismatched = 0
+    # one long-lived server for every rate, as a deployment runs it
+    srv = btas.Server(40 << 30)
     for rate in [float(x) for x in args.serve_rates.split(",")]:
         arrivals = np.cumsum(gaps / rate)
         # continuous-batching server
-        srv = btas.Server(40 << 30)
+        steps0 = srv.stats()["steps"]
         tickets = [None] * R
         lag = np.zeros(R)
         holder = [collections.deque() for _ in range(T)]   # (ticket, buffer index) in submission order
@@ -822,8 +824,11 @@ def serve(args, btas, torch):
         srv.wait_all(600)
         polls = [srv.poll(tk) for tk in tickets]
         stats = srv.stats()
-        srv.close()
+        stats["steps"] -= steps0
         lat = [p["t_done"] - p["t_submit"] + lag[i] for i, p in enumerate(polls)]
+        service = collections.defaultdict(list)  # admission -> done, per template
+        for i, p in enumerate(polls):
+            service[int(pick[i])].append(p["t_done"] - p["t_admit"])
         failed = sum(1 for p in polls if p["state"] != 2)
         span = max(p["t_done"] for p in polls) - min(p["t_submit"] - lag[i] for i, p in enumerate(polls))
         p50, p99 = pct(lat)
@@ -838,11 +843,13 @@ def serve(args, btas, torch):
                 mismatched += 0 if torch.equal(got, ref) else 1
         # serial plain execution of the same arrival sequence
         slat = []
+        sservice = collections.defaultdict(list)
         start = time.perf_counter()
         for i in range(R):
             now = time.perf_counter() - start
             if now < arrivals[i]:
                 time.sleep(arrivals[i] - now)
+            t_begin = time.perf_counter()
             t = int(pick[i])
             tp = tmpl[t]
             if tp[0] == "apsp":
@@ -853,6 +860,7 @@ def serve(args, btas, torch):
                 pools[t][0].copy_(c)
             torch.cuda.synchronize()
             slat.append(time.perf_counter() - start - arrivals[i])
+            sservice[t].append(time.perf_counter() - t_begin)
         sspan = time.perf_counter() - start
         s50, s99 = pct(slat)
         out["rates"].append({"rate_req_s": rate, "p50_ms": round(p50, 3), "p99_ms": round(p99, 3),
@@ -860,7 +868,12 @@ def serve(args, btas, torch):
                              "slowest_1pct": top_share(lat, R),
                              "serial_p50_ms": round(s50, 3), "serial_p99_ms": round(s99, 3),
                              "serial_throughput_req_s": round(R / sspan, 1),
-                             "serial_slowest_1pct": top_share(slat, R)})
+                             "serial_slowest_1pct": top_share(slat, R),
+                             "large_template_service_ms": {
+                                 f"{tmpl[t][0]} n={tmpl[t][1]}": [round(float(np.median(service[t])) * 1e3, 2),
+                                                                  round(float(np.median(sservice[t])) * 1e3, 2)]
+                                 for t in sorted(service, key=lambda t: -tmpl[t][1])[:6]}})
+    srv.close()
     out["results_checked"] = checked
     out["results_mismatched"] = mismatched
     return out

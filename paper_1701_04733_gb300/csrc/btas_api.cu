@@ -68,6 +68,17 @@ cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t st) {
 
 cudaError_t ws_free(void *p, cudaStream_t st) { return cudaFreeAsync(p, st); }
 
+cudaError_t ws_keep_at_least(uint64_t bytes) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    uint64_t cur = 0;
+    if ((e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur)) != cudaSuccess) return e;
+    if (cur >= bytes) return cudaSuccess;
+    return cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &bytes);
+}
+
 // BTAS_LOG=1 (read once) prints each entry point's execution choices to
 // stderr; 0 or unset prints nothing.
 int log_level() {

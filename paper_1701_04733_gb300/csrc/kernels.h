@@ -28,6 +28,9 @@ cudaError_t set_smem_once(const void *func, int bytes);
 // Stream-ordered workspace from the library's pool of the current device.
 cudaError_t ws_alloc(void **p, size_t bytes, cudaStream_t st);
 cudaError_t ws_free(void *p, cudaStream_t st);
+// Raise the current device pool's release threshold to at least `bytes`
+// (memory freed to the pool stays cached up to it).
+cudaError_t ws_keep_at_least(uint64_t bytes);
 
 // ---- tropical GEMM kernel registry (tgemm_*.cu)
 struct GemmKernel {

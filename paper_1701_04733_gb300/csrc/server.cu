@@ -28,12 +28,14 @@
 // batching gain -- APSP above the cooperative kernel's size limit, products
 // of more than BTAS_SERVER_BULK_TERMS terms (default 4e9) -- take a second
 // lane instead: a bulk thread runs them one at a time, in arrival order,
-// through the library's single calls (btas_apsp, btas_gemm) on a stream of
-// higher priority than the step loop's: the large requests set the latency
-// tail, and the small ones, batched in the step loop, never queue behind
-// them but take the SMs the large kernels leave free.  While the bulk lane
-// is busy the step loop does not use the cooperative whole-solve kernel,
-// whose grid must be co-resident on every SM.
+// through the library's single calls (btas_apsp, btas_gemm) on a compute
+// stream of its own, of higher priority than the step loop's: the large
+// requests set the latency tail, and the small ones, batched in the step
+// loop, never queue behind them but take the SMs the large kernels leave
+// free (and the gaps of the bulk lane's read-backs and set-up).  While the
+// bulk lane holds work the step loop does not launch the cooperative
+// whole-solve kernel, whose grid must be co-resident on every SM.  The bulk
+// lane's copies run on a copy stream of their own.
 // Requests that arrive while a step runs are admitted at once (their device
 // memory is taken on the copy stream, so their input copies overlap the
 // step) and join the next step, so their work overlaps with the squarings
@@ -122,10 +124,13 @@ struct btas_server_t {
     bool stop = false;
     std::thread worker, bulk_worker;
     std::chrono::steady_clock::time_point t0;
-    cudaStream_t compute = nullptr, copy = nullptr, bulk = nullptr;
+    cudaStream_t compute = nullptr, copy = nullptr;      // the step loop's streams
+    cudaStream_t bulk = nullptr, bulk_compute = nullptr;  // the bulk lane's copy and compute streams
     double bulk_terms = 4e9;   // products above this many terms take the bulk lane
     int64_t bulk_runs = 0;
-    bool bulk_busy = false;    // the bulk lane holds a request
+    bool bulk_busy = false;  // the bulk lane holds a request
+    void *bulk_buf = nullptr;  // the bulk lane's device block, grown as needed, kept until destroy
+    size_t bulk_cap = 0;
     // per-step device/pinned staging (double-buffered by step parity)
     void *d_stage[2] = {nullptr, nullptr};
     void *h_stage[2] = {nullptr, nullptr};
@@ -241,12 +246,13 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
     units.clear();
     double terms = 0, pending = 0;
     for (Req *r : sv->active) pending += r->remaining_terms();
-    const double small = 0.05 * sv->step_terms;
     bool bulk_busy;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         bulk_busy = sv->bulk_busy || !sv->bulk_queue.empty();
     }
+    const double cap = sv->step_terms;
+    const double small = 0.05 * cap;
     for (Req *r : sv->active) {
         // an APSP request that fits the one-block or cooperative kernel is
         // solved whole, in one unit, instead of one squaring per step -- when
@@ -258,7 +264,7 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
         r->take = 0;
         if (r->whole) {
             const double w = r->unit_terms() * std::min(r->S, 6);
-            if (!units.empty() && terms + w > sv->step_terms && w >= small) continue;
+            if (!units.empty() && terms + w > cap && w >= small) continue;
             units.push_back(r);
             terms += w;
             continue;
@@ -266,7 +272,7 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
         // the rest of the current unit, or the chunk of its output tiles that
         // fits what is left of the cap; small units always join
         const int rem = r->unit_tiles() - r->tile_next;
-        const double tt = r->tile_terms(), rem_terms = rem * tt, left = sv->step_terms - terms;
+        const double tt = r->tile_terms(), rem_terms = rem * tt, left = cap - terms;
         int take;
         if (rem_terms <= left || rem_terms < small) take = rem;
         else if (left >= tt) take = std::min(rem, std::max(1, (int)(left / tt)));
@@ -514,33 +520,63 @@ void bulk_loop(btas_server_t *sv) {
             r->state = kRunning;
             r->t_admit = sv->now();
         }
-        const cudaStream_t st = sv->bulk;
+        // memory and copies on the lane's copy stream; the single call on the
+        // compute stream, ordered by events in both directions
+        const cudaStream_t cp = sv->bulk, cs = sv->bulk_compute;
+        const double t_pick = sv->now();
+        cudaEvent_t in_ev = nullptr, out_ev = nullptr;
+        cudaEventCreateWithFlags(&in_ev, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&out_ev, cudaEventDisableTiming);
         bool ok = true;
-        void *dmem = nullptr;
+        // the lane's own device block, reused by every large request
+        const size_t need = r->kind == 0 ? 2 * a256((size_t)r->n * r->n * 4)
+                                         : a256((size_t)r->m * r->k * 4) + a256((size_t)r->k * r->n * 4) +
+                                               a256((size_t)r->m * r->n * 4);
+        if (need > sv->bulk_cap) {
+            if (sv->bulk_buf) cudaFreeAsync(sv->bulk_buf, cp);
+            sv->bulk_buf = nullptr;
+            sv->bulk_cap = 0;
+            if (ws_alloc(&sv->bulk_buf, need, cp) == cudaSuccess) sv->bulk_cap = need;
+            else ok = false;
+        }
+        void *dmem = ok ? sv->bulk_buf : nullptr;
         if (r->kind == 0) {
             const size_t nn = (size_t)r->n * r->n * 4;
-            ok = ws_alloc(&dmem, 2 * a256(nn), st) == cudaSuccess;
             if (ok) {
                 int32_t *W = static_cast<int32_t *>(dmem);
                 int32_t *D = reinterpret_cast<int32_t *>(static_cast<char *>(dmem) + a256(nn));
-                ok = cudaMemcpyAsync(W, r->hA, nn, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-                     btas_apsp(r->n, W, D, st) == BTAS_OK &&
-                     cudaMemcpyAsync(r->hC, D, nn, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+                ok = cudaMemcpyAsync(W, r->hA, nn, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                     cudaEventRecord(in_ev, cp) == cudaSuccess && cudaStreamWaitEvent(cs, in_ev, 0) == cudaSuccess &&
+                     btas_apsp(r->n, W, D, cs) == BTAS_OK && cudaEventRecord(out_ev, cs) == cudaSuccess &&
+                     cudaStreamWaitEvent(cp, out_ev, 0) == cudaSuccess &&
+                     cudaMemcpyAsync(r->hC, D, nn, cudaMemcpyDeviceToHost, cp) == cudaSuccess;
             }
         } else {
             const size_t ba = (size_t)r->m * r->k * 4, bb = (size_t)r->k * r->n * 4, bc = (size_t)r->m * r->n * 4;
-            ok = ws_alloc(&dmem, a256(ba) + a256(bb) + a256(bc), st) == cudaSuccess;
             if (ok) {
                 char *p = static_cast<char *>(dmem);
                 void *A = p, *B = p + a256(ba), *C = p + a256(ba) + a256(bb);
-                ok = cudaMemcpyAsync(A, r->hA, ba, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-                     cudaMemcpyAsync(B, r->hB, bb, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-                     btas_gemm(r->sr, r->dtype, r->m, r->n, r->k, A, r->k, B, r->n, C, r->n, st) == BTAS_OK &&
-                     cudaMemcpyAsync(r->hC, C, bc, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+                ok = cudaMemcpyAsync(A, r->hA, ba, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                     cudaMemcpyAsync(B, r->hB, bb, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                     cudaEventRecord(in_ev, cp) == cudaSuccess && cudaStreamWaitEvent(cs, in_ev, 0) == cudaSuccess &&
+                     btas_gemm(r->sr, r->dtype, r->m, r->n, r->k, A, r->k, B, r->n, C, r->n, cs) == BTAS_OK &&
+                     cudaEventRecord(out_ev, cs) == cudaSuccess && cudaStreamWaitEvent(cp, out_ev, 0) == cudaSuccess &&
+                     cudaMemcpyAsync(r->hC, C, bc, cudaMemcpyDeviceToHost, cp) == cudaSuccess;
             }
         }
-        if (cudaStreamSynchronize(st) != cudaSuccess) ok = false;
-        if (dmem) ws_free(dmem, st);
+        if (!ok) {
+            // the compute stream may still hold work of this request: the copy
+            // stream waits for it before the block is returned
+            cudaEventRecord(out_ev, cs);
+            cudaStreamWaitEvent(cp, out_ev, 0);
+        }
+        const double t_call = sv->now();
+        if (cudaStreamSynchronize(cp) != cudaSuccess) ok = false;
+        if (log_level() >= 1)
+            log_event("server bulk lane: %s n=%d: call returned after %.3f ms, result in host memory %.3f ms later",
+                      r->kind == 0 ? "apsp" : "product", r->n, (t_call - t_pick) * 1e3, (sv->now() - t_call) * 1e3);
+        cudaEventDestroy(in_ev);
+        cudaEventDestroy(out_ev);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             r->t_done = sv->now();
@@ -667,18 +703,24 @@ btas_status btas_server_create(btas_server_t **out, int64_t hbm_budget_bytes, in
     sv->t0 = std::chrono::steady_clock::now();
     cudaGetDevice(&sv->device);
     int per_sm = 0, sms = 0;
-    // the bulk lane's stream gets the highest priority, the step loop's the lowest
+    // the bulk lane's streams get the highest priority, the step loop's the lowest
     int prio_low = 0, prio_high = 0;
     cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     if (batch_kernel_prepare(&per_sm) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device) != cudaSuccess ||
         cudaStreamCreateWithPriority(&sv->compute, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
         cudaStreamCreateWithPriority(&sv->copy, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&sv->bulk, cudaStreamNonBlocking, prio_high) != cudaSuccess) {
+        cudaStreamCreateWithPriority(&sv->bulk, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&sv->bulk_compute, cudaStreamNonBlocking, prio_high) != cudaSuccess) {
         delete sv;
         return sfail(BTAS_ERR_CUDA, "btas_server_create: CUDA set-up failed");
     }
     sv->grid = std::max(1, per_sm * sms);
+    // memory freed by retired requests stays cached in the library's pool up
+    // to the budget (plus the single calls' workspace): otherwise every
+    // synchronisation above the pool's threshold hands memory back to the
+    // driver and the next large allocation maps it again
+    ws_keep_at_least((uint64_t)hbm_budget_bytes + (4ULL << 30));
     if (const char *e = getenv("BTAS_SERVER_STEP_TERMS")) sv->step_terms = atof(e) > 0 ? atof(e) : sv->step_terms;
     if (const char *e = getenv("BTAS_SERVER_NO_U16")) sv->allow_u16 = (*e && atoi(e) != 0) ? 0 : 1;
     if (const char *e = getenv("BTAS_SERVER_NO_WHOLE")) sv->allow_whole = (*e && atoi(e) != 0) ? 0 : 1;
@@ -811,6 +853,8 @@ btas_status btas_server_destroy(btas_server_t *sv) {
     cudaStreamSynchronize(sv->compute);
     cudaStreamSynchronize(sv->copy);
     cudaStreamSynchronize(sv->bulk);
+    cudaStreamSynchronize(sv->bulk_compute);
+    if (sv->bulk_buf) ws_free(sv->bulk_buf, sv->bulk);
     for (auto &kv : sv->all) {
         release(sv, kv.second);
         delete kv.second;
@@ -825,6 +869,7 @@ btas_status btas_server_destroy(btas_server_t *sv) {
     cudaStreamDestroy(sv->compute);
     cudaStreamDestroy(sv->copy);
     cudaStreamDestroy(sv->bulk);
+    cudaStreamDestroy(sv->bulk_compute);
     delete sv;
     return BTAS_OK;
 }
