@@ -799,7 +799,10 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     }
 
     Workspace ws(st);
-    const size_t flag_bytes = align256((size_t)(2 * S + 8) * 4);
+    // flags: [0, S) change flags of the device-exit path, [S+1, S+2] the domain
+    // scan, [2S+8, 4S+8) (change flag, largest finite entry) of each squaring
+    // of the adaptive path, adjacent so that one read-back fetches both
+    const size_t flag_bytes = align256((size_t)(4 * S + 8) * 4);
     // layout: [flags | X | Y | T]; T holds a transpose (or the duplicated
     // 16-bit operand) with a leading dimension rounded up to 4 elements
     const long long ldt = (n + 3) & ~3LL;
@@ -879,9 +882,8 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     }
     const bool no_u16 = env_int("BTAS_APSP_NO_U16", 0) != 0;
     const bool no_carrier = env_int("BTAS_APSP_NO_CARRIER", 0) != 0;
-    int *chg = dflags;
-    int *mxs = dflags + S + 4;
-    int ns16 = -1;  // looked up at the first packed squaring
+    int *pairs = dflags + 2 * S + 8;  // squaring s: pairs[2s] changed, pairs[2s + 1] largest finite entry
+    int ns16 = -1;                    // looked up at the first packed squaring
     auto other = [&](const void *p) -> void * { return p == (const void *)X ? (void *)Y : (void *)X; };
     // convert an n x n matrix between representations (T is free scratch here)
     auto convert = [&](int from, int to, const void *src, void *dst) -> cudaError_t {
@@ -917,9 +919,9 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
             a.B = static_cast<const uint16_t *>(cur); a.ldb = n;
             a.C = static_cast<uint16_t *>(out); a.ldc = n;
             a.prev = static_cast<const uint16_t *>(cur); a.ldp = n;
-            a.changed = &chg[s];
+            a.changed = &pairs[2 * s];
             a.one = 1;
-            a.maxfin = &mxs[s];
+            a.maxfin = &pairs[2 * s + 1];
             if (ns16 < 0) ns16 = u16_ns(n, n, n, st);
             BTAS_CUDA(launch_tgemm_u16_ws(a, reinterpret_cast<uint32_t *>(T), ns16, st), "u16 squaring");
         } else {
@@ -931,17 +933,16 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
             a.Bt = T; a.ldb = ldt;
             a.C = out; a.ldc = n;
             a.prev = cur; a.ldp = n;
-            a.changed = &chg[s];
-            a.maxfin = &mxs[s];
+            a.changed = &pairs[2 * s];
+            a.maxfin = &pairs[2 * s + 1];
             a.vec_a = aligned16(cur, n);
             a.vec_b = aligned16(T, ldt);
             btas_status r = run_nt(rep == 1 ? BTAS_F32 : BTAS_I32, kMin, a, st);
             if (r != BTAS_OK) return r;
         }
         used |= 1 << rep;
-        int host[2] = {0, 0};
-        BTAS_CUDA(cudaMemcpyAsync(&host[0], &chg[s], 4, cudaMemcpyDeviceToHost, st), "flag readback");
-        BTAS_CUDA(read_back(&host[1], &mxs[s], 4, st), "max readback");
+        int host[2] = {0, 0};  // one read-back through the pinned mailbox: change flag and maximum
+        BTAS_CUDA(read_back(host, &pairs[2 * s], 8, st), "flag readback");
         cur = out;
         m = host[1] < 0 ? 0 : host[1];
         if (host[0]) ++done;
