@@ -67,7 +67,8 @@ def parse():
     p.add_argument("--probe-ctas", type=int, default=1, help="with --probe-mix: CTAs per SM (1 or 2)")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
-    p.add_argument("--only", default=None, choices=["kernels", "batched", "serve", "next", "tune", "configs", "probe"],
+    p.add_argument("--only", default=None,
+                   choices=["kernels", "batched", "serve", "next", "tune", "configs", "probe", "mid"],
                    help="profiling aids: run one part alone and print its JSON (not a bench line)")
     return p.parse_args()
 
@@ -1154,6 +1155,22 @@ def run_only(args):
             print(json.dumps({"only": "probe", "terms_per_clk_per_sm": issue_probe(btas, full=True)}))
     elif args.only == "configs":
         print(json.dumps({"only": "configs", **config_timings(args, btas, torch)}))
+    elif args.only == "mid":
+        # one mid-size solve (p = 0.05, w in [1, 100]) at --n, five calls
+        import gen
+        n = args.n
+        W = torch.from_numpy(gen.random_graph(gen.BASE_SEED, 300 + n, n, 0.05, 1, 100)).cuda()
+        D = torch.empty_like(W)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = btas.apsp(W, out=D, info=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(round(e0.elapsed_time(e1) * 1e3, 1))
+        print(json.dumps({"only": "mid", "n": n, "us_per_call": ts, "squarings_changing": info["squarings"],
+                          "path": info["path"]}))
     else:
         print(json.dumps({"only": "serve", **serve(args, btas, torch)}))
     return 0
