@@ -187,7 +187,9 @@ btas_status btas_measure_issue_rate_ex(int mix, int ctas_per_sm, double *terms_p
  * outside leaves C unwritten and adds the count to the device's status
  * words; the call itself stays asynchronous and returns BTAS_OK.
  * btas_sync_status reports (and clears) the words.  Cost: one extra read of
- * the operands (HBM-bound).
+ * the operands (HBM-bound).  The first checked product (or btas_sync_status
+ * call) on a device allocates its 256-byte status words with cudaMalloc:
+ * make it outside stream capture.
  * ------------------------------------------------------------------------ */
 btas_status btas_gemm(int semiring, int dtype, int64_t m, int64_t n, int64_t k,
                       const void *A, int64_t lda, const void *B, int64_t ldb,

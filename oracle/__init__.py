@@ -78,6 +78,7 @@ def _load():
             "oracle_apsp_squaring_u16": (None, [i64, vp, vp, i32]),
             "oracle_fw_i32": (None, [i64, vp]),
             "oracle_apsp_paths_i32": (None, [i64, vp, vp, vp, i32]),
+            "oracle_apsp_paths_f32": (None, [i64, vp, vp, vp, i32]),
             "oracle_dijkstra_rows_i32": (None, [i64, vp, i64, vp, vp]),
             "oracle_bruteforce_apsp_i32": (i32, [i64, vp, vp]),
             "oracle_gemv_i32": (None, [i32, i32, i32, i64, i64, vp, i64, vp, vp]),
@@ -166,14 +167,17 @@ def apsp_squaring(W: np.ndarray, squarings: int | None = None) -> np.ndarray:
 
 
 def apsp_paths(W: np.ndarray, squarings: int | None = None):
-    """APSP by squaring with next-hop tracking (smallest minimising k).
-    Returns (D, Next)."""
-    W = _c(W, np.int32)
+    """APSP by squaring with next-hop tracking (smallest minimising k), int32
+    or float32 weights.  Returns (D, Next)."""
+    W = np.asarray(W)
+    dt = np.float32 if W.dtype.kind == "f" else np.int32
+    W = _c(W, dt)
     n = W.shape[0]
     s = apsp_squarings(n) if squarings is None else int(squarings)
     D = np.empty_like(W)
-    Nx = np.empty_like(W)
-    _load().oracle_apsp_paths_i32(n, _p(W), _p(D), _p(Nx), s)
+    Nx = np.empty(W.shape, dtype=np.int32)
+    fn = _load().oracle_apsp_paths_f32 if dt == np.float32 else _load().oracle_apsp_paths_i32
+    fn(n, _p(W), _p(D), _p(Nx), s)
     return D, Nx
 
 

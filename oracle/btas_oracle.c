@@ -210,6 +210,46 @@ void oracle_apsp_paths_i32(int64_t n, const int32_t *W, int32_t *D, int32_t *Nex
     free(d); free(d2); free(x); free(x2);
 }
 
+/* The same next-hop squaring on binary32 weights (+inf = no edge, weights
+ * >= 0): each term is one round-to-nearest add (otimes_f32), and the SMALLEST
+ * k whose rounded sum attains the minimum is kept, so a tie that only the
+ * rounding creates is broken towards the smaller k like any other tie.
+ * N_0 and the successor rule are those of oracle_apsp_paths_i32.  Exactly
+ * `squarings` steps. */
+void oracle_apsp_paths_f32(int64_t n, const float *W, float *D, int32_t *Next, int squarings) {
+    size_t nn = (size_t)n * (size_t)n;
+    float *d = (float *)malloc(nn ? nn * 4 : 4), *d2 = (float *)malloc(nn ? nn * 4 : 4);
+    int32_t *x = (int32_t *)malloc(nn ? nn * 4 : 4), *x2 = (int32_t *)malloc(nn ? nn * 4 : 4);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            d[i * n + j] = W[i * n + j];
+            x[i * n + j] = (i == j) ? (int32_t)i : (isinf(W[i * n + j]) ? -1 : (int32_t)j);
+        }
+    for (int s = 0; s < squarings; ++s) {
+        int64_t i;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(o_threads)
+        for (i = 0; i < n; ++i) {
+            for (int64_t j = 0; j < n; ++j) {
+                float best = INFINITY;
+                int64_t kbest = -1;
+                for (int64_t k = 0; k < n; ++k) {
+                    float t = otimes_f32(d[i * n + k], d[k * n + j]);
+                    if (t < best) { best = t; kbest = k; }
+                }
+                d2[i * n + j] = best;
+                if (isinf(best)) x2[i * n + j] = -1;
+                else if (kbest == i) x2[i * n + j] = x[i * n + j];
+                else x2[i * n + j] = x[i * n + kbest];
+            }
+        }
+        float *tf = d; d = d2; d2 = tf;
+        int32_t *t = x; x = x2; x2 = t;
+    }
+    memcpy(D, d, nn * 4);
+    memcpy(Next, x, nn * 4);
+    free(d); free(d2); free(x); free(x2);
+}
+
 /* Sequential Floyd-Warshall (Algorithm 2): pivot z outermost, relax
  * D[x][y] through z when both legs exist.  In place; row z and column z do
  * not change while z is the pivot, so the in-place update is exact. */

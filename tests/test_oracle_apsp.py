@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import gen
-from golden import as_i32, load
+from golden import as_f32, as_i32, load
 
 INF = 0x3FFFFFFF
 
@@ -187,3 +187,48 @@ def test_paths_are_valid_shortest_walks(oracle_mod, n):
         for j in range(n):
             if D[i, j] != INF:
                 assert _walk(W, Nx, i, j) == D[i, j]
+
+
+def _as_float_graph(W):
+    """An int32 graph as binary32 weights (INF -> +inf); exact for the small
+    integer weights used here."""
+    return np.where(W == INF, np.float32(np.inf), W.astype(np.float32)).astype(np.float32)
+
+
+def test_paths_f32_rounding_tie(oracle_mod):
+    """A hand-worked binary32 case whose tie exists only after rounding: the
+    smallest minimising k keeps the direct edge."""
+    g = load("apsp_paths_f32_rounding_3node.txt")
+    W, D, N = as_f32(g["W"]), as_f32(g["D"]), as_i32(g["N"])
+    d, nx = oracle_mod.apsp_paths(W)
+    np.testing.assert_array_equal(d.view(np.uint32), D.view(np.uint32))
+    np.testing.assert_array_equal(nx, N)
+
+
+@pytest.mark.parametrize("n", [3, 8, 40])
+def test_paths_f32_equal_int32_on_integer_weights(oracle_mod, n):
+    """Integer weights whose path sums stay below 2^24 are exact in binary32:
+    the fp32 next-hop squaring then gives the int32 routine's distances and
+    next hops, ties included (weights 1..6 make many)."""
+    W = gen.random_graph(21, n, n, 0.3 if n > 8 else 0.6, 1, 6)
+    d32, n32 = oracle_mod.apsp_paths(W)
+    df, nf = oracle_mod.apsp_paths(_as_float_graph(W))
+    np.testing.assert_array_equal(df, _as_float_graph(d32))
+    np.testing.assert_array_equal(nf, n32)
+
+
+@pytest.mark.parametrize("n", [5, 30])
+def test_paths_f32_distances_are_repeated_products(oracle_mod, n):
+    """With rounding in play (weights U[0,1)), the distances are those of the
+    same number of squarings by the tropical product routine, bit for bit,
+    and the next hop is -1 exactly where the distance is +inf."""
+    W = _as_float_graph(gen.random_graph(22, n, n, 0.4, 1, 2)).copy()
+    u = gen.uniform_f32(23, n, (n, n))
+    W = np.where(np.isinf(W) | (np.eye(n) == 1), W, u).astype(np.float32)
+    S = oracle_mod.apsp_squarings(n)
+    d, nx = oracle_mod.apsp_paths(W)
+    ref = W.copy()
+    for _ in range(S):
+        ref = oracle_mod.tgemm(0, ref, ref)
+    np.testing.assert_array_equal(d.view(np.uint32), ref.view(np.uint32))
+    assert ((nx == -1) == np.isinf(d)).all()
