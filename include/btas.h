@@ -389,6 +389,22 @@ btas_status btas_closure(int semiring, int dtype, int64_t n, const void *A, void
 btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Next, int flags, int *squarings_done,
                             void *stream);
 
+/* btas_apsp_paths_f32: the same squaring with successors on binary32 weights
+ * (the squaring APSP of Sec. III on real weights).  Each term is one
+ * round-to-nearest-even add, and the SMALLEST k whose rounded sum attains the
+ * minimum is kept, so D and Next are reproducible bit for bit; a tie that
+ * only the rounding creates is broken like any other.  D equals
+ * ceil(log2(n-1)) repeated fp32 min-plus squarings of W (stopped early, same
+ * result, with BTAS_APSP_EARLY_EXIT).  Because of rounding, the weight of
+ * the walk Next describes may differ from D[i][j] in the last bits.
+ * W, D: n x n float device matrices, leading dimension n; Next: n x n int32
+ * as in btas_apsp_paths (W must not overlap D or Next).  Domain (checked,
+ * BTAS_ERR_ARG): zero diagonal, every other entry >= 0 or +inf (no edge);
+ * no NaN, no -inf.  flags, squarings_done and synchronisation as
+ * btas_apsp_paths; every squaring runs on the argmin kernel. */
+btas_status btas_apsp_paths_f32(int64_t n, const float *W, float *D, int32_t *Next, int flags, int *squarings_done,
+                                void *stream);
+
 /* btas_apsp_fw: the same APSP distance matrix by blocked Floyd-Warshall --
  * Algorithm 2's pivot loop reorganised in 128 x 128 tiles: per pivot block,
  * the diagonal tile and its row and column panels relax in order, and every

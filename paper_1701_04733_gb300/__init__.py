@@ -79,6 +79,7 @@ SIGNATURES = {
     "btas_apsp_squarings": (_i32, [_i64]),
     "btas_closure": (_i32, [_i32, _i32, _i64, _vp, _vp, _i32, _vp, _vp]),
     "btas_apsp_paths": (_i32, [_i64, _vp, _vp, _vp, _i32, _vp, _vp]),
+    "btas_apsp_paths_f32": (_i32, [_i64, _vp, _vp, _vp, _i32, _vp, _vp]),
     "btas_gemv": (_i32, [_i32, _i32, _i32, _i64, _i64, _vp, _i64, _vp, _vp, _vp]),
     "btas_apsp_fw": (_i32, [_i64, _vp, _vp, _vp]),
     "btas_sssp": (_i32, [_i64, _vp, _i64, _vp, _vp, _vp]),
@@ -256,16 +257,24 @@ def btas_apsp_paths(n, W, D, Next, flags, squarings_done_ptr, stream) -> int:
     return lib().btas_apsp_paths(n, W, D, Next, flags, squarings_done_ptr, stream)
 
 
+def btas_apsp_paths_f32(n, W, D, Next, flags, squarings_ptr, stream) -> int:
+    return lib().btas_apsp_paths_f32(n, W, D, Next, flags, squarings_ptr, stream)
+
+
 def apsp_paths(W, early_exit=True, stream=None, info=False):
-    """APSP distances and next-hop matrix (int32 CUDA tensors); with
-    info=True also {"squarings": squarings that changed D}."""
+    """APSP distances and next-hop matrix of an int32 or float32 CUDA matrix
+    (the next-hop matrix is int32); with info=True also {"squarings":
+    squarings that changed D or Next}."""
     torch = _torch()
     n = W.shape[0]
+    if W.shape != (n, n) or not W.is_contiguous():
+        raise ValueError("W must be a contiguous n x n tensor")
     D = torch.empty_like(W)
-    Nx = torch.empty_like(W)
+    Nx = torch.empty((n, n), dtype=torch.int32, device=W.device)
     sq = ctypes.c_int(0)
-    check(btas_apsp_paths(n, W.data_ptr(), D.data_ptr(), Nx.data_ptr(), APSP_EARLY_EXIT if early_exit else 0,
-                          ctypes.addressof(sq), _stream(stream)))
+    fn = btas_apsp_paths_f32 if W.dtype == torch.float32 else btas_apsp_paths
+    check(fn(n, W.data_ptr(), D.data_ptr(), Nx.data_ptr(), APSP_EARLY_EXIT if early_exit else 0,
+             ctypes.addressof(sq), _stream(stream)))
     return (D, Nx, {"squarings": sq.value}) if info else (D, Nx)
 
 

@@ -1135,6 +1135,63 @@ btas_status btas_apsp_paths(int64_t n, const int32_t *W, int32_t *D, int32_t *Ne
     return BTAS_OK;
 }
 
+btas_status btas_apsp_paths_f32(int64_t n, const float *W, float *D, int32_t *Next, int flags, int *squarings_done,
+                                void *stream) {
+    Trace trace_("btas_apsp_paths_f32");
+    if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp_paths_f32: n out of range");
+    if (flags & ~BTAS_APSP_EARLY_EXIT) return fail(BTAS_ERR_ARG, "btas_apsp_paths_f32: unknown flags");
+    if (n == 0) {
+        if (squarings_done) *squarings_done = 0;
+        return BTAS_OK;
+    }
+    if (!W || !D || !Next) return fail(BTAS_ERR_ARG, "btas_apsp_paths_f32: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int S = btas_apsp_squarings(n);
+    const size_t nn = (size_t)n * (size_t)n;
+    const long long ldt = (n + 3) & ~3LL;
+    Workspace ws(st);
+    const size_t flag_bytes = align256((size_t)(S + 4) * 4);
+    BTAS_CUDA(ws.alloc(flag_bytes + 4 * align256(nn * 4) + align256((size_t)n * ldt * 4)), "workspace alloc");
+    char *base = static_cast<char *>(ws.p);
+    int *dflags = reinterpret_cast<int *>(base);  // [s] changed after squaring s, [S] domain count
+    float *Db[2];
+    int *Nb[2];
+    Db[0] = reinterpret_cast<float *>(base + flag_bytes);
+    Db[1] = reinterpret_cast<float *>(reinterpret_cast<char *>(Db[0]) + align256(nn * 4));
+    Nb[0] = reinterpret_cast<int *>(reinterpret_cast<char *>(Db[1]) + align256(nn * 4));
+    Nb[1] = reinterpret_cast<int *>(reinterpret_cast<char *>(Nb[0]) + align256(nn * 4));
+    float *T = reinterpret_cast<float *>(reinterpret_cast<char *>(Nb[1]) + align256(nn * 4));
+    BTAS_CUDA(cudaMemsetAsync(dflags, 0, flag_bytes, st), "memset");
+    {
+        int bad = 0;
+        BTAS_CUDA(launch_paths_scan_f32(W, n, dflags + S, st), "domain scan");
+        BTAS_CUDA(read_back(&bad, dflags + S, 4, st), "scan readback");
+        if (bad != 0)
+            return fail(BTAS_ERR_ARG,
+                        "btas_apsp_paths_f32: %d entries outside the domain (NaN, negative, or non-zero diagonal)",
+                        bad);
+    }
+    BTAS_CUDA(cudaMemcpyAsync(Db[0], W, nn * 4, cudaMemcpyDeviceToDevice, st), "copy");
+    BTAS_CUDA(launch_next_init_f32(W, n, Nb[0], st), "next-hop init");
+    int cur = 0, done = 0;
+    for (int s = 0; s < S; ++s) {
+        BTAS_CUDA(launch_transpose4(Db[cur], n, (int)n, (int)n, T, ldt, 0, nullptr, st), "transpose");
+        BTAS_CUDA(launch_paths_square_f32((int)n, Db[cur], n, T, ldt, Nb[cur], Db[cur ^ 1], Nb[cur ^ 1], &dflags[s],
+                                          st),
+                  "paths squaring");
+        cur ^= 1;
+        int changed = 1;
+        BTAS_CUDA(read_back(&changed, &dflags[s], 4, st), "flag readback");
+        if (changed) ++done;
+        if (!changed && (flags & BTAS_APSP_EARLY_EXIT)) break;
+    }
+    log_event("apsp paths f32 n=%lld: %d changing squarings on the argmin kernel", (long long)n, done);
+    BTAS_CUDA(cudaMemcpyAsync(D, Db[cur], nn * 4, cudaMemcpyDeviceToDevice, st), "copy D");
+    BTAS_CUDA(cudaMemcpyAsync(Next, Nb[cur], nn * 4, cudaMemcpyDeviceToDevice, st), "copy Next");
+    if (squarings_done) *squarings_done = done;
+    return BTAS_OK;
+}
+
 btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) {
     Trace trace_("btas_apsp_fw");
     if (n < 0 || n > 46340) return fail(BTAS_ERR_ARG, "btas_apsp_fw: n out of range");

@@ -97,6 +97,13 @@ cudaError_t launch_paths_encode(const int *D, int n, int *Ak, int *BkT, long lon
 cudaError_t launch_paths_decode(const int *K, const int *D, const int *N, long long n, int *Dn, int *Nn, int *changed,
                                 int *maxfin, cudaStream_t st);
 cudaError_t launch_next_init(const int *W, long long n, int *N, cudaStream_t st);
+// binary32 forms: successors of W (+inf = no edge), the weight-domain count
+// (zero diagonal, entries >= 0 or +inf; *bad must be zeroed first) and the
+// argmin squaring with one round-to-nearest add per term.
+cudaError_t launch_next_init_f32(const float *W, long long n, int *N, cudaStream_t st);
+cudaError_t launch_paths_scan_f32(const float *W, long long n, int *bad, cudaStream_t st);
+cudaError_t launch_paths_square_f32(int n, const float *D, long long ldd, const float *Dt, long long ldt,
+                                    const int *N, float *D2, int *N2, int *changed, cudaStream_t st);
 cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *Dt, long long ldt, const int *N,
                                 int *D2, int *N2, int *changed, cudaStream_t st);
 

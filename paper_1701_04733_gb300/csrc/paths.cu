@@ -28,28 +28,60 @@ constexpr int PSTAGE = 2 * PBM * PLD;
 
 constexpr int PSMEM = PST * PSTAGE * 4;  // 54 KiB: dynamic shared memory
 
+// Element type of the argmin squaring: int32 (one DPX add-min per term, INF
+// absorbed by the clamp at INF - 2^28) or binary32 (one round-to-nearest add
+// per term, +inf absorbing on its own).
+template <typename T>
+struct PathsElem;
+template <>
+struct PathsElem<int> {
+    using V = int4;
+    static __device__ __forceinline__ int start() { return 0x7FFFFFFF; }
+    static __device__ __forceinline__ int inf() { return kInfI32; }
+    // min(acc, a + b)
+    static __device__ __forceinline__ int addmin(int a, int b, int acc) { return __viaddmin_s32(a, b, acc); }
+    static __device__ __forceinline__ int sum(int a, int b) { return a + b; }
+    static __device__ __forceinline__ int finish(int v) { return v >= kClampI32 ? kInfI32 : v; }
+    static __device__ __forceinline__ bool is_inf(int v) { return v == kInfI32; }
+};
+template <>
+struct PathsElem<float> {
+    using V = float4;
+    static __device__ __forceinline__ float start() { return __int_as_float(0x7f800000); }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    static __device__ __forceinline__ float addmin(float a, float b, float acc) { return fminf(__fadd_rn(a, b), acc); }
+    static __device__ __forceinline__ float sum(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float finish(float v) { return v; }
+    static __device__ __forceinline__ bool is_inf(float v) { return isinf(v); }
+};
+
+template <typename T>
 __global__ void __launch_bounds__(PNT, 2)
-paths_square_kernel(int n, const int *__restrict__ D, long long ldd, const int *__restrict__ Dt, long long ldt,
-                    const int *__restrict__ N, int *__restrict__ D2, int *__restrict__ N2, int *changed, int vec_a) {
-    extern __shared__ __align__(16) int smem[];
+paths_square_kernel(int n, const T *__restrict__ D, long long ldd, const T *__restrict__ Dt, long long ldt,
+                    const int *__restrict__ N, T *__restrict__ D2, int *__restrict__ N2, int *changed, int vec_a) {
+    using E = PathsElem<T>;
+    using V = typename E::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x;
     const int tiles = (n + PBM - 1) / PBM;
     const int bm = (blockIdx.x / tiles) * PBM, bn = (blockIdx.x % tiles) * PBM;
     const int tr = tid >> 4, tc = tid & 15;
-    int val[4][4], idx[4][4];
+    T val[4][4];
+    int idx[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            val[i][j] = 0x7FFFFFFF;
+            val[i][j] = E::start();
             idx[i][j] = -1;
         }
     const int KT = (n + PBK - 1) / PBK;
     auto load = [&](int s, int kt) {
-        int *sa = smem + s * PSTAGE;
-        int *sb = sa + PBM * PLD;
-        stage_rows<int, PBM, PBK, PLD, PNT>(sa, D, ldd, bm, n, kt * PBK, n, vec_a != 0, kInfI32, tid, true);
-        stage_rows<int, PBM, PBK, PLD, PNT>(sb, Dt, ldt, bn, n, kt * PBK, n, true, kInfI32, tid, true);
+        T *sa = smem + s * PSTAGE;
+        T *sb = sa + PBM * PLD;
+        stage_rows<T, PBM, PBK, PLD, PNT>(sa, D, ldd, bm, n, kt * PBK, n, vec_a != 0, E::inf(), tid, true);
+        stage_rows<T, PBM, PBK, PLD, PNT>(sb, Dt, ldt, bn, n, kt * PBK, n, true, E::inf(), tid, true);
     };
 #pragma unroll
     for (int s = 0; s < PST - 1; ++s) {
@@ -61,35 +93,37 @@ paths_square_kernel(int n, const int *__restrict__ D, long long ldd, const int *
         __syncthreads();
         if (kt + PST - 1 < KT) load((kt + PST - 1) % PST, kt + PST - 1);
         cp_async_commit();
-        const int *sa = smem + (kt % PST) * PSTAGE;
-        const int *sb = sa + PBM * PLD;
+        const T *sa = smem + (kt % PST) * PSTAGE;
+        const T *sb = sa + PBM * PLD;
 #pragma unroll 2
         for (int kk = 0; kk < PBK; kk += 4) {
-            int4 a[4], b[4];
+            V a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const int4 *>(sa + (tr + 16 * i) * PLD + kk);
+            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const V *>(sa + (tr + 16 * i) * PLD + kk);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = *reinterpret_cast<const int4 *>(sb + (tc + 16 * j) * PLD + kk);
+            for (int j = 0; j < 4; ++j) b[j] = *reinterpret_cast<const V *>(sb + (tc + 16 * j) * PLD + kk);
             const int k0 = kt * PBK + kk;
             // Two levels: the minimum of the 4 sums of this k-group costs one
-            // DPX add-min per term; only when it beats the running minimum
+            // add-then-min per term; only when it beats the running minimum
             // (rarely, once the minimum has settled) is the first k of the
-            // group that attains it looked up.  An equal group minimum keeps
-            // the earlier, smaller k.  Same result as a per-term argmin.
+            // group that attains it looked up (the sums are recomputed with
+            // the same rounding, so equality is exact).  An equal group
+            // minimum keeps the earlier, smaller k.  Same result as a
+            // per-term argmin.
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    int cm = __viaddmin_s32(a[i].x, b[j].x, 0x7FFFFFFF);
-                    cm = __viaddmin_s32(a[i].y, b[j].y, cm);
-                    cm = __viaddmin_s32(a[i].z, b[j].z, cm);
-                    cm = __viaddmin_s32(a[i].w, b[j].w, cm);
+                    T cm = E::addmin(a[i].x, b[j].x, E::start());
+                    cm = E::addmin(a[i].y, b[j].y, cm);
+                    cm = E::addmin(a[i].z, b[j].z, cm);
+                    cm = E::addmin(a[i].w, b[j].w, cm);
                     if (cm < val[i][j]) {
                         val[i][j] = cm;
-                        idx[i][j] = k0 + (a[i].x + b[j].x == cm   ? 0
-                                          : a[i].y + b[j].y == cm ? 1
-                                          : a[i].z + b[j].z == cm ? 2
-                                                                  : 3);
+                        idx[i][j] = k0 + (E::sum(a[i].x, b[j].x) == cm   ? 0
+                                          : E::sum(a[i].y, b[j].y) == cm ? 1
+                                          : E::sum(a[i].z, b[j].z) == cm ? 2
+                                                                         : 3);
                     }
                 }
         }
@@ -102,9 +136,9 @@ paths_square_kernel(int n, const int *__restrict__ D, long long ldd, const int *
         for (int j = 0; j < 4; ++j) {
             const int r = bm + tr + 16 * i, c = bn + tc + 16 * j;
             if (r < n && c < n) {
-                const int d = val[i][j] >= kClampI32 ? kInfI32 : val[i][j];
+                const T d = E::finish(val[i][j]);
                 const int k = idx[i][j];
-                const int nx = d == kInfI32 ? -1 : (k == r ? N[(long long)r * n + c] : N[(long long)r * n + k]);
+                const int nx = E::is_inf(d) ? -1 : (k == r ? N[(long long)r * n + c] : N[(long long)r * n + k]);
                 if (d != D[(long long)r * ldd + c] || nx != N[(long long)r * n + c]) ch = true;
                 D2[(long long)r * n + c] = d;
                 N2[(long long)r * n + c] = nx;
@@ -187,22 +221,57 @@ __global__ void __launch_bounds__(256) paths_decode_kernel(const int *K, const i
     }
 }
 
-__global__ void next_init_kernel(const int *__restrict__ W, long long n, int *__restrict__ N) {
+template <typename T>
+__global__ void next_init_kernel(const T *__restrict__ W, long long n, int *__restrict__ N) {
     const long long total = n * n;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long r = idx / n, c = idx % n;
-        N[idx] = r == c ? (int)r : (W[idx] == kInfI32 ? -1 : (int)c);
+        N[idx] = r == c ? (int)r : (PathsElem<T>::is_inf(W[idx]) ? -1 : (int)c);
     }
+}
+
+// Weight domain of the binary32 next-hop solve: zero diagonal, every other
+// entry >= 0 or +inf (no NaN, no -inf).  out: number of entries outside it.
+__global__ void paths_scan_f32_kernel(const float *__restrict__ W, long long n, int *out) {
+    const long long total = n * n;
+    int bad = 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long r = idx / n, c = idx % n;
+        const float v = W[idx];
+        bad += r == c ? (v != 0.f) : !(v >= 0.f);  // NaN and negative values (and -inf) fail v >= 0
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(out, bad);
 }
 
 }  // namespace
 
-cudaError_t launch_next_init(const int *W, long long n, int *N, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+static int paths_grid(long long n) {
     long long b = (n * n + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
-    next_init_kernel<<<(int)b, 256, 0, st>>>(W, n, N);
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_next_init(const int *W, long long n, int *N, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    next_init_kernel<int><<<paths_grid(n), 256, 0, st>>>(W, n, N);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_next_init_f32(const float *W, long long n, int *N, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    next_init_kernel<float><<<paths_grid(n), 256, 0, st>>>(W, n, N);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_paths_scan_f32(const float *W, long long n, int *bad, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    paths_scan_f32_kernel<<<paths_grid(n), 256, 0, st>>>(W, n, bad);
     note_launch();
     return cudaGetLastError();
 }
@@ -226,15 +295,26 @@ cudaError_t launch_paths_decode(const int *K, const int *D, const int *N, long l
     return cudaGetLastError();
 }
 
-cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *Dt, long long ldt, const int *N,
-                                int *D2, int *N2, int *changed, cudaStream_t st) {
+template <typename T>
+static cudaError_t launch_paths_square_t(int n, const T *D, long long ldd, const T *Dt, long long ldt, const int *N,
+                                         T *D2, int *N2, int *changed, cudaStream_t st) {
     const int tiles = (n + PBM - 1) / PBM;
     const int vec_a = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && ((ldd & 3) == 0);
-    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(paths_square_kernel), PSMEM);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(paths_square_kernel<T>), PSMEM);
     if (e != cudaSuccess) return e;
-    paths_square_kernel<<<tiles * tiles, PNT, PSMEM, st>>>(n, D, ldd, Dt, ldt, N, D2, N2, changed, vec_a);
+    paths_square_kernel<T><<<tiles * tiles, PNT, PSMEM, st>>>(n, D, ldd, Dt, ldt, N, D2, N2, changed, vec_a);
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_paths_square(int n, const int *D, long long ldd, const int *Dt, long long ldt, const int *N,
+                                int *D2, int *N2, int *changed, cudaStream_t st) {
+    return launch_paths_square_t<int>(n, D, ldd, Dt, ldt, N, D2, N2, changed, st);
+}
+
+cudaError_t launch_paths_square_f32(int n, const float *D, long long ldd, const float *Dt, long long ldt,
+                                    const int *N, float *D2, int *N2, int *changed, cudaStream_t st) {
+    return launch_paths_square_t<float>(n, D, ldd, Dt, ldt, N, D2, N2, changed, st);
 }
 
 }  // namespace btas

@@ -138,6 +138,15 @@ def test_apsp_u16_storage_paths_fw_noalloc(btas, oracle_mod):
     _check(gD, gN)
     np.testing.assert_array_equal(host(gD.t), ref)
     np.testing.assert_array_equal(host(gN.t), host(Nx))
+    # binary32 next-hop matrix into guarded outputs
+    Wf = np.where(W >= 0x3FFFFFFF, np.float32(np.inf), W.astype(np.float32)).astype(np.float32)
+    gWf, gDf, gNf = Guarded(Wf), _out((n, n), np.float32), _out((n, n), np.int32)
+    btas.check(btas.btas_apsp_paths_f32(n, gWf.t.data_ptr(), gDf.t.data_ptr(), gNf.t.data_ptr(),
+                                        btas.APSP_EARLY_EXIT, None, st))
+    _check(gWf, gDf, gNf)
+    assert gWf.unchanged()
+    np.testing.assert_array_equal(host(gDf.t), np.where(ref >= 0x3FFFFFFF, np.float32(np.inf), ref.astype(np.float32)))
+    np.testing.assert_array_equal(host(gNf.t), host(Nx))
     # blocked Floyd-Warshall
     gF = _out((n, n), np.int32)
     btas.apsp_fw(gW.t, out=gF.t)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import gen
-from golden import as_i32, load
+from golden import as_f32, as_i32, load
 from gpu_util import INF, dev, host
 
 pytestmark = pytest.mark.gpu
@@ -93,3 +93,50 @@ def test_large_weights(btas, oracle_mod, whi):
     D, Nx = btas.apsp_paths(dev(W))
     np.testing.assert_array_equal(host(D), ref_d)
     np.testing.assert_array_equal(host(Nx), ref_n)
+
+
+def _f32_graph(seed, n, p, integer_weights):
+    """A binary32 graph: +inf for no edge, zero diagonal; weights U[0, 1) or
+    small integers (many ties)."""
+    W = gen.random_graph(seed, n, n, p, 1, 6).astype(np.float32)
+    W[W == np.float32(INF)] = np.float32(np.inf)
+    if not integer_weights:
+        u = gen.uniform_f32(seed + 1, n, (n, n))
+        W = np.where(np.isinf(W) | (np.eye(n) == 1), W, u).astype(np.float32)
+    return W
+
+
+def test_f32_hand_worked_rounding_tie(btas):
+    """The binary32 fixture whose tie only the rounding creates."""
+    g = load("apsp_paths_f32_rounding_3node.txt")
+    D, Nx = btas.apsp_paths(dev(as_f32(g["W"])))
+    np.testing.assert_array_equal(host(D).view(np.uint32), as_f32(g["D"]).view(np.uint32))
+    np.testing.assert_array_equal(host(Nx), as_i32(g["N"]))
+
+
+@pytest.mark.parametrize("integer_weights", [False, True])
+@pytest.mark.parametrize("n", [2, 5, 63, 64, 65, 130, 300])
+def test_f32_matches_oracle(btas, oracle_mod, n, integer_weights):
+    """Distances bit for bit and next hops equal to the oracle's binary32
+    squaring, over ragged sizes around the 64-wide tile, with rounding in
+    play (weights U[0, 1)) and with many ties (integer weights)."""
+    W = _f32_graph(400 + n, n, 0.2 if n > 8 else 0.6, integer_weights)
+    D, Nx = btas.apsp_paths(dev(W))
+    d_ref, n_ref = oracle_mod.apsp_paths(W)
+    np.testing.assert_array_equal(host(D).view(np.uint32), d_ref.view(np.uint32))
+    np.testing.assert_array_equal(host(Nx), n_ref)
+
+
+def test_f32_domain_is_checked(btas):
+    """NaN, a negative weight or a non-zero diagonal entry: BTAS_ERR_ARG,
+    nothing written."""
+    import torch
+    base = _f32_graph(410, 40, 0.2, False)
+    for r, c, v in ((3, 4, np.float32("nan")), (5, 6, np.float32(-0.5)), (7, 7, np.float32(1.0)),
+                    (8, 9, np.float32("-inf"))):
+        W = base.copy()
+        W[r, c] = v
+        with pytest.raises(btas.BtasError) as ei:
+            btas.apsp_paths(dev(W))
+        assert ei.value.status == 1
+    torch.cuda.synchronize()
