@@ -65,10 +65,12 @@ def parse():
     p.add_argument("--probe-mix", type=int, default=None,
                    help="with --only probe: run this one mix (btas_measure_issue_rate_ex) and nothing else")
     p.add_argument("--probe-ctas", type=int, default=1, help="with --probe-mix: CTAs per SM (1 or 2)")
+    p.add_argument("--paths-dtype", choices=["i32", "f32"], default="i32",
+                   help="with --only paths: int32 or binary32 weights")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
     p.add_argument("--only", default=None,
-                   choices=["kernels", "batched", "serve", "next", "tune", "configs", "probe", "mid"],
+                   choices=["kernels", "batched", "serve", "next", "tune", "configs", "probe", "mid", "paths"],
                    help="profiling aids: run one part alone and print its JSON (not a bench line)")
     return p.parse_args()
 
@@ -1080,8 +1082,26 @@ def next_rows(args, btas, torch):
     terms_p = min(btas.btas_apsp_squarings(np_), sq_p + 1) * float(np_) ** 3
     out["apsp_paths"] = {"n": np_, "ms": round(t_p * 1e3, 3), "squarings_computed": int(terms_p / float(np_) ** 3),
                          "terms_tops": round(terms_p / t_p / 1e12, 2)}
+    # the same solve on the argmin kernel (group records, no keys), and on
+    # binary32 weights (the same integer weights, so the same distances)
+    os.environ["BTAS_PATHS_NO_KEYED"] = "1"
+    try:
+        t_pa = timed(lambda: btas.apsp_paths(Wp), reps=1)
+        sq_pa = btas.apsp_paths(Wp, info=True)[2]["squarings"]
+    finally:
+        os.environ.pop("BTAS_PATHS_NO_KEYED", None)
+    terms_pa = min(btas.btas_apsp_squarings(np_), sq_pa + 1) * float(np_) ** 3
+    out["apsp_paths_argmin_int32"] = {"n": np_, "ms": round(t_pa * 1e3, 3),
+                                      "squarings_computed": int(terms_pa / float(np_) ** 3),
+                                      "terms_tops": round(terms_pa / t_pa / 1e12, 2)}
     Wf = torch.where(W[:np_, :np_] == btas.INF_I32, torch.tensor(float("inf"), device="cuda"),
                      W[:np_, :np_].float()).contiguous()
+    t_pf = timed(lambda: btas.apsp_paths(Wf), reps=1)
+    sq_pf = btas.apsp_paths(Wf, info=True)[2]["squarings"]
+    terms_pf = min(btas.btas_apsp_squarings(np_), sq_pf + 1) * float(np_) ** 3
+    out["apsp_paths_fp32"] = {"n": np_, "ms": round(t_pf * 1e3, 3),
+                              "squarings_computed": int(terms_pf / float(np_) ** 3),
+                              "terms_tops": round(terms_pf / t_pf / 1e12, 2)}
     t_c = timed(lambda: btas.closure(Wf, "min"), reps=1)
     sq_c = btas.closure(Wf, "min", info=True)[1]["squarings"]
     terms_c = min(btas.btas_apsp_squarings(np_) + 1, sq_c + 1) * float(np_) ** 3
@@ -1171,6 +1191,27 @@ def run_only(args):
             ts.append(round(e0.elapsed_time(e1) * 1e3, 1))
         print(json.dumps({"only": "mid", "n": n, "us_per_call": ts, "squarings_changing": info["squarings"],
                           "path": info["path"]}))
+    elif args.only == "paths":
+        # one next-hop solve at --n on the argmin kernel (no keyed squarings):
+        # p = 0.01, int32 weights in [1, 1000] or binary32 U[0, 1) on the same edges
+        import gen
+        import numpy as np
+        n = args.n
+        Wi = gen.random_graph(1, 3, n, 0.01, 1, 1000)
+        if args.paths_dtype == "f32":
+            W = np.where(Wi == btas.INF_I32, np.float32(np.inf), gen.uniform_f32(2, 5, (n, n))).astype(np.float32)
+            np.fill_diagonal(W, 0)
+        else:
+            W = Wi
+        Wd = torch.from_numpy(W).cuda()
+        os.environ["BTAS_PATHS_NO_KEYED"] = "1"
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, info = btas.apsp_paths(Wd, info=True)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "paths", "n": n, "dtype": args.paths_dtype, "ms": round(e0.elapsed_time(e1), 3),
+                          "squarings_changing": info["squarings"]}))
     else:
         print(json.dumps({"only": "serve", **serve(args, btas, torch)}))
     return 0

@@ -7,13 +7,21 @@
 // i -> k* -> j).  N_0[i][j] = j for an edge, i on the diagonal, -1 otherwise.
 // With positive weights, following N from i reaches j along a shortest path.
 //
-// Kernel: 64 x 64 output tile, 256 threads with 4 x 4 outputs each, k staged
-// through a cp.async ring (A = D rows, B = D^T rows, both k-contiguous).  Per
-// group of 4 consecutive k: the group minimum by DPX add-min (one per term);
-// only if it is strictly smaller than the running minimum is the first k of
-// the group attaining it recorded.  k increases monotonically per thread, so
-// the smallest minimising k survives.
+// Argmin kernel: BM x BN output tile, TM x TN outputs per thread (warps of
+// 4 x 8 threads, as in the product kernels), k staged through a cp.async
+// ring (A = D rows, B = D^T rows, both k-contiguous).  k is taken in groups
+// of 8: the running minimum absorbs the group's 8 terms (int32: DPX add-min,
+// or, on NS of the TN columns, multiply-adds by a runtime one and 3-input
+// mins, which moves the adds to the FMA pipe; binary32: two-lane
+// round-to-nearest adds and 3-input mins), and
+// when that lowers it the thread records the GROUP, one compare and one
+// select per 8 terms.  Groups arrive in increasing k and only a strict
+// decrease moves the record, so the recorded group is the first one that
+// attains the final minimum.  The epilogue re-forms that group's 8 sums from
+// D and D^T with the same rounding (so equality is exact) and takes the
+// smallest k among them: the smallest minimising k overall.
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -23,10 +31,28 @@ namespace btas {
 
 namespace {
 
-constexpr int PBM = 64, PBK = 32, PLD = PBK + 4, PST = 3, PNT = 256;
-constexpr int PSTAGE = 2 * PBM * PLD;
+constexpr int kGroup = 8;  // k per recorded group
 
-constexpr int PSMEM = PST * PSTAGE * 4;  // 54 KiB: dynamic shared memory
+// BK: k per shared-memory stage, ST: stages, MINB: CTAs per SM the registers
+// are sized for, UNR: groups per unrolled step, NS: int32 columns on the FMA
+// pipe.
+template <int BM_, int BN_, int TM_, int TN_, int BK_, int ST_, int MINB_, int UNR_ = 1, int NS_ = 0>
+struct ArgCfg {
+    static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, BK = BK_, ST = ST_, MINB = MINB_, UNR = UNR_;
+    static constexpr int NS = NS_;
+    static constexpr int WARPS_M = BM / (4 * TM), WARPS_N = BN / (8 * TN);
+    static constexpr int NT = WARPS_M * WARPS_N * 32;
+    static constexpr int LD = BK + 4;  // padded row: conflict-free 128-bit fragment loads
+    static constexpr int STAGE = (BM + BN) * LD;
+    static constexpr int SMEM = ST * STAGE * 4;
+    static_assert(BM % (4 * TM) == 0 && BN % (8 * TN) == 0 && BK % kGroup == 0, "tile shape");
+};
+// 64 x 64 tiles, 4 x 4 outputs per thread, two CTAs per SM, two groups per
+// unrolled step; on 2 of the 4 columns the int32 form adds on the FMA pipe.
+// Measured on GB300 against 128 x 128 (8 x 8 per thread, one CTA per SM),
+// 128 x 64, 32 x 64 (four CTAs per SM), k depth 64 and 4 stages: those were
+// 3-25 % slower, the DPX-only int32 form 3-9 % slower.
+using ArgTile = ArgCfg<64, 64, 4, 4, 32, 3, 2, 2, 2>;
 
 // Element type of the argmin squaring: int32 (one DPX add-min per term, INF
 // absorbed by the clamp at INF - 2^28) or binary32 (one round-to-nearest add
@@ -35,116 +61,187 @@ template <typename T>
 struct PathsElem;
 template <>
 struct PathsElem<int> {
-    using V = int4;
     static __device__ __forceinline__ int start() { return 0x7FFFFFFF; }
     static __device__ __forceinline__ int inf() { return kInfI32; }
-    // min(acc, a + b)
-    static __device__ __forceinline__ int addmin(int a, int b, int acc) { return __viaddmin_s32(a, b, acc); }
     static __device__ __forceinline__ int sum(int a, int b) { return a + b; }
     static __device__ __forceinline__ int finish(int v) { return v >= kClampI32 ? kInfI32 : v; }
     static __device__ __forceinline__ bool is_inf(int v) { return v == kInfI32; }
+    // min(v, the 8 sums a[q] + b[q])
+    static __device__ __forceinline__ int fold8(int v, const uint4 &a0, const uint4 &a1, const uint4 &b0,
+                                                const uint4 &b1) {
+        v = __viaddmin_s32((int)a0.x, (int)b0.x, v);
+        v = __viaddmin_s32((int)a0.y, (int)b0.y, v);
+        v = __viaddmin_s32((int)a0.z, (int)b0.z, v);
+        v = __viaddmin_s32((int)a0.w, (int)b0.w, v);
+        v = __viaddmin_s32((int)a1.x, (int)b1.x, v);
+        v = __viaddmin_s32((int)a1.y, (int)b1.y, v);
+        v = __viaddmin_s32((int)a1.z, (int)b1.z, v);
+        v = __viaddmin_s32((int)a1.w, (int)b1.w, v);
+        return v;
+    }
+    // The same minimum with the 8 adds as multiply-adds by a runtime one (FMA
+    // pipe) and four 3-input mins (ALU pipe).
+    static __device__ __forceinline__ int fold8_fma(int v, const uint4 &a0, const uint4 &a1, const uint4 &b0,
+                                                    const uint4 &b1, int one) {
+        v = __vimin3_s32(v, imad_add((int)a0.x, one, (int)b0.x), imad_add((int)a0.y, one, (int)b0.y));
+        v = __vimin3_s32(v, imad_add((int)a0.z, one, (int)b0.z), imad_add((int)a0.w, one, (int)b0.w));
+        v = __vimin3_s32(v, imad_add((int)a1.x, one, (int)b1.x), imad_add((int)a1.y, one, (int)b1.y));
+        v = __vimin3_s32(v, imad_add((int)a1.z, one, (int)b1.z), imad_add((int)a1.w, one, (int)b1.w));
+        return v;
+    }
 };
 template <>
 struct PathsElem<float> {
-    using V = float4;
     static __device__ __forceinline__ float start() { return __int_as_float(0x7f800000); }
     static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
-    static __device__ __forceinline__ float addmin(float a, float b, float acc) { return fminf(__fadd_rn(a, b), acc); }
     static __device__ __forceinline__ float sum(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float finish(float v) { return v; }
     static __device__ __forceinline__ bool is_inf(float v) { return isinf(v); }
+    static __device__ __forceinline__ float fold8(float v, const uint4 &a0, const uint4 &a1, const uint4 &b0,
+                                                  const uint4 &b1) {
+        float l, h;
+        unpack2(fadd2(pack64(a0.x, a0.y), pack64(b0.x, b0.y)), l, h);
+        v = fsel3<kMin>(v, l, h);
+        unpack2(fadd2(pack64(a0.z, a0.w), pack64(b0.z, b0.w)), l, h);
+        v = fsel3<kMin>(v, l, h);
+        unpack2(fadd2(pack64(a1.x, a1.y), pack64(b1.x, b1.y)), l, h);
+        v = fsel3<kMin>(v, l, h);
+        unpack2(fadd2(pack64(a1.z, a1.w), pack64(b1.z, b1.w)), l, h);
+        v = fsel3<kMin>(v, l, h);
+        return v;
+    }
+    static __device__ __forceinline__ float fold8_fma(float v, const uint4 &a0, const uint4 &a1, const uint4 &b0,
+                                                      const uint4 &b1, int) {
+        return fold8(v, a0, a1, b0, b1);
+    }
 };
 
 template <typename T>
-__global__ void __launch_bounds__(PNT, 2)
+__device__ __forceinline__ T as_elem(uint32_t u) {
+    if constexpr (std::is_same<T, int>::value) return (int)u;
+    else return __uint_as_float(u);
+}
+
+// The 8 values v[k0 .. k0+7] of one row (k >= n: never read, left at fill).
+template <typename T>
+__device__ __forceinline__ void load_group(const T *row, int k0, int n, bool vec, uint32_t (&v)[kGroup]) {
+    if (vec && k0 + kGroup <= n) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(row + k0));
+        const uint4 y = __ldg(reinterpret_cast<const uint4 *>(row + k0 + 4));
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+    } else {
+        const uint32_t *r = reinterpret_cast<const uint32_t *>(row);
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) v[q] = k0 + q < n ? __ldg(r + k0 + q) : 0u;
+    }
+}
+
+template <class Cfg, typename T>
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MINB)
 paths_square_kernel(int n, const T *__restrict__ D, long long ldd, const T *__restrict__ Dt, long long ldt,
-                    const int *__restrict__ N, T *__restrict__ D2, int *__restrict__ N2, int *changed, int vec_a) {
+                    const int *__restrict__ N, T *__restrict__ D2, int *__restrict__ N2, int *changed, int vec_a,
+                    int one) {
     using E = PathsElem<T>;
-    using V = typename E::V;
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, TM = Cfg::TM, TN = Cfg::TN, BK = Cfg::BK, LD = Cfg::LD;
+    constexpr int ST = Cfg::ST, NT = Cfg::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x;
-    const int tiles = (n + PBM - 1) / PBM;
-    const int bm = (blockIdx.x / tiles) * PBM, bn = (blockIdx.x % tiles) * PBM;
-    const int tr = tid >> 4, tc = tid & 15;
-    T val[4][4];
-    int idx[4][4];
+    int tm, tn;
+    raster(blockIdx.x, (n + BM - 1) / BM, (n + BN - 1) / BN, 8, tm, tn);
+    const int bm = tm * BM, bn = tn * BN;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wm = warp / Cfg::WARPS_N, wn = warp % Cfg::WARPS_N;
+    const int row_base = wm * (4 * TM) + (lane >> 3);  // + 4*i
+    const int col_base = wn * (8 * TN) + (lane & 7);   // + 8*j
+    T val[TM][TN];
+    int grp[TM][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
             val[i][j] = E::start();
-            idx[i][j] = -1;
+            grp[i][j] = -1;
         }
-    const int KT = (n + PBK - 1) / PBK;
+    const int KT = (n + BK - 1) / BK;
     auto load = [&](int s, int kt) {
-        T *sa = smem + s * PSTAGE;
-        T *sb = sa + PBM * PLD;
-        stage_rows<T, PBM, PBK, PLD, PNT>(sa, D, ldd, bm, n, kt * PBK, n, vec_a != 0, E::inf(), tid, true);
-        stage_rows<T, PBM, PBK, PLD, PNT>(sb, Dt, ldt, bn, n, kt * PBK, n, true, E::inf(), tid, true);
+        T *sa = smem + s * Cfg::STAGE;
+        T *sb = sa + BM * LD;
+        stage_rows<T, BM, BK, LD, NT>(sa, D, ldd, bm, n, kt * BK, n, vec_a != 0, E::inf(), tid, true);
+        stage_rows<T, BN, BK, LD, NT>(sb, Dt, ldt, bn, n, kt * BK, n, true, E::inf(), tid, true);
     };
 #pragma unroll
-    for (int s = 0; s < PST - 1; ++s) {
+    for (int s = 0; s < ST - 1; ++s) {
         if (s < KT) load(s, s);
         cp_async_commit();
     }
     for (int kt = 0; kt < KT; ++kt) {
-        cp_async_wait<PST - 2>();
+        cp_async_wait<ST - 2>();
         __syncthreads();
-        if (kt + PST - 1 < KT) load((kt + PST - 1) % PST, kt + PST - 1);
+        if (kt + ST - 1 < KT) load((kt + ST - 1) % ST, kt + ST - 1);
         cp_async_commit();
-        const T *sa = smem + (kt % PST) * PSTAGE;
-        const T *sb = sa + PBM * PLD;
-#pragma unroll 2
-        for (int kk = 0; kk < PBK; kk += 4) {
-            V a[4], b[4];
+        const T *sa = smem + (kt % ST) * Cfg::STAGE;
+        const T *sb = sa + BM * LD;
+#pragma unroll Cfg::UNR
+        for (int kk = 0; kk < BK; kk += kGroup) {
+            const int g = (kt * BK + kk) / kGroup;
+            uint4 b0[TN], b1[TN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const V *>(sa + (tr + 16 * i) * PLD + kk);
+            for (int j = 0; j < TN; ++j) {
+                const T *p = sb + (col_base + 8 * j) * LD + kk;
+                b0[j] = *reinterpret_cast<const uint4 *>(p);
+                b1[j] = *reinterpret_cast<const uint4 *>(p + 4);
+            }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = *reinterpret_cast<const V *>(sb + (tc + 16 * j) * PLD + kk);
-            const int k0 = kt * PBK + kk;
-            // Two levels: the minimum of the 4 sums of this k-group costs one
-            // add-then-min per term; only when it beats the running minimum
-            // (rarely, once the minimum has settled) is the first k of the
-            // group that attains it looked up (the sums are recomputed with
-            // the same rounding, so equality is exact).  An equal group
-            // minimum keeps the earlier, smaller k.  Same result as a
-            // per-term argmin.
+            for (int i = 0; i < TM; ++i) {
+                const T *p = sa + (row_base + 4 * i) * LD + kk;
+                const uint4 a0 = *reinterpret_cast<const uint4 *>(p);
+                const uint4 a1 = *reinterpret_cast<const uint4 *>(p + 4);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    T cm = E::addmin(a[i].x, b[j].x, E::start());
-                    cm = E::addmin(a[i].y, b[j].y, cm);
-                    cm = E::addmin(a[i].z, b[j].z, cm);
-                    cm = E::addmin(a[i].w, b[j].w, cm);
-                    if (cm < val[i][j]) {
-                        val[i][j] = cm;
-                        idx[i][j] = k0 + (E::sum(a[i].x, b[j].x) == cm   ? 0
-                                          : E::sum(a[i].y, b[j].y) == cm ? 1
-                                          : E::sum(a[i].z, b[j].z) == cm ? 2
-                                                                         : 3);
-                    }
+                for (int j = 0; j < TN; ++j) {
+                    const T v = j < Cfg::NS ? E::fold8_fma(val[i][j], a0, a1, b0[j], b1[j], one)
+                                            : E::fold8(val[i][j], a0, a1, b0[j], b1[j]);
+                    grp[i][j] = v < val[i][j] ? g : grp[i][j];
+                    val[i][j] = v;
                 }
+            }
         }
     }
     cp_async_wait<0>();
+
+    // Epilogue: the smallest k of the recorded group whose sum equals the
+    // minimum, then N'[r][c] = -1 (INF), N[r][c] (k == r) or N[r][k].
+    const bool vec_d = vec_a != 0;
     bool ch = false;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i) {
+        const int r = bm + row_base + 4 * i;
+        if (r >= n) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = bm + tr + 16 * i, c = bn + tc + 16 * j;
-            if (r < n && c < n) {
-                const T d = E::finish(val[i][j]);
-                const int k = idx[i][j];
-                const int nx = E::is_inf(d) ? -1 : (k == r ? N[(long long)r * n + c] : N[(long long)r * n + k]);
-                if (d != D[(long long)r * ldd + c] || nx != N[(long long)r * n + c]) ch = true;
-                D2[(long long)r * n + c] = d;
-                N2[(long long)r * n + c] = nx;
+        for (int j = 0; j < TN; ++j) {
+            const int c = bn + col_base + 8 * j;
+            if (c >= n) continue;
+            const T raw = val[i][j];
+            const T d = E::finish(raw);
+            int nx = -1;
+            if (!E::is_inf(d)) {
+                const int k0 = max(grp[i][j], 0) * kGroup;
+                uint32_t x[kGroup], y[kGroup];
+                load_group<T>(D + (long long)r * ldd, k0, n, vec_d, x);
+                load_group<T>(Dt + (long long)c * ldt, k0, n, true, y);
+                int k = k0;
+#pragma unroll
+                for (int q = kGroup - 1; q >= 0; --q)
+                    if (k0 + q < n && E::sum(as_elem<T>(x[q]), as_elem<T>(y[q])) == raw) k = k0 + q;
+                nx = N[(long long)r * n + (k == r ? c : k)];
             }
+            if (d != D[(long long)r * ldd + c] || nx != N[(long long)r * n + c]) ch = true;
+            D2[(long long)r * n + c] = d;
+            N2[(long long)r * n + c] = nx;
         }
-    if (__any_sync(0xffffffffu, ch) && (tid & 31) == 0) atomicOr(changed, 1);
+    }
+    if (__any_sync(0xffffffffu, ch) && lane == 0) atomicOr(changed, 1);
 }
 
 // Keyed squaring.  While every finite entry of D is <= kKeyMax and n <=
@@ -298,11 +395,14 @@ cudaError_t launch_paths_decode(const int *K, const int *D, const int *N, long l
 template <typename T>
 static cudaError_t launch_paths_square_t(int n, const T *D, long long ldd, const T *Dt, long long ldt, const int *N,
                                          T *D2, int *N2, int *changed, cudaStream_t st) {
-    const int tiles = (n + PBM - 1) / PBM;
+    using Cfg = ArgTile;
+    if (n <= 0) return cudaSuccess;
     const int vec_a = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && ((ldd & 3) == 0);
-    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(paths_square_kernel<T>), PSMEM);
+    const int tiles = ((n + Cfg::BM - 1) / Cfg::BM) * ((n + Cfg::BN - 1) / Cfg::BN);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void *>(paths_square_kernel<Cfg, T>), Cfg::SMEM);
     if (e != cudaSuccess) return e;
-    paths_square_kernel<T><<<tiles * tiles, PNT, PSMEM, st>>>(n, D, ldd, Dt, ldt, N, D2, N2, changed, vec_a);
+    paths_square_kernel<Cfg, T><<<tiles, Cfg::NT, Cfg::SMEM, st>>>(n, D, ldd, Dt, ldt, N, D2, N2, changed,
+                                                                          vec_a, 1);
     note_launch();
     return cudaGetLastError();
 }

@@ -6,7 +6,7 @@ import pytest
 
 import gen
 from golden import as_f32, as_i32, load
-from gpu_util import INF, dev, host
+from gpu_util import INF, bits, dev, host
 
 pytestmark = pytest.mark.gpu
 
@@ -140,3 +140,63 @@ def test_f32_domain_is_checked(btas):
             btas.apsp_paths(dev(W))
         assert ei.value.status == 1
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("dtype", ["i32", "f32"])
+@pytest.mark.parametrize("n", [8, 9, 31, 65, 130, 300, 513])
+def test_argmin_matches_oracle(btas, oracle_mod, n, dtype):
+    """The argmin squaring at sizes that leave ragged row, column and k edges
+    and a group of 8 k cut by n: distances bit for bit and next hops equal to
+    the oracle's.  int32 weights 1..20 (many ties, keyed squaring off; the
+    int32 kernel mixes two add forms across columns) and binary32 weights
+    U[0, 1) (rounding in play)."""
+    if dtype == "i32":
+        W = gen.random_graph(500 + n, n, n, 0.08 if n > 10 else 0.4, 1, 20)
+    else:
+        W = _f32_graph(600 + n, n, 0.08 if n > 10 else 0.4, False)
+    d_ref, n_ref = oracle_mod.apsp_paths(W)
+    with env(BTAS_PATHS_NO_KEYED="1"):
+        D, Nx = btas.apsp_paths(dev(W))
+    np.testing.assert_array_equal(bits(host(D)), bits(d_ref))
+    np.testing.assert_array_equal(host(Nx), n_ref)
+
+
+@pytest.mark.parametrize("dtype", ["i32", "f32"])
+def test_argmin_large(btas, oracle_mod, dtype):
+    """n = 2100 (32 full tiles and a ragged one per side) on the argmin
+    kernel.  Sampled distance rows equal the oracle's Dijkstra rows (integer
+    weights, exact in binary32 too) and sampled next-hop walks are shortest
+    paths.  For int32 the next-hop matrix also equals the keyed squaring's,
+    which gets the smallest minimising k from a plain product of encoded
+    keys instead of from group records."""
+    n = 2100
+    Wi = gen.random_graph(700, n, n, 0.01, 1, 9)
+    W = Wi if dtype == "i32" else np.where(Wi == INF, np.float32(np.inf), Wi.astype(np.float32)).astype(np.float32)
+    with env(BTAS_PATHS_NO_KEYED="1"):
+        D, Nx = btas.apsp_paths(dev(W))
+    D, Nx = host(D), host(Nx)
+    if dtype == "i32":
+        with env(BTAS_PATHS_NO_KEYED="0"):
+            Dk, Nk = btas.apsp_paths(dev(W))
+        np.testing.assert_array_equal(D, host(Dk))
+        np.testing.assert_array_equal(Nx, host(Nk))
+    srcs = [0, 1, 777, 1500, n - 1]
+    rows = oracle_mod.dijkstra_rows(Wi, srcs)
+    Dr = D[srcs]
+    if dtype == "f32":
+        Dr = np.where(np.isinf(Dr), INF, Dr).astype(np.int32)
+    np.testing.assert_array_equal(Dr, rows)
+    rng = np.random.default_rng(1)
+    for _ in range(300):
+        i, j = (int(x) for x in rng.integers(0, n, 2))
+        if (np.isinf(D[i, j]) if dtype == "f32" else D[i, j] == INF):
+            assert Nx[i, j] == -1
+            continue
+        v, tot, steps = i, 0, 0
+        while v != j:
+            u = int(Nx[v, j])
+            tot += int(Wi[v, u])
+            v = u
+            steps += 1
+            assert steps <= n
+        assert tot == int(D[i, j])
