@@ -67,10 +67,12 @@ def parse():
     p.add_argument("--probe-ctas", type=int, default=1, help="with --probe-mix: CTAs per SM (1 or 2)")
     p.add_argument("--paths-dtype", choices=["i32", "f32"], default="i32",
                    help="with --only paths: int32 or binary32 weights")
+    p.add_argument("--fw-int32", action="store_true",
+                   help="with --only fw: keep phase 3 on the int32 kernel (no packed phase 3)")
     p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-rates", default="100,300,1000,3000,5000")
     p.add_argument("--only", default=None,
-                   choices=["kernels", "batched", "serve", "next", "tune", "configs", "probe", "mid", "paths"],
+                   choices=["kernels", "batched", "serve", "next", "tune", "configs", "probe", "mid", "paths", "fw"],
                    help="profiling aids: run one part alone and print its JSON (not a bench line)")
     return p.parse_args()
 
@@ -1191,6 +1193,25 @@ def run_only(args):
             ts.append(round(e0.elapsed_time(e1) * 1e3, 1))
         print(json.dumps({"only": "mid", "n": n, "us_per_call": ts, "squarings_changing": info["squarings"],
                           "path": info["path"]}))
+    elif args.only == "fw":
+        # blocked Floyd-Warshall at --n (p = 0.01, w in [1, 1000]): one warm-up
+        # solve and three timed ones
+        import gen
+        n = args.n
+        if args.fw_int32:
+            os.environ["BTAS_FW_NO_U16"] = "1"
+        W = torch.from_numpy(gen.random_graph(gen.BASE_SEED, 7, n, 0.01, 1, 1000)).cuda()
+        D = btas.apsp_fw(W)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            btas.apsp_fw(W, out=D)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(round(e0.elapsed_time(e1), 3))
+        print(json.dumps({"only": "fw", "n": n, "int32_phase3": bool(args.fw_int32), "ms": ts,
+                          "terms_tops": round(float(n) ** 3 / min(ts) / 1e9, 2)}))
     elif args.only == "paths":
         # one next-hop solve at --n on the argmin kernel (no keyed squarings):
         # p = 0.01, int32 weights in [1, 1000] or binary32 U[0, 1) on the same edges

@@ -1282,27 +1282,11 @@ btas_status btas_apsp_fw(int64_t n, const int32_t *W, int32_t *D, void *stream) 
         // row panel D[o:o+bw, :] transposed into RPT (n x B): the k-contiguous B operand
         BTAS_CUDA(launch_transpose4(D + o * n, n, (int)bw, (int)n, RPT, B, 0, allow16 ? state + 1 : nullptr, st),
                   "panel transpose");
-        // int32 phase 3 on the rectangles around the pivot block (and around
-        // block kb + 1 when it runs ahead)
-        const long long rr[2][2] = {{0, o}, {o1 + bw1, n}};
-        for (int ri = 0; ri < 2; ++ri)
-            for (int ci = 0; ci < 2; ++ci) {
-                const long long r0 = rr[ri][0], r1 = rr[ri][1], c0 = rr[ci][0], c1 = rr[ci][1];
-                if (r1 <= r0 || c1 <= c0) continue;
-                GemmArgs a{};
-                a.m = (int)(r1 - r0);
-                a.n = (int)(c1 - c0);
-                a.k = (int)bw;
-                a.A = D + r0 * n + o; a.lda = n;
-                a.Bt = RPT + c0 * B; a.ldb = B;
-                a.C = D + r0 * n + c0; a.ldc = n;
-                a.accumulate = 1;
-                a.vec_a = aligned16(a.A, n);
-                a.vec_b = aligned16(a.Bt, B);
-                a.bypass = allow16 ? state : nullptr;  // the packed phase 3 ran instead
-                btas_status r = run_nt(BTAS_I32, kMin, a, st);
-                if (r != BTAS_OK) return r;
-            }
+        // int32 phase 3 on every tile outside block row and column kb (and
+        // kb + 1 when it runs ahead), in one launch
+        BTAS_CUDA(launch_fw_phase3_i32(D, n, o, (int)bw, RPT, kb, kb + 1 + (ahead_now ? 1 : 0),
+                                       allow16 ? state : nullptr, st),
+                  "phase 3");
         if (ahead_now)
             BTAS_CUDA(cudaStreamWaitEvent(st, side.b, 0), "event wait");
         else if (next)

@@ -152,6 +152,10 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
 // column kb + 1 only (nothing when kb is the last block).
 cudaError_t launch_fw_cross(int *D, long long n, int kb, cudaStream_t st);
 cudaError_t launch_fw_phase12(int *D, long long n, int kb, int *pmax, cudaStream_t st);
+// int32 phase 3 of pivot block (offset o, width bw) over every tile outside
+// tile rows and columns [x0, x1), in one launch; skipped when *bypass != 0.
+cudaError_t launch_fw_phase3_i32(int *D, long long n, long long o, int bw, const int *RPT, int x0, int x1,
+                                 const int *bypass, cudaStream_t st);
 // Packed phase 3 set-up for pivot block kb: state[0] = 1 if 2 * *pmax <
 // 0x7FFF (state[1] = !state[0]); when set, the column panel goes to Ad
 // (duplicated words, n x ldad) and the row panel to Bu (uint16, bw x ldbu).

@@ -317,19 +317,6 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
     const int col_base = wn * (8 * TN) + tx;  // + 8*j
 
     const T ident = Ident<T, SR>::v();
-    T acc[TM][TN];
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            T v = ident;
-            if (args.accumulate) {
-                const int r = bm + row_base + 4 * i, c = bn + col_base + 8 * j;
-                if (r < M && c < N) v = __ldcg(C + (long long)r * args.ldc + c);
-            }
-            acc[i][j] = v;
-        }
-
     const int KT = (K + BK - 1) / BK;
     const bool va = args.vec_a != 0, vb = args.vec_b != 0;
     auto load_stage = [&](int s, int kt) {
@@ -344,6 +331,22 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
         if (s < KT) load_stage(s, s);
         cp_async_commit();
     }
+
+    // The accumulator (C with accumulate) is read after the first stages'
+    // copies are issued, so the two latencies overlap (short-k accumulate
+    // products, e.g. Floyd-Warshall's phase 3 at k = 128, pay them per tile).
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            T v = ident;
+            if (args.accumulate) {
+                const int r = bm + row_base + 4 * i, c = bn + col_base + 8 * j;
+                if (r < M && c < N) v = __ldcg(C + (long long)r * args.ldc + c);
+            }
+            acc[i][j] = v;
+        }
 
     for (int kt = 0; kt < KT; ++kt) {
         cp_async_wait<ST - 2>();
