@@ -298,7 +298,8 @@ __device__ __forceinline__ void copy_tile(const GemmArgs &args, int bm, int bn, 
 template <class Cfg, int VAR, int SR, int NS>
 __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, unsigned char *smem_raw, int tid,
                                         void *Ct = nullptr, long long ldct = 0, uint32_t *Cd = nullptr,
-                                        long long ldcd = 0, uint16_t *Cu = nullptr, long long ldcu = 0) {
+                                        long long ldcd = 0, uint16_t *Cu = nullptr, long long ldcu = 0,
+                                        bool k_backward = false) {
     using T = typename VarTypes<VAR>::T;
     constexpr int FK = Cfg::FK, TM = Cfg::TM, TN = Cfg::TN;
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, LD = Cfg::kLd, ST = Cfg::STAGES;
@@ -322,6 +323,7 @@ __device__ __forceinline__ bool nt_tile(const GemmArgs &args, int bm, int bn, un
     auto load_stage = [&](int s, int kt) {
         T *sa = smem + s * Cfg::kStageElems;
         T *sb = sa + BM * LD;
+        if (k_backward) kt = KT - 1 - kt;  // (+) is order-free: same result in either k order
         stage_rows<T, BM, BK, LD, NT>(sa, A, args.lda, bm, M, kt * BK, K, va, ident, tid, args.ro_a != 0);
         stage_rows<T, BN, BK, LD, NT>(sb, Bt, args.ldb, bn, N, kt * BK, K, vb, ident, tid, args.ro_b != 0);
     };
@@ -436,14 +438,16 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::MINB) tgemm_nt_kernel(cons
     const int tid = threadIdx.x;
     const int tiles_m = (args.m + Cfg::BM - 1) / Cfg::BM, tiles_n = (args.n + Cfg::BN - 1) / Cfg::BN;
     int tm, tn;
-    raster(blockIdx.x, tiles_m, tiles_n, args.group_m, tm, tn);
+    if (args.kwave > 0) raster(blockIdx.x, tiles_n, tiles_m, args.group_m, tn, tm);
+    else raster(blockIdx.x, tiles_m, tiles_n, args.group_m, tm, tn);
     const int bm = tm * Cfg::BM, bn = tn * Cfg::BN;
     if (args.bypass != nullptr && __ldcg(args.bypass) != 0) return;
     if (args.skip != nullptr && __ldcg(args.skip) == 0) {
         copy_tile<Cfg, T>(args, bm, bn, tid);
         return;
     }
-    const bool ch = nt_tile<Cfg, VAR, SR, NS>(args, bm, bn, smem_raw, tid);
+    const bool back = args.kwave > 0 && ((blockIdx.x / args.kwave) & 1) != 0;
+    const bool ch = nt_tile<Cfg, VAR, SR, NS>(args, bm, bn, smem_raw, tid, nullptr, 0, nullptr, 0, nullptr, 0, back);
     if (args.changed != nullptr) {
         if (__any_sync(0xffffffffu, ch) && (tid & 31) == 0) atomicOr(args.changed, 1);
     }

@@ -25,6 +25,10 @@ struct GemmArgs {
     int group_m;        // CTA rasterisation: tile rows per group
     int *maxfin;        // optional: atomicMax of the largest finite output (as int)
     const int *bypass;  // optional: *bypass != 0 => do nothing (another path computes C)
+    int kwave;          // > 0: rasterise by groups of group_m tile COLUMNS (consecutive
+                        // waves share their B^T panels) and run k backwards in every other
+                        // wave of kwave CTAs, so that a wave starts on the k-slices the
+                        // previous one left in L2 (the launcher scales it by CTAs per SM)
 };
 
 }  // namespace btas

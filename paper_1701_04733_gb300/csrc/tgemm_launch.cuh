@@ -37,7 +37,9 @@ cudaError_t launch_nt(const GemmArgs &a, cudaStream_t st) {
     }
     const long long tiles = (long long)((a.m + Cfg::BM - 1) / Cfg::BM) * ((a.n + Cfg::BN - 1) / Cfg::BN);
     if (tiles <= 0) return cudaSuccess;
-    kern<<<(unsigned)tiles, Cfg::kThreads, Cfg::kSmemBytes, st>>>(a);
+    GemmArgs args = a;
+    args.kwave = a.kwave * Cfg::MINB;  // SMs -> CTAs resident at once
+    kern<<<(unsigned)tiles, Cfg::kThreads, Cfg::kSmemBytes, st>>>(args);
     note_launch();
     return cudaGetLastError();
 }

@@ -20,6 +20,7 @@
 // Inner loop: on NS of the 8 pairs, two 32-bit IMAD adds (FMA pipe) + one
 // 3-input per-halfword min; DPX __viaddmin_u16x2 on the others.
 #include <cstdint>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -55,6 +56,11 @@ struct U16KArgs {
     int *Ci;          // optional: accumulate into int32 Ci = min(Ci, widened result) instead of writing C
     long long ldci;
     int xr0, xr1, xc0, xc1;  // rows / columns of Ci not to write (another stream owns them)
+    // > 0: rasterise by groups of kgroup tile COLUMNS (rows fastest, so consecutive
+    // waves share their B panels) and run k backwards in every other wave of kwave
+    // CTAs: a wave then starts on the k-slices the previous one left in L2
+    int kwave;
+    int kgroup;
 };
 
 __global__ void dup_u16_kernel(const uint16_t *__restrict__ A, long long lda, int m, int k, uint32_t *__restrict__ Ad,
@@ -93,15 +99,28 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
     const int NP = (N + 1) / 2;  // column pairs
     const int tid = threadIdx.x;
     const int tiles_m = (M + BM - 1) / BM, tiles_n = (NP + BNP - 1) / BNP;
-    constexpr int GM = 8;
     const int pid = blockIdx.x;
-    const int per_group = GM * tiles_n;
-    const int g = pid / per_group;
-    const int first_m = g * GM;
-    const int gsz = min(tiles_m - first_m, GM);
-    const int tm = first_m + (pid % per_group) % gsz;
-    const int tn = (pid % per_group) / gsz;
+    int tm, tn;
+    if (args.kwave > 0) {
+        // groups of kgroup tile columns, rows fastest: consecutive waves share B panels
+        const int GN = args.kgroup;
+        const int per_group = GN * tiles_m;
+        const int g = pid / per_group;
+        const int first_n = g * GN;
+        const int gsz = min(tiles_n - first_n, GN);
+        tn = first_n + (pid % per_group) % gsz;
+        tm = (pid % per_group) / gsz;
+    } else {
+        constexpr int GM = 8;
+        const int per_group = GM * tiles_n;
+        const int g = pid / per_group;
+        const int first_m = g * GM;
+        const int gsz = min(tiles_m - first_m, GM);
+        tm = first_m + (pid % per_group) % gsz;
+        tn = (pid % per_group) / gsz;
+    }
     const int bm = tm * BM, bnp = tn * BNP;  // bnp in pairs; column = 2*pair
+    const bool k_back = args.kwave > 0 && ((pid / args.kwave) & 1) != 0;
 
     if (args.gate != nullptr && __ldcg(args.gate) == 0) return;
     if (args.Ci != nullptr) {
@@ -138,7 +157,7 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
     auto load_stage = [&](int s, int kt) {
         uint32_t *sa = smem + s * STAGE;
         uint32_t *sb = sa + A_ELEMS;
-        const int k0 = kt * BK;
+        const int k0 = (k_back ? KT - 1 - kt : kt) * BK;  // min is order-free
         // A: BM rows x BK words, 8 chunks per row
 #pragma unroll
         for (int t = 0; t < (BM * BK / 4) / NT; ++t) {
@@ -419,6 +438,18 @@ cudaError_t launch_tgemm_u16_ws(const U16Args &a, uint32_t *adup, int ns, cudaSt
     ka.xr1 = a.xr1;
     ka.xc0 = a.xc0;
     ka.xc1 = a.xc1;
+    {
+        // Grids of two or more waves: groups of 12 tile columns, k backwards in
+        // every other wave (see U16KArgs::kwave); BTAS_KWAVE=0 turns it off.
+        DeviceInfo di{};
+        const int sms = current_device_info(&di, nullptr) ? di.sms : 152;
+        const long long tiles = (long long)((a.m + u16::BM - 1) / u16::BM) * (((a.n + 1) / 2 + u16::BNP - 1) / u16::BNP);
+        const char *kw = getenv("BTAS_KWAVE");
+        if (tiles >= 2LL * sms && !(kw && atoi(kw) == 0)) {
+            ka.kwave = sms;
+            ka.kgroup = 12;
+        }
+    }
     ka.vec_a = (reinterpret_cast<uintptr_t>(adup) & 15) == 0;
     ka.vec_b = (reinterpret_cast<uintptr_t>(a.B) & 15) == 0 && (a.ldb & 7) == 0;
     switch (ns) {

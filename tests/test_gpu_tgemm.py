@@ -294,3 +294,32 @@ def test_checked_out_of_domain(btas, dt, sr):
     np.testing.assert_array_equal(bits(host(out)), bits(C0))
     assert btas.sync_status() == (0, 0, 0)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("dt", ["i32", "f32", "u16"])
+def test_wave_raster_and_backward_k(btas, oracle_mod, dt):
+    """Grids of two or more waves take the column-group raster with k run
+    backwards in every other wave: same bits as the oracle and as the
+    row-group raster (BTAS_KWAVE=0), at ragged m, n and k (k = 77 and 45 end
+    on a partial slice, which a backward wave loads first)."""
+    if dt == "u16":
+        m, n, k = 4100, 2400, 45
+        A = gen.uniform_int(61, 1, (m, k), 0, 0x7FFF).astype(np.uint16)
+        B = gen.uniform_int(62, 1, (k, n), 0, 0x7FFF).astype(np.uint16)
+        ref = oracle_mod.tgemm_u16(A, B)
+        C = host(btas.gemm(dev(A.view(np.int16)), dev(B.view(np.int16)), 0)).view(np.uint16)
+        with env(BTAS_KWAVE="0"):
+            C0 = host(btas.gemm(dev(A.view(np.int16)), dev(B.view(np.int16)), 0)).view(np.uint16)
+    else:
+        m, n, k = 3200, 3100, 77
+        A, B = _inputs(dt, 0, m, n, k, 63)
+        oracle_mod.set_threads(os.cpu_count() or 1)
+        try:
+            ref = oracle_mod.tgemm(0, A, B)
+        finally:
+            oracle_mod.set_threads(1)
+        C = host(btas.gemm(dev(A), dev(B), 0))
+        with env(BTAS_KWAVE="0"):
+            C0 = host(btas.gemm(dev(A), dev(B), 0))
+    np.testing.assert_array_equal(bits(C), bits(ref))
+    np.testing.assert_array_equal(bits(C0), bits(ref))
