@@ -283,7 +283,7 @@ PROBE_MIXES = ((0, "int32_dpx"), (4, "int32_iadd_min3"), (5, "int32_imad_min3"),
                (8, "ffma_imm_operand"))
 PROBE_DIAG_MIXES = ((9, "fp32_2fadd_imm_min3"), (10, "int32_iadd_imm_min3"),
                     (11, "int32_dpx_imm"), (12, "int32_3pipe_dpx3_imad3_fadd2"), (13, "dpx3_f32x2_5"),
-                    (14, "int32_imad_imm_min3"))
+                    (14, "int32_imad_imm_min3"), (15, "int32_dpx_a_rotated"))
 
 
 def issue_probe(btas, full=False):

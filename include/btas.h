@@ -138,10 +138,12 @@ btas_status btas_measure_issue_rate(int mix, double *terms_per_clock_per_sm);
  *   12 = int32 three-pipe split (DPX on 3 of 8 columns, IMAD + 3-input min
  *        on 3, FADD + 3-input min on 2),
  *   13 = DPX on 3 of 8 columns, add.f32x2 + 3-input min on 5,
- *   14 = int32 two IMAD of an immediate addend + 3-input min.
+ *   14 = int32 two IMAD of an immediate addend + 3-input min,
+ *   15 = mix 0 with a different A register in every consecutive
+ *        instruction (the other mixes keep a row's A across 8 of them).
  * The rate of an SM is taken from its first CTA's start to its last CTA's
  * end; the slowest SM is reported.  Errors: BTAS_ERR_ARG for a mix outside
- * 0..14 or ctas_per_sm outside {1, 2}. */
+ * 0..15 or ctas_per_sm outside {1, 2}. */
 btas_status btas_measure_issue_rate_ex(int mix, int ctas_per_sm, double *terms_per_clock_per_sm);
 
 /* ------------------------------------------------------------------------

@@ -13,7 +13,11 @@
 //   * pipe throughput (ALU, FMA-heavy, FMA-lite lanes per clock);
 //   * register-operand reads per clock (the same instruction with one operand
 //     an immediate, so one register read fewer per instruction);
-//   * warps available to hide latency (1 or 2 CTAs per SM).
+//   * warps available to hide latency (1 or 2 CTAs per SM);
+//   * operand reuse between consecutive instructions: the mixes above keep a
+//     row's A operand in consecutive instructions (the product kernels'
+//     order); mix 15 is DPX with a different A in every consecutive
+//     instruction.
 #include <cstdint>
 #include <vector>
 
@@ -86,6 +90,16 @@ __device__ __forceinline__ void probe_row(float (&acc)[8], uint64_t xi, const ui
     if constexpr (J + 1 < 8) probe_row<MIX, J + 1>(acc, xi, y, one);
 }
 
+// Mix 15: the DPX terms of mix 0 with output (i, j) taking A operand
+// x[(i + j) % 8], so that consecutive instructions (j inner) never share an A
+// register.
+template <int J>
+__device__ __forceinline__ void probe_row_rotated(float (&acc)[8], int i, const uint64_t (&x)[8],
+                                                  const uint64_t (&y)[8], int one) {
+    acc[J] = probe_term<0, J>(acc[J], x[(i + J) & 7], y[J], one);
+    if constexpr (J + 1 < 8) probe_row_rotated<J + 1>(acc, i, x, y, one);
+}
+
 template <int MIX, int MINB>
 __global__ void __launch_bounds__(256, MINB) probe_kernel(const float *in, float *out, int iters, long long *cyc,
                                                         int one) {
@@ -109,7 +123,10 @@ __global__ void __launch_bounds__(256, MINB) probe_kernel(const float *in, float
 #pragma unroll
         for (int j = 0; j < 8; ++j) y[j] = fadd2(y[j], inc);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) probe_row<MIX, 0>(acc[i], x[i], y, one);
+        for (int i = 0; i < 8; ++i) {
+            if constexpr (MIX == 15) probe_row_rotated<0>(acc[i], i, x, y, one);
+            else probe_row<MIX, 0>(acc[i], x[i], y, one);
+        }
     }
     __syncthreads();
     const long long t1 = clock64();
@@ -128,7 +145,7 @@ __global__ void __launch_bounds__(256, MINB) probe_kernel(const float *in, float
     }
 }
 
-constexpr int kMaxMix = 14;
+constexpr int kMaxMix = 15;
 
 // Dynamic shared memory that lets exactly MINB probe CTAs share an SM.
 template <int MINB>
@@ -157,7 +174,7 @@ using namespace btas;
 
 extern "C" btas_status btas_measure_issue_rate_ex(int mix, int ctas_per_sm, double *terms_per_clock_per_sm) {
     if (mix < 0 || mix > kMaxMix || (ctas_per_sm != 1 && ctas_per_sm != 2) || !terms_per_clock_per_sm) {
-        record_error("btas_measure_issue_rate_ex: mix must be 0..14 and ctas_per_sm 1 or 2");
+        record_error("btas_measure_issue_rate_ex: mix must be 0..15 and ctas_per_sm 1 or 2");
         return BTAS_ERR_ARG;
     }
     int dev = 0, sms = 0;

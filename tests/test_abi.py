@@ -60,8 +60,8 @@ def test_host_side_argument_errors(libpath):
     assert "lda" in btas.last_error()
     # max-plus on the 16-bit path is not offered
     assert btas.btas_gemm(1, 2, 4, 4, 4, 1, 4, 1, 4, 1, 4, None) == 7
-    # the issue-rate probe: mixes 0..14 at 1 or 2 CTAs per SM
-    assert btas.btas_measure_issue_rate_ex(15, 1, None) == 1
+    # the issue-rate probe: mixes 0..15 at 1 or 2 CTAs per SM
+    assert btas.btas_measure_issue_rate_ex(16, 1, None) == 1
     assert btas.btas_measure_issue_rate_ex(0, 3, None) == 1
     assert btas.btas_measure_issue_rate(8, None) == 1  # the diagnostic mixes need the _ex form
     # the batched launch's tile tuner takes 1 <= n_max <= 2048

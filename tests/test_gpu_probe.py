@@ -19,7 +19,7 @@ def btas():
 
 @pytest.mark.parametrize("ctas", [1, 2])
 def test_every_mix_reports_a_physical_rate(btas, ctas):
-    for mix in range(15):
+    for mix in range(16):
         r = btas.measure_issue_rate(mix, ctas)
         limit = 256.0 if mix == 2 else 128.0 * 2
         assert 1.0 < r <= limit, (mix, ctas, r)
