@@ -483,6 +483,17 @@ def run_btas(args):
         roof_i32["measured_issue_ceiling_tops"] = round(ceil, 3)
         roof_i32["measured_issue_ceiling_basis"] = "best int32 instruction mix of the probe"
         roof_i32["frac_of_measured_ceiling"] = round(n3 / t_i32min / 1e12 / ceil, 4)
+    # fp32: the same lane-clock peak, and the survey's two-instruction count
+    # (FADD + FMNMX per term: half the lane-clock peak in terms); the kernel
+    # itself issues one instruction per term (add.f32x2 + 3-input min per
+    # two terms)
+    roof_f32 = roof("tgemm_nt fp32 min-plus 8192^3", n3, t_f32min)
+    roof_f32["traffic"] = traffic.get("tgemm_nt fp32 min-plus 8192^3")
+    roof_f32["frac_two_instruction_basis"] = round(2 * n3 / t_f32min / 1e12 / peak_tops, 4)
+    if isinstance(probe.get("fp32_f32x2_min3"), float):
+        ceil_f = probe["fp32_f32x2_min3"] * sms * max_mhz * 1e6 / 1e12
+        roof_f32["measured_issue_ceiling_tops"] = round(ceil_f, 3)
+        roof_f32["frac_of_measured_ceiling"] = round(n3 / t_f32min / 1e12 / ceil_f, 4)
     if isinstance(probe.get("ffma_reference"), float) and isinstance(probe.get("ffma_imm_operand"), float):
         # the same FFMA stream with one register operand replaced by an
         # immediate: the speed-up shows the register-operand read limit
@@ -505,6 +516,7 @@ def run_btas(args):
                        "apsp": round(computed * n3 / t_apsp / 1e9, 1)},
         "roofline": roofline,
         "roofline_int32_minplus": roof_i32,
+        "roofline_fp32_minplus": roof_f32,
         "issue_probe_terms_per_clk_per_sm": probe,
         "clocks": clocks,
         "gpu_launches": launches,
