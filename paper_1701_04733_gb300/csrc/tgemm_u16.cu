@@ -380,6 +380,176 @@ __global__ void __launch_bounds__(u16::NT, 1) tgemm_u16_kernel(const U16KArgs ar
     }
 }
 
+
+// Floyd-Warshall's packed phase 3 (Ci accumulate at k = 128) at 2 CTAs per
+// SM: 128 x 128 tiles (64 column pairs), 8 rows x 4 pairs per thread, DPX
+// add-min on every term.  With k / BK = 4 slices per tile, the prologue and
+// the accumulate epilogue of one CTA overlap the other CTA's products, which
+// the 1-CTA/SM kernel above cannot do.
+namespace u16c2 {
+constexpr int BM = 128, BNP = 64, BK = 32, ST = 3, NT = 256, RI = 8, PQ = 4;
+constexpr int LDA = BK + 4, LDB = BNP;
+constexpr int STAGE = BM * LDA + BK * LDB;
+constexpr int SMEM = ST * STAGE * 4;  // 79872 bytes
+}  // namespace u16c2
+
+__global__ void __launch_bounds__(u16c2::NT, 2) tgemm_u16_ci2_kernel(const U16KArgs args) {
+    using namespace u16c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *smem = reinterpret_cast<uint32_t *>(smem_raw);
+    const int M = args.m, N = args.n, K = args.k;
+    const int NP = (N + 1) / 2;
+    const int tid = threadIdx.x;
+    const int tiles_m = (M + BM - 1) / BM, tiles_n = (NP + BNP - 1) / BNP;
+    const int pid = blockIdx.x;
+    constexpr int GM = 8;
+    const int per_group = GM * tiles_n;
+    const int g = pid / per_group;
+    const int first_m = g * GM;
+    const int gsz = min(tiles_m - first_m, GM);
+    const int bm = (first_m + (pid % per_group) % gsz) * BM;
+    const int bnp = ((pid % per_group) / gsz) * BNP;  // first column pair
+    if (args.gate != nullptr && __ldcg(args.gate) == 0) return;
+    // this tile of Ci into L2 while its products run (the epilogue reads it)
+    for (int l = tid; l < BM * 4; l += NT) {  // 4 lines of 32 words per tile row
+        const int r = bm + (l >> 2), c = 2 * bnp + (l & 3) * 32;
+        if (r < M && c < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(args.Ci + (long long)r * args.ldci + c));
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int ty = lane >> 3, tx = lane & 7;
+    const int row_base = wm * (4 * RI) + ty;        // + 4*i
+    const int pair_base = wn * (8 * PQ) + tx * PQ;  // + q
+    uint32_t acc[RI][PQ];
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int j = 0; j < PQ; ++j) acc[i][j] = kInfU16x2;
+    const int KT = (K + BK - 1) / BK;
+    auto load = [&](int s, int kt) {
+        uint32_t *sa = smem + s * STAGE;
+        uint32_t *sb = sa + BM * LDA;
+        const int k0 = kt * BK;
+#pragma unroll
+        for (int t = 0; t < (BM * BK / 4) / NT; ++t) {
+            const int c = tid + t * NT;
+            const int r = c >> 3, kc = (c & 7) * 4;
+            const int gr = bm + r, gk = k0 + kc;
+            uint32_t *dst = sa + r * LDA + kc;
+            if (args.vec_a && gr < M && gk + 4 <= K) {
+                cp_async16(dst, args.Ad + (long long)gr * args.ldad + gk);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    dst[e] = (gr < M && gk + e < K) ? args.Ad[(long long)gr * args.ldad + gk + e] : kInfU16x2;
+            }
+        }
+        constexpr int CPR = BNP / 4;  // chunks of 4 words per B row
+#pragma unroll
+        for (int t = 0; t < (BK * BNP / 4) / NT; ++t) {
+            const int c = tid + t * NT;
+            const int r = c / CPR, wc = (c % CPR) * 4;
+            const int gk = k0 + r, gcol = 2 * (bnp + wc);
+            uint32_t *dst = sb + r * LDB + wc;
+            if (args.vec_b && gk < K && gcol + 8 <= N) {
+                cp_async16(dst, args.B + (long long)gk * args.ldb + gcol);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c0 = gcol + 2 * e;
+                    uint32_t lo = BTAS_INF_U16, hi = BTAS_INF_U16;
+                    if (gk < K) {
+                        if (c0 < N) lo = args.B[(long long)gk * args.ldb + c0];
+                        if (c0 + 1 < N) hi = args.B[(long long)gk * args.ldb + c0 + 1];
+                    }
+                    dst[e] = lo | (hi << 16);
+                }
+            }
+        }
+    };
+#pragma unroll
+    for (int s = 0; s < ST - 1; ++s) {
+        if (s < KT) load(s, s);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < KT; ++kt) {
+        cp_async_wait<ST - 2>();
+        __syncthreads();
+        if (kt + ST - 1 < KT) load((kt + ST - 1) % ST, kt + ST - 1);
+        cp_async_commit();
+        const uint32_t *sa = smem + (kt % ST) * STAGE;
+        const uint32_t *sb = sa + BM * LDA;
+#pragma unroll 2
+        for (int kk = 0; kk < BK; kk += 4) {
+            uint4 av[RI];
+#pragma unroll
+            for (int i = 0; i < RI; ++i) av[i] = *reinterpret_cast<const uint4 *>(sa + (row_base + 4 * i) * LDA + kk);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 t = *reinterpret_cast<const uint4 *>(sb + (kk + q) * LDB + pair_base);
+                const uint32_t b[PQ] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int i = 0; i < RI; ++i) {
+                    const uint32_t ai = q == 0 ? av[i].x : q == 1 ? av[i].y : q == 2 ? av[i].z : av[i].w;
+#pragma unroll
+                    for (int j = 0; j < PQ; ++j) acc[i][j] = u16x2_addmin(ai, b[j], acc[i][j]);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+    // Ci = min(Ci, result), INF16 read as INF; rows [xr0, xr1) and columns
+    // [xc0, xc1) left alone.  This thread's 8 columns are consecutive: rows
+    // are read and written as 16-byte vectors, four rows' loads in flight
+    // before any store.
+    const int c0 = 2 * (bnp + pair_base);
+    const bool vec = ((reinterpret_cast<uintptr_t>(args.Ci) & 15) == 0) && ((args.ldci & 3) == 0);
+#pragma unroll
+    for (int i0 = 0; i0 < RI; i0 += 4) {
+        int4 old[4][2];
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+            const int r = bm + row_base + 4 * (i0 + ii);
+            const int *pc = args.Ci + (long long)r * args.ldci + c0;
+            if (vec && r < M && c0 + 8 <= N) {
+                old[ii][0] = *reinterpret_cast<const int4 *>(pc);
+                old[ii][1] = *reinterpret_cast<const int4 *>(pc + 4);
+            } else {
+                int t[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) t[e] = (r < M && c0 + e < N) ? pc[e] : kInfI32;
+                old[ii][0] = make_int4(t[0], t[1], t[2], t[3]);
+                old[ii][1] = make_int4(t[4], t[5], t[6], t[7]);
+            }
+        }
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+            const int i = i0 + ii;
+            const int r = bm + row_base + 4 * i;
+            if (r >= M || (r >= args.xr0 && r < args.xr1)) continue;
+            int v[8] = {old[ii][0].x, old[ii][0].y, old[ii][0].z, old[ii][0].w,
+                        old[ii][1].x, old[ii][1].y, old[ii][1].z, old[ii][1].w};
+#pragma unroll
+            for (int q = 0; q < PQ; ++q) {
+                const uint32_t w = acc[i][q];
+                const uint32_t lo = w & 0xFFFFu, hi = w >> 16;
+                if (lo < BTAS_INF_U16) v[2 * q] = min(v[2 * q], (int)lo);
+                if (hi < BTAS_INF_U16) v[2 * q + 1] = min(v[2 * q + 1], (int)hi);
+            }
+            int *pc = args.Ci + (long long)r * args.ldci + c0;
+            const bool clear = c0 + 8 <= args.xc0 || c0 >= args.xc1;  // none of the 8 excluded
+            if (vec && c0 + 8 <= N && clear) {
+                *reinterpret_cast<int4 *>(pc) = make_int4(v[0], v[1], v[2], v[3]);
+                *reinterpret_cast<int4 *>(pc + 4) = make_int4(v[4], v[5], v[6], v[7]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (c0 + e < N && (c0 + e < args.xc0 || c0 + e >= args.xc1)) pc[e] = v[e];
+            }
+        }
+    }
+}
+
 static int grid_for(long long total) {
     long long b = (total + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
@@ -402,6 +572,17 @@ cudaError_t launch_widen_u16_i32(const uint16_t *src, long long total, int *dst,
 
 template <int NS>
 static cudaError_t launch_ns(const U16KArgs &ka, cudaStream_t st) {
+    const char *one = getenv("BTAS_U16_CI_1CTA");
+    if (ka.Ci != nullptr && ka.skip == nullptr && ka.prev == nullptr && ka.maxfin == nullptr && ka.changed == nullptr &&
+        !(one && *one == '1')) {
+        cudaError_t e = set_smem_once(reinterpret_cast<const void *>(tgemm_u16_ci2_kernel), u16c2::SMEM);
+        if (e != cudaSuccess) return e;
+        const long long tiles =
+            (long long)((ka.m + u16c2::BM - 1) / u16c2::BM) * (((ka.n + 1) / 2 + u16c2::BNP - 1) / u16c2::BNP);
+        tgemm_u16_ci2_kernel<<<(unsigned)tiles, u16c2::NT, u16c2::SMEM, st>>>(ka);
+        note_launch();
+        return cudaGetLastError();
+    }
     auto kern = tgemm_u16_kernel<NS>;
     cudaError_t e = set_smem_once(reinterpret_cast<const void *>(kern), u16::SMEM);
     if (e != cudaSuccess) return e;

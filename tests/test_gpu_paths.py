@@ -200,3 +200,35 @@ def test_argmin_large(btas, oracle_mod, dtype):
             steps += 1
             assert steps <= n
         assert tot == int(D[i, j])
+
+
+@pytest.mark.parametrize("dtype", ["i32", "f32"])
+def test_above_the_key_range_n8200(btas, oracle_mod, dtype):
+    """n = 8200, above the keyed squaring's n <= 8192: every squaring runs on
+    the argmin kernel by default.  Sampled distance rows equal the oracle's
+    Dijkstra rows and sampled next-hop walks are shortest paths."""
+    n = 8200
+    Wi = gen.random_graph(710, n, n, 0.002, 1, 9)
+    W = Wi if dtype == "i32" else np.where(Wi == INF, np.float32(np.inf), Wi.astype(np.float32)).astype(np.float32)
+    D, Nx = btas.apsp_paths(dev(W))
+    D, Nx = host(D), host(Nx)
+    srcs = [0, 4099, n - 1]
+    rows = oracle_mod.dijkstra_rows(Wi, srcs)
+    Dr = D[srcs]
+    if dtype == "f32":
+        Dr = np.where(np.isinf(Dr), INF, Dr).astype(np.int32)
+    np.testing.assert_array_equal(Dr, rows)
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        i, j = (int(x) for x in rng.integers(0, n, 2))
+        if (np.isinf(D[i, j]) if dtype == "f32" else D[i, j] == INF):
+            assert Nx[i, j] == -1
+            continue
+        v, tot, steps = i, 0, 0
+        while v != j:
+            u = int(Nx[v, j])
+            tot += int(Wi[v, u])
+            v = u
+            steps += 1
+            assert steps <= n
+        assert tot == int(D[i, j])

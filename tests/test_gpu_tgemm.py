@@ -321,5 +321,15 @@ def test_wave_raster_and_backward_k(btas, oracle_mod, dt):
         C = host(btas.gemm(dev(A), dev(B), 0))
         with env(BTAS_KWAVE="0"):
             C0 = host(btas.gemm(dev(A), dev(B), 0))
+        # accumulate into a prior C, B supplied transposed: the same raster
+        Cp = (int_matrix(64, (m, n), 0) if dt == "i32" else f32_matrix(64, (m, n), 0))
+        oracle_mod.set_threads(os.cpu_count() or 1)
+        try:
+            ref_acc = oracle_mod.tgemm(0, A, B, Cp)
+        finally:
+            oracle_mod.set_threads(1)
+        acc = dev(Cp)
+        btas.gemm(dev(A), dev(np.ascontiguousarray(B.T)), 0, out=acc, accumulate=True, trans_b=True)
+        np.testing.assert_array_equal(bits(host(acc)), bits(ref_acc))
     np.testing.assert_array_equal(bits(C), bits(ref))
     np.testing.assert_array_equal(bits(C0), bits(ref))
