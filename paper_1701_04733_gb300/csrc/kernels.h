@@ -138,7 +138,8 @@ cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool ea
 // domain, [1] largest finite weight, [2] squarings that changed D, [3]
 // status, [4] representations used (1 int32, 4 packed 16-bit).  packed_ok =
 // false keeps every squaring on int32 (so does BTAS_MID_NO_U16=1 in the
-// environment).
+// environment).  From n = 1408 (BTAS_MID_WIDE_MIN_N) the launch takes the
+// warp-specialised form with 128 x 128 tiles.
 int apsp_mid_max_n();
 size_t apsp_mid_workspace(long long n, int S);
 int *apsp_mid_info(void *ws, long long n);

@@ -320,6 +320,342 @@ __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) 
     }
 }
 
+
+// ---- Wide warp-specialised form for the larger mid sizes: 128 x 128
+// tiles, one block per SM, two producer warps that stage each unit (128 x 32
+// of A transposed to k-major, 32 x 128 of B; the packed forms converted)
+// into a kWStages-deep shared ring, and eight consumer warps with 8 x 8
+// outputs per thread (a third of the shared-memory loads per term of the
+// 64 x 64 form).  Full/empty mbarriers order the ring.  Every mbarrier wait
+// is bounded: on expiry the waiting thread records BTAS_ERR_TIMEOUT and
+// leaves the squaring, and the grid barrier that follows returns false in
+// every block.
+constexpr int kWConsumers = 256, kWProducers = 64, kWThreads = kWConsumers + kWProducers;
+constexpr int kWT = 128;        // tile edge
+constexpr int kWLdA = kWT + 4;  // k-major A row (words)
+constexpr int kWStages = 4;
+
+struct WwStage {
+    int a[kKc][kWLdA];  // A[k][row]; packed: duplicated 16-bit words
+    int b[kKc][kWT];    // B[k][col]; packed: column pairs in the first kWT / 2 words
+};
+struct WwSmem {
+    WwStage st[kWStages];
+    unsigned long long full[kWStages], empty[kWStages];
+};
+constexpr int kWwSmem = (int)sizeof(WwSmem);
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(b)) : "memory");
+    (void)state;
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of the phase with this parity; false (and
+// the status word set) on expiry or once another block has given up.
+__device__ __forceinline__ bool mbar_wait(const MidArgs &a, unsigned long long *b, unsigned parity) {
+    if (mbar_test(b, parity)) return true;
+    const long long t0 = clock64();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_test(b, parity)) return true;
+        if ((it & 255) == 0 && gsync::ld_relaxed_i32(a.info + 3) != 0) return false;
+        if (clock64() - t0 > a.timeout_cycles) {
+            atomicCAS(a.info + 3, 0, BTAS_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Producers: every unit of the share [u0, u1) into ring slot q % kWStages, q =
+// qbase + (u - u0).  Returns false on a timeout.
+template <bool U16>
+__device__ __forceinline__ bool ww_produce(const MidArgs &a, const int *in, int tiles, int KS, long long u0,
+                                           long long u1, long long qbase, WwSmem &sm, int ptid) {
+    const int n = a.n;
+    const long long ldx = a.ldx;
+    const int lane = ptid & 31;
+    const int4 inf4 = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+    for (long long u = u0; u < u1; ++u) {
+        const long long q = qbase + (u - u0);
+        const int slot = (int)(q % kWStages);
+        const long long round = q / kWStages;
+        if (round > 0 && !mbar_wait(a, &sm.empty[slot], (unsigned)((round - 1) & 1))) return false;
+        const int tile = (int)(u / KS), ks = (int)(u % KS);
+        const int bm = (tile / tiles) * kWT, bn = (tile % tiles) * kWT;
+        const int kb = ks * kKc, k1 = min(n, kb + kKc);
+        WwStage &st = sm.st[slot];
+        // A: 128 rows x 8 k-groups of 4 (1024 vectors, 16 per thread, all in
+        // flight before any store); element e: k-group (e & 1) + 2 * ((e >> 5)
+        // & 3), row ((e >> 1) & 15) + 16 * (e >> 7), so that a warp's
+        // transposing stores hit 32 distinct banks.  A vector that starts
+        // inside the matrix ends inside the padded row (ldx is a multiple of
+        // 4) and reads INF padding past column n - 1.
+        {
+            int4 v[16];
+#pragma unroll
+            for (int q4 = 0; q4 < 16; ++q4) {
+                const int e = ptid + q4 * kWProducers;
+                const int kg = (e & 1) + 2 * ((e >> 5) & 3), r = ((e >> 1) & 15) + 16 * (e >> 7);
+                const int gi = bm + r, gk = kb + 4 * kg;
+                v[q4] = (gi < n && gk < k1) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)gi * ldx + gk))
+                                            : inf4;
+            }
+#pragma unroll
+            for (int q4 = 0; q4 < 16; ++q4) {
+                const int e = ptid + q4 * kWProducers;
+                const int kg = (e & 1) + 2 * ((e >> 5) & 3), r = ((e >> 1) & 15) + 16 * (e >> 7);
+                int *col = &st.a[4 * kg][r];
+                if (U16) {
+                    col[0] = (int)(u16_of(v[q4].x) * 0x10001u);
+                    col[kWLdA] = (int)(u16_of(v[q4].y) * 0x10001u);
+                    col[2 * kWLdA] = (int)(u16_of(v[q4].z) * 0x10001u);
+                    col[3 * kWLdA] = (int)(u16_of(v[q4].w) * 0x10001u);
+                } else {
+                    col[0] = v[q4].x;
+                    col[kWLdA] = v[q4].y;
+                    col[2 * kWLdA] = v[q4].z;
+                    col[3 * kWLdA] = v[q4].w;
+                }
+            }
+        }
+        // B: 32 k-rows x 32 column groups of 4 (1024 vectors), rows contiguous
+        {
+            int4 v[16];
+#pragma unroll
+            for (int q4 = 0; q4 < 16; ++q4) {
+                const int e = ptid + q4 * kWProducers;
+                const int rk = e >> 5, cb = (e & 31) * 4;
+                const int gkb = kb + rk, gj = bn + cb;
+                v[q4] = (gkb < k1 && gj < n) ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)gkb * ldx + gj))
+                                             : inf4;
+            }
+#pragma unroll
+            for (int q4 = 0; q4 < 16; ++q4) {
+                const int e = ptid + q4 * kWProducers;
+                const int rk = e >> 5, cb = (e & 31) * 4;
+                if (U16) {
+                    const uint2 w = make_uint2(u16_of(v[q4].x) | (u16_of(v[q4].y) << 16),
+                                               u16_of(v[q4].z) | (u16_of(v[q4].w) << 16));
+                    *reinterpret_cast<uint2 *>(&st.b[rk][cb / 2]) = w;
+                } else {
+                    *reinterpret_cast<int4 *>(&st.b[rk][cb]) = v[q4];
+                }
+            }
+        }
+        __threadfence_block();
+        __syncwarp();  // every lane's stores, ordered before the warp's arrival
+        if (lane == 0) mbar_arrive(&sm.full[slot]);
+    }
+    return true;
+}
+
+// Consumers: the pieces of the share (a tile and its consecutive units),
+// computed from the ring and merged as in run_item.  Thread (ty, tx) =
+// (tid / 16, tid % 16) owns rows bm + 8 ty .. + 7 and columns bn + 8 tx .. + 7
+// (packed: pairs 4 tx .. 4 tx + 3).  Returns false on a timeout.
+template <bool U16>
+__device__ __forceinline__ bool ww_consume(const MidArgs &a, const int *in, int *out, int tiles, int KS, long long u0,
+                                           long long u1, long long qbase, WwSmem &sm, int tid, bool &ch, int &mx) {
+    const int n = a.n;
+    const long long ldx = a.ldx;
+    const int ty = tid >> 4, tx = tid & 15, lane = tid & 31;
+    long long u = u0;
+    while (u < u1) {
+        const int tile = (int)(u / KS), ks = (int)(u % KS);
+        const long long pe = min(u1, (long long)(tile + 1) * KS);
+        const int k0 = ks * kKc, k1 = min(n, (int)(pe - (long long)tile * KS) * kKc);
+        const int bm = (tile / tiles) * kWT, bn = (tile % tiles) * kWT;
+        const int r0 = bm + ty * 8, c0 = bn + tx * 8;
+        int acc[8][8];         // int32 mode
+        unsigned acc16[8][4];  // packed mode: columns (c0 + 2p, c0 + 2p + 1)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            if (U16) {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc16[r][p] = kInfU16x2;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = kInfI32;
+            }
+        }
+        for (long long v = u; v < pe; ++v) {
+            const long long q = qbase + (v - u0);
+            const int slot = (int)(q % kWStages);
+            if (!mbar_wait(a, &sm.full[slot], (unsigned)((q / kWStages) & 1))) return false;
+            const WwStage &st = sm.st[slot];
+#pragma unroll 4
+            for (int k = 0; k < kKc; ++k) {
+                const int4 a0 = *reinterpret_cast<const int4 *>(&st.a[k][ty * 8]);
+                const int4 a1 = *reinterpret_cast<const int4 *>(&st.a[k][ty * 8 + 4]);
+                const int ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                if (U16) {
+                    const uint4 bv = *reinterpret_cast<const uint4 *>(&st.b[k][tx * 4]);
+                    const unsigned br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) acc16[r][p] = u16x2_addmin((unsigned)ar[r], br[p], acc16[r][p]);
+                } else {
+                    const int4 b0 = *reinterpret_cast<const int4 *>(&st.b[k][tx * 8]);
+                    const int4 b1 = *reinterpret_cast<const int4 *>(&st.b[k][tx * 8 + 4]);
+                    const int br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) acc[r][c] = __viaddmin_s32(ar[r], br[c], acc[r][c]);
+                }
+            }
+            __syncwarp();  // the warp is done reading the slot
+            if (lane == 0) mbar_arrive(&sm.empty[slot]);
+        }
+        // merge, with X_{s-1} read row by row now: p < old, or p == old from
+        // the piece holding k = j
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = r0 + r;
+            int o[8];
+            if (i < n && c0 < n) {
+                // a vector that starts inside the row ends inside the padded row
+                const int4 inf4 = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+                const int4 x0 = __ldcg(reinterpret_cast<const int4 *>(in + (long long)i * ldx + c0));
+                const int4 x1 =
+                    c0 + 4 < n ? __ldcg(reinterpret_cast<const int4 *>(in + (long long)i * ldx + c0 + 4)) : inf4;
+                o[0] = x0.x; o[1] = x0.y; o[2] = x0.z; o[3] = x0.w;
+                o[4] = x1.x; o[5] = x1.y; o[6] = x1.z; o[7] = x1.w;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) o[c] = kInfI32;
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = c0 + c;
+                int p;
+                if (U16) {
+                    const unsigned hh = (acc16[r][c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
+                    p = hh >= (unsigned)BTAS_INF_U16 ? kInfI32 : (int)hh;
+                } else {
+                    p = clamp_i32<kMin>(acc[r][c]);
+                }
+                if (i < n && j < n && p < kInfI32 && (p < o[c] || (p == o[c] && j >= k0 && j < k1))) {
+                    atomicMin(out + (long long)i * ldx + j, p);
+                    mx = max(mx, p);
+                    ch |= p < o[c];
+                }
+            }
+        }
+        u = pe;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kWThreads, 1) apsp_mid_wide_kernel(const MidArgs a) {
+    extern __shared__ __align__(16) unsigned char ww_raw[];
+    WwSmem &sm = *reinterpret_cast<WwSmem *>(ww_raw);
+    const int n = a.n, tid = threadIdx.x;
+    const bool producer = tid >= kWConsumers;
+    const long long ldx = a.ldx;
+    const long long nx = (long long)n * ldx;
+    const long long gthreads = (long long)gridDim.x * kWThreads;
+    const long long gtid = (long long)blockIdx.x * kWThreads + tid;
+    unsigned gen = 0;
+    if (tid == 0) {
+        for (int s = 0; s < kWStages; ++s) {
+            mbar_init(&sm.full[s], kWProducers / 32);
+            mbar_init(&sm.empty[s], kWConsumers / 32);
+        }
+    }
+    __syncthreads();
+    // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF
+    bool bad_block = false;
+    {
+        int bad = 0, mx = 0;
+        for (long long idx = gtid; idx < nx; idx += gthreads) {
+            const int i = (int)(idx / ldx), j = (int)(idx % ldx);
+            int v = kInfI32;
+            if (j < n) {
+                v = a.W[(long long)i * a.ldw + j];
+                const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
+                if ((!fin && v != kInfI32) || (i == j && v != 0)) ++bad;
+                if (fin) mx = max(mx, v);
+            }
+            a.buf2[idx] = v;
+            a.buf0[idx] = kInfI32;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bad += __shfl_xor_sync(0xffffffffu, bad, o);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if ((tid & 31) == 0) {
+            if (bad) atomicAdd(a.info + 0, bad);
+            atomicMax(a.info + 1, mx);
+        }
+        bad_block = bad != 0;
+    }
+    int nbad = 0, bound = 0;
+    if (a.withhold && blockIdx.x == gridDim.x - 1) return;
+    if (!grid_barrier(a, gen, bad_block, a.info + 1, nbad, bound)) return;
+    if (nbad != 0) return;  // D untouched
+
+    const int tiles = (n + kWT - 1) / kWT, KS = (n + kKc - 1) / kKc;
+    const long long U = (long long)tiles * tiles * KS;
+    const long long u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
+    const int4 inf4 = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+    const int *in = a.buf2;
+    int cur = 0, done = 0, path = 0;
+    long long qbase = 0;  // units through this block's ring so far
+    for (int s = 1; s <= a.S; ++s) {
+        int *out = bufp(a, cur);
+        if (s < a.S) {
+            int4 *nxt = reinterpret_cast<int4 *>(bufp(a, (cur + 1) % 3));
+            for (long long idx = gtid; idx < nx / 4; idx += gthreads) nxt[idx] = inf4;
+        }
+        const bool u16 = a.u16_ok && bound <= kU16Max;
+        path |= u16 ? 4 : 1;
+        bool ch = false;
+        int mx = 0;
+        if (producer) {
+            if (u16) ww_produce<true>(a, in, tiles, KS, u0, u1, qbase, sm, tid - kWConsumers);
+            else ww_produce<false>(a, in, tiles, KS, u0, u1, qbase, sm, tid - kWConsumers);
+        } else {
+            if (u16) ww_consume<true>(a, in, out, tiles, KS, u0, u1, qbase, sm, tid, ch, mx);
+            else ww_consume<false>(a, in, out, tiles, KS, u0, u1, qbase, sm, tid, ch, mx);
+        }
+        qbase += u1 - u0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0 && mx > 0) atomicMax(reinterpret_cast<int *>(a.bar + 64 + s), mx);
+        int changed = 0;
+        if (!grid_barrier(a, gen, ch, reinterpret_cast<const int *>(a.bar + 64 + s), changed, bound)) return;
+        done += changed != 0;
+        in = out;
+        cur = (cur + 1) % 3;
+        if (!changed && a.early) break;
+    }
+    // result: X_last -> D (W was read only in phase 0, so D may be W)
+    for (long long idx = gtid; idx < (long long)n * n; idx += gthreads)
+        a.D[(idx / n) * a.ldd + idx % n] = __ldcg(in + (idx / n) * ldx + idx % n);
+    if (blockIdx.x == 0 && tid == 0) {
+        a.info[2] = done;
+        a.info[4] = path;
+    }
+}
 }  // namespace
 
 int apsp_mid_max_n() {
@@ -367,11 +703,26 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
         }
     }
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    // the wide form from n = 1408 up: measured on GB300 (p = 0.05, w in [1,
+    // 100]) it ties the 64 x 64 form at n = 1280 (591 vs 592 us) and is 10 %
+    // faster at 1536 (862 vs 955 us) and 1792 (1290 vs 1462 us); at 1024 it is
+    // slower (396 vs 341 us).  BTAS_MID_WIDE_MIN_N overrides the boundary.
+    const char *wmin = getenv("BTAS_MID_WIDE_MIN_N");
+    const bool wide = n >= (wmin && *wmin ? atoi(wmin) : 1408);
+    int per_sm_w = 0;
+    if (wide) {
+        cudaError_t e = set_smem_once(reinterpret_cast<const void *>(apsp_mid_wide_kernel), kWwSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_w, apsp_mid_wide_kernel, kWThreads, kWwSmem);
+        if (e != cudaSuccess) return e;
+        if (per_sm_w < 1) return cudaErrorCooperativeLaunchTooLarge;
+    }
     if (S > 63) return cudaErrorInvalidValue;  // per-squaring maxima at bar[64 + s]
     const int sms = di.sms, clk_khz = di.clock_khz;
-    const long long tiles = (n + kT - 1) / kT, KS = (n + kKc - 1) / kKc;
+    const int tile = wide ? kWT : kT;
+    const long long tiles = (n + tile - 1) / tile, KS = (n + kKc - 1) / kKc;
     const long long units = tiles * tiles * KS;
-    const int grid = (int)std::max(1LL, std::min(units, (long long)per_sm * sms));
+    const int grid = (int)std::max(1LL, std::min(units, (long long)(wide ? per_sm_w : per_sm) * sms));
     const long long ldx = (n + 3) & ~3LL;
     const size_t mat = ((size_t)n * ldx * 4 + 255) & ~size_t(255);
     char *base = static_cast<char *>(ws);
@@ -399,8 +750,12 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     cudaError_t e = cudaMemsetAsync(base + 3 * mat, 0, info_out_dev ? 512 : 768, st);
     if (e != cudaSuccess) return e;
     void *args[] = {&a};
-    e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(apsp_mid_kernel), dim3(grid), dim3(kThreads), args, 0,
-                                    st);
+    if (wide)
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(apsp_mid_wide_kernel), dim3(grid), dim3(kWThreads),
+                                        args, kWwSmem, st);
+    else
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(apsp_mid_kernel), dim3(grid), dim3(kThreads), args,
+                                        0, st);
     note_launch();
     return e;
 }

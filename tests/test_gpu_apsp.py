@@ -305,20 +305,45 @@ def test_cooperative_path_above_1024(btas, oracle_mod):
     assert info["squarings"] == info2["squarings"]
 
 
-def test_cooperative_barrier_timeout_is_reported(btas, oracle_mod):
+@pytest.mark.parametrize("wide", ["0", "1"])
+def test_cooperative_barrier_timeout_is_reported(btas, oracle_mod, wide):
     """Failure detection without a fault: with BTAS_MID_WITHHOLD=1 one block of
-    the cooperative kernel never arrives at its first grid barrier, the
-    others' bounded waits expire (about 2 s), and the call returns
-    BTAS_ERR_TIMEOUT with D untouched; the next call on the same context
-    succeeds."""
+    the cooperative kernel (64 x 64 form, or the warp-specialised 128 x 128
+    form) never arrives at its first grid barrier, the others' bounded waits
+    expire (about 2 s), and the call returns BTAS_ERR_TIMEOUT with D
+    untouched; the next call on the same context succeeds."""
     import torch
     n = 300
     W = gen.random_graph(gen.BASE_SEED, 960, n, 0.05, 1, 100)
     out = dev(np.full((n, n), 41, np.int32))
-    with env(BTAS_MID_WITHHOLD="1"):
-        with pytest.raises(btas.BtasError) as ei:
-            btas.apsp(dev(W), out=out)
-    assert ei.value.status == 5
-    assert (host(out) == 41).all()
-    torch.cuda.synchronize()
-    np.testing.assert_array_equal(host(btas.apsp(dev(W))), oracle_mod.floyd_warshall(W))
+    with env(BTAS_MID_WIDE_MIN_N="0" if wide == "1" else "100000"):
+        with env(BTAS_MID_WITHHOLD="1"):
+            with pytest.raises(btas.BtasError) as ei:
+                btas.apsp(dev(W), out=out)
+        assert ei.value.status == 5
+        assert (host(out) == 41).all()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host(btas.apsp(dev(W))), oracle_mod.floyd_warshall(W))
+
+
+@pytest.mark.parametrize("n", [3, 7, 129, 200, 333, 513, 1100])
+def test_wide_cooperative_form(btas, oracle_mod, n, cooperative_from_3):
+    """The warp-specialised 128 x 128 form of the cooperative kernel (producer
+    warps staging through an mbarrier ring, consumer warps with 8 x 8
+    outputs), forced at every size with BTAS_MID_WIDE_MIN_N=0: ragged edges of
+    the 128-wide tiles, packed and int32 squarings, early exit or not, in
+    place.  Same distances and squarings count as the oracle and the tiled
+    path."""
+    with env(BTAS_MID_WIDE_MIN_N="0"):
+        for p, whi in ((0.05, 100), (3.0 / n, 10 ** 6), (0.02, 12000)):
+            W = gen.random_graph(gen.BASE_SEED, 980 + n, n, p, 1, whi)
+            ref = oracle_mod.floyd_warshall(W)
+            for early in (0, 1):
+                D, info = btas.apsp(dev(W), flags=early, info=True)
+                with env(BTAS_APSP_NO_MID="1"):
+                    _, info2 = btas.apsp(dev(W), flags=early | btas.APSP_FORCE_I32, info=True)
+                np.testing.assert_array_equal(host(D), ref)
+                assert info["squarings"] == info2["squarings"]
+            t = dev(W)
+            btas.apsp(t, out=t)
+            np.testing.assert_array_equal(host(t), ref)
