@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--probe-ctas", type=int, default=1, help="with --probe-mix: CTAs per SM (1 or 2)")
     p.add_argument("--paths-dtype", choices=["i32", "f32"], default="i32",
                    help="with --only paths: int32 or binary32 weights")
+    p.add_argument("--mid-whi", type=int, default=100,
+                   help="with --only mid: largest edge weight (10^6 keeps the squarings on int32)")
     p.add_argument("--fw-int32", action="store_true",
                    help="with --only fw: keep phase 3 on the int32 kernel (no packed phase 3)")
     p.add_argument("--serve-requests", type=int, default=2000)
@@ -1190,10 +1192,10 @@ def run_only(args):
     elif args.only == "configs":
         print(json.dumps({"only": "configs", **config_timings(args, btas, torch)}))
     elif args.only == "mid":
-        # one mid-size solve (p = 0.05, w in [1, 100]) at --n, five calls
+        # one mid-size solve (p = 0.05, w in [1, 100], or [1, --mid-whi]) at --n, five calls
         import gen
         n = args.n
-        W = torch.from_numpy(gen.random_graph(gen.BASE_SEED, 300 + n, n, 0.05, 1, 100)).cuda()
+        W = torch.from_numpy(gen.random_graph(gen.BASE_SEED, 300 + n, n, 0.05, 1, args.mid_whi)).cuda()
         D = torch.empty_like(W)
         ts = []
         for _ in range(5):

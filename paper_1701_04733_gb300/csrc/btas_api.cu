@@ -803,7 +803,9 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
 
     // mid-size graphs: every squaring in one cooperative launch (one
     // read-back); BTAS_APSP_NO_MID=1 disables it
-    if (S >= 1 && n > apsp_small_limit() && n <= apsp_mid_max_n() &&
+    DeviceInfo dinfo{};
+    const int dev_sms = current_device_info(&dinfo) ? dinfo.sms : 0;
+    if (S >= 1 && n > apsp_small_limit() && apsp_mid_takes(n, dev_sms) &&
         !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) && env_int("BTAS_APSP_NO_MID", 0) == 0) {
         const int r = apsp_mid_solve(n, W, D, S, early, !(flags & BTAS_APSP_FORCE_I32), squarings_done, bound_out,
                                      path_out, st);

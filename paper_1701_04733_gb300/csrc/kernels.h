@@ -141,6 +141,14 @@ cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool ea
 // environment).  From n = 1408 (BTAS_MID_WIDE_MIN_N) the launch takes the
 // warp-specialised form with 128 x 128 tiles.
 int apsp_mid_max_n();
+// Whether btas_apsp solves n on the cooperative kernel: every n <=
+// apsp_mid_max_n(), and for n <= 3584 (unless BTAS_APSP_MID_MAX_N is set)
+// the sizes where the tiled packed squaring's last wave of 128 x 256 tiles
+// on `sms` SMs would leave the grid less than three-quarters full (measured
+// on GB300: n = 2304: 2.50 vs 3.40 ms, 2560: 3.33 vs 3.77 ms, 3328: 7.00 vs
+// 7.12 ms; and with int32 squarings 4.62 vs 6.03, 6.25 vs 6.68, 13.38 vs
+// 13.90 ms; the tiled path wins at 2048, 2816, 3072 and 3584).
+bool apsp_mid_takes(long long n, int sms);
 size_t apsp_mid_workspace(long long n, int S);
 int *apsp_mid_info(void *ws, long long n);
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,

@@ -670,6 +670,16 @@ int apsp_mid_max_n() {
     return v < 0 ? 0 : v > 4096 ? 4096 : v;
 }
 
+bool apsp_mid_takes(long long n, int sms) {
+    if (n <= apsp_mid_max_n()) return true;
+    const char *e = getenv("BTAS_APSP_MID_MAX_N");
+    if ((e && *e) || n > 3584 || sms < 1) return false;  // an explicit limit wins
+    // the tiled packed squaring: 128 x 256 tiles, one CTA per SM
+    const long long tiles = ((n + 127) / 128) * (((n + 1) / 2 + 127) / 128);
+    const long long waves = (tiles + sms - 1) / sms;
+    return 4 * tiles < 3 * waves * sms;
+}
+
 // workspace: three n x ldx matrices, then 512 bytes of barrier words and
 // 256 bytes for the status words of a caller that passes info = null
 size_t apsp_mid_workspace(long long n, int S) {

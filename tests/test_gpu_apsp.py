@@ -347,3 +347,23 @@ def test_wide_cooperative_form(btas, oracle_mod, n, cooperative_from_3):
             t = dev(W)
             btas.apsp(t, out=t)
             np.testing.assert_array_equal(host(t), ref)
+
+
+@pytest.mark.parametrize("n", [2304, 2560])
+def test_cooperative_where_tiles_quantise(btas, oracle_mod, n):
+    """Above n = 1792 btas_apsp takes the cooperative kernel where the tiled
+    packed squaring would leave its last wave less than three-quarters full
+    (2304 and 2560 on 152 SMs): distances equal Floyd-Warshall's and the
+    squarings count equals the tiled path's."""
+    W = gen.random_graph(gen.BASE_SEED, 990 + n, n, 0.02, 1, 100)
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    try:
+        ref = oracle_mod.floyd_warshall(W)
+    finally:
+        oracle_mod.set_threads(1)
+    D, info = btas.apsp(dev(W), info=True)
+    with env(BTAS_APSP_NO_MID="1"):
+        D2, info2 = btas.apsp(dev(W), info=True)
+    np.testing.assert_array_equal(host(D), ref)
+    np.testing.assert_array_equal(host(D2), ref)
+    assert info["squarings"] == info2["squarings"]
