@@ -296,12 +296,17 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  *                   wait; BTAS_ERR_TIMEOUT if it expires) per squaring; each
  *                   squaring packed 16-bit while every finite entry of its
  *                   operand is <= 16383 (a bound the previous squaring
- *                   reports), else int32 (always int32 with FORCE_I32);
+ *                   reports), else int32 (always int32 with FORCE_I32); from
+ *                   n = 1408 with 128 x 128 tiles and warp-specialised
+ *                   staging; the same up to n = 3584 where the tiled
+ *                   squaring's last wave of tiles would leave the GPU less
+ *                   than three-quarters full;
  *   larger n        the tiled product kernels, one launch per squaring, with
  *                   the per-squaring exact representation described below.
  * BTAS_APSP_SMALL_MAX_N=m (0 .. 128) and BTAS_APSP_MID_MAX_N=m (0 .. 4096) in
- * the environment move the two boundaries; BTAS_APSP_NO_SMALL=1 /
- * BTAS_APSP_NO_MID=1 send the first two regimes to the tiled path.
+ * the environment move the two boundaries (the latter as a plain size
+ * limit); BTAS_APSP_NO_SMALL=1 / BTAS_APSP_NO_MID=1 send the first two
+ * regimes to the tiled path.
  * ------------------------------------------------------------------------ */
 btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
