@@ -239,6 +239,52 @@ __device__ __forceinline__ void squaring(const MidArgs &a, const int *in, int *o
     }
 }
 
+// Phase 0 of both forms of the kernel: the domain check, W -> X_0 (buf2) and
+// X_1's buffer (buf0) to INF; the entries outside the domain and the largest
+// finite weight go to info[0] and info[1].  Returns whether this block found
+// an entry outside the domain.
+__device__ __forceinline__ bool mid_phase0(const MidArgs &a, long long gtid, long long gthreads) {
+    const int n = a.n;
+    const long long ldx = a.ldx, nx = (long long)n * ldx;
+    int bad = 0, mx = 0;
+    for (long long idx = gtid; idx < nx; idx += gthreads) {
+        const int i = (int)(idx / ldx), j = (int)(idx % ldx);
+        int v = kInfI32;
+        if (j < n) {
+            v = a.W[(long long)i * a.ldw + j];
+            const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
+            if ((!fin && v != kInfI32) || (i == j && v != 0)) ++bad;
+            if (fin) mx = max(mx, v);
+        }
+        a.buf2[idx] = v;
+        a.buf0[idx] = kInfI32;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(a.info + 0, bad);
+        atomicMax(a.info + 1, mx);
+    }
+    return __syncthreads_or(bad != 0) != 0;
+}
+
+// The result X_last -> D (W was read only in phase 0, so D may be W), and the
+// squarings that changed D and the representations used to info[2], info[4].
+__device__ __forceinline__ void mid_finish(const MidArgs &a, const int *in, long long gtid, long long gthreads,
+                                           int done, int path) {
+    const int n = a.n;
+    const long long ldx = a.ldx;
+    for (long long idx = gtid; idx < (long long)n * n; idx += gthreads)
+        a.D[(idx / n) * a.ldd + idx % n] = __ldcg(in + (idx / n) * ldx + idx % n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.info[2] = done;
+        a.info[4] = path;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) {
     __shared__ __align__(16) MidSmem sm;
     const int n = a.n, tid = threadIdx.x;
@@ -249,32 +295,7 @@ __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) 
     unsigned gen = 0;
 
     // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF
-    bool bad_block = false;
-    {
-        int bad = 0, mx = 0;
-        for (long long idx = gtid; idx < nx; idx += gthreads) {
-            const int i = (int)(idx / ldx), j = (int)(idx % ldx);
-            int v = kInfI32;
-            if (j < n) {
-                v = a.W[(long long)i * a.ldw + j];
-                const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
-                if ((!fin && v != kInfI32) || (i == j && v != 0)) ++bad;
-                if (fin) mx = max(mx, v);
-            }
-            a.buf2[idx] = v;
-            a.buf0[idx] = kInfI32;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            bad += __shfl_xor_sync(0xffffffffu, bad, o);
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        if ((tid & 31) == 0) {
-            if (bad) atomicAdd(a.info + 0, bad);
-            atomicMax(a.info + 1, mx);
-        }
-        bad_block = bad != 0;
-    }
+    const bool bad_block = mid_phase0(a, gtid, gthreads);
     int nbad = 0, bound = 0;  // bound: >= every finite entry of X_{s-1}
     if (a.withhold && blockIdx.x == gridDim.x - 1) return;
     if (!grid_barrier(a, gen, bad_block, a.info + 1, nbad, bound)) return;
@@ -311,13 +332,7 @@ __global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) 
         cur = (cur + 1) % 3;
         if (!changed && a.early) break;
     }
-    // result: X_last -> D (W was read only in phase 0, so D may be W)
-    for (long long idx = gtid; idx < (long long)n * n; idx += gthreads)
-        a.D[(idx / n) * a.ldd + idx % n] = __ldcg(in + (idx / n) * ldx + idx % n);
-    if (blockIdx.x == 0 && tid == 0) {
-        a.info[2] = done;
-        a.info[4] = path;
-    }
+    mid_finish(a, in, gtid, gthreads, done, path);
 }
 
 
@@ -352,9 +367,9 @@ __device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
-    unsigned long long state;
+    unsigned long long state;  // the arrival's phase token, not needed here
     asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(b)) : "memory");
-    (void)state;
+    asm volatile("" ::"l"(state));
 }
 __device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity) {
     unsigned ok;
@@ -582,32 +597,7 @@ __global__ void __launch_bounds__(kWThreads, 1) apsp_mid_wide_kernel(const MidAr
     }
     __syncthreads();
     // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF
-    bool bad_block = false;
-    {
-        int bad = 0, mx = 0;
-        for (long long idx = gtid; idx < nx; idx += gthreads) {
-            const int i = (int)(idx / ldx), j = (int)(idx % ldx);
-            int v = kInfI32;
-            if (j < n) {
-                v = a.W[(long long)i * a.ldw + j];
-                const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
-                if ((!fin && v != kInfI32) || (i == j && v != 0)) ++bad;
-                if (fin) mx = max(mx, v);
-            }
-            a.buf2[idx] = v;
-            a.buf0[idx] = kInfI32;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            bad += __shfl_xor_sync(0xffffffffu, bad, o);
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        if ((tid & 31) == 0) {
-            if (bad) atomicAdd(a.info + 0, bad);
-            atomicMax(a.info + 1, mx);
-        }
-        bad_block = bad != 0;
-    }
+    const bool bad_block = mid_phase0(a, gtid, gthreads);
     int nbad = 0, bound = 0;
     if (a.withhold && blockIdx.x == gridDim.x - 1) return;
     if (!grid_barrier(a, gen, bad_block, a.info + 1, nbad, bound)) return;
@@ -648,13 +638,7 @@ __global__ void __launch_bounds__(kWThreads, 1) apsp_mid_wide_kernel(const MidAr
         cur = (cur + 1) % 3;
         if (!changed && a.early) break;
     }
-    // result: X_last -> D (W was read only in phase 0, so D may be W)
-    for (long long idx = gtid; idx < (long long)n * n; idx += gthreads)
-        a.D[(idx / n) * a.ldd + idx % n] = __ldcg(in + (idx / n) * ldx + idx % n);
-    if (blockIdx.x == 0 && tid == 0) {
-        a.info[2] = done;
-        a.info[4] = path;
-    }
+    mid_finish(a, in, gtid, gthreads, done, path);
 }
 }  // namespace
 
