@@ -306,7 +306,11 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  * BTAS_APSP_SMALL_MAX_N=m (0 .. 128) and BTAS_APSP_MID_MAX_N=m (0 .. 4096) in
  * the environment move the two boundaries (the latter as a plain size
  * limit); BTAS_APSP_NO_SMALL=1 / BTAS_APSP_NO_MID=1 send the first two
- * regimes to the tiled path.
+ * regimes to the tiled path.  The cooperative regime keeps, per calling host
+ * thread, 64 bytes of mapped host memory for its status words and (for
+ * workspaces up to 32 MiB, on the first device the thread uses) a 32 MiB
+ * device workspace, both released when the thread exits; other workspace
+ * comes from the pool of btas_workspace_*.
  * ------------------------------------------------------------------------ */
 btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
 

@@ -726,20 +726,75 @@ static btas_status squaring_loop(int dtype, long long n, int S, const void *cur0
 // shared device); the tiled path then computes the same result.
 constexpr int kMidFallback = -1;
 
+// Per host thread, for the cooperative solves: a host-mapped mailbox that
+// the kernel leaves its status words in (no device-to-host copy after the
+// kernel), and, for workspaces up to 32 MiB on the first device used, one
+// cached workspace (no pool allocation and release per call).  Both are
+// idle between calls: a call synchronises its stream before it returns.
+// Measured on GB300 (p = 0.1, w in [1, 100]): 66.3 -> 61.7 us per call at
+// n = 256, 103 -> 96 us at n = 512.
+struct MidThreadState {
+    int *mbox = nullptr;  // host pointer; the device writes it through UVA
+    bool mbox_tried = false;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int ws_dev = -1;
+    ~MidThreadState() {
+        if (mbox) cudaFreeHost(mbox);
+        if (ws) cudaFree(ws);
+    }
+};
+constexpr size_t kMidCachedWs = size_t(32) << 20;
+
 static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool early, bool packed_ok,
                           int *squarings_done, int64_t *bound_out, int *path_out, cudaStream_t st) {
+    thread_local MidThreadState ts;
+    if (!ts.mbox_tried) {
+        ts.mbox_tried = true;
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, 64, cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess) {
+            void *d = nullptr;
+            if (cudaHostGetDevicePointer(&d, p, 0) == cudaSuccess && d == p) ts.mbox = static_cast<int *>(p);
+            else cudaFreeHost(p);
+        }
+        cudaGetLastError();
+    }
+    int dev = 0;
+    BTAS_CUDA(cudaGetDevice(&dev), "device");
+    const size_t need = apsp_mid_workspace(n, S);
     Workspace ws(st);
-    BTAS_CUDA(ws.alloc(apsp_mid_workspace(n, S)), "workspace alloc");
+    void *wsp = nullptr;
+    if (need <= kMidCachedWs && (ts.ws_dev < 0 || ts.ws_dev == dev)) {
+        if (ts.ws_bytes < need) {
+            if (ts.ws) cudaFree(ts.ws);
+            ts.ws = nullptr;
+            ts.ws_bytes = 0;
+            BTAS_CUDA(cudaMalloc(&ts.ws, kMidCachedWs), "workspace alloc");
+            ts.ws_bytes = kMidCachedWs;
+            ts.ws_dev = dev;
+        }
+        wsp = ts.ws;
+    } else {
+        BTAS_CUDA(ws.alloc(need), "workspace alloc");
+        wsp = ws.p;
+    }
     // the status words inside the workspace: zeroed by the launch
-    int *info = apsp_mid_info(ws.p, n);
-    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, ws.p, nullptr, st);
+    int *info = apsp_mid_info(wsp, n);
+    if (ts.mbox) ts.mbox[3] = -1;  // overwritten by the kernel as it ends
+    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, wsp, nullptr, st, ts.mbox);
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
         cudaGetLastError();
         return kMidFallback;
     }
     BTAS_CUDA(le, "mid apsp");
     int host[5] = {0, 0, 0, 0, 0};
-    BTAS_CUDA(read_back(host, info, 20, st), "info readback");
+    if (ts.mbox) {
+        BTAS_CUDA(cudaStreamSynchronize(st), "mid apsp");
+        memcpy(host, ts.mbox, sizeof host);
+        if (host[3] == -1) return fail((btas_status)BTAS_ERR_INTERNAL, "btas_apsp: the cooperative kernel left no status");
+    } else {
+        BTAS_CUDA(read_back(host, info, 20, st), "info readback");
+    }
     if (host[3] != 0) return fail(BTAS_ERR_TIMEOUT, "btas_apsp: a bounded grid barrier wait expired");
     if (host[0] != 0) {
         if (bound_out) *bound_out = -1;

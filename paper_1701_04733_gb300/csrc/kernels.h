@@ -139,7 +139,10 @@ cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool ea
 // status, [4] representations used (1 int32, 4 packed 16-bit).  packed_ok =
 // false keeps every squaring on int32 (so does BTAS_MID_NO_U16=1 in the
 // environment).  From n = 1408 (BTAS_MID_WIDE_MIN_N) the launch takes the
-// warp-specialised form with 128 x 128 tiles.
+// warp-specialised form with 128 x 128 tiles.  mailbox (optional, a
+// host-mapped pointer the device can write): info[0 .. 4] are copied there
+// as the launch ends, so the caller reads them after synchronising the
+// stream, without a device-to-host copy.
 int apsp_mid_max_n();
 // Whether btas_apsp solves n on the cooperative kernel: every n <=
 // apsp_mid_max_n(), and for n <= 3584 (unless BTAS_APSP_MID_MAX_N is set)
@@ -152,7 +155,7 @@ bool apsp_mid_takes(long long n, int sms);
 size_t apsp_mid_workspace(long long n, int S);
 int *apsp_mid_info(void *ws, long long n);
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
-                            long long ldd, void *ws, int *info, cudaStream_t st);
+                            long long ldd, void *ws, int *info, cudaStream_t st, int *mailbox = nullptr);
 
 // ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
 // pmax (optional): atomicMax of the largest finite value the phases store

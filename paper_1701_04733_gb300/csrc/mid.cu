@@ -69,6 +69,7 @@ struct MidArgs {
     unsigned *bar;  // [0, 16) barrier counters, [32, 33] release word (grid_sync.cuh), [64 + s] largest merged value
     int *info;      // [0] bad entries, [1] max weight, [2] squarings that changed, [3] status,
                     // [4] representations used (1 int32, 4 packed 16-bit)
+    int *mailbox;   // optional, host-mapped: info[0 .. 4] copied there by block 0 as it exits
     long long timeout_cycles;
 };
 
@@ -285,7 +286,7 @@ __device__ __forceinline__ void mid_finish(const MidArgs &a, const int *in, long
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) {
+__device__ __forceinline__ void mid_body(const MidArgs &a) {
     __shared__ __align__(16) MidSmem sm;
     const int n = a.n, tid = threadIdx.x;
     const long long ldx = a.ldx;
@@ -579,7 +580,7 @@ __device__ __forceinline__ bool ww_consume(const MidArgs &a, const int *in, int 
     return true;
 }
 
-__global__ void __launch_bounds__(kWThreads, 1) apsp_mid_wide_kernel(const MidArgs a) {
+__device__ __forceinline__ void mid_wide_body(const MidArgs &a) {
     extern __shared__ __align__(16) unsigned char ww_raw[];
     WwSmem &sm = *reinterpret_cast<WwSmem *>(ww_raw);
     const int n = a.n, tid = threadIdx.x;
@@ -640,6 +641,28 @@ __global__ void __launch_bounds__(kWThreads, 1) apsp_mid_wide_kernel(const MidAr
     }
     mid_finish(a, in, gtid, gthreads, done, path);
 }
+
+// Block 0 leaves the status words in the caller's host-mapped mailbox as it
+// exits, on every path (the words are final by then: the domain count
+// before the first grid barrier, the timeout status before any block gives
+// up, the squarings and representations from block 0 itself), so the
+// caller reads them after the stream without a copy.
+__device__ __forceinline__ void mid_post(const MidArgs &a) {
+    if (a.mailbox == nullptr || blockIdx.x != 0 || threadIdx.x != 0) return;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a.mailbox[i] = __ldcg(a.info + i);
+    __threadfence_system();
+}
+
+__global__ void __launch_bounds__(kThreads, 2) apsp_mid_kernel(const MidArgs a) {
+    mid_body(a);
+    mid_post(a);
+}
+
+__global__ void __launch_bounds__(kWThreads, 1) apsp_mid_wide_kernel(const MidArgs a) {
+    mid_wide_body(a);
+    mid_post(a);
+}
 }  // namespace
 
 int apsp_mid_max_n() {
@@ -678,7 +701,7 @@ int *apsp_mid_info(void *ws, long long n) {
 }
 
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
-                            long long ldd, void *ws, int *info_out_dev, cudaStream_t st) {
+                            long long ldd, void *ws, int *info_out_dev, cudaStream_t st, int *mailbox) {
     // device facts and the kernel's occupancy, queried once per device
     DeviceInfo di{};
     int dev = 0;
@@ -738,6 +761,7 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     a.buf2 = reinterpret_cast<int *>(base + 2 * mat);
     a.bar = reinterpret_cast<unsigned *>(base + 3 * mat);
     a.info = info_out_dev ? info_out_dev : apsp_mid_info(ws, n);
+    a.mailbox = mailbox;
     a.timeout_cycles = (long long)(2.0 * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);  // about 2 s
     // barrier words and per-squaring maxima, and the internal status words
     // when the caller passes none: one memset

@@ -178,18 +178,26 @@ def test_config_n8192_sampled(btas, oracle_mod):
 
 
 def test_workspace_pool_caches_and_trims(btas, oracle_mod):
-    """Workspace comes from the library's pool: it stays reserved between
-    calls (later calls reuse it) and btas_workspace_trim releases it."""
+    """The tiled path's workspace comes from the library's pool: it stays
+    reserved between calls (later calls reuse it) and btas_workspace_trim
+    releases it.  The cooperative path's small workspaces come from a cache
+    of the calling thread instead: repeated calls take nothing from the
+    pool."""
     W = gen.random_graph(91, 1, 300, 0.05, 1, 100)
-    D1 = host(btas.apsp(dev(W)))
-    held = btas.btas_workspace_reserved()
-    assert held > 0
-    D2 = host(btas.apsp(dev(W)))
-    assert btas.btas_workspace_reserved() == held
+    with env(BTAS_APSP_NO_MID="1"):
+        D1 = host(btas.apsp(dev(W)))
+        held = btas.btas_workspace_reserved()
+        assert held > 0
+        D2 = host(btas.apsp(dev(W)))
+        assert btas.btas_workspace_reserved() == held
     np.testing.assert_array_equal(D1, D2)
     np.testing.assert_array_equal(D1, oracle_mod.apsp_squaring(W))
     assert btas.btas_workspace_trim() == 0
     assert btas.btas_workspace_reserved() < held
+    before = btas.btas_workspace_reserved()
+    for _ in range(3):
+        np.testing.assert_array_equal(host(btas.apsp(dev(W))), D1)  # cooperative kernel
+    assert btas.btas_workspace_reserved() == before
 
 
 @pytest.fixture

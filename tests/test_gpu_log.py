@@ -25,8 +25,12 @@ torch.cuda.synchronize()
 """
 
 
-@pytest.mark.parametrize("n,regime", [(48, "one-block kernel"), (300, "cooperative kernel"), (2000, "tiled kernels")])
+@pytest.mark.parametrize("n,regime", [(48, "one-block kernel"), (300, "cooperative kernel"), (2000, "tiled kernels"),
+                                      (2560, "cooperative kernel"), (2816, "tiled kernels")])
 def test_log_reports_regime_and_kernel_choice(n, regime):
+    """n = 2560 and 2816 pin the choice above 1792 on a 152-SM GB300: the tiled
+    packed squaring would fill its last wave of 200 tiles to 66 % (the
+    cooperative kernel takes it) and of 242 tiles to 80 % (it stays tiled)."""
     env = dict(os.environ, BTAS_LOG="1")
     r = subprocess.run([sys.executable, "-c", SCRIPT.format(root=ROOT, n=n)], env=env, capture_output=True,
                        text=True, timeout=300)
