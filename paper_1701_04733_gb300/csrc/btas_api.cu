@@ -726,10 +726,11 @@ static btas_status squaring_loop(int dtype, long long n, int S, const void *cur0
 // shared device); the tiled path then computes the same result.
 constexpr int kMidFallback = -1;
 
-// Per host thread, for the cooperative solves: a host-mapped mailbox that
-// the kernel leaves its status words in (no device-to-host copy after the
-// kernel), and, for workspaces up to 32 MiB on the first device used, one
-// cached workspace (no pool allocation and release per call).  Both are
+// Per host thread, for the one-block and cooperative solves: a host-mapped
+// mailbox that the kernel leaves its status words in (no device-to-host copy
+// after the kernel), and, for cooperative workspaces up to 32 MiB on the
+// first device used, one cached workspace (no pool allocation and release
+// per call).  Both are
 // idle between calls: a call synchronises its stream before it returns.
 // Measured on GB300 (p = 0.1, w in [1, 100]): 66.3 -> 61.7 us per call at
 // n = 256, 103 -> 96 us at n = 512.
@@ -746,8 +747,7 @@ struct MidThreadState {
 };
 constexpr size_t kMidCachedWs = size_t(32) << 20;
 
-static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool early, bool packed_ok,
-                          int *squarings_done, int64_t *bound_out, int *path_out, cudaStream_t st) {
+static MidThreadState &thread_state() {
     thread_local MidThreadState ts;
     if (!ts.mbox_tried) {
         ts.mbox_tried = true;
@@ -759,6 +759,12 @@ static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool e
         }
         cudaGetLastError();
     }
+    return ts;
+}
+
+static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool early, bool packed_ok,
+                          int *squarings_done, int64_t *bound_out, int *path_out, cudaStream_t st) {
+    MidThreadState &ts = thread_state();
     int dev = 0;
     BTAS_CUDA(cudaGetDevice(&dev), "device");
     const size_t need = apsp_mid_workspace(n, S);
@@ -791,7 +797,8 @@ static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool e
     if (ts.mbox) {
         BTAS_CUDA(cudaStreamSynchronize(st), "mid apsp");
         memcpy(host, ts.mbox, sizeof host);
-        if (host[3] == -1) return fail((btas_status)BTAS_ERR_INTERNAL, "btas_apsp: the cooperative kernel left no status");
+        if (host[3] == -1)
+            return fail((btas_status)BTAS_ERR_INTERNAL, "btas_apsp: the cooperative kernel left no status");
     } else {
         BTAS_CUDA(read_back(host, info, 20, st), "info readback");
     }
@@ -836,12 +843,27 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
     // read-back) on the int32 arithmetic; BTAS_APSP_NO_SMALL=1 disables it
     if (S >= 1 && n <= apsp_small_limit() && !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) &&
         env_int("BTAS_APSP_NO_SMALL", 0) == 0) {
+        // the status words straight into the thread's host-mapped mailbox
+        // (the kernel writes them once, from one thread, as it ends), else
+        // into workspace read back
+        MidThreadState &ts = thread_state();
         Workspace ws(st);
-        BTAS_CUDA(ws.alloc(256), "workspace alloc");
-        int *info = static_cast<int *>(ws.p);
+        int *info = ts.mbox;
+        if (!info) {
+            BTAS_CUDA(ws.alloc(256), "workspace alloc");
+            info = static_cast<int *>(ws.p);
+        }
         int host[3] = {0, 0, 0};
+        if (ts.mbox) ts.mbox[2] = -1;  // overwritten by the kernel as it ends
         BTAS_CUDA(launch_apsp_small(W, n, (int)n, S, early, D, n, info, st), "small apsp");
-        BTAS_CUDA(read_back(host, info, 12, st), "info readback");
+        if (ts.mbox) {
+            BTAS_CUDA(cudaStreamSynchronize(st), "small apsp");
+            memcpy(host, ts.mbox, sizeof host);
+            if (host[2] == -1)
+                return fail((btas_status)BTAS_ERR_INTERNAL, "btas_apsp: the one-block kernel left no status");
+        } else {
+            BTAS_CUDA(read_back(host, info, 12, st), "info readback");
+        }
         if (host[0] != 0) {
             if (bound_out) *bound_out = -1;
             return fail(BTAS_ERR_ARG,
