@@ -300,7 +300,15 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  *                   n = 1408 with 128 x 128 tiles and warp-specialised
  *                   staging; the same up to n = 3584 where the tiled
  *                   squaring's last wave of tiles would leave the GPU less
- *                   than three-quarters full;
+ *                   than three-quarters full.  This launch also builds the
+ *                   edge lists of W: when every row has at most
+ *                   min(256, max(32, n / 4)) edges (rounded to 32) the first
+ *                   squaring runs as sparse products over them, and after a
+ *                   squaring that lowered few entries a closure certificate
+ *                   (X (x) W >= X, checked at the lowered entries) can stop
+ *                   the solve without the squaring that would only confirm
+ *                   the fixpoint (early exit only); D and the squarings count
+ *                   are the same;
  *   larger n        the tiled product kernels, one launch per squaring, with
  *                   the per-squaring exact representation described below.
  * BTAS_APSP_SMALL_MAX_N=m (0 .. 128) and BTAS_APSP_MID_MAX_N=m (0 .. 4096) in
@@ -342,7 +350,8 @@ btas_status btas_apsp(int64_t n, const int32_t *W, int32_t *D, void *stream);
  *                    returns BTAS_ERR_ARG after synchronising).
  *  path            : HOST pointer or NULL; receives the set of
  *                    representations used, as bits: 1 = int32, 2 = FP32
- *                    carrier, 4 = packed 16-bit.
+ *                    carrier, 4 = packed 16-bit, 8 = the first squaring as
+ *                    sparse products over edge lists (cooperative regime).
  * The domain scan (zero diagonal, weights in [0, 2^28] or INF) runs on the
  * device and synchronises `stream` once, except in the FORCE_I32 mode above.
  */
@@ -468,7 +477,8 @@ int btas_apsp_squarings(int64_t n);
  * domain.
  * ------------------------------------------------------------------------ */
 #define BTAS_NOALLOC_MAX_N 1024
-#define BTAS_NOALLOC_SCRATCH_BYTES (256 + 3 * 4 * BTAS_NOALLOC_MAX_N * BTAS_NOALLOC_MAX_N + 1024)
+#define BTAS_NOALLOC_SCRATCH_BYTES \
+    (256 + 3 * 4 * BTAS_NOALLOC_MAX_N * BTAS_NOALLOC_MAX_N + 2048 + 4 * BTAS_NOALLOC_MAX_N + 8 * 256 * BTAS_NOALLOC_MAX_N)
 btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D, void *stream);
 
 /* Outcome of the most recent btas_apsp_noalloc call on the current device,

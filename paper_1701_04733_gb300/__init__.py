@@ -522,7 +522,7 @@ def apsp(W, out=None, flags=APSP_EARLY_EXIT, stream=None, info=False):
     if info:
         check(btas_apsp_ex(n, W.data_ptr(), out.data_ptr(), flags, ctypes.addressof(sq), ctypes.addressof(bd),
                            ctypes.addressof(pt), _stream(stream)))
-        names = [nm for bit, nm in ((1, "int32"), (2, "fp32-carrier"), (4, "u16x2")) if pt.value & bit]
+        names = [nm for bit, nm in ((1, "int32"), (2, "fp32-carrier"), (4, "u16x2"), (8, "sparse")) if pt.value & bit]
         return out, {"squarings": sq.value, "bound": bd.value, "path": "+".join(names)}
     if flags == APSP_EARLY_EXIT:
         check(btas_apsp(n, W.data_ptr(), out.data_ptr(), _stream(stream)))

@@ -787,7 +787,7 @@ static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool e
     // the status words inside the workspace: zeroed by the launch
     int *info = apsp_mid_info(wsp, n);
     if (ts.mbox) ts.mbox[3] = -1;  // overwritten by the kernel as it ends
-    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, wsp, nullptr, st, ts.mbox);
+    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, wsp, need, nullptr, st, ts.mbox);
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
         cudaGetLastError();
         return kMidFallback;

@@ -6,10 +6,10 @@
 // (g - 1) % 8: each block adds 1, plus 2^32 if its flag is set, so the last
 // block to arrive learns the grid's flag from the value its add returns.  It
 // resets the slot barrier g + 4 will use (every block is past barrier g - 4,
-// its previous user, and none can reach g + 4 before this release), reads
-// the word *pval, and publishes barrier number, flag and value in one 64-bit
-// release word; the other blocks poll that word, so one load gives them the
-// release and both results.  Every wait is bounded: on expiry the block sets
+// its previous user, and none can reach g + 4 before this release), computes
+// a value (by default it reads one word), and publishes barrier number, flag
+// and value in one 64-bit release word; the other blocks poll that word, so
+// one load gives them the release and both results.  Every wait is bounded: on expiry the block sets
 // *status to BTAS_ERR_TIMEOUT and the barrier returns false, as it does once
 // any block has set the status.  No trap, no fault.
 #pragma once
@@ -46,10 +46,12 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
 }  // namespace gsync
 
 // flag: this block's contribution (ORed over the grid, returned in v0);
-// pval: optional word in [0, 2^30) read after all arrivals (v1).  Returns
-// false if the status word is set: the caller returns.
-__device__ __forceinline__ bool grid_barrier(const GridSync &g, unsigned &gen, bool flag, const int *pval, int &v0,
-                                             int &v1) {
+// value(): called by the last block to arrive, once every block's writes
+// before the barrier are visible; its low 30 bits are published (v1).
+// Returns false if the status word is set: the caller returns.
+template <class ValueFn>
+__device__ __forceinline__ bool grid_barrier_fn(const GridSync &g, unsigned &gen, bool flag, ValueFn value, int &v0,
+                                                int &v1) {
     __shared__ int s_ok, s_v0, s_v1;
     const int any = __syncthreads_or(flag ? 1 : 0);
     ++gen;
@@ -63,7 +65,7 @@ __device__ __forceinline__ bool grid_barrier(const GridSync &g, unsigned &gen, b
             __threadfence();
             atomicExch(ring + ((gen + 3) & 7), 0ull);
             const unsigned f = ((prev >> 32) != 0 || any != 0) ? 1u : 0u;
-            const unsigned v = pval ? (unsigned)gsync::ld_relaxed_i32(pval) & 0x3FFFFFFFu : 0u;
+            const unsigned v = (unsigned)value() & 0x3FFFFFFFu;
             word = (unsigned long long)gen | ((unsigned long long)f << 32) | ((unsigned long long)v << 33);
             __threadfence();
             gsync::st_release_u64(pub, word);
@@ -89,6 +91,13 @@ __device__ __forceinline__ bool grid_barrier(const GridSync &g, unsigned &gen, b
     v0 = s_v0;
     v1 = s_v1;
     return s_ok != 0;
+}
+
+// pval: optional word in [0, 2^30) read after all arrivals (v1).
+__device__ __forceinline__ bool grid_barrier(const GridSync &g, unsigned &gen, bool flag, const int *pval, int &v0,
+                                             int &v1) {
+    return grid_barrier_fn(
+        g, gen, flag, [pval]() -> unsigned { return pval ? (unsigned)gsync::ld_relaxed_i32(pval) : 0u; }, v0, v1);
 }
 
 }  // namespace btas

@@ -132,11 +132,16 @@ cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool ea
                               int *info, cudaStream_t st);
 
 // ---- APSP in one cooperative launch for apsp_small_limit() < n <=
-// apsp_mid_max_n() (mid.cu).  ws: apsp_mid_workspace(n, S) bytes; info
+// apsp_mid_max_n() (mid.cu).  ws: ws_bytes >= apsp_mid_workspace_min(n)
+// bytes; with apsp_mid_workspace(n, S) bytes the launch also builds edge
+// lists of W, which give the first squaring by sparse products (when every
+// row has at most apsp_mid_list_cap(n) edges) and the closure certificate
+// that saves the squaring which would only confirm the fixpoint.  info
 // (device, 5 ints zeroed by the caller; or null: the words at
 // apsp_mid_info(ws, n), zeroed by the launch): [0] entries outside the
 // domain, [1] largest finite weight, [2] squarings that changed D, [3]
-// status, [4] representations used (1 int32, 4 packed 16-bit).  packed_ok =
+// status, [4] representations used (1 int32, 4 packed 16-bit, 8 the first
+// squaring from the edge lists).  packed_ok =
 // false keeps every squaring on int32 (so does BTAS_MID_NO_U16=1 in the
 // environment).  From n = 1408 (BTAS_MID_WIDE_MIN_N) the launch takes the
 // warp-specialised form with 128 x 128 tiles.  mailbox (optional, a
@@ -152,10 +157,13 @@ int apsp_mid_max_n();
 // 7.12 ms; and with int32 squarings 4.62 vs 6.03, 6.25 vs 6.68, 13.38 vs
 // 13.90 ms; the tiled path wins at 2048, 2816, 3072 and 3584).
 bool apsp_mid_takes(long long n, int sms);
+int apsp_mid_list_cap(long long n);
+size_t apsp_mid_workspace_min(long long n);
 size_t apsp_mid_workspace(long long n, int S);
 int *apsp_mid_info(void *ws, long long n);
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
-                            long long ldd, void *ws, int *info, cudaStream_t st, int *mailbox = nullptr);
+                            long long ldd, void *ws, size_t ws_bytes, int *info, cudaStream_t st,
+                            int *mailbox = nullptr);
 
 // ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
 // pmax (optional): atomicMax of the largest finite value the phases store

@@ -71,7 +71,21 @@ struct MidArgs {
                     // [4] representations used (1 int32, 4 packed 16-bit)
     int *mailbox;   // optional, host-mapped: info[0 .. 4] copied there by block 0 as it exits
     long long timeout_cycles;
+    // Edge lists of W (null when the workspace has no room for them): row i's
+    // edges (j + 1, W[i][j]), j != i, in lists[i * cap .. i * cap + deg[i]) in
+    // no particular order; the other slots are zero.  aux: [0] set if a row has more than cap edges, [1]
+    // edges in all, [64 + s] entries that squaring s lowered, counted per
+    // piece (an over-estimate).  deg, aux and lists are zeroed by the launch.
+    int *deg;
+    int2 *lists;
+    int *aux;
+    int cap;
+    int sparse;  // 1: the first squaring from the edge lists when they hold every edge
+    int cert;    // 0: never; 1: the closure certificate where the estimate allows; 2: after every changing squaring
 };
+
+constexpr int kBoundSat = (1 << 29) - 1;  // published values: a bound saturated to 29 bits, and one flag bit
+constexpr int kFlagBit = 1 << 29;
 
 struct MidSmem {
     int a[2][kKc][kLdA];  // A stage, k-major: a[k][row]; packed mode: duplicated 16-bit words
@@ -83,7 +97,45 @@ __device__ __forceinline__ bool grid_barrier(const MidArgs &a, unsigned &gen, bo
     return btas::grid_barrier(GridSync{a.bar, a.info + 3, a.timeout_cycles}, gen, flag, pval, v0, v1);
 }
 
+__device__ __forceinline__ GridSync gsync_of(const MidArgs &a) { return GridSync{a.bar, a.info + 3, a.timeout_cycles}; }
+
 __device__ __forceinline__ int *bufp(const MidArgs &a, int i) { return i == 0 ? a.buf0 : i == 1 ? a.buf1 : a.buf2; }
+
+// Published after phase 0: the largest weight (saturated), and the flag bit
+// when there are no usable edge lists (none, or a row longer than cap).
+__device__ __forceinline__ unsigned phase0_value(const MidArgs &a) {
+    const unsigned mw = (unsigned)gsync::ld_relaxed_i32(a.info + 1);
+    const bool no_lists = a.lists == nullptr || gsync::ld_relaxed_i32(a.aux) != 0;
+    return min(mw, (unsigned)kBoundSat) | (no_lists ? (unsigned)kFlagBit : 0u);
+}
+
+// Published after squaring s: the largest merged value (saturated; only its
+// comparison with 16383 matters), and the flag bit when the closure
+// certificate should be tried: its edge-list reads, about (entries lowered)
+// x (edges / n), are estimated at most 1/64 of a squaring's n^3 terms.
+__device__ __forceinline__ unsigned squaring_value(const MidArgs &a, int s) {
+    const unsigned m = (unsigned)gsync::ld_relaxed_i32(reinterpret_cast<const int *>(a.bar + 64 + s));
+    bool c = a.cert == 2;
+    if (a.cert == 1 && a.aux != nullptr) {
+        const long long lowered = gsync::ld_relaxed_i32(a.aux + 64 + s), edges = gsync::ld_relaxed_i32(a.aux + 1);
+        const long long n = a.n;
+        c = lowered * edges <= n * n * n * n / 64;
+    }
+    return min(m, (unsigned)kBoundSat) | (c ? (unsigned)kFlagBit : 0u);
+}
+
+// A squaring's largest merged value and lowered-entry count, one atomic per warp.
+__device__ __forceinline__ void report(const MidArgs &a, int s, int mx, int cnt) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx > 0) atomicMax(reinterpret_cast<int *>(a.bar + 64 + s), mx);
+        if (cnt > 0 && a.aux != nullptr) atomicAdd(a.aux + 64 + s, cnt);
+    }
+}
 
 // 16-bit form of an entry of a packed squaring's operand: <= 16383, or 0x7FFF for INF
 __device__ __forceinline__ unsigned u16_of(int v) { return (unsigned)min(v, BTAS_INF_U16); }
@@ -147,7 +199,7 @@ __device__ __forceinline__ void stash(MidSmem &sm, int buf, int tid, const int4 
 // k-step's operands are in flight while this one is computed.
 template <bool U16>
 __device__ __forceinline__ void run_item(const MidArgs &a, const int *in, int *out, int bm, int bn, int k0, int k1,
-                                         MidSmem &sm, int tid, bool &ch, int &mx) {
+                                         MidSmem &sm, int tid, bool &ch, int &mx, int &cnt) {
     const int n = a.n;
     const long long ldx = a.ldx;
     const int ty = tid >> 4, tx = tid & 15;
@@ -219,6 +271,7 @@ __device__ __forceinline__ void run_item(const MidArgs &a, const int *in, int *o
                 atomicMin(out + (long long)i * ldx + j, p);
                 mx = max(mx, p);
                 ch |= p < o[c];
+                cnt += p < o[c];
             }
         }
     }
@@ -228,49 +281,352 @@ __device__ __forceinline__ void run_item(const MidArgs &a, const int *in, int *o
 // u / KS, as pieces of consecutive units of one tile.
 template <bool U16>
 __device__ __forceinline__ void squaring(const MidArgs &a, const int *in, int *out, int tiles, int KS, long long u0,
-                                         long long u1, MidSmem &sm, int tid, bool &ch, int &mx) {
+                                         long long u1, MidSmem &sm, int tid, bool &ch, int &mx, int &cnt) {
     const int n = a.n;
     long long u = u0;
     while (u < u1) {
         const int tile = (int)(u / KS), ks = (int)(u % KS);
         const long long pe = min(u1, (long long)(tile + 1) * KS);
         const int k0 = ks * kKc, k1 = min(n, (int)(pe - (long long)tile * KS) * kKc);
-        run_item<U16>(a, in, out, (tile / tiles) * kT, (tile % tiles) * kT, k0, k1, sm, tid, ch, mx);
+        run_item<U16>(a, in, out, (tile / tiles) * kT, (tile % tiles) * kT, k0, k1, sm, tid, ch, mx, cnt);
         u = pe;
     }
 }
 
 // Phase 0 of both forms of the kernel: the domain check, W -> X_0 (buf2) and
 // X_1's buffer (buf0) to INF; the entries outside the domain and the largest
-// finite weight go to info[0] and info[1].  Returns whether this block found
-// an entry outside the domain.
+// finite weight go to info[0] and info[1].  With edge lists, each warp also
+// appends the edges of its 256-column row segments to its row's list (one
+// atomicAdd on deg[i] per segment reserves the slots).  Returns whether this
+// block found an entry outside the domain.
 __device__ __forceinline__ bool mid_phase0(const MidArgs &a, long long gtid, long long gthreads) {
-    const int n = a.n;
-    const long long ldx = a.ldx, nx = (long long)n * ldx;
-    int bad = 0, mx = 0;
-    for (long long idx = gtid; idx < nx; idx += gthreads) {
-        const int i = (int)(idx / ldx), j = (int)(idx % ldx);
-        int v = kInfI32;
-        if (j < n) {
-            v = a.W[(long long)i * a.ldw + j];
-            const bool fin = v >= 0 && v <= BTAS_I32_FINITE_MAX;
-            if ((!fin && v != kInfI32) || (i == j && v != 0)) ++bad;
-            if (fin) mx = max(mx, v);
+    const int n = a.n, lane = threadIdx.x & 31;
+    const long long ldx = a.ldx;
+    const int spr = (int)((ldx + 255) / 256);  // segments per row
+    const long long nseg = (long long)n * spr, gw = gtid >> 5, nw = gthreads >> 5;
+    int bad = 0, mx = 0, edges = 0;
+    for (long long sg = gw; sg < nseg; sg += nw) {
+        const int i = (int)(sg / spr), c0 = (int)(sg % spr) * 256;
+        int v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int j = c0 + 32 * t + lane;
+            v[t] = j < n ? a.W[(long long)i * a.ldw + j] : kInfI32;
         }
-        a.buf2[idx] = v;
-        a.buf0[idx] = kInfI32;
+        unsigned m[8];
+        int tot = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int j = c0 + 32 * t + lane;
+            const bool fin = v[t] >= 0 && v[t] <= BTAS_I32_FINITE_MAX;  // false past column n - 1 (INF)
+            if (j < n && ((!fin && v[t] != kInfI32) || (i == j && v[t] != 0))) ++bad;
+            if (fin) mx = max(mx, v[t]);
+            if (j < ldx) {
+                a.buf2[(long long)i * ldx + j] = v[t];
+                a.buf0[(long long)i * ldx + j] = kInfI32;
+            }
+            m[t] = __ballot_sync(0xffffffffu, fin && j != i);
+            tot += __popc(m[t]);
+        }
+        if (a.lists != nullptr && tot > 0) {  // warp-uniform
+            int base = 0;
+            if (lane == 0) base = atomicAdd(a.deg + i, tot);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (lane == 0 && base + tot > a.cap) atomicOr(a.aux, 1);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int q = base + __popc(m[t] & ((1u << lane) - 1u));
+                if (((m[t] >> lane) & 1u) && q < a.cap)
+                    a.lists[(long long)i * a.cap + q] = make_int2(c0 + 32 * t + lane + 1, v[t]);
+                base += __popc(m[t]);
+            }
+            edges += tot;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         bad += __shfl_xor_sync(0xffffffffu, bad, o);
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (bad) atomicAdd(a.info + 0, bad);
         atomicMax(a.info + 1, mx);
+        if (edges) atomicAdd(a.aux + 1, edges);
     }
     return __syncthreads_or(bad != 0) != 0;
 }
+
+// The rows of this block in the sparse first squaring and the closure
+// certificate: an equal contiguous share of the n rows.
+__device__ __forceinline__ void block_rows(int n, int &r0, int &r1) {
+    r0 = (int)((long long)n * blockIdx.x / gridDim.x);
+    r1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
+}
+
+// Up to 64 rows of a block at a time in shared memory, and beside them the
+// prefix sums of their degrees (65 words) or a list of entries.
+constexpr int kRowsMax = 64;
+constexpr int kPfxWords = 128;
+
+// Rows of a chunk: each takes its X row (ldx words) and, in the sparse
+// squaring, its own edge list (2 cap words).
+__device__ __forceinline__ int sparse_rows(const MidArgs &a, int smem_words) {
+    return min(kRowsMax, (smem_words - kPfxWords) / (int)(a.ldx + 2 * a.cap));
+}
+__device__ __forceinline__ bool sparse_fits(const MidArgs &a, int smem_words) { return sparse_rows(a, smem_words) >= 1; }
+__device__ __forceinline__ bool certify_fits(const MidArgs &a, int smem_words) {
+    return (smem_words / 2) / a.ldx >= 1 && smem_words / 2 > kPfxWords;
+}
+
+// The first 32 H entries of edge list k, H per lane.  Entries hold (j + 1,
+// w) and unused slots are zero, so a list ends at its first zero slot (or at
+// cap).
+template <int H>
+__device__ __forceinline__ void list_head(const MidArgs &a, int k, int lane, int2 (&ev)[H]) {
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int q = lane + 32 * h;
+        ev[h] = q < a.cap ? __ldcg(a.lists + (long long)k * a.cap + q) : make_int2(0, 0);
+    }
+}
+
+// Squaring 1 from the edge lists.  X_1[i][j] = min over k of X_0[i][k] +
+// X_0[k][j]; the terms k = i and k = j are W[i][j] itself, and every other
+// finite term is w_ik + w_kj over edges (i, k) and (k, j), at most 2^29, so
+// no clamp applies.  A chunk of the block's rows starts as W[i][.] in shared
+// memory, beside the rows' own edge lists; the block's warps take the (row,
+// k) pairs (warp w: pairs w, w + warps, ...), read the lists of 8 k at once
+// with the lanes along each list, and lower the row entries with
+// shared-memory atomicMin.  The rows then go to out (whose padding columns
+// stay INF), with the change test against X_0, the largest finite entry and
+// the count of lowered entries.
+template <int IF, int UN, int H>
+__device__ __forceinline__ void sparse_first(const MidArgs &a, int *out, int *smem, int smem_words, bool &ch,
+                                             int &mx, int &cnt) {
+    const int n = a.n, cap = a.cap, tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int ldx = (int)a.ldx;
+    const int R = sparse_rows(a, smem_words);  // >= 1: checked by the caller
+    int *pfx = smem + (smem_words - kPfxWords);
+    int ra, rb;
+    block_rows(n, ra, rb);
+    for (int r0 = ra; r0 < rb; r0 += R) {
+        const int nr = min(R, rb - r0);
+        int2 *own = reinterpret_cast<int2 *>(smem + nr * ldx);  // nr x cap edges, 8-byte aligned
+        // rows of X_0, the rows' own lists and their degrees: all loads in flight together
+        const int rwords = nr * ldx, lwords = nr * cap * 2, total = rwords + lwords;
+        if (warp == 0) {  // inclusive scan of the degrees: pfx[r + 1] = edges of rows r0 .. r0 + r
+            int d0 = lane < nr ? __ldcg(a.deg + r0 + lane) : 0;
+            int d1 = lane + 32 < nr ? __ldcg(a.deg + r0 + lane + 32) : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x0 = __shfl_up_sync(0xffffffffu, d0, o), x1 = __shfl_up_sync(0xffffffffu, d1, o);
+                if (lane >= o) d0 += x0, d1 += x1;
+            }
+            d1 += __shfl_sync(0xffffffffu, d0, 31);
+            pfx[lane + 1] = d0;
+            pfx[lane + 33] = d1;
+            if (lane == 0) pfx[0] = 0;
+        }
+        for (int e0 = 0; e0 < total; e0 += nthr * 4 * UN) {
+            int4 w[UN];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int e = e0 + (u * nthr + tid) * 4;
+                if (e < rwords) w[u] = __ldcg(reinterpret_cast<const int4 *>(a.buf2 + (long long)r0 * ldx + e));
+                else if (e < total) w[u] = __ldcg(reinterpret_cast<const int4 *>(a.lists + (long long)r0 * cap) + (e - rwords) / 4);
+            }
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int e = e0 + (u * nthr + tid) * 4;
+                if (e < total) *reinterpret_cast<int4 *>(smem + e) = w[u];
+            }
+        }
+        __syncthreads();
+        const int P = pfx[nr];
+        for (int g0 = warp; g0 < P; g0 += nwarp * 32) {
+            // lane l sets up the warp's pair g0 + nwarp * l from shared memory
+            const int p = g0 + nwarp * lane;
+            int r = 0, k = 0, wik = 0;
+            if (p < P) {
+                int lo = 0, hi = nr;  // the row r with pfx[r] <= p < pfx[r + 1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pfx[mid] <= p) lo = mid;
+                    else hi = mid;
+                }
+                r = lo;
+                const int2 e = own[r * cap + (p - pfx[r])];
+                k = e.x - 1;
+                wik = e.y;
+            }
+            const int np = min(32, (P - g0 + nwarp - 1) / nwarp);
+            for (int t = 0; t < np; t += IF) {
+                int2 ev[IF][H];  // the heads of IF lists; the pairs' values are taken again below
+#pragma unroll
+                for (int u = 0; u < IF; ++u) {
+                    const int kk = __shfl_sync(0xffffffffu, k, (t + u) & 31);
+                    if (t + u < np) list_head<H>(a, kk, lane, ev[u]);
+                    else {
+#pragma unroll
+                        for (int h = 0; h < H; ++h) ev[u][h] = make_int2(0, 0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < IF; ++u) {
+                    const int src = (t + u) & 31;
+                    int *row = smem + __shfl_sync(0xffffffffu, r, src) * ldx;
+                    const int ww = __shfl_sync(0xffffffffu, wik, src);
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        if (ev[u][h].x > 0) atomicMin(row + ev[u][h].x - 1, ww + ev[u][h].y);
+                    // a full head: the rest of the list (warp-uniform test)
+                    if (__shfl_sync(0xffffffffu, ev[u][H - 1].x, 31) > 0 && cap > 32 * H) {
+                        const int kk = __shfl_sync(0xffffffffu, k, src);
+                        const int dk = __ldcg(a.deg + kk);
+                        for (int q = 32 * H + lane; q < dk; q += 32) {
+                            const int2 e = __ldcg(a.lists + (long long)kk * cap + q);
+                            atomicMin(row + e.x - 1, ww + e.y);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int e0 = 0; e0 < rwords; e0 += nthr * 4 * UN) {
+            int4 o[UN];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int e = e0 + (u * nthr + tid) * 4;
+                if (e < rwords) o[u] = __ldcg(reinterpret_cast<const int4 *>(a.buf2 + (long long)r0 * ldx + e));
+            }
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int e = e0 + (u * nthr + tid) * 4;
+                if (e >= rwords) continue;
+                const int4 v = *reinterpret_cast<const int4 *>(smem + e);
+                *reinterpret_cast<int4 *>(out + (long long)r0 * ldx + e) = v;
+                const int vv[4] = {v.x, v.y, v.z, v.w}, oo[4] = {o[u].x, o[u].y, o[u].z, o[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (vv[c] < kInfI32) mx = max(mx, vv[c]);
+                    if (vv[c] < oo[c]) {
+                        ch = true;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the chunk's shared memory is reused by the next chunk
+    }
+}
+
+// Closure certificate after squaring s.  Y = X_s is the closure exactly when
+// Y[i][j] <= c(Y[i][k] + W[k][j]) for all i, k, j, with c the clamp of the
+// products (sums >= INF - 2^28 become INF): then Y (x) Y = Y, so squaring
+// s + 1 would change nothing.  A pair (i, k) that squaring s left unchanged
+// satisfies it: Y[i][j] <= c(X_{s-1}[i][k] + X_{s-1}[k][j]) and X_{s-1} <= W.
+// So only the entries squaring s lowered are checked, against the edges
+// (k, j), j != k, of their column k (j = k adds 0).  The block's rows go to
+// shared memory with the list of their lowered entries; the warps take the
+// entries (warp w: entries w, w + warps, ...) and read the edge lists of 8
+// entries at once along the lanes.  Returns true if this block found a
+// violation, or could not hold its list of lowered entries (then it
+// certifies nothing).
+template <int IF, int UN, int H>
+__device__ __forceinline__ bool certify(const MidArgs &a, const int *Y, const int *Xp, int *smem, int smem_words) {
+    const int n = a.n, cap = a.cap, tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int ldx = (int)a.ldx;
+    const int R = min(kRowsMax, (smem_words / 2) / ldx);  // >= 1: checked by the caller
+    int *plist = smem + R * ldx;
+    const int L = smem_words - R * ldx - kPfxWords;  // list capacity, >= smem_words / 2 - kPfxWords
+    int *s_cnt = smem + (smem_words - kPfxWords);
+    bool viol = false;
+    int ra, rb;
+    block_rows(n, ra, rb);
+    for (int r0 = ra; r0 < rb; r0 += R) {
+        const int nr = min(R, rb - r0);
+        if (tid == 0) *s_cnt = 0;
+        __syncthreads();
+        const int total = nr * ldx;
+        for (int e0 = 0; e0 < total; e0 += nthr * 4 * UN) {  // the same trip count in every lane
+            int4 y[UN], x[UN];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {  // all loads in flight first
+                const int e = e0 + (u * nthr + tid) * 4;
+                y[u] = x[u] = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+                if (e < total) {
+                    const long long g = (long long)r0 * ldx + e;
+                    y[u] = __ldcg(reinterpret_cast<const int4 *>(Y + g));
+                    x[u] = __ldcg(reinterpret_cast<const int4 *>(Xp + g));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int e = e0 + (u * nthr + tid) * 4;
+                if (e < total) *reinterpret_cast<int4 *>(smem + e) = y[u];
+                const int yy[4] = {y[u].x, y[u].y, y[u].z, y[u].w}, xx[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool low = yy[c] < xx[c];
+                    const unsigned m = __ballot_sync(0xffffffffu, low);
+                    int base = 0;
+                    if (lane == 0 && m) base = atomicAdd(s_cnt, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const int q = base + __popc(m & ((1u << lane) - 1u));
+                    if (low && q < L) plist[q] = e + c;
+                }
+            }
+        }
+        __syncthreads();
+        const int P = *s_cnt;
+        if (P > L) viol = true;  // the list did not fit: no certificate from this block
+        const int PP = P > L ? 0 : P;
+        for (int g0 = warp; g0 < PP; g0 += nwarp * 32) {  // as in sparse_first
+            const int p = g0 + nwarp * lane;
+            const int idx = p < PP ? plist[p] : 0;
+            const int np = min(32, (PP - g0 + nwarp - 1) / nwarp);
+            for (int t = 0; t < np; t += IF) {
+                int2 ev[IF][H];
+#pragma unroll
+                for (int u = 0; u < IF; ++u) {
+                    const int k = __shfl_sync(0xffffffffu, idx, (t + u) & 31) % ldx;
+                    if (t + u < np) list_head<H>(a, k, lane, ev[u]);
+                    else {
+#pragma unroll
+                        for (int h = 0; h < H; ++h) ev[u][h] = make_int2(0, 0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < IF; ++u) {
+                    const int ii = __shfl_sync(0xffffffffu, idx, (t + u) & 31);
+                    const int k = ii % ldx;
+                    const int *row = smem + (ii - k);
+                    const int yk = smem[ii];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        if (ev[u][h].x > 0) {
+                            const int sum = yk + ev[u][h].y;
+                            viol |= sum < kClampI32 && sum < row[ev[u][h].x - 1];
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, ev[u][H - 1].x, 31) > 0 && cap > 32 * H) {  // a full head
+                        const int dk = __ldcg(a.deg + k);
+                        for (int q = 32 * H + lane; q < dk; q += 32) {
+                            const int2 e = __ldcg(a.lists + (long long)k * cap + q);
+                            const int sum = yk + e.y;
+                            viol |= sum < kClampI32 && sum < row[e.x - 1];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    return viol;
+}
+
 
 // The result X_last -> D (W was read only in phase 0, so D may be W), and the
 // squarings that changed D and the representations used to info[2], info[4].
@@ -295,12 +651,16 @@ __device__ __forceinline__ void mid_body(const MidArgs &a) {
     const long long gtid = (long long)blockIdx.x * kThreads + tid;
     unsigned gen = 0;
 
-    // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF
+    // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF, edge lists
     const bool bad_block = mid_phase0(a, gtid, gthreads);
-    int nbad = 0, bound = 0;  // bound: >= every finite entry of X_{s-1}
+    int nbad = 0, v = 0;
     if (a.withhold && blockIdx.x == gridDim.x - 1) return;
-    if (!grid_barrier(a, gen, bad_block, a.info + 1, nbad, bound)) return;
+    if (!grid_barrier_fn(gsync_of(a), gen, bad_block, [&a]() { return phase0_value(a); }, nbad, v)) return;
     if (nbad != 0) return;  // D untouched
+    int bound = v & kBoundSat;  // >= every finite entry of X_{s-1}
+    const bool lists_ok = (v & kFlagBit) == 0;
+    int *smem = reinterpret_cast<int *>(&sm);
+    constexpr int smem_words = (int)(sizeof(MidSmem) / 4);
 
     // stream-K split of the (tile, k-step) units: equal shares, +-1 unit
     const int tiles = (n + kT - 1) / kT, KS = (n + kKc - 1) / kKc;
@@ -315,23 +675,32 @@ __device__ __forceinline__ void mid_body(const MidArgs &a) {
             int4 *nxt = reinterpret_cast<int4 *>(bufp(a, (cur + 1) % 3));
             for (long long idx = gtid; idx < nx / 4; idx += gthreads) nxt[idx] = inf4;
         }
+        const bool sparse = s == 1 && lists_ok && a.sparse && sparse_fits(a, smem_words);
         const bool u16 = a.u16_ok && bound <= kU16Max;
-        path |= u16 ? 4 : 1;
+        path |= sparse ? 8 : u16 ? 4 : 1;
         bool ch = false;
-        int mx = 0;
-        if (u16)
-            squaring<true>(a, in, out, tiles, KS, u0, u1, sm, tid, ch, mx);
+        int mx = 0, cnt = 0;
+        if (sparse)
+            sparse_first<8, 2, 2>(a, out, smem, smem_words, ch, mx, cnt);
+        else if (u16)
+            squaring<true>(a, in, out, tiles, KS, u0, u1, sm, tid, ch, mx, cnt);
         else
-            squaring<false>(a, in, out, tiles, KS, u0, u1, sm, tid, ch, mx);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((tid & 31) == 0 && mx > 0) atomicMax(reinterpret_cast<int *>(a.bar + 64 + s), mx);
+            squaring<false>(a, in, out, tiles, KS, u0, u1, sm, tid, ch, mx, cnt);
+        report(a, s, mx, cnt);
         int changed = 0;
-        if (!grid_barrier(a, gen, ch, reinterpret_cast<const int *>(a.bar + 64 + s), changed, bound)) return;
+        if (!grid_barrier_fn(gsync_of(a), gen, ch, [&a, s]() { return squaring_value(a, s); }, changed, v)) return;
+        bound = v & kBoundSat;
         done += changed != 0;
+        const int *prev = in;
         in = out;
         cur = (cur + 1) % 3;
         if (!changed && a.early) break;
+        if ((v & kFlagBit) && lists_ok && a.early && s < a.S && certify_fits(a, smem_words)) {
+            const bool viol = certify<8, 2, 2>(a, in, prev, smem, smem_words);
+            int any = 0, unused = 0;
+            if (!grid_barrier(a, gen, viol, nullptr, any, unused)) return;
+            if (!any) break;  // X_s is the closure: squaring s + 1 would change nothing
+        }
     }
     mid_finish(a, in, gtid, gthreads, done, path);
 }
@@ -487,7 +856,8 @@ __device__ __forceinline__ bool ww_produce(const MidArgs &a, const int *in, int 
 // (packed: pairs 4 tx .. 4 tx + 3).  Returns false on a timeout.
 template <bool U16>
 __device__ __forceinline__ bool ww_consume(const MidArgs &a, const int *in, int *out, int tiles, int KS, long long u0,
-                                           long long u1, long long qbase, WwSmem &sm, int tid, bool &ch, int &mx) {
+                                           long long u1, long long qbase, WwSmem &sm, int tid, bool &ch, int &mx,
+                                           int &cnt) {
     const int n = a.n;
     const long long ldx = a.ldx;
     const int ty = tid >> 4, tx = tid & 15, lane = tid & 31;
@@ -572,6 +942,7 @@ __device__ __forceinline__ bool ww_consume(const MidArgs &a, const int *in, int 
                     atomicMin(out + (long long)i * ldx + j, p);
                     mx = max(mx, p);
                     ch |= p < o[c];
+                    cnt += p < o[c];
                 }
             }
         }
@@ -580,8 +951,22 @@ __device__ __forceinline__ bool ww_consume(const MidArgs &a, const int *in, int 
     return true;
 }
 
+extern __shared__ __align__(16) unsigned char ww_raw[];  // the wide form's dynamic shared memory
+
+// The wide form's certificate and the grid barrier that combines it (barrier
+// number gen + 1), on the ring's stages: 1 if X_s is the closure, 0 if not,
+// -1 if the barrier gave up (status set).  Not inlined: it runs at most a few
+// times per solve, and inside the squaring loop its code would take
+// registers from the products.
+__device__ __noinline__ int certify_step_wide(const MidArgs &a, unsigned gen, const int *Y, const int *Xp) {
+    int *smem = reinterpret_cast<int *>(reinterpret_cast<WwSmem *>(ww_raw)->st);
+    const bool viol = certify<8, 1, 4>(a, Y, Xp, smem, (int)(sizeof(WwStage) * kWStages / 4));
+    int any = 0, unused = 0;
+    if (!grid_barrier(a, gen, viol, nullptr, any, unused)) return -1;
+    return any ? 0 : 1;
+}
+
 __device__ __forceinline__ void mid_wide_body(const MidArgs &a) {
-    extern __shared__ __align__(16) unsigned char ww_raw[];
     WwSmem &sm = *reinterpret_cast<WwSmem *>(ww_raw);
     const int n = a.n, tid = threadIdx.x;
     const bool producer = tid >= kWConsumers;
@@ -597,12 +982,15 @@ __device__ __forceinline__ void mid_wide_body(const MidArgs &a) {
         }
     }
     __syncthreads();
-    // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF
+    // phase 0: domain check, W -> X_0 (buf2), X_1's buffer to INF, edge lists
     const bool bad_block = mid_phase0(a, gtid, gthreads);
-    int nbad = 0, bound = 0;
+    int nbad = 0, v = 0;
     if (a.withhold && blockIdx.x == gridDim.x - 1) return;
-    if (!grid_barrier(a, gen, bad_block, a.info + 1, nbad, bound)) return;
+    if (!grid_barrier_fn(gsync_of(a), gen, bad_block, [&a]() { return phase0_value(a); }, nbad, v)) return;
     if (nbad != 0) return;  // D untouched
+    int bound = v & kBoundSat;
+    const bool lists_ok = (v & kFlagBit) == 0;
+    constexpr int smem_words = (int)(sizeof(WwStage) * kWStages / 4);  // the ring's stages, idle between squarings
 
     const int tiles = (n + kWT - 1) / kWT, KS = (n + kKc - 1) / kKc;
     const long long U = (long long)tiles * tiles * KS;
@@ -617,27 +1005,37 @@ __device__ __forceinline__ void mid_wide_body(const MidArgs &a) {
             int4 *nxt = reinterpret_cast<int4 *>(bufp(a, (cur + 1) % 3));
             for (long long idx = gtid; idx < nx / 4; idx += gthreads) nxt[idx] = inf4;
         }
+        const bool sparse = s == 1 && lists_ok && a.sparse && sparse_fits(a, smem_words);
         const bool u16 = a.u16_ok && bound <= kU16Max;
-        path |= u16 ? 4 : 1;
+        path |= sparse ? 8 : u16 ? 4 : 1;
         bool ch = false;
-        int mx = 0;
-        if (producer) {
-            if (u16) ww_produce<true>(a, in, tiles, KS, u0, u1, qbase, sm, tid - kWConsumers);
-            else ww_produce<false>(a, in, tiles, KS, u0, u1, qbase, sm, tid - kWConsumers);
+        int mx = 0, cnt = 0;
+        if (sparse) {
+            sparse_first<8, 1, 4>(a, out, reinterpret_cast<int *>(sm.st), smem_words, ch, mx, cnt);
         } else {
-            if (u16) ww_consume<true>(a, in, out, tiles, KS, u0, u1, qbase, sm, tid, ch, mx);
-            else ww_consume<false>(a, in, out, tiles, KS, u0, u1, qbase, sm, tid, ch, mx);
+            if (producer) {
+                if (u16) ww_produce<true>(a, in, tiles, KS, u0, u1, qbase, sm, tid - kWConsumers);
+                else ww_produce<false>(a, in, tiles, KS, u0, u1, qbase, sm, tid - kWConsumers);
+            } else {
+                if (u16) ww_consume<true>(a, in, out, tiles, KS, u0, u1, qbase, sm, tid, ch, mx, cnt);
+                else ww_consume<false>(a, in, out, tiles, KS, u0, u1, qbase, sm, tid, ch, mx, cnt);
+            }
+            qbase += u1 - u0;  // units through the ring
         }
-        qbase += u1 - u0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((tid & 31) == 0 && mx > 0) atomicMax(reinterpret_cast<int *>(a.bar + 64 + s), mx);
+        report(a, s, mx, cnt);
         int changed = 0;
-        if (!grid_barrier(a, gen, ch, reinterpret_cast<const int *>(a.bar + 64 + s), changed, bound)) return;
+        if (!grid_barrier_fn(gsync_of(a), gen, ch, [&a, s]() { return squaring_value(a, s); }, changed, v)) return;
+        bound = v & kBoundSat;
         done += changed != 0;
+        const int *prev = in;
         in = out;
         cur = (cur + 1) % 3;
         if (!changed && a.early) break;
+        if ((v & kFlagBit) && lists_ok && a.early && s < a.S && certify_fits(a, smem_words)) {
+            const int c = certify_step_wide(a, gen++, in, prev);
+            if (c < 0) return;
+            if (c > 0) break;  // X_s is the closure: squaring s + 1 would change nothing
+        }
     }
     mid_finish(a, in, gtid, gthreads, done, path);
 }
@@ -688,20 +1086,41 @@ bool apsp_mid_takes(long long n, int sms) {
 }
 
 // workspace: three n x ldx matrices, then 512 bytes of barrier words and
-// 256 bytes for the status words of a caller that passes info = null
+// 256 bytes for the status words of a caller that passes info = null (the
+// minimum); then 1 KiB of aux words, the row degrees and the edge lists.
+namespace {
+size_t mid_mat_bytes(long long n) { return ((size_t)n * ((n + 3) & ~3LL) * 4 + 255) & ~size_t(255); }
+size_t mid_deg_bytes(long long n) { return ((size_t)n * 4 + 255) & ~size_t(255); }
+}  // namespace
+
+// Edges per row the lists hold: n / 4 rounded up to a multiple of 32, in [32,
+// 256] (a first squaring with more edges per row gains little from them);
+// BTAS_MID_LIST_CAP overrides it (tests), rounded up to an even number so
+// that every row's list starts on a 16-byte boundary.
+int apsp_mid_list_cap(long long n) {
+    const char *e = getenv("BTAS_MID_LIST_CAP");
+    if (e && *e) {
+        const int v = atoi(e);
+        return v < 2 ? 2 : v > 4096 ? 4096 : (v + 1) & ~1;
+    }
+    const long long c = ((n / 4 + 31) / 32) * 32;
+    return (int)std::min(256LL, std::max(32LL, c));
+}
+
+size_t apsp_mid_workspace_min(long long n) { return 3 * mid_mat_bytes(n) + 1024; }
+
 size_t apsp_mid_workspace(long long n, int S) {
     (void)S;
-    const size_t mat = ((size_t)n * ((n + 3) & ~3LL) * 4 + 255) & ~size_t(255);
-    return 3 * mat + 1024;
+    return 3 * mid_mat_bytes(n) + 2048 + mid_deg_bytes(n) + (size_t)n * (size_t)apsp_mid_list_cap(n) * 8;
 }
 
 int *apsp_mid_info(void *ws, long long n) {
-    const size_t mat = ((size_t)n * ((n + 3) & ~3LL) * 4 + 255) & ~size_t(255);
-    return reinterpret_cast<int *>(static_cast<char *>(ws) + 3 * mat + 512);
+    return reinterpret_cast<int *>(static_cast<char *>(ws) + 3 * mid_mat_bytes(n) + 512);
 }
 
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
-                            long long ldd, void *ws, int *info_out_dev, cudaStream_t st, int *mailbox) {
+                            long long ldd, void *ws, size_t ws_bytes, int *info_out_dev, cudaStream_t st,
+                            int *mailbox) {
     // device facts and the kernel's occupancy, queried once per device
     DeviceInfo di{};
     int dev = 0;
@@ -741,8 +1160,13 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     const long long units = tiles * tiles * KS;
     const int grid = (int)std::max(1LL, std::min(units, (long long)(wide ? per_sm_w : per_sm) * sms));
     const long long ldx = (n + 3) & ~3LL;
-    const size_t mat = ((size_t)n * ldx * 4 + 255) & ~size_t(255);
+    const size_t mat = mid_mat_bytes(n);
     char *base = static_cast<char *>(ws);
+    // The edge lists (sparse first squaring, closure certificate) from n =
+    // 384 (BTAS_MID_LISTS_MIN_N): below it a squaring is a few microseconds,
+    // bound by the grid barrier, and the list reads cost as much as they save.
+    const char *lmin = getenv("BTAS_MID_LISTS_MIN_N");
+    const bool lists = ws_bytes >= apsp_mid_workspace(n, S) && n >= (lmin && *lmin ? atoi(lmin) : 384);
     const char *no_u16 = getenv("BTAS_MID_NO_U16");
     MidArgs a{};
     a.W = W;
@@ -763,9 +1187,22 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     a.info = info_out_dev ? info_out_dev : apsp_mid_info(ws, n);
     a.mailbox = mailbox;
     a.timeout_cycles = (long long)(2.0 * (clk_khz > 0 ? clk_khz : 2000000) * 1e3);  // about 2 s
-    // barrier words and per-squaring maxima, and the internal status words
-    // when the caller passes none: one memset
-    cudaError_t e = cudaMemsetAsync(base + 3 * mat, 0, info_out_dev ? 512 : 768, st);
+    // BTAS_MID_NO_SPARSE, BTAS_MID_NO_CERT: the first squaring dense, no
+    // closure certificate; BTAS_MID_CERT_ALWAYS: the certificate after every
+    // changing squaring (tests)
+    const char *no_sp = getenv("BTAS_MID_NO_SPARSE"), *no_ce = getenv("BTAS_MID_NO_CERT"),
+               *ce_all = getenv("BTAS_MID_CERT_ALWAYS");
+    a.cap = apsp_mid_list_cap(n);
+    a.aux = lists ? reinterpret_cast<int *>(base + 3 * mat + 1024) : nullptr;
+    a.deg = lists ? reinterpret_cast<int *>(base + 3 * mat + 2048) : nullptr;
+    a.lists = lists ? reinterpret_cast<int2 *>(base + 3 * mat + 2048 + mid_deg_bytes(n)) : nullptr;
+    a.sparse = (no_sp && *no_sp && atoi(no_sp) != 0) ? 0 : 1;
+    a.cert = (no_ce && *no_ce && atoi(no_ce) != 0) ? 0 : (ce_all && *ce_all && atoi(ce_all) != 0) ? 2 : 1;
+    // barrier words and per-squaring maxima, the internal status words when
+    // the caller passes none, and with edge lists the aux words, degrees and
+    // lists: one memset
+    const size_t zero = lists ? apsp_mid_workspace(n, S) - 3 * mat : info_out_dev ? 512 : 768;
+    cudaError_t e = cudaMemsetAsync(base + 3 * mat, 0, zero, st);
     if (e != cudaSuccess) return e;
     void *args[] = {&a};
     if (wide)

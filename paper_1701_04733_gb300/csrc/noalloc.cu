@@ -46,11 +46,15 @@ namespace {
 constexpr long long kMaxN = BTAS_NOALLOC_MAX_N;
 constexpr size_t kFlagBytes = 256;                                  // change flags (<= 64 ints)
 constexpr size_t kMatBytes = (size_t)kMaxN * (size_t)kMaxN * 4;     // one n x n int32 matrix
-static_assert(BTAS_NOALLOC_SCRATCH_BYTES == kFlagBytes + 3 * kMatBytes + 1024, "scratch layout");
+constexpr size_t kMidBytes = BTAS_NOALLOC_SCRATCH_BYTES - kFlagBytes;  // the cooperative kernel's workspace
+static_assert(BTAS_NOALLOC_SCRATCH_BYTES ==
+                  kFlagBytes + 3 * kMatBytes + 2048 + 4 * (size_t)kMaxN + 8 * 256 * (size_t)kMaxN,
+              "scratch layout");
 
 // The scratch: [flags | X (ping-pong output) | T (transpose, row pitch
-// round4(n)) | one more matrix + 1 KiB]; the cooperative kernel takes
-// everything after the flags as its workspace.
+// round4(n)) | one more matrix, 2 KiB and the edge lists of up to 256 edges
+// per row]; the cooperative kernel takes everything after the flags as its
+// workspace.
 static __device__ __align__(256) unsigned char g_scratch[BTAS_NOALLOC_SCRATCH_BYTES];
 
 // How the most recent call on each device ran, so that the status query
@@ -152,9 +156,8 @@ extern "C" btas_status btas_apsp_noalloc(int64_t n, const int32_t *W, int32_t *D
         return BTAS_OK;
     }
     const char *no_mid = getenv("BTAS_APSP_NO_MID");  // as in btas_apsp: tiled squarings
-    if (n <= apsp_mid_max_n() && apsp_mid_workspace(n, S) <= 3 * kMatBytes + 1024 &&
-        !(no_mid && *no_mid && atoi(no_mid) != 0)) {
-        e = launch_apsp_mid(W, n, (int)n, S, true, true, D, n, X, flags, st);
+    if (n <= apsp_mid_max_n() && apsp_mid_workspace_min(n) <= kMidBytes && !(no_mid && *no_mid && atoi(no_mid) != 0)) {
+        e = launch_apsp_mid(W, n, (int)n, S, true, true, D, n, X, kMidBytes, flags, st);
         if (e == cudaSuccess) {
             note_regime(dev, kCooperative, S);
             return BTAS_OK;

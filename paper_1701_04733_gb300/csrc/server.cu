@@ -451,7 +451,9 @@ int launch_step(btas_server_t *sv, std::vector<Req *> &units) {
                                   static_cast<int *>(r->P[1]), r->ldp, info, sv->compute);
         else
             e = launch_apsp_mid(static_cast<const int *>(r->P[0]), r->ldp, r->n, r->S, true, true,
-                                static_cast<int *>(r->P[1]), r->ldp, r->Q[0], info, sv->compute);
+                                static_cast<int *>(r->P[1]), r->ldp, r->Q[0],
+                                (size_t)(reinterpret_cast<char *>(r->dflag) - static_cast<char *>(r->Q[0])), info,
+                                sv->compute);
         if (e != cudaSuccess) return -1;
         cudaMemcpyAsync(sv->h_flags + i, info, 4, cudaMemcpyDeviceToHost, sv->compute);
         cudaMemcpyAsync(sv->h_flags + sv->flag_slots + 1 + i, info + 3, 4, cudaMemcpyDeviceToHost, sv->compute);

@@ -1,6 +1,7 @@
 """GPU parity of APSP by repeated squaring (Sec. III) against the oracle:
 Floyd-Warshall (Algorithm 2), the oracle's own squaring, Dijkstra and graph
 invariants.  Distances are integers: bit-exact."""
+import ctypes
 import os
 
 import numpy as np
@@ -54,7 +55,9 @@ def test_config_n256_all_paths(btas, oracle_mod):
         for early in (0, 1):
             D, info = btas.apsp(dev(W), flags=force | early, info=True)
             np.testing.assert_array_equal(host(D), ref, err_msg=f"{name} early={early}")
-            assert info["path"] == {"int32": "int32", "carrier": "fp32-carrier", "u16": "u16x2"}[name]
+            # the cooperative kernel may add its sparse first squaring ("sparse")
+            reps = set(info["path"].split("+")) - {"sparse"}
+            assert reps == {{"int32": "int32", "carrier": "fp32-carrier", "u16": "u16x2"}[name]}
             assert info["bound"] == 255 * int(W[W < INF].max())
     D = host(btas.apsp(dev(W)))
     np.testing.assert_array_equal(D, ref)
@@ -250,8 +253,9 @@ def test_small_graph_single_block_path(btas, oracle_mod, n, one_block_up_to_128)
 
 @pytest.fixture
 def cooperative_from_3():
-    """Send every n >= 3 up to the cooperative kernel's limit to it."""
-    with env(BTAS_APSP_SMALL_MAX_N="0"):
+    """Send every n >= 3 up to the cooperative kernel's limit to it, with its
+    edge lists at every size (by default from n = 384)."""
+    with env(BTAS_APSP_SMALL_MAX_N="0", BTAS_MID_LISTS_MIN_N="0"):
         yield
 
 
@@ -273,15 +277,23 @@ def test_mid_graph_cooperative_path(btas, oracle_mod, n, cooperative_from_3):
             with env(BTAS_MID_NO_U16="1"):
                 D3, info3 = btas.apsp(dev(W), flags=early, info=True)
             D4, info4 = btas.apsp(dev(W), flags=early | btas.APSP_FORCE_I32, info=True)
-            for X in (D, D2, D3, D4):
+            with env(BTAS_MID_NO_SPARSE="1", BTAS_MID_NO_CERT="1"):  # every squaring dense, none skipped
+                D5, info5 = btas.apsp(dev(W), flags=early, info=True)
+            for X in (D, D2, D3, D4, D5):
                 np.testing.assert_array_equal(host(X), ref)
+            # these graphs have few edges per row: the first squaring runs on the edge lists
+            assert "sparse" in info["path"].split("+")
             if expect is None:  # first squaring packed (max w <= 16383), later ones on int32
-                assert "u16x2" in info["path"].split("+")
+                assert "u16x2" in info5["path"].split("+")
             else:
-                assert info["path"] == expect
-            assert info3["path"] == info4["path"] == "int32"
-            assert info["squarings"] == info2["squarings"] == info3["squarings"] == info4["squarings"]
-            assert info["bound"] == info2["bound"] == (n - 1) * int(W[W < INF].max())
+                assert info5["path"] == expect
+                assert set(info["path"].split("+")) - {"sparse"} <= {expect}
+            assert set(info3["path"].split("+")) - {"sparse"} <= {"int32"}
+            assert set(info4["path"].split("+")) - {"sparse"} <= {"int32"}
+            assert info5["path"] != "" and "sparse" not in info5["path"]
+            assert (info["squarings"] == info2["squarings"] == info3["squarings"] == info4["squarings"]
+                    == info5["squarings"])
+            assert info["bound"] == info2["bound"] == info5["bound"] == (n - 1) * int(W[W < INF].max())
         t = dev(W)
         btas.apsp(t, out=t)
         np.testing.assert_array_equal(host(t), ref)
@@ -309,7 +321,7 @@ def test_cooperative_path_above_1024(btas, oracle_mod):
     with env(BTAS_APSP_NO_MID="1"):
         _, info2 = btas.apsp(dev(W), flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32, info=True)
     np.testing.assert_array_equal(host(D), ref)
-    assert info["path"] == "u16x2"
+    assert info["path"] == "u16x2+sparse"  # the first squaring from the edge lists
     assert info["squarings"] == info2["squarings"]
 
 
@@ -355,6 +367,92 @@ def test_wide_cooperative_form(btas, oracle_mod, n, cooperative_from_3):
             t = dev(W)
             btas.apsp(t, out=t)
             np.testing.assert_array_equal(host(t), ref)
+
+
+def _cap(n):
+    """Edges per row the cooperative kernel's lists hold by default."""
+    return min(256, max(32, ((n // 4 + 31) // 32) * 32))
+
+
+def _graphs_for_lists(n):
+    """Graphs for the edge-list paths: sparse random graphs (the usual
+    case), a dense one (its rows overflow the lists, so every squaring is
+    dense), a directed path (every squaring lowers entries, so a certificate
+    tried after each one fails until the last), and rows with exactly cap and
+    cap + 1 edges."""
+    out = [("p0.05", gen.random_graph(gen.BASE_SEED, 1200 + n, n, 0.05, 1, 100)),
+           ("p3/n", gen.random_graph(gen.BASE_SEED, 1300 + n, n, min(1.0, 3.0 / n), 1, 10 ** 6)),
+           ("dense", gen.random_graph(gen.BASE_SEED, 1400 + n, n, 0.6, 1, 1000))]
+    P = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(P, 0)
+    P[np.arange(n - 1), np.arange(1, n)] = 7
+    out.append(("path", P))
+    cap = _cap(n)
+    if cap + 2 <= n:
+        for extra in (0, 1):
+            G = gen.random_graph(gen.BASE_SEED, 1500 + n + extra, n, 2.0 / n, 1, 50)
+            row = G[1].copy()
+            row[:] = INF
+            row[1] = 0
+            cols = [j for j in range(n) if j != 1][: cap + extra]
+            row[cols] = np.arange(1, len(cols) + 1, dtype=np.int32) % 97 + 1
+            G[1] = row
+            out.append((f"deg{cap + extra}", G))
+    return out
+
+
+@pytest.mark.parametrize("wide", [False, True])
+@pytest.mark.parametrize("n", [65, 130, 257, 700, 1100])
+def test_edge_lists_and_certificate(btas, oracle_mod, n, wide, cooperative_from_3):
+    """The cooperative kernel's edge lists: the first squaring as sparse
+    products over them (rows with at most cap edges), and the closure
+    certificate that stops a solve without the squaring that would only
+    confirm the fixpoint.  Every setting -- both on (default), the certificate
+    tried after every changing squaring (BTAS_MID_CERT_ALWAYS=1), lists too
+    short for any row (BTAS_MID_LIST_CAP=4), either one off -- gives the
+    oracle's distances and the squarings count and bound of the run with
+    both off, in both forms of the kernel, with and without early exit."""
+    settings = ({}, {"BTAS_MID_CERT_ALWAYS": "1"}, {"BTAS_MID_LIST_CAP": "4"}, {"BTAS_MID_NO_SPARSE": "1"},
+                {"BTAS_MID_NO_CERT": "1"})
+    form = {"BTAS_MID_WIDE_MIN_N": "0" if wide else "100000"}
+    for name, W in _graphs_for_lists(n):
+        ref = oracle_mod.floyd_warshall(W)
+        deg = ((W < INF).sum(1) - 1).max()
+        for early in (0, 1):
+            with env(BTAS_MID_NO_SPARSE="1", BTAS_MID_NO_CERT="1", **form):
+                D0, info0 = btas.apsp(dev(W), flags=early, info=True)
+            np.testing.assert_array_equal(host(D0), ref)
+            for extra in settings:
+                with env(**form, **extra):
+                    D, info = btas.apsp(dev(W), flags=early, info=True)
+                np.testing.assert_array_equal(host(D), ref, err_msg=f"{name} {extra} early={early}")
+                assert info["squarings"] == info0["squarings"], (name, extra, early)
+                assert info["bound"] == info0["bound"]
+                lists_hold = deg <= int(extra.get("BTAS_MID_LIST_CAP", _cap(n)))
+                used = "sparse" in info["path"].split("+")
+                assert used == (lists_hold and "BTAS_MID_NO_SPARSE" not in extra), (name, extra, info["path"])
+        t = dev(W)
+        btas.apsp(t, out=t)
+        np.testing.assert_array_equal(host(t), ref)
+
+
+def test_edge_lists_allocation_free(btas, oracle_mod, cooperative_from_3):
+    """The allocation-free entry point gives the cooperative kernel room for
+    its edge lists up to n = 1024: same distances and squarings as
+    btas_apsp."""
+    import torch
+    for n in (300, 1024):
+        W = gen.random_graph(gen.BASE_SEED, 1600 + n, n, 0.05, 1, 100)
+        ref = oracle_mod.floyd_warshall(W)
+        Wd = dev(W)
+        D = torch.empty_like(Wd)
+        st = torch.cuda.current_stream().cuda_stream
+        assert btas.btas_apsp_noalloc(n, Wd.data_ptr(), D.data_ptr(), st) == 0
+        sq = ctypes.c_int(-1)
+        assert btas.btas_apsp_noalloc_status(st, ctypes.addressof(sq)) == 0
+        np.testing.assert_array_equal(host(D), ref)
+        _, info = btas.apsp(Wd, info=True)
+        assert sq.value == info["squarings"]
 
 
 @pytest.mark.parametrize("n", [2304, 2560])

@@ -108,7 +108,7 @@ def test_loaded_entry_is_used_and_exact(btas, oracle_mod, tmp_path, entry):
     # weights above 2^23: every squaring runs on the int32 kernels
     W = gen.random_graph(61, 0, n, 0.05, 1, 2 * 10**7)
     D, info = btas.apsp(dev(W), info=True)
-    assert info["path"] == "int32"
+    assert set(info["path"].split("+")) - {"sparse"} == {"int32"}
     np.testing.assert_array_equal(host(D), oracle_mod.apsp_squaring(W))
 
 
