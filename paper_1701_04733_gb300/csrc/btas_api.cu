@@ -725,6 +725,7 @@ static btas_status squaring_loop(int dtype, long long n, int S, const void *cur0
 // kMidFallback if the grid cannot be co-resident on this device (e.g. a
 // shared device); the tiled path then computes the same result.
 constexpr int kMidFallback = -1;
+constexpr int kMidDense = -2;  // the graph is too dense for the cooperative kernel's edge lists: tiled path
 
 // Per host thread, for the one-block and cooperative solves: a host-mapped
 // mailbox that the kernel leaves its status words in (no device-to-host copy
@@ -787,7 +788,9 @@ static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool e
     // the status words inside the workspace: zeroed by the launch
     int *info = apsp_mid_info(wsp, n);
     if (ts.mbox) ts.mbox[3] = -1;  // overwritten by the kernel as it ends
-    const cudaError_t le = launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, wsp, need, nullptr, st, ts.mbox);
+    const bool bail = n > apsp_mid_max_n();  // above it only graphs that fit the edge lists stay here
+    const cudaError_t le =
+        launch_apsp_mid(W, n, (int)n, S, early, packed_ok, D, n, wsp, need, nullptr, st, ts.mbox, bail);
     if (le == cudaErrorCooperativeLaunchTooLarge || le == cudaErrorNotSupported) {
         cudaGetLastError();
         return kMidFallback;
@@ -809,6 +812,10 @@ static int apsp_mid_solve(int64_t n, const int32_t *W, int32_t *D, int S, bool e
                     "btas_apsp: %d entries outside the domain (negative weight, weight > 2^28, or non-zero "
                     "diagonal)",
                     host[0]);
+    }
+    if (host[4] == kMidDeclined) {
+        log_event("apsp n=%lld: too dense for the cooperative kernel's edge lists", (long long)n);
+        return kMidDense;
     }
     if (bound_out) *bound_out = (long long)(n - 1) * host[1];
     if (squarings_done) *squarings_done = host[2];
@@ -886,8 +893,8 @@ static btas_status apsp_impl(int64_t n, const int32_t *W, int32_t *D, int flags,
         !(flags & (BTAS_APSP_FORCE_U16 | BTAS_APSP_FORCE_CARRIER)) && env_int("BTAS_APSP_NO_MID", 0) == 0) {
         const int r = apsp_mid_solve(n, W, D, S, early, !(flags & BTAS_APSP_FORCE_I32), squarings_done, bound_out,
                                      path_out, st);
-        if (r != kMidFallback) return static_cast<btas_status>(r);
-        log_event("apsp n=%lld: cooperative launch not possible here, tiled path", (long long)n);
+        if (r != kMidFallback && r != kMidDense) return static_cast<btas_status>(r);
+        if (r == kMidFallback) log_event("apsp n=%lld: cooperative launch not possible here, tiled path", (long long)n);
     }
 
     Workspace ws(st);

@@ -147,15 +147,21 @@ cudaError_t launch_apsp_small(const int *W, long long ldw, int n, int S, bool ea
 // warp-specialised form with 128 x 128 tiles.  mailbox (optional, a
 // host-mapped pointer the device can write): info[0 .. 4] are copied there
 // as the launch ends, so the caller reads them after synchronising the
-// stream, without a device-to-host copy.
+// stream, without a device-to-host copy.  bail_dense (with the full
+// workspace): if some row of W has more edges than the lists hold, the
+// launch stops after the domain check with D untouched and info[4] =
+// kMidDeclined, and the caller solves on the tiled kernels.
+constexpr int kMidDeclined = 16;
+constexpr long long kMidSparseMaxN = 4096;  // largest n btas_apsp offers the cooperative kernel with bail_dense
 int apsp_mid_max_n();
-// Whether btas_apsp solves n on the cooperative kernel: every n <=
-// apsp_mid_max_n(), and for n <= 3584 (unless BTAS_APSP_MID_MAX_N is set)
-// the sizes where the tiled packed squaring's last wave of 128 x 256 tiles
-// on `sms` SMs would leave the grid less than three-quarters full (measured
-// on GB300: n = 2304: 2.50 vs 3.40 ms, 2560: 3.33 vs 3.77 ms, 3328: 7.00 vs
-// 7.12 ms; and with int32 squarings 4.62 vs 6.03, 6.25 vs 6.68, 13.38 vs
-// 13.90 ms; the tiled path wins at 2048, 2816, 3072 and 3584).
+// Whether btas_apsp offers n to the cooperative kernel: every n <=
+// apsp_mid_max_n(), and (unless BTAS_APSP_MID_MAX_N is set) every n <=
+// kMidSparseMaxN with bail_dense, so that only graphs sparse enough for the
+// edge lists stay there.  With the first squaring from the lists and the
+// closure certificate it beats the tiled kernels on such graphs at every
+// size measured up to 4096 (GB300, p = 0.02 and 0.05: 1.38 vs 1.62 ms at
+// n = 2048, 4.95 vs 5.31 ms at 3072, 10.9 vs 13.7 ms at 4096); on dense
+// graphs neither applies and the tiled kernels are faster above 1792.
 bool apsp_mid_takes(long long n, int sms);
 int apsp_mid_list_cap(long long n);
 size_t apsp_mid_workspace_min(long long n);
@@ -163,7 +169,7 @@ size_t apsp_mid_workspace(long long n, int S);
 int *apsp_mid_info(void *ws, long long n);
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
                             long long ldd, void *ws, size_t ws_bytes, int *info, cudaStream_t st,
-                            int *mailbox = nullptr);
+                            int *mailbox = nullptr, bool bail_dense = false);
 
 // ---- blocked Floyd-Warshall (fw.cu): phases 1 and 2 of pivot block kb
 // pmax (optional): atomicMax of the largest finite value the phases store

@@ -82,6 +82,7 @@ struct MidArgs {
     int cap;
     int sparse;  // 1: the first squaring from the edge lists when they hold every edge
     int cert;    // 0: never; 1: the closure certificate where the estimate allows; 2: after every changing squaring
+    int bail;    // 1: return after phase 0 (D untouched, info[4] = kMidDeclined) unless the lists hold every edge
 };
 
 constexpr int kBoundSat = (1 << 29) - 1;  // published values: a bound saturated to 29 bits, and one flag bit
@@ -111,15 +112,23 @@ __device__ __forceinline__ unsigned phase0_value(const MidArgs &a) {
 
 // Published after squaring s: the largest merged value (saturated; only its
 // comparison with 16383 matters), and the flag bit when the closure
-// certificate should be tried: its edge-list reads, about (entries lowered)
-// x (edges / n), are estimated at most 1/64 of a squaring's n^3 terms.
+// certificate should be tried.  On random graphs the squaring that reaches
+// the fixpoint follows one that lowered far fewer entries than the one
+// before it (3-16 % of it at n = 256 ... 2048, p = 0.02 ... 0.1), while the
+// earlier ones lower a similar share (20 % or more).  So the certificate is
+// tried when squaring s lowered at most 1/6 as many entries as squaring s - 1
+// (all n^2 for s = 1), and its edge-list reads, about (lowered) x (edges / n),
+// are at most n^3 / 128.  (The counts are per piece, up to a few times the
+// entries; a list read costs the time of about 180 product terms, so a
+// certificate that fails costs at most about one squaring.)
 __device__ __forceinline__ unsigned squaring_value(const MidArgs &a, int s) {
     const unsigned m = (unsigned)gsync::ld_relaxed_i32(reinterpret_cast<const int *>(a.bar + 64 + s));
     bool c = a.cert == 2;
     if (a.cert == 1 && a.aux != nullptr) {
-        const long long lowered = gsync::ld_relaxed_i32(a.aux + 64 + s), edges = gsync::ld_relaxed_i32(a.aux + 1);
         const long long n = a.n;
-        c = lowered * edges <= n * n * n * n / 64;
+        const long long lowered = gsync::ld_relaxed_i32(a.aux + 64 + s), edges = gsync::ld_relaxed_i32(a.aux + 1);
+        const long long before = s > 1 ? gsync::ld_relaxed_i32(a.aux + 64 + s - 1) : n * n;
+        c = 6 * lowered <= before && lowered * edges <= n * n * n * n / 128;
     }
     return min(m, (unsigned)kBoundSat) | (c ? (unsigned)kFlagBit : 0u);
 }
@@ -659,6 +668,10 @@ __device__ __forceinline__ void mid_body(const MidArgs &a) {
     if (nbad != 0) return;  // D untouched
     int bound = v & kBoundSat;  // >= every finite entry of X_{s-1}
     const bool lists_ok = (v & kFlagBit) == 0;
+    if (a.bail && !lists_ok) {  // too dense for the edge lists: the caller takes the tiled kernels
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.info[4] = kMidDeclined;
+        return;
+    }
     int *smem = reinterpret_cast<int *>(&sm);
     constexpr int smem_words = (int)(sizeof(MidSmem) / 4);
 
@@ -990,6 +1003,10 @@ __device__ __forceinline__ void mid_wide_body(const MidArgs &a) {
     if (nbad != 0) return;  // D untouched
     int bound = v & kBoundSat;
     const bool lists_ok = (v & kFlagBit) == 0;
+    if (a.bail && !lists_ok) {  // too dense for the edge lists: the caller takes the tiled kernels
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.info[4] = kMidDeclined;
+        return;
+    }
     constexpr int smem_words = (int)(sizeof(WwStage) * kWStages / 4);  // the ring's stages, idle between squarings
 
     const int tiles = (n + kWT - 1) / kWT, KS = (n + kKc - 1) / kKc;
@@ -1064,10 +1081,12 @@ __global__ void __launch_bounds__(kWThreads, 1) apsp_mid_wide_kernel(const MidAr
 }  // namespace
 
 int apsp_mid_max_n() {
-    // largest n btas_apsp sends here: above about 1800 vertices the tiled
-    // product kernels have enough tiles to fill the GPU and win (measured:
-    // 937 vs 1290 us at n = 1536, 2134 vs 1666 us at 2048);
-    // BTAS_APSP_MID_MAX_N overrides it (up to 4096)
+    // largest n btas_apsp always sends here (and the server's whole solves
+    // and the allocation-free entry point): above it, with 128 x 256 tiles
+    // enough to fill the GPU, the tiled kernels win on dense graphs, and
+    // btas_apsp keeps only graphs sparse enough for the edge lists here (up
+    // to kMidSparseMaxN, see apsp_mid_takes); BTAS_APSP_MID_MAX_N overrides
+    // it (up to 4096) and then is a plain limit
     static const int dflt = 1792;
     const char *e = getenv("BTAS_APSP_MID_MAX_N");
     if (!e || !*e) return dflt;
@@ -1076,13 +1095,11 @@ int apsp_mid_max_n() {
 }
 
 bool apsp_mid_takes(long long n, int sms) {
+    (void)sms;
     if (n <= apsp_mid_max_n()) return true;
     const char *e = getenv("BTAS_APSP_MID_MAX_N");
-    if ((e && *e) || n > 3584 || sms < 1) return false;  // an explicit limit wins
-    // the tiled packed squaring: 128 x 256 tiles, one CTA per SM
-    const long long tiles = ((n + 127) / 128) * (((n + 1) / 2 + 127) / 128);
-    const long long waves = (tiles + sms - 1) / sms;
-    return 4 * tiles < 3 * waves * sms;
+    if (e && *e) return false;  // an explicit limit wins
+    return n <= kMidSparseMaxN;  // launched with bail_dense: dense graphs go to the tiled kernels
 }
 
 // workspace: three n x ldx matrices, then 512 bytes of barrier words and
@@ -1120,7 +1137,7 @@ int *apsp_mid_info(void *ws, long long n) {
 
 cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool early, bool packed_ok, int *D,
                             long long ldd, void *ws, size_t ws_bytes, int *info_out_dev, cudaStream_t st,
-                            int *mailbox) {
+                            int *mailbox, bool bail_dense) {
     // device facts and the kernel's occupancy, queried once per device
     DeviceInfo di{};
     int dev = 0;
@@ -1198,6 +1215,7 @@ cudaError_t launch_apsp_mid(const int *W, long long ldw, int n, int S, bool earl
     a.lists = lists ? reinterpret_cast<int2 *>(base + 3 * mat + 2048 + mid_deg_bytes(n)) : nullptr;
     a.sparse = (no_sp && *no_sp && atoi(no_sp) != 0) ? 0 : 1;
     a.cert = (no_ce && *no_ce && atoi(no_ce) != 0) ? 0 : (ce_all && *ce_all && atoi(ce_all) != 0) ? 2 : 1;
+    a.bail = bail_dense && lists && a.sparse ? 1 : 0;
     // barrier words and per-squaring maxima, the internal status words when
     // the caller passes none, and with edge lists the aux words, degrees and
     // lists: one memset

@@ -455,12 +455,11 @@ def test_edge_lists_allocation_free(btas, oracle_mod, cooperative_from_3):
         assert sq.value == info["squarings"]
 
 
-@pytest.mark.parametrize("n", [2304, 2560])
-def test_cooperative_where_tiles_quantise(btas, oracle_mod, n):
-    """Above n = 1792 btas_apsp takes the cooperative kernel where the tiled
-    packed squaring would leave its last wave less than three-quarters full
-    (2304 and 2560 on 152 SMs): distances equal Floyd-Warshall's and the
-    squarings count equals the tiled path's."""
+@pytest.mark.parametrize("n", [2304, 2560, 3000])
+def test_cooperative_above_1792_for_sparse_graphs(btas, oracle_mod, n):
+    """Above n = 1792 btas_apsp keeps a graph on the cooperative kernel when
+    every row fits its edge lists (p = 0.02 here): distances equal
+    Floyd-Warshall's and the squarings count equals the tiled path's."""
     W = gen.random_graph(gen.BASE_SEED, 990 + n, n, 0.02, 1, 100)
     oracle_mod.set_threads(os.cpu_count() or 1)
     try:
@@ -473,3 +472,27 @@ def test_cooperative_where_tiles_quantise(btas, oracle_mod, n):
     np.testing.assert_array_equal(host(D), ref)
     np.testing.assert_array_equal(host(D2), ref)
     assert info["squarings"] == info2["squarings"]
+    assert "sparse" in info["path"].split("+") and "sparse" not in info2["path"]
+
+
+def test_dense_graph_above_1792_goes_tiled(btas, oracle_mod):
+    """A graph too dense for the edge lists (p = 0.5 at n = 2048) is declined
+    by the cooperative kernel after its domain check and solved on the tiled
+    kernels: same distances as Floyd-Warshall, and a domain error is still
+    reported with D untouched."""
+    n = 2048
+    W = gen.random_graph(gen.BASE_SEED, 995, n, 0.5, 1, 1000)
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    try:
+        ref = oracle_mod.floyd_warshall(W)
+    finally:
+        oracle_mod.set_threads(1)
+    D, info = btas.apsp(dev(W), info=True)
+    np.testing.assert_array_equal(host(D), ref)
+    assert "sparse" not in info["path"]
+    bad = W.copy()
+    bad[5, 5] = 3
+    out = dev(np.full((n, n), 11, np.int32))
+    with pytest.raises(btas.BtasError):
+        btas.apsp(dev(bad), out=out)
+    assert (host(out) == 11).all()
