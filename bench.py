@@ -981,7 +981,9 @@ PAPER_TABLE2_MS = {4: (0.008, 0.001062), 16: (0.078, 0.001163999), 32: (0.543, 0
 def config_timings(args, btas, torch):
     """The smaller configurations as timings: one APSP solve at n = 256
     (p = 0.1, w in [1, 100]); the n = 4096 graph with w in [1, 7] on the
-    packed kernel vs the int32 kernel (same bits); and the Floyd-Warshall
+    packed kernel vs the int32 kernel (same bits); mid sizes n = 192 ... 4096
+    (p = 0.05) on the cooperative kernel (the default there), the same with
+    its edge-list shortcuts off, and the tiled path; and the Floyd-Warshall
     sizes of the paper's Table II (4 ... 128 vertices), blocked FW and
     squaring, with the paper's own numbers beside them as context."""
     import gen
@@ -1017,17 +1019,26 @@ def config_timings(args, btas, torch):
     out["n4096_p0.05_w1-7"] = {"packed_u16x2_ms": round(t_u16 / 1e3, 3), "int32_ms": round(t_i32 / 1e3, 3),
                                "speedup": round(t_i32 / t_u16, 3), "identical": bool(torch.equal(D3a, D3b))}
     mid = []
-    for n in (192, 256, 512, 1024):
+    for n in (192, 256, 512, 1024, 1536, 2048, 3072, 4096):
         W = torch.from_numpy(gen.random_graph(s, 300 + n, n, 0.05, 1, 100)).cuda()
         D = torch.empty_like(W)
-        t_coop = lat(lambda: btas.apsp(W, out=D), reps=5)
+        row = {"n": n, "cooperative_us": lat(lambda: btas.apsp(W, out=D), reps=5)}
+        if n >= 512:  # the edge lists' shortcuts off: first squaring dense, confirming squaring computed
+            os.environ.update(BTAS_MID_NO_SPARSE="1", BTAS_MID_NO_CERT="1", BTAS_APSP_MID_MAX_N="4096")
+            try:
+                row["cooperative_no_shortcuts_us"] = lat(lambda: btas.apsp(W, out=D), reps=5)
+            finally:
+                for k in ("BTAS_MID_NO_SPARSE", "BTAS_MID_NO_CERT", "BTAS_APSP_MID_MAX_N"):
+                    del os.environ[k]
         os.environ["BTAS_APSP_NO_MID"] = "1"
         try:
-            t_gen = lat(lambda: btas.apsp(W, out=D), reps=5)
-            t_dev = lat(lambda: btas.apsp(W, out=D, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32), reps=5)
+            row["tiled_adaptive_us"] = lat(lambda: btas.apsp(W, out=D), reps=5)
+            if n <= 1024:
+                row["tiled_int32_device_exit_us"] = lat(
+                    lambda: btas.apsp(W, out=D, flags=btas.APSP_EARLY_EXIT | btas.APSP_FORCE_I32), reps=5)
         finally:
             del os.environ["BTAS_APSP_NO_MID"]
-        mid.append({"n": n, "cooperative_us": t_coop, "tiled_adaptive_us": t_gen, "tiled_int32_device_exit_us": t_dev})
+        mid.append(row)
     out["mid_sizes_p0.05_w1-100"] = mid
     t2 = []
     for n, (cpu_ms, gpu_ms) in PAPER_TABLE2_MS.items():

@@ -298,17 +298,17 @@ btas_status btas_mul(int semiring, int dtype, int64_t n, const void *x, const vo
  *                   operand is <= 16383 (a bound the previous squaring
  *                   reports), else int32 (always int32 with FORCE_I32); from
  *                   n = 1408 with 128 x 128 tiles and warp-specialised
- *                   staging; the same up to n = 3584 where the tiled
- *                   squaring's last wave of tiles would leave the GPU less
- *                   than three-quarters full.  This launch also builds the
- *                   edge lists of W: when every row has at most
- *                   min(256, max(32, n / 4)) edges (rounded to 32) the first
- *                   squaring runs as sparse products over them, and after a
- *                   squaring that lowered few entries a closure certificate
- *                   (X (x) W >= X, checked at the lowered entries) can stop
- *                   the solve without the squaring that would only confirm
- *                   the fixpoint (early exit only); D and the squarings count
- *                   are the same;
+ *                   staging.  From n = 384 the launch also builds edge lists
+ *                   of W: when every row has at most min(256, max(32, n / 4))
+ *                   edges (rounded to 32) the first squaring runs as sparse
+ *                   products over them, and after a squaring that lowered
+ *                   few entries a closure certificate (X (x) W >= X, checked
+ *                   at the lowered entries) can stop the solve without the
+ *                   squaring that would only confirm the fixpoint (early exit
+ *                   only); D and the squarings count are the same;
+ *   1792 < n <= 4096  the same launch for graphs whose rows fit the edge
+ *                   lists; it declines any other graph after the domain check
+ *                   (D untouched), which then takes the tiled kernels;
  *   larger n        the tiled product kernels, one launch per squaring, with
  *                   the per-squaring exact representation described below.
  * BTAS_APSP_SMALL_MAX_N=m (0 .. 128) and BTAS_APSP_MID_MAX_N=m (0 .. 4096) in
