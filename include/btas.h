@@ -610,7 +610,7 @@ int btas_tune_entries(void);
 typedef struct btas_batch_t btas_batch_t;
 #define BTAS_BATCH_NO_GRAPH 0x1
 #define BTAS_BATCH_PROFILE 0x2
-#define BTAS_BATCH_PROFILE_SLOTS 10
+#define BTAS_BATCH_PROFILE_SLOTS 12
 #define BTAS_BATCH_SLOT_TRANSPOSE 0   /* level-0 transposes (and 16-bit forms) */
 #define BTAS_BATCH_SLOT_COPY 1        /* n <= 2 APSP: D = W */
 #define BTAS_BATCH_SLOT_APSP_U16 2    /* APSP squaring tile, packed u16x2 */
@@ -621,6 +621,8 @@ typedef struct btas_batch_t btas_batch_t;
 #define BTAS_BATCH_SLOT_SQUARE_U16 7  /* server single-squaring tile, u16x2 */
 #define BTAS_BATCH_SLOT_SQUARE_I32 8  /* server single-squaring tile, int32 */
 #define BTAS_BATCH_SLOT_WAIT 9        /* waiting for the previous level */
+#define BTAS_BATCH_SLOT_LISTS 10      /* APSP edge lists of W (level 0) */
+#define BTAS_BATCH_SLOT_CERT 11       /* APSP closure certificate after a squaring */
 btas_status btas_batch_create(btas_batch_t **out, int flags);
 btas_status btas_batch_add_apsp(btas_batch_t *b, int64_t n, const int32_t *W, int32_t *D);
 btas_status btas_batch_add_gemm(btas_batch_t *b, int semiring, int dtype, int64_t m, int64_t n, int64_t k,

@@ -42,9 +42,9 @@ STATUS = {0: "BTAS_OK", 1: "BTAS_ERR_ARG", 2: "BTAS_ERR_BOUND", 3: "BTAS_ERR_NOM
           5: "BTAS_ERR_TIMEOUT", 6: "BTAS_ERR_BUDGET", 7: "BTAS_ERR_UNSUPPORTED", 8: "BTAS_ERR_INTERNAL"}
 TUNE_VARIANT_U16 = 16
 BATCH_PROFILE = 0x2
-BATCH_PROFILE_SLOTS = 10
+BATCH_PROFILE_SLOTS = 12
 BATCH_SLOT_NAMES = ("transpose", "copy", "apsp_u16", "apsp_i32", "apsp_done", "gemm_i32", "gemm_f32",
-                    "square_u16", "square_i32", "wait")
+                    "square_u16", "square_i32", "wait", "lists", "cert")
 
 
 class BtasError(RuntimeError):

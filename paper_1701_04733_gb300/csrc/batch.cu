@@ -45,9 +45,183 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
+constexpr int kListRows = 32;  // rows of W per edge-list task (4 per warp)
+
+// The persistent kernel's dynamic shared memory, in words: a product tile's
+// stages or a 128 x 128 transpose, whichever is larger.
+__host__ __device__ constexpr int batch_smem_words() {
+    return (BCfg::kSmemBytes > kBT * (kBT + 1) * 4 ? BCfg::kSmemBytes : kBT * (kBT + 1) * 4) / 4;
+}
+
+__host__ __device__ __forceinline__ int list_tasks(const BInst &I) { return (I.n + kListRows - 1) / kListRows; }
+constexpr int kCertRows = 64;  // rows of D per certificate task, checked in chunks of cert_rows
+__host__ __device__ __forceinline__ int cert_tasks(const BInst &I) {
+    return I.cert_rows > 0 ? (I.n + kCertRows - 1) / kCertRows : 0;
+}
+
+// Certificate tasks follow squarings 2 .. levels - 1 (after the first one
+// nearly every entry is lowered, and the last one ends the solve anyway).
+__host__ __device__ __forceinline__ bool has_cert(const BInst &I, int level) {
+    return I.cert && level >= 2 && level < I.levels;
+}
+
+// Tasks of an instance's level: level 0 the transposes (and an APSP's edge
+// lists), level s >= 1 the output tiles (and, after an APSP squaring s <
+// levels, the certificate tasks).
 __device__ __forceinline__ int tasks_at(const BInst &I, int level) {
-    if (level == 0) return I.t0_rows > 0 ? ((I.t0_rows + kBT - 1) / kBT) * ((I.t0_cols + kBT - 1) / kBT) : 0;
-    return I.tiles_m * I.tiles_n;
+    if (level == 0)
+        return (I.t0_rows > 0 ? ((I.t0_rows + kBT - 1) / kBT) * ((I.t0_cols + kBT - 1) / kBT) : 0) +
+               (I.cert ? list_tasks(I) : 0);
+    return I.tiles_m * I.tiles_n + (has_cert(I, level) ? cert_tasks(I) : 0);
+}
+
+// Edge lists of rows 32 t .. 32 t + 31 of W, four rows per warp: row i's
+// edges (j + 1, w) in lists[i * cap ..] in column order, then zeros up to
+// cap, and deg[i]; a row with more than cap edges sets *ovf.
+__device__ __forceinline__ void lists_task(const BInst &I, int t, int tid, int *ovf) {
+    const int lane = tid & 31, warp = tid >> 5, n = I.n, cap = I.cap;
+    const int *W = static_cast<const int *>(I.A);
+    for (int q = 0; q < kListRows / 8; ++q) {
+        const int i = t * kListRows + warp * (kListRows / 8) + q;
+        if (i >= n) break;  // warp-uniform
+        int2 *L = I.lists + (long long)i * cap;
+        int cnt = 0;
+        for (int j0 = 0; j0 < n; j0 += 256) {
+            int v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + 32 * u + lane;
+                v[u] = j < n ? __ldg(W + (long long)i * I.lda + j) : kInfI32;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + 32 * u + lane;
+                const bool e = j != i && v[u] >= 0 && v[u] <= BTAS_I32_FINITE_MAX;  // false past n - 1
+                const unsigned m = __ballot_sync(0xffffffffu, e);
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                if (e && pos < cap) L[pos] = make_int2(j + 1, v[u]);
+                cnt += __popc(m);
+            }
+        }
+        for (int q2 = cnt + lane; q2 < cap; q2 += 32) L[q2] = make_int2(0, 0);
+        if (lane == 0) {
+            I.deg[i] = cnt;
+            if (cnt > cap) atomicOr(ovf, 1);
+        }
+    }
+}
+
+// Closure certificate after squaring s >= 2 over rows 64 t .. 64 t + 63, in
+// chunks of R = cert_rows rows: Y = D_s is the closure exactly when Y[i][j]
+// <= c(Y[i][k] + W[k][j]) for all i, k, j (c: the products' clamp); pairs
+// (i, k) that squaring s left unchanged satisfy it (Y[i][j] <= c(D_{s-1}[i][k]
+// + D_{s-1}[k][j]) and D_{s-1} <= W), so only the lowered entries are
+// checked, against the edges of column k.  Returns true (for every thread)
+// on a violation, when a chunk's lowered entries exceed an eighth of its
+// entries or the shared list, or when another task of this level has failed
+// already (*failed): then it certifies nothing.
+__device__ __forceinline__ bool cert_task(const BInst &I, int s, int t, int *smem, int smem_words, int tid,
+                                          const int *failed) {
+    const int n = I.n, cap = I.cap, ldx = (int)I.ldx, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    const int R = I.cert_rows;
+    // s >= 2: D_s and D_{s-1} both live in X0 / X1 with the 16-byte pitch ldx
+    const int *Y = static_cast<const int *>((s & 1) ? I.X0 : I.X1);
+    const int *Xp = static_cast<const int *>((s & 1) ? I.X1 : I.X0);
+    int *plist = smem + R * ldx;
+    int *s_cnt = smem + (smem_words - 32);
+    const int rend = min(n, (t + 1) * kCertRows);
+    bool viol = false;
+    for (int r0 = t * kCertRows; r0 < rend && !viol; r0 += R) {
+        const int nr = min(R, rend - r0);
+        const int L = min(smem_words - R * ldx - 32, nr * n / 8);
+        if (tid == 0) {
+            *s_cnt = 0;
+            s_cnt[1] = ld_acquire(failed);  // another task of this level failed already: stop
+        }
+        __syncthreads();
+        if (s_cnt[1] != 0) {  // s_cnt[1] is not written again before the next barrier
+            viol = true;
+            break;
+        }
+        const int total = nr * ldx;  // padding columns (n .. ldx - 1) are never written: masked below
+        for (int e0 = 0; e0 < total; e0 += nthr * 16) {  // the same trip count in every lane
+            int4 y[4], x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {  // all loads in flight first
+                const int e = e0 + (u * nthr + tid) * 4;
+                y[u] = x[u] = make_int4(kInfI32, kInfI32, kInfI32, kInfI32);
+                if (e < total) {
+                    y[u] = __ldcg(reinterpret_cast<const int4 *>(Y + (long long)r0 * ldx + e));
+                    x[u] = __ldcg(reinterpret_cast<const int4 *>(Xp + (long long)r0 * ldx + e));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + (u * nthr + tid) * 4;
+                if (e < total) *reinterpret_cast<int4 *>(smem + e) = y[u];
+                const int col = e % ldx;  // a 16-byte vector stays inside its row (ldx % 4 == 0)
+                const int yy[4] = {y[u].x, y[u].y, y[u].z, y[u].w}, xx[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool low = col + c < n && yy[c] < xx[c];
+                    const unsigned m = __ballot_sync(0xffffffffu, low);
+                    int base = 0;
+                    if (lane == 0 && m) base = atomicAdd(s_cnt, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const int q = base + __popc(m & ((1u << lane) - 1u));
+                    if (low && q < L) plist[q] = e + c;
+                }
+            }
+        }
+        __syncthreads();
+        const int P = *s_cnt;
+        viol = P > L;
+        const int PP = viol ? 0 : P;
+        bool v = false;
+        for (int g0 = warp; g0 < PP; g0 += nwarp * 32) {  // warp w: entries w, w + warps, ...
+            const int p = g0 + nwarp * lane;
+            const int idx = p < PP ? plist[p] : 0;
+            const int np = min(32, (PP - g0 + nwarp - 1) / nwarp);
+            for (int t0 = 0; t0 < np; t0 += 8) {
+                int2 ev[8][2];  // the first 64 entries of 8 lists
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = __shfl_sync(0xffffffffu, idx, (t0 + u) & 31) % ldx;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int q = lane + 32 * h;
+                        ev[u][h] =
+                            (t0 + u < np && q < cap) ? __ldcg(I.lists + (long long)k * cap + q) : make_int2(0, 0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int ii = __shfl_sync(0xffffffffu, idx, (t0 + u) & 31);
+                    const int k = ii % ldx;
+                    const int *row = smem + (ii - k);
+                    const int yk = smem[ii];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (ev[u][h].x > 0) {
+                            const int sum = yk + ev[u][h].y;
+                            v |= sum < kClampI32 && sum < row[ev[u][h].x - 1];
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, ev[u][1].x, 31) > 0 && cap > 64) {  // a full head: the rest
+                        const int dk = __ldcg(I.deg + k);
+                        for (int q = 64 + lane; q < dk; q += 32) {
+                            const int2 e = __ldcg(I.lists + (long long)k * cap + q);
+                            const int sum = yk + e.y;
+                            v |= sum < kClampI32 && sum < row[e.x - 1];
+                        }
+                    }
+                }
+            }
+        }
+        viol = __syncthreads_or((viol || v) ? 1 : 0) != 0;  // also: the chunk's shared memory is free again
+    }
+    return viol;
 }
 
 // 128 x 128 transpose of a 4-byte matrix through shared memory.  With Cd /
@@ -129,6 +303,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
     __shared__ int s_task[4];
     __shared__ int s_flag;
     __shared__ int s_flag2;
+    __shared__ int s_closed;
     __shared__ int s_m;
     __shared__ long long s_wait;
     const int tid = threadIdx.x;
@@ -140,13 +315,18 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
             s_task[0] = w.x; s_task[1] = w.y; s_task[2] = w.z; s_task[3] = w.w;
             s_flag = 1;
             s_flag2 = 1;
+            s_closed = 0;
             s_m = 0x7FFFFFFF;
             s_wait = 0;
             if (w.x >= 0 && w.z > 0) {
-                // wait until every task of the previous level of this instance is done
+                // wait until every task of the previous level of this instance
+                // is done; a certificate task waits for the output tiles of its
+                // own level (claimed before it)
                 const BInst &I = p.insts[w.y];
-                const int need = tasks_at(I, w.z - 1) + (w.y == p.withhold_inst ? 1 : 0);
-                const int *cnt = p.done + I.done_base + w.z - 1;
+                const bool cert = w.x == kTaskCert;
+                const int need = (cert ? I.tiles_m * I.tiles_n : tasks_at(I, w.z - 1)) +
+                                 (w.y == p.withhold_inst ? 1 : 0);
+                const int *cnt = p.done + I.done_base + w.z - (cert ? 0 : 1);
                 const long long t0 = clock64();
                 while (ld_acquire(cnt) < need) {
                     if (ld_acquire(p.status) != 0) { s_task[0] = -1; break; }
@@ -158,17 +338,27 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                     __nanosleep(200);
                 }
                 s_wait = clock64() - t0;
-                if (s_task[0] >= 0 && I.kind == kInstApsp && w.z >= 2)
-                    s_flag = ld_acquire(p.changed + I.flag_base + w.z - 1);
-                if (s_task[0] >= 0 && I.kind == kInstApsp && w.z >= 3)
-                    s_flag2 = ld_acquire(p.changed + I.flag_base + w.z - 2);
-                if (s_task[0] >= 0 && I.kind == kInstApsp) s_m = ld_acquire(p.maxfin + I.flag_base + w.z - 1);
+                if (s_task[0] >= 0 && cert) {
+                    // squaring w.z changed something, and the lists hold every edge
+                    s_flag = ld_acquire(p.changed + I.flag_base + w.z);
+                    s_flag2 = ld_acquire(p.certfail + I.flag_base);
+                } else {
+                    if (s_task[0] >= 0 && I.kind == kInstApsp && w.z >= 2)
+                        s_flag = ld_acquire(p.changed + I.flag_base + w.z - 1);
+                    if (s_task[0] >= 0 && I.kind == kInstApsp && w.z >= 3)
+                        s_flag2 = ld_acquire(p.changed + I.flag_base + w.z - 2);
+                    if (s_task[0] >= 0 && I.kind == kInstApsp) s_m = ld_acquire(p.maxfin + I.flag_base + w.z - 1);
+                    // the certificate after squaring w.z - 1 held
+                    if (s_task[0] >= 0 && I.kind == kInstApsp && has_cert(I, w.z - 1))
+                        s_closed = ld_acquire(p.certfail + I.flag_base + w.z - 1) == 0 ? 1 : 0;
+                }
             }
         }
         __syncthreads();
         const int type = s_task[0], inst = s_task[1], level = s_task[2], tile = s_task[3];
         const int prev_changed = s_flag;
         const int prev_changed2 = s_flag2;
+        const int prev_closed = s_closed;
         const int prev_max = s_m;
         __syncthreads();
         if (type < 0) break;
@@ -187,6 +377,20 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                            reinterpret_cast<uint32_t *>(smem_raw), tid, forms ? I.Ad0 : nullptr,
                            forms ? I.U0 : nullptr, I.ldq, I.ldu,
                            (forms && I.kind == kInstApsp) ? p.maxfin + I.flag_base : nullptr);
+        } else if (type == kTaskLists) {
+            slot = BTAS_BATCH_SLOT_LISTS;
+            lists_task(I, tile, tid, p.certfail + I.flag_base);
+        } else if (type == kTaskCert) {
+            slot = BTAS_BATCH_SLOT_CERT;
+            // prev_changed: squaring `level` changed something; prev_changed2:
+            // a row had more edges than the lists hold.  Unchanged: the next
+            // level copies the fixpoint anyway.
+            if (prev_changed) {
+                const bool fail = prev_changed2 != 0 || cert_task(I, level, tile, reinterpret_cast<int *>(smem_raw),
+                                                                  batch_smem_words(), tid,
+                                                                  p.certfail + I.flag_base + level);
+                if (fail && tid == 0) atomicOr(p.certfail + I.flag_base + level, 1);
+            }
         } else if (type == kTaskCopy) {
             // n <= 2: D = W
             const int bm = (tile / I.tiles_n) * TT, bn = (tile % I.tiles_n) * TT;
@@ -233,6 +437,12 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
                     a.ldc = I.ldc;
                     copy_task_tile(small, a, bm, bn, tid);
                 }
+            } else if (prev_closed) {
+                // the certificate after squaring s - 1 held: D_{s-1} is the
+                // closure, so D_s = D_{s-1}, with no change; the next level
+                // copies it into D as after a converged squaring
+                slot = BTAS_BATCH_SLOT_APSP_DONE;
+                copy_task_tile(small, a, bm, bn, tid);
             } else if (I.use_u16 && 2LL * prev_max < BTAS_INF_U16) {
                 slot = BTAS_BATCH_SLOT_APSP_U16;
                 // every finite entry of D_{s-1} is < 0x7FFF / 2: the packed squaring is exact
@@ -325,7 +535,7 @@ __global__ void __launch_bounds__(BCfg::kThreads, BCfg::MINB) batch_kernel(const
 }
 
 
-int batch_kernel_smem() { return std::max(BCfg::kSmemBytes, kBT * (kBT + 1) * 4); }
+int batch_kernel_smem() { return batch_smem_words() * 4; }
 int batch_kernel_threads() { return BCfg::kThreads; }
 
 cudaError_t batch_kernel_prepare(int *ctas_per_sm) {
@@ -484,6 +694,12 @@ btas_status build_plan(btas_batch_t *b) {
     // BTAS_BATCH_NO_U16 keeps every batched squaring in int32
     const char *no16 = getenv("BTAS_BATCH_NO_U16");
     const int allow16 = (no16 && *no16 && atoi(no16) != 0) ? 0 : 1;
+    // The closure certificate for graphs from n = 256 (BTAS_BATCH_CERT_MIN_N;
+    // BTAS_BATCH_NO_CERT=1 turns it off): below that a squaring is one or
+    // two tiles, no dearer than the certificate tasks.
+    const char *no_cert = getenv("BTAS_BATCH_NO_CERT"), *cert_min = getenv("BTAS_BATCH_CERT_MIN_N");
+    const bool allow_cert = !(no_cert && *no_cert && atoi(no_cert) != 0);
+    const long long cert_min_n = (cert_min && *cert_min) ? atoll(cert_min) : 256;
     for (size_t i = 0; i < ninst; ++i) {
         BInst I = b->reqs[i].inst;
         I.tile = choose_tile(b, dev, I);
@@ -498,6 +714,15 @@ btas_status build_plan(btas_batch_t *b) {
                 I.use_u16 = allow16;
                 // X0, X1, Q0, Q1 (int32), Ad0, Ad1 (duplicated words), U0, U1 (uint16)
                 ws += 6 * al256((size_t)I.n * I.ldq * 4) + 2 * al256((size_t)I.n * I.ldu * 2);
+                // the certificate: rows per task that fit shared memory with their list of
+                // lowered entries; edge lists of up to min(256, max(32, n / 4)) edges per row
+                const int rows = std::min(16, (batch_smem_words() / 2) / (int)I.ldx);
+                I.cert = allow_cert && I.levels >= 3 && I.n >= cert_min_n && rows >= 1 ? 1 : 0;
+                if (I.cert) {
+                    I.cert_rows = rows;
+                    I.cap = (int)std::min(256LL, std::max(32LL, ((I.n / 4 + 31) / 32) * 32LL));
+                    ws += al256((size_t)I.n * I.cap * 8) + al256((size_t)I.n * 4);
+                }
             }
         } else if (!I.trans_b) {
             I.ldq = (I.k + 3) & ~3LL;
@@ -519,6 +744,8 @@ btas_status build_plan(btas_batch_t *b) {
                     const int nt = ((I.t0_rows + kBT - 1) / kBT) * ((I.t0_cols + kBT - 1) / kBT);
                     for (int t = 0; t < nt; ++t) tasks.push_back(make_int4(kTaskTranspose, oi, 0, t));
                 }
+                if (I.cert)
+                    for (int t = 0; t < list_tasks(I); ++t) tasks.push_back(make_int4(kTaskLists, oi, 0, t));
                 continue;
             }
             const int nt = I.tiles_m * I.tiles_n;
@@ -531,11 +758,18 @@ btas_status build_plan(btas_batch_t *b) {
                 for (int t = 0; t < nt; ++t) tasks.push_back(make_int4(kTaskGemm, oi, 1, t));
             }
         }
+        // the certificates of this level after every instance's tiles of it:
+        // each waits only for tasks claimed before it
+        for (int oi : order) {
+            const BInst &I = insts[oi];
+            if (I.kind == kInstApsp && has_cert(I, level))
+                for (int t = 0; t < cert_tasks(I); ++t) tasks.push_back(make_int4(kTaskCert, oi, level, t));
+        }
     }
     b->total = (int)tasks.size();
     const size_t task_bytes = al256(tasks.size() * sizeof(int4));
     const size_t inst_bytes = al256(ninst * sizeof(BInst));
-    b->counter_bytes = al256((size_t)(2 + 3 * counters) * 4);
+    b->counter_bytes = al256((size_t)(2 + 4 * counters) * 4);
     b->workspace_bytes = (long long)ws;
     const size_t prof_bytes = (b->flags & BTAS_BATCH_PROFILE) ? al256(2 * BTAS_BATCH_PROFILE_SLOTS * 8) : 0;
     b->dev_bytes = task_bytes + inst_bytes + b->counter_bytes + prof_bytes + ws;
@@ -563,6 +797,11 @@ btas_status build_plan(btas_batch_t *b) {
             I.Ad1 = reinterpret_cast<uint32_t *>(w + 5 * blk);
             I.U0 = reinterpret_cast<uint16_t *>(w + 6 * blk);
             I.U1 = reinterpret_cast<uint16_t *>(w + 6 * blk + al256((size_t)I.n * I.ldu * 2));
+            if (I.cert) {
+                char *l = w + 6 * blk + 2 * al256((size_t)I.n * I.ldu * 2);
+                I.lists = reinterpret_cast<int2 *>(l);
+                I.deg = reinterpret_cast<int *>(l + al256((size_t)I.n * I.cap * 8));
+            }
         } else if (I.kind == kInstGemm && !I.trans_b) {
             I.Q0 = w;
         }
@@ -578,6 +817,7 @@ btas_status build_plan(btas_batch_t *b) {
     p.done = b->d_counters + 2;
     p.changed = b->d_counters + 2 + counters;
     p.maxfin = b->d_counters + 2 + 2 * counters;
+    p.certfail = b->d_counters + 2 + 3 * counters;
     p.insts = d_insts;
     p.timeout_cycles = batch_timeout_cycles(dev);
     p.prof = b->d_prof;

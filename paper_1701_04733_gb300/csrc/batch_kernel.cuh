@@ -10,7 +10,15 @@ namespace btas {
 constexpr int kBT = 128;  // task tile edge (level-0 transposes, and the default output tile)
 constexpr int kBTSmall = 64;  // the smaller output tile an instance can take instead
 
-enum TaskType : int { kTaskTranspose = 0, kTaskApsp = 1, kTaskGemm = 2, kTaskCopy = 3, kTaskSquare = 4 };
+enum TaskType : int {
+    kTaskTranspose = 0,
+    kTaskApsp = 1,
+    kTaskGemm = 2,
+    kTaskCopy = 3,
+    kTaskSquare = 4,
+    kTaskLists = 5,  // APSP level 0: the edge lists of 32 rows of W
+    kTaskCert = 6    // APSP after squaring s (its level): the closure certificate over a block of rows
+};
 enum InstKind : int { kInstApsp = 0, kInstGemm = 1, kInstSquare = 2 };
 
 // One problem of a launch.  kInstApsp: a whole APSP solve (levels = S
@@ -52,6 +60,16 @@ struct BInst {
     int *maxfin_ptr;      // square: atomicMax of the largest finite output
     const int *maxfin_in; // square with use_u16 == 2: largest finite entry of the input,
                           // written before the launch
+    // APSP closure certificate (cert = 1): edge lists of W built at level 0
+    // (row i: (j + 1, W[i][j]) for its edges j != i in lists[i * cap ..],
+    // then zeros; deg[i] edges), and after each squaring s < levels a
+    // certificate over blocks of cert_rows rows; when it holds, squaring s + 1
+    // copies D_s forward instead of computing it
+    int cert;
+    int cap;
+    int cert_rows;
+    int2 *lists;
+    int *deg;
 };
 
 struct BatchParams {
@@ -61,6 +79,8 @@ struct BatchParams {
     int *done;
     int *changed;
     int *maxfin;        // per (instance, level): largest finite entry of D_level
+    int *certfail;      // per (instance, level): [0] a row has more edges than the lists hold;
+                        // [s] the certificate after squaring s failed
     int *status;
     const BInst *insts;
     long long timeout_cycles;

@@ -117,6 +117,55 @@ def test_batch_of_config_sizes(btas, oracle_mod):
     b.close()
 
 
+@pytest.mark.parametrize("tile", [None, "64"])
+def test_certificate_tasks(btas, oracle_mod, tile):
+    """The batched APSP's closure certificate: edge lists built at level 0,
+    certificate tasks after squarings 2 .. S - 1, and a certified level that
+    copies D forward instead of squaring.  Sparse random graphs (the
+    certificate passes), a dense one (its rows overflow the lists), a
+    directed path (it fails until the last squaring), for every size
+    (BTAS_BATCH_CERT_MIN_N=0): all equal the oracle and the run without it."""
+    import torch
+    graphs = []
+    for i, n in enumerate((40, 130, 257, 300, 513)):
+        graphs.append(gen.random_graph(gen.BASE_SEED, 1700 + i, n, 0.05, 1, 100))
+        graphs.append(gen.random_graph(gen.BASE_SEED, 1750 + i, n, min(1.0, 3.0 / n), 1, 10 ** 6))
+    graphs.append(gen.random_graph(gen.BASE_SEED, 1790, 300, 0.6, 1, 100))
+    P = np.full((150, 150), btas.INF_I32, np.int32)
+    np.fill_diagonal(P, 0)
+    P[np.arange(149), np.arange(1, 150)] = 4
+    graphs.append(P)
+    refs = [oracle_mod.floyd_warshall(W) for W in graphs]
+    outs = {}
+    for name, kv in (("on", {"BTAS_BATCH_CERT_MIN_N": "0"}), ("off", {"BTAS_BATCH_NO_CERT": "1"})):
+        os.environ.update(kv)
+        try:
+            with _tile(tile):
+                b = btas.Batch(profile=True)
+                Ds = []
+                for W in graphs:
+                    Wd = dev(W)
+                    D = torch.full_like(Wd, -7)
+                    b.add_apsp(Wd, D)
+                    Ds.append((Wd, D))
+                for _ in range(2):
+                    b.launch()
+                    b.wait()
+                outs[name] = [host(D) for _, D in Ds]
+                prof = b.profile()
+                b.close()
+        finally:
+            for k in kv:
+                del os.environ[k]
+        if name == "on":
+            assert prof["lists"]["tasks"] > 0 and prof["cert"]["tasks"] > 0
+        else:
+            assert prof["lists"]["tasks"] == 0 and prof["cert"]["tasks"] == 0
+    for W, ref, on, off in zip(graphs, refs, outs["on"], outs["off"]):
+        np.testing.assert_array_equal(on, ref, err_msg=f"n={W.shape[0]}")
+        np.testing.assert_array_equal(off, ref)
+
+
 def test_withheld_dependency_times_out(btas):
     """The host withholds one completion of instance 0: its tasks' bounded
     waits run out, the launch reports BTAS_ERR_TIMEOUT, and a later batch on
@@ -212,6 +261,9 @@ def test_profile_counts_every_task(btas, oracle_mod):
     assert prof["gemm_i32"]["tasks"] > 0 and prof["gemm_f32"]["tasks"] > 0
     assert prof["apsp_u16"]["tasks"] > 0  # weights <= 100: the packed squaring runs
     assert prof["square_u16"]["tasks"] == prof["square_i32"]["tasks"] == 0
+    # graphs of n >= 256 build edge lists and run certificate tasks
+    n_lists = 2 * sum((W.shape[0] + 31) // 32 for W, _, _ in apsp if W.shape[0] >= 256)
+    assert prof["lists"]["tasks"] == n_lists and prof["cert"]["tasks"] > 0
     for W, Wd, D in apsp:
         np.testing.assert_array_equal(host(D), oracle_mod.apsp_squaring(W))
     for A, B, Ad, Bd, C, sr, tb in gemm:
