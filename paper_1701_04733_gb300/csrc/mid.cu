@@ -2,10 +2,11 @@
 // cooperative launch.
 //
 // Between the one-block kernel (n <= 64) and the tiled product kernels (n >
-// 1792) a solve is bound by launches and host round trips: a few dozen
-// tiles per squaring cannot fill the GPU, and every squaring waits for the
-// previous one's change flag.  Here one cooperative grid runs the domain check and all
-// squarings, with ONE grid barrier per squaring.
+// 1792; for graphs that fit the edge lists below, n > 4096) a solve is bound
+// by launches and host round trips: a few dozen tiles per squaring cannot
+// fill the GPU, and every squaring waits for the previous one's change flag.
+// Here one cooperative grid runs the domain check and all squarings, with
+// ONE grid barrier per squaring.
 //
 // Work split.  Squaring s is a space of units (64 x 64 output tile, 32-wide
 // k-step), cut into equal contiguous shares, one per block ("stream-K"): a
@@ -39,6 +40,14 @@
 // carries its change flag and merged maximum to every block.  Every barrier
 // wait is bounded (clock64); on expiry the kernel records BTAS_ERR_TIMEOUT
 // and all blocks return.
+//
+// Edge lists (from n = 384, when the workspace has room).  Phase 0 also
+// builds per-row lists of W's edges.  When every row fits them, squaring 1
+// runs as sparse products over them (sparse_first), and after a squaring
+// that lowered few entries a closure certificate (certify) checks
+// X_s (x) W >= X_s at the lowered entries only; when it holds, squaring
+// s + 1 would change nothing and the solve stops.  Both give the results
+// and squaring counts of the literal sequence.
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
