@@ -16,9 +16,14 @@
 // An APSP squaring tile also stores its output transposed (through shared
 // memory), so the next squaring finds its B operand ready.  Early exit: the
 // first squaring whose predecessor changed nothing copies that fixpoint into
-// D, and the squarings after it do nothing (the result is unchanged).  The
-// launch (counter reset + kernel) is captured once in
-// a CUDA graph and replayed.
+// D, and the squarings after it do nothing (the result is unchanged).
+// Closure certificate (graphs of n >= 256): level 0 also builds W's edge
+// lists, and after squarings 2 .. S-1 certificate tasks, placed after all of
+// their level's tiles, check X_s (x) W >= X_s at the entries squaring s
+// lowered; when every block passes, squaring s + 1 copies X_s forward
+// instead of computing it, and the early exit finishes the solve.  The
+// launch (counter reset + kernel) is captured once in a CUDA graph and
+// replayed.
 #include <algorithm>
 #include <map>
 #include <tuple>
