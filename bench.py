@@ -45,7 +45,7 @@ LANES_PER_SM = 128
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="btas", choices=["btas", "reference"])
     p.add_argument("--n", type=int, default=N)
