@@ -385,6 +385,9 @@ __device__ __forceinline__ void block_rows(int n, int &r0, int &r1) {
 // prefix sums of their degrees (65 words) or a list of entries.
 constexpr int kRowsMax = 64;
 constexpr int kPfxWords = 128;
+// The 64 x 64 form reads 16 edge lists at once (measured against 8: 247.6 vs
+// 252.4 us per call at n = 1024, 153.3 vs 155.0 at 768, and 96.1 vs 93.9 at
+// 512, where the lists hold about 26 edges; both depths in one kernel spill).
 
 // Rows of a chunk: each takes its X row (ldx words) and, in the sparse
 // squaring, its own edge list (2 cap words).
@@ -703,7 +706,7 @@ __device__ __forceinline__ void mid_body(const MidArgs &a) {
         bool ch = false;
         int mx = 0, cnt = 0;
         if (sparse)
-            sparse_first<8, 2, 2>(a, out, smem, smem_words, ch, mx, cnt);
+            sparse_first<16, 2, 2>(a, out, smem, smem_words, ch, mx, cnt);
         else if (u16)
             squaring<true>(a, in, out, tiles, KS, u0, u1, sm, tid, ch, mx, cnt);
         else
@@ -718,7 +721,7 @@ __device__ __forceinline__ void mid_body(const MidArgs &a) {
         cur = (cur + 1) % 3;
         if (!changed && a.early) break;
         if ((v & kFlagBit) && lists_ok && a.early && s < a.S && certify_fits(a, smem_words)) {
-            const bool viol = certify<8, 2, 2>(a, in, prev, smem, smem_words);
+            const bool viol = certify<16, 2, 2>(a, in, prev, smem, smem_words);
             int any = 0, unused = 0;
             if (!grid_barrier(a, gen, viol, nullptr, any, unused)) return;
             if (!any) break;  // X_s is the closure: squaring s + 1 would change nothing
