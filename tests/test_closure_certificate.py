@@ -116,3 +116,41 @@ def test_a_lowered_entry_is_needed_to_fail():
         not (j != k and W[k, j] < BIG and X[i, k] + W[k, j] < X[i, j])
         for i in range(n) for k in range(n) if X[i, k] == X_prev[i, k] for j in range(n))
     assert unchanged_only and not certificate(W, X, X_prev)
+
+
+def minplus_clamped(A, B, T):
+    """The products' arithmetic: sums >= T become "no path" (BIG)."""
+    C = np.min(A[:, :, None] + B[None, :, :], axis=1)
+    return np.where(C >= T, BIG, C)
+
+
+def certificate_clamped(W, X, Xprev, T):
+    n = W.shape[0]
+    for i, k in zip(*np.nonzero(X < Xprev)):
+        for j in range(n):
+            s = X[i, k] + W[k, j]
+            if j != k and W[k, j] < BIG and s < T and s < X[i, j]:
+                return False
+    return True
+
+
+@pytest.mark.parametrize("T", [12, 25, 60])
+def test_certificate_under_the_clamp(T):
+    """With the clamp at a small threshold T, so that long paths saturate to
+    "no path" as they do above INF - 2^28 in the kernels, the certificate
+    still holds exactly when the next clamped squaring changes nothing."""
+    rng = np.random.default_rng(100 + T)
+    checked = 0
+    for _ in range(30):
+        n = int(rng.integers(5, 20))
+        W = graph(rng, n, float(rng.choice([0.1, 0.25, 0.5])), 9)
+        X_prev, X = W, minplus_clamped(W, W, T)
+        for _s in range(8):
+            nxt = minplus_clamped(X, X, T)
+            fixed = bool((nxt == X).all())
+            assert certificate_clamped(W, X, X_prev, T) == fixed
+            checked += 1
+            if fixed:
+                break
+            X_prev, X = X, nxt
+    assert checked > 30
