@@ -436,6 +436,17 @@ def test_edge_lists_and_certificate(btas, oracle_mod, n, wide, cooperative_from_
         np.testing.assert_array_equal(host(t), ref)
 
 
+@pytest.mark.parametrize("n,lists", [(256, False), (383, False), (384, True), (512, True)])
+def test_edge_lists_size_floor(btas, oracle_mod, n, lists):
+    """By default the cooperative kernel builds its edge lists from n = 384:
+    below it a squaring is bound by the grid barrier and the shortcuts do not
+    pay.  Distances equal the oracle's either way."""
+    W = gen.random_graph(gen.BASE_SEED, 1650 + n, n, 0.05, 1, 100)
+    D, info = btas.apsp(dev(W), info=True)
+    np.testing.assert_array_equal(host(D), oracle_mod.floyd_warshall(W))
+    assert ("sparse" in info["path"].split("+")) == lists, info["path"]
+
+
 def test_edge_lists_allocation_free(btas, oracle_mod, cooperative_from_3):
     """The allocation-free entry point gives the cooperative kernel room for
     its edge lists up to n = 1024: same distances and squarings as
